@@ -1,0 +1,394 @@
+"""Benchmark of the MFWH hot path on GB300.
+
+One step = one GMRES(20) cycle of the MFWH solve of the 1025^2, N_f = 8
+workload, from a zero initial guess: b = Pi(0) (one forced wave solve), 20
+Arnoldi steps on (I - S) V = b (one homogeneous wave solve, two Gram-Schmidt
+passes and a Givens update each), the solution update, and the Helmholtz
+residual check of the result.  Every wave solve is N_t leapfrog steps fused
+with the N_f filter accumulations and, on the last step, the B^{-1} solve.
+
+Metric: Gpts/s = interior grid points x time steps x wave solves / time.
+With --solve, one unrestarted GMRES solve to a relative residual of 1e-8 is
+timed as well (time to solution).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--solve]
+
+Multi-GPU (torchrun): every rank solves its own independent problem (seed
+offset by the rank); no data-path collective; weak scaling.
+"""
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+RESTART = 20
+TOL = 1e-8
+MAX_ITERS = RESTART          # one restart cycle per step
+SOLVE_MAX_ITERS = 800        # unrestarted solve for the time to solution
+WORD = 8  # float64
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--seed", type=int, default=2000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--solve", action="store_true", help="also time one unrestarted solve to 1e-8")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+# Nominal FP64 FMA rate of GB300 (1.25 TFLOP/s dense, the profiling recipe's table).
+FP64_PEAK_TFLOPS = 1.25
+
+
+def bytes_per_point_step(nf, forced):
+    """Algorithmic HBM bytes of one unblocked leapfrog+filter point-step:
+    read W^n, W^{n-1}, q_m (and f_m when forced), write W^{n+1}, q_m."""
+    return (3 + (3 if forced else 2) * nf) * WORD
+
+
+def flops_per_point_step(nf, forced, dim=2):
+    """FP64 flops: stencil adds (2 dim - 1), three FMAs for the leapfrog, N_f FMAs for the
+    filter, and N_f FMAs for the forcing when forced (an FMA counts 2)."""
+    fma = 3 + nf + (nf if forced else 0)
+    adds = 2 * dim - 1
+    return 2 * fma + adds
+
+
+def kernel_traffic(kernel_key):
+    """dram bytes per launch from the committed ncu summary, if it is for this source."""
+    path = os.path.join(ROOT, "profiles", "k_step_square1025_nf8.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as fh:
+        for line in fh:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("source_sha256") != kernel_key:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def kernel_source_key():
+    h = hashlib.sha256()
+    for f in ("wave.cu", "kernels.h"):
+        with open(os.path.join(ROOT, "paper_2507_23613_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(wl, budget_s=15.0):
+    """The oracle's map on the full grid for a bounded number of time steps (test
+    infrastructure, timed as it stands); returns Gpts/s and a description."""
+    from oracle import wave as W
+    import copy
+    g = W.Grid(wl.n, wl.length)
+    prob = W.make_problem(g, wl.omega, wl.forcing, cfl=wl.cfl, n_p=wl.n_p)
+    n_full = prob.setup.n_t
+    # calibrate on a few steps, then run a sample of about budget_s seconds
+    steps = 4
+    while True:
+        sub = copy.copy(prob)
+        sub.setup = copy.copy(prob.setup)
+        sub.setup.n_t = steps
+        sub.setup.w = prob.setup.w[:steps + 1]
+        t0 = time.perf_counter()
+        W.apply_Pi(sub, np.zeros_like(wl.forcing), forced=False)
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 4 or steps >= n_full:
+            break
+        steps = min(n_full, int(steps * max(2.0, budget_s / max(dt, 1e-3))))
+    pts = wl.interior_points * steps
+    return {"value": pts / dt / 1e9, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
+            "sample": (f"numpy oracle, homogeneous map, {steps} of {n_full} leapfrog+filter steps "
+                       f"on the full {wl.n[0] + 1}x{wl.n[1] + 1} grid, N_f={wl.nf}, "
+                       f"{dt:.1f} s, single-threaded numpy")}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2507_23613_gb300 import inputs
+    wl = inputs.square_large(args.seed)
+    per = []
+    for _ in range(args.warmup):
+        cpu_baseline(wl, budget_s=5.0)
+    info = None
+    for _ in range(args.steps):
+        info = cpu_baseline(wl, budget_s=10.0)
+        per.append(info["value"])
+    value = statistics.mean(per)
+    line = {"impl": "reference", "metric": "stencil Gpts/s (+N_f filters)", "value": value,
+            "unit": "Gpts/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(wl, None),
+            "cpu_baseline": {**info, "value": value},
+            "e2e": {"value": value, "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(wl, n_t):
+    return {"workload": f"square{wl.n[0] + 1}x{wl.n[1] + 1}_nf{wl.nf}_np{wl.n_p}_gmres{RESTART}_cycle",
+            "step": "one GMRES(20) cycle from zero: b = Pi(0), 20 Arnoldi steps, update, residual check",
+            "grid": [wl.n[0] + 1, wl.n[1] + 1], "nf": wl.nf, "n_p": wl.n_p, "n_t": n_t,
+            "omega_band": [10.0, 60.0], "gaussian_b": 400.0, "cfl": wl.cfl,
+            "restart": RESTART, "tol": TOL, "precision": "fp64",
+            "l2": "working set (forcing, accumulators, Krylov basis: > 1 GB) is larger than L2"}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_2507_23613_gb300 as M
+    from paper_2507_23613_gb300 import build, inputs
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    M._lib.load()
+
+    wl = inputs.square_large(args.seed + rank)
+    stream = torch.cuda.Stream()
+    f_dev = torch.from_numpy(wl.forcing).cuda()
+    solver = M.Solver(wl.n, wl.length, wl.omega, f_dev, stream=stream.cuda_stream,
+                      n_p=wl.n_p, cfl=wl.cfl)
+    n_t = solver.setup["n_t"]
+    N = wl.forcing.size
+    v = torch.zeros(wl.forcing.shape, dtype=torch.float64, device="cuda")
+
+    def one_step():
+        with torch.cuda.stream(stream):
+            v.zero_()
+        info = solver.solve_gmres(v, restart=RESTART, tol=TOL, max_iters=MAX_ITERS,
+                                  raise_on_error=False)
+        if info["status"] not in (M._lib.OK, M._lib.ERR_NOT_CONVERGED):
+            raise M.MfwhError(info["status"], "GMRES cycle failed")
+        ms, step_launches, launches = solver.last_timing()
+        return info, ms, step_launches, launches + 1
+
+    for _ in range(max(3, args.warmup)):
+        one_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    infos = []
+    for _ in range(args.steps):
+        infos.append(one_step())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    if dist:
+        dist.barrier()
+
+    pi_apps = sum(i[0]["pi_applications"] for i in infos)
+    forced_apps = sum(1 for _ in infos)          # one forced map (b) per solve
+    homog_apps = pi_apps - forced_apps
+    pts_steps = wl.interior_points * n_t * pi_apps
+    step_ms_total = sum(i[1] for i in infos)
+    step_launches = sum(i[2] for i in infos)
+    launches = sum(i[3] for i in infos)
+    alg_bytes = wl.interior_points * n_t * (forced_apps * bytes_per_point_step(wl.nf, True)
+                                           + homog_apps * bytes_per_point_step(wl.nf, False))
+    alg_flops = wl.interior_points * n_t * (forced_apps * flops_per_point_step(wl.nf, True)
+                                           + homog_apps * flops_per_point_step(wl.nf, False))
+    achieved_gbs = alg_bytes / (step_ms_total * 1e-3) / 1e9
+    achieved_tf = alg_flops / (step_ms_total * 1e-3) / 1e12
+    hbm_peak, peak_kind = peaks()
+
+    # whole-job numbers: max time over ranks, points summed over ranks
+    t_max = elapsed_ms
+    total_pts = pts_steps
+    if dist:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        p = torch.tensor([float(pts_steps)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(p)
+        total_pts = float(p.item())
+    value = total_pts / (t_max * 1e-3) / 1e9
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        f_host = torch.from_numpy(wl.forcing).pin_memory()
+        v_host = torch.zeros(wl.forcing.shape, dtype=torch.float64).pin_memory()
+        e2e_steps = max(1, args.steps)
+        e_pts = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            v_host.zero_()
+            solver.set_forcing(f_host)
+            info = solver.solve_gmres(v_host.numpy(), restart=RESTART, tol=TOL, max_iters=MAX_ITERS,
+                                      raise_on_error=False)
+            e_pts += wl.interior_points * n_t * info["pi_applications"]
+        e_s = time.perf_counter() - t0
+        e2e = {"value": e_pts / e_s / 1e9, "unit": "Gpts/s",
+               "h2d_bytes_per_step": 2 * N * WORD, "d2h_bytes_per_step": N * WORD,
+               "note": "forcing and initial guess copied from pinned host memory, solution read back, every step"}
+
+    tts = None
+    if args.solve:
+        with torch.cuda.stream(stream):
+            v.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = solver.solve_gmres(v, restart=SOLVE_MAX_ITERS, tol=TOL, max_iters=SOLVE_MAX_ITERS,
+                                  raise_on_error=False)
+        tts = {"seconds": round(time.perf_counter() - t0, 3), "tol": TOL, "restart": "none",
+               "converged": info["status"] == M._lib.OK, "iterations": info["iterations"],
+               "rel_residual": info["rel_residual"],
+               "max_helmholtz_residual": float(np.max(info["helmholtz_residual"]))}
+
+    if rank != 0:
+        return
+    traffic = kernel_traffic(kernel_source_key())
+    homog_launch_bytes = wl.interior_points * bytes_per_point_step(wl.nf, False)
+    t_hbm = alg_bytes / (hbm_peak * 1e9)
+    t_alu = alg_flops / (FP64_PEAK_TFLOPS * 1e12)
+    if t_hbm >= t_alu:
+        roof = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved_gbs / hbm_peak, 4)}
+    else:
+        roof = {"bound": "alu", "achieved": round(achieved_tf, 4), "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": round(achieved_tf / FP64_PEAK_TFLOPS, 4)}
+    roof.update({"traffic": traffic, "kernel": "k_step/k_last (leapfrog + N_f filters)",
+                 "peak_source": peak_kind,
+                 "alg_bytes_per_launch": round(alg_bytes / max(step_launches, 1)),
+                 "avg_launch_us": round(step_ms_total * 1e3 / max(step_launches, 1), 2),
+                 "hbm_frac": round(achieved_gbs / hbm_peak, 4),
+                 "fp64_alu_frac": round(achieved_tf / FP64_PEAK_TFLOPS, 4)})
+    line = {
+        "metric": "stencil Gpts/s (+N_f filters)", "value": round(value, 3), "unit": "Gpts/s",
+        "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
+        "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(wl, n_t),
+        "roofline": roof,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "e2e": e2e,
+        "cycle": {"pi_applications_per_step": pi_apps / args.steps,
+                  "gmres_iterations_per_step": sum(i[0]["iterations"] for i in infos) / args.steps,
+                  "rel_residual_after_cycle": infos[-1][0]["rel_residual"],
+                  "max_helmholtz_residual": float(np.max(infos[-1][0]["helmholtz_residual"]))},
+        "time_to_solution": tts,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * mfwh.h -- C ABI of libmfwh: the Multi-Frequency WaveHoltz (MFWH) hot path on
+ * one NVIDIA GB300 (sm_103a).
+ *
+ * MFWH (arXiv 2507.23613) computes N_f Helmholtz solutions
+ *     L u_m + omega_m^2 u_m = f_m,  L = c^2 Delta,  u_m = 0 on the boundary
+ * (eq. MultipleHelmholtz) by iterating a map Pi that solves ONE wave equation
+ * forced by sum_m f_m cos(omega~_m t) (eq. waveEqnCompositeForcings, eq.
+ * WaveScheme) and applies N_f time filters to it (eq. pDefQ), followed by an
+ * N_f x N_f solve with the filter matrix B at every grid point (eq. filterA,
+ * eq. waveHoltzMatrixIteration).  The fixed point of Pi is the discrete
+ * Helmholtz solution (eq. discreteHelmholtz); GMRES on A = I - S accelerates
+ * it (eq. krylovSystem).  Discretisation: uniform Cartesian grid in 2D or 3D,
+ * second-order Laplacian, explicit leapfrog in time (alpha = 0, beta = 1),
+ * Dirichlet data zero.
+ *
+ * Conventions for every call
+ *   - Grid functions are dense float64 arrays over ALL grid points, boundary
+ *     included, x fastest: index ((k * (ny+1)) + j) * (nx+1) + i.  A stack of
+ *     N_f grid functions is N_f such arrays back to back ([N_f][points]).
+ *   - Boundary values of inputs are ignored (treated as 0); outputs are 0 there.
+ *   - Pointers documented as "host or device" may point to either; the library
+ *     asks the CUDA driver which and copies as needed.  Pointers documented as
+ *     "device" must be device memory of the handle's current device.
+ *   - The caller owns every buffer it passes in; the handle owns its own
+ *     workspace, allocated in mfwh_create and released in mfwh_destroy.
+ *   - Every call returns an mfwh_status; on failure mfwh_last_error() gives a
+ *     message (thread-local, valid until the next call on that thread).
+ *   - A handle may be used from one host thread at a time.
+ */
+#ifndef MFWH_H
+#define MFWH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MFWH_MAX_NF 16  /* largest number of frequencies per problem */
+
+typedef enum {
+  MFWH_OK = 0,
+  MFWH_ERR_INVALID_ARG = 1,   /* bad size, ordering, mode or pointer */
+  MFWH_ERR_SINGULAR = 2,      /* B or the optimiser's constraint matrix G is (near) singular */
+  MFWH_ERR_CUDA = 3,          /* a CUDA runtime call failed (message has the CUDA error) */
+  MFWH_ERR_NOMEM = 4,         /* device or host allocation failed */
+  MFWH_ERR_NOT_CONVERGED = 5, /* GMRES reached max_iters above the tolerance */
+  MFWH_ERR_SPURIOUS = 6,      /* GMRES converged but the Helmholtz residual check failed */
+  MFWH_ERR_NONFINITE = 7      /* NaN or Inf in an iterate or residual */
+} mfwh_status;
+
+enum { MFWH_FILTER_OPTIMIZED = 0, MFWH_FILTER_TRADITIONAL = 1, MFWH_FILTER_USER = 2 };
+enum { MFWH_PREC_FP64 = 0 };
+enum { MFWH_C_CONST = 0, MFWH_C_TWO_LAYER = 1 };
+
+typedef struct mfwh_handle_s* mfwh_handle_t;
+
+/* Problem statement (Section "Governing equations", eq. MultipleHelmholtz,
+ * eq. gaussianSource inputs; time-step recipe of Section "Time-step determination"). */
+typedef struct {
+  int dim;                   /* 2 or 3 */
+  int64_t n[3];              /* cells per axis, x first; points per axis = n+1; n >= 2 */
+  double length[3];          /* domain extent per axis (> 0); h_i = length_i / n_i */
+  int nf;                    /* number of frequencies, 1..MFWH_MAX_NF */
+  const double* omega;       /* host, [nf], 0 < omega_1 < ... < omega_nf */
+  const double* forcing;     /* host or device, [nf][points] values of f_m at the grid points;
+                                copied into the handle by mfwh_create (may be NULL: zero forcing) */
+  int c_mode;                /* MFWH_C_CONST: c = c_lo everywhere;
+                                MFWH_C_TWO_LAYER: c = c_lo where x_axis < interface, c_hi elsewhere */
+  double c_lo, c_hi;         /* wave speeds (> 0) */
+  double interface;          /* coordinate of the layer interface (TWO_LAYER) */
+  int layer_axis;            /* 0 = x, 1 = y, 2 = z (TWO_LAYER) */
+  int n_p;                   /* N_p: periods of the longest period integrated (>= 1) */
+  double cfl;                /* fraction (0, 1] of the explicit von Neumann step limit */
+  int filter_mode;           /* MFWH_FILTER_* */
+  const double* user_params; /* host, [nf][3] (a, c, s) when filter_mode == MFWH_FILTER_USER */
+  int n_delta;               /* N_delta of eq. LambdaRange (paper: 20) */
+  double c_delta;            /* c_delta of eq. LambdaRange (paper: 2) */
+  int precision;             /* MFWH_PREC_FP64 */
+} mfwh_problem;
+
+/* Everything the set-up derives from a problem (Algorithm 1, first two lines;
+ * eq. omegaImplicit, eq. TbarDef, eq. DefNI, Algorithm 2, eq. filterA). */
+typedef struct {
+  double dt;                                /* time step */
+  int n_t;                                  /* N_t: steps per wave solve */
+  int nf;
+  double h[3];
+  double omega_tilde[MFWH_MAX_NF];          /* adjusted frequencies omega~_m */
+  int n_pm[MFWH_MAX_NF];                    /* N_{p,m} */
+  double t_fm[MFWH_MAX_NF];                 /* T~_{f,m} = N_{p,m} 2 pi / omega~_m */
+  double params[MFWH_MAX_NF][3];            /* filter parameters (a, c, s) per frequency */
+  double B[MFWH_MAX_NF][MFWH_MAX_NF];       /* B[m][j] = sum_n w_{n,m} cos(omega~_j t^n) */
+  double B_inv[MFWH_MAX_NF][MFWH_MAX_NF];
+  double lam_max;                           /* right end of Lambda (optimised filters) */
+  int n_lambda;                             /* N_lambda (optimised filters) */
+  int64_t points;                           /* grid points per grid function */
+  int64_t interior_points;
+} mfwh_setup;
+
+/* Outcome of mfwh_solve_gmres. */
+typedef struct {
+  int iterations;              /* Arnoldi steps taken (one homogeneous Pi each) */
+  int pi_applications;         /* all applications of Pi (forced and homogeneous) */
+  int restarts;                /* restart cycles started */
+  double rel_residual;         /* final ||b - A x||_2 / ||b||_2 (Arnoldi estimate) */
+  double helmholtz_residual[MFWH_MAX_NF]; /* r_h^{(m)} of the returned solution (eq. errorAndResid) */
+  int history_len;             /* entries written to history (<= history_capacity) */
+  int history_capacity;        /* set by the caller: capacity of history */
+  double* history;             /* host, caller-owned, may be NULL: residual after each Arnoldi step */
+} mfwh_solve_info;
+
+/* ---- host-only set-up arithmetic (no GPU needed) ------------------------------ */
+
+/* Full set-up of a problem without touching a GPU (time step, omega~, N_{p,m},
+ * quadrature, filter parameters, B and B^{-1}).  Time step reading: dt_stab =
+ * 1/(c_max sqrt(sum 1/h_i^2)); N_t = ceil(N_p (2 pi/omega_1) / (cfl dt_stab));
+ * dt = 2 sin(pi N_p / N_t) / omega_1 so that omega~_1 N_t dt = 2 pi N_p.
+ * Returns MFWH_ERR_SINGULAR if B has 1-norm condition number > 1e12 or the
+ * optimiser's constraint matrix G one > 1e15. */
+mfwh_status mfwh_plan(const mfwh_problem* prob, mfwh_setup* out);
+
+/* Filter weights w_{n,m} = (2/T~_{f,m}) sigma_{n,m} K(omega~_m t^n; p_m) (eq. pDefQ)
+ * of a planned problem, written to w_out[(n_t+1) * nf] (host, row n, column m). */
+mfwh_status mfwh_plan_weights(const mfwh_problem* prob, double* w_out, int64_t capacity);
+
+/* Adjusted frequencies of eq. omegaImplicit for scheme weights (alpha, beta):
+ * out[m] = acos((1 - beta/2 (omega_m dt)^2) / (1 + alpha (omega_m dt)^2)) / dt.  Host arrays. */
+mfwh_status mfwh_adjusted_frequency(int nf, const double* omega, double dt,
+                                    double alpha, double beta, double* out);
+
+/* Algorithm 2 (optParameters), discrete form: least-squares filter parameters for
+ * frequencies omega[nf] (already adjusted if desired) integrated over N_t equal
+ * steps of T_f = max_m T_{f,m} with the trapezoid weights of eq. DefNI.
+ * params_out: host [nf][3] (a~, c~, s~).  lam_max / n_lambda may be NULL. */
+mfwh_status mfwh_opt_parameters(int nf, const double* omega, int n_p, int n_t,
+                                int n_delta, double c_delta, double* params_out,
+                                double* lam_max, int* n_lambda);
+
+/* ---- device calls ------------------------------------------------------------ */
+
+/* Plan the problem and allocate its device workspace on the current CUDA device.
+ * stream: cudaStream_t all work is issued on (NULL = legacy default stream). */
+mfwh_status mfwh_create(const mfwh_problem* prob, void* stream, mfwh_handle_t* out);
+
+/* Replace the forcing f_m: host or device [nf][points].  Ordered on the handle's stream. */
+mfwh_status mfwh_set_forcing(mfwh_handle_t h, const double* forcing);
+
+/* One application of the MFWH map (the loop body of Algorithm 1):
+ * v_out = Pi(v_in) = B^{-1} q(v_in) with the forcing (forced = 1), or
+ * v_out = S v_in without it (forced = 0).  v_in may be NULL (zero initial data).
+ * v_in, v_out: device [nf][points]; they may alias.  Asynchronous on the stream. */
+mfwh_status mfwh_apply_Pi(mfwh_handle_t h, const double* v_in, double* v_out, int forced);
+
+/* Fixed-point iteration of Algorithm 1: v <- Pi(v), `iters` times.
+ * v: host or device [nf][points], in: V^0, out: V^iters.  Synchronous. */
+mfwh_status mfwh_solve_fpi(mfwh_handle_t h, int iters, double* v);
+
+/* Restarted GMRES(restart), 1 <= restart <= 1023 (restart >= max_iters: no
+ * restart, as in the paper), on (I - S) v = Pi(0) (eq. discreteMFWHmapping,
+ * eq. krylovSystem): no preconditioner, classical Gram-Schmidt applied twice
+ * for the Arnoldi vectors in FP64 on the device, Hessenberg least squares by Givens rotations on the host, stopping
+ * when the Arnoldi residual estimate ||b - A v||_2 / ||b||_2 < tol.
+ * v: host or device [nf][points]; in: initial guess (warm start), out: solution.
+ * The Krylov basis ((restart+1) * nf * points doubles) is allocated on the
+ * first call that needs it and kept by the handle.
+ * After convergence the Helmholtz residual r_h (eq. errorAndResid) is checked:
+ * if max_m r_h^{(m)} > spurious_tol (> 0) the call returns MFWH_ERR_SPURIOUS
+ * (convergence to a non-solution, Section "Acceleration by Krylov methods");
+ * spurious_tol <= 0 skips the check.  info may be NULL.  Synchronous. */
+mfwh_status mfwh_solve_gmres(mfwh_handle_t h, int restart, double tol, int max_iters,
+                             double spurious_tol, double* v, mfwh_solve_info* info);
+
+/* Helmholtz residual r_h^{(m)} = max_int |f_m - (L_h + omega_m^2) v_m| / max_int |f_m|
+ * (eq. errorAndResid, with +omega^2 as in eq. MultipleHelmholtz).
+ * v: host or device [nf][points]; r_out: host [nf].  Synchronous. */
+mfwh_status mfwh_residual(mfwh_handle_t h, const double* v, double* r_out);
+
+/* Copy of the handle's set-up. */
+mfwh_status mfwh_get_setup(mfwh_handle_t h, mfwh_setup* out);
+
+/* Timing of the most recent mfwh_apply_Pi / mfwh_solve_fpi / mfwh_solve_gmres /
+ * mfwh_residual call, measured with CUDA events on the handle's stream:
+ * step_ms = device time of the leapfrog+filter step kernels (the N_t launches of
+ * every Pi application, the initial W^0 kernel excluded), step_launches = how
+ * many such launches, total_launches = every kernel the call launched.  For
+ * mfwh_apply_Pi the call synchronises the stream to read the events.  Any
+ * output pointer may be NULL. */
+mfwh_status mfwh_last_timing(mfwh_handle_t h, double* step_ms, int64_t* step_launches,
+                             int64_t* total_launches);
+
+/* Release the handle and its device workspace (waits for its stream). */
+void mfwh_destroy(mfwh_handle_t h);
+
+const char* mfwh_last_error(void);
+const char* mfwh_status_string(mfwh_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MFWH_H */

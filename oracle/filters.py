@@ -122,6 +122,7 @@ class OptResult:
     n_lambda: int           # number of midpoint quadrature points
     t_f: float              # N_p T_1
     n_pm: np.ndarray        # N_{p,m}
+    cond_M: float = float("nan")   # 2-norm condition number of the least-squares matrix M
 
 
 class _QuadratureBasis:
@@ -192,7 +193,7 @@ def _optimise(basis, omega, n_pm, n_delta, c_delta):
     x_a = np.linalg.lstsq(M, m0, rcond=None)[0]
     y = np.linalg.solve(G, z - H @ x_a)
     params = np.stack([x_a, y[:nf], y[nf:]], axis=1)
-    return params, lam_max, n_lambda
+    return params, lam_max, n_lambda, float(np.linalg.cond(M))
 
 
 def opt_parameters_discrete(omega, n_p, n_t, n_delta=20, c_delta=2.0):
@@ -211,8 +212,8 @@ def opt_parameters_discrete(omega, n_p, n_t, n_delta=20, c_delta=2.0):
     t = np.arange(n_t + 1) * dt
     basis = _QuadratureBasis(omega, t_fm, [t] * omega.size,
                              [sigma[:, m] for m in range(omega.size)])
-    params, lam_max, n_lambda = _optimise(basis, omega, n_pm, n_delta, c_delta)
-    return OptResult(params, lam_max, n_lambda, t_f, n_pm)
+    params, lam_max, n_lambda, cond_m = _optimise(basis, omega, n_pm, n_delta, c_delta)
+    return OptResult(params, lam_max, n_lambda, t_f, n_pm, cond_m)
 
 
 def opt_parameters_continuous(omega, n_p, n_delta=20, c_delta=2.0, n_gauss=512):
@@ -228,8 +229,8 @@ def opt_parameters_continuous(omega, n_p, n_delta=20, c_delta=2.0, n_gauss=512):
     nodes = [0.5 * tm * (x + 1.0) for tm in t_fm]
     weights = [0.5 * tm * wx for tm in t_fm]
     basis = _QuadratureBasis(omega, t_fm, nodes, weights)
-    params, lam_max, n_lambda = _optimise(basis, omega, n_pm, n_delta, c_delta)
-    return OptResult(params, lam_max, n_lambda, t_f, n_pm)
+    params, lam_max, n_lambda, cond_m = _optimise(basis, omega, n_pm, n_delta, c_delta)
+    return OptResult(params, lam_max, n_lambda, t_f, n_pm, cond_m)
 
 
 # ---------------------------------------------------------------------------
@@ -294,6 +295,7 @@ class Setup:
     params: np.ndarray       # (N_f, 3)
     w: np.ndarray            # (N_t+1, N_f) filter weights
     B: np.ndarray            # (N_f, N_f)
+    cond_M: float = float("nan")   # conditioning of Algorithm 2's least-squares matrix (optimised mode)
 
 
 def make_setup(omega, h, c_max, cfl=0.5, n_p=1, filter_mode=FILTER_OPTIMIZED,
@@ -311,12 +313,14 @@ def make_setup(omega, h, c_max, cfl=0.5, n_p=1, filter_mode=FILTER_OPTIMIZED,
     omega_t = adjusted_frequency(omega, dt, EXPLICIT)
     n_pm, t_fm, _ = period_counts(omega_t, n_p)
     sigma = trapezoid_weights(n_t, dt, t_fm)
+    cond_m = float("nan")
     if filter_mode == FILTER_OPTIMIZED:
-        params = opt_parameters_discrete(omega_t, n_p, n_t, n_delta, c_delta).params
+        opt = opt_parameters_discrete(omega_t, n_p, n_t, n_delta, c_delta)
+        params, cond_m = opt.params, opt.cond_M
     elif filter_mode == FILTER_TRADITIONAL:
         params = traditional_parameters(omega_t, dt)
     else:
         params = np.asarray(user_params, dtype=np.float64).reshape(omega.size, 3)
     w = filter_weights(omega_t, dt, n_t, sigma, t_fm, params)
     B = filter_matrix(w, omega_t, dt)
-    return Setup(dt, n_t, omega, omega_t, n_pm, t_fm, sigma, params, w, B)
+    return Setup(dt, n_t, omega, omega_t, n_pm, t_fm, sigma, params, w, B, cond_m)

@@ -1,0 +1,187 @@
+"""GB300-native Multi-Frequency WaveHoltz (arXiv 2507.23613): Python binding of libmfwh.
+
+The compute path is the CUDA library libmfwh.so (include/mfwh.h); this package
+only marshals arguments.  Device buffers are torch CUDA tensors (float64,
+contiguous), host buffers numpy float64 arrays; both hold N_f grid functions
+over all grid points, x fastest ([N_f, (nz+1,) ny+1, nx+1]).
+"""
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import MfwhError  # noqa: F401
+
+
+def _as_ptr(x):
+    """Raw pointer of a torch tensor or numpy array (float64, contiguous)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        import torch
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise TypeError("expected a contiguous float64 tensor")
+        return C.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
+            raise TypeError("expected a C-contiguous float64 array")
+        return C.c_void_p(x.ctypes.data)
+    raise TypeError(f"unsupported buffer type {type(x)!r}")
+
+
+def _dptr(arr):
+    return arr.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def make_problem(n, length, omega, forcing=None, c_lo=1.0, c_hi=None, interface=0.5,
+                 layer_axis=2, n_p=1, cfl=0.5, filter_mode=_lib.FILTER_OPTIMIZED,
+                 user_params=None, n_delta=20, c_delta=2.0):
+    """Fill an mfwh_problem.  Returned keep-alive list holds the arrays it points to."""
+    p = _lib.Problem()
+    p.dim = len(n)
+    for a in range(3):
+        p.n[a] = int(n[a]) if a < len(n) else 0
+        p.length[a] = float(length[a]) if a < len(n) else 0.0
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    p.nf = om.size
+    p.omega = _dptr(om)
+    keep = [om]
+    if forcing is not None:
+        ptr = _as_ptr(forcing)
+        p.forcing = C.cast(ptr, C.POINTER(C.c_double))
+        keep.append(forcing)
+    p.c_mode = _lib.C_CONST if c_hi is None else _lib.C_TWO_LAYER
+    p.c_lo = float(c_lo)
+    p.c_hi = float(c_hi if c_hi is not None else c_lo)
+    p.interface = float(interface)
+    p.layer_axis = int(layer_axis)
+    p.n_p = int(n_p)
+    p.cfl = float(cfl)
+    p.filter_mode = int(filter_mode)
+    if user_params is not None:
+        up = np.ascontiguousarray(user_params, dtype=np.float64).reshape(-1)
+        p.user_params = _dptr(up)
+        keep.append(up)
+    p.n_delta = int(n_delta)
+    p.c_delta = float(c_delta)
+    p.precision = _lib.PREC_FP64
+    return p, keep
+
+
+def plan(problem):
+    s = _lib.Setup()
+    _lib.check(_lib.load().mfwh_plan(C.byref(problem), C.byref(s)))
+    return s
+
+
+def plan_weights(problem, n_t, nf):
+    w = np.zeros((n_t + 1) * nf)
+    _lib.check(_lib.load().mfwh_plan_weights(C.byref(problem), _dptr(w), w.size))
+    return w.reshape(n_t + 1, nf)
+
+
+def adjusted_frequency(omega, dt, alpha=0.0, beta=1.0):
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    out = np.zeros_like(om)
+    _lib.check(_lib.load().mfwh_adjusted_frequency(om.size, _dptr(om), dt, alpha, beta, _dptr(out)))
+    return out
+
+
+def opt_parameters(omega, n_p, n_t, n_delta=20, c_delta=2.0):
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    out = np.zeros((om.size, 3))
+    lam = C.c_double()
+    nl = C.c_int()
+    _lib.check(_lib.load().mfwh_opt_parameters(om.size, _dptr(om), n_p, n_t, n_delta, c_delta,
+                                               _dptr(out), C.byref(lam), C.byref(nl)))
+    return out, lam.value, nl.value
+
+
+def setup_arrays(s):
+    """numpy views of an mfwh_setup's tables, trimmed to nf."""
+    nf = s.nf
+    return {
+        "dt": s.dt, "n_t": s.n_t, "nf": nf,
+        "omega_tilde": np.array(s.omega_tilde[:nf]),
+        "n_pm": np.array(s.n_pm[:nf]),
+        "t_fm": np.array(s.t_fm[:nf]),
+        "params": np.array([[s.params[m][k] for k in range(3)] for m in range(nf)]),
+        "B": np.array([[s.B[m][j] for j in range(nf)] for m in range(nf)]),
+        "B_inv": np.array([[s.B_inv[m][j] for j in range(nf)] for m in range(nf)]),
+        "lam_max": s.lam_max, "n_lambda": s.n_lambda,
+        "points": s.points, "interior_points": s.interior_points,
+    }
+
+
+class Solver:
+    """One MFWH problem on the current CUDA device (an mfwh_handle_t)."""
+
+    def __init__(self, n, length, omega, forcing=None, stream=None, **kw):
+        lib = _lib.load()
+        self._problem, self._keep = make_problem(n, length, omega, forcing, **kw)
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self._handle = C.c_void_p()
+        _lib.check(lib.mfwh_create(C.byref(self._problem), C.c_void_p(stream), C.byref(self._handle)))
+        self._keep = None
+        self.nf = len(omega)
+        s = _lib.Setup()
+        _lib.check(lib.mfwh_get_setup(self._handle, C.byref(s)))
+        self.setup = setup_arrays(s)
+
+    def close(self):
+        if getattr(self, "_handle", None) and self._handle.value:
+            _lib.load().mfwh_destroy(self._handle)
+            self._handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_forcing(self, forcing):
+        _lib.check(_lib.load().mfwh_set_forcing(self._handle, _as_ptr(forcing)))
+
+    def mfwh_apply_Pi(self, v_in, v_out, forced=True):
+        _lib.check(_lib.load().mfwh_apply_Pi(self._handle, _as_ptr(v_in), _as_ptr(v_out), int(forced)))
+
+    apply_Pi = mfwh_apply_Pi
+
+    def solve_fpi(self, v, iters):
+        _lib.check(_lib.load().mfwh_solve_fpi(self._handle, int(iters), _as_ptr(v)))
+
+    def solve_gmres(self, v, restart=20, tol=1e-8, max_iters=1000, spurious_tol=0.0,
+                    history=512, raise_on_error=True):
+        info = _lib.SolveInfo()
+        hist = np.zeros(max(history, 1))
+        info.history_capacity = history
+        info.history = _dptr(hist)
+        st = _lib.load().mfwh_solve_gmres(self._handle, int(restart), float(tol), int(max_iters),
+                                          float(spurious_tol), _as_ptr(v), C.byref(info))
+        if raise_on_error:
+            _lib.check(st)
+        out = {
+            "status": st,
+            "iterations": info.iterations,
+            "pi_applications": info.pi_applications,
+            "restarts": info.restarts,
+            "rel_residual": info.rel_residual,
+            "helmholtz_residual": np.array(info.helmholtz_residual[:self.nf]),
+            "history": hist[:info.history_len].copy(),
+        }
+        return out
+
+    def residual(self, v):
+        r = np.zeros(self.nf)
+        _lib.check(_lib.load().mfwh_residual(self._handle, _as_ptr(v), _dptr(r)))
+        return r
+
+    def last_timing(self):
+        ms = C.c_double()
+        sl = C.c_int64()
+        tl = C.c_int64()
+        _lib.check(_lib.load().mfwh_last_timing(self._handle, C.byref(ms), C.byref(sl), C.byref(tl)))
+        return ms.value, sl.value, tl.value

@@ -1,0 +1,581 @@
+// C ABI of libmfwh: handle life cycle, the MFWH map Pi, the fixed-point
+// iteration (Algorithm 1), GMRES on A = I - S (Section "Acceleration by Krylov
+// methods") and the Helmholtz residual (eq. errorAndResid).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "kernels.h"
+
+namespace mfwh {
+
+static thread_local std::string g_error;
+
+void set_error(const std::string& msg) { g_error = msg; }
+
+}  // namespace mfwh
+
+using namespace mfwh;
+
+namespace {
+
+constexpr int kEventPool = 2048;    // event slots: two per timed Pi application
+constexpr int kMaxRestart = kMaxKrylov - 1;
+
+mfwh_status cuda_fail(cudaError_t e, const char* what) {
+  std::ostringstream os;
+  os << what << ": " << cudaGetErrorName(e) << " (" << cudaGetErrorString(e) << ")";
+  set_error(os.str());
+  return e == cudaErrorMemoryAllocation ? MFWH_ERR_NOMEM : MFWH_ERR_CUDA;
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);       \
+  } while (0)
+
+mfwh_status fail(mfwh_status st, const std::string& msg) {
+  set_error(msg);
+  return st;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes attr;
+  cudaError_t e = cudaPointerGetAttributes(&attr, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct mfwh_handle_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  Plan plan;
+  Geom geom{};
+  int nf = 0;
+  int64_t P = 0, N = 0;            // points per grid function, nf * points
+  double inv_h2[3] = {0, 0, 0};
+  double omega2[MFWH_MAX_NF] = {};
+  double* f = nullptr;              // forcing [nf][P]
+  double* Wa = nullptr;             // wave levels (ping-pong)
+  double* Wb = nullptr;
+  double* q = nullptr;              // filter accumulators [nf][P]
+  double* res_partial = nullptr;
+  double* res_out = nullptr;
+  double* dot_partial = nullptr;
+  double* dot_out = nullptr;
+  double* vec_b = nullptr;          // GMRES right-hand side Pi(0)
+  double* vec_x = nullptr;          // iterate when the caller's buffer is on the host
+  double* basis = nullptr;          // Krylov basis [(restart+1)][N]
+  int basis_vectors = 0;
+  double* pinned = nullptr;         // host pinned scratch (kPinned doubles)
+  std::vector<cudaEvent_t> ev;      // event pool: pairs around the step loop of each Pi
+  int ev_used = 0;
+  double last_step_ms = 0.0;
+  int64_t step_launches = 0;
+  int64_t total_launches = 0;
+  StepHost sh;                      // per-step kernel arguments (reused)
+};
+
+namespace {
+
+constexpr int kPinned = kMaxKrylov + 64;
+
+void reset_timing(mfwh_handle_t h) {
+  h->ev_used = 0;
+  h->last_step_ms = 0.0;
+  h->step_launches = 0;
+  h->total_launches = 0;
+}
+
+mfwh_status collect_timing(mfwh_handle_t h) {
+  double ms = 0.0;
+  for (int i = 0; i + 1 < h->ev_used; i += 2) {
+    float t = 0.0f;
+    CK(cudaEventElapsedTime(&t, h->ev[i], h->ev[i + 1]));
+    ms += t;
+  }
+  h->last_step_ms = ms;
+  return MFWH_OK;
+}
+
+void layer_coef(const mfwh_handle_t h, double c2, double a_cur, double kappa, LayerCoef* L) {
+  const double k = kappa * c2;
+  L->Ax = k * h->inv_h2[0];
+  L->Ay = k * h->inv_h2[1];
+  L->Az = k * h->inv_h2[2];
+  L->A0 = a_cur - 2.0 * (L->Ax + L->Ay + L->Az);
+}
+
+// v_out = Pi(v_in) (forced) or S v_in; with vsub: v_out = vsub - (that).
+mfwh_status apply_pi(mfwh_handle_t h, const double* vin, double* vout, int forced,
+                     const double* vsub) {
+  const Plan& P = h->plan;
+  const int nf = h->nf;
+  const int n_t = P.s.n_t;
+  const double dt = P.s.dt;
+  cudaStream_t st = h->stream;
+  launch_init(nf, h->geom, vin, h->Wa, h->q, &P.w[0], st);
+  h->total_launches += 1;
+  const bool timed = h->ev_used + 2 <= (int)h->ev.size();
+  if (timed) CK(cudaEventRecord(h->ev[h->ev_used], st));
+  double* Wc = h->Wa;
+  double* Wp = h->Wb;
+  StepHost& a = h->sh;
+  a.forced = forced;
+  a.subtract = vsub != nullptr;
+  for (int n = 0; n < n_t; ++n) {
+    const bool first = n == 0;
+    const double kappa = first ? 0.5 * dt * dt : dt * dt;
+    const double a_cur = first ? 1.0 : 2.0;
+    layer_coef(h, P.c2_lo, a_cur, kappa, &a.lo);
+    layer_coef(h, P.c2_hi, a_cur, kappa, &a.hi);
+    a.first = first;
+    for (int m = 0; m < nf; ++m) {
+      a.fc[m] = kappa * P.cosf[(size_t)n * nf + m];
+      a.wq[m] = P.w[(size_t)(n + 1) * nf + m];
+    }
+    if (n + 1 < n_t) {
+      launch_step(nf, h->geom, Wc, Wp, h->f, h->q, a, st);
+      std::swap(Wc, Wp);
+    } else {
+      launch_last(nf, h->geom, Wc, Wp, h->f, h->q, vout, vsub, a, st);
+    }
+  }
+  h->step_launches += n_t;
+  h->total_launches += n_t;
+  if (timed) {
+    CK(cudaEventRecord(h->ev[h->ev_used + 1], st));
+    h->ev_used += 2;
+  }
+  CK(cudaGetLastError());
+  return MFWH_OK;
+}
+
+mfwh_status dots(mfwh_handle_t h, const double* V, int k, const double* w, double* out_host) {
+  launch_multidot(V, h->N, k, w, h->N, h->dot_partial, h->dot_out, h->stream);
+  h->total_launches += multidot_launches(k);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(h->pinned, h->dot_out, sizeof(double) * k, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  std::memcpy(out_host, h->pinned, sizeof(double) * k);
+  return MFWH_OK;
+}
+
+mfwh_status residual_dev(mfwh_handle_t h, const double* v_dev, double* r_out) {
+  launch_residual(h->nf, h->geom, v_dev, h->f, h->omega2, h->plan.c2_lo, h->plan.c2_hi, h->inv_h2,
+                  h->res_partial, h->res_out, h->stream);
+  h->total_launches += 2;
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(h->pinned, h->res_out, sizeof(double) * 2 * h->nf, cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  bool finite = true;
+  for (int m = 0; m < h->nf; ++m) {
+    const double num = h->pinned[m], den = h->pinned[h->nf + m];
+    r_out[m] = den > 0.0 ? num / den : num;
+    finite = finite && std::isfinite(r_out[m]);
+  }
+  if (!finite) return fail(MFWH_ERR_NONFINITE, "non-finite value in the Helmholtz residual");
+  return MFWH_OK;
+}
+
+mfwh_status ensure_basis(mfwh_handle_t h, int vectors) {
+  if (h->basis_vectors >= vectors) return MFWH_OK;
+  if (h->basis) cudaFree(h->basis);
+  h->basis = nullptr;
+  h->basis_vectors = 0;
+  CK(cudaMalloc(&h->basis, sizeof(double) * h->N * vectors));
+  h->basis_vectors = vectors;
+  return MFWH_OK;
+}
+
+// Stage a host-or-device stack of grid functions on the device.
+mfwh_status stage_in(mfwh_handle_t h, const double* v, double** dev, bool* on_device) {
+  *on_device = is_device_ptr(v);
+  if (*on_device) {
+    *dev = const_cast<double*>(v);
+    return MFWH_OK;
+  }
+  CK(cudaMemcpyAsync(h->vec_x, v, sizeof(double) * h->N, cudaMemcpyHostToDevice, h->stream));
+  *dev = h->vec_x;
+  return MFWH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mfwh_last_error(void) { return g_error.c_str(); }
+
+const char* mfwh_status_string(mfwh_status s) {
+  switch (s) {
+    case MFWH_OK: return "ok";
+    case MFWH_ERR_INVALID_ARG: return "invalid argument";
+    case MFWH_ERR_SINGULAR: return "singular filter system";
+    case MFWH_ERR_CUDA: return "CUDA error";
+    case MFWH_ERR_NOMEM: return "out of memory";
+    case MFWH_ERR_NOT_CONVERGED: return "not converged";
+    case MFWH_ERR_SPURIOUS: return "converged to a non-solution (Helmholtz residual check failed)";
+    case MFWH_ERR_NONFINITE: return "non-finite values";
+  }
+  return "unknown status";
+}
+
+mfwh_status mfwh_plan(const mfwh_problem* prob, mfwh_setup* out) {
+  if (!out) return fail(MFWH_ERR_INVALID_ARG, "null output");
+  Plan P;
+  mfwh_status st = plan_problem(prob, &P);
+  if (st == MFWH_OK) *out = P.s;
+  return st;
+}
+
+mfwh_status mfwh_plan_weights(const mfwh_problem* prob, double* w_out, int64_t capacity) {
+  if (!w_out) return fail(MFWH_ERR_INVALID_ARG, "null output");
+  Plan P;
+  mfwh_status st = plan_problem(prob, &P);
+  if (st != MFWH_OK) return st;
+  if ((int64_t)P.w.size() > capacity) return fail(MFWH_ERR_INVALID_ARG, "w_out too small");
+  std::memcpy(w_out, P.w.data(), sizeof(double) * P.w.size());
+  return MFWH_OK;
+}
+
+mfwh_status mfwh_adjusted_frequency(int nf, const double* omega, double dt, double alpha,
+                                    double beta, double* out) {
+  if (nf < 1 || !omega || !out || !(dt > 0.0)) return fail(MFWH_ERR_INVALID_ARG, "bad arguments");
+  for (int m = 0; m < nf; ++m) {
+    const double x = omega[m] * dt;
+    const double c = (1.0 - 0.5 * beta * x * x) / (1.0 + alpha * x * x);
+    if (c < -1.0 || c > 1.0) return fail(MFWH_ERR_INVALID_ARG, "frequency beyond the scheme's range");
+    out[m] = std::acos(c) / dt;
+  }
+  return MFWH_OK;
+}
+
+mfwh_status mfwh_opt_parameters(int nf, const double* omega, int n_p, int n_t, int n_delta,
+                                double c_delta, double* params_out, double* lam_max,
+                                int* n_lambda) {
+  if (nf < 1 || nf > MFWH_MAX_NF || !omega || !params_out || n_p < 1 || n_t < 2 || n_delta < 1)
+    return fail(MFWH_ERR_INVALID_ARG, "bad arguments");
+  for (int m = 0; m < nf; ++m)
+    if (!(omega[m] > 0.0) || (m > 0 && !(omega[m] > omega[m - 1])))
+      return fail(MFWH_ERR_INVALID_ARG, "frequencies must be positive and increasing");
+  return optimise_parameters(nf, omega, n_p, n_t, n_delta, c_delta, params_out, lam_max, n_lambda);
+}
+
+mfwh_status mfwh_create(const mfwh_problem* prob, void* stream, mfwh_handle_t* out) {
+  if (!out) return fail(MFWH_ERR_INVALID_ARG, "null output");
+  *out = nullptr;
+  auto* h = new (std::nothrow) mfwh_handle_s();
+  if (!h) return fail(MFWH_ERR_NOMEM, "host allocation failed");
+  mfwh_status st = plan_problem(prob, &h->plan);
+  if (st != MFWH_OK) {
+    delete h;
+    return st;
+  }
+  const Plan& P = h->plan;
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->nf = P.s.nf;
+  h->P = P.s.points;
+  h->N = h->P * h->nf;
+  for (int a = 0; a < 3; ++a) h->inv_h2[a] = a < P.dim ? 1.0 / (P.s.h[a] * P.s.h[a]) : 0.0;
+  for (int m = 0; m < h->nf; ++m) h->omega2[m] = prob->omega[m] * prob->omega[m];
+  Geom& g = h->geom;
+  g.nx = P.n[0];
+  g.ny = P.n[1];
+  g.nz = P.dim == 3 ? P.n[2] : 0;
+  g.sy = g.nx + 1;
+  g.sz = (g.nx + 1) * (g.ny + 1);
+  g.points = h->P;
+  g.dim = P.dim;
+  g.layer_axis = P.layer_axis;
+  g.layer_split = P.layer_split;
+
+  auto cleanup = [&](mfwh_status s) {
+    mfwh_destroy(h);
+    return s;
+  };
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaGetDevice"));
+  struct {
+    double** p;
+    int64_t n;
+  } bufs[] = {{&h->f, h->N},
+              {&h->Wa, h->P},
+              {&h->Wb, h->P},
+              {&h->q, h->N},
+              {&h->res_partial, residual_partial_size(MFWH_MAX_NF)},
+              {&h->res_out, 2 * MFWH_MAX_NF},
+              {&h->dot_partial, dot_partial_size()},
+              {&h->dot_out, kMaxKrylov},
+              {&h->vec_b, h->N},
+              {&h->vec_x, h->N}};
+  for (auto& b : bufs) {
+    e = cudaMalloc(b.p, sizeof(double) * b.n);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc (workspace)"));
+  }
+  e = cudaMallocHost(&h->pinned, sizeof(double) * kPinned);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMallocHost"));
+  h->ev.resize(kEventPool);
+  for (auto& x : h->ev) {
+    e = cudaEventCreate(&x);
+    if (e != cudaSuccess) {
+      x = nullptr;
+      return cleanup(cuda_fail(e, "cudaEventCreate"));
+    }
+  }
+  // Boundary values of the wave levels are never written by the step kernels and must be 0.
+  e = cudaMemsetAsync(h->Wa, 0, sizeof(double) * h->P, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->Wb, 0, sizeof(double) * h->P, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->f, 0, sizeof(double) * h->N, h->stream);
+  if (e == cudaSuccess && prob->forcing)
+    e = cudaMemcpyAsync(h->f, prob->forcing, sizeof(double) * h->N, cudaMemcpyDefault, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "initialising workspace"));
+  std::memset(&h->sh, 0, sizeof(h->sh));
+  for (int m = 0; m < h->nf; ++m)
+    for (int j = 0; j < h->nf; ++j) h->sh.binv[m * MFWH_MAX_NF + j] = P.s.B_inv[m][j];
+  *out = h;
+  return MFWH_OK;
+}
+
+mfwh_status mfwh_set_forcing(mfwh_handle_t h, const double* forcing) {
+  if (!h || !forcing) return fail(MFWH_ERR_INVALID_ARG, "null argument");
+  CK(cudaMemcpyAsync(h->f, forcing, sizeof(double) * h->N, cudaMemcpyDefault, h->stream));
+  return MFWH_OK;
+}
+
+mfwh_status mfwh_apply_Pi(mfwh_handle_t h, const double* v_in, double* v_out, int forced) {
+  if (!h || !v_out) return fail(MFWH_ERR_INVALID_ARG, "null argument");
+  if (!is_device_ptr(v_out) || (v_in && !is_device_ptr(v_in)))
+    return fail(MFWH_ERR_INVALID_ARG, "mfwh_apply_Pi takes device pointers");
+  reset_timing(h);
+  return apply_pi(h, v_in, v_out, forced ? 1 : 0, nullptr);
+}
+
+mfwh_status mfwh_solve_fpi(mfwh_handle_t h, int iters, double* v) {
+  if (!h || !v || iters < 0) return fail(MFWH_ERR_INVALID_ARG, "bad argument");
+  reset_timing(h);
+  double* x = nullptr;
+  bool on_dev = false;
+  mfwh_status st = stage_in(h, v, &x, &on_dev);
+  if (st != MFWH_OK) return st;
+  for (int k = 0; k < iters; ++k) {
+    st = apply_pi(h, x, x, 1, nullptr);
+    if (st != MFWH_OK) return st;
+  }
+  if (!on_dev) CK(cudaMemcpyAsync(v, x, sizeof(double) * h->N, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return collect_timing(h);
+}
+
+mfwh_status mfwh_solve_gmres(mfwh_handle_t h, int restart, double tol, int max_iters,
+                             double spurious_tol, double* v, mfwh_solve_info* info) {
+  if (!h || !v) return fail(MFWH_ERR_INVALID_ARG, "null argument");
+  if (restart < 1 || restart > kMaxRestart)
+    return fail(MFWH_ERR_INVALID_ARG, "restart must be in 1..1023");
+  if (max_iters < 1 || !(tol >= 0.0)) return fail(MFWH_ERR_INVALID_ARG, "bad max_iters or tol");
+  if (restart > max_iters) restart = max_iters;   // a longer basis would never be used
+  reset_timing(h);
+  mfwh_status st = ensure_basis(h, restart + 1);
+  if (st != MFWH_OK) return st;
+  mfwh_solve_info local{};
+  mfwh_solve_info& I = info ? *info : local;
+  I.iterations = I.pi_applications = I.restarts = 0;
+  I.history_len = 0;
+  I.rel_residual = NAN;
+  const int64_t N = h->N;
+  cudaStream_t s = h->stream;
+  double* x = nullptr;
+  bool on_dev = false;
+  st = stage_in(h, v, &x, &on_dev);
+  if (st != MFWH_OK) return st;
+
+  // b = Pi(0) (eq. discreteMFWHmapping)
+  st = apply_pi(h, nullptr, h->vec_b, 1, nullptr);
+  if (st != MFWH_OK) return st;
+  I.pi_applications++;
+  double bb = 0.0, xx = 0.0;
+  st = dots(h, h->vec_b, 1, h->vec_b, &bb);
+  if (st != MFWH_OK) return st;
+  st = dots(h, x, 1, x, &xx);
+  if (st != MFWH_OK) return st;
+  const double bnorm = std::sqrt(bb);
+  if (!std::isfinite(bnorm) || !std::isfinite(xx))
+    return fail(MFWH_ERR_NONFINITE, "non-finite right-hand side or initial guess");
+  bool x_nonzero = xx > 0.0;
+  bool converged = false;
+  std::vector<double> H((restart + 1) * restart), cs(restart), sn(restart), g(restart + 1),
+      y(restart), hcol(restart + 1), h2(restart + 1);
+  if (bnorm == 0.0) {
+    launch_axpby(x, 0.0, x, 0.0, N, s);
+    converged = true;
+    I.rel_residual = 0.0;
+  }
+  while (!converged && I.iterations < max_iters) {
+    double* V0 = h->basis;
+    I.restarts++;
+    if (x_nonzero) {   // r = b - (x - S x)
+      st = apply_pi(h, x, V0, 0, x);
+      if (st != MFWH_OK) return st;
+      I.pi_applications++;
+      launch_axpby(V0, 1.0, h->vec_b, -1.0, N, s);
+    } else {
+      launch_axpby(V0, 1.0, h->vec_b, 0.0, N, s);
+    }
+    h->total_launches++;
+    double rr = 0.0;
+    st = dots(h, V0, 1, V0, &rr);
+    if (st != MFWH_OK) return st;
+    const double beta = std::sqrt(rr);
+    if (!std::isfinite(beta)) return fail(MFWH_ERR_NONFINITE, "non-finite Krylov residual");
+    I.rel_residual = beta / bnorm;
+    if (I.rel_residual < tol) {
+      converged = true;
+      break;
+    }
+    launch_axpby(V0, 1.0 / beta, V0, 0.0, N, s);
+    h->total_launches++;
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int j_done = 0;
+    double res = beta;
+    for (int j = 0; j < restart; ++j) {
+      double* Vj = h->basis + (int64_t)j * N;
+      double* w = h->basis + (int64_t)(j + 1) * N;
+      st = apply_pi(h, Vj, w, 0, Vj);   // w = A v_j = v_j - S v_j
+      if (st != MFWH_OK) return st;
+      I.pi_applications++;
+      I.iterations++;
+      // classical Gram-Schmidt, applied twice
+      st = dots(h, h->basis, j + 1, w, hcol.data());
+      if (st != MFWH_OK) return st;
+      launch_multi_axpy(w, h->basis, N, j + 1, hcol.data(), N, s);
+      h->total_launches += multi_axpy_launches(j + 1);
+      st = dots(h, h->basis, j + 1, w, h2.data());
+      if (st != MFWH_OK) return st;
+      launch_multi_axpy(w, h->basis, N, j + 1, h2.data(), N, s);
+      h->total_launches += multi_axpy_launches(j + 1);
+      for (int i = 0; i <= j; ++i) hcol[i] += h2[i];
+      double ww = 0.0;
+      st = dots(h, w, 1, w, &ww);
+      if (st != MFWH_OK) return st;
+      const double hnext = std::sqrt(ww);
+      if (!std::isfinite(hnext)) return fail(MFWH_ERR_NONFINITE, "non-finite Arnoldi vector");
+      // Givens rotations on the new Hessenberg column
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * hcol[i] + sn[i] * hcol[i + 1];
+        hcol[i + 1] = -sn[i] * hcol[i] + cs[i] * hcol[i + 1];
+        hcol[i] = t;
+      }
+      const double r = std::hypot(hcol[j], hnext);
+      cs[j] = r > 0.0 ? hcol[j] / r : 1.0;
+      sn[j] = r > 0.0 ? hnext / r : 0.0;
+      hcol[j] = r;
+      for (int i = 0; i <= j; ++i) H[i * restart + j] = hcol[i];
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      res = std::fabs(g[j + 1]);
+      if (I.history && I.history_len < I.history_capacity) I.history[I.history_len++] = res / bnorm;
+      j_done = j + 1;
+      if (res / bnorm < tol || I.iterations >= max_iters || hnext == 0.0) break;
+      launch_axpby(w, 1.0 / hnext, w, 0.0, N, s);
+      h->total_launches++;
+    }
+    // y = R^{-1} g, then x += V y
+    for (int i = j_done - 1; i >= 0; --i) {
+      double acc = g[i];
+      for (int k = i + 1; k < j_done; ++k) acc -= H[i * restart + k] * y[k];
+      y[i] = acc / H[i * restart + i];
+    }
+    for (int i = 0; i < j_done; ++i) y[i] = -y[i];   // multi_axpy subtracts
+    launch_multi_axpy(x, h->basis, N, j_done, y.data(), N, s);
+    h->total_launches += multi_axpy_launches(j_done);
+    x_nonzero = true;
+    I.rel_residual = res / bnorm;
+    if (I.rel_residual < tol) converged = true;
+  }
+  CK(cudaGetLastError());
+  double r[MFWH_MAX_NF];
+  st = residual_dev(h, x, r);
+  for (int m = 0; m < h->nf; ++m) I.helmholtz_residual[m] = st == MFWH_OK ? r[m] : NAN;
+  if (!on_dev) CK(cudaMemcpyAsync(v, x, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  mfwh_status ts = collect_timing(h);
+  if (ts != MFWH_OK) return ts;
+  if (st != MFWH_OK) return st;
+  if (!converged) {
+    std::ostringstream os;
+    os << "GMRES stopped after " << I.iterations << " iterations at relative residual "
+       << I.rel_residual;
+    return fail(MFWH_ERR_NOT_CONVERGED, os.str());
+  }
+  if (spurious_tol > 0.0) {
+    double worst = 0.0;
+    for (int m = 0; m < h->nf; ++m) worst = std::fmax(worst, r[m]);
+    if (worst > spurious_tol) {
+      std::ostringstream os;
+      os << "GMRES converged but the Helmholtz residual is " << worst << " > " << spurious_tol
+         << " (spurious resonance?)";
+      return fail(MFWH_ERR_SPURIOUS, os.str());
+    }
+  }
+  return MFWH_OK;
+}
+
+mfwh_status mfwh_residual(mfwh_handle_t h, const double* v, double* r_out) {
+  if (!h || !v || !r_out) return fail(MFWH_ERR_INVALID_ARG, "null argument");
+  reset_timing(h);
+  double* x = nullptr;
+  bool on_dev = false;
+  mfwh_status st = stage_in(h, v, &x, &on_dev);
+  if (st != MFWH_OK) return st;
+  return residual_dev(h, x, r_out);
+}
+
+mfwh_status mfwh_get_setup(mfwh_handle_t h, mfwh_setup* out) {
+  if (!h || !out) return fail(MFWH_ERR_INVALID_ARG, "null argument");
+  *out = h->plan.s;
+  return MFWH_OK;
+}
+
+mfwh_status mfwh_last_timing(mfwh_handle_t h, double* step_ms, int64_t* step_launches,
+                             int64_t* total_launches) {
+  if (!h) return fail(MFWH_ERR_INVALID_ARG, "null handle");
+  if (h->ev_used > 0) {
+    CK(cudaEventSynchronize(h->ev[h->ev_used - 1]));
+    mfwh_status st = collect_timing(h);
+    if (st != MFWH_OK) return st;
+  }
+  if (step_ms) *step_ms = h->last_step_ms;
+  if (step_launches) *step_launches = h->step_launches;
+  if (total_launches) *total_launches = h->total_launches;
+  return MFWH_OK;
+}
+
+void mfwh_destroy(mfwh_handle_t h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  double* bufs[] = {h->f, h->Wa, h->Wb, h->q, h->res_partial, h->res_out, h->dot_partial,
+                    h->dot_out, h->vec_b, h->vec_x, h->basis};
+  for (double* b : bufs)
+    if (b) cudaFree(b);
+  if (h->pinned) cudaFreeHost(h->pinned);
+  for (auto& x : h->ev)
+    if (x) cudaEventDestroy(x);
+  delete h;
+}
+
+}  // extern "C"

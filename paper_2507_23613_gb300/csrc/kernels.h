@@ -1,0 +1,80 @@
+// Device-side launchers of libmfwh (implemented in wave.cu and krylov.cu).
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "mfwh.h"
+
+namespace mfwh {
+
+// Grid geometry as the kernels see it.  Points are indexed
+// p = k * sz + j * sy + i with 0 <= i <= nx, 0 <= j <= ny, 0 <= k <= nz.
+struct Geom {
+  int64_t nx, ny, nz;        // cells per axis (nz = 0 in 2D)
+  int64_t sy, sz;            // strides of j and k
+  int64_t points;            // points per grid function (stride between frequencies)
+  int dim;                   // 2 or 3
+  int layer_axis;            // axis whose index selects the c^2 layer
+  int64_t layer_split;       // indices >= layer_split use the upper-layer coefficients
+};
+
+// Leapfrog update at one point, written as
+//   W^{n+1} = A0 W^n + a_prev W^{n-1} + Ax (W_e + W_w) + Ay (W_n + W_s) + Az (W_u + W_d)
+//             - sum_m fneg_m f_m,
+// with A0 = a_cur - 2 kappa c^2 sum_i 1/h_i^2, A_i = kappa c^2 / h_i^2,
+// (a_cur, a_prev, kappa) = (2, -1, dt^2) for a regular step (eq. WaveSchemeA) and
+// (1, 0, dt^2/2) for the first step (eq. implicitFirstStep with alpha = 0).
+struct LayerCoef {
+  double A0, Ax, Ay, Az;
+};
+
+struct StepHost {
+  LayerCoef lo, hi;                 // coefficients below / above the layer split
+  int first;                        // 1 on the first step: no W^{n-1} term
+  int forced;                       // 0: homogeneous map S (no forcing)
+  double fc[MFWH_MAX_NF];           // kappa cos(omega~_m t^n)
+  double wq[MFWH_MAX_NF];           // w_{n+1,m}: filter weight of the new level
+  // epilogue (last step only)
+  int subtract;                     // 1: v_out = v_sub - B^{-1} q, else v_out = B^{-1} q
+  double binv[MFWH_MAX_NF * MFWH_MAX_NF];
+};
+
+// W^0 = sum_m v_m (0 on the boundary; v == nullptr gives W^0 = 0) and q_m = w0_m W^0.
+void launch_init(int nf, const Geom& g, const double* v, double* W0, double* q, const double* w0,
+                 cudaStream_t st);
+// One leapfrog step n -> n+1 fused with q_m += w_{n+1,m} W^{n+1}.  W^{n+1} overwrites Wp.
+void launch_step(int nf, const Geom& g, const double* Wc, double* Wp, const double* f, double* q,
+                 const StepHost& a, cudaStream_t st);
+// Last step fused with the filter solve: v_out = B^{-1}(q + w_{N_t} W^{N_t}) (or v_sub - that).
+void launch_last(int nf, const Geom& g, const double* Wc, const double* Wp, const double* f,
+                 const double* q, double* vout, const double* vsub, const StepHost& a,
+                 cudaStream_t st);
+// Per-frequency max_int |f_m - (c^2 Delta_h + omega_m^2) v_m| and max_int |f_m|, reduced over the
+// grid into out[2 * nf] (device): out[m] = residual max, out[nf + m] = forcing max.
+// partial: device scratch of at least residual_partial_size(nf) doubles.
+void launch_residual(int nf, const Geom& g, const double* v, const double* f, const double* omega2,
+                     double c2_lo, double c2_hi, const double* inv_h2, double* partial, double* out,
+                     cudaStream_t st);
+int64_t residual_partial_size(int nf);
+
+// ---- Krylov vector kernels (krylov.cu), FP64 -------------------------------------
+constexpr int kMaxDots = 32;       // vectors handled by one multi-dot / multi-axpy launch
+constexpr int kMaxKrylov = 1024;   // largest Krylov basis (restart length + 1)
+// out[i] = <V_i, w> for i < k, V_i = V + i * ldv (device), N entries, in chunks of
+// kMaxDots vectors per launch; partial: device scratch of at least dot_partial_size()
+// doubles; out: device [k].  k <= kMaxKrylov.
+void launch_multidot(const double* V, int64_t ldv, int k, const double* w, int64_t N,
+                     double* partial, double* out, cudaStream_t st);
+int64_t dot_partial_size();
+// number of kernel launches launch_multidot issues for k vectors
+int multidot_launches(int k);
+// w -= sum_i coef[i] V_i (coef host, k <= kMaxKrylov), kMaxDots vectors per pass over w.
+void launch_multi_axpy(double* w, const double* V, int64_t ldv, int k, const double* coef,
+                       int64_t N, cudaStream_t st);
+int multi_axpy_launches(int k);
+// y = a x + b y
+void launch_axpby(double* y, double a, const double* x, double b, int64_t N, cudaStream_t st);
+
+}  // namespace mfwh

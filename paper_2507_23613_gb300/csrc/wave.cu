@@ -1,0 +1,352 @@
+// MFWH wave-solve kernels for sm_103a, FP64.
+//
+// One application of the MFWH map (Algorithm 1, loop body) is
+//   k_init  : W^0 = sum_m V_m, q_m = w_{0,m} W^0
+//   k_step  : W^{n+1} = 2 W^n - W^{n-1} + dt^2 (c^2 Delta_h W^n - F^n)        (eq. WaveSchemeA)
+//             (first step: W^1 = W^0 + dt^2/2 (c^2 Delta_h W^0 - F^0),       eq. implicitFirstStep)
+//             fused with the N_f filter sums q_m += w_{n+1,m} W^{n+1}         (eq. pDefQ)
+//   k_last  : the final step fused with the filter solve V = B^{-1} q          (eq. waveHoltzMatrixIteration)
+// F^n = sum_m f_m cos(omega~_m t^n) (eq. WaveSchemeForcing).  The wave levels are
+// stored as two ping-pong grids; W^{n+1} overwrites W^{n-1} at the same point, so
+// each point is read and written by one thread only.  The forcing grids f_m and
+// the accumulators q_m are [N_f][points] arrays; the N_f accumulations of a point
+// run in registers on the value just computed, so W^{n+1} is never re-read.
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+
+namespace mfwh {
+namespace {
+
+constexpr int kBX = 32, kBY = 8;
+
+template <int NF>
+struct StepParams {
+  LayerCoef lo, hi;
+  double fneg[NF];   // kappa cos(omega~_m t^n)
+  double wq[NF];
+  int first, forced;
+};
+
+template <int NF>
+struct LastParams {
+  StepParams<NF> st;
+  double binv[NF * NF];
+  int subtract;
+};
+
+template <int NF>
+struct InitParams {
+  double w0[NF];
+};
+
+template <int NF>
+StepParams<NF> to_params(const StepHost& a) {
+  StepParams<NF> p;
+  p.lo = a.lo;
+  p.hi = a.hi;
+  for (int m = 0; m < NF; ++m) {
+    p.fneg[m] = a.fc[m];
+    p.wq[m] = a.wq[m];
+  }
+  p.first = a.first;
+  p.forced = a.forced;
+  return p;
+}
+
+struct PointIndex {
+  int64_t i, j, k, p;
+  bool inside, interior;
+};
+
+template <int DIM>
+__device__ __forceinline__ PointIndex point_index(const Geom& g) {
+  PointIndex r;
+  r.i = (int64_t)blockIdx.x * kBX + threadIdx.x;
+  r.j = (int64_t)blockIdx.y * kBY + threadIdx.y;
+  r.k = (DIM == 3) ? (int64_t)blockIdx.z : 0;
+  r.inside = r.i <= g.nx && r.j <= g.ny;
+  r.p = r.k * g.sz + r.j * g.sy + r.i;
+  r.interior = r.inside && r.i > 0 && r.i < g.nx && r.j > 0 && r.j < g.ny &&
+               (DIM == 2 || (r.k > 0 && r.k < g.nz));
+  return r;
+}
+
+// New wave level at an interior point (the leapfrog update with the composite forcing).
+template <int NF, int DIM>
+__device__ __forceinline__ double leapfrog_point(const double* __restrict__ Wc,
+                                                 const double* __restrict__ Wp,
+                                                 const double* __restrict__ f,
+                                                 const StepParams<NF>& a, const Geom& g,
+                                                 const PointIndex& x) {
+  const int64_t li = g.layer_axis == 0 ? x.i : (g.layer_axis == 1 ? x.j : x.k);
+  const bool up = li >= g.layer_split;
+  const double A0 = up ? a.hi.A0 : a.lo.A0;
+  const double Ax = up ? a.hi.Ax : a.lo.Ax;
+  const double Ay = up ? a.hi.Ay : a.lo.Ay;
+  const int64_t p = x.p;
+  const double wc = Wc[p];
+  const double sx = Wc[p - 1] + Wc[p + 1];
+  const double sy = Wc[p - g.sy] + Wc[p + g.sy];
+  double acc = a.first ? A0 * wc : fma(A0, wc, -Wp[p]);
+  acc = fma(Ax, sx, acc);
+  acc = fma(Ay, sy, acc);
+  if (DIM == 3) {
+    const double Az = up ? a.hi.Az : a.lo.Az;
+    const double sz = Wc[p - g.sz] + Wc[p + g.sz];
+    acc = fma(Az, sz, acc);
+  }
+  if (a.forced) {
+#pragma unroll
+    for (int m = 0; m < NF; ++m) acc = fma(-a.fneg[m], f[m * g.points + p], acc);
+  }
+  return acc;
+}
+
+template <int NF, int DIM>
+__global__ void __launch_bounds__(kBX * kBY)
+k_init(const double* __restrict__ v, double* __restrict__ W0, double* __restrict__ q,
+       const InitParams<NF> a, const Geom g) {
+  const PointIndex x = point_index<DIM>(g);
+  if (!x.inside) return;
+  double w = 0.0;
+  if (x.interior && v != nullptr) {
+#pragma unroll
+    for (int m = 0; m < NF; ++m) w += v[m * g.points + x.p];
+  }
+  W0[x.p] = w;
+#pragma unroll
+  for (int m = 0; m < NF; ++m) q[m * g.points + x.p] = a.w0[m] * w;
+}
+
+template <int NF, int DIM>
+__global__ void __launch_bounds__(kBX * kBY)
+k_step(const double* __restrict__ Wc, double* __restrict__ Wp, const double* __restrict__ f,
+       double* __restrict__ q, const StepParams<NF> a, const Geom g) {
+  const PointIndex x = point_index<DIM>(g);
+  if (!x.interior) return;           // boundary values stay 0 (Dirichlet, g = 0)
+  const double wn = leapfrog_point<NF, DIM>(Wc, Wp, f, a, g, x);
+  Wp[x.p] = wn;
+#pragma unroll
+  for (int m = 0; m < NF; ++m) {
+    double* qm = q + m * g.points + x.p;
+    *qm = fma(a.wq[m], wn, *qm);
+  }
+}
+
+template <int NF, int DIM>
+__global__ void __launch_bounds__(kBX * kBY)
+k_last(const double* __restrict__ Wc, const double* __restrict__ Wp, const double* __restrict__ f,
+       const double* __restrict__ q, double* vout, const double* vsub, const LastParams<NF> a,
+       const Geom g) {
+  const PointIndex x = point_index<DIM>(g);
+  if (!x.inside) return;
+  if (!x.interior) {
+#pragma unroll
+    for (int m = 0; m < NF; ++m) vout[m * g.points + x.p] = 0.0;
+    return;
+  }
+  const double wn = leapfrog_point<NF, DIM>(Wc, Wp, f, a.st, g, x);
+  double qq[NF];
+#pragma unroll
+  for (int m = 0; m < NF; ++m) qq[m] = fma(a.st.wq[m], wn, q[m * g.points + x.p]);
+  double out[NF];
+#pragma unroll
+  for (int m = 0; m < NF; ++m) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < NF; ++j) s = fma(a.binv[m * NF + j], qq[j], s);
+    out[m] = a.subtract ? vsub[m * g.points + x.p] - s : s;
+  }
+#pragma unroll
+  for (int m = 0; m < NF; ++m) vout[m * g.points + x.p] = out[m];
+}
+
+// ---- Helmholtz residual -------------------------------------------------------
+
+constexpr int kResBlocks = 4 * 152;
+
+__device__ __forceinline__ double nanmax(double a, double b) {
+  // max that propagates NaN so that non-finite iterates are reported
+  return (b > a || b != b) ? b : a;
+}
+
+template <int NF>
+struct ResParams {
+  double omega2[NF];
+  double c2_lo, c2_hi;
+  double ihx2, ihy2, ihz2;
+};
+
+template <int NF, int DIM>
+__global__ void __launch_bounds__(256)
+k_residual(const double* __restrict__ v, const double* __restrict__ f, const ResParams<NF> a,
+           const Geom g, double* __restrict__ partial) {
+  double rmax[NF], fmax_[NF];
+#pragma unroll
+  for (int m = 0; m < NF; ++m) rmax[m] = fmax_[m] = 0.0;
+  const int64_t nx1 = g.nx + 1, ny1 = g.ny + 1;
+  const int64_t total = g.points;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = p % nx1;
+    const int64_t j = (p / nx1) % ny1;
+    const int64_t k = (DIM == 3) ? p / (nx1 * ny1) : 0;
+    if (i == 0 || i == g.nx || j == 0 || j == g.ny) continue;
+    if (DIM == 3 && (k == 0 || k == g.nz)) continue;
+    const int64_t li = g.layer_axis == 0 ? i : (g.layer_axis == 1 ? j : k);
+    const double c2 = li >= g.layer_split ? a.c2_hi : a.c2_lo;
+#pragma unroll
+    for (int m = 0; m < NF; ++m) {
+      const double* vm = v + m * g.points;
+      const double vc = vm[p];
+      double lap = a.ihx2 * (vm[p - 1] - 2.0 * vc + vm[p + 1]) +
+                   a.ihy2 * (vm[p - g.sy] - 2.0 * vc + vm[p + g.sy]);
+      if (DIM == 3) lap += a.ihz2 * (vm[p - g.sz] - 2.0 * vc + vm[p + g.sz]);
+      const double fm = f[m * g.points + p];
+      const double r = fm - (c2 * lap + a.omega2[m] * vc);
+      rmax[m] = nanmax(rmax[m], fabs(r));
+      fmax_[m] = nanmax(fmax_[m], fabs(fm));
+    }
+  }
+  __shared__ double red[2 * NF][8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int m = 0; m < NF; ++m) {
+    double r = rmax[m], fv = fmax_[m];
+    for (int o = 16; o > 0; o >>= 1) {
+      r = nanmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+      fv = nanmax(fv, __shfl_xor_sync(0xffffffffu, fv, o));
+    }
+    if (lane == 0) {
+      red[m][warp] = r;
+      red[NF + m][warp] = fv;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * NF) {
+    double r = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = nanmax(r, red[threadIdx.x][w]);
+    partial[(int64_t)blockIdx.x * 2 * NF + threadIdx.x] = r;
+  }
+}
+
+__global__ void k_max_partials(const double* __restrict__ partial, int nblocks, int width,
+                               double* __restrict__ out) {
+  // one thread per output column
+  const int c = threadIdx.x;
+  if (c >= width) return;
+  double r = 0.0;
+  for (int b = 0; b < nblocks; ++b) r = nanmax(r, partial[(int64_t)b * width + c]);
+  out[c] = r;
+}
+
+dim3 step_grid(const Geom& g) {
+  return dim3((unsigned)((g.nx + 1 + kBX - 1) / kBX), (unsigned)((g.ny + 1 + kBY - 1) / kBY),
+              (unsigned)(g.dim == 3 ? g.nz + 1 : 1));
+}
+
+template <int NF>
+void init_nf(const Geom& g, const double* v, double* W0, double* q, const double* w0,
+             cudaStream_t st) {
+  InitParams<NF> a;
+  for (int m = 0; m < NF; ++m) a.w0[m] = w0[m];
+  dim3 blk(kBX, kBY);
+  if (g.dim == 2)
+    k_init<NF, 2><<<step_grid(g), blk, 0, st>>>(v, W0, q, a, g);
+  else
+    k_init<NF, 3><<<step_grid(g), blk, 0, st>>>(v, W0, q, a, g);
+}
+
+template <int NF>
+void step_nf(const Geom& g, const double* Wc, double* Wp, const double* f, double* q,
+             const StepHost& h, cudaStream_t st) {
+  const StepParams<NF> a = to_params<NF>(h);
+  dim3 blk(kBX, kBY);
+  if (g.dim == 2)
+    k_step<NF, 2><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, q, a, g);
+  else
+    k_step<NF, 3><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, q, a, g);
+}
+
+template <int NF>
+void last_nf(const Geom& g, const double* Wc, const double* Wp, const double* f, const double* q,
+             double* vout, const double* vsub, const StepHost& h, cudaStream_t st) {
+  LastParams<NF> a;
+  a.st = to_params<NF>(h);
+  for (int m = 0; m < NF; ++m)
+    for (int j = 0; j < NF; ++j) a.binv[m * NF + j] = h.binv[m * MFWH_MAX_NF + j];
+  a.subtract = h.subtract;
+  dim3 blk(kBX, kBY);
+  if (g.dim == 2)
+    k_last<NF, 2><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, q, vout, vsub, a, g);
+  else
+    k_last<NF, 3><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, q, vout, vsub, a, g);
+}
+
+template <int NF>
+void residual_nf(const Geom& g, const double* v, const double* f, const double* omega2,
+                 double c2_lo, double c2_hi, const double* inv_h2, double* partial, double* out,
+                 cudaStream_t st) {
+  ResParams<NF> a;
+  for (int m = 0; m < NF; ++m) a.omega2[m] = omega2[m];
+  a.c2_lo = c2_lo;
+  a.c2_hi = c2_hi;
+  a.ihx2 = inv_h2[0];
+  a.ihy2 = inv_h2[1];
+  a.ihz2 = inv_h2[2];
+  if (g.dim == 2)
+    k_residual<NF, 2><<<kResBlocks, 256, 0, st>>>(v, f, a, g, partial);
+  else
+    k_residual<NF, 3><<<kResBlocks, 256, 0, st>>>(v, f, a, g, partial);
+  k_max_partials<<<1, 64, 0, st>>>(partial, kResBlocks, 2 * NF, out);
+}
+
+}  // namespace
+
+#define MFWH_NF_SWITCH(nf, CALL)                                   \
+  switch (nf) {                                                    \
+    case 1: CALL(1); break;   case 2: CALL(2); break;              \
+    case 3: CALL(3); break;   case 4: CALL(4); break;              \
+    case 5: CALL(5); break;   case 6: CALL(6); break;              \
+    case 7: CALL(7); break;   case 8: CALL(8); break;              \
+    case 9: CALL(9); break;   case 10: CALL(10); break;            \
+    case 11: CALL(11); break; case 12: CALL(12); break;            \
+    case 13: CALL(13); break; case 14: CALL(14); break;            \
+    case 15: CALL(15); break; case 16: CALL(16); break;            \
+    default: break;                                                \
+  }
+
+void launch_init(int nf, const Geom& g, const double* v, double* W0, double* q, const double* w0,
+                 cudaStream_t st) {
+#define CALL(N) init_nf<N>(g, v, W0, q, w0, st)
+  MFWH_NF_SWITCH(nf, CALL)
+#undef CALL
+}
+
+void launch_step(int nf, const Geom& g, const double* Wc, double* Wp, const double* f, double* q,
+                 const StepHost& a, cudaStream_t st) {
+#define CALL(N) step_nf<N>(g, Wc, Wp, f, q, a, st)
+  MFWH_NF_SWITCH(nf, CALL)
+#undef CALL
+}
+
+void launch_last(int nf, const Geom& g, const double* Wc, const double* Wp, const double* f,
+                 const double* q, double* vout, const double* vsub, const StepHost& a,
+                 cudaStream_t st) {
+#define CALL(N) last_nf<N>(g, Wc, Wp, f, q, vout, vsub, a, st)
+  MFWH_NF_SWITCH(nf, CALL)
+#undef CALL
+}
+
+void launch_residual(int nf, const Geom& g, const double* v, const double* f, const double* omega2,
+                     double c2_lo, double c2_hi, const double* inv_h2, double* partial, double* out,
+                     cudaStream_t st) {
+#define CALL(N) residual_nf<N>(g, v, f, omega2, c2_lo, c2_hi, inv_h2, partial, out, st)
+  MFWH_NF_SWITCH(nf, CALL)
+#undef CALL
+}
+
+int64_t residual_partial_size(int nf) { return (int64_t)kResBlocks * 2 * nf; }
+
+}  // namespace mfwh

@@ -1,0 +1,165 @@
+"""Host-side checks of libmfwh that need no GPU: the shared library loads and
+exports every function include/mfwh.h declares, its host set-up (time step,
+omega~, weights, Algorithm 2, B) agrees with the oracle and with the paper's
+printed parameters, and invalid problems are rejected."""
+
+import json
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2507_23613_gb300 as M
+from paper_2507_23613_gb300 import _lib, build, inputs
+from oracle import filters as F
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mfwh.h")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def header_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mfwh_[a-zA-Z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = header_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(_lib.declared_symbols()) == names
+
+
+def _compare_setup(wl, n_p=1, mode=F.FILTER_OPTIMIZED, user=None, c_hi=None):
+    kw = dict(n_p=n_p, filter_mode={F.FILTER_OPTIMIZED: 0, F.FILTER_TRADITIONAL: 1,
+                                     F.FILTER_USER: 2}[mode], user_params=user)
+    if c_hi is not None:
+        kw.update(c_lo=1.0, c_hi=c_hi, interface=0.5, layer_axis=len(wl.n) - 1)
+    prob, keep = M.make_problem(wl.n, wl.length, wl.omega, **kw)
+    s = M.setup_arrays(M.plan(prob))
+    h = [L / n for L, n in zip(wl.length, wl.n)]
+    o = F.make_setup(wl.omega, h, 1.0 if c_hi is None else max(1.0, c_hi), 0.5, n_p, mode, user)
+    assert s["n_t"] == o.n_t
+    assert abs(s["dt"] - o.dt) <= 1e-15 * o.dt
+    np.testing.assert_allclose(s["omega_tilde"], o.omega_t, rtol=1e-14)
+    assert list(s["n_pm"]) == list(o.n_pm)
+    np.testing.assert_allclose(s["t_fm"], o.t_fm, rtol=1e-14)
+    # least-squares parameters agree to the accuracy the problem determines them:
+    # eps cond(M)^2 relative (non-zero residual); given parameters agree to rounding
+    eps = np.finfo(float).eps
+    rel = 1e-12 if not np.isfinite(o.cond_M) else max(1e-12, 10 * eps * o.cond_M ** 2)
+    scale = np.max(np.abs(o.params))
+    np.testing.assert_allclose(s["params"], o.params, atol=rel * scale)
+    np.testing.assert_allclose(s["B"], o.B, atol=max(1e-12, rel) * 10 * np.max(np.abs(o.B)))
+    w = M.plan_weights(prob, s["n_t"], wl.nf)
+    np.testing.assert_allclose(w, o.w, atol=max(1e-12, rel) * 10 * np.max(np.abs(o.w)))
+    np.testing.assert_allclose(s["B_inv"] @ s["B"], np.eye(wl.nf), atol=1e-9)
+    return s, o
+
+
+def test_plan_matches_oracle_small():
+    _compare_setup(inputs.square_small())
+
+
+def test_plan_matches_oracle_traditional_and_user():
+    wl = inputs.square_small()
+    _compare_setup(wl, mode=F.FILTER_TRADITIONAL)
+    user = np.array([[-0.25, 1.0, 0.1], [0.3, 0.9, -0.2]])
+    _compare_setup(wl, mode=F.FILTER_USER, user=user)
+
+
+def test_plan_matches_oracle_large_workload():
+    wl = inputs.square_large()
+    s, o = _compare_setup(wl, n_p=wl.n_p)
+    assert s["interior_points"] == 1023 * 1023
+
+
+def test_plan_matches_oracle_ill_conditioned_optimiser():
+    """Clustered frequencies on a 70 x 45 grid: cond(M) ~ 6e4, parameters agree to eps cond(M)^2."""
+    wl = inputs.gaussian_workload("ragged", (70, 45), 8,
+                                  lambda r: inputs.draw_frequencies(r, 8, 10.0, 60.0), 400.0, 77,
+                                  length=(1.3, 0.9))
+    s, o = _compare_setup(wl, n_p=2)
+    assert o.cond_M > 1e4
+
+
+def test_plan_matches_oracle_3d_two_layer():
+    wl = inputs.gaussian_workload("t3", (24, 20, 16), 4, [8.3, 12.1, 19.0, 27.5], 300.0, 5,
+                                  length=(1.0, 1.1, 0.9))
+    _compare_setup(wl, c_hi=1.5)
+
+
+def _implicit_dt(omega1, n_p, n_t):
+    # trapezoidal scheme (alpha, beta) = (1/2, 0): cos(omega~ dt) = 1 / (1 + (omega dt)^2 / 2)
+    # and omega~_1 N_t dt = 2 pi N_p, so (omega_1 dt)^2 = 2 (1 - cos theta) / cos theta.
+    theta = 2 * math.pi * n_p / n_t
+    return math.sqrt(2 * (1 - math.cos(theta)) / math.cos(theta)) / omega1
+
+
+def test_optimiser_reproduces_printed_parameters(printed_close):
+    """Algorithm 2 in the library against the optimised cases printed in the paper."""
+    with open(os.path.join(ROOT, "tests", "golden", "paper_filter_parameters.json")) as fh:
+        cases = json.load(fh)["discrete_cases"]
+    for case in cases:
+        om = np.array(case["omega"])
+        dt = _implicit_dt(om[0], case["n_p"], case["n_t"])
+        omt = M.adjusted_frequency(om, dt, 0.5, 0.0)
+        params, lam_max, n_lambda = M.opt_parameters(omt, case["n_p"], case["n_t"])
+        assert n_lambda == case["n_lambda"]
+        if "lam_max_abs_tol" in case:
+            assert abs(lam_max - float(case["lam_max"])) <= case["lam_max_abs_tol"]
+        else:
+            printed_close(lam_max, case["lam_max"], "lam_max")
+        if case.get("params"):
+            for m, p in enumerate(case["params"]):
+                for k in range(3):
+                    printed_close(params[m, k], p[k], f"p[{m}][{k}]")
+        if case.get("params_columns"):
+            for k, key in enumerate("acs"):
+                for m, text in enumerate(case["params_columns"][key]):
+                    printed_close(params[m, k], text, f"{key}[{m}]")
+
+
+def test_adjusted_frequency_matches_definition():
+    om = np.array([3.0, 9.3, 41.0])
+    dt = 0.013
+    for alpha, beta in ((0.0, 1.0), (0.5, 0.0)):
+        got = M.adjusted_frequency(om, dt, alpha, beta)
+        x = om * dt
+        want = np.arccos((1 - 0.5 * beta * x * x) / (1 + alpha * x * x)) / dt
+        np.testing.assert_allclose(got, want, rtol=1e-14)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(omega=[9.3, 5.5]),            # not increasing
+    dict(omega=[-1.0, 5.5]),           # not positive
+    dict(n=(1, 64)),                   # too few cells
+    dict(cfl=1.5),
+    dict(n_p=0),
+    dict(omega=[1.0] * 17),            # too many frequencies
+])
+def test_invalid_problems_are_rejected(bad):
+    args = dict(n=(64, 64), length=(1.0, 1.0), omega=[5.5, 9.3])
+    args.update(bad)
+    omega = args.pop("omega")
+    n, length = args.pop("n"), args.pop("length")
+    prob, keep = M.make_problem(n, length, omega, **args)
+    with pytest.raises(_lib.MfwhError) as e:
+        M.plan(prob)
+    assert e.value.status == _lib.ERR_INVALID_ARG
+
+
+def test_nearly_equal_frequencies_are_singular():
+    prob, keep = M.make_problem((32, 32), (1.0, 1.0), [7.0, 7.0 + 1e-9])
+    with pytest.raises(_lib.MfwhError) as e:
+        M.plan(prob)
+    assert e.value.status == _lib.ERR_SINGULAR
