@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--solve", action="store_true", help="also time one unrestarted solve to 1e-8")
+    ap.add_argument("--no-clocks", action="store_true",
+                    help="do not sample nvidia-smi (for runs under a profiler)")
     return ap.parse_args()
 
 
@@ -270,13 +272,14 @@ def main():
         ms, step_launches, launches = solver.last_timing()
         return info, ms, step_launches, launches + 1
 
-    for _ in range(max(3, args.warmup)):
+    for _ in range(args.warmup):
         one_step()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     sampler = ClockSampler(local)
-    sampler.start()
+    if not args.no_clocks:
+        sampler.start()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -371,7 +374,7 @@ def main():
                  "fp64_alu_frac": round(achieved_tf / FP64_PEAK_TFLOPS, 4)})
     line = {
         "metric": "stencil Gpts/s (+N_f filters)", "value": round(value, 3), "unit": "Gpts/s",
-        "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(wl, n_t),
