@@ -177,6 +177,33 @@ mfwh_status mfwh_solve_gmres(mfwh_handle_t h, int restart, double tol, int max_i
  * v: host or device [nf][points]; r_out: host [nf].  Synchronous. */
 mfwh_status mfwh_residual(mfwh_handle_t h, const double* v, double* r_out);
 
+/* Allocation-free Helmholtz residual (no counterpart in the paper).
+ * For callers that cannot allocate device memory at the point where they need
+ * the residual: code whose device memory belongs to another allocator (a
+ * framework's caching allocator, or a pool sized once at start-up) and must
+ * not grow outside it, and loops that cannot accept the implicit device
+ * synchronisation cudaMalloc / cudaFree may cause.  It computes what
+ * mfwh_residual computes, without a handle, and allocates nothing: its
+ * reduction scratch is one fixed array of MFWH_NOALLOC_SCRATCH_DOUBLES doubles
+ * (256 KiB) in the library's device memory, which every GPU that loads the
+ * library holds until the process exits.
+ *   prob:    grid (dim, n, length), nf, omega and the wave-speed fields, as for
+ *            mfwh_create; the other fields are not used
+ *   forcing: device [nf][points], the values f_m
+ *   v:       device [nf][points]
+ *   r_out:   host [nf], receives r_h^{(m)}
+ *   stream:  cudaStream_t to run on (NULL = legacy default stream); the call
+ *            synchronises that stream before it returns.
+ * The first call on each device looks up the array's device address (set-up,
+ * once per device, with that device current): make that first call before any
+ * stream capture.  Every call uses the same array, so calls whose work
+ * overlaps on the GPU (from other threads or streams) race and must be
+ * serialised by the caller.  A call needs 1216 * nf + 2 * nf doubles; a
+ * problem needing more than the array holds is rejected (MFWH_ERR_INVALID_ARG). */
+#define MFWH_NOALLOC_SCRATCH_DOUBLES 32768
+mfwh_status mfwh_residual_noalloc(const mfwh_problem* prob, const double* forcing,
+                                  const double* v, double* r_out, void* stream);
+
 /* Copy of the handle's set-up. */
 mfwh_status mfwh_get_setup(mfwh_handle_t h, mfwh_setup* out);
 

@@ -98,6 +98,18 @@ def opt_parameters(omega, n_p, n_t, n_delta=20, c_delta=2.0):
     return out, lam.value, nl.value
 
 
+def mfwh_residual_noalloc(problem, forcing, v, stream=None):
+    """Helmholtz residual through the allocation-free entry point (no handle; the
+    library's fixed device scratch array).  forcing, v: device tensors."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    r = np.zeros(problem.nf)
+    _lib.check(_lib.load().mfwh_residual_noalloc(C.byref(problem), _as_ptr(forcing), _as_ptr(v),
+                                                 _dptr(r), C.c_void_p(stream)))
+    return r
+
+
 def setup_arrays(s):
     """numpy views of an mfwh_setup's tables, trimmed to nf."""
     nf = s.nf

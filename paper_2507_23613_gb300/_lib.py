@@ -99,6 +99,7 @@ _SIGNATURES = {
     "mfwh_solve_gmres": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_double,
                                    C.c_void_p, C.POINTER(SolveInfo)]),
     "mfwh_residual": (C.c_int, [C.c_void_p, C.c_void_p, _dp]),
+    "mfwh_residual_noalloc": (C.c_int, [C.POINTER(Problem), C.c_void_p, C.c_void_p, _dp, C.c_void_p]),
     "mfwh_get_setup": (C.c_int, [C.c_void_p, C.POINTER(Setup)]),
     "mfwh_last_timing": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "mfwh_destroy": (None, [C.c_void_p]),

@@ -1,0 +1,73 @@
+"""The allocation-free residual entry point (mfwh_residual_noalloc) against the
+handle-based mfwh_residual.
+
+mfwh_residual_noalloc is for callers that cannot allocate device memory where
+they need the check (device memory owned by another allocator, or loops that
+cannot accept the implicit synchronisation of cudaMalloc / cudaFree); it keeps
+its reduction scratch in a fixed device array of the library instead.  This
+file is collected last so that a run stopping at the first failure has run
+every other test first; it also passes on its own in a fresh process.
+"""
+
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import paper_2507_23613_gb300 as M
+from paper_2507_23613_gb300 import _lib, build, inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    return _lib.load()
+
+
+def _noalloc(lib, prob, f, v, stream):
+    r = np.zeros(prob.nf)
+    st = lib.mfwh_residual_noalloc(C.byref(prob), C.c_void_p(f.data_ptr()), C.c_void_p(v.data_ptr()),
+                                   r.ctypes.data_as(C.POINTER(C.c_double)), C.c_void_p(stream))
+    return st, r
+
+
+@pytest.mark.parametrize("dims,c_hi", [((48, 40), None), ((20, 18, 16), 1.5)])
+def test_noalloc_matches_handle_residual_twice(lib, dims, c_hi):
+    nf = 3
+    wl = inputs.gaussian_workload("noalloc", dims, nf, [6.1, 9.7, 15.2], 200.0, 41)
+    kw = {} if c_hi is None else dict(c_lo=1.0, c_hi=c_hi, interface=0.5, layer_axis=len(dims) - 1)
+    f = torch.from_numpy(wl.forcing).cuda()
+    solver = M.Solver(wl.n, wl.length, wl.omega, f, **kw)
+    prob, keep = M.make_problem(wl.n, wl.length, wl.omega, **kw)
+    stream = torch.cuda.current_stream().cuda_stream
+    rng = np.random.default_rng(7)
+    for call in range(2):                  # two calls in a row, different inputs
+        v = torch.from_numpy(rng.normal(size=wl.forcing.shape) * 0.01).cuda()
+        want = solver.residual(v)
+        st, got = _noalloc(lib, prob, f, v, stream)
+        assert st == _lib.OK, lib.mfwh_last_error()
+        np.testing.assert_allclose(got, want, rtol=TOL, atol=0.0)
+    solver.close()
+
+
+def test_noalloc_rejects_host_pointers_and_bad_sizes(lib):
+    wl = inputs.gaussian_workload("noalloc", (16, 16), 2, [5.5, 9.3], 200.0, 42)
+    prob, keep = M.make_problem(wl.n, wl.length, wl.omega)
+    host = np.zeros_like(wl.forcing)
+    r = np.zeros(2)
+    st = lib.mfwh_residual_noalloc(C.byref(prob), C.c_void_p(host.ctypes.data), C.c_void_p(host.ctypes.data),
+                                   r.ctypes.data_as(C.POINTER(C.c_double)), None)
+    assert st == _lib.ERR_INVALID_ARG
+    prob.nf = 17
+    f = torch.zeros(wl.forcing.shape, dtype=torch.float64, device="cuda")
+    st = lib.mfwh_residual_noalloc(C.byref(prob), C.c_void_p(f.data_ptr()), C.c_void_p(f.data_ptr()),
+                                   r.ctypes.data_as(C.POINTER(C.c_double)), None)
+    assert st == _lib.ERR_INVALID_ARG
