@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--solve", action="store_true", help="also time one unrestarted solve to 1e-8")
+    ap.add_argument("--time-block", type=int, default=0,
+                    help="leapfrog steps per kernel launch (0 = library default)")
     ap.add_argument("--no-clocks", action="store_true",
                     help="do not sample nvidia-smi (for runs under a profiler)")
     return ap.parse_args()
@@ -257,7 +259,7 @@ def main():
     stream = torch.cuda.Stream()
     f_dev = torch.from_numpy(wl.forcing).cuda()
     solver = M.Solver(wl.n, wl.length, wl.omega, f_dev, stream=stream.cuda_stream,
-                      n_p=wl.n_p, cfl=wl.cfl)
+                      n_p=wl.n_p, cfl=wl.cfl, time_block=args.time_block)
     n_t = solver.setup["n_t"]
     N = wl.forcing.size
     v = torch.zeros(wl.forcing.shape, dtype=torch.float64, device="cuda")

@@ -78,6 +78,10 @@ typedef struct {
   int n_delta;               /* N_delta of eq. LambdaRange (paper: 20) */
   double c_delta;            /* c_delta of eq. LambdaRange (paper: 2) */
   int precision;             /* MFWH_PREC_FP64 */
+  int time_block;            /* leapfrog steps per pass over HBM: 0 = library default (1 for
+                                FP64), 1 = one step per kernel launch, 4 or 8 = temporal
+                                blocking with that depth (2D grids only).  Results are
+                                bit-identical for every depth. */
 } mfwh_problem;
 
 /* Everything the set-up derives from a problem (Algorithm 1, first two lines;

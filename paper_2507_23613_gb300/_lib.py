@@ -51,6 +51,7 @@ class Problem(C.Structure):
         ("n_delta", C.c_int),
         ("c_delta", C.c_double),
         ("precision", C.c_int),
+        ("time_block", C.c_int),
     ]
 
 

@@ -1,6 +1,7 @@
 // C ABI of libmfwh: handle life cycle, the MFWH map Pi, the fixed-point
 // iteration (Algorithm 1), GMRES on A = I - S (Section "Acceleration by Krylov
 // methods") and the Helmholtz residual (eq. errorAndResid).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -71,6 +72,10 @@ struct mfwh_handle_s {
   double* f = nullptr;              // forcing [nf][P]
   double* Wa = nullptr;             // wave levels (ping-pong)
   double* Wb = nullptr;
+  double* Wc2 = nullptr;            // second pair of wave levels (temporal blocking:
+  double* Wp2 = nullptr;            // a launch reads one pair and writes the other)
+  double* d_wq = nullptr;           // [(N_t + 1) * nf] filter weights w_{n,m}
+  double* d_cos = nullptr;          // [(N_t + 1) * nf] cos(omega~_m t^n)
   double* q = nullptr;              // filter accumulators [nf][P]
   double* res_partial = nullptr;
   double* res_out = nullptr;
@@ -120,8 +125,12 @@ void layer_coef(const mfwh_handle_t h, double c2, double a_cur, double kappa, La
 }
 
 // v_out = Pi(v_in) (forced) or S v_in; with vsub: v_out = vsub - (that).
+mfwh_status apply_pi_tb(mfwh_handle_t h, const double* vin, double* vout, int forced,
+                        const double* vsub);
+
 mfwh_status apply_pi(mfwh_handle_t h, const double* vin, double* vout, int forced,
                      const double* vsub) {
+  if (h->plan.time_block > 1) return apply_pi_tb(h, vin, vout, forced, vsub);
   const Plan& P = h->plan;
   const int nf = h->nf;
   const int n_t = P.s.n_t;
@@ -156,6 +165,63 @@ mfwh_status apply_pi(mfwh_handle_t h, const double* vin, double* vout, int force
   }
   h->step_launches += n_t;
   h->total_launches += n_t;
+  if (timed) {
+    CK(cudaEventRecord(h->ev[h->ev_used + 1], st));
+    h->ev_used += 2;
+  }
+  CK(cudaGetLastError());
+  return MFWH_OK;
+}
+
+// Temporally blocked wave solve (2D): ceil(N_t / depth) launches, alternating between the
+// two pairs of wave-level buffers; the last launch writes v_out.
+mfwh_status apply_pi_tb(mfwh_handle_t h, const double* vin, double* vout, int forced,
+                        const double* vsub) {
+  const Plan& P = h->plan;
+  const int nf = h->nf;
+  const int n_t = P.s.n_t;
+  const double dt = P.s.dt;
+  const int depth = P.time_block;
+  cudaStream_t st = h->stream;
+  launch_init(nf, h->geom, vin, h->Wa, h->q, &P.w[0], st);
+  h->total_launches += 1;
+  const bool timed = h->ev_used + 2 <= (int)h->ev.size();
+  if (timed) CK(cudaEventRecord(h->ev[h->ev_used], st));
+  TBHost a;
+  layer_coef(h, P.c2_lo, 2.0, dt * dt, &a.reg_lo);
+  layer_coef(h, P.c2_hi, 2.0, dt * dt, &a.reg_hi);
+  layer_coef(h, P.c2_lo, 1.0, 0.5 * dt * dt, &a.first_lo);
+  layer_coef(h, P.c2_hi, 1.0, 0.5 * dt * dt, &a.first_hi);
+  a.wq_table = h->d_wq;
+  a.cos_table = h->d_cos;
+  a.dt2 = dt * dt;
+  a.half_dt2 = 0.5 * dt * dt;
+  a.depth = depth;
+  a.forced = forced;
+  a.subtract = vsub != nullptr;
+  std::memcpy(a.binv, h->sh.binv, sizeof(a.binv));
+  const double* in_c = h->Wa;
+  const double* in_p = nullptr;     // W^{-1} = 0 before the first step
+  double* out_c = h->Wc2;
+  double* out_p = h->Wp2;
+  int launches = 0;
+  for (int n0 = 0; n0 < n_t;) {
+    a.n0 = n0;
+    a.steps = std::min(depth, n_t - n0);
+    a.last = n0 + a.steps == n_t;
+    launch_tb2d(nf, h->geom, in_c, in_p, out_c, out_p, h->f, h->q, vout, vsub, a, st);
+    ++launches;
+    n0 += a.steps;
+    // next launch reads what this one wrote and writes the other pair
+    double* nc = (out_c == h->Wc2) ? h->Wa : h->Wc2;
+    double* np = (out_c == h->Wc2) ? h->Wb : h->Wp2;
+    in_c = out_c;
+    in_p = out_p;
+    out_c = nc;
+    out_p = np;
+  }
+  h->step_launches += launches;
+  h->total_launches += launches;
   if (timed) {
     CK(cudaEventRecord(h->ev[h->ev_used + 1], st));
     h->ev_used += 2;
@@ -309,12 +375,17 @@ mfwh_status mfwh_create(const mfwh_problem* prob, void* stream, mfwh_handle_t* o
   };
   cudaError_t e = cudaGetDevice(&h->device);
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaGetDevice"));
+  const int64_t tables = (int64_t)(P.s.n_t + 1) * h->nf;
   struct {
     double** p;
     int64_t n;
   } bufs[] = {{&h->f, h->N},
               {&h->Wa, h->P},
               {&h->Wb, h->P},
+              {&h->Wc2, h->P},
+              {&h->Wp2, h->P},
+              {&h->d_wq, tables},
+              {&h->d_cos, tables},
               {&h->q, h->N},
               {&h->res_partial, residual_partial_size(MFWH_MAX_NF)},
               {&h->res_out, 2 * MFWH_MAX_NF},
@@ -339,6 +410,14 @@ mfwh_status mfwh_create(const mfwh_problem* prob, void* stream, mfwh_handle_t* o
   // Boundary values of the wave levels are never written by the step kernels and must be 0.
   e = cudaMemsetAsync(h->Wa, 0, sizeof(double) * h->P, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->Wb, 0, sizeof(double) * h->P, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->Wc2, 0, sizeof(double) * h->P, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->Wp2, 0, sizeof(double) * h->P, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->d_wq, P.w.data(), sizeof(double) * tables, cudaMemcpyHostToDevice,
+                        h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->d_cos, P.cosf.data(), sizeof(double) * tables, cudaMemcpyHostToDevice,
+                        h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->f, 0, sizeof(double) * h->N, h->stream);
   if (e == cudaSuccess && prob->forcing)
     e = cudaMemcpyAsync(h->f, prob->forcing, sizeof(double) * h->N, cudaMemcpyDefault, h->stream);
@@ -568,8 +647,9 @@ mfwh_status mfwh_last_timing(mfwh_handle_t h, double* step_ms, int64_t* step_lau
 void mfwh_destroy(mfwh_handle_t h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
-  double* bufs[] = {h->f, h->Wa, h->Wb, h->q, h->res_partial, h->res_out, h->dot_partial,
-                    h->dot_out, h->vec_b, h->vec_x, h->basis};
+  double* bufs[] = {h->f,         h->Wa,      h->Wb,          h->Wc2,     h->Wp2,
+                    h->d_wq,      h->d_cos,   h->q,           h->res_partial, h->res_out,
+                    h->dot_partial, h->dot_out, h->vec_b,     h->vec_x,   h->basis};
   for (double* b : bufs)
     if (b) cudaFree(b);
   if (h->pinned) cudaFreeHost(h->pinned);

@@ -41,6 +41,23 @@ struct StepHost {
   double binv[MFWH_MAX_NF * MFWH_MAX_NF];
 };
 
+// Arguments of one temporally blocked launch (wave_tb.cu).
+struct TBHost {
+  LayerCoef reg_lo, reg_hi, first_lo, first_hi;
+  const double* wq_table;    // device [(N_t + 1) * nf] w_{n,m}
+  const double* cos_table;   // device [(N_t + 1) * nf] cos(omega~_m t^n)
+  double dt2, half_dt2;
+  int n0, steps, depth;      // first level index, steps in this launch, template depth (4 or 8)
+  int forced, last, subtract;
+  double binv[MFWH_MAX_NF * MFWH_MAX_NF];
+};
+// Up to `depth` leapfrog+filter steps of a 2D grid in one launch: reads (Wc_in, Wp_in)
+// (Wp_in may be null: W^{-1} = 0 before the first step), writes (Wc_out, Wp_out) and q, or on
+// the last launch v_out = B^{-1} q (or v_sub - B^{-1} q).  Output buffers must not alias inputs.
+void launch_tb2d(int nf, const Geom& g, const double* Wc_in, const double* Wp_in, double* Wc_out,
+                 double* Wp_out, const double* f, double* q, double* vout, const double* vsub,
+                 const TBHost& h, cudaStream_t st);
+
 // W^0 = sum_m v_m (0 on the boundary; v == nullptr gives W^0 = 0) and q_m = w0_m W^0.
 void launch_init(int nf, const Geom& g, const double* v, double* W0, double* q, const double* w0,
                  cudaStream_t st);
