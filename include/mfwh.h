@@ -51,7 +51,10 @@ typedef enum {
 } mfwh_status;
 
 enum { MFWH_FILTER_OPTIMIZED = 0, MFWH_FILTER_TRADITIONAL = 1, MFWH_FILTER_USER = 2 };
-enum { MFWH_PREC_FP64 = 0 };
+/* Arithmetic of the wave solve.  FP64: every step in FP64.  FP32_KAHAN: wave levels and
+   steps in FP32 (increment form of the leapfrog scheme), filter sums with Kahan
+   compensation, the filter solve B^{-1} q, GMRES and the residual in FP64. */
+enum { MFWH_PREC_FP64 = 0, MFWH_PREC_FP32_KAHAN = 1 };
 enum { MFWH_C_CONST = 0, MFWH_C_TWO_LAYER = 1 };
 
 typedef struct mfwh_handle_s* mfwh_handle_t;
@@ -77,11 +80,13 @@ typedef struct {
   const double* user_params; /* host, [nf][3] (a, c, s) when filter_mode == MFWH_FILTER_USER */
   int n_delta;               /* N_delta of eq. LambdaRange (paper: 20) */
   double c_delta;            /* c_delta of eq. LambdaRange (paper: 2) */
-  int precision;             /* MFWH_PREC_FP64 */
+  int precision;             /* MFWH_PREC_FP64 or MFWH_PREC_FP32_KAHAN */
   int time_block;            /* leapfrog steps per pass over HBM: 0 = library default (1 for
-                                FP64), 1 = one step per kernel launch, 4 or 8 = temporal
-                                blocking with that depth (2D grids only).  Results are
-                                bit-identical for every depth. */
+                                FP64; 8 for FP32 in 2D), 1 = one step per kernel launch,
+                                4 or 8 (or 16 for FP32) = temporal blocking with that depth
+                                (2D grids only).  Results are bit-identical for every depth. */
+  int tile_shape;            /* FP32 blocked kernel: 0 = 32x32 tile, 512 threads (default);
+                                1 = 32x32, 256 threads; 2 = 32x64, 512 threads */
 } mfwh_problem;
 
 /* Everything the set-up derives from a problem (Algorithm 1, first two lines;

@@ -25,6 +25,7 @@ FILTER_OPTIMIZED = 0
 FILTER_TRADITIONAL = 1
 FILTER_USER = 2
 PREC_FP64 = 0
+PREC_FP32_KAHAN = 1
 C_CONST = 0
 C_TWO_LAYER = 1
 
@@ -52,6 +53,7 @@ class Problem(C.Structure):
         ("c_delta", C.c_double),
         ("precision", C.c_int),
         ("time_block", C.c_int),
+        ("tile_shape", C.c_int),
     ]
 
 

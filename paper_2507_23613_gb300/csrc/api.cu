@@ -92,6 +92,14 @@ struct mfwh_handle_s {
   int64_t step_launches = 0;
   int64_t total_launches = 0;
   StepHost sh;                      // per-step kernel arguments (reused)
+  // FP32 path (precision MFWH_PREC_FP32_KAHAN)
+  float* f32 = nullptr;             // forcing rounded to FP32 [nf][P]
+  float* W32[4] = {};               // (W, D) pairs: W32[0], W32[1] and W32[2], W32[3]
+  float* qs = nullptr;              // Kahan sums [nf][P]
+  float* qc = nullptr;              // Kahan compensations [nf][P]
+  float* wq32 = nullptr;            // device [(N_t + 1) * nf] w_{n,m}
+  float* fc32 = nullptr;            // device [N_t * nf] kappa_n cos(omega~_m t^n)
+  std::vector<float> wq32_h, fc32_h;
 };
 
 namespace {
@@ -124,12 +132,97 @@ void layer_coef(const mfwh_handle_t h, double c2, double a_cur, double kappa, La
   L->A0 = a_cur - 2.0 * (L->Ax + L->Ay + L->Az);
 }
 
+void layer_coef32(const mfwh_handle_t h, double c2, double kappa, Coef32* L) {
+  const double k = kappa * c2;
+  L->Ax = (float)(k * h->inv_h2[0]);
+  L->Ay = (float)(k * h->inv_h2[1]);
+  L->Az = (float)(k * h->inv_h2[2]);
+}
+
+// FP32 wave solve (increment form, Kahan filter sums), FP64 filter solve.
+mfwh_status apply_pi32(mfwh_handle_t h, const double* vin, double* vout, int forced,
+                       const double* vsub) {
+  const Plan& P = h->plan;
+  const int nf = h->nf;
+  const int n_t = P.s.n_t;
+  const double dt = P.s.dt;
+  cudaStream_t st = h->stream;
+  float w0[MFWH_MAX_NF];
+  for (int m = 0; m < nf; ++m) w0[m] = h->wq32_h[m];
+  launch_init32(nf, h->geom, vin, h->W32[0], h->qs, h->qc, w0, st);
+  h->total_launches += 1;
+  const bool timed = h->ev_used + 2 <= (int)h->ev.size();
+  if (timed) CK(cudaEventRecord(h->ev[h->ev_used], st));
+  Coef32 reg_lo, reg_hi, first_lo, first_hi;
+  layer_coef32(h, P.c2_lo, dt * dt, &reg_lo);
+  layer_coef32(h, P.c2_hi, dt * dt, &reg_hi);
+  layer_coef32(h, P.c2_lo, 0.5 * dt * dt, &first_lo);
+  layer_coef32(h, P.c2_hi, 0.5 * dt * dt, &first_hi);
+  int launches = 0;
+  if (P.time_block > 1) {
+    TB32Host a;
+    a.reg_lo = reg_lo;
+    a.reg_hi = reg_hi;
+    a.first_lo = first_lo;
+    a.first_hi = first_hi;
+    a.wq = h->wq32;
+    a.fc = h->fc32;
+    a.binv = h->sh.binv;
+    a.depth = P.time_block;
+    a.shape = P.tile_shape;
+    a.forced = forced;
+    int cur = 0;                 // pair holding the input: (W32[2 cur], W32[2 cur + 1])
+    for (int n0 = 0; n0 < n_t;) {
+      a.n0 = n0;
+      a.steps = std::min(P.time_block, n_t - n0);
+      a.last = n0 + a.steps == n_t;
+      const float* D_in = n0 == 0 ? nullptr : h->W32[2 * cur + 1];
+      launch_tb2d32(nf, h->geom, h->W32[2 * cur], D_in, h->W32[2 * (1 - cur)],
+                    h->W32[2 * (1 - cur) + 1], h->f32, h->qs, h->qc, vout, vsub, a, st);
+      ++launches;
+      n0 += a.steps;
+      cur = 1 - cur;
+    }
+  } else {
+    Step32Host a;
+    a.forced = forced;
+    float* Wc = h->W32[0];
+    float* Wn = h->W32[2];
+    float* D = h->W32[1];
+    for (int n = 0; n < n_t; ++n) {
+      a.lo = n == 0 ? first_lo : reg_lo;
+      a.hi = n == 0 ? first_hi : reg_hi;
+      for (int m = 0; m < nf; ++m) {
+        a.fc[m] = h->fc32_h[(size_t)n * nf + m];
+        a.wq[m] = h->wq32_h[(size_t)(n + 1) * nf + m];
+      }
+      const float* D_in = n == 0 ? nullptr : D;
+      if (n + 1 < n_t) {
+        launch_step32(nf, h->geom, Wc, D_in, Wn, D, h->f32, h->qs, h->qc, a, st);
+        std::swap(Wc, Wn);
+      } else {
+        launch_last32(nf, h->geom, Wc, D_in, h->f32, h->qs, h->qc, vout, vsub, a, h->sh.binv, st);
+      }
+      ++launches;
+    }
+  }
+  h->step_launches += launches;
+  h->total_launches += launches;
+  if (timed) {
+    CK(cudaEventRecord(h->ev[h->ev_used + 1], st));
+    h->ev_used += 2;
+  }
+  CK(cudaGetLastError());
+  return MFWH_OK;
+}
+
 // v_out = Pi(v_in) (forced) or S v_in; with vsub: v_out = vsub - (that).
 mfwh_status apply_pi_tb(mfwh_handle_t h, const double* vin, double* vout, int forced,
                         const double* vsub);
 
 mfwh_status apply_pi(mfwh_handle_t h, const double* vin, double* vout, int forced,
                      const double* vsub) {
+  if (h->plan.precision == MFWH_PREC_FP32_KAHAN) return apply_pi32(h, vin, vout, forced, vsub);
   if (h->plan.time_block > 1) return apply_pi_tb(h, vin, vout, forced, vsub);
   const Plan& P = h->plan;
   const int nf = h->nf;
@@ -397,6 +490,39 @@ mfwh_status mfwh_create(const mfwh_problem* prob, void* stream, mfwh_handle_t* o
     e = cudaMalloc(b.p, sizeof(double) * b.n);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc (workspace)"));
   }
+  if (P.precision == MFWH_PREC_FP32_KAHAN) {
+    const int nf = h->nf;
+    const int n_t = P.s.n_t;
+    const double dt = P.s.dt;
+    h->wq32_h.resize((size_t)(n_t + 1) * nf);
+    h->fc32_h.resize((size_t)n_t * nf);
+    for (size_t i = 0; i < h->wq32_h.size(); ++i) h->wq32_h[i] = (float)P.w[i];
+    for (int n = 0; n < n_t; ++n) {
+      const double kappa = n == 0 ? 0.5 * dt * dt : dt * dt;
+      for (int m = 0; m < nf; ++m)
+        h->fc32_h[(size_t)n * nf + m] = (float)(kappa * P.cosf[(size_t)n * nf + m]);
+    }
+    struct {
+      float** p;
+      int64_t n;
+    } fb[] = {{&h->f32, h->N}, {&h->W32[0], h->P}, {&h->W32[1], h->P}, {&h->W32[2], h->P},
+              {&h->W32[3], h->P}, {&h->qs, h->N}, {&h->qc, h->N},
+              {&h->wq32, (int64_t)h->wq32_h.size()}, {&h->fc32, (int64_t)h->fc32_h.size()}};
+    for (auto& b : fb) {
+      e = cudaMalloc(b.p, sizeof(float) * std::max<int64_t>(b.n, 1));
+      if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc (FP32 workspace)"));
+    }
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+      e = cudaMemsetAsync(h->W32[i], 0, sizeof(float) * h->P, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->wq32, h->wq32_h.data(), sizeof(float) * h->wq32_h.size(),
+                          cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && !h->fc32_h.empty())
+      e = cudaMemcpyAsync(h->fc32, h->fc32_h.data(), sizeof(float) * h->fc32_h.size(),
+                          cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "initialising FP32 workspace"));
+  }
   e = cudaMallocHost(&h->pinned, sizeof(double) * kPinned);
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMallocHost"));
   h->ev.resize(kEventPool);
@@ -421,6 +547,10 @@ mfwh_status mfwh_create(const mfwh_problem* prob, void* stream, mfwh_handle_t* o
   if (e == cudaSuccess) e = cudaMemsetAsync(h->f, 0, sizeof(double) * h->N, h->stream);
   if (e == cudaSuccess && prob->forcing)
     e = cudaMemcpyAsync(h->f, prob->forcing, sizeof(double) * h->N, cudaMemcpyDefault, h->stream);
+  if (e == cudaSuccess && h->f32) {
+    launch_to_float(h->f, h->f32, h->N, h->stream);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "initialising workspace"));
   std::memset(&h->sh, 0, sizeof(h->sh));
@@ -433,6 +563,11 @@ mfwh_status mfwh_create(const mfwh_problem* prob, void* stream, mfwh_handle_t* o
 mfwh_status mfwh_set_forcing(mfwh_handle_t h, const double* forcing) {
   if (!h || !forcing) return fail(MFWH_ERR_INVALID_ARG, "null argument");
   CK(cudaMemcpyAsync(h->f, forcing, sizeof(double) * h->N, cudaMemcpyDefault, h->stream));
+  if (h->f32) {
+    launch_to_float(h->f, h->f32, h->N, h->stream);
+    h->total_launches++;
+    CK(cudaGetLastError());
+  }
   return MFWH_OK;
 }
 
@@ -651,6 +786,10 @@ void mfwh_destroy(mfwh_handle_t h) {
                     h->d_wq,      h->d_cos,   h->q,           h->res_partial, h->res_out,
                     h->dot_partial, h->dot_out, h->vec_b,     h->vec_x,   h->basis};
   for (double* b : bufs)
+    if (b) cudaFree(b);
+  float* fbufs[] = {h->f32, h->W32[0], h->W32[1], h->W32[2], h->W32[3], h->qs, h->qc,
+                    h->wq32, h->fc32};
+  for (float* b : fbufs)
     if (b) cudaFree(b);
   if (h->pinned) cudaFreeHost(h->pinned);
   for (auto& x : h->ev)

@@ -21,7 +21,9 @@ struct Plan {
   int64_t layer_split = 0;           // first grid index along layer_axis in the upper layer
   int layer_axis = 0;
   int dim = 2;
-  int time_block = 1;          // steps per wave-kernel launch (1, 4 or 8)
+  int time_block = 1;          // steps per wave-kernel launch (1, 4, 8 or 16)
+  int tile_shape = 0;          // FP32 blocked-kernel tile shape
+  int precision = MFWH_PREC_FP64;
   int64_t n[3] = {1, 1, 1};
   std::vector<double> w;       // [(n_t + 1) * nf]  filter weights w_{n,m}
   std::vector<double> cosf;    // [(n_t + 1) * nf]  cos(omega~_m t^n)

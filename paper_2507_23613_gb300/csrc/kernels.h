@@ -58,6 +58,42 @@ void launch_tb2d(int nf, const Geom& g, const double* Wc_in, const double* Wp_in
                  double* Wp_out, const double* f, double* q, double* vout, const double* vsub,
                  const TBHost& h, cudaStream_t st);
 
+// ---- FP32 path with compensated filter sums (wave32.cu) ----------------------------
+// Increment form: D' = D + kappa c^2 Delta_h W - sum_m fc_m f_m, W' = W + D', with
+// kappa c^2 / h_i^2 per layer in Coef32.  Filter sums are Kahan pairs (qs, qc), q = qs - qc.
+struct Coef32 {
+  float Ax, Ay, Az;
+};
+struct Step32Host {
+  Coef32 lo, hi;
+  float fc[MFWH_MAX_NF];   // kappa_n cos(omega~_m t^n), rounded to FP32
+  float wq[MFWH_MAX_NF];   // w_{n+1,m}, rounded to FP32
+  int forced;
+};
+struct TB32Host {
+  Coef32 reg_lo, reg_hi, first_lo, first_hi;
+  const float* wq;         // device [(N_t + 1) * nf]
+  const float* fc;         // device [N_t * nf]
+  const double* binv;      // host [MFWH_MAX_NF * MFWH_MAX_NF], row-major, leading dim 16
+  int n0, steps, depth, shape, forced, last;
+};
+// W^0 = fl32(sum_m v_m) (0 on the boundary), qs_m = w0_m W^0, qc_m = 0.
+void launch_init32(int nf, const Geom& g, const double* v, float* W0, float* qs, float* qc,
+                   const float* w0, cudaStream_t st);
+// One step: W_out = W + D', D_out = D' (D_in == nullptr: D = 0; D_out may equal D_in).
+void launch_step32(int nf, const Geom& g, const float* W, const float* D_in, float* W_out,
+                   float* D_out, const float* f, float* qs, float* qc, const Step32Host& h,
+                   cudaStream_t st);
+// Last step fused with V = B^{-1} q in FP64 (or v_sub - that); boundary of v_out = 0.
+void launch_last32(int nf, const Geom& g, const float* W, const float* D, const float* f,
+                   const float* qs, const float* qc, double* vout, const double* vsub,
+                   const Step32Host& h, const double* binv, cudaStream_t st);
+// Up to h.depth (4, 8 or 16) steps of a 2D grid per launch; outputs must not alias inputs.
+void launch_tb2d32(int nf, const Geom& g, const float* W_in, const float* D_in, float* W_out,
+                   float* D_out, const float* f, float* qs, float* qc, double* vout,
+                   const double* vsub, const TB32Host& h, cudaStream_t st);
+void launch_to_float(const double* x, float* y, int64_t n, cudaStream_t st);
+
 // W^0 = sum_m v_m (0 on the boundary; v == nullptr gives W^0 = 0) and q_m = w0_m W^0.
 void launch_init(int nf, const Geom& g, const double* v, double* W0, double* q, const double* w0,
                  cudaStream_t st);

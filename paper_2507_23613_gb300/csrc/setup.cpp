@@ -302,9 +302,14 @@ mfwh_status plan_problem(const mfwh_problem* p, Plan* out) {
     return fail(MFWH_ERR_INVALID_ARG, "user_params is NULL");
   if (p->filter_mode == MFWH_FILTER_OPTIMIZED && (p->n_delta < 1 || !(p->c_delta >= 0.0)))
     return fail(MFWH_ERR_INVALID_ARG, "n_delta must be >= 1 and c_delta >= 0");
-  if (p->precision != MFWH_PREC_FP64) return fail(MFWH_ERR_INVALID_ARG, "unsupported precision");
-  if (p->time_block != 0 && p->time_block != 1 && p->time_block != 4 && p->time_block != 8)
-    return fail(MFWH_ERR_INVALID_ARG, "time_block must be 0, 1, 4 or 8");
+  if (p->precision != MFWH_PREC_FP64 && p->precision != MFWH_PREC_FP32_KAHAN)
+    return fail(MFWH_ERR_INVALID_ARG, "unsupported precision");
+  const bool fp32 = p->precision == MFWH_PREC_FP32_KAHAN;
+  if (p->time_block != 0 && p->time_block != 1 && p->time_block != 4 && p->time_block != 8 &&
+      !(fp32 && p->time_block == 16))
+    return fail(MFWH_ERR_INVALID_ARG, "time_block must be 0, 1, 4 or 8 (or 16 for FP32)");
+  if (p->tile_shape < 0 || p->tile_shape > 2)
+    return fail(MFWH_ERR_INVALID_ARG, "tile_shape must be 0, 1 or 2");
   if (p->dim == 3 && p->time_block > 1)
     return fail(MFWH_ERR_INVALID_ARG, "temporal blocking is available for 2D grids only");
 
@@ -316,7 +321,10 @@ mfwh_status plan_problem(const mfwh_problem* p, Plan* out) {
   P.dim = p->dim;
   // FP64 default: one step per launch.  On GB300 the FP64 step is bound by the FP64 pipe
   // (about 1.2 TFLOP/s), so blocking saves HBM bytes it is not waiting for and adds halo work.
-  P.time_block = p->time_block != 0 ? p->time_block : 1;
+  // FP32 default: 8 steps per launch in 2D (fastest measured depth on GB300).
+  P.time_block = p->time_block != 0 ? p->time_block : (fp32 && p->dim == 2 ? 8 : 1);
+  P.tile_shape = p->tile_shape;
+  P.precision = p->precision;
   double inv_h2 = 0.0;
   s.points = 1;
   s.interior_points = 1;

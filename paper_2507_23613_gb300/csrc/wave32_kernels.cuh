@@ -1,0 +1,508 @@
+// FP32 MFWH wave solve with compensated filter sums, sm_103a.
+//
+// The wave levels are FP32 and the leapfrog scheme (eq. WaveSchemeA, first step
+// eq. implicitFirstStep with alpha = 0) is advanced in its increment form
+//   D^{n+1/2} = D^{n-1/2} + kappa_n (c^2 Delta_h W^n - F^n),   W^{n+1} = W^n + D^{n+1/2},
+// with D^{-1/2} = 0, kappa_0 = dt^2/2 and kappa_n = dt^2 otherwise.  In exact
+// arithmetic this is the same recurrence as W^{n+1} = 2W^n - W^{n-1} + ...; in
+// FP32 it keeps the velocity D exactly where the two-level form would round it,
+// so a rounding of W^{n+1} stays a position error instead of turning into a
+// velocity error that grows over the N_t steps.  The Laplacian is taken as sums
+// of neighbour differences, (W_e - W) + (W_w - W), which are small and nearly
+// exact for smooth fields.
+//
+// The filter sums q_m = sum_n w_{n,m} W^n (eq. pDefQ) are accumulated in FP32
+// with Kahan's compensated summation: a pair (s_m, c_m) per point and frequency,
+// q_m = s_m - c_m.  The filter solve V = B^{-1} q (eq. waveHoltzMatrixIteration)
+// and everything after it are FP64.
+//
+// Two kernels advance the scheme:
+//  * k_tb2d32: 2D, T steps per launch on a 32 x (TY K) tile with a T-point halo in
+//    shared memory (the tile plus a ring of radius T-1-s updated at step s), the
+//    Kahan pairs of the tile's points in registers for all T steps;
+//  * k_step32 / k_last32: one step per launch, 2D or 3D.
+// Both perform the same FP32 operations per point in the same order, so their
+// results are bit-identical.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+
+namespace mfwh {
+
+// The four host launchers of one frequency count, collected so that the
+// translation units wave32_p*.cu can each instantiate a range of counts.
+struct W32Ops {
+  void (*init)(const Geom&, const double*, float*, float*, float*, const float*, cudaStream_t);
+  void (*step)(const Geom&, const float*, const float*, float*, float*, const float*, float*,
+               float*, const Step32Host&, cudaStream_t);
+  void (*last)(const Geom&, const float*, const float*, const float*, const float*, const float*,
+               double*, const double*, const Step32Host&, const double*, cudaStream_t);
+  void (*tb)(const Geom&, const float*, const float*, float*, float*, const float*, float*, float*,
+             double*, const double*, const TB32Host&, cudaStream_t);
+};
+
+namespace {
+
+template <int NF>
+struct Last32Binv {
+  double binv[NF * NF];
+};
+
+template <int NF>
+struct Init32Args {
+  float w0[NF];
+};
+
+template <int NF>
+struct Step32Args {
+  Coef32 lo, hi;
+  float fc[NF];     // kappa_n cos(omega~_m t^n)
+  float wq[NF];     // w_{n+1,m}
+  int forced;
+};
+
+__device__ __forceinline__ bool interior2(int64_t gx, int64_t gy, const Geom& g) {
+  return gx > 0 && gx < g.nx && gy > 0 && gy < g.ny;
+}
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float w, float x) {
+  const float y = fmaf(w, x, -c);
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// kappa c^2 Delta_h W at a point whose value is w and whose neighbour sums of
+// differences are dxx, dyy, dzz, minus the forcing; same order in every kernel.
+template <int NF, int DIM>
+__device__ __forceinline__ float increment(const Coef32& L, float dxx, float dyy, float dzz,
+                                           const float* fc, const float* __restrict__ f,
+                                           int64_t p, int64_t points, int forced) {
+  float inc = L.Ay * dyy;
+  if (DIM == 3) inc = fmaf(L.Az, dzz, inc);
+  inc = fmaf(L.Ax, dxx, inc);
+  if (forced) {
+#pragma unroll
+    for (int m = 0; m < NF; ++m) inc = fmaf(-fc[m], f[m * points + p], inc);
+  }
+  return inc;
+}
+
+// ---- one step per launch (2D and 3D) -------------------------------------------
+
+constexpr int kBX = 32, kBY = 8;
+
+template <int DIM>
+__device__ __forceinline__ bool index_of(const Geom& g, int64_t& i, int64_t& j, int64_t& k,
+                                         int64_t& p, bool& interior) {
+  i = (int64_t)blockIdx.x * kBX + threadIdx.x;
+  j = (int64_t)blockIdx.y * kBY + threadIdx.y;
+  k = DIM == 3 ? (int64_t)blockIdx.z : 0;
+  const bool inside = i <= g.nx && j <= g.ny;
+  p = k * g.sz + j * g.sy + i;
+  interior = inside && i > 0 && i < g.nx && j > 0 && j < g.ny &&
+             (DIM == 2 || (k > 0 && k < g.nz));
+  return inside;
+}
+
+template <int NF, int DIM>
+__device__ __forceinline__ void step_point(const float* __restrict__ W, const float* D,
+                                           const float* __restrict__ f, const Step32Args<NF>& a,
+                                           const Geom& g, int64_t i, int64_t j, int64_t k,
+                                           int64_t p, float& wn, float& dn) {
+  const int64_t li = g.layer_axis == 0 ? i : (g.layer_axis == 1 ? j : k);
+  const Coef32& L = li >= g.layer_split ? a.hi : a.lo;
+  const float w = W[p];
+  const float dxx = (W[p - 1] - w) + (W[p + 1] - w);
+  const float dyy = (W[p - g.sy] - w) + (W[p + g.sy] - w);
+  const float dzz = DIM == 3 ? (W[p - g.sz] - w) + (W[p + g.sz] - w) : 0.0f;
+  const float inc = increment<NF, DIM>(L, dxx, dyy, dzz, a.fc, f, p, g.points, a.forced);
+  dn = (D ? D[p] : 0.0f) + inc;
+  wn = w + dn;
+}
+
+// W_out = W + D', D' = D + increment (D_out may alias D_in; W_out must not alias W_in);
+// Kahan sums updated in place.
+template <int NF, int DIM>
+__global__ void __launch_bounds__(kBX * kBY)
+k_step32(const float* __restrict__ W, const float* D_in, float* __restrict__ W_out, float* D_out,
+         const float* __restrict__ f, float* __restrict__ qs, float* __restrict__ qc,
+         const Step32Args<NF> a, const Geom g) {
+  int64_t i, j, k, p;
+  bool interior;
+  index_of<DIM>(g, i, j, k, p, interior);
+  if (!interior) return;
+  float wn, dn;
+  step_point<NF, DIM>(W, D_in, f, a, g, i, j, k, p, wn, dn);
+  W_out[p] = wn;
+  D_out[p] = dn;
+#pragma unroll
+  for (int m = 0; m < NF; ++m) {
+    float s = qs[m * g.points + p], c = qc[m * g.points + p];
+    kahan_add(s, c, a.wq[m], wn);
+    qs[m * g.points + p] = s;
+    qc[m * g.points + p] = c;
+  }
+}
+
+template <int NF>
+__device__ __forceinline__ void filter_solve_out(const float* s, const float* c, const double* binv,
+                                                 int subtract, const double* vsub, double* vout,
+                                                 int64_t p, int64_t points, bool interior) {
+  double qd[NF];
+#pragma unroll
+  for (int m = 0; m < NF; ++m) qd[m] = (double)s[m] - (double)c[m];
+#pragma unroll
+  for (int m = 0; m < NF; ++m) {
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < NF; ++j) acc = fma(binv[m * NF + j], qd[j], acc);
+    double val = 0.0;
+    if (interior) val = subtract ? vsub[m * points + p] - acc : acc;
+    vout[m * points + p] = val;
+  }
+}
+
+template <int NF, int DIM>
+__global__ void __launch_bounds__(kBX * kBY)
+k_last32(const float* __restrict__ W, const float* __restrict__ D, const float* __restrict__ f,
+         const float* __restrict__ qs, const float* __restrict__ qc, double* vout,
+         const double* vsub, const Step32Args<NF> a, const Last32Binv<NF> b, int subtract,
+         const Geom g) {
+  int64_t i, j, k, p;
+  bool interior;
+  if (!index_of<DIM>(g, i, j, k, p, interior)) return;
+  float s[NF], c[NF];
+#pragma unroll
+  for (int m = 0; m < NF; ++m) s[m] = c[m] = 0.0f;
+  if (interior) {
+    float wn, dn;
+    step_point<NF, DIM>(W, D, f, a, g, i, j, k, p, wn, dn);
+#pragma unroll
+    for (int m = 0; m < NF; ++m) {
+      s[m] = qs[m * g.points + p];
+      c[m] = qc[m * g.points + p];
+      kahan_add(s[m], c[m], a.wq[m], wn);
+    }
+  }
+  filter_solve_out<NF>(s, c, b.binv, subtract, vsub, vout, p, g.points, interior);
+}
+
+// ---- temporally blocked 2D kernel ----------------------------------------------
+
+template <int NF>
+struct TB32Args {
+  Coef32 reg_lo, reg_hi, first_lo, first_hi;
+  const float* wq;   // [(N_t + 1) * NF]
+  const float* fc;   // [N_t * NF]
+  int n0, steps, forced, last, subtract;
+};
+
+template <int NF, int T, int TY, int K, int MB>
+__global__ void __launch_bounds__(32 * TY, MB)
+k_tb2d32(const float* __restrict__ W_in, const float* __restrict__ D_in,
+         float* __restrict__ W_out, float* __restrict__ D_out, const float* __restrict__ f,
+         float* __restrict__ qs, float* __restrict__ qc, double* vout, const double* vsub,
+         const TB32Args<NF> a, const Last32Binv<NF> b, const Geom g) {
+  constexpr int BX = 32, BY = TY * K;
+  constexpr int EX = BX + 2 * T, EY = BY + 2 * T, E = EX * EY;
+  constexpr int NT = 32 * TY;
+  extern __shared__ float sm32[];
+  float* Wc = sm32;             // W^n on the extended tile
+  float* Wn = sm32 + E;         // W^{n+1}
+  float* Dv = sm32 + 2 * E;     // D, updated in place
+  float* s_wq = sm32 + 3 * E;   // [T][NF]
+  float* s_fc = s_wq + T * NF;  // [T][NF]
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * 32 + tx;
+  const int64_t bx0 = (int64_t)blockIdx.x * BX, by0 = (int64_t)blockIdx.y * BY;
+  const int64_t x0 = bx0 - T, y0 = by0 - T;
+
+  for (int e = tid; e < E; e += NT) {
+    const int lx = e % EX, ly = e / EX;
+    const int64_t gx = x0 + lx, gy = y0 + ly;
+    const bool in = gx >= 0 && gx <= g.nx && gy >= 0 && gy <= g.ny;
+    const int64_t p = gy * g.sy + gx;
+    const float w = in ? W_in[p] : 0.0f;
+    Wc[e] = w;
+    Wn[e] = w;
+    Dv[e] = (in && D_in != nullptr) ? D_in[p] : 0.0f;
+  }
+  for (int e = tid; e < a.steps * NF; e += NT) {
+    const int st = e / NF, m = e % NF;
+    const int n = a.n0 + st;
+    s_wq[e] = a.wq[(n + 1) * NF + m];
+    s_fc[e] = a.forced ? a.fc[n * NF + m] : 0.0f;
+  }
+  float ks[K][NF], kc[K][NF];
+  bool own_int[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int64_t gx = bx0 + tx, gy = by0 + ty + TY * k;
+    own_int[k] = interior2(gx, gy, g);
+    const int64_t p = gy * g.sy + gx;
+#pragma unroll
+    for (int m = 0; m < NF; ++m) {
+      ks[k][m] = own_int[k] ? qs[m * g.points + p] : 0.0f;
+      kc[k][m] = own_int[k] ? qc[m * g.points + p] : 0.0f;
+    }
+  }
+  __syncthreads();
+
+  for (int s = 0; s < a.steps; ++s) {
+    const int r = a.steps - 1 - s;
+    const bool first = a.n0 + s == 0;
+    const Coef32 lo = first ? a.first_lo : a.reg_lo;
+    const Coef32 hi = first ? a.first_hi : a.reg_hi;
+    const float* fc = s_fc + s * NF;
+    const float* wq = s_wq + s * NF;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (!own_int[k]) continue;
+      const int ly = T + ty + TY * k, lx = T + tx;
+      const int l = ly * EX + lx;
+      const int64_t gx = bx0 + tx, gy = by0 + ty + TY * k;
+      const int64_t li = g.layer_axis == 0 ? gx : gy;
+      const Coef32& L = li >= g.layer_split ? hi : lo;
+      const float w = Wc[l];
+      const float dxx = (Wc[l - 1] - w) + (Wc[l + 1] - w);
+      const float dyy = (Wc[l - EX] - w) + (Wc[l + EX] - w);
+      const float inc =
+          increment<NF, 2>(L, dxx, dyy, 0.0f, fc, f, gy * g.sy + gx, g.points, a.forced);
+      const float dn = Dv[l] + inc;
+      const float wn = w + dn;
+      Dv[l] = dn;
+      Wn[l] = wn;
+#pragma unroll
+      for (int m = 0; m < NF; ++m) kahan_add(ks[k][m], kc[k][m], wq[m], wn);
+    }
+    if (r > 0) {
+      const int RW = BX + 2 * r;
+      const int ring = 2 * r * RW + 2 * r * BY;
+      for (int e = tid; e < ring; e += NT) {
+        int lx, ly;
+        if (e < 2 * r * RW) {             // rows above and below the tile
+          const int row = e / RW;
+          lx = T - r + (e - row * RW);
+          ly = row < r ? T - r + row : T + BY + (row - r);
+        } else {                          // columns left and right of the tile
+          const int e2 = e - 2 * r * RW;
+          const int row = e2 / (2 * r);
+          const int col = e2 - row * 2 * r;
+          ly = T + row;
+          lx = col < r ? T - r + col : T + BX + (col - r);
+        }
+        const int64_t gx = x0 + lx, gy = y0 + ly;
+        if (!interior2(gx, gy, g)) continue;
+        const int64_t li = g.layer_axis == 0 ? gx : gy;
+        const Coef32& L = li >= g.layer_split ? hi : lo;
+        const int l = ly * EX + lx;
+        const float w = Wc[l];
+        const float dxx = (Wc[l - 1] - w) + (Wc[l + 1] - w);
+        const float dyy = (Wc[l - EX] - w) + (Wc[l + EX] - w);
+        const float inc =
+            increment<NF, 2>(L, dxx, dyy, 0.0f, fc, f, gy * g.sy + gx, g.points, a.forced);
+        const float dn = Dv[l] + inc;
+        Dv[l] = dn;
+        Wn[l] = w + dn;
+      }
+    }
+    __syncthreads();
+    float* t = Wc;
+    Wc = Wn;
+    Wn = t;
+  }
+  // Wc = W^{n0+steps}, Dv = D^{n0+steps-1/2} on the tile
+  if (!a.last) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (!own_int[k]) continue;
+      const int l = (T + ty + TY * k) * EX + (T + tx);
+      const int64_t p = (by0 + ty + TY * k) * g.sy + bx0 + tx;
+      W_out[p] = Wc[l];
+      D_out[p] = Dv[l];
+#pragma unroll
+      for (int m = 0; m < NF; ++m) {
+        qs[m * g.points + p] = ks[k][m];
+        qc[m * g.points + p] = kc[k][m];
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int64_t gx = bx0 + tx, gy = by0 + ty + TY * k;
+      if (gx > g.nx || gy > g.ny) continue;
+      filter_solve_out<NF>(ks[k], kc[k], b.binv, a.subtract, vsub, vout, gy * g.sy + gx,
+                           g.points, own_int[k]);
+    }
+  }
+}
+
+// ---- init and conversion ---------------------------------------------------------
+
+template <int NF, int DIM>
+__global__ void __launch_bounds__(kBX * kBY)
+k_init32(const double* __restrict__ v, float* __restrict__ W0, float* __restrict__ qs,
+         float* __restrict__ qc, const Init32Args<NF> a, const Geom g) {
+  int64_t i, j, k, p;
+  bool interior;
+  if (!index_of<DIM>(g, i, j, k, p, interior)) return;
+  double w = 0.0;
+  if (interior && v != nullptr) {
+#pragma unroll
+    for (int m = 0; m < NF; ++m) w += v[m * g.points + p];
+  }
+  const float wf = (float)w;
+  W0[p] = wf;
+#pragma unroll
+  for (int m = 0; m < NF; ++m) {
+    qs[m * g.points + p] = a.w0[m] * wf;
+    qc[m * g.points + p] = 0.0f;
+  }
+}
+
+// ---- host launchers --------------------------------------------------------------
+
+template <int NF>
+Step32Args<NF> step_args(const Step32Host& h) {
+  Step32Args<NF> a;
+  a.lo = h.lo;
+  a.hi = h.hi;
+  for (int m = 0; m < NF; ++m) {
+    a.fc[m] = h.fc[m];
+    a.wq[m] = h.wq[m];
+  }
+  a.forced = h.forced;
+  return a;
+}
+
+template <int NF>
+Last32Binv<NF> binv_args(const double* binv) {
+  Last32Binv<NF> b;
+  for (int m = 0; m < NF; ++m)
+    for (int j = 0; j < NF; ++j) b.binv[m * NF + j] = binv[m * MFWH_MAX_NF + j];
+  return b;
+}
+
+dim3 grid_of(const Geom& g) {
+  return dim3((unsigned)((g.nx + kBX) / kBX), (unsigned)((g.ny + kBY) / kBY),
+              (unsigned)(g.dim == 3 ? g.nz + 1 : 1));
+}
+
+template <int NF>
+void step32_nf(const Geom& g, const float* W, const float* D_in, float* W_out, float* D_out,
+               const float* f, float* qs, float* qc, const Step32Host& h, cudaStream_t st) {
+  const Step32Args<NF> a = step_args<NF>(h);
+  if (g.dim == 3)
+    k_step32<NF, 3><<<grid_of(g), dim3(kBX, kBY), 0, st>>>(W, D_in, W_out, D_out, f, qs, qc, a, g);
+  else
+    k_step32<NF, 2><<<grid_of(g), dim3(kBX, kBY), 0, st>>>(W, D_in, W_out, D_out, f, qs, qc, a, g);
+}
+
+template <int NF>
+void last32_nf(const Geom& g, const float* W, const float* D, const float* f, const float* qs,
+               const float* qc, double* vout, const double* vsub, const Step32Host& h,
+               const double* binv, cudaStream_t st) {
+  const Step32Args<NF> a = step_args<NF>(h);
+  const Last32Binv<NF> b = binv_args<NF>(binv);
+  const int sub = vsub != nullptr;
+  if (g.dim == 3)
+    k_last32<NF, 3><<<grid_of(g), dim3(kBX, kBY), 0, st>>>(W, D, f, qs, qc, vout, vsub, a, b, sub, g);
+  else
+    k_last32<NF, 2><<<grid_of(g), dim3(kBX, kBY), 0, st>>>(W, D, f, qs, qc, vout, vsub, a, b, sub, g);
+}
+
+template <int NF>
+void init32_nf(const Geom& g, const double* v, float* W0, float* qs, float* qc, const float* w0,
+               cudaStream_t st) {
+  Init32Args<NF> a;
+  for (int m = 0; m < NF; ++m) a.w0[m] = w0[m];
+  if (g.dim == 3)
+    k_init32<NF, 3><<<grid_of(g), dim3(kBX, kBY), 0, st>>>(v, W0, qs, qc, a, g);
+  else
+    k_init32<NF, 2><<<grid_of(g), dim3(kBX, kBY), 0, st>>>(v, W0, qs, qc, a, g);
+}
+
+template <int NF, int T, int TY, int K, int MB>
+void tb32_launch(const Geom& g, const float* W_in, const float* D_in, float* W_out, float* D_out,
+                 const float* f, float* qs, float* qc, double* vout, const double* vsub,
+                 const TB32Host& h, cudaStream_t st) {
+  constexpr int BY = TY * K;
+  constexpr int EX = 32 + 2 * T, EY = BY + 2 * T;
+  constexpr size_t smem = sizeof(float) * (3 * EX * EY + 2 * T * NF);
+  static bool configured[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !configured[dev]) {
+    cudaFuncSetAttribute(k_tb2d32<NF, T, TY, K, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    if (dev >= 0 && dev < 64) configured[dev] = true;
+  }
+  TB32Args<NF> a;
+  a.reg_lo = h.reg_lo;
+  a.reg_hi = h.reg_hi;
+  a.first_lo = h.first_lo;
+  a.first_hi = h.first_hi;
+  a.wq = h.wq;
+  a.fc = h.fc;
+  a.n0 = h.n0;
+  a.steps = h.steps;
+  a.forced = h.forced;
+  a.last = h.last;
+  a.subtract = vsub != nullptr;
+  const Last32Binv<NF> b = binv_args<NF>(h.binv);
+  dim3 grid((unsigned)((g.nx + 32) / 32), (unsigned)((g.ny + BY) / BY));
+  k_tb2d32<NF, T, TY, K, MB><<<grid, dim3(32, TY), smem, st>>>(W_in, D_in, W_out, D_out, f, qs,
+                                                               qc, vout, vsub, a, b, g);
+}
+
+template <int NF, int T>
+void tb32_shape(const Geom& g, const float* W_in, const float* D_in, float* W_out, float* D_out,
+                const float* f, float* qs, float* qc, double* vout, const double* vsub,
+                const TB32Host& h, cudaStream_t st) {
+  // Tile shapes (points per thread K halves above 8 frequencies to bound registers):
+  //  0: 512 threads, tile 32 x 32 (32 x 16 above 8 frequencies), two CTAs per SM;
+  //  1: 1024 threads, tile 32 x 32, one point per thread;
+  //  2: 512 threads, tile 32 x 64 (32 x 32), one CTA per SM.
+  constexpr int KS = NF <= 8 ? 2 : 1;
+  switch (h.shape) {
+    case 1:
+      tb32_launch<NF, T, 32, 1, 1>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, h, st);
+      break;
+    case 2:
+      tb32_launch<NF, T, 16, 2 * KS, 1>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, h, st);
+      break;
+    default:
+      tb32_launch<NF, T, 16, KS, 2>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, h, st);
+      break;
+  }
+}
+
+template <int NF>
+void tb32_nf(const Geom& g, const float* W_in, const float* D_in, float* W_out, float* D_out,
+             const float* f, float* qs, float* qc, double* vout, const double* vsub,
+             const TB32Host& h, cudaStream_t st) {
+  if (h.depth <= 4)
+    tb32_shape<NF, 4>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, h, st);
+  else if (h.depth <= 8)
+    tb32_shape<NF, 8>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, h, st);
+  else
+    tb32_shape<NF, 16>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, h, st);
+}
+
+template <int NF>
+W32Ops make_w32_ops() {
+  return W32Ops{init32_nf<NF>, step32_nf<NF>, last32_nf<NF>, tb32_nf<NF>};
+}
+
+}  // namespace
+
+// Defined in wave32_p1.cu .. wave32_p4.cu for nf in 1-4, 5-8, 9-12, 13-16.
+W32Ops w32_ops_p1(int nf);
+W32Ops w32_ops_p2(int nf);
+W32Ops w32_ops_p3(int nf);
+W32Ops w32_ops_p4(int nf);
+
+}  // namespace mfwh
