@@ -52,9 +52,12 @@ typedef enum {
 
 enum { MFWH_FILTER_OPTIMIZED = 0, MFWH_FILTER_TRADITIONAL = 1, MFWH_FILTER_USER = 2 };
 /* Arithmetic of the wave solve.  FP64: every step in FP64.  FP32_KAHAN: wave levels and
-   steps in FP32 (increment form of the leapfrog scheme), filter sums with Kahan
-   compensation, the filter solve B^{-1} q, GMRES and the residual in FP64. */
-enum { MFWH_PREC_FP64 = 0, MFWH_PREC_FP32_KAHAN = 1 };
+   steps in FP32 (increment form of the leapfrog scheme), filter sums with a Kahan update at
+   every step; the filter solve B^{-1} q, GMRES and the residual stay FP64.  FP32_BLOCKSUM:
+   as FP32_KAHAN, but a blocked launch of T steps sums its T filter terms in plain FP32 and
+   folds that partial sum into the Kahan pair once (compensated across launches); with one
+   step per launch it is FP32_KAHAN. */
+enum { MFWH_PREC_FP64 = 0, MFWH_PREC_FP32_KAHAN = 1, MFWH_PREC_FP32_BLOCKSUM = 2 };
 enum { MFWH_C_CONST = 0, MFWH_C_TWO_LAYER = 1 };
 
 typedef struct mfwh_handle_s* mfwh_handle_t;
@@ -80,13 +83,14 @@ typedef struct {
   const double* user_params; /* host, [nf][3] (a, c, s) when filter_mode == MFWH_FILTER_USER */
   int n_delta;               /* N_delta of eq. LambdaRange (paper: 20) */
   double c_delta;            /* c_delta of eq. LambdaRange (paper: 2) */
-  int precision;             /* MFWH_PREC_FP64 or MFWH_PREC_FP32_KAHAN */
+  int precision;             /* MFWH_PREC_FP64, MFWH_PREC_FP32_KAHAN or MFWH_PREC_FP32_BLOCKSUM */
   int time_block;            /* leapfrog steps per pass over HBM: 0 = library default (1 for
                                 FP64; 8 for FP32 in 2D), 1 = one step per kernel launch,
                                 4 or 8 (or 16 for FP32) = temporal blocking with that depth
                                 (2D grids only).  Results are bit-identical for every depth. */
-  int tile_shape;            /* FP32 blocked kernel: 0 = 32x32 tile, 512 threads (default);
-                                1 = 32x32, 256 threads; 2 = 32x64, 512 threads */
+  int tile_shape;            /* FP32 blocked kernel tile: 0 = 32x32, 512 threads (default);
+                                1 = 32x64, 512 threads; 2 = 64x64, 1024 threads (halved in
+                                y above 8 frequencies) */
 } mfwh_problem;
 
 /* Everything the set-up derives from a problem (Algorithm 1, first two lines;

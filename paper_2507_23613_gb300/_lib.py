@@ -26,6 +26,7 @@ FILTER_TRADITIONAL = 1
 FILTER_USER = 2
 PREC_FP64 = 0
 PREC_FP32_KAHAN = 1
+PREC_FP32_BLOCKSUM = 2
 C_CONST = 0
 C_TWO_LAYER = 1
 

@@ -92,7 +92,7 @@ struct mfwh_handle_s {
   int64_t step_launches = 0;
   int64_t total_launches = 0;
   StepHost sh;                      // per-step kernel arguments (reused)
-  // FP32 path (precision MFWH_PREC_FP32_KAHAN)
+  // FP32 paths (precision MFWH_PREC_FP32_KAHAN or MFWH_PREC_FP32_BLOCKSUM)
   float* f32 = nullptr;             // forcing rounded to FP32 [nf][P]
   float* W32[4] = {};               // (W, D) pairs: W32[0], W32[1] and W32[2], W32[3]
   float* qs = nullptr;              // Kahan sums [nf][P]
@@ -170,6 +170,7 @@ mfwh_status apply_pi32(mfwh_handle_t h, const double* vin, double* vout, int for
     a.binv = h->sh.binv;
     a.depth = P.time_block;
     a.shape = P.tile_shape;
+    a.acc = P.precision == MFWH_PREC_FP32_BLOCKSUM ? 1 : 0;
     a.forced = forced;
     int cur = 0;                 // pair holding the input: (W32[2 cur], W32[2 cur + 1])
     for (int n0 = 0; n0 < n_t;) {
@@ -222,7 +223,7 @@ mfwh_status apply_pi_tb(mfwh_handle_t h, const double* vin, double* vout, int fo
 
 mfwh_status apply_pi(mfwh_handle_t h, const double* vin, double* vout, int forced,
                      const double* vsub) {
-  if (h->plan.precision == MFWH_PREC_FP32_KAHAN) return apply_pi32(h, vin, vout, forced, vsub);
+  if (h->plan.precision != MFWH_PREC_FP64) return apply_pi32(h, vin, vout, forced, vsub);
   if (h->plan.time_block > 1) return apply_pi_tb(h, vin, vout, forced, vsub);
   const Plan& P = h->plan;
   const int nf = h->nf;
@@ -490,7 +491,7 @@ mfwh_status mfwh_create(const mfwh_problem* prob, void* stream, mfwh_handle_t* o
     e = cudaMalloc(b.p, sizeof(double) * b.n);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc (workspace)"));
   }
-  if (P.precision == MFWH_PREC_FP32_KAHAN) {
+  if (P.precision != MFWH_PREC_FP64) {
     const int nf = h->nf;
     const int n_t = P.s.n_t;
     const double dt = P.s.dt;

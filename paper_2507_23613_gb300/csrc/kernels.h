@@ -76,6 +76,7 @@ struct TB32Host {
   const float* fc;         // device [N_t * nf]
   const double* binv;      // host [MFWH_MAX_NF * MFWH_MAX_NF], row-major, leading dim 16
   int n0, steps, depth, shape, forced, last;
+  int acc;                 // 0: Kahan update every step; 1: per-launch partial sums folded
 };
 // W^0 = fl32(sum_m v_m) (0 on the boundary), qs_m = w0_m W^0, qc_m = 0.
 void launch_init32(int nf, const Geom& g, const double* v, float* W0, float* qs, float* qc,

@@ -302,9 +302,10 @@ mfwh_status plan_problem(const mfwh_problem* p, Plan* out) {
     return fail(MFWH_ERR_INVALID_ARG, "user_params is NULL");
   if (p->filter_mode == MFWH_FILTER_OPTIMIZED && (p->n_delta < 1 || !(p->c_delta >= 0.0)))
     return fail(MFWH_ERR_INVALID_ARG, "n_delta must be >= 1 and c_delta >= 0");
-  if (p->precision != MFWH_PREC_FP64 && p->precision != MFWH_PREC_FP32_KAHAN)
+  if (p->precision != MFWH_PREC_FP64 && p->precision != MFWH_PREC_FP32_KAHAN &&
+      p->precision != MFWH_PREC_FP32_BLOCKSUM)
     return fail(MFWH_ERR_INVALID_ARG, "unsupported precision");
-  const bool fp32 = p->precision == MFWH_PREC_FP32_KAHAN;
+  const bool fp32 = p->precision != MFWH_PREC_FP64;
   if (p->time_block != 0 && p->time_block != 1 && p->time_block != 4 && p->time_block != 8 &&
       !(fp32 && p->time_block == 16))
     return fail(MFWH_ERR_INVALID_ARG, "time_block must be 0, 1, 4 or 8 (or 16 for FP32)");

@@ -200,56 +200,168 @@ struct TB32Args {
   int n0, steps, forced, last, subtract;
 };
 
-template <int NF, int T, int TY, int K, int MB>
-__global__ void __launch_bounds__(32 * TY, MB)
+// A global offset clamped into [lo, hi] as a 32-bit local coordinate.
+__device__ __forceinline__ int clamp_local(int64_t v, int lo, int hi) {
+  return v < lo ? lo : (v > hi ? hi : (int)v);
+}
+
+// One leapfrog update at local point l of the extended tile (increment form).
+template <int NF, int EX>
+__device__ __forceinline__ float tb_update(const float* Wc, float* Wn, float* Dv, int l,
+                                           const Coef32& L, const float* fc,
+                                           const float* __restrict__ f, int64_t p,
+                                           int64_t points, int forced) {
+  const float w = Wc[l];
+  const float dxx = (Wc[l - 1] - w) + (Wc[l + 1] - w);
+  const float dyy = (Wc[l - EX] - w) + (Wc[l + EX] - w);
+  const float inc = increment<NF, 2>(L, dxx, dyy, 0.0f, fc, f, p, points, forced);
+  const float dn = Dv[l] + inc;
+  const float wn = w + dn;
+  Dv[l] = dn;
+  Wn[l] = wn;
+  return wn;
+}
+
+// Fold a partial sum x into the Kahan pair (s, c).
+__device__ __forceinline__ void kahan_fold(float& s, float& c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// The halo ring of radius r around a BX x BY tile at one step, enumerated evenly over all
+// threads: first the 2r rows of BX + 2r points above and below the tile, then the BY rows of
+// 2r points to its left and right.  Quotients by the row lengths come from a float
+// reciprocal: (e + 1/2) / len is at least 1/(2 len) from an integer, far above the rounding.
+// SIMPLE: every ring point is interior and has the same c^2 (no bounds or layer tests).
+template <int NF, int T, int BX, int BY, bool SIMPLE>
+__device__ __forceinline__ void ring_pass(const float* Wc, float* Wn, float* Dv, int r, int tid,
+                                          int nthreads, int ilx, int ihx, int ily, int ihy,
+                                          bool lay_x, int lay_thr, const Coef32& lo,
+                                          const Coef32& hi, const float* fc,
+                                          const float* __restrict__ f, int64_t y0, int64_t x0,
+                                          const Geom& g, int forced) {
+  constexpr int EX = BX + 2 * T;
+  const int RW = BX + 2 * r;
+  const int top = 2 * r * RW;
+  const int ring = top + 2 * r * BY;
+  const float inv_rw = 1.0f / (float)RW, inv_2r = 1.0f / (float)(2 * r);
+  for (int e = tid; e < ring; e += nthreads) {
+    int lx, ly;
+    if (e < top) {
+      const int row = (int)(((float)e + 0.5f) * inv_rw);
+      lx = T - r + (e - row * RW);
+      ly = row < r ? T - r + row : T + BY + row - r;
+    } else {
+      const int e2 = e - top;
+      const int row = (int)(((float)e2 + 0.5f) * inv_2r);
+      const int col = e2 - row * 2 * r;
+      ly = T + row;
+      lx = col < r ? T - r + col : T + BX + col - r;
+    }
+    if (!SIMPLE && (lx < ilx || lx > ihx || ly < ily || ly > ihy)) continue;
+    const Coef32& L = SIMPLE ? lo : (((lay_x ? lx : ly) >= lay_thr) ? hi : lo);
+    tb_update<NF, EX>(Wc, Wn, Dv, ly * EX + lx, L, fc, f, (y0 + ly) * g.sy + x0 + lx, g.points,
+                      forced);
+  }
+}
+
+// ACC = 0: Kahan update of (s_m, c_m) at every step.
+// ACC = 1: plain FP32 partial sums over the steps of one launch, folded into the Kahan
+//          pair once per launch (compensated across launches; the partial of at most T
+//          terms carries a rounding error far below that of the FP32 wave levels).
+//
+// The CTA has BX x TY threads (BX = 32 or 64) and a BX x (TY K) tile.  Thread (tx, ty) owns
+// the K consecutive tile rows ty K .. ty K + K - 1 of column tx.  The wave values W and
+// increments D of its own points stay in registers for all T steps; only the left and right
+// neighbours and the rows just above and below the strip come from shared memory.  The halo
+// ring is updated from shared memory by all threads.
+template <int NF, int T, int BX, int TY, int K, int MB, int ACC>
+__global__ void __launch_bounds__(BX * TY, MB)
 k_tb2d32(const float* __restrict__ W_in, const float* __restrict__ D_in,
          float* __restrict__ W_out, float* __restrict__ D_out, const float* __restrict__ f,
          float* __restrict__ qs, float* __restrict__ qc, double* vout, const double* vsub,
          const TB32Args<NF> a, const Last32Binv<NF> b, const Geom g) {
-  constexpr int BX = 32, BY = TY * K;
+  constexpr int BY = TY * K, NT = BX * TY;
   constexpr int EX = BX + 2 * T, EY = BY + 2 * T, E = EX * EY;
-  constexpr int NT = 32 * TY;
   extern __shared__ float sm32[];
   float* Wc = sm32;             // W^n on the extended tile
   float* Wn = sm32 + E;         // W^{n+1}
-  float* Dv = sm32 + 2 * E;     // D, updated in place
+  float* Dv = sm32 + 2 * E;     // D on the halo (the tile's own D lives in registers)
   float* s_wq = sm32 + 3 * E;   // [T][NF]
   float* s_fc = s_wq + T * NF;  // [T][NF]
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int tid = ty * 32 + tx;
-  const int64_t bx0 = (int64_t)blockIdx.x * BX, by0 = (int64_t)blockIdx.y * BY;
-  const int64_t x0 = bx0 - T, y0 = by0 - T;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+  const int64_t x0 = (int64_t)blockIdx.x * BX - T, y0 = (int64_t)blockIdx.y * BY - T;
+  // Local-coordinate bounds (32-bit): grid points gl*, interior points il*.
+  const int glx = clamp_local(-x0, 0, EX), ghx = clamp_local(g.nx - x0, -1, EX - 1);
+  const int gly = clamp_local(-y0, 0, EY), ghy = clamp_local(g.ny - y0, -1, EY - 1);
+  const int ilx = clamp_local(1 - x0, 0, EX), ihx = clamp_local(g.nx - 1 - x0, -1, EX - 1);
+  const int ily = clamp_local(1 - y0, 0, EY), ihy = clamp_local(g.ny - 1 - y0, -1, EY - 1);
+  // c^2 layer: points whose local coordinate along the layer axis is >= lay_thr use hi.
+  const bool lay_x = g.layer_axis == 0;
+  const int lay_thr = clamp_local(g.layer_split - (lay_x ? x0 : y0), -1, EX + EY);
+  // Every point of the largest ring interior, all with one c^2: the ring needs no tests.
+  const bool simple = ilx <= 1 && ihx >= EX - 2 && ily <= 1 && ihy >= EY - 2 &&
+                      (lay_thr <= 0 || lay_thr >= (lay_x ? EX : EY));
+  const bool all_hi = lay_thr <= 0;
 
-  for (int e = tid; e < E; e += NT) {
-    const int lx = e % EX, ly = e / EX;
-    const int64_t gx = x0 + lx, gy = y0 + ly;
-    const bool in = gx >= 0 && gx <= g.nx && gy >= 0 && gy <= g.ny;
-    const int64_t p = gy * g.sy + gx;
-    const float w = in ? W_in[p] : 0.0f;
-    Wc[e] = w;
-    Wn[e] = w;
-    Dv[e] = (in && D_in != nullptr) ? D_in[p] : 0.0f;
+  for (int ly = ty; ly < EY; ly += TY) {
+    const bool row = ly >= gly && ly <= ghy;
+    const int64_t rbase = (y0 + ly) * g.sy + x0;
+    for (int lx = tx; lx < EX; lx += BX) {
+      const bool in = row && lx >= glx && lx <= ghx;
+      const int l = ly * EX + lx;
+      const float w = in ? W_in[rbase + lx] : 0.0f;
+      Wc[l] = w;
+      Wn[l] = w;
+      Dv[l] = (in && D_in != nullptr) ? D_in[rbase + lx] : 0.0f;
+    }
   }
   for (int e = tid; e < a.steps * NF; e += NT) {
-    const int st = e / NF, m = e % NF;
+    const int st = e / NF, m = e - st * NF;
     const int n = a.n0 + st;
     s_wq[e] = a.wq[(n + 1) * NF + m];
     s_fc[e] = a.forced ? a.fc[n * NF + m] : 0.0f;
   }
-  float ks[K][NF], kc[K][NF];
-  bool own_int[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const int64_t gx = bx0 + tx, gy = by0 + ty + TY * k;
-    own_int[k] = interior2(gx, gy, g);
-    const int64_t p = gy * g.sy + gx;
-#pragma unroll
-    for (int m = 0; m < NF; ++m) {
-      ks[k][m] = own_int[k] ? qs[m * g.points + p] : 0.0f;
-      kc[k][m] = own_int[k] ? qc[m * g.points + p] : 0.0f;
+  // The strip: local column lxo, rows lyo .. lyo + K - 1.
+  const int lxo = T + tx, lyo = T + ty * K;
+  const int64_t p0 = (y0 + lyo) * g.sy + x0 + lxo;
+  if (ACC == 1) {
+    // Ask L2 for the Kahan pairs folded at the end of the launch.  A warp's 32 columns of
+    // one row span at most two 128-byte lines; each lane prefetches some of the warp's
+    // (row, frequency, array) lines.
+    const int lane = tid & 31;
+    const int64_t wbase = p0 - (tx & 31);
+    for (int c = lane; c < 4 * K * NF; c += 32) {
+      const int half = c & 1, k = (c >> 1) % K, m = ((c >> 1) / K) % NF, arr = c / (2 * K * NF);
+      const int64_t pl = wbase + k * g.sy + half * 31;
+      if (lxo - (tx & 31) + half * 31 <= ihx && lyo + k <= ihy) {
+        const float* ptr = (arr ? qc : qs) + m * g.points + pl;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+      }
     }
   }
+  const bool col_int = lxo >= ilx && lxo <= ihx;
+  bool own_int[K], own_up[K];
+  float wr[K], dr[K], ks[K][NF], kc[K][NF], part[K][NF];
   __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int ly = lyo + k;
+    own_int[k] = col_int && ly >= ily && ly <= ihy;
+    own_up[k] = (lay_x ? lxo : ly) >= lay_thr;
+    wr[k] = Wc[ly * EX + lxo];
+    dr[k] = Dv[ly * EX + lxo];
+#pragma unroll
+    for (int m = 0; m < NF; ++m) {
+      part[k][m] = 0.0f;
+      if (ACC == 0) {
+        ks[k][m] = own_int[k] ? qs[m * g.points + p0 + k * g.sy] : 0.0f;
+        kc[k][m] = own_int[k] ? qc[m * g.points + p0 + k * g.sy] : 0.0f;
+      }
+    }
+  }
 
   for (int s = 0; s < a.steps; ++s) {
     const int r = a.steps - 1 - s;
@@ -257,85 +369,87 @@ k_tb2d32(const float* __restrict__ W_in, const float* __restrict__ D_in,
     const Coef32 lo = first ? a.first_lo : a.reg_lo;
     const Coef32 hi = first ? a.first_hi : a.reg_hi;
     const float* fc = s_fc + s * NF;
-    const float* wq = s_wq + s * NF;
+    float wq[NF];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      if (!own_int[k]) continue;
-      const int ly = T + ty + TY * k, lx = T + tx;
-      const int l = ly * EX + lx;
-      const int64_t gx = bx0 + tx, gy = by0 + ty + TY * k;
-      const int64_t li = g.layer_axis == 0 ? gx : gy;
-      const Coef32& L = li >= g.layer_split ? hi : lo;
-      const float w = Wc[l];
-      const float dxx = (Wc[l - 1] - w) + (Wc[l + 1] - w);
-      const float dyy = (Wc[l - EX] - w) + (Wc[l + EX] - w);
-      const float inc =
-          increment<NF, 2>(L, dxx, dyy, 0.0f, fc, f, gy * g.sy + gx, g.points, a.forced);
-      const float dn = Dv[l] + inc;
-      const float wn = w + dn;
-      Dv[l] = dn;
-      Wn[l] = wn;
+    for (int m = 0; m < NF; ++m) wq[m] = s_wq[s * NF + m];
+    // the strip: centre values from registers, neighbours from shared memory
+    {
+      const float above = Wc[(lyo - 1) * EX + lxo];
+      const float below = Wc[(lyo + K) * EX + lxo];
+      float wnew[K];
 #pragma unroll
-      for (int m = 0; m < NF; ++m) kahan_add(ks[k][m], kc[k][m], wq[m], wn);
+      for (int k = 0; k < K; ++k) {
+        const float w = wr[k];
+        wnew[k] = w;
+        if (!own_int[k]) continue;     // boundary and outside points keep W = 0
+        const int l = (lyo + k) * EX + lxo;
+        const float up = k == 0 ? above : wr[k - 1];
+        const float dn = k == K - 1 ? below : wr[k + 1];
+        const float dxx = (Wc[l - 1] - w) + (Wc[l + 1] - w);
+        const float dyy = (up - w) + (dn - w);
+        const Coef32 L = own_up[k] ? hi : lo;
+        const float inc = increment<NF, 2>(L, dxx, dyy, 0.0f, fc, f, p0 + k * g.sy, g.points,
+                                           a.forced);
+        dr[k] = dr[k] + inc;
+        wnew[k] = w + dr[k];
+      }
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        wr[k] = wnew[k];
+        Wn[(lyo + k) * EX + lxo] = wnew[k];
+        if (own_int[k]) {
+#pragma unroll
+          for (int m = 0; m < NF; ++m) {
+            if (ACC == 0)
+              kahan_add(ks[k][m], kc[k][m], wq[m], wnew[k]);
+            else
+              part[k][m] = fmaf(wq[m], wnew[k], part[k][m]);
+          }
+        }
+      }
     }
     if (r > 0) {
-      const int RW = BX + 2 * r;
-      const int ring = 2 * r * RW + 2 * r * BY;
-      for (int e = tid; e < ring; e += NT) {
-        int lx, ly;
-        if (e < 2 * r * RW) {             // rows above and below the tile
-          const int row = e / RW;
-          lx = T - r + (e - row * RW);
-          ly = row < r ? T - r + row : T + BY + (row - r);
-        } else {                          // columns left and right of the tile
-          const int e2 = e - 2 * r * RW;
-          const int row = e2 / (2 * r);
-          const int col = e2 - row * 2 * r;
-          ly = T + row;
-          lx = col < r ? T - r + col : T + BX + (col - r);
-        }
-        const int64_t gx = x0 + lx, gy = y0 + ly;
-        if (!interior2(gx, gy, g)) continue;
-        const int64_t li = g.layer_axis == 0 ? gx : gy;
-        const Coef32& L = li >= g.layer_split ? hi : lo;
-        const int l = ly * EX + lx;
-        const float w = Wc[l];
-        const float dxx = (Wc[l - 1] - w) + (Wc[l + 1] - w);
-        const float dyy = (Wc[l - EX] - w) + (Wc[l + EX] - w);
-        const float inc =
-            increment<NF, 2>(L, dxx, dyy, 0.0f, fc, f, gy * g.sy + gx, g.points, a.forced);
-        const float dn = Dv[l] + inc;
-        Dv[l] = dn;
-        Wn[l] = w + dn;
-      }
+      if (simple)
+        ring_pass<NF, T, BX, BY, true>(Wc, Wn, Dv, r, tid, NT, ilx, ihx, ily, ihy, lay_x, lay_thr,
+                                       all_hi ? hi : lo, hi, fc, f, y0, x0, g, a.forced);
+      else
+        ring_pass<NF, T, BX, BY, false>(Wc, Wn, Dv, r, tid, NT, ilx, ihx, ily, ihy, lay_x,
+                                        lay_thr, lo, hi, fc, f, y0, x0, g, a.forced);
     }
     __syncthreads();
     float* t = Wc;
     Wc = Wn;
     Wn = t;
   }
-  // Wc = W^{n0+steps}, Dv = D^{n0+steps-1/2} on the tile
-  if (!a.last) {
+  // wr = W^{n0+steps}, dr = D^{n0+steps-1/2} on the strip
+  const bool col_in = lxo <= ghx;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
+  for (int k = 0; k < K; ++k) {
+    const int64_t p = p0 + k * g.sy;
+    if (ACC == 1 && own_int[k]) {
+#pragma unroll
+      for (int m = 0; m < NF; ++m) {
+        ks[k][m] = qs[m * g.points + p];
+        kc[k][m] = qc[m * g.points + p];
+        kahan_fold(ks[k][m], kc[k][m], part[k][m]);
+      }
+    }
+    if (!a.last) {
       if (!own_int[k]) continue;
-      const int l = (T + ty + TY * k) * EX + (T + tx);
-      const int64_t p = (by0 + ty + TY * k) * g.sy + bx0 + tx;
-      W_out[p] = Wc[l];
-      D_out[p] = Dv[l];
+      W_out[p] = wr[k];
+      D_out[p] = dr[k];
 #pragma unroll
       for (int m = 0; m < NF; ++m) {
         qs[m * g.points + p] = ks[k][m];
         qc[m * g.points + p] = kc[k][m];
       }
-    }
-  } else {
+    } else {
+      if (!col_in || lyo + k > ghy) continue;
+      if (!own_int[k]) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const int64_t gx = bx0 + tx, gy = by0 + ty + TY * k;
-      if (gx > g.nx || gy > g.ny) continue;
-      filter_solve_out<NF>(ks[k], kc[k], b.binv, a.subtract, vsub, vout, gy * g.sy + gx,
-                           g.points, own_int[k]);
+        for (int m = 0; m < NF; ++m) ks[k][m] = kc[k][m] = 0.0f;
+      }
+      filter_solve_out<NF>(ks[k], kc[k], b.binv, a.subtract, vsub, vout, p, g.points, own_int[k]);
     }
   }
 }
@@ -425,18 +539,19 @@ void init32_nf(const Geom& g, const double* v, float* W0, float* qs, float* qc, 
     k_init32<NF, 2><<<grid_of(g), dim3(kBX, kBY), 0, st>>>(v, W0, qs, qc, a, g);
 }
 
-template <int NF, int T, int TY, int K, int MB>
+template <int NF, int T, int BX, int TY, int K, int MB, int ACC>
 void tb32_launch(const Geom& g, const float* W_in, const float* D_in, float* W_out, float* D_out,
                  const float* f, float* qs, float* qc, double* vout, const double* vsub,
                  const TB32Host& h, cudaStream_t st) {
   constexpr int BY = TY * K;
-  constexpr int EX = 32 + 2 * T, EY = BY + 2 * T;
+  constexpr int EX = BX + 2 * T, EY = BY + 2 * T;
   constexpr size_t smem = sizeof(float) * (3 * EX * EY + 2 * T * NF);
   static bool configured[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64 || !configured[dev]) {
-    cudaFuncSetAttribute(k_tb2d32<NF, T, TY, K, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_tb2d32<NF, T, BX, TY, K, MB, ACC>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     if (dev >= 0 && dev < 64) configured[dev] = true;
   }
@@ -453,31 +568,46 @@ void tb32_launch(const Geom& g, const float* W_in, const float* D_in, float* W_o
   a.last = h.last;
   a.subtract = vsub != nullptr;
   const Last32Binv<NF> b = binv_args<NF>(h.binv);
-  dim3 grid((unsigned)((g.nx + 32) / 32), (unsigned)((g.ny + BY) / BY));
-  k_tb2d32<NF, T, TY, K, MB><<<grid, dim3(32, TY), smem, st>>>(W_in, D_in, W_out, D_out, f, qs,
-                                                               qc, vout, vsub, a, b, g);
+  dim3 grid((unsigned)((g.nx + BX) / BX), (unsigned)((g.ny + BY) / BY));
+  k_tb2d32<NF, T, BX, TY, K, MB, ACC><<<grid, dim3(BX, TY), smem, st>>>(
+      W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, a, b, g);
 }
 
-template <int NF, int T>
+template <int NF, int T, int ACC>
 void tb32_shape(const Geom& g, const float* W_in, const float* D_in, float* W_out, float* D_out,
                 const float* f, float* qs, float* qc, double* vout, const double* vsub,
                 const TB32Host& h, cudaStream_t st) {
-  // Tile shapes (points per thread K halves above 8 frequencies to bound registers):
-  //  0: 512 threads, tile 32 x 32 (32 x 16 above 8 frequencies), two CTAs per SM;
-  //  1: 1024 threads, tile 32 x 32, one point per thread;
-  //  2: 512 threads, tile 32 x 64 (32 x 32), one CTA per SM.
+  // Tile shapes, K consecutive rows per thread (K halves above 8 frequencies to bound
+  // registers):
+  //  0: 512 threads, tile 32 x 32 (K = 2; 32 x 16), two CTAs per SM (one with ACC = 0);
+  //  1: 512 threads, tile 32 x 64 (K = 4; 32 x 32), one CTA per SM;
+  //  2: 1024 threads, tile 64 x 64 (K = 4; 64 x 32), one CTA per SM.
   constexpr int KS = NF <= 8 ? 2 : 1;
+  constexpr int M2 = ACC == 0 ? 1 : 2;
   switch (h.shape) {
     case 1:
-      tb32_launch<NF, T, 32, 1, 1>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, h, st);
+      tb32_launch<NF, T, 32, 16, 2 * KS, 1, ACC>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout,
+                                                 vsub, h, st);
       break;
     case 2:
-      tb32_launch<NF, T, 16, 2 * KS, 1>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, h, st);
+      tb32_launch<NF, T, 64, 16, 2 * KS, 1, ACC>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout,
+                                                 vsub, h, st);
       break;
     default:
-      tb32_launch<NF, T, 16, KS, 2>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, h, st);
+      tb32_launch<NF, T, 32, 16, KS, M2, ACC>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub,
+                                              h, st);
       break;
   }
+}
+
+template <int NF, int T>
+void tb32_acc(const Geom& g, const float* W_in, const float* D_in, float* W_out, float* D_out,
+              const float* f, float* qs, float* qc, double* vout, const double* vsub,
+              const TB32Host& h, cudaStream_t st) {
+  if (h.acc == 1)
+    tb32_shape<NF, T, 1>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, h, st);
+  else
+    tb32_shape<NF, T, 0>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, h, st);
 }
 
 template <int NF>
@@ -485,11 +615,11 @@ void tb32_nf(const Geom& g, const float* W_in, const float* D_in, float* W_out, 
              const float* f, float* qs, float* qc, double* vout, const double* vsub,
              const TB32Host& h, cudaStream_t st) {
   if (h.depth <= 4)
-    tb32_shape<NF, 4>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, h, st);
+    tb32_acc<NF, 4>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, h, st);
   else if (h.depth <= 8)
-    tb32_shape<NF, 8>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, h, st);
+    tb32_acc<NF, 8>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, h, st);
   else
-    tb32_shape<NF, 16>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, h, st);
+    tb32_acc<NF, 16>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, h, st);
 }
 
 template <int NF>

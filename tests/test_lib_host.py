@@ -149,7 +149,7 @@ def test_adjusted_frequency_matches_definition():
     dict(time_block=3),                # temporal-blocking depth not 0, 1, 4 or 8
     dict(n=(8, 8, 8), length=(1.0, 1.0, 1.0), time_block=8),   # 3D is not blocked
     dict(time_block=16),               # depth 16 is FP32-only
-    dict(precision=2),                 # unknown precision
+    dict(precision=3),                 # unknown precision
     dict(tile_shape=3),
 ])
 def test_invalid_problems_are_rejected(bad):

@@ -1,0 +1,48 @@
+"""Host check of the halo-ring index decode of the blocked FP32 kernel.
+
+At step s of a launch of T steps the kernel updates the ring of radius
+r = T - 1 - s around its BX x BY tile, enumerated by a flat index e; row and
+column come from a float32 reciprocal of the row length.  This test replays
+that decode in float32 for every tile shape and depth the library builds and
+checks that the ring is covered exactly once and stays inside the extended
+tile (so every shared-memory access of the kernel is in bounds)."""
+
+import numpy as np
+import pytest
+
+BX = 32
+SHAPES = [16 * 2, 16 * 1, 32 * 1, 16 * 4, 16 * 2]   # BY of tile shapes 0-2 (K = 2 or 1)
+
+
+def decode(e, r, T, BY):
+    RW = BX + 2 * r
+    top = 2 * r * RW
+    inv_rw = np.float32(1.0) / np.float32(RW)
+    inv_2r = np.float32(1.0) / np.float32(2 * r)
+    if e < top:
+        row = int((np.float32(e) + np.float32(0.5)) * inv_rw)
+        lx = T - r + (e - row * RW)
+        ly = T - r + row if row < r else T + BY + row - r
+    else:
+        e2 = e - top
+        row = int((np.float32(e2) + np.float32(0.5)) * inv_2r)
+        col = e2 - row * 2 * r
+        ly = T + row
+        lx = T - r + col if col < r else T + BX + col - r
+    return lx, ly
+
+
+@pytest.mark.parametrize("T", [4, 8, 16])
+@pytest.mark.parametrize("BY", sorted(set(SHAPES)))
+def test_ring_decode_covers_each_point_once(T, BY):
+    EX, EY = BX + 2 * T, BY + 2 * T
+    for r in range(1, T):
+        ring = 2 * r * (BX + 2 * r) + 2 * r * BY
+        seen = set()
+        for e in range(ring):
+            lx, ly = decode(e, r, T, BY)
+            assert 1 <= lx <= EX - 2 and 1 <= ly <= EY - 2
+            seen.add((lx, ly))
+        want = {(x, y) for x in range(T - r, T + BX + r) for y in range(T - r, T + BY + r)
+                if not (T <= x < T + BX and T <= y < T + BY)}
+        assert len(seen) == ring and seen == want
