@@ -122,6 +122,7 @@ typedef struct {
   int history_len;             /* entries written to history (<= history_capacity) */
   int history_capacity;        /* set by the caller: capacity of history */
   double* history;             /* host, caller-owned, may be NULL: residual after each Arnoldi step */
+  int refinements;             /* mfwh_solve_refined: corrections applied (0 for other solvers) */
 } mfwh_solve_info;
 
 /* ---- host-only set-up arithmetic (no GPU needed) ------------------------------ */
@@ -184,6 +185,23 @@ mfwh_status mfwh_solve_fpi(mfwh_handle_t h, int iters, double* v);
  * spurious_tol <= 0 skips the check.  info may be NULL.  Synchronous. */
 mfwh_status mfwh_solve_gmres(mfwh_handle_t h, int restart, double tol, int max_iters,
                              double spurious_tol, double* v, mfwh_solve_info* info);
+
+/* Mixed-precision solve: iterative refinement (GMRES-IR) of the MFWH fixed-point system
+ * (I - S) v = Pi(0) (eq. discreteMFWHmapping, eq. krylovSystem), whose solution is the
+ * discrete Helmholtz solution.  b = Pi(0) and every outer residual r = b - (v - S v) use FP64
+ * wave solves; each correction solves (I - S) e = r by GMRES(restart) from zero to the
+ * Arnoldi tolerance inner_tol with the handle's wave precision (FP32 wave solves for the FP32
+ * precisions, whose products are accurate to about 1e-5 relative) and adds e to v in FP64.
+ * The Helmholtz residual r_h (eq. errorAndResid) of v is computed in FP64 before every
+ * correction; the solve stops with MFWH_OK once max_m r_h^{(m)} <= target, and with
+ * MFWH_ERR_NOT_CONVERGED after max_refinements corrections or max_iters Arnoldi steps in all.
+ * v: host or device [nf][points]; in: initial guess (warm start), out: solution.
+ * info (may be NULL): Arnoldi steps and Pi applications summed over all corrections,
+ * refinements, rel_residual = ||r||_2 / ||b||_2 of the last outer residual, final r_h.
+ * Synchronous. */
+mfwh_status mfwh_solve_refined(mfwh_handle_t h, int restart, double inner_tol, int max_iters,
+                               double target, int max_refinements, double* v,
+                               mfwh_solve_info* info);
 
 /* Helmholtz residual r_h^{(m)} = max_int |f_m - (L_h + omega_m^2) v_m| / max_int |f_m|
  * (eq. errorAndResid, with +omega^2 as in eq. MultipleHelmholtz).

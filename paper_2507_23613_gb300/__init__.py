@@ -189,6 +189,29 @@ class Solver:
         }
         return out
 
+    def solve_refined(self, v, target=1e-6, inner_tol=1e-5, restart=200, max_iters=1000,
+                      max_refinements=8, history=512, raise_on_error=True):
+        """Mixed-precision defect correction to max_m r_h <= target (mfwh_solve_refined)."""
+        info = _lib.SolveInfo()
+        hist = np.zeros(max(history, 1))
+        info.history_capacity = history
+        info.history = _dptr(hist)
+        st = _lib.load().mfwh_solve_refined(self._handle, int(restart), float(inner_tol),
+                                            int(max_iters), float(target), int(max_refinements),
+                                            _as_ptr(v), C.byref(info))
+        if raise_on_error:
+            _lib.check(st)
+        return {
+            "status": st,
+            "iterations": info.iterations,
+            "pi_applications": info.pi_applications,
+            "restarts": info.restarts,
+            "refinements": info.refinements,
+            "rel_residual": info.rel_residual,
+            "helmholtz_residual": np.array(info.helmholtz_residual[:self.nf]),
+            "history": hist[:info.history_len].copy(),
+        }
+
     def residual(self, v):
         r = np.zeros(self.nf)
         _lib.check(_lib.load().mfwh_residual(self._handle, _as_ptr(v), _dptr(r)))

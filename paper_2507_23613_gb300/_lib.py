@@ -87,6 +87,7 @@ class SolveInfo(C.Structure):
         ("history_len", C.c_int),
         ("history_capacity", C.c_int),
         ("history", _dp),
+        ("refinements", C.c_int),
     ]
 
 
@@ -102,6 +103,8 @@ _SIGNATURES = {
     "mfwh_solve_fpi": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "mfwh_solve_gmres": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_double,
                                    C.c_void_p, C.POINTER(SolveInfo)]),
+    "mfwh_solve_refined": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_double,
+                                     C.c_int, C.c_void_p, C.POINTER(SolveInfo)]),
     "mfwh_residual": (C.c_int, [C.c_void_p, C.c_void_p, _dp]),
     "mfwh_residual_noalloc": (C.c_int, [C.POINTER(Problem), C.c_void_p, C.c_void_p, _dp, C.c_void_p]),
     "mfwh_get_setup": (C.c_int, [C.c_void_p, C.POINTER(Setup)]),

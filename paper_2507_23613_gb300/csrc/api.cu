@@ -70,6 +70,9 @@ struct mfwh_handle_s {
   double inv_h2[3] = {0, 0, 0};
   double omega2[MFWH_MAX_NF] = {};
   double* f = nullptr;              // forcing [nf][P]
+  bool use32 = false;               // wave solves in FP32 (the FP32 precisions)
+  double* vec_r = nullptr;          // outer residual of the refined solve [nf][P] (lazy)
+  double* vec_e = nullptr;          // correction of the refined solve [nf][P] (lazy)
   double* Wa = nullptr;             // wave levels (ping-pong)
   double* Wb = nullptr;
   double* Wc2 = nullptr;            // second pair of wave levels (temporal blocking:
@@ -223,8 +226,11 @@ mfwh_status apply_pi_tb(mfwh_handle_t h, const double* vin, double* vout, int fo
 
 mfwh_status apply_pi(mfwh_handle_t h, const double* vin, double* vout, int forced,
                      const double* vsub) {
-  if (h->plan.precision != MFWH_PREC_FP64) return apply_pi32(h, vin, vout, forced, vsub);
-  if (h->plan.time_block > 1) return apply_pi_tb(h, vin, vout, forced, vsub);
+  if (h->use32) return apply_pi32(h, vin, vout, forced, vsub);
+  // The FP64 blocked kernel serves FP64 handles (depth 4 or 8); FP64 wave solves of an FP32
+  // handle (the outer residuals of mfwh_solve_refined) take one step per launch.
+  if (h->plan.time_block > 1 && h->plan.precision == MFWH_PREC_FP64)
+    return apply_pi_tb(h, vin, vout, forced, vsub);
   const Plan& P = h->plan;
   const int nf = h->nf;
   const int n_t = P.s.n_t;
@@ -276,6 +282,7 @@ mfwh_status apply_pi_tb(mfwh_handle_t h, const double* vin, double* vout, int fo
   const int n_t = P.s.n_t;
   const double dt = P.s.dt;
   const int depth = P.time_block;
+  if (depth != 4 && depth != 8) return fail(MFWH_ERR_INVALID_ARG, "FP64 blocking depth must be 4 or 8");
   cudaStream_t st = h->stream;
   launch_init(nf, h->geom, vin, h->Wa, h->q, &P.w[0], st);
   h->total_launches += 1;
@@ -371,6 +378,126 @@ mfwh_status stage_in(mfwh_handle_t h, const double* v, double** dev, bool* on_de
   }
   CK(cudaMemcpyAsync(h->vec_x, v, sizeof(double) * h->N, cudaMemcpyHostToDevice, h->stream));
   *dev = h->vec_x;
+  return MFWH_OK;
+}
+
+// GMRES(restart) on (I - S) x = Pi(0) for a device iterate x, counting into I (which it
+// does not reset).  *converged reports whether the Arnoldi residual fell below tol.
+mfwh_status gmres_core(mfwh_handle_t h, int restart, double tol, int max_iters, double* x,
+                       const double* rhs, mfwh_solve_info& I, bool* converged_out) {
+  const int64_t N = h->N;
+  cudaStream_t s = h->stream;
+  const int it0 = I.iterations;
+  mfwh_status st;
+  const double* b = rhs;
+  if (!b) {
+    // b = Pi(0) (eq. discreteMFWHmapping)
+    st = apply_pi(h, nullptr, h->vec_b, 1, nullptr);
+    if (st != MFWH_OK) return st;
+    I.pi_applications++;
+    b = h->vec_b;
+  }
+  double bb = 0.0, xx = 0.0;
+  st = dots(h, b, 1, b, &bb);
+  if (st != MFWH_OK) return st;
+  st = dots(h, x, 1, x, &xx);
+  if (st != MFWH_OK) return st;
+  const double bnorm = std::sqrt(bb);
+  if (!std::isfinite(bnorm) || !std::isfinite(xx))
+    return fail(MFWH_ERR_NONFINITE, "non-finite right-hand side or initial guess");
+  bool x_nonzero = xx > 0.0;
+  bool converged = false;
+  std::vector<double> H((restart + 1) * restart), cs(restart), sn(restart), g(restart + 1),
+      y(restart), hcol(restart + 1), h2(restart + 1);
+  if (bnorm == 0.0) {
+    launch_axpby(x, 0.0, x, 0.0, N, s);
+    converged = true;
+    I.rel_residual = 0.0;
+  }
+  while (!converged && I.iterations - it0 < max_iters) {
+    double* V0 = h->basis;
+    I.restarts++;
+    if (x_nonzero) {   // r = b - (x - S x)
+      st = apply_pi(h, x, V0, 0, x);
+      if (st != MFWH_OK) return st;
+      I.pi_applications++;
+      launch_axpby(V0, 1.0, b, -1.0, N, s);
+    } else {
+      launch_axpby(V0, 1.0, b, 0.0, N, s);
+    }
+    h->total_launches++;
+    double rr = 0.0;
+    st = dots(h, V0, 1, V0, &rr);
+    if (st != MFWH_OK) return st;
+    const double beta = std::sqrt(rr);
+    if (!std::isfinite(beta)) return fail(MFWH_ERR_NONFINITE, "non-finite Krylov residual");
+    I.rel_residual = beta / bnorm;
+    if (I.rel_residual < tol) {
+      converged = true;
+      break;
+    }
+    launch_axpby(V0, 1.0 / beta, V0, 0.0, N, s);
+    h->total_launches++;
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int j_done = 0;
+    double res = beta;
+    for (int j = 0; j < restart; ++j) {
+      double* Vj = h->basis + (int64_t)j * N;
+      double* w = h->basis + (int64_t)(j + 1) * N;
+      st = apply_pi(h, Vj, w, 0, Vj);   // w = A v_j = v_j - S v_j
+      if (st != MFWH_OK) return st;
+      I.pi_applications++;
+      I.iterations++;
+      // classical Gram-Schmidt, applied twice
+      st = dots(h, h->basis, j + 1, w, hcol.data());
+      if (st != MFWH_OK) return st;
+      launch_multi_axpy(w, h->basis, N, j + 1, hcol.data(), N, s);
+      h->total_launches += multi_axpy_launches(j + 1);
+      st = dots(h, h->basis, j + 1, w, h2.data());
+      if (st != MFWH_OK) return st;
+      launch_multi_axpy(w, h->basis, N, j + 1, h2.data(), N, s);
+      h->total_launches += multi_axpy_launches(j + 1);
+      for (int i = 0; i <= j; ++i) hcol[i] += h2[i];
+      double ww = 0.0;
+      st = dots(h, w, 1, w, &ww);
+      if (st != MFWH_OK) return st;
+      const double hnext = std::sqrt(ww);
+      if (!std::isfinite(hnext)) return fail(MFWH_ERR_NONFINITE, "non-finite Arnoldi vector");
+      // Givens rotations on the new Hessenberg column
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * hcol[i] + sn[i] * hcol[i + 1];
+        hcol[i + 1] = -sn[i] * hcol[i] + cs[i] * hcol[i + 1];
+        hcol[i] = t;
+      }
+      const double r = std::hypot(hcol[j], hnext);
+      cs[j] = r > 0.0 ? hcol[j] / r : 1.0;
+      sn[j] = r > 0.0 ? hnext / r : 0.0;
+      hcol[j] = r;
+      for (int i = 0; i <= j; ++i) H[i * restart + j] = hcol[i];
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      res = std::fabs(g[j + 1]);
+      if (I.history && I.history_len < I.history_capacity) I.history[I.history_len++] = res / bnorm;
+      j_done = j + 1;
+      if (res / bnorm < tol || I.iterations - it0 >= max_iters || hnext == 0.0) break;
+      launch_axpby(w, 1.0 / hnext, w, 0.0, N, s);
+      h->total_launches++;
+    }
+    // y = R^{-1} g, then x += V y
+    for (int i = j_done - 1; i >= 0; --i) {
+      double acc = g[i];
+      for (int k = i + 1; k < j_done; ++k) acc -= H[i * restart + k] * y[k];
+      y[i] = acc / H[i * restart + i];
+    }
+    for (int i = 0; i < j_done; ++i) y[i] = -y[i];   // multi_axpy subtracts
+    launch_multi_axpy(x, h->basis, N, j_done, y.data(), N, s);
+    h->total_launches += multi_axpy_launches(j_done);
+    x_nonzero = true;
+    I.rel_residual = res / bnorm;
+    if (I.rel_residual < tol) converged = true;
+  }
+  *converged_out = converged;
   return MFWH_OK;
 }
 
@@ -554,6 +681,7 @@ mfwh_status mfwh_create(const mfwh_problem* prob, void* stream, mfwh_handle_t* o
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "initialising workspace"));
+  h->use32 = P.precision != MFWH_PREC_FP64;
   std::memset(&h->sh, 0, sizeof(h->sh));
   for (int m = 0; m < h->nf; ++m)
     for (int j = 0; j < h->nf; ++j) h->sh.binv[m * MFWH_MAX_NF + j] = P.s.B_inv[m][j];
@@ -608,7 +736,7 @@ mfwh_status mfwh_solve_gmres(mfwh_handle_t h, int restart, double tol, int max_i
   if (st != MFWH_OK) return st;
   mfwh_solve_info local{};
   mfwh_solve_info& I = info ? *info : local;
-  I.iterations = I.pi_applications = I.restarts = 0;
+  I.iterations = I.pi_applications = I.restarts = I.refinements = 0;
   I.history_len = 0;
   I.rel_residual = NAN;
   const int64_t N = h->N;
@@ -618,110 +746,9 @@ mfwh_status mfwh_solve_gmres(mfwh_handle_t h, int restart, double tol, int max_i
   st = stage_in(h, v, &x, &on_dev);
   if (st != MFWH_OK) return st;
 
-  // b = Pi(0) (eq. discreteMFWHmapping)
-  st = apply_pi(h, nullptr, h->vec_b, 1, nullptr);
-  if (st != MFWH_OK) return st;
-  I.pi_applications++;
-  double bb = 0.0, xx = 0.0;
-  st = dots(h, h->vec_b, 1, h->vec_b, &bb);
-  if (st != MFWH_OK) return st;
-  st = dots(h, x, 1, x, &xx);
-  if (st != MFWH_OK) return st;
-  const double bnorm = std::sqrt(bb);
-  if (!std::isfinite(bnorm) || !std::isfinite(xx))
-    return fail(MFWH_ERR_NONFINITE, "non-finite right-hand side or initial guess");
-  bool x_nonzero = xx > 0.0;
   bool converged = false;
-  std::vector<double> H((restart + 1) * restart), cs(restart), sn(restart), g(restart + 1),
-      y(restart), hcol(restart + 1), h2(restart + 1);
-  if (bnorm == 0.0) {
-    launch_axpby(x, 0.0, x, 0.0, N, s);
-    converged = true;
-    I.rel_residual = 0.0;
-  }
-  while (!converged && I.iterations < max_iters) {
-    double* V0 = h->basis;
-    I.restarts++;
-    if (x_nonzero) {   // r = b - (x - S x)
-      st = apply_pi(h, x, V0, 0, x);
-      if (st != MFWH_OK) return st;
-      I.pi_applications++;
-      launch_axpby(V0, 1.0, h->vec_b, -1.0, N, s);
-    } else {
-      launch_axpby(V0, 1.0, h->vec_b, 0.0, N, s);
-    }
-    h->total_launches++;
-    double rr = 0.0;
-    st = dots(h, V0, 1, V0, &rr);
-    if (st != MFWH_OK) return st;
-    const double beta = std::sqrt(rr);
-    if (!std::isfinite(beta)) return fail(MFWH_ERR_NONFINITE, "non-finite Krylov residual");
-    I.rel_residual = beta / bnorm;
-    if (I.rel_residual < tol) {
-      converged = true;
-      break;
-    }
-    launch_axpby(V0, 1.0 / beta, V0, 0.0, N, s);
-    h->total_launches++;
-    std::fill(g.begin(), g.end(), 0.0);
-    g[0] = beta;
-    int j_done = 0;
-    double res = beta;
-    for (int j = 0; j < restart; ++j) {
-      double* Vj = h->basis + (int64_t)j * N;
-      double* w = h->basis + (int64_t)(j + 1) * N;
-      st = apply_pi(h, Vj, w, 0, Vj);   // w = A v_j = v_j - S v_j
-      if (st != MFWH_OK) return st;
-      I.pi_applications++;
-      I.iterations++;
-      // classical Gram-Schmidt, applied twice
-      st = dots(h, h->basis, j + 1, w, hcol.data());
-      if (st != MFWH_OK) return st;
-      launch_multi_axpy(w, h->basis, N, j + 1, hcol.data(), N, s);
-      h->total_launches += multi_axpy_launches(j + 1);
-      st = dots(h, h->basis, j + 1, w, h2.data());
-      if (st != MFWH_OK) return st;
-      launch_multi_axpy(w, h->basis, N, j + 1, h2.data(), N, s);
-      h->total_launches += multi_axpy_launches(j + 1);
-      for (int i = 0; i <= j; ++i) hcol[i] += h2[i];
-      double ww = 0.0;
-      st = dots(h, w, 1, w, &ww);
-      if (st != MFWH_OK) return st;
-      const double hnext = std::sqrt(ww);
-      if (!std::isfinite(hnext)) return fail(MFWH_ERR_NONFINITE, "non-finite Arnoldi vector");
-      // Givens rotations on the new Hessenberg column
-      for (int i = 0; i < j; ++i) {
-        const double t = cs[i] * hcol[i] + sn[i] * hcol[i + 1];
-        hcol[i + 1] = -sn[i] * hcol[i] + cs[i] * hcol[i + 1];
-        hcol[i] = t;
-      }
-      const double r = std::hypot(hcol[j], hnext);
-      cs[j] = r > 0.0 ? hcol[j] / r : 1.0;
-      sn[j] = r > 0.0 ? hnext / r : 0.0;
-      hcol[j] = r;
-      for (int i = 0; i <= j; ++i) H[i * restart + j] = hcol[i];
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
-      res = std::fabs(g[j + 1]);
-      if (I.history && I.history_len < I.history_capacity) I.history[I.history_len++] = res / bnorm;
-      j_done = j + 1;
-      if (res / bnorm < tol || I.iterations >= max_iters || hnext == 0.0) break;
-      launch_axpby(w, 1.0 / hnext, w, 0.0, N, s);
-      h->total_launches++;
-    }
-    // y = R^{-1} g, then x += V y
-    for (int i = j_done - 1; i >= 0; --i) {
-      double acc = g[i];
-      for (int k = i + 1; k < j_done; ++k) acc -= H[i * restart + k] * y[k];
-      y[i] = acc / H[i * restart + i];
-    }
-    for (int i = 0; i < j_done; ++i) y[i] = -y[i];   // multi_axpy subtracts
-    launch_multi_axpy(x, h->basis, N, j_done, y.data(), N, s);
-    h->total_launches += multi_axpy_launches(j_done);
-    x_nonzero = true;
-    I.rel_residual = res / bnorm;
-    if (I.rel_residual < tol) converged = true;
-  }
+  st = gmres_core(h, restart, tol, max_iters, x, nullptr, I, &converged);
+  if (st != MFWH_OK) return st;
   CK(cudaGetLastError());
   double r[MFWH_MAX_NF];
   st = residual_dev(h, x, r);
@@ -746,6 +773,102 @@ mfwh_status mfwh_solve_gmres(mfwh_handle_t h, int restart, double tol, int max_i
          << " (spurious resonance?)";
       return fail(MFWH_ERR_SPURIOUS, os.str());
     }
+  }
+  return MFWH_OK;
+}
+
+mfwh_status mfwh_solve_refined(mfwh_handle_t h, int restart, double inner_tol, int max_iters,
+                               double target, int max_refinements, double* v,
+                               mfwh_solve_info* info) {
+  if (!h || !v) return fail(MFWH_ERR_INVALID_ARG, "null argument");
+  if (restart < 1 || restart > kMaxRestart)
+    return fail(MFWH_ERR_INVALID_ARG, "restart must be in 1..1023");
+  if (max_iters < 1 || !(inner_tol >= 0.0) || !(target > 0.0) || max_refinements < 0)
+    return fail(MFWH_ERR_INVALID_ARG, "bad max_iters, inner_tol, target or max_refinements");
+  if (restart > max_iters) restart = max_iters;
+  reset_timing(h);
+  mfwh_status st = ensure_basis(h, restart + 1);
+  if (st != MFWH_OK) return st;
+  if (!h->vec_r) CK(cudaMalloc(&h->vec_r, sizeof(double) * h->N));
+  if (!h->vec_e) CK(cudaMalloc(&h->vec_e, sizeof(double) * h->N));
+  mfwh_solve_info local{};
+  mfwh_solve_info& I = info ? *info : local;
+  I.iterations = I.pi_applications = I.restarts = I.refinements = 0;
+  I.history_len = 0;
+  I.rel_residual = NAN;
+  const int64_t N = h->N;
+  cudaStream_t s = h->stream;
+  double* x = nullptr;
+  bool on_dev = false;
+  st = stage_in(h, v, &x, &on_dev);
+  if (st != MFWH_OK) return st;
+  const bool inner32 = h->plan.precision != MFWH_PREC_FP64;
+  // b = Pi(0) with an FP64 wave solve
+  h->use32 = false;
+  st = apply_pi(h, nullptr, h->vec_b, 1, nullptr);
+  I.pi_applications++;
+  double bb = 0.0, xx = 0.0;
+  if (st == MFWH_OK) st = dots(h, h->vec_b, 1, h->vec_b, &bb);
+  if (st == MFWH_OK) st = dots(h, x, 1, x, &xx);
+  if (st == MFWH_OK && (!std::isfinite(bb) || !std::isfinite(xx)))
+    st = fail(MFWH_ERR_NONFINITE, "non-finite right-hand side or initial guess");
+  const double bnorm = std::sqrt(bb);
+  bool x_nonzero = xx > 0.0;
+  double r[MFWH_MAX_NF];
+  bool done = false;
+  mfwh_status inner = MFWH_OK;
+  for (int k = 0; st == MFWH_OK; ++k) {
+    st = residual_dev(h, x, r);       // r_h of the current iterate, FP64
+    if (st != MFWH_OK) break;
+    double worst = 0.0;
+    for (int m = 0; m < h->nf; ++m) worst = std::fmax(worst, r[m]);
+    if (worst <= target || bnorm == 0.0) {
+      done = true;
+      break;
+    }
+    if (k == max_refinements || I.iterations >= max_iters) break;
+    // outer residual in FP64: r = b - (x - S x)
+    h->use32 = false;
+    if (x_nonzero) {
+      st = apply_pi(h, x, h->vec_r, 0, x);
+      if (st != MFWH_OK) break;
+      I.pi_applications++;
+      launch_axpby(h->vec_r, 1.0, h->vec_b, -1.0, N, s);
+    } else {
+      launch_axpby(h->vec_r, 1.0, h->vec_b, 0.0, N, s);
+    }
+    h->total_launches++;
+    double rr = 0.0;
+    st = dots(h, h->vec_r, 1, h->vec_r, &rr);
+    if (st != MFWH_OK) break;
+    I.rel_residual = std::sqrt(rr) / bnorm;
+    // inner solve (I - S) e = r with the handle's wave precision
+    h->use32 = inner32;
+    launch_axpby(h->vec_e, 0.0, h->vec_e, 0.0, N, s);
+    h->total_launches++;
+    bool conv = false;
+    st = gmres_core(h, restart, inner_tol, max_iters - I.iterations, h->vec_e, h->vec_r, I, &conv);
+    if (st != MFWH_OK) break;
+    if (!conv) inner = MFWH_ERR_NOT_CONVERGED;
+    launch_axpby(x, 1.0, h->vec_e, 1.0, N, s);   // x += e
+    h->total_launches++;
+    x_nonzero = true;
+    I.refinements++;
+  }
+  h->use32 = inner32;
+  for (int m = 0; m < h->nf; ++m) I.helmholtz_residual[m] = st == MFWH_OK ? r[m] : NAN;
+  if (!on_dev) CK(cudaMemcpyAsync(v, x, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  mfwh_status ts = collect_timing(h);
+  if (st != MFWH_OK) return st;
+  if (ts != MFWH_OK) return ts;
+  if (!done) {
+    std::ostringstream os;
+    os << "refinement stopped after " << I.refinements << " corrections and " << I.iterations
+       << " Arnoldi steps"
+       << (inner != MFWH_OK ? " (an inner GMRES solve did not reach its tolerance)" : "")
+       << "; Helmholtz residual above the target " << target;
+    return fail(MFWH_ERR_NOT_CONVERGED, os.str());
   }
   return MFWH_OK;
 }
@@ -783,6 +906,8 @@ mfwh_status mfwh_last_timing(mfwh_handle_t h, double* step_ms, int64_t* step_lau
 void mfwh_destroy(mfwh_handle_t h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  if (h->vec_r) cudaFree(h->vec_r);
+  if (h->vec_e) cudaFree(h->vec_e);
   double* bufs[] = {h->f,         h->Wa,      h->Wb,          h->Wc2,     h->Wp2,
                     h->d_wq,      h->d_cos,   h->q,           h->res_partial, h->res_out,
                     h->dot_partial, h->dot_out, h->vec_b,     h->vec_x,   h->basis};

@@ -112,6 +112,10 @@ void launch_residual(int nf, const Geom& g, const double* v, const double* f, co
                      double c2_lo, double c2_hi, const double* inv_h2, double* partial, double* out,
                      cudaStream_t st);
 int64_t residual_partial_size(int nf);
+// Defect field R_m = f_m - (c^2 Delta_h + omega_m^2) v_m (0 on the boundary), [nf][points].
+void launch_residual_field(int nf, const Geom& g, const double* v, const double* f,
+                           const double* omega2, double c2_lo, double c2_hi, const double* inv_h2,
+                           double* R, cudaStream_t st);
 
 // ---- Krylov vector kernels (krylov.cu), FP64 -------------------------------------
 constexpr int kMaxDots = 32;       // vectors handled by one multi-dot / multi-axpy launch

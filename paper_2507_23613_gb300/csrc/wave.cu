@@ -284,6 +284,50 @@ void last_nf(const Geom& g, const double* Wc, const double* Wp, const double* f,
     k_last<NF, 3><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, q, vout, vsub, a, g);
 }
 
+// R_m = f_m - (c^2 Delta_h + omega_m^2) v_m at interior points, 0 on the boundary: the
+// defect of v in the discrete Helmholtz system (eq. MultipleHelmholtz), one thread per point.
+template <int NF, int DIM>
+__global__ void __launch_bounds__(kBX * kBY)
+k_residual_field(const double* __restrict__ v, const double* __restrict__ f,
+                 const ResParams<NF> a, const Geom g, double* __restrict__ R) {
+  const PointIndex x = point_index<DIM>(g);
+  if (!x.inside) return;
+  if (!x.interior) {
+#pragma unroll
+    for (int m = 0; m < NF; ++m) R[m * g.points + x.p] = 0.0;
+    return;
+  }
+  const int64_t li = g.layer_axis == 0 ? x.i : (g.layer_axis == 1 ? x.j : x.k);
+  const double c2 = li >= g.layer_split ? a.c2_hi : a.c2_lo;
+  const int64_t p = x.p;
+#pragma unroll
+  for (int m = 0; m < NF; ++m) {
+    const double* vm = v + m * g.points;
+    const double c = vm[p];
+    double lap = a.ihx2 * ((vm[p - 1] - c) + (vm[p + 1] - c)) +
+                 a.ihy2 * ((vm[p - g.sy] - c) + (vm[p + g.sy] - c));
+    if (DIM == 3) lap += a.ihz2 * ((vm[p - g.sz] - c) + (vm[p + g.sz] - c));
+    R[m * g.points + p] = f[m * g.points + p] - (c2 * lap + a.omega2[m] * c);
+  }
+}
+
+template <int NF>
+void residual_field_nf(const Geom& g, const double* v, const double* f, const double* omega2,
+                       double c2_lo, double c2_hi, const double* inv_h2, double* R,
+                       cudaStream_t st) {
+  ResParams<NF> a;
+  for (int m = 0; m < NF; ++m) a.omega2[m] = omega2[m];
+  a.c2_lo = c2_lo;
+  a.c2_hi = c2_hi;
+  a.ihx2 = inv_h2[0];
+  a.ihy2 = inv_h2[1];
+  a.ihz2 = inv_h2[2];
+  if (g.dim == 2)
+    k_residual_field<NF, 2><<<step_grid(g), dim3(kBX, kBY), 0, st>>>(v, f, a, g, R);
+  else
+    k_residual_field<NF, 3><<<step_grid(g), dim3(kBX, kBY), 0, st>>>(v, f, a, g, R);
+}
+
 template <int NF>
 void residual_nf(const Geom& g, const double* v, const double* f, const double* omega2,
                  double c2_lo, double c2_hi, const double* inv_h2, double* partial, double* out,
@@ -348,5 +392,13 @@ void launch_residual(int nf, const Geom& g, const double* v, const double* f, co
 }
 
 int64_t residual_partial_size(int nf) { return (int64_t)kResBlocks * 2 * nf; }
+
+void launch_residual_field(int nf, const Geom& g, const double* v, const double* f,
+                           const double* omega2, double c2_lo, double c2_hi, const double* inv_h2,
+                           double* R, cudaStream_t st) {
+#define CALL(N) residual_field_nf<N>(g, v, f, omega2, c2_lo, c2_hi, inv_h2, R, st)
+  MFWH_NF_SWITCH(nf, CALL)
+#undef CALL
+}
 
 }  // namespace mfwh

@@ -163,3 +163,49 @@ def test_fp32_gmres_reaches_discrete_helmholtz_solution():
     assert np.all(info["helmholtz_residual"] <= TOL_RH32), info["helmholtz_residual"]
     r = s.residual(x)
     np.testing.assert_allclose(r, W.helmholtz_residual(prob, x.cpu().numpy()), rtol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# Mixed-precision defect correction (mfwh_solve_refined)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", [_lib.PREC_FP32_KAHAN, _lib.PREC_FP32_BLOCKSUM])
+def test_refined_fp32_reaches_fp64_accuracy(prec):
+    """FP32 wave solves inside an FP64 defect-correction loop reach the discrete Helmholtz
+    solution to FP64-level accuracy (the FP32-only solve stops near 2e-7)."""
+    wl = inputs.square_small()
+    prob = W.make_problem(W.Grid(wl.n, wl.length), wl.omega, wl.forcing, cfl=wl.cfl, n_p=wl.n_p)
+    U = W.helmholtz_direct(prob)
+    s = M.Solver(wl.n, wl.length, wl.omega, dev(wl.forcing), n_p=wl.n_p, cfl=wl.cfl,
+                 precision=prec)
+    before = apply(s, np.zeros_like(wl.forcing), True)
+    x = torch.zeros(wl.forcing.shape, dtype=torch.float64, device="cuda")
+    info = s.solve_refined(x, target=1e-10, inner_tol=1e-7, restart=100, max_iters=100,
+                           max_refinements=8)
+    assert info["status"] == _lib.OK and 1 <= info["refinements"] <= 8
+    err = rel_err(x.cpu().numpy(), U)
+    assert np.all(err <= 1e-9), err
+    rh = W.helmholtz_residual(prob, x.cpu().numpy())
+    assert np.all(rh <= 1e-10), rh
+    np.testing.assert_allclose(info["helmholtz_residual"], rh, rtol=1e-6, atol=1e-14)
+    # the handle's own forcing is back in place for the wave solve
+    assert np.array_equal(apply(s, np.zeros_like(wl.forcing), True), before)
+
+
+def test_refined_fp64_handle_and_warm_start():
+    wl = inputs.square_small()
+    prob = W.make_problem(W.Grid(wl.n, wl.length), wl.omega, wl.forcing, cfl=wl.cfl, n_p=wl.n_p)
+    U = W.helmholtz_direct(prob)
+    s = M.Solver(wl.n, wl.length, wl.omega, dev(wl.forcing), n_p=wl.n_p, cfl=wl.cfl)
+    x = torch.zeros(wl.forcing.shape, dtype=torch.float64, device="cuda")
+    info = s.solve_refined(x, target=1e-9, inner_tol=1e-10, restart=100, max_iters=100)
+    assert info["status"] == _lib.OK
+    assert np.all(rel_err(x.cpu().numpy(), U) <= 1e-9)
+    # starting from the solution: no correction is needed
+    info2 = s.solve_refined(x, target=1e-8, inner_tol=1e-10, restart=100, max_iters=100)
+    assert info2["refinements"] == 0 and info2["iterations"] == 0
+    # a target that cannot be met within the allowed corrections is reported
+    y = torch.zeros_like(x)
+    info3 = s.solve_refined(y, target=1e-14, inner_tol=1e-2, restart=5, max_iters=5,
+                            max_refinements=1, raise_on_error=False)
+    assert info3["status"] == _lib.ERR_NOT_CONVERGED and info3["refinements"] == 1
