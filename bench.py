@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--solve", action="store_true", help="also time one unrestarted solve to 1e-8")
     ap.add_argument("--time-block", type=int, default=0,
                     help="leapfrog steps per kernel launch (0 = library default)")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 wave-solve leg")
+    ap.add_argument("--fp32-only", action="store_true",
+                    help="run only the FP32 leg and print it (for profiling its kernel)")
     ap.add_argument("--no-clocks", action="store_true",
                     help="do not sample nvidia-smi (for runs under a profiler)")
     return ap.parse_args()
@@ -91,9 +94,9 @@ def flops_per_point_step(nf, forced, dim=2):
     return 2 * fma + adds
 
 
-def kernel_traffic(kernel_key):
-    """dram bytes per launch from the committed ncu summary, if it is for this source."""
-    path = os.path.join(ROOT, "profiles", "k_step_square1025_nf8.txt")
+def kernel_traffic(profile, kernel_key):
+    """dram bytes per launch from a committed ncu summary, if it is for this kernel source."""
+    path = os.path.join(ROOT, "profiles", profile)
     if not os.path.exists(path):
         return None
     vals = {}
@@ -110,11 +113,26 @@ def kernel_traffic(kernel_key):
         return None
 
 
+def _region(path, end_marker):
+    with open(os.path.join(ROOT, "paper_2507_23613_gb300", "csrc", path), "rb") as fh:
+        text = fh.read()
+    cut = text.find(end_marker.encode())
+    return text if cut < 0 else text[:cut]
+
+
 def kernel_source_key():
+    """Hash of the FP64 step kernels' source: wave.cu up to the residual kernels and the
+    kernel argument structs of kernels.h."""
     h = hashlib.sha256()
-    for f in ("wave.cu", "kernels.h"):
-        with open(os.path.join(ROOT, "paper_2507_23613_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    h.update(_region("wave.cu", "// ---- Helmholtz residual"))
+    h.update(_region("kernels.h", "// Arguments of one temporally blocked launch"))
+    return h.hexdigest()[:16]
+
+
+def fp32_kernel_source_key():
+    """Hash of the FP32 blocked kernel's source (wave32_kernels.cuh)."""
+    h = hashlib.sha256()
+    h.update(_region("wave32_kernels.cuh", "// ---- init and conversion"))
     return h.hexdigest()[:16]
 
 
@@ -223,6 +241,87 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def fp32_bytes_per_point_launch(nf, forced):
+    """Algorithmic HBM bytes per interior point of one blocked FP32 launch (any depth T):
+    read and write W and D (4 B each) and the Kahan pairs (2 x 4 B per frequency), read the
+    FP32 forcing when forced."""
+    return 4 * (4 + 4 * nf + (nf if forced else 0))
+
+
+def fp32_leg(args, wl, f_dev, stream, n_t):
+    """The same GMRES(20) cycle with FP32 wave solves (increment form, filter partial sums
+    folded into Kahan pairs once per blocked launch), and the FP32 map's error per
+    frequency against the FP64 map."""
+    import torch
+    import paper_2507_23613_gb300 as M
+    from paper_2507_23613_gb300 import _lib
+    s32 = M.Solver(wl.n, wl.length, wl.omega, f_dev, stream=stream.cuda_stream, n_p=wl.n_p,
+                   cfl=wl.cfl, precision=_lib.PREC_FP32_BLOCKSUM)
+    v = torch.zeros(wl.forcing.shape, dtype=torch.float64, device="cuda")
+
+    def cycle():
+        with torch.cuda.stream(stream):
+            v.zero_()
+        info = s32.solve_gmres(v, restart=RESTART, tol=TOL, max_iters=MAX_ITERS,
+                               raise_on_error=False)
+        ms, step_launches, launches = s32.last_timing()
+        return info, ms, step_launches, launches + 1
+
+    for _ in range(max(1, args.warmup)):
+        cycle()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    infos = [cycle() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    elapsed = ev0.elapsed_time(ev1)
+    pi_apps = sum(i[0]["pi_applications"] for i in infos)
+    forced_apps = len(infos)
+    step_ms = sum(i[1] for i in infos)
+    step_launches = sum(i[2] for i in infos)
+    alg = wl.interior_points * (forced_apps * fp32_bytes_per_point_launch(wl.nf, True)
+                                + (pi_apps - forced_apps) * fp32_bytes_per_point_launch(wl.nf, False))
+    launches_per_pi = step_launches / max(pi_apps, 1)
+    alg_bytes = alg * launches_per_pi
+    gbs = alg_bytes / (step_ms * 1e-3) / 1e9
+    hbm_peak, peak_kind = peaks()
+    # error of one FP32 map against the FP64 map, per frequency
+    rng = np.random.default_rng(11)
+    x = rng.normal(size=wl.forcing.shape) * 0.01
+    g = x.reshape(wl.nf, wl.n[1] + 1, wl.n[0] + 1)
+    g[:, [0, -1], :] = 0.0
+    g[:, :, [0, -1]] = 0.0
+    xd = torch.from_numpy(x).cuda()
+    o32 = torch.empty_like(xd)
+    o64 = torch.empty_like(xd)
+    s64 = M.Solver(wl.n, wl.length, wl.omega, f_dev, stream=stream.cuda_stream, n_p=wl.n_p,
+                   cfl=wl.cfl)
+    with torch.cuda.stream(stream):
+        s32.apply_Pi(xd, o32, forced=True)
+        s64.apply_Pi(xd, o64, forced=True)
+    torch.cuda.synchronize()
+    a = o32.cpu().numpy().reshape(wl.nf, -1)
+    b = o64.cpu().numpy().reshape(wl.nf, -1)
+    err = (np.max(np.abs(a - b), axis=1) / np.max(np.abs(b), axis=1)).tolist()
+    s64.close()
+    s32.close()
+    return {"precision": "fp32 wave steps, Kahan filter pairs folded per launch, FP64 Arnoldi",
+            "value": round(wl.interior_points * n_t * pi_apps / (elapsed * 1e-3) / 1e9, 3),
+            "unit": "Gpts/s", "ms_per_step": round(elapsed / args.steps, 3),
+            "roofline": {"bound": "hbm", "kernel": "k_tb2d32 (blocked FP32 leapfrog + filters)",
+                         "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                         "frac": round(gbs / hbm_peak, 4), "peak_source": peak_kind,
+                         "alg_bytes_per_launch": round(alg_bytes / max(step_launches, 1)),
+                         "avg_launch_us": round(step_ms * 1e3 / max(step_launches, 1), 2),
+                         "steps_per_launch": round(n_t / launches_per_pi, 2),
+                         "traffic": kernel_traffic("k_tb2d32_square1025_nf8.txt",
+                                                   fp32_kernel_source_key())},
+            "pi_rel_err_vs_fp64_per_freq": [float(f"{e:.3e}") for e in err],
+            "rel_residual_after_cycle": infos[-1][0]["rel_residual"]}
+
+
 def workload_config(wl, n_t):
     return {"workload": f"square{wl.n[0] + 1}x{wl.n[1] + 1}_nf{wl.nf}_np{wl.n_p}_gmres{RESTART}_cycle",
             "step": "one GMRES(20) cycle from zero: b = Pi(0), 20 Arnoldi steps, update, residual check",
@@ -258,6 +357,11 @@ def main():
     wl = inputs.square_large(args.seed + rank)
     stream = torch.cuda.Stream()
     f_dev = torch.from_numpy(wl.forcing).cuda()
+    if args.fp32_only:
+        from paper_2507_23613_gb300 import _lib
+        n_t32 = M.plan(M.make_problem(wl.n, wl.length, wl.omega, n_p=wl.n_p, cfl=wl.cfl)[0]).n_t
+        print(json.dumps({"fp32": fp32_leg(args, wl, f_dev, stream, n_t32)}), flush=True)
+        return
     solver = M.Solver(wl.n, wl.length, wl.omega, f_dev, stream=stream.cuda_stream,
                       n_p=wl.n_p, cfl=wl.cfl, time_block=args.time_block)
     n_t = solver.setup["n_t"]
@@ -356,9 +460,11 @@ def main():
                "rel_residual": info["rel_residual"],
                "max_helmholtz_residual": float(np.max(info["helmholtz_residual"]))}
 
+    fp32 = None if args.no_fp32 else fp32_leg(args, wl, f_dev, stream, n_t)
+
     if rank != 0:
         return
-    traffic = kernel_traffic(kernel_source_key())
+    traffic = kernel_traffic("k_step_square1025_nf8.txt", kernel_source_key())
     homog_launch_bytes = wl.interior_points * bytes_per_point_step(wl.nf, False)
     t_hbm = alg_bytes / (hbm_peak * 1e9)
     t_alu = alg_flops / (FP64_PEAK_TFLOPS * 1e12)
@@ -389,6 +495,7 @@ def main():
                   "rel_residual_after_cycle": infos[-1][0]["rel_residual"],
                   "max_helmholtz_residual": float(np.max(infos[-1][0]["helmholtz_residual"]))},
         "time_to_solution": tts,
+        "fp32": fp32,
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(wl)
