@@ -203,6 +203,40 @@ mfwh_status mfwh_solve_refined(mfwh_handle_t h, int restart, double inner_tol, i
                                double target, int max_refinements, double* v,
                                mfwh_solve_info* info);
 
+/* ---- many problems: graphs, batches, autotuning (SURVEY's batched workload; the paper
+ * solves one problem at a time) ---------------------------------------------------- */
+
+/* CUDA-graph mode for one handle.  With enable != 0, each variant of the wave solve used by
+ * the handle's calls (forced or homogeneous, with or without an input, with or without the
+ * v - S v subtraction, FP64 or FP32 arithmetic) is captured once into a CUDA graph on two
+ * staging vectors owned by the handle (2 * nf * points doubles, allocated here) and replayed
+ * as one graph launch per application of Pi, between a device-to-device copy in and out.
+ * Results are bit-identical to direct launches.  enable = 0 drops the graphs.  Synchronises
+ * the handle's stream.  Capture happens on the first use of a variant: do not call the
+ * handle inside another stream capture then. */
+mfwh_status mfwh_set_graphs(mfwh_handle_t h, int enable);
+
+/* Solve count independent problems concurrently: one host thread per handle runs
+ * mfwh_solve_gmres(handles[i], restart, tol, max_iters, 0, v[i], &infos[i]) on the handle's
+ * own stream (give the handles distinct streams to overlap them on the GPU; handles in graph
+ * mode launch one graph per Pi).  seconds[i] (host array, may be NULL) receives the time from
+ * the common start to the end of problem i's solve.  Handles must be distinct; infos may be
+ * NULL.  Returns MFWH_OK when every solve converged, else the first failing status (hard
+ * errors before MFWH_ERR_NOT_CONVERGED) with its problem index in mfwh_last_error(). */
+mfwh_status mfwh_solve_batch(const mfwh_handle_t* handles, int count, int restart, double tol,
+                             int max_iters, double* const* v, mfwh_solve_info* infos,
+                             double* seconds);
+
+/* Autotuner for the blocked wave kernels.  Times the first steps (at most 96) of a
+ * homogeneous wave solve of prob on the current device for each candidate temporal depth and
+ * tile shape (FP32, 2D: depths 4, 8, 16 x tile shapes 0, 1, 2; FP64, 2D: depths 1, 4, 8;
+ * 3D: depth 1), keeping the fastest: *time_block and *tile_shape receive it, *ms_per_step
+ * (may be NULL) its time per leapfrog step.  Results are cached per device, grid, number of
+ * frequencies and precision for the life of the process.  Allocates (and frees) one handle's
+ * workspace per candidate on the given stream; synchronous. */
+mfwh_status mfwh_autotune(const mfwh_problem* prob, void* stream, int* time_block,
+                          int* tile_shape, double* ms_per_step);
+
 /* Helmholtz residual r_h^{(m)} = max_int |f_m - (L_h + omega_m^2) v_m| / max_int |f_m|
  * (eq. errorAndResid, with +omega^2 as in eq. MultipleHelmholtz).
  * v: host or device [nf][points]; r_out: host [nf].  Synchronous. */

@@ -113,6 +113,37 @@ def mfwh_residual_noalloc(problem, forcing, v, stream=None):
     return r
 
 
+def autotune(n, length, omega, stream=None, **kw):
+    """Best (time_block, tile_shape, ms per step) for a problem on the current device."""
+    problem, keep = make_problem(n, length, omega, None, **kw)
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    tb, shape, ms = C.c_int(), C.c_int(), C.c_double()
+    _lib.check(_lib.load().mfwh_autotune(C.byref(problem), C.c_void_p(stream), C.byref(tb),
+                                         C.byref(shape), C.byref(ms)))
+    return tb.value, shape.value, ms.value
+
+
+def solve_batch(solvers, vs, restart=20, tol=1e-8, max_iters=1000, raise_on_error=True):
+    """Concurrent GMRES solves of independent problems (mfwh_solve_batch).
+    Returns (status, per-problem info dicts, per-problem seconds)."""
+    n = len(solvers)
+    hs = (C.c_void_p * n)(*[s._handle.value for s in solvers])
+    ptrs = (C.c_void_p * n)(*[_as_ptr(v).value for v in vs])
+    infos = (_lib.SolveInfo * n)()
+    secs = np.zeros(n)
+    st = _lib.load().mfwh_solve_batch(hs, n, int(restart), float(tol), int(max_iters), ptrs,
+                                      infos, _dptr(secs))
+    if raise_on_error:
+        _lib.check(st)
+    out = [{"iterations": infos[i].iterations, "pi_applications": infos[i].pi_applications,
+            "rel_residual": infos[i].rel_residual,
+            "helmholtz_residual": np.array(infos[i].helmholtz_residual[:solvers[i].nf])}
+           for i in range(n)]
+    return st, out, secs
+
+
 def setup_arrays(s):
     """numpy views of an mfwh_setup's tables, trimmed to nf."""
     nf = s.nf
@@ -211,6 +242,9 @@ class Solver:
             "helmholtz_residual": np.array(info.helmholtz_residual[:self.nf]),
             "history": hist[:info.history_len].copy(),
         }
+
+    def set_graphs(self, enable=True):
+        _lib.check(_lib.load().mfwh_set_graphs(self._handle, int(bool(enable))))
 
     def residual(self, v):
         r = np.zeros(self.nf)

@@ -105,6 +105,11 @@ _SIGNATURES = {
                                    C.c_void_p, C.POINTER(SolveInfo)]),
     "mfwh_solve_refined": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_double,
                                      C.c_int, C.c_void_p, C.POINTER(SolveInfo)]),
+    "mfwh_set_graphs": (C.c_int, [C.c_void_p, C.c_int]),
+    "mfwh_solve_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_double, C.c_int,
+                                   C.POINTER(C.c_void_p), C.POINTER(SolveInfo), _dp]),
+    "mfwh_autotune": (C.c_int, [C.POINTER(Problem), C.c_void_p, C.POINTER(C.c_int),
+                                C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "mfwh_residual": (C.c_int, [C.c_void_p, C.c_void_p, _dp]),
     "mfwh_residual_noalloc": (C.c_int, [C.POINTER(Problem), C.c_void_p, C.c_void_p, _dp, C.c_void_p]),
     "mfwh_get_setup": (C.c_int, [C.c_void_p, C.POINTER(Setup)]),

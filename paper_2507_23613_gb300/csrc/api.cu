@@ -2,7 +2,13 @@
 // iteration (Algorithm 1), GMRES on A = I - S (Section "Acceleration by Krylov
 // methods") and the Helmholtz residual (eq. errorAndResid).
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <tuple>
 #include <cstdio>
 #include <cstring>
 #include <sstream>
@@ -71,6 +77,16 @@ struct mfwh_handle_s {
   double omega2[MFWH_MAX_NF] = {};
   double* f = nullptr;              // forcing [nf][P]
   bool use32 = false;               // wave solves in FP32 (the FP32 precisions)
+  // CUDA-graph mode (mfwh_set_graphs): each variant of the wave solve is captured once on the
+  // staging buffers g_in / g_out and replayed as one graph launch.
+  bool graphs = false;
+  cudaStream_t gstream = nullptr;   // private stream the graphs are captured and replayed on
+  cudaEvent_t gev[2] = {};          // orders gstream after / before the caller's stream
+  double* g_in = nullptr;
+  double* g_out = nullptr;
+  cudaGraphExec_t gexec[16] = {};
+  int64_t g_steps[16] = {}, g_total[16] = {};
+  int tune_steps = 0;               // autotuner only: stop the wave solve after this many steps
   double* vec_r = nullptr;          // outer residual of the refined solve [nf][P] (lazy)
   double* vec_e = nullptr;          // correction of the refined solve [nf][P] (lazy)
   double* Wa = nullptr;             // wave levels (ping-pong)
@@ -148,6 +164,7 @@ mfwh_status apply_pi32(mfwh_handle_t h, const double* vin, double* vout, int for
   const Plan& P = h->plan;
   const int nf = h->nf;
   const int n_t = P.s.n_t;
+  const int n_run = h->tune_steps > 0 ? std::min(h->tune_steps, n_t) : n_t;
   const double dt = P.s.dt;
   cudaStream_t st = h->stream;
   float w0[MFWH_MAX_NF];
@@ -176,9 +193,9 @@ mfwh_status apply_pi32(mfwh_handle_t h, const double* vin, double* vout, int for
     a.acc = P.precision == MFWH_PREC_FP32_BLOCKSUM ? 1 : 0;
     a.forced = forced;
     int cur = 0;                 // pair holding the input: (W32[2 cur], W32[2 cur + 1])
-    for (int n0 = 0; n0 < n_t;) {
+    for (int n0 = 0; n0 < n_run;) {
       a.n0 = n0;
-      a.steps = std::min(P.time_block, n_t - n0);
+      a.steps = std::min(P.time_block, n_run - n0);
       a.last = n0 + a.steps == n_t;
       const float* D_in = n0 == 0 ? nullptr : h->W32[2 * cur + 1];
       launch_tb2d32(nf, h->geom, h->W32[2 * cur], D_in, h->W32[2 * (1 - cur)],
@@ -193,7 +210,7 @@ mfwh_status apply_pi32(mfwh_handle_t h, const double* vin, double* vout, int for
     float* Wc = h->W32[0];
     float* Wn = h->W32[2];
     float* D = h->W32[1];
-    for (int n = 0; n < n_t; ++n) {
+    for (int n = 0; n < n_run; ++n) {
       a.lo = n == 0 ? first_lo : reg_lo;
       a.hi = n == 0 ? first_hi : reg_hi;
       for (int m = 0; m < nf; ++m) {
@@ -224,8 +241,8 @@ mfwh_status apply_pi32(mfwh_handle_t h, const double* vin, double* vout, int for
 mfwh_status apply_pi_tb(mfwh_handle_t h, const double* vin, double* vout, int forced,
                         const double* vsub);
 
-mfwh_status apply_pi(mfwh_handle_t h, const double* vin, double* vout, int forced,
-                     const double* vsub) {
+mfwh_status apply_pi_direct(mfwh_handle_t h, const double* vin, double* vout, int forced,
+                            const double* vsub) {
   if (h->use32) return apply_pi32(h, vin, vout, forced, vsub);
   // The FP64 blocked kernel serves FP64 handles (depth 4 or 8); FP64 wave solves of an FP32
   // handle (the outer residuals of mfwh_solve_refined) take one step per launch.
@@ -234,6 +251,7 @@ mfwh_status apply_pi(mfwh_handle_t h, const double* vin, double* vout, int force
   const Plan& P = h->plan;
   const int nf = h->nf;
   const int n_t = P.s.n_t;
+  const int n_run = h->tune_steps > 0 ? std::min(h->tune_steps, n_t) : n_t;
   const double dt = P.s.dt;
   cudaStream_t st = h->stream;
   launch_init(nf, h->geom, vin, h->Wa, h->q, &P.w[0], st);
@@ -245,7 +263,7 @@ mfwh_status apply_pi(mfwh_handle_t h, const double* vin, double* vout, int force
   StepHost& a = h->sh;
   a.forced = forced;
   a.subtract = vsub != nullptr;
-  for (int n = 0; n < n_t; ++n) {
+  for (int n = 0; n < n_run; ++n) {
     const bool first = n == 0;
     const double kappa = first ? 0.5 * dt * dt : dt * dt;
     const double a_cur = first ? 1.0 : 2.0;
@@ -263,8 +281,8 @@ mfwh_status apply_pi(mfwh_handle_t h, const double* vin, double* vout, int force
       launch_last(nf, h->geom, Wc, Wp, h->f, h->q, vout, vsub, a, st);
     }
   }
-  h->step_launches += n_t;
-  h->total_launches += n_t;
+  h->step_launches += n_run;
+  h->total_launches += n_run;
   if (timed) {
     CK(cudaEventRecord(h->ev[h->ev_used + 1], st));
     h->ev_used += 2;
@@ -280,6 +298,7 @@ mfwh_status apply_pi_tb(mfwh_handle_t h, const double* vin, double* vout, int fo
   const Plan& P = h->plan;
   const int nf = h->nf;
   const int n_t = P.s.n_t;
+  const int n_run = h->tune_steps > 0 ? std::min(h->tune_steps, n_t) : n_t;
   const double dt = P.s.dt;
   const int depth = P.time_block;
   if (depth != 4 && depth != 8) return fail(MFWH_ERR_INVALID_ARG, "FP64 blocking depth must be 4 or 8");
@@ -306,9 +325,9 @@ mfwh_status apply_pi_tb(mfwh_handle_t h, const double* vin, double* vout, int fo
   double* out_c = h->Wc2;
   double* out_p = h->Wp2;
   int launches = 0;
-  for (int n0 = 0; n0 < n_t;) {
+  for (int n0 = 0; n0 < n_run;) {
     a.n0 = n0;
-    a.steps = std::min(depth, n_t - n0);
+    a.steps = std::min(depth, n_run - n0);
     a.last = n0 + a.steps == n_t;
     launch_tb2d(nf, h->geom, in_c, in_p, out_c, out_p, h->f, h->q, vout, vsub, a, st);
     ++launches;
@@ -329,6 +348,73 @@ mfwh_status apply_pi_tb(mfwh_handle_t h, const double* vin, double* vout, int fo
   }
   CK(cudaGetLastError());
   return MFWH_OK;
+}
+
+// One wave solve: replayed from a captured graph in graph mode, launched directly otherwise.
+mfwh_status apply_pi(mfwh_handle_t h, const double* vin, double* vout, int forced,
+                     const double* vsub) {
+  if (!h->graphs || (vsub && vsub != vin) || h->tune_steps > 0)
+    return apply_pi_direct(h, vin, vout, forced, vsub);
+  const int key = (vin ? 1 : 0) | (forced ? 2 : 0) | (vsub ? 4 : 0) | (h->use32 ? 8 : 0);
+  cudaStream_t st = h->gstream;
+  CK(cudaEventRecord(h->gev[0], h->stream));
+  CK(cudaStreamWaitEvent(st, h->gev[0], 0));
+  if (!h->gexec[key]) {
+    const int saved_ev = h->ev_used;
+    const int64_t sl = h->step_launches, tl = h->total_launches;
+    h->ev_used = (int)h->ev.size();   // no timing events inside the graph
+    cudaStream_t user = h->stream;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+    h->stream = st;
+    mfwh_status cs = apply_pi_direct(h, vin ? h->g_in : nullptr, h->g_out, forced,
+                                     vsub ? h->g_in : nullptr);
+    h->stream = user;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    h->ev_used = saved_ev;
+    h->g_steps[key] = h->step_launches - sl;
+    h->g_total[key] = h->total_launches - tl;
+    h->step_launches = sl;
+    h->total_launches = tl;
+    if (cs != MFWH_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return cs;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->gexec[key], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      h->gexec[key] = nullptr;
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+  }
+  if (vin) CK(cudaMemcpyAsync(h->g_in, vin, sizeof(double) * h->N, cudaMemcpyDeviceToDevice, st));
+  const bool timed = h->ev_used + 2 <= (int)h->ev.size();
+  if (timed) CK(cudaEventRecord(h->ev[h->ev_used], st));
+  CK(cudaGraphLaunch(h->gexec[key], st));
+  if (timed) {
+    CK(cudaEventRecord(h->ev[h->ev_used + 1], st));
+    h->ev_used += 2;
+  }
+  CK(cudaMemcpyAsync(vout, h->g_out, sizeof(double) * h->N, cudaMemcpyDeviceToDevice, st));
+  CK(cudaEventRecord(h->gev[1], st));
+  CK(cudaStreamWaitEvent(h->stream, h->gev[1], 0));
+  h->step_launches += h->g_steps[key];
+  h->total_launches += h->g_total[key];
+  return MFWH_OK;
+}
+
+mfwh_status collect_timing_sync(mfwh_handle_t h) {
+  CK(cudaStreamSynchronize(h->stream));
+  return collect_timing(h);
+}
+
+void drop_graphs(mfwh_handle_t h) {
+  for (auto& g : h->gexec)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
 }
 
 mfwh_status dots(mfwh_handle_t h, const double* V, int k, const double* w, double* out_host) {
@@ -906,6 +992,15 @@ mfwh_status mfwh_last_timing(mfwh_handle_t h, double* step_ms, int64_t* step_lau
 void mfwh_destroy(mfwh_handle_t h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  drop_graphs(h);
+  if (h->gstream) {
+    cudaStreamSynchronize(h->gstream);
+    cudaStreamDestroy(h->gstream);
+  }
+  for (auto& e : h->gev)
+    if (e) cudaEventDestroy(e);
+  if (h->g_in) cudaFree(h->g_in);
+  if (h->g_out) cudaFree(h->g_out);
   if (h->vec_r) cudaFree(h->vec_r);
   if (h->vec_e) cudaFree(h->vec_e);
   double* bufs[] = {h->f,         h->Wa,      h->Wb,          h->Wc2,     h->Wp2,
@@ -921,6 +1016,141 @@ void mfwh_destroy(mfwh_handle_t h) {
   for (auto& x : h->ev)
     if (x) cudaEventDestroy(x);
   delete h;
+}
+
+mfwh_status mfwh_set_graphs(mfwh_handle_t h, int enable) {
+  if (!h) return fail(MFWH_ERR_INVALID_ARG, "null handle");
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->gstream) CK(cudaStreamSynchronize(h->gstream));
+  drop_graphs(h);
+  if (enable && !h->g_in) {
+    CK(cudaMalloc(&h->g_in, sizeof(double) * h->N));
+    CK(cudaMalloc(&h->g_out, sizeof(double) * h->N));
+    CK(cudaMemsetAsync(h->g_in, 0, sizeof(double) * h->N, h->stream));
+    CK(cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
+    for (auto& e : h->gev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  h->graphs = enable != 0;
+  return MFWH_OK;
+}
+
+mfwh_status mfwh_solve_batch(const mfwh_handle_t* handles, int count, int restart, double tol,
+                             int max_iters, double* const* v, mfwh_solve_info* infos,
+                             double* seconds) {
+  if (!handles || !v || count < 1) return fail(MFWH_ERR_INVALID_ARG, "bad batch arguments");
+  for (int i = 0; i < count; ++i) {
+    if (!handles[i] || !v[i]) return fail(MFWH_ERR_INVALID_ARG, "null handle or buffer in batch");
+    for (int j = 0; j < i; ++j)
+      if (handles[j] == handles[i]) return fail(MFWH_ERR_INVALID_ARG, "a handle appears twice");
+  }
+  std::vector<mfwh_status> status(count, MFWH_OK);
+  std::vector<std::string> msg(count);
+  std::vector<double> secs(count, 0.0);
+  std::vector<mfwh_solve_info> local(count);
+  std::atomic<int> ready{0};
+  std::atomic<bool> go{false};
+  std::chrono::steady_clock::time_point t0;   // written before `go`, read after it
+  auto work = [&](int i) {
+    mfwh_handle_t h = handles[i];
+    cudaSetDevice(h->device);
+    mfwh_solve_info& I = infos ? infos[i] : local[i];
+    ready.fetch_add(1);
+    while (!go.load()) std::this_thread::yield();
+    status[i] = mfwh_solve_gmres(h, restart, tol, max_iters, 0.0, v[i], &I);
+    secs[i] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (status[i] != MFWH_OK) msg[i] = g_error;
+  };
+  std::vector<std::thread> pool;
+  pool.reserve(count);
+  for (int i = 0; i < count; ++i) pool.emplace_back(work, i);
+  while (ready.load() < count) std::this_thread::yield();
+  t0 = std::chrono::steady_clock::now();
+  go.store(true);
+  for (auto& t : pool) t.join();
+  if (seconds)
+    for (int i = 0; i < count; ++i) seconds[i] = secs[i];
+  for (int i = 0; i < count; ++i)
+    if (status[i] != MFWH_OK && status[i] != MFWH_ERR_NOT_CONVERGED) {
+      set_error("problem " + std::to_string(i) + ": " + msg[i]);
+      return status[i];
+    }
+  for (int i = 0; i < count; ++i)
+    if (status[i] != MFWH_OK) {
+      set_error("problem " + std::to_string(i) + ": " + msg[i]);
+      return status[i];
+    }
+  return MFWH_OK;
+}
+
+mfwh_status mfwh_autotune(const mfwh_problem* prob, void* stream, int* time_block,
+                          int* tile_shape, double* ms_per_step) {
+  if (!prob || !time_block || !tile_shape) return fail(MFWH_ERR_INVALID_ARG, "null argument");
+  Plan P;
+  mfwh_status st = plan_problem(prob, &P);
+  if (st != MFWH_OK) return st;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  using Key = std::tuple<int, int, int64_t, int64_t, int64_t, int, int>;
+  static std::mutex mu;
+  static std::map<Key, std::tuple<int, int, double>> cache;
+  const Key key{dev, P.dim, P.n[0], P.n[1], P.dim == 3 ? P.n[2] : 0, P.s.nf, P.precision};
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      *time_block = std::get<0>(it->second);
+      *tile_shape = std::get<1>(it->second);
+      if (ms_per_step) *ms_per_step = std::get<2>(it->second);
+      return MFWH_OK;
+    }
+  }
+  std::vector<std::pair<int, int>> cand;
+  if (P.dim == 3) {
+    cand = {{1, 0}};
+  } else if (P.precision == MFWH_PREC_FP64) {
+    cand = {{1, 0}, {4, 0}, {8, 0}};
+  } else {
+    for (int T : {4, 8, 16})
+      for (int shape : {0, 1, 2}) cand.push_back({T, shape});
+  }
+  // Each candidate times the first tune_n steps of a homogeneous wave solve (whole launches
+  // for every depth), after one untimed warm-up of the same length.
+  const int tune_n = std::min(P.s.n_t, 96);
+  double best = 1e300;
+  int best_tb = cand[0].first, best_shape = cand[0].second;
+  for (auto [tb, shape] : cand) {
+    mfwh_problem q = *prob;
+    q.time_block = tb;
+    q.tile_shape = shape;
+    mfwh_handle_t h = nullptr;
+    st = mfwh_create(&q, stream, &h);
+    if (st != MFWH_OK) return st;
+    h->tune_steps = tune_n;
+    double ms = 1e300;
+    for (int rep = 0; rep < 3 && st == MFWH_OK; ++rep) {
+      reset_timing(h);
+      st = apply_pi(h, nullptr, h->vec_b, 0, nullptr);
+      if (st == MFWH_OK) st = collect_timing_sync(h);
+      if (rep > 0) ms = std::min(ms, h->last_step_ms);
+    }
+    mfwh_destroy(h);
+    if (st != MFWH_OK) return st;
+    if (ms < best) {
+      best = ms;
+      best_tb = tb;
+      best_shape = shape;
+    }
+  }
+  const double per_step = best / tune_n;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = {best_tb, best_shape, per_step};
+  }
+  *time_block = best_tb;
+  *tile_shape = best_shape;
+  if (ms_per_step) *ms_per_step = per_step;
+  return MFWH_OK;
 }
 
 }  // extern "C"
