@@ -55,6 +55,15 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 wave-solve leg")
     ap.add_argument("--fp32-only", action="store_true",
                     help="run only the FP32 leg and print it (for profiling its kernel)")
+    ap.add_argument("--batched", action="store_true",
+                    help="run the batched workload (independent 2D problems solved concurrently)")
+    ap.add_argument("--batch", type=int, default=48, help="problems in the batched workload")
+    ap.add_argument("--batch-iters", type=int, default=10,
+                    help="GMRES(10) Arnoldi steps per problem in the batched workload")
+    ap.add_argument("--batch-mem-gb", type=float, default=180.0,
+                    help="device-memory budget of the batched workload")
+    ap.add_argument("--cube", action="store_true",
+                    help="run the 3D two-layer workload (257^3, N_f = 4, GMRES(15) cycle)")
     ap.add_argument("--no-clocks", action="store_true",
                     help="do not sample nvidia-smi (for runs under a profiler)")
     return ap.parse_args()
@@ -322,6 +331,147 @@ def fp32_leg(args, wl, f_dev, stream, n_t):
             "rel_residual_after_cycle": infos[-1][0]["rel_residual"]}
 
 
+def run_batched(args):
+    """Independent 2D problems (sizes 257^2..2049^2, N_f 1..16) solved concurrently: one
+    host thread and one stream per problem, each wave solve one CUDA-graph launch, blocking
+    depth and tile from the autotuner, FP32 wave solves with compensated filter sums.
+    Reports the per-problem solve times (p50, p99) and the aggregate stencil rate."""
+    import torch
+    import paper_2507_23613_gb300 as M
+    from paper_2507_23613_gb300 import _lib, build, inputs
+    torch.cuda.set_device(0)
+    build.build()
+    M._lib.load()
+    prec = _lib.PREC_FP32_BLOCKSUM
+    restart = 10
+    chosen, seed, mem = [], args.seed + 5000, 0.0
+    t_gen = time.perf_counter()
+    while len(chosen) < args.batch and seed < args.seed + 5000 + 50 * args.batch:
+        wl = inputs.batch_workload(seed)
+        seed += 1
+        try:
+            s = M.plan(M.make_problem(wl.n, wl.length, wl.omega, n_p=wl.n_p, cfl=wl.cfl,
+                                      precision=prec)[0])
+        except M.MfwhError:
+            continue                      # ill-conditioned filter system: draw again
+        need = wl.forcing.size * (148 + 8 * (restart - 10)) / 1e9
+        if mem + need > args.batch_mem_gb:
+            continue
+        mem += need
+        chosen.append((wl, s.n_t))
+    t_gen = time.perf_counter() - t_gen
+    t_tune = time.perf_counter()
+    tuned = [M.autotune(wl.n, wl.length, wl.omega, n_p=wl.n_p, cfl=wl.cfl, precision=prec)
+             for wl, _ in chosen]
+    t_tune = time.perf_counter() - t_tune
+    # smaller problems on higher-priority streams, so that they are not queued behind the
+    # long wave solves of the large ones
+    lo_pri, hi_pri = torch.cuda.Stream.priority_range()
+    streams = [torch.cuda.Stream(priority=hi_pri if wl.n[0] <= 512 else lo_pri)
+               for wl, _ in chosen]
+    solvers, xs = [], []
+    for (wl, _), (tb, shape, _), st in zip(chosen, tuned, streams):
+        s = M.Solver(wl.n, wl.length, wl.omega, torch.from_numpy(wl.forcing).cuda(),
+                     stream=st.cuda_stream, n_p=wl.n_p, cfl=wl.cfl, precision=prec,
+                     time_block=tb, tile_shape=shape)
+        s.set_graphs(True)
+        solvers.append(s)
+        xs.append(torch.zeros(wl.forcing.shape, dtype=torch.float64, device="cuda"))
+    # warm-up: one solve of one Arnoldi step each captures the graphs
+    M.solve_batch(solvers, xs, restart=1, tol=0.0, max_iters=1, raise_on_error=False)
+    for x in xs:
+        x.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, infos, secs = M.solve_batch(solvers, xs, restart=restart, tol=0.0,
+                                    max_iters=args.batch_iters, raise_on_error=False)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    pts = sum((wl.n[0] - 1) * (wl.n[1] - 1) * n_t * info["pi_applications"]
+              for (wl, n_t), info in zip(chosen, infos))
+    sizes = [wl.n[0] + 1 for wl, _ in chosen]
+    line = {"metric": "batched MFWH: per-problem GMRES solve time", "impl": "native",
+            "value": round(pts / wall / 1e9, 3), "unit": "Gpts/s (aggregate)",
+            "p50_s": round(float(np.percentile(secs, 50)), 3),
+            "p99_s": round(float(np.percentile(secs, 99)), 3),
+            "max_s": round(float(np.max(secs)), 3), "wall_s": round(wall, 3),
+            "n_gpus": 1, "dtype": "f32 wave steps / f64 Krylov", "data": "synthetic",
+            "config": {"workload": f"batch{len(chosen)}_2d_sizes257-2049_nf1-16_omega5-80",
+                       "problems": len(chosen),
+                       "size_counts": {str(k + 1): sizes.count(k + 1) for k in inputs.BATCH_SIZES},
+                       "nf": [wl.nf for wl, _ in chosen], "n_t": [n for _, n in chosen],
+                       "solver": f"GMRES({restart}), {args.batch_iters} Arnoldi steps per problem",
+                       "tuned": [list(t[:2]) for t in tuned], "device_gb": round(mem, 1)},
+            "status": st, "generate_s": round(t_gen, 1), "autotune_s": round(t_tune, 1)}
+    print(json.dumps(line), flush=True)
+    for s in solvers:
+        s.close()
+
+
+def run_cube(args):
+    """The 3D workload: 257^3 unit cube, 7-point Laplacian, c = 1.0 / 1.5 split at z = 0.5,
+    N_f = 4 frequencies in [8, 30], one GMRES(15) cycle from zero with FP64 and with FP32
+    wave solves (FP64 Arnoldi); Gpts/s, HBM fraction of the step kernel, and the FP32 map's
+    error against the FP64 map per frequency."""
+    import torch
+    import paper_2507_23613_gb300 as M
+    from paper_2507_23613_gb300 import _lib, build, inputs
+    torch.cuda.set_device(0)
+    build.build()
+    M._lib.load()
+    wl = inputs.cube_layered(args.seed + 1000)
+    lay = wl.layer
+    f = torch.from_numpy(wl.forcing).cuda()
+    stream = torch.cuda.Stream()
+    hbm_peak, peak_kind = peaks()
+    out = {"metric": "stencil Gpts/s (+N_f filters), 3D", "n_gpus": 1, "data": "synthetic",
+           "config": {"workload": f"cube{wl.n[0] + 1}_nf{wl.nf}_two_layer_gmres15_cycle",
+                      "grid": [k + 1 for k in wl.n], "nf": wl.nf,
+                      "omega": [round(float(o), 3) for o in wl.omega],
+                      "c": [lay["c_lo"], lay["c_hi"]], "interface_z": lay["interface"]}}
+    x = torch.from_numpy(np.random.default_rng(3).normal(size=wl.forcing.shape) * 0.01).cuda()
+    maps = {}
+    for name, prec in (("fp64", _lib.PREC_FP64), ("fp32", _lib.PREC_FP32_BLOCKSUM)):
+        s = M.Solver(wl.n, wl.length, wl.omega, f, stream=stream.cuda_stream, n_p=wl.n_p,
+                     cfl=wl.cfl, c_lo=lay["c_lo"], c_hi=lay["c_hi"], interface=lay["interface"],
+                     layer_axis=lay["axis"], precision=prec)
+        n_t = s.setup["n_t"]
+        v = torch.zeros_like(f)
+        s.solve_gmres(v, restart=15, tol=0.0, max_iters=1, raise_on_error=False)   # warm-up
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            v.zero_()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        info = s.solve_gmres(v, restart=15, tol=0.0, max_iters=15, raise_on_error=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        step_ms, step_launches, _ = s.last_timing()
+        apps = info["pi_applications"]
+        interior = (wl.n[0] - 1) * (wl.n[1] - 1) * (wl.n[2] - 1)
+        w = 8 if name == "fp64" else 4
+        # one-step kernels: read W^n, the previous level or D, the filter state; write them
+        per_pt = (3 + 2 * wl.nf) * w if name == "fp64" else (4 + 4 * wl.nf) * 4
+        gbs = interior * per_pt * step_launches / (step_ms * 1e-3) / 1e9
+        out[name] = {"value": round(interior * n_t * apps / (ms * 1e-3) / 1e9, 3),
+                     "unit": "Gpts/s", "ms_per_cycle": round(ms, 1), "n_t": n_t,
+                     "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak,
+                                  "unit": "GB/s", "frac": round(gbs / hbm_peak, 4),
+                                  "peak_source": peak_kind,
+                                  "kernel": "k_step<NF,3>" if name == "fp64" else "k_step32<NF,3>"}}
+        o = torch.empty_like(x)
+        with torch.cuda.stream(stream):
+            s.apply_Pi(x, o, forced=True)
+        torch.cuda.synchronize()
+        maps[name] = o.cpu().numpy().reshape(wl.nf, -1)
+        s.close()
+    a, b = maps["fp32"], maps["fp64"]
+    out["fp32"]["pi_rel_err_vs_fp64_per_freq"] = [
+        float(f"{e:.3e}") for e in np.max(np.abs(a - b), axis=1) / np.max(np.abs(b), axis=1)]
+    print(json.dumps(out), flush=True)
+
+
 def workload_config(wl, n_t):
     return {"workload": f"square{wl.n[0] + 1}x{wl.n[1] + 1}_nf{wl.nf}_np{wl.n_p}_gmres{RESTART}_cycle",
             "step": "one GMRES(20) cycle from zero: b = Pi(0), 20 Arnoldi steps, update, residual check",
@@ -336,6 +486,10 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.batched:
+        return run_batched(args) if rank == 0 else None
+    if args.cube:
+        return run_cube(args) if rank == 0 else None
 
     import torch
     import paper_2507_23613_gb300 as M

@@ -116,3 +116,21 @@ def cube_layered(seed=3000, n=256, nf=4):
                            lambda r: draw_frequencies(r, nf, 8.0, 30.0), 300.0, seed, c2=c2)
     wl.layer = {"c_lo": 1.0, "c_hi": 1.5, "interface": 0.5, "axis": 2}
     return wl
+
+
+BATCH_SIZES = (256, 512, 1024, 2048)
+
+
+def batch_workload(seed):
+    """One problem of the batched workload: a 2D unit square with a size drawn from
+    {257^2, 513^2, 1025^2, 2049^2}, N_f drawn in 1..16, frequencies uniform in [5, 80]
+    (adjacent gaps >= 1.5), 1-4 Gaussian sources per frequency with b uniform in
+    [200, 400], c = 1, CFL 0.5, N_p = 1."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = int(rng.choice(BATCH_SIZES))
+    nf = int(rng.integers(1, 17))
+    omega = draw_frequencies(rng, nf, 5.0, 80.0, min_gap=1.5)
+    b = float(rng.uniform(200.0, 400.0))
+    k = int(rng.integers(1, 5))
+    return gaussian_workload(f"batch{seed}_n{n + 1}_nf{nf}", (n, n), nf, omega, b,
+                             int(rng.integers(0, 2**31)), sources_per_freq=k)
