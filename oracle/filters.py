@@ -25,7 +25,7 @@ def adjusted_frequency(omega, dt, scheme=EXPLICIT):
     return np.arccos((1.0 - 0.5 * beta * x * x) / (1.0 + alpha * x * x)) / dt
 
 
-def explicit_time_step(h, c_max, cfl, omega1, n_p):
+def explicit_time_step(h, c_max, cfl, omega1, n_p, order=2):
     """Explicit time step and step count (Section "Time-step determination").
 
     Reading: the von Neumann limit of leapfrog with the second-order Laplacian
@@ -35,9 +35,15 @@ def explicit_time_step(h, c_max, cfl, omega1, n_p):
     the adjusted final time N_p 2 pi / omega~_1 equal to N_t dt.  With the
     explicit omega~ that condition reads 1 - (omega_1 dt)^2/2 = cos(2 pi N_p/N_t),
     i.e. dt = 2 sin(pi N_p / N_t) / omega_1.
+
+    For the fourth-order operator L_{4h} (order = 4) the spectral radius of -L_h is
+    c_max^2 sum_i (16/3)/h_i^2 instead of c_max^2 sum_i 4/h_i^2, and leapfrog needs
+    dt^2 rho(-L_h) <= 4, so dt_stab is smaller by the factor sqrt(3)/2.
     """
     h = np.atleast_1d(np.asarray(h, dtype=np.float64))
     dt_stab = 1.0 / (c_max * math.sqrt(float(np.sum(1.0 / (h * h)))))
+    if order == 4:
+        dt_stab *= math.sqrt(3.0) / 2.0
     t_final = n_p * 2.0 * math.pi / omega1
     n_t = max(2 * n_p + 1, int(math.ceil(t_final / (cfl * dt_stab))))
     dt = 2.0 * math.sin(math.pi * n_p / n_t) / omega1
@@ -299,7 +305,7 @@ class Setup:
 
 
 def make_setup(omega, h, c_max, cfl=0.5, n_p=1, filter_mode=FILTER_OPTIMIZED,
-               user_params=None, n_delta=20, c_delta=2.0):
+               user_params=None, n_delta=20, c_delta=2.0, order=2):
     """Set-up of Algorithm 1 (its first two lines) for the explicit scheme.
 
     Time step per explicit_time_step; omega~ per eq. omegaImplicit with
@@ -309,7 +315,7 @@ def make_setup(omega, h, c_max, cfl=0.5, n_p=1, filter_mode=FILTER_OPTIMIZED,
     (eq. origParamAdjust) or given; then w and B.
     """
     omega = np.asarray(omega, dtype=np.float64)
-    dt, n_t = explicit_time_step(h, c_max, cfl, float(omega[0]), n_p)
+    dt, n_t = explicit_time_step(h, c_max, cfl, float(omega[0]), n_p, order)
     omega_t = adjusted_frequency(omega, dt, EXPLICIT)
     n_pm, t_fm, _ = period_counts(omega_t, n_p)
     sigma = trapezoid_weights(n_t, dt, t_fm)

@@ -46,19 +46,37 @@ class Grid:
         return tuple(reversed(mesh))
 
 
-def laplacian(W, grid, c2):
-    """L_h W = c^2 Delta_h W at interior points (second-order central differences,
-    the p = 2 case of L_{ph}); zero on the boundary.  c2 is a scalar or a grid array."""
+def laplacian(W, grid, c2, order=2):
+    """L_{ph} W = c^2 Delta_h W at interior points; zero on the boundary.  c2 is a scalar or
+    a grid array.
+
+    order = 2: second-order central differences, (W_{j-1} - 2 W_j + W_{j+1}) / h^2 per axis.
+    order = 4: fourth-order central differences,
+        (-W_{j-2} + 16 W_{j-1} - 30 W_j + 16 W_{j+1} - W_{j+2}) / (12 h^2) per axis,
+    the p = 4 case of L_{ph} (Section "Discretizing the wave equation and filter").  At the
+    points next to the boundary the stencil reaches one ghost point, whose value is the odd
+    reflection W_{-1} = -W_1 (and W_{N+1} = -W_{N-1}) of homogeneous Dirichlet data.
+    """
     out = np.zeros_like(W)
     inner = grid.interior()
+    if order == 4:
+        Wp = np.pad(W, 1, mode="reflect", reflect_type="odd")   # 2 W_0 - W_1 = -W_1
+        core = tuple(slice(2, -2) for _ in range(grid.dim))
     acc = np.zeros_like(W[inner])
     for axis_x, h in enumerate(grid.h):          # axis_x = 0 is x, the last array axis
         ax = grid.dim - 1 - axis_x
-        plus = [slice(1, -1)] * grid.dim
-        minus = [slice(1, -1)] * grid.dim
-        plus[ax] = slice(2, None)
-        minus[ax] = slice(0, -2)
-        acc += (W[tuple(plus)] - 2.0 * W[inner] + W[tuple(minus)]) / (h * h)
+        if order == 4:
+            def sh(k):
+                sl = list(core)
+                sl[ax] = slice(2 + k, Wp.shape[ax] - 2 + k)
+                return Wp[tuple(sl)]
+            acc += (-sh(-2) + 16.0 * sh(-1) - 30.0 * sh(0) + 16.0 * sh(1) - sh(2)) / (12.0 * h * h)
+        else:
+            plus = [slice(1, -1)] * grid.dim
+            minus = [slice(1, -1)] * grid.dim
+            plus[ax] = slice(2, None)
+            minus[ax] = slice(0, -2)
+            acc += (W[tuple(plus)] - 2.0 * W[inner] + W[tuple(minus)]) / (h * h)
     c2 = c2 if np.isscalar(c2) else c2[inner]
     out[inner] = c2 * acc
     return out
@@ -70,6 +88,7 @@ class Problem:
     forcing: np.ndarray          # (N_f, *grid.shape), f^{(m)} at the grid points
     c2: object                   # scalar or grid array of c^2
     setup: filters.Setup = field(repr=False)
+    order: int = 2               # order p of L_{ph}: 2 or 4
 
     @property
     def nf(self):
@@ -78,11 +97,11 @@ class Problem:
 
 def make_problem(grid, omega, forcing, c2=1.0, cfl=0.5, n_p=1,
                  filter_mode=filters.FILTER_OPTIMIZED, user_params=None,
-                 n_delta=20, c_delta=2.0):
+                 n_delta=20, c_delta=2.0, order=2):
     c_max = math.sqrt(float(np.max(c2)))
     setup = filters.make_setup(omega, grid.h, c_max, cfl, n_p, filter_mode,
-                               user_params, n_delta, c_delta)
-    return Problem(grid, np.asarray(forcing, dtype=np.float64), c2, setup)
+                               user_params, n_delta, c_delta, order)
+    return Problem(grid, np.asarray(forcing, dtype=np.float64), c2, setup, order)
 
 
 def composite_forcing(prob, n):
@@ -122,7 +141,7 @@ def apply_Pi(prob, V, forced=True):
         q[m] += s.w[0, m] * W0
 
     W1 = np.zeros_like(W0)
-    W1[inner] = (W0 + 0.5 * dt2 * (laplacian(W0, g, prob.c2) - F(0)))[inner]
+    W1[inner] = (W0 + 0.5 * dt2 * (laplacian(W0, g, prob.c2, prob.order) - F(0)))[inner]
     for m in range(prob.nf):
         q[m] += s.w[1, m] * W1
 
@@ -130,7 +149,7 @@ def apply_Pi(prob, V, forced=True):
     for n in range(1, s.n_t):
         W_next = np.zeros_like(W_cur)
         W_next[inner] = (2.0 * W_cur - W_prev
-                         + dt2 * (laplacian(W_cur, g, prob.c2) - F(n)))[inner]
+                         + dt2 * (laplacian(W_cur, g, prob.c2, prob.order) - F(n)))[inner]
         for m in range(prob.nf):
             q[m] += s.w[n + 1, m] * W_next
         W_prev, W_cur = W_cur, W_next
@@ -244,7 +263,7 @@ def helmholtz_residual(prob, V):
     inner = prob.grid.interior()
     out = np.zeros(prob.nf)
     for m in range(prob.nf):
-        Hv = laplacian(V[m], prob.grid, prob.c2) + prob.setup.omega[m] ** 2 * V[m]
+        Hv = laplacian(V[m], prob.grid, prob.c2, prob.order) + prob.setup.omega[m] ** 2 * V[m]
         num = np.max(np.abs(prob.forcing[m][inner] - Hv[inner]))
         den = np.max(np.abs(prob.forcing[m][inner]))
         out[m] = num / den
@@ -255,11 +274,24 @@ def helmholtz_residual(prob, V):
 # References used by the pins: sparse direct solve and the Dirichlet spectrum
 # ---------------------------------------------------------------------------
 
-def laplacian_matrix(grid, c2):
-    """Sparse L_h on interior unknowns (x fastest), Dirichlet zero boundary."""
+def laplacian_matrix(grid, c2, order=2):
+    """Sparse L_{ph} on interior unknowns (x fastest), Dirichlet zero boundary; for order 4
+    the ghost value -W_1 folds into the first and last rows (-W_{-1} = +W_1)."""
     mats = []
     for n, h in zip(grid.n, grid.h):
         k = n - 1
+        if order == 4:
+            main = -30.0 * np.ones(k)
+            main[0] += 1.0
+            main[-1] += 1.0
+            off1 = 16.0 * np.ones(k - 1)
+            off2 = -np.ones(max(k - 2, 0))
+            diags = [off2, off1, main, off1, off2] if k > 2 else [off1, main, off1]
+            offs = [-2, -1, 0, 1, 2] if k > 2 else [-1, 0, 1]
+            if k == 1:
+                diags, offs = [main], [0]
+            mats.append(sp.diags(diags, offs, shape=(k, k)) / (12.0 * h * h))
+            continue
         main = -2.0 * np.ones(k)
         off = np.ones(k - 1)
         mats.append(sp.diags([off, main, off], [-1, 0, 1], shape=(k, k)) / (h * h))
@@ -278,7 +310,7 @@ def laplacian_matrix(grid, c2):
 
 def helmholtz_direct(prob):
     """U_m solving L_h U + omega_m^2 U = f_m at interior points (eq. discreteHelmholtz), U = 0 on the boundary."""
-    L = laplacian_matrix(prob.grid, prob.c2).tocsc()
+    L = laplacian_matrix(prob.grid, prob.c2, prob.order).tocsc()
     inner = prob.grid.interior()
     I = sp.identity(L.shape[0], format="csc")
     U = np.zeros_like(prob.forcing)
@@ -289,14 +321,20 @@ def helmholtz_direct(prob):
     return U
 
 
-def dirichlet_mode(grid, k):
+def dirichlet_mode(grid, k, order=2):
     """Discrete Dirichlet eigenfunction prod_i sin(k_i pi x_i / L_i) and its eigenvalue
-    lambda^2 = sum_i (4/h_i^2) sin^2(k_i pi / (2 n_i)) of -Delta_h (k listed x first)."""
+    lambda^2 of -Delta_h (k listed x first): sum_i (4/h_i^2) sin^2(theta_i/2) for order 2 and
+    sum_i (30 - 32 cos theta_i + 2 cos 2 theta_i) / (12 h_i^2) for order 4, theta_i = k_i pi / n_i
+    (the sine modes satisfy the odd-reflection ghost values exactly)."""
     xs = grid.coords()
     phi = np.ones(grid.shape)
     lam2 = 0.0
     for x, kk, L, n, h in zip(xs, k, grid.length, grid.n, grid.h):
         phi = phi * np.sin(kk * math.pi * x / L)
-        lam2 += 4.0 / (h * h) * math.sin(kk * math.pi / (2 * n)) ** 2
+        th = kk * math.pi / n
+        if order == 4:
+            lam2 += (30.0 - 32.0 * math.cos(th) + 2.0 * math.cos(2.0 * th)) / (12.0 * h * h)
+        else:
+            lam2 += 4.0 / (h * h) * math.sin(th / 2.0) ** 2
     zero_boundary(phi, grid)
     return phi, lam2
