@@ -127,9 +127,9 @@ def test_closed_form_catches_dropped_half_in_first_step(monkeypatch):
     orig = W.laplacian
     calls = {"n": 0}
 
-    def doubled_first(Wg, grid, c2):       # doubles L_h only on its first call (the W^1 update)
+    def doubled_first(Wg, grid, c2, order=2):   # doubles L_h only on its first call (W^1)
         calls["n"] += 1
-        return orig(Wg, grid, c2) * (2.0 if calls["n"] == 1 else 1.0)
+        return orig(Wg, grid, c2, order) * (2.0 if calls["n"] == 1 else 1.0)
 
     monkeypatch.setattr(W, "laplacian", doubled_first)
     bad = W.apply_Pi(p, v[:, None, None] * phi)
