@@ -88,6 +88,12 @@ typedef struct {
                                 FP64; 8 for FP32 in 2D), 1 = one step per kernel launch,
                                 4 or 8 (or 16 for FP32) = temporal blocking with that depth
                                 (2D grids only).  Results are bit-identical for every depth. */
+  int order;                 /* order p of the spatial operator L_{ph}: 2 (0 means 2) or 4.
+                                Order 4: (-W_{j-2} + 16 W_{j-1} - 30 W_j + 16 W_{j+1} - W_{j+2})
+                                / (12 h^2) per axis, ghost values W_{-1} = -W_1 and
+                                W_{N+1} = -W_{N-1} (odd reflection of homogeneous Dirichlet data),
+                                time step limit sqrt(3)/2 of the second-order one, one step
+                                per kernel launch (time_block 0 or 1) */
   int tile_shape;            /* FP32 blocked kernel tile: 0 = 32x32, 512 threads (default);
                                 1 = 32x64, 512 threads; 2 = 64x64, 1024 threads (halved in
                                 y above 8 frequencies) */

@@ -54,6 +54,7 @@ class Problem(C.Structure):
         ("c_delta", C.c_double),
         ("precision", C.c_int),
         ("time_block", C.c_int),
+        ("order", C.c_int),
         ("tile_shape", C.c_int),
     ]
 

@@ -145,14 +145,28 @@ mfwh_status collect_timing(mfwh_handle_t h) {
 
 void layer_coef(const mfwh_handle_t h, double c2, double a_cur, double kappa, LayerCoef* L) {
   const double k = kappa * c2;
+  if (h->plan.order == 4) {
+    const double s = k * (h->inv_h2[0] + h->inv_h2[1] + h->inv_h2[2]);
+    L->Ax = (4.0 / 3.0) * k * h->inv_h2[0];
+    L->Ay = (4.0 / 3.0) * k * h->inv_h2[1];
+    L->Az = (4.0 / 3.0) * k * h->inv_h2[2];
+    L->Bx = -k * h->inv_h2[0] / 12.0;
+    L->By = -k * h->inv_h2[1] / 12.0;
+    L->Bz = -k * h->inv_h2[2] / 12.0;
+    L->A0 = a_cur - 2.5 * s;
+    return;
+  }
   L->Ax = k * h->inv_h2[0];
   L->Ay = k * h->inv_h2[1];
   L->Az = k * h->inv_h2[2];
+  L->Bx = L->By = L->Bz = 0.0;
   L->A0 = a_cur - 2.0 * (L->Ax + L->Ay + L->Az);
 }
 
+// FP32 increment coefficients: kappa c^2 / h_i^2, divided by 12 for the fourth-order
+// operator (whose kernels form 16 d1 - d2 from first and second neighbour differences).
 void layer_coef32(const mfwh_handle_t h, double c2, double kappa, Coef32* L) {
-  const double k = kappa * c2;
+  const double k = kappa * c2 / (h->plan.order == 4 ? 12.0 : 1.0);
   L->Ax = (float)(k * h->inv_h2[0]);
   L->Ay = (float)(k * h->inv_h2[1]);
   L->Az = (float)(k * h->inv_h2[2]);
@@ -675,6 +689,7 @@ mfwh_status mfwh_create(const mfwh_problem* prob, void* stream, mfwh_handle_t* o
   g.dim = P.dim;
   g.layer_axis = P.layer_axis;
   g.layer_split = P.layer_split;
+  g.order = P.order;
 
   auto cleanup = [&](mfwh_status s) {
     mfwh_destroy(h);
@@ -1106,7 +1121,7 @@ mfwh_status mfwh_autotune(const mfwh_problem* prob, void* stream, int* time_bloc
     }
   }
   std::vector<std::pair<int, int>> cand;
-  if (P.dim == 3) {
+  if (P.dim == 3 || P.order == 4) {
     cand = {{1, 0}};
   } else if (P.precision == MFWH_PREC_FP64) {
     cand = {{1, 0}, {4, 0}, {8, 0}};

@@ -24,6 +24,7 @@ struct Plan {
   int time_block = 1;          // steps per wave-kernel launch (1, 4, 8 or 16)
   int tile_shape = 0;          // FP32 blocked-kernel tile shape
   int precision = MFWH_PREC_FP64;
+  int order = 2;               // order of L_{ph}: 2 or 4
   int64_t n[3] = {1, 1, 1};
   std::vector<double> w;       // [(n_t + 1) * nf]  filter weights w_{n,m}
   std::vector<double> cosf;    // [(n_t + 1) * nf]  cos(omega~_m t^n)

@@ -18,6 +18,7 @@ struct Geom {
   int dim;                   // 2 or 3
   int layer_axis;            // axis whose index selects the c^2 layer
   int64_t layer_split;       // indices >= layer_split use the upper-layer coefficients
+  int order;                 // order of L_{ph}: 2 or 4 (0 reads as 2)
 };
 
 // Leapfrog update at one point, written as
@@ -26,8 +27,12 @@ struct Geom {
 // with A0 = a_cur - 2 kappa c^2 sum_i 1/h_i^2, A_i = kappa c^2 / h_i^2,
 // (a_cur, a_prev, kappa) = (2, -1, dt^2) for a regular step (eq. WaveSchemeA) and
 // (1, 0, dt^2/2) for the first step (eq. implicitFirstStep with alpha = 0).
+// Fourth order adds the second neighbours: + Bx (W_ee + W_ww) + By (...) + Bz (...), with
+// A_i = (4/3) kappa c^2 / h_i^2, B_i = -kappa c^2 / (12 h_i^2), A0 = a_cur - (5/2) kappa c^2
+// sum_i 1/h_i^2; a ghost value beyond the boundary is minus the point next to it.
 struct LayerCoef {
   double A0, Ax, Ay, Az;
+  double Bx, By, Bz;
 };
 
 struct StepHost {

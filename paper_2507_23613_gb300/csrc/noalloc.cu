@@ -97,6 +97,7 @@ extern "C" mfwh_status mfwh_residual_noalloc(const mfwh_problem* p, const double
   g.sz = (g.nx + 1) * (g.ny + 1);
   g.points = g.sz * (p->dim == 3 ? g.nz + 1 : 1);
   g.dim = p->dim;
+  g.order = p->order == 4 ? 4 : 2;
   if (!(p->c_lo > 0.0)) return bad("mfwh_residual_noalloc: c_lo must be > 0");
   double c2_lo = p->c_lo * p->c_lo, c2_hi = c2_lo;
   g.layer_axis = 0;

@@ -311,6 +311,10 @@ mfwh_status plan_problem(const mfwh_problem* p, Plan* out) {
     return fail(MFWH_ERR_INVALID_ARG, "time_block must be 0, 1, 4 or 8 (or 16 for FP32)");
   if (p->tile_shape < 0 || p->tile_shape > 2)
     return fail(MFWH_ERR_INVALID_ARG, "tile_shape must be 0, 1 or 2");
+  if (p->order != 0 && p->order != 2 && p->order != 4)
+    return fail(MFWH_ERR_INVALID_ARG, "order must be 2 or 4");
+  if (p->order == 4 && p->time_block > 1)
+    return fail(MFWH_ERR_INVALID_ARG, "the fourth-order operator takes one step per launch");
   if (p->dim == 3 && p->time_block > 1)
     return fail(MFWH_ERR_INVALID_ARG, "temporal blocking is available for 2D grids only");
 
@@ -323,8 +327,10 @@ mfwh_status plan_problem(const mfwh_problem* p, Plan* out) {
   // FP64 default: one step per launch.  On GB300 the FP64 step is bound by the FP64 pipe
   // (about 1.2 TFLOP/s), so blocking saves HBM bytes it is not waiting for and adds halo work.
   // FP32 default: 8 steps per launch in 2D (fastest measured depth on GB300).
-  P.time_block = p->time_block != 0 ? p->time_block : (fp32 && p->dim == 2 ? 8 : 1);
+  P.time_block = p->time_block != 0 ? p->time_block
+                                     : (fp32 && p->dim == 2 && p->order != 4 ? 8 : 1);
   P.tile_shape = p->tile_shape;
+  P.order = p->order == 4 ? 4 : 2;
   P.precision = p->precision;
   double inv_h2 = 0.0;
   s.points = 1;
@@ -359,7 +365,9 @@ mfwh_status plan_problem(const mfwh_problem* p, Plan* out) {
   }
 
   // Time step (explicit leapfrog; Section "Time-step determination").
-  const double dt_stab = 1.0 / (P.c_max * std::sqrt(inv_h2));
+  // Leapfrog needs dt^2 rho(-L_h) <= 4; rho = c_max^2 sum_i 4/h_i^2 for the second-order
+  // operator and c_max^2 sum_i (16/3)/h_i^2 for the fourth-order one.
+  const double dt_stab = (P.order == 4 ? std::sqrt(3.0) / 2.0 : 1.0) / (P.c_max * std::sqrt(inv_h2));
   const double t1 = p->n_p * 2.0 * kPi / p->omega[0];
   double nt_real = std::ceil(t1 / (p->cfl * dt_stab));
   if (nt_real > 5e7) return fail(MFWH_ERR_INVALID_ARG, "too many time steps");

@@ -73,7 +73,9 @@ __device__ __forceinline__ PointIndex point_index(const Geom& g) {
 }
 
 // New wave level at an interior point (the leapfrog update with the composite forcing).
-template <int NF, int DIM>
+// ORDER 4 adds the second neighbours along each axis; beyond the boundary the ghost value is
+// minus the centre point (odd reflection of homogeneous Dirichlet data).
+template <int NF, int DIM, int ORDER>
 __device__ __forceinline__ double leapfrog_point(const double* __restrict__ Wc,
                                                  const double* __restrict__ Wp,
                                                  const double* __restrict__ f,
@@ -95,6 +97,19 @@ __device__ __forceinline__ double leapfrog_point(const double* __restrict__ Wc,
     const double Az = up ? a.hi.Az : a.lo.Az;
     const double sz = Wc[p - g.sz] + Wc[p + g.sz];
     acc = fma(Az, sz, acc);
+  }
+  if (ORDER == 4) {
+    const double Bx = up ? a.hi.Bx : a.lo.Bx;
+    const double By = up ? a.hi.By : a.lo.By;
+    const double tx = (x.i == 1 ? -wc : Wc[p - 2]) + (x.i == g.nx - 1 ? -wc : Wc[p + 2]);
+    const double ty = (x.j == 1 ? -wc : Wc[p - 2 * g.sy]) + (x.j == g.ny - 1 ? -wc : Wc[p + 2 * g.sy]);
+    acc = fma(Bx, tx, acc);
+    acc = fma(By, ty, acc);
+    if (DIM == 3) {
+      const double Bz = up ? a.hi.Bz : a.lo.Bz;
+      const double tz = (x.k == 1 ? -wc : Wc[p - 2 * g.sz]) + (x.k == g.nz - 1 ? -wc : Wc[p + 2 * g.sz]);
+      acc = fma(Bz, tz, acc);
+    }
   }
   if (a.forced) {
 #pragma unroll
@@ -119,13 +134,13 @@ k_init(const double* __restrict__ v, double* __restrict__ W0, double* __restrict
   for (int m = 0; m < NF; ++m) q[m * g.points + x.p] = a.w0[m] * w;
 }
 
-template <int NF, int DIM>
+template <int NF, int DIM, int ORDER>
 __global__ void __launch_bounds__(kBX * kBY)
 k_step(const double* __restrict__ Wc, double* __restrict__ Wp, const double* __restrict__ f,
        double* __restrict__ q, const StepParams<NF> a, const Geom g) {
   const PointIndex x = point_index<DIM>(g);
   if (!x.interior) return;           // boundary values stay 0 (Dirichlet, g = 0)
-  const double wn = leapfrog_point<NF, DIM>(Wc, Wp, f, a, g, x);
+  const double wn = leapfrog_point<NF, DIM, ORDER>(Wc, Wp, f, a, g, x);
   Wp[x.p] = wn;
 #pragma unroll
   for (int m = 0; m < NF; ++m) {
@@ -134,7 +149,7 @@ k_step(const double* __restrict__ Wc, double* __restrict__ Wp, const double* __r
   }
 }
 
-template <int NF, int DIM>
+template <int NF, int DIM, int ORDER>
 __global__ void __launch_bounds__(kBX * kBY)
 k_last(const double* __restrict__ Wc, const double* __restrict__ Wp, const double* __restrict__ f,
        const double* __restrict__ q, double* vout, const double* vsub, const LastParams<NF> a,
@@ -146,7 +161,7 @@ k_last(const double* __restrict__ Wc, const double* __restrict__ Wp, const doubl
     for (int m = 0; m < NF; ++m) vout[m * g.points + x.p] = 0.0;
     return;
   }
-  const double wn = leapfrog_point<NF, DIM>(Wc, Wp, f, a.st, g, x);
+  const double wn = leapfrog_point<NF, DIM, ORDER>(Wc, Wp, f, a.st, g, x);
   double qq[NF];
 #pragma unroll
   for (int m = 0; m < NF; ++m) qq[m] = fma(a.st.wq[m], wn, q[m * g.points + x.p]);
@@ -169,6 +184,15 @@ constexpr int kResBlocks = 4 * 152;
 __device__ __forceinline__ double nanmax(double a, double b) {
   // max that propagates NaN so that non-finite iterates are reported
   return (b > a || b != b) ? b : a;
+}
+
+// h^2 times the fourth-order second difference along one axis at index idx of n cells
+// (ghost values beyond the boundary are minus the centre value vc).
+__device__ __forceinline__ double diff4(const double* vm, int64_t p, int64_t s, int64_t idx,
+                                        int64_t n, double vc) {
+  const double m2 = idx == 1 ? -vc : vm[p - 2 * s];
+  const double p2 = idx == n - 1 ? -vc : vm[p + 2 * s];
+  return (16.0 * (vm[p - s] + vm[p + s]) - (m2 + p2) - 30.0 * vc) / 12.0;
 }
 
 template <int NF>
@@ -200,9 +224,15 @@ k_residual(const double* __restrict__ v, const double* __restrict__ f, const Res
     for (int m = 0; m < NF; ++m) {
       const double* vm = v + m * g.points;
       const double vc = vm[p];
-      double lap = a.ihx2 * (vm[p - 1] - 2.0 * vc + vm[p + 1]) +
-                   a.ihy2 * (vm[p - g.sy] - 2.0 * vc + vm[p + g.sy]);
-      if (DIM == 3) lap += a.ihz2 * (vm[p - g.sz] - 2.0 * vc + vm[p + g.sz]);
+      double lap;
+      if (g.order == 4) {
+        lap = a.ihx2 * diff4(vm, p, 1, i, g.nx, vc) + a.ihy2 * diff4(vm, p, g.sy, j, g.ny, vc);
+        if (DIM == 3) lap += a.ihz2 * diff4(vm, p, g.sz, k, g.nz, vc);
+      } else {
+        lap = a.ihx2 * (vm[p - 1] - 2.0 * vc + vm[p + 1]) +
+              a.ihy2 * (vm[p - g.sy] - 2.0 * vc + vm[p + g.sy]);
+        if (DIM == 3) lap += a.ihz2 * (vm[p - g.sz] - 2.0 * vc + vm[p + g.sz]);
+      }
       const double fm = f[m * g.points + p];
       const double r = fm - (c2 * lap + a.omega2[m] * vc);
       rmax[m] = nanmax(rmax[m], fabs(r));
@@ -263,10 +293,16 @@ void step_nf(const Geom& g, const double* Wc, double* Wp, const double* f, doubl
              const StepHost& h, cudaStream_t st) {
   const StepParams<NF> a = to_params<NF>(h);
   dim3 blk(kBX, kBY);
-  if (g.dim == 2)
-    k_step<NF, 2><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, q, a, g);
-  else
-    k_step<NF, 3><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, q, a, g);
+  if (g.order == 4) {
+    if (g.dim == 2)
+      k_step<NF, 2, 4><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, q, a, g);
+    else
+      k_step<NF, 3, 4><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, q, a, g);
+  } else if (g.dim == 2) {
+    k_step<NF, 2, 2><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, q, a, g);
+  } else {
+    k_step<NF, 3, 2><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, q, a, g);
+  }
 }
 
 template <int NF>
@@ -278,10 +314,16 @@ void last_nf(const Geom& g, const double* Wc, const double* Wp, const double* f,
     for (int j = 0; j < NF; ++j) a.binv[m * NF + j] = h.binv[m * MFWH_MAX_NF + j];
   a.subtract = h.subtract;
   dim3 blk(kBX, kBY);
-  if (g.dim == 2)
-    k_last<NF, 2><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, q, vout, vsub, a, g);
-  else
-    k_last<NF, 3><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, q, vout, vsub, a, g);
+  if (g.order == 4) {
+    if (g.dim == 2)
+      k_last<NF, 2, 4><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, q, vout, vsub, a, g);
+    else
+      k_last<NF, 3, 4><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, q, vout, vsub, a, g);
+  } else if (g.dim == 2) {
+    k_last<NF, 2, 2><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, q, vout, vsub, a, g);
+  } else {
+    k_last<NF, 3, 2><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, q, vout, vsub, a, g);
+  }
 }
 
 // R_m = f_m - (c^2 Delta_h + omega_m^2) v_m at interior points, 0 on the boundary: the
@@ -304,9 +346,15 @@ k_residual_field(const double* __restrict__ v, const double* __restrict__ f,
   for (int m = 0; m < NF; ++m) {
     const double* vm = v + m * g.points;
     const double c = vm[p];
-    double lap = a.ihx2 * ((vm[p - 1] - c) + (vm[p + 1] - c)) +
-                 a.ihy2 * ((vm[p - g.sy] - c) + (vm[p + g.sy] - c));
-    if (DIM == 3) lap += a.ihz2 * ((vm[p - g.sz] - c) + (vm[p + g.sz] - c));
+    double lap;
+    if (g.order == 4) {
+      lap = a.ihx2 * diff4(vm, p, 1, x.i, g.nx, c) + a.ihy2 * diff4(vm, p, g.sy, x.j, g.ny, c);
+      if (DIM == 3) lap += a.ihz2 * diff4(vm, p, g.sz, x.k, g.nz, c);
+    } else {
+      lap = a.ihx2 * ((vm[p - 1] - c) + (vm[p + 1] - c)) +
+            a.ihy2 * ((vm[p - g.sy] - c) + (vm[p + g.sy] - c));
+      if (DIM == 3) lap += a.ihz2 * ((vm[p - g.sz] - c) + (vm[p + g.sz] - c));
+    }
     R[m * g.points + p] = f[m * g.points + p] - (c2 * lap + a.omega2[m] * c);
   }
 }

@@ -20,7 +20,7 @@
 //  * k_tb2d32: 2D, T steps per launch on a 32 x (TY K) tile with a T-point halo in
 //    shared memory (the tile plus a ring of radius T-1-s updated at step s), the
 //    Kahan pairs of the tile's points in registers for all T steps;
-//  * k_step32 / k_last32: one step per launch, 2D or 3D.
+//  * k_step32 / k_last32: one step per launch, 2D or 3D, second- or fourth-order L_h.
 // Both perform the same FP32 operations per point in the same order, so their
 // results are bit-identical.
 #pragma once
@@ -107,7 +107,17 @@ __device__ __forceinline__ bool index_of(const Geom& g, int64_t& i, int64_t& j, 
   return inside;
 }
 
-template <int NF, int DIM>
+// Fourth-order combination 16 d1 - d2 along one axis at index idx of n cells, from the
+// first-neighbour difference sum d1 and the second neighbours (ghost values beyond the
+// boundary are minus the centre value, so their difference is -2w).
+__device__ __forceinline__ float comb4(const float* W, int64_t p, int64_t s, int64_t idx,
+                                       int64_t n, float w, float d1) {
+  const float dm = idx == 1 ? -2.0f * w : W[p - 2 * s] - w;
+  const float dp = idx == n - 1 ? -2.0f * w : W[p + 2 * s] - w;
+  return fmaf(16.0f, d1, -(dm + dp));
+}
+
+template <int NF, int DIM, int ORDER>
 __device__ __forceinline__ void step_point(const float* __restrict__ W, const float* D,
                                            const float* __restrict__ f, const Step32Args<NF>& a,
                                            const Geom& g, int64_t i, int64_t j, int64_t k,
@@ -115,9 +125,14 @@ __device__ __forceinline__ void step_point(const float* __restrict__ W, const fl
   const int64_t li = g.layer_axis == 0 ? i : (g.layer_axis == 1 ? j : k);
   const Coef32& L = li >= g.layer_split ? a.hi : a.lo;
   const float w = W[p];
-  const float dxx = (W[p - 1] - w) + (W[p + 1] - w);
-  const float dyy = (W[p - g.sy] - w) + (W[p + g.sy] - w);
-  const float dzz = DIM == 3 ? (W[p - g.sz] - w) + (W[p + g.sz] - w) : 0.0f;
+  float dxx = (W[p - 1] - w) + (W[p + 1] - w);
+  float dyy = (W[p - g.sy] - w) + (W[p + g.sy] - w);
+  float dzz = DIM == 3 ? (W[p - g.sz] - w) + (W[p + g.sz] - w) : 0.0f;
+  if (ORDER == 4) {
+    dxx = comb4(W, p, 1, i, g.nx, w, dxx);
+    dyy = comb4(W, p, g.sy, j, g.ny, w, dyy);
+    if (DIM == 3) dzz = comb4(W, p, g.sz, k, g.nz, w, dzz);
+  }
   const float inc = increment<NF, DIM>(L, dxx, dyy, dzz, a.fc, f, p, g.points, a.forced);
   dn = (D ? D[p] : 0.0f) + inc;
   wn = w + dn;
@@ -125,7 +140,7 @@ __device__ __forceinline__ void step_point(const float* __restrict__ W, const fl
 
 // W_out = W + D', D' = D + increment (D_out may alias D_in; W_out must not alias W_in);
 // Kahan sums updated in place.
-template <int NF, int DIM>
+template <int NF, int DIM, int ORDER>
 __global__ void __launch_bounds__(kBX * kBY)
 k_step32(const float* __restrict__ W, const float* D_in, float* __restrict__ W_out, float* D_out,
          const float* __restrict__ f, float* __restrict__ qs, float* __restrict__ qc,
@@ -135,7 +150,7 @@ k_step32(const float* __restrict__ W, const float* D_in, float* __restrict__ W_o
   index_of<DIM>(g, i, j, k, p, interior);
   if (!interior) return;
   float wn, dn;
-  step_point<NF, DIM>(W, D_in, f, a, g, i, j, k, p, wn, dn);
+  step_point<NF, DIM, ORDER>(W, D_in, f, a, g, i, j, k, p, wn, dn);
   W_out[p] = wn;
   D_out[p] = dn;
 #pragma unroll
@@ -165,7 +180,7 @@ __device__ __forceinline__ void filter_solve_out(const float* s, const float* c,
   }
 }
 
-template <int NF, int DIM>
+template <int NF, int DIM, int ORDER>
 __global__ void __launch_bounds__(kBX * kBY)
 k_last32(const float* __restrict__ W, const float* __restrict__ D, const float* __restrict__ f,
          const float* __restrict__ qs, const float* __restrict__ qc, double* vout,
@@ -179,7 +194,7 @@ k_last32(const float* __restrict__ W, const float* __restrict__ D, const float* 
   for (int m = 0; m < NF; ++m) s[m] = c[m] = 0.0f;
   if (interior) {
     float wn, dn;
-    step_point<NF, DIM>(W, D, f, a, g, i, j, k, p, wn, dn);
+    step_point<NF, DIM, ORDER>(W, D, f, a, g, i, j, k, p, wn, dn);
 #pragma unroll
     for (int m = 0; m < NF; ++m) {
       s[m] = qs[m * g.points + p];
@@ -509,10 +524,17 @@ template <int NF>
 void step32_nf(const Geom& g, const float* W, const float* D_in, float* W_out, float* D_out,
                const float* f, float* qs, float* qc, const Step32Host& h, cudaStream_t st) {
   const Step32Args<NF> a = step_args<NF>(h);
-  if (g.dim == 3)
-    k_step32<NF, 3><<<grid_of(g), dim3(kBX, kBY), 0, st>>>(W, D_in, W_out, D_out, f, qs, qc, a, g);
-  else
-    k_step32<NF, 2><<<grid_of(g), dim3(kBX, kBY), 0, st>>>(W, D_in, W_out, D_out, f, qs, qc, a, g);
+  const dim3 grid = grid_of(g), blk(kBX, kBY);
+  if (g.order == 4) {
+    if (g.dim == 3)
+      k_step32<NF, 3, 4><<<grid, blk, 0, st>>>(W, D_in, W_out, D_out, f, qs, qc, a, g);
+    else
+      k_step32<NF, 2, 4><<<grid, blk, 0, st>>>(W, D_in, W_out, D_out, f, qs, qc, a, g);
+  } else if (g.dim == 3) {
+    k_step32<NF, 3, 2><<<grid, blk, 0, st>>>(W, D_in, W_out, D_out, f, qs, qc, a, g);
+  } else {
+    k_step32<NF, 2, 2><<<grid, blk, 0, st>>>(W, D_in, W_out, D_out, f, qs, qc, a, g);
+  }
 }
 
 template <int NF>
@@ -522,10 +544,17 @@ void last32_nf(const Geom& g, const float* W, const float* D, const float* f, co
   const Step32Args<NF> a = step_args<NF>(h);
   const Last32Binv<NF> b = binv_args<NF>(binv);
   const int sub = vsub != nullptr;
-  if (g.dim == 3)
-    k_last32<NF, 3><<<grid_of(g), dim3(kBX, kBY), 0, st>>>(W, D, f, qs, qc, vout, vsub, a, b, sub, g);
-  else
-    k_last32<NF, 2><<<grid_of(g), dim3(kBX, kBY), 0, st>>>(W, D, f, qs, qc, vout, vsub, a, b, sub, g);
+  const dim3 grid = grid_of(g), blk(kBX, kBY);
+  if (g.order == 4) {
+    if (g.dim == 3)
+      k_last32<NF, 3, 4><<<grid, blk, 0, st>>>(W, D, f, qs, qc, vout, vsub, a, b, sub, g);
+    else
+      k_last32<NF, 2, 4><<<grid, blk, 0, st>>>(W, D, f, qs, qc, vout, vsub, a, b, sub, g);
+  } else if (g.dim == 3) {
+    k_last32<NF, 3, 2><<<grid, blk, 0, st>>>(W, D, f, qs, qc, vout, vsub, a, b, sub, g);
+  } else {
+    k_last32<NF, 2, 2><<<grid, blk, 0, st>>>(W, D, f, qs, qc, vout, vsub, a, b, sub, g);
+  }
 }
 
 template <int NF>

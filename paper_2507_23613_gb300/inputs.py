@@ -134,3 +134,17 @@ def batch_workload(seed):
     k = int(rng.integers(1, 5))
     return gaussian_workload(f"batch{seed}_n{n + 1}_nf{nf}", (n, n), nf, omega, b,
                              int(rng.integers(0, 2**31)), sources_per_freq=k)
+
+
+def paper_three_frequency(n=128):
+    """The paper's explicit three-frequency example (eq. Nf3parameters): unit square with
+    n x n cells, omega = {5.1, 10.1, 15.1}, Gaussians f_m = a_m exp(-b_m^2 ||x - x0_m||^2)
+    with a = {25, 100, 225}, b = 15 and centres (0.6, 0.45), (0.4, 0.5), (0.55, 0.5)
+    (eq. gaussianSource), N_p = 2."""
+    dims = (n, n)
+    coords = coordinates(dims, (1.0, 1.0))
+    omega = np.array([5.1, 10.1, 15.1])
+    amps = (25.0, 100.0, 225.0)
+    centres = ((0.6, 0.45), (0.4, 0.5), (0.55, 0.5))
+    forcing = np.stack([gaussian(coords, c, a, 15.0 ** 2) for a, c in zip(amps, centres)])
+    return Workload(f"paper3freq_square{n}", dims, (1.0, 1.0), omega, forcing, 1.0, 0.5, 2)

@@ -39,15 +39,16 @@ def test_exports_every_declared_symbol(lib):
     assert sorted(_lib.declared_symbols()) == names
 
 
-def _compare_setup(wl, n_p=1, mode=F.FILTER_OPTIMIZED, user=None, c_hi=None):
+def _compare_setup(wl, n_p=1, mode=F.FILTER_OPTIMIZED, user=None, c_hi=None, order=2):
     kw = dict(n_p=n_p, filter_mode={F.FILTER_OPTIMIZED: 0, F.FILTER_TRADITIONAL: 1,
-                                     F.FILTER_USER: 2}[mode], user_params=user)
+                                     F.FILTER_USER: 2}[mode], user_params=user, order=order)
     if c_hi is not None:
         kw.update(c_lo=1.0, c_hi=c_hi, interface=0.5, layer_axis=len(wl.n) - 1)
     prob, keep = M.make_problem(wl.n, wl.length, wl.omega, **kw)
     s = M.setup_arrays(M.plan(prob))
     h = [L / n for L, n in zip(wl.length, wl.n)]
-    o = F.make_setup(wl.omega, h, 1.0 if c_hi is None else max(1.0, c_hi), 0.5, n_p, mode, user)
+    o = F.make_setup(wl.omega, h, 1.0 if c_hi is None else max(1.0, c_hi), 0.5, n_p, mode, user,
+                     order=order)
     assert s["n_t"] == o.n_t
     assert abs(s["dt"] - o.dt) <= 1e-15 * o.dt
     np.testing.assert_allclose(s["omega_tilde"], o.omega_t, rtol=1e-14)
@@ -90,6 +91,16 @@ def test_plan_matches_oracle_ill_conditioned_optimiser():
                                   length=(1.3, 0.9))
     s, o = _compare_setup(wl, n_p=2)
     assert o.cond_M > 1e4
+
+
+def test_plan_matches_oracle_fourth_order():
+    """Order 4: the time-step limit is sqrt(3)/2 of the second-order one, so N_t grows."""
+    wl = inputs.square_small()
+    s4, o4 = _compare_setup(wl, order=4)
+    s2, _ = _compare_setup(wl, order=2)
+    assert s4["n_t"] > s2["n_t"]
+    wl3 = inputs.gaussian_workload("t3o4", (20, 18, 16), 3, [7.0, 11.0, 16.0], 150.0, 5)
+    _compare_setup(wl3, c_hi=1.5, order=4)
 
 
 def test_plan_matches_oracle_3d_two_layer():
@@ -151,6 +162,8 @@ def test_adjusted_frequency_matches_definition():
     dict(time_block=16),               # depth 16 is FP32-only
     dict(precision=3),                 # unknown precision
     dict(tile_shape=3),
+    dict(order=3),                     # only second and fourth order
+    dict(order=4, time_block=8),       # fourth order takes one step per launch
 ])
 def test_invalid_problems_are_rejected(bad):
     args = dict(n=(64, 64), length=(1.0, 1.0), omega=[5.5, 9.3])

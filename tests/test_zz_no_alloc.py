@@ -39,11 +39,13 @@ def _noalloc(lib, prob, f, v, stream):
     return st, r
 
 
-@pytest.mark.parametrize("dims,c_hi", [((48, 40), None), ((20, 18, 16), 1.5)])
-def test_noalloc_matches_handle_residual_twice(lib, dims, c_hi):
+@pytest.mark.parametrize("dims,c_hi,order", [((48, 40), None, 2), ((20, 18, 16), 1.5, 2),
+                                             ((48, 40), None, 4)])
+def test_noalloc_matches_handle_residual_twice(lib, dims, c_hi, order):
     nf = 3
     wl = inputs.gaussian_workload("noalloc", dims, nf, [6.1, 9.7, 15.2], 200.0, 41)
     kw = {} if c_hi is None else dict(c_lo=1.0, c_hi=c_hi, interface=0.5, layer_axis=len(dims) - 1)
+    kw["order"] = order
     f = torch.from_numpy(wl.forcing).cuda()
     solver = M.Solver(wl.n, wl.length, wl.omega, f, **kw)
     prob, keep = M.make_problem(wl.n, wl.length, wl.omega, **kw)
