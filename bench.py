@@ -508,7 +508,8 @@ def main():
         dist.barrier()
     M._lib.load()
 
-    wl = inputs.square_large(args.seed + rank)
+    from paper_2507_23613_gb300 import multi
+    wl = inputs.square_large(multi.problem_seed(args.seed, rank))
     stream = torch.cuda.Stream()
     f_dev = torch.from_numpy(wl.forcing).cuda()
     if args.fp32_only:
@@ -570,16 +571,7 @@ def main():
     hbm_peak, peak_kind = peaks()
 
     # whole-job numbers: max time over ranks, points summed over ranks
-    t_max = elapsed_ms
-    total_pts = pts_steps
-    if dist:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        p = torch.tensor([float(pts_steps)], device="cuda", dtype=torch.float64)
-        dist.all_reduce(p)
-        total_pts = float(p.item())
-    value = total_pts / (t_max * 1e-3) / 1e9
+    value, t_max, total_pts = multi.weak_scaling_rate(elapsed_ms, pts_steps, dist, "cuda")
 
     # end to end through the public API with pinned host buffers
     e2e = None
