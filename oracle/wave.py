@@ -89,6 +89,7 @@ class Problem:
     c2: object                   # scalar or grid array of c^2
     setup: filters.Setup = field(repr=False)
     order: int = 2               # order p of L_{ph}: 2 or 4
+    explicit_filter: bool = False  # filter update with the current iterate (footnote to eq. filterII)
 
     @property
     def nf(self):
@@ -97,11 +98,11 @@ class Problem:
 
 def make_problem(grid, omega, forcing, c2=1.0, cfl=0.5, n_p=1,
                  filter_mode=filters.FILTER_OPTIMIZED, user_params=None,
-                 n_delta=20, c_delta=2.0, order=2):
+                 n_delta=20, c_delta=2.0, order=2, explicit_filter=False):
     c_max = math.sqrt(float(np.max(c2)))
     setup = filters.make_setup(omega, grid.h, c_max, cfl, n_p, filter_mode,
                                user_params, n_delta, c_delta, order)
-    return Problem(grid, np.asarray(forcing, dtype=np.float64), c2, setup, order)
+    return Problem(grid, np.asarray(forcing, dtype=np.float64), c2, setup, order, explicit_filter)
 
 
 def composite_forcing(prob, n):
@@ -124,6 +125,8 @@ def apply_Pi(prob, V, forced=True):
     q_m = sum_n w_{n,m} W^n (eq. pDefQ) accumulate while stepping, and the new
     iterate solves B V^{k+1} = q at every grid point (eq. waveHoltzMatrixIteration).
     With forced=False the forcing is dropped, which gives S V (eq. discreteMFWHmapping).
+    With prob.explicit_filter the update is the explicit filter of the footnote to
+    eq. filterII: B_mm V_m^{k+1} = q_m - sum_{j != m} B_mj V_j^k.
     """
     s = prob.setup
     g = prob.grid
@@ -155,8 +158,22 @@ def apply_Pi(prob, V, forced=True):
         W_prev, W_cur = W_cur, W_next
 
     flat = q.reshape(prob.nf, -1)
+    if prob.explicit_filter:
+        # explicit filter: B_mm V_m^{k+1} = q_m - sum_{j != m} B_mj V_j^k, the variant with
+        # v^{(j,k)} in place of v^{(j,k+1)} in the sum of eq. MFWHIteration / eq. filterII
+        Vk = np.asarray(V, dtype=np.float64).reshape(prob.nf, -1).copy()
+        Vk[:, ~_interior_mask(g).ravel()] = 0.0
+        off = s.B - np.diag(np.diag(s.B))
+        V_new = ((flat - off @ Vk) / np.diag(s.B)[:, None]).reshape(q.shape)
+        return V_new
     V_new = np.linalg.solve(s.B, flat).reshape(q.shape)
     return V_new
+
+
+def _interior_mask(grid):
+    mask = np.zeros(grid.shape, dtype=bool)
+    mask[grid.interior()] = True
+    return mask
 
 
 def zero_boundary(W, grid):
