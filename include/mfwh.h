@@ -58,6 +58,8 @@ enum { MFWH_FILTER_OPTIMIZED = 0, MFWH_FILTER_TRADITIONAL = 1, MFWH_FILTER_USER 
    folds that partial sum into the Kahan pair once (compensated across launches); with one
    step per launch it is FP32_KAHAN. */
 enum { MFWH_PREC_FP64 = 0, MFWH_PREC_FP32_KAHAN = 1, MFWH_PREC_FP32_BLOCKSUM = 2 };
+/* How the filter sums become the next iterate (Section "The MFWH algorithm"). */
+enum { MFWH_UPDATE_IMPLICIT = 0, MFWH_UPDATE_EXPLICIT = 1 };
 enum { MFWH_C_CONST = 0, MFWH_C_TWO_LAYER = 1 };
 
 typedef struct mfwh_handle_s* mfwh_handle_t;
@@ -94,6 +96,10 @@ typedef struct {
                                 W_{N+1} = -W_{N-1} (odd reflection of homogeneous Dirichlet data),
                                 time step limit sqrt(3)/2 of the second-order one, one step
                                 per kernel launch (time_block 0 or 1) */
+  int filter_update;         /* MFWH_UPDATE_IMPLICIT (0, default): B V^{k+1} = q, the implicit
+                                filter of eq. vkUpdate; MFWH_UPDATE_EXPLICIT: B_mm V_m^{k+1} =
+                                q_m - sum_{j != m} B_mj V_j^k, the explicit filter of the
+                                footnote to eq. filterII (same fixed point) */
   int tile_shape;            /* FP32 blocked kernel tile: 0 = 32x32, 512 threads (default);
                                 1 = 32x64, 512 threads; 2 = 64x64, 1024 threads (halved in
                                 y above 8 frequencies) */

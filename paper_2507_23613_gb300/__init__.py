@@ -37,7 +37,7 @@ def _dptr(arr):
 def make_problem(n, length, omega, forcing=None, c_lo=1.0, c_hi=None, interface=0.5,
                  layer_axis=2, n_p=1, cfl=0.5, filter_mode=_lib.FILTER_OPTIMIZED,
                  user_params=None, n_delta=20, c_delta=2.0, time_block=0, precision=None,
-                 tile_shape=0, order=2):
+                 tile_shape=0, order=2, filter_update=0):
     """Fill an mfwh_problem.  Returned keep-alive list holds the arrays it points to."""
     p = _lib.Problem()
     p.dim = len(n)
@@ -70,6 +70,7 @@ def make_problem(n, length, omega, forcing=None, c_lo=1.0, c_hi=None, interface=
     p.time_block = int(time_block)
     p.tile_shape = int(tile_shape)
     p.order = int(order)
+    p.filter_update = int(filter_update)
     return p, keep
 
 

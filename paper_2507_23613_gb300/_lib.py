@@ -27,6 +27,8 @@ FILTER_USER = 2
 PREC_FP64 = 0
 PREC_FP32_KAHAN = 1
 PREC_FP32_BLOCKSUM = 2
+UPDATE_IMPLICIT = 0
+UPDATE_EXPLICIT = 1
 C_CONST = 0
 C_TWO_LAYER = 1
 
@@ -55,6 +57,7 @@ class Problem(C.Structure):
         ("precision", C.c_int),
         ("time_block", C.c_int),
         ("order", C.c_int),
+        ("filter_update", C.c_int),
         ("tile_shape", C.c_int),
     ]
 

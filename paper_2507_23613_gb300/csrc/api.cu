@@ -202,6 +202,9 @@ mfwh_status apply_pi32(mfwh_handle_t h, const double* vin, double* vout, int for
     a.wq = h->wq32;
     a.fc = h->fc32;
     a.binv = h->sh.binv;
+    a.emat = h->sh.emat;
+    a.has_e = h->sh.has_e;
+    a.vprev = vin;
     a.depth = P.time_block;
     a.shape = P.tile_shape;
     a.acc = P.precision == MFWH_PREC_FP32_BLOCKSUM ? 1 : 0;
@@ -236,7 +239,8 @@ mfwh_status apply_pi32(mfwh_handle_t h, const double* vin, double* vout, int for
         launch_step32(nf, h->geom, Wc, D_in, Wn, D, h->f32, h->qs, h->qc, a, st);
         std::swap(Wc, Wn);
       } else {
-        launch_last32(nf, h->geom, Wc, D_in, h->f32, h->qs, h->qc, vout, vsub, a, h->sh.binv, st);
+        h->sh.vprev = vin;
+        launch_last32(nf, h->geom, Wc, D_in, h->f32, h->qs, h->qc, vout, vsub, a, h->sh, st);
       }
       ++launches;
     }
@@ -277,6 +281,7 @@ mfwh_status apply_pi_direct(mfwh_handle_t h, const double* vin, double* vout, in
   StepHost& a = h->sh;
   a.forced = forced;
   a.subtract = vsub != nullptr;
+  a.vprev = vin;
   for (int n = 0; n < n_run; ++n) {
     const bool first = n == 0;
     const double kappa = first ? 0.5 * dt * dt : dt * dt;
@@ -334,6 +339,9 @@ mfwh_status apply_pi_tb(mfwh_handle_t h, const double* vin, double* vout, int fo
   a.forced = forced;
   a.subtract = vsub != nullptr;
   std::memcpy(a.binv, h->sh.binv, sizeof(a.binv));
+  std::memcpy(a.emat, h->sh.emat, sizeof(a.emat));
+  a.has_e = h->sh.has_e;
+  a.vprev = vin;
   const double* in_c = h->Wa;
   const double* in_p = nullptr;     // W^{-1} = 0 before the first step
   double* out_c = h->Wc2;
@@ -784,8 +792,17 @@ mfwh_status mfwh_create(const mfwh_problem* prob, void* stream, mfwh_handle_t* o
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "initialising workspace"));
   h->use32 = P.precision != MFWH_PREC_FP64;
   std::memset(&h->sh, 0, sizeof(h->sh));
+  // Epilogue V^{k+1} = C q + E V^k: implicit filter C = B^{-1}, E = 0; explicit filter
+  // C = diag(B)^{-1}, E = -diag(B)^{-1} (B - diag(B)).
+  const bool expl = P.filter_update == MFWH_UPDATE_EXPLICIT;
   for (int m = 0; m < h->nf; ++m)
-    for (int j = 0; j < h->nf; ++j) h->sh.binv[m * MFWH_MAX_NF + j] = P.s.B_inv[m][j];
+    for (int j = 0; j < h->nf; ++j) {
+      h->sh.binv[m * MFWH_MAX_NF + j] =
+          expl ? (m == j ? 1.0 / P.s.B[m][m] : 0.0) : P.s.B_inv[m][j];
+      h->sh.emat[m * MFWH_MAX_NF + j] = (expl && m != j) ? -P.s.B[m][j] / P.s.B[m][m] : 0.0;
+    }
+  h->sh.has_e = expl ? 1 : 0;
+  h->sh.vprev = nullptr;
   *out = h;
   return MFWH_OK;
 }

@@ -25,6 +25,7 @@ struct Plan {
   int tile_shape = 0;          // FP32 blocked-kernel tile shape
   int precision = MFWH_PREC_FP64;
   int order = 2;               // order of L_{ph}: 2 or 4
+  int filter_update = MFWH_UPDATE_IMPLICIT;
   int64_t n[3] = {1, 1, 1};
   std::vector<double> w;       // [(n_t + 1) * nf]  filter weights w_{n,m}
   std::vector<double> cosf;    // [(n_t + 1) * nf]  cos(omega~_m t^n)

@@ -41,9 +41,14 @@ struct StepHost {
   int forced;                       // 0: homogeneous map S (no forcing)
   double fc[MFWH_MAX_NF];           // kappa cos(omega~_m t^n)
   double wq[MFWH_MAX_NF];           // w_{n+1,m}: filter weight of the new level
-  // epilogue (last step only)
-  int subtract;                     // 1: v_out = v_sub - B^{-1} q, else v_out = B^{-1} q
-  double binv[MFWH_MAX_NF * MFWH_MAX_NF];
+  // epilogue (last step only): V^{k+1} = C q + E V^k, then v_out = V^{k+1} or v_sub - V^{k+1}.
+  // Implicit filter: C = B^{-1}, E = 0.  Explicit filter: C = diag(B)^{-1},
+  // E = -diag(B)^{-1} (B - diag(B)).  Matrices row-major with leading dimension MFWH_MAX_NF.
+  int subtract;
+  double binv[MFWH_MAX_NF * MFWH_MAX_NF];   // C
+  double emat[MFWH_MAX_NF * MFWH_MAX_NF];   // E
+  int has_e;                                // E != 0 (applied when V^k is given)
+  const double* vprev;                      // V^k (device), or null for V^k = 0
 };
 
 // Arguments of one temporally blocked launch (wave_tb.cu).
@@ -54,7 +59,10 @@ struct TBHost {
   double dt2, half_dt2;
   int n0, steps, depth;      // first level index, steps in this launch, template depth (4 or 8)
   int forced, last, subtract;
-  double binv[MFWH_MAX_NF * MFWH_MAX_NF];
+  double binv[MFWH_MAX_NF * MFWH_MAX_NF];   // epilogue as in StepHost
+  double emat[MFWH_MAX_NF * MFWH_MAX_NF];
+  int has_e;
+  const double* vprev;
 };
 // Up to `depth` leapfrog+filter steps of a 2D grid in one launch: reads (Wc_in, Wp_in)
 // (Wp_in may be null: W^{-1} = 0 before the first step), writes (Wc_out, Wp_out) and q, or on
@@ -79,7 +87,10 @@ struct TB32Host {
   Coef32 reg_lo, reg_hi, first_lo, first_hi;
   const float* wq;         // device [(N_t + 1) * nf]
   const float* fc;         // device [N_t * nf]
-  const double* binv;      // host [MFWH_MAX_NF * MFWH_MAX_NF], row-major, leading dim 16
+  const double* binv;      // host [MFWH_MAX_NF * MFWH_MAX_NF], row-major, leading dim 16 (C)
+  const double* emat;      // host, same layout (E of the explicit filter)
+  int has_e;
+  const double* vprev;     // device V^k, or null
   int n0, steps, depth, shape, forced, last;
   int acc;                 // 0: Kahan update every step; 1: per-launch partial sums folded
 };
@@ -93,7 +104,7 @@ void launch_step32(int nf, const Geom& g, const float* W, const float* D_in, flo
 // Last step fused with V = B^{-1} q in FP64 (or v_sub - that); boundary of v_out = 0.
 void launch_last32(int nf, const Geom& g, const float* W, const float* D, const float* f,
                    const float* qs, const float* qc, double* vout, const double* vsub,
-                   const Step32Host& h, const double* binv, cudaStream_t st);
+                   const Step32Host& h, const StepHost& epi, cudaStream_t st);
 // Up to h.depth (4, 8 or 16) steps of a 2D grid per launch; outputs must not alias inputs.
 void launch_tb2d32(int nf, const Geom& g, const float* W_in, const float* D_in, float* W_out,
                    float* D_out, const float* f, float* qs, float* qc, double* vout,

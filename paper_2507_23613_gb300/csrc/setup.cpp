@@ -311,6 +311,8 @@ mfwh_status plan_problem(const mfwh_problem* p, Plan* out) {
     return fail(MFWH_ERR_INVALID_ARG, "time_block must be 0, 1, 4 or 8 (or 16 for FP32)");
   if (p->tile_shape < 0 || p->tile_shape > 2)
     return fail(MFWH_ERR_INVALID_ARG, "tile_shape must be 0, 1 or 2");
+  if (p->filter_update != MFWH_UPDATE_IMPLICIT && p->filter_update != MFWH_UPDATE_EXPLICIT)
+    return fail(MFWH_ERR_INVALID_ARG, "filter_update must be implicit or explicit");
   if (p->order != 0 && p->order != 2 && p->order != 4)
     return fail(MFWH_ERR_INVALID_ARG, "order must be 2 or 4");
   if (p->order == 4 && p->time_block > 1)
@@ -331,6 +333,7 @@ mfwh_status plan_problem(const mfwh_problem* p, Plan* out) {
                                      : (fp32 && p->dim == 2 && p->order != 4 ? 8 : 1);
   P.tile_shape = p->tile_shape;
   P.order = p->order == 4 ? 4 : 2;
+  P.filter_update = p->filter_update;
   P.precision = p->precision;
   double inv_h2 = 0.0;
   s.points = 1;

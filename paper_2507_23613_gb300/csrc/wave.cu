@@ -31,8 +31,10 @@ struct StepParams {
 template <int NF>
 struct LastParams {
   StepParams<NF> st;
-  double binv[NF * NF];
-  int subtract;
+  double binv[NF * NF];      // C of V^{k+1} = C q + E V^k
+  double emat[NF * NF];      // E (explicit filter)
+  const double* vprev;       // V^k
+  int subtract, has_e;
 };
 
 template <int NF>
@@ -165,12 +167,21 @@ k_last(const double* __restrict__ Wc, const double* __restrict__ Wp, const doubl
   double qq[NF];
 #pragma unroll
   for (int m = 0; m < NF; ++m) qq[m] = fma(a.st.wq[m], wn, q[m * g.points + x.p]);
+  double vk[NF];
+  if (a.has_e) {
+#pragma unroll
+    for (int j = 0; j < NF; ++j) vk[j] = a.vprev[j * g.points + x.p];
+  }
   double out[NF];
 #pragma unroll
   for (int m = 0; m < NF; ++m) {
     double s = 0.0;
 #pragma unroll
     for (int j = 0; j < NF; ++j) s = fma(a.binv[m * NF + j], qq[j], s);
+    if (a.has_e) {
+#pragma unroll
+      for (int j = 0; j < NF; ++j) s = fma(a.emat[m * NF + j], vk[j], s);
+    }
     out[m] = a.subtract ? vsub[m * g.points + x.p] - s : s;
   }
 #pragma unroll
@@ -311,8 +322,13 @@ void last_nf(const Geom& g, const double* Wc, const double* Wp, const double* f,
   LastParams<NF> a;
   a.st = to_params<NF>(h);
   for (int m = 0; m < NF; ++m)
-    for (int j = 0; j < NF; ++j) a.binv[m * NF + j] = h.binv[m * MFWH_MAX_NF + j];
+    for (int j = 0; j < NF; ++j) {
+      a.binv[m * NF + j] = h.binv[m * MFWH_MAX_NF + j];
+      a.emat[m * NF + j] = h.emat[m * MFWH_MAX_NF + j];
+    }
   a.subtract = h.subtract;
+  a.has_e = h.has_e && h.vprev != nullptr;
+  a.vprev = h.vprev;
   dim3 blk(kBX, kBY);
   if (g.order == 4) {
     if (g.dim == 2)

@@ -36,8 +36,8 @@ void launch_step32(int nf, const Geom& g, const float* W, const float* D_in, flo
 
 void launch_last32(int nf, const Geom& g, const float* W, const float* D, const float* f,
                    const float* qs, const float* qc, double* vout, const double* vsub,
-                   const Step32Host& h, const double* binv, cudaStream_t st) {
-  ops_for(nf).last(g, W, D, f, qs, qc, vout, vsub, h, binv, st);
+                   const Step32Host& h, const StepHost& epi, cudaStream_t st) {
+  ops_for(nf).last(g, W, D, f, qs, qc, vout, vsub, h, epi, st);
 }
 
 void launch_tb2d32(int nf, const Geom& g, const float* W_in, const float* D_in, float* W_out,

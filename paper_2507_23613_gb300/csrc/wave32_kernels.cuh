@@ -38,16 +38,20 @@ struct W32Ops {
   void (*step)(const Geom&, const float*, const float*, float*, float*, const float*, float*,
                float*, const Step32Host&, cudaStream_t);
   void (*last)(const Geom&, const float*, const float*, const float*, const float*, const float*,
-               double*, const double*, const Step32Host&, const double*, cudaStream_t);
+               double*, const double*, const Step32Host&, const StepHost&, cudaStream_t);
   void (*tb)(const Geom&, const float*, const float*, float*, float*, const float*, float*, float*,
              double*, const double*, const TB32Host&, cudaStream_t);
 };
 
 namespace {
 
+// Epilogue V^{k+1} = C q + E V^k (E != 0 only for the explicit filter).
 template <int NF>
 struct Last32Binv {
-  double binv[NF * NF];
+  double binv[NF * NF];      // C
+  double emat[NF * NF];      // E
+  const double* vprev;       // V^k
+  int has_e;
 };
 
 template <int NF>
@@ -163,17 +167,25 @@ k_step32(const float* __restrict__ W, const float* D_in, float* __restrict__ W_o
 }
 
 template <int NF>
-__device__ __forceinline__ void filter_solve_out(const float* s, const float* c, const double* binv,
-                                                 int subtract, const double* vsub, double* vout,
+__device__ __forceinline__ void filter_solve_out(const float* s, const float* c,
+                                                 const Last32Binv<NF>& b, int subtract,
+                                                 const double* vsub, double* vout,
                                                  int64_t p, int64_t points, bool interior) {
-  double qd[NF];
+  double qd[NF], vk[NF];
 #pragma unroll
-  for (int m = 0; m < NF; ++m) qd[m] = (double)s[m] - (double)c[m];
+  for (int m = 0; m < NF; ++m) {
+    qd[m] = (double)s[m] - (double)c[m];
+    vk[m] = (b.has_e && interior) ? b.vprev[m * points + p] : 0.0;
+  }
 #pragma unroll
   for (int m = 0; m < NF; ++m) {
     double acc = 0.0;
 #pragma unroll
-    for (int j = 0; j < NF; ++j) acc = fma(binv[m * NF + j], qd[j], acc);
+    for (int j = 0; j < NF; ++j) acc = fma(b.binv[m * NF + j], qd[j], acc);
+    if (b.has_e) {
+#pragma unroll
+      for (int j = 0; j < NF; ++j) acc = fma(b.emat[m * NF + j], vk[j], acc);
+    }
     double val = 0.0;
     if (interior) val = subtract ? vsub[m * points + p] - acc : acc;
     vout[m * points + p] = val;
@@ -202,7 +214,7 @@ k_last32(const float* __restrict__ W, const float* __restrict__ D, const float* 
       kahan_add(s[m], c[m], a.wq[m], wn);
     }
   }
-  filter_solve_out<NF>(s, c, b.binv, subtract, vsub, vout, p, g.points, interior);
+  filter_solve_out<NF>(s, c, b, subtract, vsub, vout, p, g.points, interior);
 }
 
 // ---- temporally blocked 2D kernel ----------------------------------------------
@@ -464,7 +476,7 @@ k_tb2d32(const float* __restrict__ W_in, const float* __restrict__ D_in,
 #pragma unroll
         for (int m = 0; m < NF; ++m) ks[k][m] = kc[k][m] = 0.0f;
       }
-      filter_solve_out<NF>(ks[k], kc[k], b.binv, a.subtract, vsub, vout, p, g.points, own_int[k]);
+      filter_solve_out<NF>(ks[k], kc[k], b, a.subtract, vsub, vout, p, g.points, own_int[k]);
     }
   }
 }
@@ -508,10 +520,16 @@ Step32Args<NF> step_args(const Step32Host& h) {
 }
 
 template <int NF>
-Last32Binv<NF> binv_args(const double* binv) {
+Last32Binv<NF> binv_args(const double* binv, const double* emat, int has_e,
+                         const double* vprev) {
   Last32Binv<NF> b;
   for (int m = 0; m < NF; ++m)
-    for (int j = 0; j < NF; ++j) b.binv[m * NF + j] = binv[m * MFWH_MAX_NF + j];
+    for (int j = 0; j < NF; ++j) {
+      b.binv[m * NF + j] = binv[m * MFWH_MAX_NF + j];
+      b.emat[m * NF + j] = emat[m * MFWH_MAX_NF + j];
+    }
+  b.has_e = has_e && vprev != nullptr;
+  b.vprev = vprev;
   return b;
 }
 
@@ -540,9 +558,9 @@ void step32_nf(const Geom& g, const float* W, const float* D_in, float* W_out, f
 template <int NF>
 void last32_nf(const Geom& g, const float* W, const float* D, const float* f, const float* qs,
                const float* qc, double* vout, const double* vsub, const Step32Host& h,
-               const double* binv, cudaStream_t st) {
+               const StepHost& epi, cudaStream_t st) {
   const Step32Args<NF> a = step_args<NF>(h);
-  const Last32Binv<NF> b = binv_args<NF>(binv);
+  const Last32Binv<NF> b = binv_args<NF>(epi.binv, epi.emat, epi.has_e, epi.vprev);
   const int sub = vsub != nullptr;
   const dim3 grid = grid_of(g), blk(kBX, kBY);
   if (g.order == 4) {
@@ -596,7 +614,7 @@ void tb32_launch(const Geom& g, const float* W_in, const float* D_in, float* W_o
   a.forced = h.forced;
   a.last = h.last;
   a.subtract = vsub != nullptr;
-  const Last32Binv<NF> b = binv_args<NF>(h.binv);
+  const Last32Binv<NF> b = binv_args<NF>(h.binv, h.emat, h.has_e, h.vprev);
   dim3 grid((unsigned)((g.nx + BX) / BX), (unsigned)((g.ny + BY) / BY));
   k_tb2d32<NF, T, BX, TY, K, MB, ACC><<<grid, dim3(BX, TY), smem, st>>>(
       W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, a, b, g);

@@ -36,8 +36,11 @@ struct TBParams {
   int steps;                      // 1 .. T
   int forced;
   int last;                       // fuse the filter solve; v_out written instead of W and q
-  int subtract;                   // v_out = v_sub - B^{-1} q
-  double binv[NF * NF];
+  int subtract;                   // v_out = v_sub - V^{k+1}
+  int has_e;                      // V^{k+1} = C q + E V^k with E != 0 (explicit filter)
+  const double* vprev;            // V^k
+  double binv[NF * NF];           // C
+  double emat[NF * NF];           // E
 };
 
 __device__ __forceinline__ bool interior_pt(int64_t gx, int64_t gy, const Geom& g) {
@@ -186,12 +189,20 @@ k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       if (!own_in[k]) continue;
+      double vk[NF];
+#pragma unroll
+      for (int j = 0; j < NF; ++j)
+        vk[j] = (a.has_e && own_int[k]) ? a.vprev[j * g.points + own_p[k]] : 0.0;
       double out[NF];
 #pragma unroll
       for (int m = 0; m < NF; ++m) {
         double s = 0.0;
 #pragma unroll
         for (int j = 0; j < NF; ++j) s = fma(a.binv[m * NF + j], qr[k][j], s);
+        if (a.has_e) {
+#pragma unroll
+          for (int j = 0; j < NF; ++j) s = fma(a.emat[m * NF + j], vk[j], s);
+        }
         out[m] = s;
       }
 #pragma unroll
@@ -234,8 +245,13 @@ void tb_launch_nf(const Geom& g, const double* Wc_in, const double* Wp_in, doubl
   a.forced = h.forced;
   a.last = h.last;
   a.subtract = h.subtract;
+  a.has_e = h.has_e && h.vprev != nullptr;
+  a.vprev = h.vprev;
   for (int m = 0; m < NF; ++m)
-    for (int j = 0; j < NF; ++j) a.binv[m * NF + j] = h.binv[m * MFWH_MAX_NF + j];
+    for (int j = 0; j < NF; ++j) {
+      a.binv[m * NF + j] = h.binv[m * MFWH_MAX_NF + j];
+      a.emat[m * NF + j] = h.emat[m * MFWH_MAX_NF + j];
+    }
   dim3 grid((unsigned)((g.nx + 1 + BX - 1) / BX), (unsigned)((g.ny + 1 + BY - 1) / BY));
   k_tb2d<NF, T, K><<<grid, dim3(kTX, kTY), smem, st>>>(Wc_in, Wp_in, Wc_out, Wp_out, f, q, vout,
                                                        vsub, a, g);

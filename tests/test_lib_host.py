@@ -163,6 +163,7 @@ def test_adjusted_frequency_matches_definition():
     dict(precision=3),                 # unknown precision
     dict(tile_shape=3),
     dict(order=3),                     # only second and fourth order
+    dict(filter_update=2),             # implicit (0) or explicit (1) only
     dict(order=4, time_block=8),       # fourth order takes one step per launch
 ])
 def test_invalid_problems_are_rejected(bad):
