@@ -87,7 +87,7 @@ typedef struct {
   double c_delta;            /* c_delta of eq. LambdaRange (paper: 2) */
   int precision;             /* MFWH_PREC_FP64, MFWH_PREC_FP32_KAHAN or MFWH_PREC_FP32_BLOCKSUM */
   int time_block;            /* leapfrog steps per pass over HBM: 0 = library default (1 for
-                                FP64; 8 for FP32 in 2D), 1 = one step per kernel launch,
+                                FP64; 16 for FP32 in 2D), 1 = one step per kernel launch,
                                 4 or 8 (or 16 for FP32) = temporal blocking with that depth
                                 (2D grids only).  Results are bit-identical for every depth. */
   int order;                 /* order p of the spatial operator L_{ph}: 2 (0 means 2) or 4.

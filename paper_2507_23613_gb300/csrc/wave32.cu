@@ -1,5 +1,5 @@
 // Host entry points of the FP32 wave solve: dispatch on the number of
-// frequencies to the instantiations in wave32_p1.cu .. wave32_p4.cu.  The
+// frequencies to the instantiations in wave32_p1.cu .. wave32_p8.cu.  The
 // kernels and the arithmetic they follow are described in wave32_kernels.cuh.
 #include <cuda_runtime.h>
 
@@ -15,10 +15,16 @@ __global__ void k_to_float(const double* __restrict__ x, float* __restrict__ y, 
 }
 
 W32Ops ops_for(int nf) {
-  if (nf <= 4) return w32_ops_p1(nf);
-  if (nf <= 8) return w32_ops_p2(nf);
-  if (nf <= 12) return w32_ops_p3(nf);
-  return w32_ops_p4(nf);
+  switch ((nf + 1) / 2) {
+    case 1: return w32_ops_p1(nf);
+    case 2: return w32_ops_p2(nf);
+    case 3: return w32_ops_p3(nf);
+    case 4: return w32_ops_p4(nf);
+    case 5: return w32_ops_p5(nf);
+    case 6: return w32_ops_p6(nf);
+    case 7: return w32_ops_p7(nf);
+    default: return w32_ops_p8(nf);
+  }
 }
 
 }  // namespace

@@ -27,12 +27,14 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "kernels.h"
 
 namespace mfwh {
 
 // The four host launchers of one frequency count, collected so that the
-// translation units wave32_p*.cu can each instantiate a range of counts.
+// translation units wave32_p1.cu .. wave32_p8.cu can each instantiate two counts.
 struct W32Ops {
   void (*init)(const Geom&, const double*, float*, float*, float*, const float*, cudaStream_t);
   void (*step)(const Geom&, const float*, const float*, float*, float*, const float*, float*,
@@ -390,64 +392,76 @@ k_tb2d32(const float* __restrict__ W_in, const float* __restrict__ D_in,
     }
   }
 
-  for (int s = 0; s < a.steps; ++s) {
-    const int r = a.steps - 1 - s;
-    const bool first = a.n0 + s == 0;
-    const Coef32 lo = first ? a.first_lo : a.reg_lo;
-    const Coef32 hi = first ? a.first_hi : a.reg_hi;
-    const float* fc = s_fc + s * NF;
-    float wq[NF];
+  // The T steps in two compiled copies with the same arithmetic per point: ALLINT, for
+  // homogeneous launches of CTAs whose updated points are all interior with one c^2, without
+  // the forcing terms and the per-point interior and layer tests; and the general one.
+  auto run_steps = [&](auto allint_c) {
+    constexpr bool ALLINT = decltype(allint_c)::value;
+    const int forcing = ALLINT ? 0 : a.forced;
+    for (int s = 0; s < a.steps; ++s) {
+      const int r = a.steps - 1 - s;
+      const bool first = a.n0 + s == 0;
+      const Coef32 lo = first ? a.first_lo : a.reg_lo;
+      const Coef32 hi = first ? a.first_hi : a.reg_hi;
+      const float* fc = s_fc + s * NF;
+      float wq[NF];
 #pragma unroll
-    for (int m = 0; m < NF; ++m) wq[m] = s_wq[s * NF + m];
-    // the strip: centre values from registers, neighbours from shared memory
-    {
-      const float above = Wc[(lyo - 1) * EX + lxo];
-      const float below = Wc[(lyo + K) * EX + lxo];
-      float wnew[K];
+      for (int m = 0; m < NF; ++m) wq[m] = s_wq[s * NF + m];
+      // the strip: centre values from registers, neighbours from shared memory
+      {
+        const float above = Wc[(lyo - 1) * EX + lxo];
+        const float below = Wc[(lyo + K) * EX + lxo];
+        float wnew[K];
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const float w = wr[k];
-        wnew[k] = w;
-        if (!own_int[k]) continue;     // boundary and outside points keep W = 0
-        const int l = (lyo + k) * EX + lxo;
-        const float up = k == 0 ? above : wr[k - 1];
-        const float dn = k == K - 1 ? below : wr[k + 1];
-        const float dxx = (Wc[l - 1] - w) + (Wc[l + 1] - w);
-        const float dyy = (up - w) + (dn - w);
-        const Coef32 L = own_up[k] ? hi : lo;
-        const float inc = increment<NF, 2>(L, dxx, dyy, 0.0f, fc, f, p0 + k * g.sy, g.points,
-                                           a.forced);
-        dr[k] = dr[k] + inc;
-        wnew[k] = w + dr[k];
-      }
+        for (int k = 0; k < K; ++k) {
+          const float w = wr[k];
+          wnew[k] = w;
+          if (!ALLINT && !own_int[k]) continue;   // boundary and outside points keep W = 0
+          const int l = (lyo + k) * EX + lxo;
+          const float up = k == 0 ? above : wr[k - 1];
+          const float dn = k == K - 1 ? below : wr[k + 1];
+          const float dxx = (Wc[l - 1] - w) + (Wc[l + 1] - w);
+          const float dyy = (up - w) + (dn - w);
+          const Coef32 L = ALLINT ? (all_hi ? hi : lo) : (own_up[k] ? hi : lo);
+          const float inc = increment<NF, 2>(L, dxx, dyy, 0.0f, fc, f, p0 + k * g.sy, g.points,
+                                             forcing);
+          dr[k] = dr[k] + inc;
+          wnew[k] = w + dr[k];
+        }
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        wr[k] = wnew[k];
-        Wn[(lyo + k) * EX + lxo] = wnew[k];
-        if (own_int[k]) {
+        for (int k = 0; k < K; ++k) {
+          wr[k] = wnew[k];
+          Wn[(lyo + k) * EX + lxo] = wnew[k];
+          if (ALLINT || own_int[k]) {
 #pragma unroll
-          for (int m = 0; m < NF; ++m) {
-            if (ACC == 0)
-              kahan_add(ks[k][m], kc[k][m], wq[m], wnew[k]);
-            else
-              part[k][m] = fmaf(wq[m], wnew[k], part[k][m]);
+            for (int m = 0; m < NF; ++m) {
+              if (ACC == 0)
+                kahan_add(ks[k][m], kc[k][m], wq[m], wnew[k]);
+              else
+                part[k][m] = fmaf(wq[m], wnew[k], part[k][m]);
+            }
           }
         }
       }
+      if (r > 0) {
+        if (ALLINT || simple)
+          ring_pass<NF, T, BX, BY, true>(Wc, Wn, Dv, r, tid, NT, ilx, ihx, ily, ihy, lay_x,
+                                         lay_thr, all_hi ? hi : lo, hi, fc, f, y0, x0, g,
+                                         forcing);
+        else
+          ring_pass<NF, T, BX, BY, false>(Wc, Wn, Dv, r, tid, NT, ilx, ihx, ily, ihy, lay_x,
+                                          lay_thr, lo, hi, fc, f, y0, x0, g, forcing);
+      }
+      __syncthreads();
+      float* t = Wc;
+      Wc = Wn;
+      Wn = t;
     }
-    if (r > 0) {
-      if (simple)
-        ring_pass<NF, T, BX, BY, true>(Wc, Wn, Dv, r, tid, NT, ilx, ihx, ily, ihy, lay_x, lay_thr,
-                                       all_hi ? hi : lo, hi, fc, f, y0, x0, g, a.forced);
-      else
-        ring_pass<NF, T, BX, BY, false>(Wc, Wn, Dv, r, tid, NT, ilx, ihx, ily, ihy, lay_x,
-                                        lay_thr, lo, hi, fc, f, y0, x0, g, a.forced);
-    }
-    __syncthreads();
-    float* t = Wc;
-    Wc = Wn;
-    Wn = t;
-  }
+  };
+  if (simple && !a.forced)
+    run_steps(std::true_type{});
+  else
+    run_steps(std::false_type{});
   // wr = W^{n0+steps}, dr = D^{n0+steps-1/2} on the strip
   const bool col_in = lxo <= ghx;
 #pragma unroll
@@ -661,9 +675,9 @@ template <int NF>
 void tb32_nf(const Geom& g, const float* W_in, const float* D_in, float* W_out, float* D_out,
              const float* f, float* qs, float* qc, double* vout, const double* vsub,
              const TB32Host& h, cudaStream_t st) {
-  if (h.depth <= 4)
-    tb32_acc<NF, 4>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, h, st);
-  else if (h.depth <= 8)
+  // Depth 4 runs on the depth-8 instantiation: a launch of at most 4 steps only needs the
+  // inner 4 points of its 8-point halo, and the arithmetic per point is the same.
+  if (h.depth <= 8)
     tb32_acc<NF, 8>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, h, st);
   else
     tb32_acc<NF, 16>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, h, st);
@@ -676,10 +690,14 @@ W32Ops make_w32_ops() {
 
 }  // namespace
 
-// Defined in wave32_p1.cu .. wave32_p4.cu for nf in 1-4, 5-8, 9-12, 13-16.
+// Defined in wave32_p1.cu .. wave32_p8.cu for nf in 1-2, 3-4, ..., 15-16.
 W32Ops w32_ops_p1(int nf);
 W32Ops w32_ops_p2(int nf);
 W32Ops w32_ops_p3(int nf);
 W32Ops w32_ops_p4(int nf);
+W32Ops w32_ops_p5(int nf);
+W32Ops w32_ops_p6(int nf);
+W32Ops w32_ops_p7(int nf);
+W32Ops w32_ops_p8(int nf);
 
 }  // namespace mfwh
