@@ -73,6 +73,8 @@ struct mfwh_handle_s {
   Geom geom{};
   int nf = 0;
   int64_t P = 0, N = 0;            // points per grid function, nf * points
+  int64_t PW = 0;                   // entries of one FP32 wave-level array (padded rows in 2D)
+  int* d_err = nullptr;             // device flag of the blocked FP32 kernel (tensor copy timeout)
   double inv_h2[3] = {0, 0, 0};
   double omega2[MFWH_MAX_NF] = {};
   double* f = nullptr;              // forcing [nf][P]
@@ -133,6 +135,16 @@ void reset_timing(mfwh_handle_t h) {
 }
 
 mfwh_status collect_timing(mfwh_handle_t h) {
+  if (h->d_err) {   // a blocked FP32 launch reports a tile copy that did not complete
+    CK(cudaMemcpyAsync(h->pinned, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    int flag = 0;
+    std::memcpy(&flag, h->pinned, sizeof(int));
+    if (flag) {
+      CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
+      return fail(MFWH_ERR_CUDA, "FP32 wave kernel: a tile's tensor copy did not complete");
+    }
+  }
   double ms = 0.0;
   for (int i = 0; i + 1 < h->ev_used; i += 2) {
     float t = 0.0f;
@@ -208,6 +220,7 @@ mfwh_status apply_pi32(mfwh_handle_t h, const double* vin, double* vout, int for
     a.depth = P.time_block;
     a.shape = P.tile_shape;
     a.acc = P.precision == MFWH_PREC_FP32_BLOCKSUM ? 1 : 0;
+    a.err = h->d_err;
     a.forced = forced;
     int cur = 0;                 // pair holding the input: (W32[2 cur], W32[2 cur + 1])
     for (int n0 = 0; n0 < n_run;) {
@@ -698,6 +711,11 @@ mfwh_status mfwh_create(const mfwh_problem* prob, void* stream, mfwh_handle_t* o
   g.layer_axis = P.layer_axis;
   g.layer_split = P.layer_split;
   g.order = P.order;
+  // FP32 2D wave levels: rows padded to 32 floats (16-byte aligned for tensor copies)
+  const bool pad_w = P.precision != MFWH_PREC_FP64 && P.dim == 2;
+  g.syw = pad_w ? (g.nx + 1 + 31) / 32 * 32 : g.sy;
+  g.szw = pad_w ? g.syw * (g.ny + 1) : g.sz;
+  h->PW = pad_w ? g.syw * (g.ny + 1) : h->P;
 
   auto cleanup = [&](mfwh_status s) {
     mfwh_destroy(h);
@@ -742,15 +760,17 @@ mfwh_status mfwh_create(const mfwh_problem* prob, void* stream, mfwh_handle_t* o
     struct {
       float** p;
       int64_t n;
-    } fb[] = {{&h->f32, h->N}, {&h->W32[0], h->P}, {&h->W32[1], h->P}, {&h->W32[2], h->P},
-              {&h->W32[3], h->P}, {&h->qs, h->N}, {&h->qc, h->N},
+    } fb[] = {{&h->f32, h->N}, {&h->W32[0], h->PW}, {&h->W32[1], h->PW}, {&h->W32[2], h->PW},
+              {&h->W32[3], h->PW}, {&h->qs, h->N}, {&h->qc, h->N},
               {&h->wq32, (int64_t)h->wq32_h.size()}, {&h->fc32, (int64_t)h->fc32_h.size()}};
     for (auto& b : fb) {
       e = cudaMalloc(b.p, sizeof(float) * std::max<int64_t>(b.n, 1));
       if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc (FP32 workspace)"));
     }
     for (int i = 0; i < 4 && e == cudaSuccess; ++i)
-      e = cudaMemsetAsync(h->W32[i], 0, sizeof(float) * h->P, h->stream);
+      e = cudaMemsetAsync(h->W32[i], 0, sizeof(float) * h->PW, h->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(h->wq32, h->wq32_h.data(), sizeof(float) * h->wq32_h.size(),
                           cudaMemcpyHostToDevice, h->stream);
@@ -1040,6 +1060,7 @@ void mfwh_destroy(mfwh_handle_t h) {
                     h->dot_partial, h->dot_out, h->vec_b,     h->vec_x,   h->basis};
   for (double* b : bufs)
     if (b) cudaFree(b);
+  if (h->d_err) cudaFree(h->d_err);
   float* fbufs[] = {h->f32, h->W32[0], h->W32[1], h->W32[2], h->W32[3], h->qs, h->qc,
                     h->wq32, h->fc32};
   for (float* b : fbufs)

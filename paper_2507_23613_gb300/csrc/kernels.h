@@ -19,6 +19,8 @@ struct Geom {
   int layer_axis;            // axis whose index selects the c^2 layer
   int64_t layer_split;       // indices >= layer_split use the upper-layer coefficients
   int order;                 // order of L_{ph}: 2 or 4 (0 reads as 2)
+  int64_t syw, szw;          // strides of j and k in the FP32 wave-level arrays W and D (2D
+                             // FP32 handles pad rows to 32 floats for tensor copies; else sy, sz)
 };
 
 // Leapfrog update at one point, written as
@@ -93,6 +95,7 @@ struct TB32Host {
   const double* vprev;     // device V^k, or null
   int n0, steps, depth, shape, forced, last;
   int acc;                 // 0: Kahan update every step; 1: per-launch partial sums folded
+  int* err;                // device flag set to 1 when a tile's tensor copy does not complete
 };
 // W^0 = fl32(sum_m v_m) (0 on the boundary), qs_m = w0_m W^0, qc_m = 0.
 void launch_init32(int nf, const Geom& g, const double* v, float* W0, float* qs, float* qc,

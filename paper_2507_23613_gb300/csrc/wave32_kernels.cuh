@@ -25,8 +25,10 @@
 // results are bit-identical.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <type_traits>
 
 #include "kernels.h"
@@ -123,6 +125,11 @@ __device__ __forceinline__ float comb4(const float* W, int64_t p, int64_t s, int
   return fmaf(16.0f, d1, -(dm + dp));
 }
 
+// Index of grid point (i, j, k) in the wave-level arrays W and D (padded rows in 2D).
+__device__ __forceinline__ int64_t wpos(const Geom& g, int64_t i, int64_t j, int64_t k) {
+  return k * g.szw + j * g.syw + i;
+}
+
 template <int NF, int DIM, int ORDER>
 __device__ __forceinline__ void step_point(const float* __restrict__ W, const float* D,
                                            const float* __restrict__ f, const Step32Args<NF>& a,
@@ -130,17 +137,18 @@ __device__ __forceinline__ void step_point(const float* __restrict__ W, const fl
                                            int64_t p, float& wn, float& dn) {
   const int64_t li = g.layer_axis == 0 ? i : (g.layer_axis == 1 ? j : k);
   const Coef32& L = li >= g.layer_split ? a.hi : a.lo;
-  const float w = W[p];
-  float dxx = (W[p - 1] - w) + (W[p + 1] - w);
-  float dyy = (W[p - g.sy] - w) + (W[p + g.sy] - w);
-  float dzz = DIM == 3 ? (W[p - g.sz] - w) + (W[p + g.sz] - w) : 0.0f;
+  const int64_t q = wpos(g, i, j, k);
+  const float w = W[q];
+  float dxx = (W[q - 1] - w) + (W[q + 1] - w);
+  float dyy = (W[q - g.syw] - w) + (W[q + g.syw] - w);
+  float dzz = DIM == 3 ? (W[q - g.szw] - w) + (W[q + g.szw] - w) : 0.0f;
   if (ORDER == 4) {
-    dxx = comb4(W, p, 1, i, g.nx, w, dxx);
-    dyy = comb4(W, p, g.sy, j, g.ny, w, dyy);
-    if (DIM == 3) dzz = comb4(W, p, g.sz, k, g.nz, w, dzz);
+    dxx = comb4(W, q, 1, i, g.nx, w, dxx);
+    dyy = comb4(W, q, g.syw, j, g.ny, w, dyy);
+    if (DIM == 3) dzz = comb4(W, q, g.szw, k, g.nz, w, dzz);
   }
   const float inc = increment<NF, DIM>(L, dxx, dyy, dzz, a.fc, f, p, g.points, a.forced);
-  dn = (D ? D[p] : 0.0f) + inc;
+  dn = (D ? D[q] : 0.0f) + inc;
   wn = w + dn;
 }
 
@@ -157,8 +165,8 @@ k_step32(const float* __restrict__ W, const float* D_in, float* __restrict__ W_o
   if (!interior) return;
   float wn, dn;
   step_point<NF, DIM, ORDER>(W, D_in, f, a, g, i, j, k, p, wn, dn);
-  W_out[p] = wn;
-  D_out[p] = dn;
+  W_out[wpos(g, i, j, k)] = wn;
+  D_out[wpos(g, i, j, k)] = dn;
 #pragma unroll
   for (int m = 0; m < NF; ++m) {
     float s = qs[m * g.points + p], c = qc[m * g.points + p];
@@ -226,6 +234,7 @@ struct TB32Args {
   Coef32 reg_lo, reg_hi, first_lo, first_hi;
   const float* wq;   // [(N_t + 1) * NF]
   const float* fc;   // [N_t * NF]
+  int* err;          // set to 1 when a tile's tensor copy does not complete
   int n0, steps, forced, last, subtract;
 };
 
@@ -306,15 +315,50 @@ __device__ __forceinline__ void ring_pass(const float* Wc, float* Wn, float* Dv,
 // increments D of its own points stay in registers for all T steps; only the left and right
 // neighbours and the rows just above and below the strip come from shared memory.  The halo
 // ring is updated from shared memory by all threads.
+// Tensor-memory-accelerator (TMA) copies of the extended tile: one 2D tiled copy of EX x EY
+// floats per array, completing on an mbarrier with a transaction count.  Points outside the
+// grid (negative or past the extents) arrive as zeros.
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void tma_tile_2d(float* dst, const CUtensorMap* map, int x, int y,
+                                            unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Bounded wait for phase `parity` of an mbarrier; false when the bound ran out.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, int limit) {
+  for (int it = 0; it < limit; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
 template <int NF, int T, int BX, int TY, int K, int MB, int ACC>
 __global__ void __launch_bounds__(BX * TY, MB)
 k_tb2d32(const float* __restrict__ W_in, const float* __restrict__ D_in,
          float* __restrict__ W_out, float* __restrict__ D_out, const float* __restrict__ f,
          float* __restrict__ qs, float* __restrict__ qc, double* vout, const double* vsub,
-         const TB32Args<NF> a, const Last32Binv<NF> b, const Geom g) {
+         const TB32Args<NF> a, const Last32Binv<NF> b, const Geom g,
+         const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmD,
+         int use_tma) {
   constexpr int BY = TY * K, NT = BX * TY;
   constexpr int EX = BX + 2 * T, EY = BY + 2 * T, E = EX * EY;
-  extern __shared__ float sm32[];
+  static_assert((E * sizeof(float)) % 128 == 0, "tile arrays must stay 128-byte aligned");
+  extern __shared__ __align__(128) float sm32[];
+  __shared__ __align__(8) uint64_t tile_bar;
   float* Wc = sm32;             // W^n on the extended tile
   float* Wn = sm32 + E;         // W^{n+1}
   float* Dv = sm32 + 2 * E;     // D on the halo (the tile's own D lives in registers)
@@ -335,16 +379,45 @@ k_tb2d32(const float* __restrict__ W_in, const float* __restrict__ D_in,
                       (lay_thr <= 0 || lay_thr >= (lay_x ? EX : EY));
   const bool all_hi = lay_thr <= 0;
 
-  for (int ly = ty; ly < EY; ly += TY) {
-    const bool row = ly >= gly && ly <= ghy;
-    const int64_t rbase = (y0 + ly) * g.sy + x0;
-    for (int lx = tx; lx < EX; lx += BX) {
-      const bool in = row && lx >= glx && lx <= ghx;
-      const int l = ly * EX + lx;
-      const float w = in ? W_in[rbase + lx] : 0.0f;
-      Wc[l] = w;
-      Wn[l] = w;
-      Dv[l] = (in && D_in != nullptr) ? D_in[rbase + lx] : 0.0f;
+  if (use_tma) {
+    // W twice (current level and the buffer of the next one, whose boundary values must be
+    // in place) and D once, by tensor copies issued from one thread.
+    const unsigned bar = smem_addr(&tile_bar);
+    if (tid == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const unsigned bytes = (D_in != nullptr ? 3u : 2u) * (unsigned)(E * sizeof(float));
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                   : "memory");
+      tma_tile_2d(Wc, &tmW, (int)x0, (int)y0, bar);
+      tma_tile_2d(Wn, &tmW, (int)x0, (int)y0, bar);
+      if (D_in != nullptr) tma_tile_2d(Dv, &tmD, (int)x0, (int)y0, bar);
+    }
+    if (D_in == nullptr)
+      for (int e = tid; e < E; e += NT) Dv[e] = 0.0f;
+    const bool ok = mbar_wait(bar, 0, 1 << 22);
+    if (__syncthreads_or(!ok)) {
+      // The copies did not complete within the bound: report it, give them one more bounded
+      // wait so that none lands in shared memory after the CTA is gone, and stop.
+      if (tid == 0) atomicExch(a.err, 1);
+      mbar_wait(bar, 0, 1 << 22);
+      return;
+    }
+  } else {
+    for (int ly = ty; ly < EY; ly += TY) {
+      const bool row = ly >= gly && ly <= ghy;
+      const int64_t rbase = (y0 + ly) * g.syw + x0;
+      for (int lx = tx; lx < EX; lx += BX) {
+        const bool in = row && lx >= glx && lx <= ghx;
+        const int l = ly * EX + lx;
+        const float w = in ? W_in[rbase + lx] : 0.0f;
+        Wc[l] = w;
+        Wn[l] = w;
+        Dv[l] = (in && D_in != nullptr) ? D_in[rbase + lx] : 0.0f;
+      }
     }
   }
   for (int e = tid; e < a.steps * NF; e += NT) {
@@ -477,8 +550,8 @@ k_tb2d32(const float* __restrict__ W_in, const float* __restrict__ D_in,
     }
     if (!a.last) {
       if (!own_int[k]) continue;
-      W_out[p] = wr[k];
-      D_out[p] = dr[k];
+      W_out[(y0 + lyo + k) * g.syw + x0 + lxo] = wr[k];
+      D_out[(y0 + lyo + k) * g.syw + x0 + lxo] = dr[k];
 #pragma unroll
       for (int m = 0; m < NF; ++m) {
         qs[m * g.points + p] = ks[k][m];
@@ -510,7 +583,7 @@ k_init32(const double* __restrict__ v, float* __restrict__ W0, float* __restrict
     for (int m = 0; m < NF; ++m) w += v[m * g.points + p];
   }
   const float wf = (float)w;
-  W0[p] = wf;
+  W0[wpos(g, i, j, k)] = wf;
 #pragma unroll
   for (int m = 0; m < NF; ++m) {
     qs[m * g.points + p] = a.w0[m] * wf;
@@ -600,6 +673,43 @@ void init32_nf(const Geom& g, const double* v, float* W0, float* qs, float* qc, 
     k_init32<NF, 2><<<grid_of(g), dim3(kBX, kBY), 0, st>>>(v, W0, qs, qc, a, g);
 }
 
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once through the runtime (no driver library link).
+inline EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// Tensor map of one 2D wave-level array for EX x EY boxes; false if unavailable, in which
+// case the kernel loads its tile with ordinary loads.
+inline bool wave_tensor_map(CUtensorMap* m, const float* base, const Geom& g, int ex, int ey) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn || !base || g.dim != 2 || (g.syw * sizeof(float)) % 16 != 0 ||
+      (reinterpret_cast<uintptr_t>(base) & 15) != 0)
+    return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)(g.nx + 1), (cuuint64_t)(g.ny + 1)};
+  const cuuint64_t strides[1] = {(cuuint64_t)(g.syw * sizeof(float))};
+  const cuuint32_t box[2] = {(cuuint32_t)ex, (cuuint32_t)ey};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int NF, int T, int BX, int TY, int K, int MB, int ACC>
 void tb32_launch(const Geom& g, const float* W_in, const float* D_in, float* W_out, float* D_out,
                  const float* f, float* qs, float* qc, double* vout, const double* vsub,
@@ -628,10 +738,15 @@ void tb32_launch(const Geom& g, const float* W_in, const float* D_in, float* W_o
   a.forced = h.forced;
   a.last = h.last;
   a.subtract = vsub != nullptr;
+  a.err = h.err;
   const Last32Binv<NF> b = binv_args<NF>(h.binv, h.emat, h.has_e, h.vprev);
   dim3 grid((unsigned)((g.nx + BX) / BX), (unsigned)((g.ny + BY) / BY));
+  CUtensorMap tmW{}, tmD{};
+  int use_tma = h.err != nullptr && wave_tensor_map(&tmW, W_in, g, EX, EY) &&
+                (D_in == nullptr || wave_tensor_map(&tmD, D_in, g, EX, EY));
+  if (D_in == nullptr) tmD = tmW;
   k_tb2d32<NF, T, BX, TY, K, MB, ACC><<<grid, dim3(BX, TY), smem, st>>>(
-      W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, a, b, g);
+      W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, a, b, g, tmW, tmD, use_tma);
 }
 
 template <int NF, int T, int ACC>
