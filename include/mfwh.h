@@ -249,6 +249,35 @@ mfwh_status mfwh_solve_batch(const mfwh_handle_t* handles, int count, int restar
 mfwh_status mfwh_autotune(const mfwh_problem* prob, void* stream, int* time_block,
                           int* tile_shape, double* ms_per_step);
 
+/* ---- learned warm start (SURVEY's warm-start extension; the paper starts GMRES from zero)
+ * A small convolutional network maps one frequency's forcing (and its frequency, as a second
+ * constant channel) to an initial iterate V_m^0.  L layers of 3 x 3 "same" convolutions
+ * (zero padding) with bias and ReLU after every layer but the last; in_channels inputs,
+ * `channels` hidden channels, one output.  Activations and weights in BF16, products summed in
+ * FP32 on the tensor cores (mma.sync); gradients, master weights and Adam state in FP32.
+ * Images are device float32 arrays [B][C][H][W] (x fastest).  Parameters, flat FP32: for each
+ * layer l, w_l[Cout][Cin][3][3] (cross-correlation: out[y][x] += w[dy][dx] in[y+dy-1][x+dx-1])
+ * then b_l[Cout].  The network owns its workspace, which grows with B * H * W. */
+typedef struct mfwh_cnn_s* mfwh_cnn_t;
+
+/* layers 2..16, channels and in_channels 1..32; He-normal weights from `seed`, zero biases. */
+mfwh_status mfwh_cnn_create(int layers, int channels, int in_channels, uint64_t seed,
+                            void* stream, mfwh_cnn_t* out);
+int64_t mfwh_cnn_param_count(mfwh_cnn_t c);
+/* Replace the parameters (host, param_count floats) and reset the Adam state.  Synchronous. */
+mfwh_status mfwh_cnn_set_params(mfwh_cnn_t c, const float* host, int64_t count);
+/* Copy parameters and, if grads_host != NULL, the gradients of the last training step.
+ * Synchronous. */
+mfwh_status mfwh_cnn_get_params(mfwh_cnn_t c, float* host, float* grads_host, int64_t count);
+/* y[B][1][H][W] (device) = network(x[B][in_channels][H][W]) (device).  Asynchronous. */
+mfwh_status mfwh_cnn_forward(mfwh_cnn_t c, const float* x, int B, int H, int W, float* y);
+/* One Adam step (learning rate lr, betas 0.9 / 0.999, eps 1e-8) on the mean squared error
+ * between network(x) and target[B][1][H][W] over the points where mask[H][W] is 1 (device
+ * arrays); *loss (host, may be NULL) receives the loss before the step.  Synchronous. */
+mfwh_status mfwh_cnn_train_step(mfwh_cnn_t c, const float* x, const float* target,
+                                const float* mask, int B, int H, int W, float lr, float* loss);
+void mfwh_cnn_destroy(mfwh_cnn_t c);
+
 /* Helmholtz residual r_h^{(m)} = max_int |f_m - (L_h + omega_m^2) v_m| / max_int |f_m|
  * (eq. errorAndResid, with +omega^2 as in eq. MultipleHelmholtz).
  * v: host or device [nf][points]; r_out: host [nf].  Synchronous. */

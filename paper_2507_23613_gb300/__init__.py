@@ -259,3 +259,59 @@ class Solver:
         tl = C.c_int64()
         _lib.check(_lib.load().mfwh_last_timing(self._handle, C.byref(ms), C.byref(sl), C.byref(tl)))
         return ms.value, sl.value, tl.value
+
+
+class CNN:
+    """The warm-start network (an mfwh_cnn_t): float32 device tensors [B][C][H][W] in and out."""
+
+    def __init__(self, layers=5, channels=32, in_channels=2, seed=0, stream=None):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self._h = C.c_void_p()
+        _lib.check(_lib.load().mfwh_cnn_create(int(layers), int(channels), int(in_channels),
+                                               int(seed), C.c_void_p(stream), C.byref(self._h)))
+        self.layers, self.channels, self.in_channels = layers, channels, in_channels
+        self.n_params = int(_lib.load().mfwh_cnn_param_count(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.load().mfwh_cnn_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        _lib.check(_lib.load().mfwh_cnn_set_params(self._h, a.ctypes.data_as(C.c_void_p), a.size))
+
+    def get_params(self, grads=False):
+        p = np.zeros(self.n_params, dtype=np.float32)
+        g = np.zeros(self.n_params, dtype=np.float32) if grads else None
+        _lib.check(_lib.load().mfwh_cnn_get_params(
+            self._h, p.ctypes.data_as(C.c_void_p), g.ctypes.data_as(C.c_void_p) if grads else None,
+            p.size))
+        return (p, g) if grads else p
+
+    @staticmethod
+    def _f32(t):
+        import torch
+        if t.dtype != torch.float32 or not t.is_contiguous() or not t.is_cuda:
+            raise TypeError("expected a contiguous float32 CUDA tensor")
+        return C.c_void_p(t.data_ptr())
+
+    def forward(self, x, y):
+        B, _, H, W = x.shape
+        _lib.check(_lib.load().mfwh_cnn_forward(self._h, self._f32(x), B, H, W, self._f32(y)))
+
+    def train_step(self, x, target, mask, lr):
+        B, _, H, W = x.shape
+        loss = C.c_float()
+        _lib.check(_lib.load().mfwh_cnn_train_step(self._h, self._f32(x), self._f32(target),
+                                                   self._f32(mask), B, H, W, float(lr),
+                                                   C.byref(loss)))
+        return loss.value

@@ -114,6 +114,15 @@ _SIGNATURES = {
                                    C.POINTER(C.c_void_p), C.POINTER(SolveInfo), _dp]),
     "mfwh_autotune": (C.c_int, [C.POINTER(Problem), C.c_void_p, C.POINTER(C.c_int),
                                 C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "mfwh_cnn_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_void_p,
+                                  C.POINTER(C.c_void_p)]),
+    "mfwh_cnn_param_count": (C.c_int64, [C.c_void_p]),
+    "mfwh_cnn_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "mfwh_cnn_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
+    "mfwh_cnn_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p]),
+    "mfwh_cnn_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                      C.c_int, C.c_int, C.c_float, C.POINTER(C.c_float)]),
+    "mfwh_cnn_destroy": (None, [C.c_void_p]),
     "mfwh_residual": (C.c_int, [C.c_void_p, C.c_void_p, _dp]),
     "mfwh_residual_noalloc": (C.c_int, [C.POINTER(Problem), C.c_void_p, C.c_void_p, _dp, C.c_void_p]),
     "mfwh_get_setup": (C.c_int, [C.c_void_p, C.POINTER(Setup)]),
