@@ -62,6 +62,15 @@ def parse():
                     help="GMRES(10) Arnoldi steps per problem in the batched workload")
     ap.add_argument("--batch-mem-gb", type=float, default=180.0,
                     help="device-memory budget of the batched workload")
+    ap.add_argument("--warm-start", action="store_true",
+                    help="train the warm-start network on MFWH solutions and compare GMRES from "
+                         "its prediction with GMRES from zero")
+    ap.add_argument("--ws-n", type=int, default=128, help="cells per axis of the warm-start workload")
+    ap.add_argument("--ws-train", type=int, default=683, help="training problems (6 samples each)")
+    ap.add_argument("--ws-test", type=int, default=24, help="held-out problems")
+    ap.add_argument("--ws-epochs", type=int, default=15)
+    ap.add_argument("--ws-gen-seconds", type=float, default=300.0,
+                    help="time limit of the training-data generation")
     ap.add_argument("--cube", action="store_true",
                     help="run the 3D two-layer workload (257^3, N_f = 4, GMRES(15) cycle)")
     ap.add_argument("--no-clocks", action="store_true",
@@ -472,6 +481,120 @@ def run_cube(args):
     print(json.dumps(out), flush=True)
 
 
+def run_warm_start(args):
+    """Learned warm start: MFWH-converged FP64 solutions of seeded problems train the network
+    (inputs f_m / max|f_m| and omega_m / 45, target the shape V_m / max|V_m|, amplitude fitted to
+    the Helmholtz residual at prediction time); held-out problems are then solved by GMRES to
+    1e-6 from zero and from the network's prediction."""
+    import torch
+    import paper_2507_23613_gb300 as M
+    from paper_2507_23613_gb300 import _lib, build, inputs
+    torch.cuda.set_device(0)
+    build.build()
+    M._lib.load()
+    restart, omega_scale, group = 800, 45.0, 48
+    n = args.ws_n
+    H = W = n + 1
+    # training data from batched FP64 solves
+    xs, ts, gen_t0, seed, solved, iters = [], [], time.perf_counter(), args.seed + 9000, 0, []
+    while solved < args.ws_train and time.perf_counter() - gen_t0 < args.ws_gen_seconds:
+        wls = []
+        while len(wls) < min(group, args.ws_train - solved):
+            wl = inputs.warm_start_workload(seed, n=n)
+            seed += 1
+            try:
+                M.plan(M.make_problem(wl.n, wl.length, wl.omega, n_p=wl.n_p, cfl=wl.cfl)[0])
+            except M.MfwhError:
+                continue
+            wls.append(wl)
+        streams = [torch.cuda.Stream() for _ in wls]
+        sol = [M.Solver(wl.n, wl.length, wl.omega, torch.from_numpy(wl.forcing).cuda(),
+                        stream=st.cuda_stream, n_p=wl.n_p, cfl=wl.cfl) for wl, st in zip(wls, streams)]
+        for s in sol:
+            s.set_graphs(True)
+        vs = [torch.zeros(wl.forcing.shape, dtype=torch.float64, device="cuda") for wl in wls]
+        torch.cuda.synchronize()
+        _, infos, _ = M.solve_batch(sol, vs, restart=restart, tol=1e-8, max_iters=restart,
+                                    raise_on_error=False)
+        for s, v, info in zip(sol, vs, infos):
+            if info["rel_residual"] < 1e-7:
+                x = torch.empty((s.nf, 2, H, W), dtype=torch.float32, device="cuda")
+                t = torch.empty((s.nf, 1, H, W), dtype=torch.float32, device="cuda")
+                s.warm_start_data(v, x, t, omega_scale)
+                xs.append(x)
+                ts.append(t)
+                iters.append(info["iterations"])
+            s.close()
+        solved += len(wls)
+    gen_s = time.perf_counter() - gen_t0
+    X = torch.cat(xs)
+    T = torch.cat(ts)
+    mask = torch.ones((H, W), dtype=torch.float32, device="cuda")
+    mask[0, :] = mask[-1, :] = 0
+    mask[:, 0] = mask[:, -1] = 0
+    # training
+    net = M.CNN(layers=5, channels=32, in_channels=2, seed=args.seed)
+    S, bs = X.shape[0], 32
+    gen = torch.Generator().manual_seed(args.seed)
+    tr_t0 = time.perf_counter()
+    losses = []
+    for ep in range(args.ws_epochs):
+        lr = 1e-3 if ep < 0.7 * args.ws_epochs else 2e-4
+        perm = torch.randperm(S, generator=gen).cuda()
+        ep_loss = []
+        for i in range(0, S - bs + 1, bs):
+            idx = perm[i:i + bs]
+            ep_loss.append(net.train_step(X[idx].contiguous(), T[idx].contiguous(), mask, lr))
+        losses.append(float(np.mean(ep_loss)))
+    train_s = time.perf_counter() - tr_t0
+    # held-out comparison
+    rows = []
+    for k in range(args.ws_test):
+        wl = inputs.warm_start_workload(args.seed + 50000 + k, n=n)
+        try:
+            s = M.Solver(wl.n, wl.length, wl.omega, torch.from_numpy(wl.forcing).cuda(),
+                         n_p=wl.n_p, cfl=wl.cfl)
+        except M.MfwhError:
+            continue
+        res = {}
+        for mode in ("zero", "cnn"):
+            v = torch.zeros(wl.forcing.shape, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            kept, ratio0 = (False, 1.0)
+            if mode == "cnn":
+                kept, ratio0 = s.warm_start(net, v, omega_scale)
+            info = s.solve_gmres(v, restart=restart, tol=1e-6, max_iters=restart,
+                                 raise_on_error=False)
+            res[mode] = {"seconds": time.perf_counter() - t0, "iterations": info["iterations"],
+                         "kept": kept, "start_residual_ratio": float(ratio0),
+                         "rel_residual": info["rel_residual"]}
+        rows.append(res)
+        s.close()
+    med = lambda key, mode: float(np.median([r[mode][key] for r in rows]))
+    line = {"metric": "learned warm start: GMRES iterations and time to 1e-6, CNN start vs zero",
+            "impl": "native", "unit": "iterations",
+            "value": med("iterations", "cnn"), "zero_start_iterations": med("iterations", "zero"),
+            "cnn_seconds_median": round(med("seconds", "cnn"), 4),
+            "zero_seconds_median": round(med("seconds", "zero"), 4),
+            "kept_fraction": float(np.mean([r["cnn"]["kept"] for r in rows])),
+            "cnn_start_residual_ratio_median": med("start_residual_ratio", "cnn"),
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "dtype": "bf16 network (fp32 accumulate), f64 MFWH",
+            "config": {"workload": f"warm_start_square{H}_nf6_omega15-45_np2",
+                       "network": "5 layers, 3x3, 32 channels, inputs (f/max|f|, omega/45)",
+                       "training_samples": int(S), "training_problems": solved,
+                       "training_solve_iterations_median": float(np.median(iters)),
+                       "epochs": args.ws_epochs, "batch": bs,
+                       "loss_first_last_epoch": [losses[0], losses[-1]],
+                       "generate_s": round(gen_s, 1), "train_s": round(train_s, 1),
+                       "test_problems": len(rows)},
+            "per_problem": [{m: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
+                                 for kk, vv in r[m].items()} for m in r} for r in rows]}
+    print(json.dumps(line), flush=True)
+    net.close()
+
+
 def workload_config(wl, n_t):
     return {"workload": f"square{wl.n[0] + 1}x{wl.n[1] + 1}_nf{wl.nf}_np{wl.n_p}_gmres{RESTART}_cycle",
             "step": "one GMRES(20) cycle from zero: b = Pi(0), 20 Arnoldi steps, update, residual check",
@@ -490,6 +613,8 @@ def main():
         return run_batched(args) if rank == 0 else None
     if args.cube:
         return run_cube(args) if rank == 0 else None
+    if args.warm_start:
+        return run_warm_start(args) if rank == 0 else None
 
     import torch
     import paper_2507_23613_gb300 as M

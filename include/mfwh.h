@@ -278,6 +278,23 @@ mfwh_status mfwh_cnn_train_step(mfwh_cnn_t c, const float* x, const float* targe
                                 const float* mask, int B, int H, int W, float lr, float* loss);
 void mfwh_cnn_destroy(mfwh_cnn_t c);
 
+/* Training pairs of the warm start from a solved 2D problem: for each frequency m, inputs
+ * x_out[m][0] = f_m / max|f_m| and x_out[m][1] = omega_m / omega_scale (device float32
+ * [nf][2][ny+1][nx+1]) and target t_out[m] = V_m / max|V_m|, the shape of the solution (device
+ * float32 [nf][ny+1][nx+1]), from the solution v (device [nf][points]).  Synchronous. */
+mfwh_status mfwh_warm_start_data(mfwh_handle_t h, double omega_scale, const double* v,
+                                 float* x_out, float* t_out);
+/* Initial iterate for GMRES from the network (2D): V_m^0 = alpha_m phi_m, where phi_m is the
+ * network's output on the inputs above (0 on the boundary) and alpha_m = <A phi_m, f_m> /
+ * <A phi_m, A phi_m> (A = L_h + omega_m^2, interior points) minimises the L2 Helmholtz
+ * residual, computed in FP64 on the device.  It is kept only if it lowers GMRES's initial
+ * residual, ||b - (V^0 - S V^0)|| < ||b|| with b = Pi(0) (two applications of Pi); otherwise v
+ * is set to 0 and the call returns MFWH_ERR_NOT_CONVERGED.  *ratio_out (may be NULL) receives
+ * ||b - (V^0 - S V^0)|| / ||b|| of the returned start (1 for zero).  v: host or device
+ * [nf][points].  Allocates temporary device buffers.  Synchronous. */
+mfwh_status mfwh_warm_start(mfwh_handle_t h, mfwh_cnn_t net, double omega_scale, double* v,
+                            double* ratio_out);
+
 /* Helmholtz residual r_h^{(m)} = max_int |f_m - (L_h + omega_m^2) v_m| / max_int |f_m|
  * (eq. errorAndResid, with +omega^2 as in eq. MultipleHelmholtz).
  * v: host or device [nf][points]; r_out: host [nf].  Synchronous. */

@@ -245,6 +245,23 @@ class Solver:
             "history": hist[:info.history_len].copy(),
         }
 
+    def warm_start_data(self, v, x_out, t_out, omega_scale=45.0):
+        """Network inputs [nf][2][H][W] and targets [nf][1][H][W] (float32 device tensors)
+        from a solution v of this problem (mfwh_warm_start_data)."""
+        _lib.check(_lib.load().mfwh_warm_start_data(self._handle, float(omega_scale), _as_ptr(v),
+                                                    C.c_void_p(x_out.data_ptr()),
+                                                    C.c_void_p(t_out.data_ptr())))
+
+    def warm_start(self, net, v, omega_scale=45.0):
+        """Write the network's initial iterate into v (mfwh_warm_start); returns (kept, ratio)
+        with ratio = ||b - (v - S v)|| / ||b|| of the returned start."""
+        ratio = C.c_double()
+        st = _lib.load().mfwh_warm_start(self._handle, net._h, float(omega_scale), _as_ptr(v),
+                                         C.byref(ratio))
+        if st not in (_lib.OK, _lib.ERR_NOT_CONVERGED):
+            _lib.check(st)
+        return st == _lib.OK, ratio.value
+
     def set_graphs(self, enable=True):
         _lib.check(_lib.load().mfwh_set_graphs(self._handle, int(bool(enable))))
 

@@ -123,6 +123,10 @@ _SIGNATURES = {
     "mfwh_cnn_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                       C.c_int, C.c_int, C.c_float, C.POINTER(C.c_float)]),
     "mfwh_cnn_destroy": (None, [C.c_void_p]),
+    "mfwh_warm_start_data": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p,
+                                       C.c_void_p]),
+    "mfwh_warm_start": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
+                                  C.POINTER(C.c_double)]),
     "mfwh_residual": (C.c_int, [C.c_void_p, C.c_void_p, _dp]),
     "mfwh_residual_noalloc": (C.c_int, [C.POINTER(Problem), C.c_void_p, C.c_void_p, _dp, C.c_void_p]),
     "mfwh_get_setup": (C.c_int, [C.c_void_p, C.POINTER(Setup)]),

@@ -1206,4 +1206,83 @@ mfwh_status mfwh_autotune(const mfwh_problem* prob, void* stream, int* time_bloc
   return MFWH_OK;
 }
 
+mfwh_status mfwh_warm_start_data(mfwh_handle_t h, double omega_scale, const double* v,
+                                 float* x_out, float* t_out) {
+  if (!h || !v || !x_out || !t_out || !(omega_scale > 0.0))
+    return fail(MFWH_ERR_INVALID_ARG, "bad warm-start data arguments");
+  if (h->plan.dim != 2) return fail(MFWH_ERR_INVALID_ARG, "the warm start is for 2D grids");
+  if (!is_device_ptr(v) || !is_device_ptr(x_out) || !is_device_ptr(t_out))
+    return fail(MFWH_ERR_INVALID_ARG, "mfwh_warm_start_data takes device pointers");
+  double omega[MFWH_MAX_NF];
+  for (int m = 0; m < h->nf; ++m) omega[m] = std::sqrt(h->omega2[m]);
+  mfwh_status st = cnn_ws_data(h->f, v, omega, h->nf, (int)h->geom.ny + 1, (int)h->geom.nx + 1,
+                               omega_scale, x_out, t_out, h->res_out, h->stream);
+  if (st != MFWH_OK) return st;
+  CK(cudaStreamSynchronize(h->stream));
+  return MFWH_OK;
+}
+
+mfwh_status mfwh_warm_start(mfwh_handle_t h, mfwh_cnn_t net, double omega_scale, double* v,
+                            double* ratio_out) {
+  if (!h || !net || !v || !(omega_scale > 0.0))
+    return fail(MFWH_ERR_INVALID_ARG, "bad warm-start arguments");
+  if (h->plan.dim != 2) return fail(MFWH_ERR_INVALID_ARG, "the warm start is for 2D grids");
+  double* x = nullptr;
+  bool on_dev = false;
+  mfwh_status st = stage_in(h, v, &x, &on_dev);
+  if (st != MFWH_OK) return st;
+  double omega[MFWH_MAX_NF];
+  for (int m = 0; m < h->nf; ++m) omega[m] = std::sqrt(h->omega2[m]);
+  st = cnn_ws_predict(net, h->f, omega, h->nf, (int)h->geom.ny + 1, (int)h->geom.nx + 1,
+                      omega_scale, x, h->stream);
+  if (st != MFWH_OK) return st;
+  // Amplitude of each predicted shape phi_m: alpha_m = <A phi_m, f_m> / <A phi_m, A phi_m>
+  // with A = L_h + omega_m^2 minimises the L2 Helmholtz residual ||f_m - alpha A phi_m||.
+  if (!h->vec_r) CK(cudaMalloc(&h->vec_r, sizeof(double) * h->N));
+  if (!h->vec_e) CK(cudaMalloc(&h->vec_e, sizeof(double) * h->N));
+  CK(cudaMemsetAsync(h->vec_e, 0, sizeof(double) * h->N, h->stream));
+  // defect of phi against a zero forcing is -A phi at interior points, 0 on the boundary
+  launch_residual_field(h->nf, h->geom, x, h->vec_e, h->omega2, h->plan.c2_lo, h->plan.c2_hi,
+                        h->inv_h2, h->vec_r, h->stream);
+  launch_axpby(h->vec_r, 0.0, h->vec_r, -1.0, h->N, h->stream);
+  h->total_launches += 2;
+  const int64_t P = h->P;
+  for (int m = 0; m < h->nf; ++m) {
+    double af = 0.0, aa = 0.0;
+    const double* Am = h->vec_r + m * P;
+    launch_multidot(Am, P, 1, h->f + m * P, P, h->dot_partial, h->dot_out, h->stream);
+    CK(cudaMemcpyAsync(h->pinned, h->dot_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    af = h->pinned[0];
+    launch_multidot(Am, P, 1, Am, P, h->dot_partial, h->dot_out, h->stream);
+    CK(cudaMemcpyAsync(h->pinned, h->dot_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    aa = h->pinned[0];
+    const double alpha = (aa > 0.0 && std::isfinite(af / aa)) ? af / aa : 0.0;
+    launch_axpby(x + m * P, alpha, x + m * P, 0.0, P, h->stream);
+  }
+  // Keep the prediction only if it lowers GMRES's initial residual: ||b - (x - S x)|| < ||b||
+  // with b = Pi(0) (two applications of Pi, in the handle's precision).
+  st = apply_pi(h, nullptr, h->vec_b, 1, nullptr);
+  if (st != MFWH_OK) return st;
+  st = apply_pi(h, x, h->vec_e, 0, x);                       // vec_e = x - S x
+  if (st != MFWH_OK) return st;
+  launch_axpby(h->vec_e, 1.0, h->vec_b, -1.0, h->N, h->stream);   // b - (x - S x)
+  h->total_launches++;
+  double bb = 0.0, rr = 0.0;
+  st = dots(h, h->vec_b, 1, h->vec_b, &bb);
+  if (st == MFWH_OK) st = dots(h, h->vec_e, 1, h->vec_e, &rr);
+  if (st != MFWH_OK) return st;
+  double ratio = bb > 0.0 ? std::sqrt(rr / bb) : 1.0;
+  const bool better = std::isfinite(ratio) && ratio < 1.0;
+  if (!better) {
+    launch_axpby(x, 0.0, x, 0.0, h->N, h->stream);
+    ratio = 1.0;
+  }
+  if (ratio_out) *ratio_out = ratio;
+  if (!on_dev) CK(cudaMemcpyAsync(v, x, sizeof(double) * h->N, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return better ? MFWH_OK : MFWH_ERR_NOT_CONVERGED;
+}
+
 }  // extern "C"

@@ -204,6 +204,57 @@ __global__ void k_pack(const float* __restrict__ w, int Cin, int Cout, int Kp, i
   }
 }
 
+// ---- features and targets of the warm start (2D grids, H = ny + 1 rows, W = nx + 1) ----
+// For frequency m: input channels x[m][0] = f_m / max|f_m| and x[m][1] = omega_m / omega_scale;
+// target t[m] = V_m / max|V_m| (the shape of the solution); the prediction is that shape with
+// 0 on the boundary, its amplitude fitted afterwards to the Helmholtz residual.
+
+__global__ void k_ws_scale(const double* __restrict__ f, int64_t P, double* __restrict__ scale) {
+  const int m = blockIdx.x;
+  double mx = 0.0;
+  for (int64_t i = threadIdx.x; i < P; i += blockDim.x) mx = fmax(mx, fabs(f[m * P + i]));
+  __shared__ double red[8];
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < 8; ++w) v = fmax(v, red[w]);
+    scale[m] = v > 0.0 ? v : 1.0;
+  }
+}
+
+struct WsFreq {
+  double omega[MFWH_MAX_NF];
+};
+
+__global__ void k_ws_features(const double* __restrict__ f, const double* __restrict__ v,
+                              const double* __restrict__ fscale, const double* __restrict__ vscale,
+                              const WsFreq fr, int nf, int64_t P, double omega_scale,
+                              float* __restrict__ x, float* __restrict__ t) {
+  const int64_t n = (int64_t)nf * P;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int m = (int)(e / P);
+    const int64_t i = e - (int64_t)m * P;
+    x[((int64_t)m * 2) * P + i] = (float)(f[e] / fscale[m]);
+    x[((int64_t)m * 2 + 1) * P + i] = (float)(fr.omega[m] / omega_scale);
+    if (t) t[e] = (float)(v[e] / vscale[m]);
+  }
+}
+
+__global__ void k_ws_output(const float* __restrict__ y, int nf, int H, int W,
+                            double* __restrict__ v) {
+  const int64_t P = (int64_t)H * W, n = (int64_t)nf * P;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % P;
+    const int xx = (int)(i % W), yy = (int)(i / W);
+    const bool interior = xx > 0 && xx < W - 1 && yy > 0 && yy < H - 1;
+    v[e] = interior ? (double)y[e] : 0.0;
+  }
+}
+
 mfwh_status cnn_fail(mfwh_status st, const std::string& m) {
   set_error(m);
   return st;
@@ -472,3 +523,54 @@ void mfwh_cnn_destroy(mfwh_cnn_t c) {
 }
 
 }  // extern "C"
+
+namespace mfwh {
+
+// Training pairs of one solved 2D problem (device arrays; see the feature definition above).
+// scale: device scratch of 2 nf doubles.
+mfwh_status cnn_ws_data(const double* f, const double* v, const double* omega, int nf, int H,
+                        int W, double omega_scale, float* x, float* t, double* scale,
+                        cudaStream_t st) {
+  WsFreq fr{};
+  for (int m = 0; m < nf; ++m) fr.omega[m] = omega[m];
+  const int64_t P = (int64_t)H * W;
+  k_ws_scale<<<nf, 256, 0, st>>>(f, P, scale);
+  if (v) k_ws_scale<<<nf, 256, 0, st>>>(v, P, scale + nf);
+  k_ws_features<<<256, 256, 0, st>>>(f, v, scale, scale + nf, fr, nf, P, omega_scale, x, t);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? MFWH_OK : cnn_fail(MFWH_ERR_CUDA, cudaGetErrorString(e));
+}
+
+// The network's solution shape for every frequency of a 2D problem (0 on the boundary).
+mfwh_status cnn_ws_predict(mfwh_cnn_t c, const double* f, const double* omega, int nf, int H,
+                           int W, double omega_scale, double* v, cudaStream_t st) {
+  if (c->in_channels != 2) return cnn_fail(MFWH_ERR_INVALID_ARG, "warm start needs 2 inputs");
+  const int64_t P = (int64_t)H * W;
+  float* x = nullptr;
+  float* y = nullptr;
+  double* scale = nullptr;
+  mfwh_status res = MFWH_OK;
+  if (cudaMalloc(&x, sizeof(float) * 2 * nf * P) != cudaSuccess ||
+      cudaMalloc(&y, sizeof(float) * nf * P) != cudaSuccess ||
+      cudaMalloc(&scale, sizeof(double) * 2 * nf) != cudaSuccess) {
+    res = cnn_fail(MFWH_ERR_NOMEM, "warm start: allocation failed");
+  } else {
+    res = cnn_ws_data(f, nullptr, omega, nf, H, W, omega_scale, x, nullptr, scale, st);
+    cudaStream_t keep = c->stream;
+    c->stream = st;
+    if (res == MFWH_OK) res = mfwh_cnn_forward(c, x, nf, H, W, y);
+    c->stream = keep;
+    if (res == MFWH_OK) {
+      k_ws_output<<<256, 256, 0, st>>>(y, nf, H, W, v);
+      if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+        res = cnn_fail(MFWH_ERR_CUDA, "warm start: output kernel failed");
+    }
+  }
+  cudaStreamSynchronize(st);
+  if (x) cudaFree(x);
+  if (y) cudaFree(y);
+  if (scale) cudaFree(scale);
+  return res;
+}
+
+}  // namespace mfwh

@@ -154,4 +154,14 @@ int multi_axpy_launches(int k);
 // y = a x + b y
 void launch_axpby(double* y, double a, const double* x, double b, int64_t N, cudaStream_t st);
 
+// ---- warm start (cnn.cu) -----------------------------------------------------------
+// Training pairs of a solved 2D problem: x [nf][2][H][W], t [nf][H][W] (t may be null with
+// v null); scale: device scratch of 2 nf doubles (max |f_m|, max |V_m|).
+mfwh_status cnn_ws_data(const double* f, const double* v, const double* omega, int nf, int H,
+                        int W, double omega_scale, float* x, float* t, double* scale,
+                        cudaStream_t st);
+// Solution shapes [nf][H][W] (device) from the network; boundary values 0.  Synchronous.
+mfwh_status cnn_ws_predict(mfwh_cnn_t c, const double* f, const double* omega, int nf, int H,
+                           int W, double omega_scale, double* v, cudaStream_t st);
+
 }  // namespace mfwh

@@ -148,3 +148,17 @@ def paper_three_frequency(n=128):
     centres = ((0.6, 0.45), (0.4, 0.5), (0.55, 0.5))
     forcing = np.stack([gaussian(coords, c, a, 15.0 ** 2) for a, c in zip(amps, centres)])
     return Workload(f"paper3freq_square{n}", dims, (1.0, 1.0), omega, forcing, 1.0, 0.5, 2)
+
+
+def warm_start_workload(seed, n=128, nf=6):
+    """One problem of the learned-warm-start workload: unit square with n x n cells, N_f
+    frequencies uniform in [15, 45] (adjacent gaps >= 1.5), 1-4 Gaussian sources per frequency
+    with b uniform in [200, 400], c = 1, CFL 0.5, N_p = 2."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    omega = draw_frequencies(rng, nf, 15.0, 45.0, min_gap=1.5)
+    b = float(rng.uniform(200.0, 400.0))
+    k = int(rng.integers(1, 5))
+    wl = gaussian_workload(f"ws{seed}_n{n + 1}_nf{nf}", (n, n), nf, omega, b,
+                           int(rng.integers(0, 2**31)), sources_per_freq=k)
+    wl.n_p = 2
+    return wl

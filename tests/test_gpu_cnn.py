@@ -93,3 +93,66 @@ def test_cnn_training_reduces_the_loss_and_rejects_bad_arguments():
         M.CNN(layers=1)
     with pytest.raises(_lib.MfwhError):
         net.set_params(np.zeros(3, dtype=np.float32))
+
+
+def test_warm_start_features_targets_and_prediction():
+    """mfwh_warm_start_data builds x = (f_m / max|f_m|, omega_m / scale) and t = V_m omega_m^2 /
+    max|f_m|; mfwh_warm_start maps the network output back, keeping it only if it lowers the
+    Helmholtz residual of every frequency (else V^0 = 0)."""
+    from paper_2507_23613_gb300 import inputs
+    wl = inputs.gaussian_workload("ws", (40, 36), 3, [16.0, 24.0, 33.0], 300.0, 7,
+                                  sources_per_freq=2)
+    wl.n_p = 2
+    s = M.Solver(wl.n, wl.length, wl.omega, torch.from_numpy(wl.forcing).cuda(), n_p=2)
+    H, W = wl.n[1] + 1, wl.n[0] + 1
+    v = torch.from_numpy(np.random.default_rng(3).normal(size=wl.forcing.shape)).cuda()
+    x = torch.empty((wl.nf, 2, H, W), dtype=torch.float32, device="cuda")
+    t = torch.empty((wl.nf, 1, H, W), dtype=torch.float32, device="cuda")
+    s.warm_start_data(v, x, t, omega_scale=45.0)
+    f = wl.forcing
+    sc = np.max(np.abs(f.reshape(wl.nf, -1)), axis=1)
+    np.testing.assert_allclose(x[:, 0].cpu().numpy(), f / sc[:, None, None], rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(x[:, 1].cpu().numpy(),
+                               np.broadcast_to((wl.omega / 45.0)[:, None, None], (wl.nf, H, W)),
+                               rtol=1e-6)
+    vn = v.cpu().numpy()
+    want_t = vn / np.max(np.abs(vn.reshape(wl.nf, -1)), axis=1)[:, None, None]
+    np.testing.assert_allclose(t[:, 0].cpu().numpy(), want_t, rtol=1e-6, atol=1e-7)
+    net = M.CNN(layers=3, channels=8, in_channels=2, seed=4)
+    y = torch.empty((wl.nf, 1, H, W), dtype=torch.float32, device="cuda")
+    net.forward(x, y)
+    torch.cuda.synchronize()
+    shape = y[:, 0].cpu().numpy().astype(np.float64)
+    shape[:, [0, -1], :] = 0.0
+    shape[:, :, [0, -1]] = 0.0
+    # the amplitude that minimises the L2 Helmholtz residual, from the oracle's operator
+    from oracle import wave as Wv
+    g = Wv.Grid(wl.n, wl.length)
+    inner = g.interior()
+    alpha = []
+    for m in range(wl.nf):
+        Aphi = Wv.laplacian(shape[m], g, 1.0) + wl.omega[m] ** 2 * shape[m]
+        Aphi[[0, -1], :] = 0.0                      # interior points only
+        Aphi[:, [0, -1]] = 0.0
+        alpha.append(np.sum(Aphi * f[m]) / np.sum(Aphi * Aphi))
+    pred = shape * np.array(alpha)[:, None, None]
+    v0 = torch.zeros(wl.forcing.shape, dtype=torch.float64, device="cuda")
+    kept, ratio = s.warm_start(net, v0, omega_scale=45.0)
+    got = v0.cpu().numpy()
+    # the kept/rejected decision follows ||b - (v - S v)|| / ||b|| of the prediction
+    b = torch.empty_like(v0)
+    s.apply_Pi(torch.zeros_like(v0), b, forced=True)
+    pv = torch.from_numpy(pred).cuda()
+    spv = torch.empty_like(v0)
+    s.apply_Pi(pv, spv, forced=False)
+    want_ratio = float(torch.linalg.norm(b - (pv - spv)) / torch.linalg.norm(b))
+    assert kept == (want_ratio < 1.0)
+    if kept:
+        np.testing.assert_allclose(got, pred, rtol=1e-5, atol=1e-6 * np.max(np.abs(pred)))
+        assert ratio == pytest.approx(want_ratio, rel=1e-6)
+    else:
+        assert not np.any(got) and ratio == 1.0
+    # the fitted amplitude never raises the L2 residual above that of the zero start
+    for m in range(wl.nf):
+        Aphi = Wv.laplacian(pred[m], g, 1.0) + wl.omega[m] ** 2 * pred[m]
+        assert np.linalg.norm((f[m] - Aphi)[inner]) <= np.linalg.norm(f[m][inner]) * (1 + 1e-12)
