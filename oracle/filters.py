@@ -55,8 +55,8 @@ def implicit_time_step(omega1, omega_max, n_p, steps_per_period=10, scheme=TRAPE
 
     Reading: N_t = ceil(steps_per_period * N_p * omega_Nf / omega_1) steps (10 per
     shortest period over N_p longest periods); dt solves omega~_1 dt = theta with
-    theta = 2 pi N_p / N_t, i.e. (omega_1 dt)^2 = (1 - cos theta) / (beta/2 + alpha cos theta).
-    Used only to reproduce the paper's printed optimiser cases.
+    theta = 2 pi N_p / N_t, i.e. (omega_1 dt)^2 = (1 - cos theta) / (beta/2 + alpha cos theta),
+    so that the adjusted final time N_p 2 pi / omega~_1 is N_t dt.
     """
     alpha, beta = scheme
     n_t = int(math.ceil(steps_per_period * n_p * omega_max / omega1 - 1e-12))
@@ -302,21 +302,34 @@ class Setup:
     w: np.ndarray            # (N_t+1, N_f) filter weights
     B: np.ndarray            # (N_f, N_f)
     cond_M: float = float("nan")   # conditioning of Algorithm 2's least-squares matrix (optimised mode)
+    scheme: tuple = EXPLICIT       # (alpha, beta) of eq. WaveSchemeA
 
 
 def make_setup(omega, h, c_max, cfl=0.5, n_p=1, filter_mode=FILTER_OPTIMIZED,
-               user_params=None, n_delta=20, c_delta=2.0, order=2):
-    """Set-up of Algorithm 1 (its first two lines) for the explicit scheme.
+               user_params=None, n_delta=20, c_delta=2.0, order=2,
+               time_stepping="explicit", steps_per_period=10):
+    """Set-up of Algorithm 1 (its first two lines).
 
-    Time step per explicit_time_step; omega~ per eq. omegaImplicit with
-    (alpha, beta) = (0, 1); N_{p,m} and T~_{f,m} per eq. TbarDef using omega~;
-    sigma per eq. DefNI; parameters optimised (Algorithm 2 in its discrete form
-    with inputs omega~, N_p, N_t, no further adjustment) or traditional
-    (eq. origParamAdjust) or given; then w and B.
+    Explicit scheme (alpha, beta) = (0, 1): time step per explicit_time_step.
+    Implicit trapezoidal scheme (alpha, beta) = (1/2, 0) (time_stepping =
+    "implicit"): time step per implicit_time_step with steps_per_period steps over
+    the shortest period.  Then omega~ per eq. omegaImplicit with the scheme's
+    (alpha, beta); N_{p,m} and T~_{f,m} per eq. TbarDef using omega~; sigma per
+    eq. DefNI; parameters optimised (Algorithm 2 in its discrete form with inputs
+    omega~, N_p, N_t, no further adjustment) or traditional (eq. origParamAdjust)
+    or given; then w and B.
     """
     omega = np.asarray(omega, dtype=np.float64)
-    dt, n_t = explicit_time_step(h, c_max, cfl, float(omega[0]), n_p, order)
-    omega_t = adjusted_frequency(omega, dt, EXPLICIT)
+    if time_stepping == "implicit":
+        scheme = TRAPEZOIDAL
+        dt, n_t = implicit_time_step(float(omega[0]), float(omega[-1]), n_p,
+                                     steps_per_period, scheme)
+    elif time_stepping == "explicit":
+        scheme = EXPLICIT
+        dt, n_t = explicit_time_step(h, c_max, cfl, float(omega[0]), n_p, order)
+    else:
+        raise ValueError("time_stepping must be 'explicit' or 'implicit'")
+    omega_t = adjusted_frequency(omega, dt, scheme)
     n_pm, t_fm, _ = period_counts(omega_t, n_p)
     sigma = trapezoid_weights(n_t, dt, t_fm)
     cond_m = float("nan")
@@ -329,4 +342,4 @@ def make_setup(omega, h, c_max, cfl=0.5, n_p=1, filter_mode=FILTER_OPTIMIZED,
         params = np.asarray(user_params, dtype=np.float64).reshape(omega.size, 3)
     w = filter_weights(omega_t, dt, n_t, sigma, t_fm, params)
     B = filter_matrix(w, omega_t, dt)
-    return Setup(dt, n_t, omega, omega_t, n_pm, t_fm, sigma, params, w, B, cond_m)
+    return Setup(dt, n_t, omega, omega_t, n_pm, t_fm, sigma, params, w, B, cond_m, scheme)

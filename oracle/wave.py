@@ -98,21 +98,26 @@ class Problem:
 
 def make_problem(grid, omega, forcing, c2=1.0, cfl=0.5, n_p=1,
                  filter_mode=filters.FILTER_OPTIMIZED, user_params=None,
-                 n_delta=20, c_delta=2.0, order=2, explicit_filter=False):
+                 n_delta=20, c_delta=2.0, order=2, explicit_filter=False,
+                 time_stepping="explicit", steps_per_period=10):
     c_max = math.sqrt(float(np.max(c2)))
     setup = filters.make_setup(omega, grid.h, c_max, cfl, n_p, filter_mode,
-                               user_params, n_delta, c_delta, order)
+                               user_params, n_delta, c_delta, order,
+                               time_stepping, steps_per_period)
     return Problem(grid, np.asarray(forcing, dtype=np.float64), c2, setup, order, explicit_filter)
 
 
 def composite_forcing(prob, n):
-    """F^n = sum_m f^{(m)} cos(omega~_m t^n) (eq. WaveSchemeForcing with alpha=0, beta=1), interior only."""
+    """F^n = sum_m f^{(m)} cos(omega~_m t^n) (beta + 2 alpha cos(omega~_m dt))
+    (eq. WaveSchemeForcing), interior only; the last factor is 1 for the explicit scheme."""
     s = prob.setup
+    alpha, beta = s.scheme
     t = n * s.dt
     F = np.zeros(prob.grid.shape)
     inner = prob.grid.interior()
     for m in range(prob.nf):
-        F[inner] += prob.forcing[m][inner] * math.cos(s.omega_t[m] * t)
+        factor = beta + 2.0 * alpha * math.cos(s.omega_t[m] * s.dt)
+        F[inner] += prob.forcing[m][inner] * math.cos(s.omega_t[m] * t) * factor
     return F
 
 
@@ -128,6 +133,8 @@ def apply_Pi(prob, V, forced=True):
     With prob.explicit_filter the update is the explicit filter of the footnote to
     eq. filterII: B_mm V_m^{k+1} = q_m - sum_{j != m} B_mj V_j^k.
     """
+    if prob.setup.scheme != filters.EXPLICIT:
+        return _apply_Pi_implicit(prob, V, forced)
     s = prob.setup
     g = prob.grid
     inner = g.interior()
@@ -157,6 +164,66 @@ def apply_Pi(prob, V, forced=True):
             q[m] += s.w[n + 1, m] * W_next
         W_prev, W_cur = W_cur, W_next
 
+    return _filter_update(prob, q, V)
+
+
+def _apply_Pi_implicit(prob, V, forced=True):
+    """One application of the MFWH map with an implicit scheme (alpha > 0), eq. WaveScheme.
+
+    With A = I - alpha dt^2 L_h on the interior unknowns (Dirichlet data zero):
+      first step (eq. implicitFirstStep):
+        A W^1 = W^0 + (beta/2) dt^2 L_h W^0 - (dt^2/2) F^0,
+      later steps (eq. WaveSchemeA solved for W^{n+1}):
+        A W^{n+1} = 2 W^n - W^{n-1} + dt^2 L_h (beta W^n + alpha W^{n-1}) - dt^2 F^n,
+    for n = 1..N_t-1, with F^n of eq. WaveSchemeForcing.  Each A-solve is a sparse
+    LU solve (scipy's splu of the assembled matrix), which is the definition of the
+    step; the filter sums and the update are those of the explicit map.
+    """
+    s = prob.setup
+    g = prob.grid
+    inner = g.interior()
+    alpha, beta = s.scheme
+    dt2 = s.dt * s.dt
+    L = laplacian_matrix(g, prob.c2, prob.order).tocsc()
+    A = (sp.identity(L.shape[0], format="csc") - alpha * dt2 * L).tocsc()
+    lu = spla.splu(A)
+
+    def solve(rhs_grid):
+        out = np.zeros(g.shape)
+        out[inner] = lu.solve(rhs_grid[inner].ravel()).reshape(out[inner].shape)
+        return out
+
+    def F(n):
+        return composite_forcing(prob, n) if forced else np.zeros(g.shape)
+
+    def Lh(W):
+        return laplacian(W, g, prob.c2, prob.order)
+
+    W0 = np.sum(V, axis=0).copy()
+    zero_boundary(W0, g)
+    q = np.zeros((prob.nf,) + g.shape)
+    for m in range(prob.nf):
+        q[m] += s.w[0, m] * W0
+
+    W1 = solve(W0 + 0.5 * beta * dt2 * Lh(W0) - 0.5 * dt2 * F(0))
+    for m in range(prob.nf):
+        q[m] += s.w[1, m] * W1
+
+    W_prev, W_cur = W0, W1
+    for n in range(1, s.n_t):
+        W_next = solve(2.0 * W_cur - W_prev + dt2 * Lh(beta * W_cur + alpha * W_prev)
+                       - dt2 * F(n))
+        for m in range(prob.nf):
+            q[m] += s.w[n + 1, m] * W_next
+        W_prev, W_cur = W_cur, W_next
+    return _filter_update(prob, q, V)
+
+
+def _filter_update(prob, q, V):
+    """V^{k+1} from the filter sums: B V^{k+1} = q at every grid point (eq.
+    waveHoltzMatrixIteration), or the explicit filter of the footnote to eq. filterII."""
+    s = prob.setup
+    g = prob.grid
     flat = q.reshape(prob.nf, -1)
     if prob.explicit_filter:
         # explicit filter: B_mm V_m^{k+1} = q_m - sum_{j != m} B_mj V_j^k, the variant with
