@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--ws-epochs", type=int, default=15)
     ap.add_argument("--ws-gen-seconds", type=float, default=300.0,
                     help="time limit of the training-data generation")
+    ap.add_argument("--implicit", action="store_true",
+                    help="implicit trapezoidal time stepping (multigrid) beside explicit FP64")
     ap.add_argument("--cube", action="store_true",
                     help="run the 3D two-layer workload (257^3, N_f = 4, GMRES(15) cycle)")
     ap.add_argument("--no-clocks", action="store_true",
@@ -481,6 +483,100 @@ def run_cube(args):
     print(json.dumps(out), flush=True)
 
 
+def implicit_bytes_per_point(nf, forced, cycles_per_solve, dim=2):
+    """Algorithmic bytes per interior point of one implicit step (FP64): the V-cycles at the
+    finest level (2 red-black sweeps before and 1 after the coarse correction, each reading u
+    and f and writing u; the residual pass reading u, f and writing r; full weighting reading
+    r and writing the coarse f and u; prolongation reading the coarse u and updating u),
+    scaled by the coarser levels' share (1/(1 - 2^-dim)), the converged pre-smoothing and
+    residual test, and the update of W, q and the next right-hand side."""
+    w = 8
+    fine = 3 * 3 * w + 3 * w + (w + 2 * w / 2 ** dim) + (2 * w + w / 2 ** dim)
+    cyc = fine / (1.0 - 2.0 ** -dim)
+    check = 2 * 3 * w + 3 * w
+    update = 4 * w + (3 if forced else 2) * nf * w
+    return cycles_per_solve * cyc + check + update
+
+
+def run_implicit(args):
+    """Implicit trapezoidal time stepping (10 steps per shortest period, multigrid step solves
+    to 1e-10) on the 1025^2, N_f = 8, N_p = 2 workload: one GMRES(20) cycle from zero, timed
+    beside the explicit FP64 cycle of the same problem; ms per wave solve, multigrid cycles
+    per step, and the step kernel's achieved bandwidth on the algorithmic byte model."""
+    import torch
+    import paper_2507_23613_gb300 as M
+    from paper_2507_23613_gb300 import build, inputs
+    torch.cuda.set_device(0)
+    build.build()
+    M._lib.load()
+    wl = inputs.square_large(args.seed)
+    f = torch.from_numpy(wl.forcing).cuda()
+    stream = torch.cuda.Stream()
+    hbm_peak, peak_kind = peaks()
+    res = {}
+    for name, kw in (("implicit", dict(time_stepping="implicit")), ("explicit", {})):
+        s = M.Solver(wl.n, wl.length, wl.omega, f, stream=stream.cuda_stream, n_p=wl.n_p,
+                     cfl=wl.cfl, **kw)
+        n_t = s.setup["n_t"]
+        v = torch.zeros_like(f)
+        for _ in range(max(1, args.warmup)):
+            s.solve_gmres(v, restart=RESTART, tol=0.0, max_iters=RESTART, raise_on_error=False)
+        if name == "implicit":
+            s.mg_stats(reset=True)
+        ms_tot, step_ms, step_l, launches, apps = 0.0, 0.0, 0, 0, 0
+        for _ in range(max(1, args.steps)):
+            with torch.cuda.stream(stream):
+                v.zero_()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            info = s.solve_gmres(v, restart=RESTART, tol=0.0, max_iters=RESTART,
+                                 raise_on_error=False)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms_tot += ev0.elapsed_time(ev1)
+            a, b, c = s.last_timing()
+            step_ms += a
+            step_l += b
+            launches += c
+            apps += info["pi_applications"]
+        k = max(1, args.steps)
+        r = {"n_t": n_t, "dt": s.setup["dt"], "ms_per_cycle": round(ms_tot / k, 2),
+             "ms_per_wave_solve": round(step_ms / apps, 3),
+             "pi_applications_per_cycle": apps / k,
+             "rel_residual_after_cycle": info["rel_residual"],
+             "gpu_launches_per_cycle": launches / k}
+        if name == "implicit":
+            st = s.mg_stats()
+            cps = st["cycles"] / max(st["solves"], 1)
+            r.update({"mg_levels": st["levels"], "mg_cycles_per_step": round(cps, 3),
+                      "mg_unconverged_steps": st["unconverged"]})
+            interior = wl.interior_points
+            # one forced map per cycle, the rest homogeneous
+            per_app = [implicit_bytes_per_point(wl.nf, i == 0, cps) for i in range(apps // k)]
+            alg = interior * n_t * sum(per_app) * k
+            gbs = alg / (step_ms * 1e-3) / 1e9
+            r["roofline"] = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak,
+                             "unit": "GB/s", "frac": round(gbs / hbm_peak, 4),
+                             "peak_source": peak_kind, "kernel": "k_imp_step<2>",
+                             "alg_bytes_per_launch": round(alg / step_l),
+                             "avg_launch_us": round(step_ms * 1e3 / step_l, 2),
+                             "note": "finest-level multigrid arrays (3 x 8.4 MB) are L2-resident"}
+        res[name] = r
+        s.close()
+    out = {"metric": "implicit vs explicit FP64 MFWH wave solve", "unit": "ms",
+           "value": res["implicit"]["ms_per_wave_solve"], "higher_is_better": False,
+           "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"square{wl.n[0] + 1}x{wl.n[1] + 1}_nf{wl.nf}_np{wl.n_p}"
+                                  f"_implicit_gmres{RESTART}_cycle",
+                      "grid": [wl.n[0] + 1, wl.n[1] + 1], "nf": wl.nf, "n_p": wl.n_p,
+                      "steps_per_period": 10, "mg_tol": 1e-10},
+           "implicit": res["implicit"], "explicit": res["explicit"],
+           "speedup_per_wave_solve": round(res["explicit"]["ms_per_wave_solve"]
+                                           / res["implicit"]["ms_per_wave_solve"], 3)}
+    print(json.dumps(out), flush=True)
+
+
 def run_warm_start(args):
     """Learned warm start: MFWH-converged FP64 solutions of seeded problems train the network
     (inputs f_m / max|f_m| and omega_m / 45, target the shape V_m / max|V_m|, amplitude fitted to
@@ -615,6 +711,8 @@ def main():
         return run_cube(args) if rank == 0 else None
     if args.warm_start:
         return run_warm_start(args) if rank == 0 else None
+    if args.implicit:
+        return run_implicit(args) if rank == 0 else None
 
     import torch
     import paper_2507_23613_gb300 as M

@@ -61,6 +61,8 @@ enum { MFWH_PREC_FP64 = 0, MFWH_PREC_FP32_KAHAN = 1, MFWH_PREC_FP32_BLOCKSUM = 2
 /* How the filter sums become the next iterate (Section "The MFWH algorithm"). */
 enum { MFWH_UPDATE_IMPLICIT = 0, MFWH_UPDATE_EXPLICIT = 1 };
 enum { MFWH_C_CONST = 0, MFWH_C_TWO_LAYER = 1 };
+/* Time stepping of the wave solve (Section "Explicit and implicit time-stepping"). */
+enum { MFWH_TIME_EXPLICIT = 0, MFWH_TIME_IMPLICIT = 1 };
 
 typedef struct mfwh_handle_s* mfwh_handle_t;
 
@@ -103,6 +105,19 @@ typedef struct {
   int tile_shape;            /* FP32 blocked kernel tile: 0 = 32x32, 512 threads (default);
                                 1 = 32x64, 512 threads; 2 = 64x64, 1024 threads (halved in
                                 y above 8 frequencies) */
+  int time_stepping;         /* MFWH_TIME_EXPLICIT (0, default): leapfrog, alpha = 0, beta = 1;
+                                MFWH_TIME_IMPLICIT: trapezoidal scheme alpha = 1/2, beta = 0 of
+                                eq. WaveScheme (FP64, second order, one step per launch).  Every
+                                step solves (I - dt^2/2 L_h) Z = 2 W^n - dt^2 F^n by geometric
+                                multigrid on the device; W^{n+1} = Z - W^{n-1} (W^1 = Z/2).
+                                Grids must halve (all n_i even, n_i/2 >= 2) down to a level of
+                                at most 5000 points. */
+  int steps_per_period;      /* implicit: steps over the shortest period 2 pi / omega_nf
+                                (0 means 10; >= 5).  N_t = ceil(steps_per_period N_p omega_nf /
+                                omega_1); dt solves omega~_1 N_t dt = 2 pi N_p. */
+  double mg_tol;             /* implicit: a step's multigrid solve stops when
+                                max|rhs - A Z| <= mg_tol max|rhs| (0 means 1e-10) */
+  int mg_max_cycles;         /* implicit: V-cycles per step at most (0 means 30; <= 60) */
 } mfwh_problem;
 
 /* Everything the set-up derives from a problem (Algorithm 1, first two lines;
@@ -245,7 +260,8 @@ mfwh_status mfwh_solve_batch(const mfwh_handle_t* handles, int count, int restar
  * 3D: depth 1), keeping the fastest: *time_block and *tile_shape receive it, *ms_per_step
  * (may be NULL) its time per leapfrog step.  Results are cached per device, grid, number of
  * frequencies and precision for the life of the process.  Allocates (and frees) one handle's
- * workspace per candidate on the given stream; synchronous. */
+ * workspace per candidate on the given stream; synchronous.  Implicit time stepping has no
+ * candidates: depth 1, tile shape 0 and *ms_per_step = 0 without timing. */
 mfwh_status mfwh_autotune(const mfwh_problem* prob, void* stream, int* time_block,
                           int* tile_shape, double* ms_per_step);
 
@@ -339,6 +355,15 @@ mfwh_status mfwh_get_setup(mfwh_handle_t h, mfwh_setup* out);
  * output pointer may be NULL. */
 mfwh_status mfwh_last_timing(mfwh_handle_t h, double* step_ms, int64_t* step_launches,
                              int64_t* total_launches);
+
+/* Multigrid statistics of an implicit handle (MFWH_TIME_IMPLICIT), accumulated over every
+ * step solve since the handle was created or the counters were last reset:
+ * solves = step solves, cycles = V-cycles applied (a solve whose start already meets
+ * mg_tol applies none), unconverged = solves that reached mg_max_cycles above mg_tol.
+ * levels = levels of the hierarchy (always written).  reset != 0 zeroes the counters after
+ * reading them.  Synchronises the stream.  MFWH_ERR_INVALID_ARG for an explicit handle. */
+mfwh_status mfwh_mg_stats(mfwh_handle_t h, int64_t* solves, int64_t* cycles,
+                          int64_t* unconverged, int* levels, int reset);
 
 /* Release the handle and its device workspace (waits for its stream). */
 void mfwh_destroy(mfwh_handle_t h);

@@ -37,8 +37,10 @@ def _dptr(arr):
 def make_problem(n, length, omega, forcing=None, c_lo=1.0, c_hi=None, interface=0.5,
                  layer_axis=2, n_p=1, cfl=0.5, filter_mode=_lib.FILTER_OPTIMIZED,
                  user_params=None, n_delta=20, c_delta=2.0, time_block=0, precision=None,
-                 tile_shape=0, order=2, filter_update=0):
-    """Fill an mfwh_problem.  Returned keep-alive list holds the arrays it points to."""
+                 tile_shape=0, order=2, filter_update=0, time_stepping="explicit",
+                 steps_per_period=0, mg_tol=0.0, mg_max_cycles=0):
+    """Fill an mfwh_problem.  Returned keep-alive list holds the arrays it points to.
+    time_stepping: "explicit" (leapfrog) or "implicit" (trapezoidal, multigrid solves)."""
     p = _lib.Problem()
     p.dim = len(n)
     for a in range(3):
@@ -71,6 +73,12 @@ def make_problem(n, length, omega, forcing=None, c_lo=1.0, c_hi=None, interface=
     p.tile_shape = int(tile_shape)
     p.order = int(order)
     p.filter_update = int(filter_update)
+    if time_stepping not in ("explicit", "implicit"):
+        raise ValueError("time_stepping must be 'explicit' or 'implicit'")
+    p.time_stepping = _lib.TIME_IMPLICIT if time_stepping == "implicit" else _lib.TIME_EXPLICIT
+    p.steps_per_period = int(steps_per_period)
+    p.mg_tol = float(mg_tol)
+    p.mg_max_cycles = int(mg_max_cycles)
     return p, keep
 
 
@@ -276,6 +284,16 @@ class Solver:
         tl = C.c_int64()
         _lib.check(_lib.load().mfwh_last_timing(self._handle, C.byref(ms), C.byref(sl), C.byref(tl)))
         return ms.value, sl.value, tl.value
+
+    def mg_stats(self, reset=False):
+        """Multigrid statistics of an implicit handle: dict with solves, cycles, unconverged,
+        levels (accumulated since creation or the last reset)."""
+        sv, cy, un = C.c_int64(), C.c_int64(), C.c_int64()
+        lv = C.c_int()
+        _lib.check(_lib.load().mfwh_mg_stats(self._handle, C.byref(sv), C.byref(cy), C.byref(un),
+                                             C.byref(lv), int(bool(reset))))
+        return {"solves": sv.value, "cycles": cy.value, "unconverged": un.value,
+                "levels": lv.value}
 
 
 class CNN:

@@ -31,6 +31,8 @@ UPDATE_IMPLICIT = 0
 UPDATE_EXPLICIT = 1
 C_CONST = 0
 C_TWO_LAYER = 1
+TIME_EXPLICIT = 0
+TIME_IMPLICIT = 1
 
 _dp = C.POINTER(C.c_double)
 
@@ -59,6 +61,10 @@ class Problem(C.Structure):
         ("order", C.c_int),
         ("filter_update", C.c_int),
         ("tile_shape", C.c_int),
+        ("time_stepping", C.c_int),
+        ("steps_per_period", C.c_int),
+        ("mg_tol", C.c_double),
+        ("mg_max_cycles", C.c_int),
     ]
 
 
@@ -131,6 +137,8 @@ _SIGNATURES = {
     "mfwh_residual_noalloc": (C.c_int, [C.POINTER(Problem), C.c_void_p, C.c_void_p, _dp, C.c_void_p]),
     "mfwh_get_setup": (C.c_int, [C.c_void_p, C.POINTER(Setup)]),
     "mfwh_last_timing": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "mfwh_mg_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                C.POINTER(C.c_int64), C.POINTER(C.c_int), C.c_int]),
     "mfwh_destroy": (None, [C.c_void_p]),
     "mfwh_last_error": (C.c_char_p, []),
     "mfwh_status_string": (C.c_char_p, [C.c_int]),

@@ -121,6 +121,16 @@ struct mfwh_handle_s {
   float* wq32 = nullptr;            // device [(N_t + 1) * nf] w_{n,m}
   float* fc32 = nullptr;            // device [N_t * nf] kappa_n cos(omega~_m t^n)
   std::vector<float> wq32_h, fc32_h;
+  // implicit time stepping (MFWH_TIME_IMPLICIT)
+  bool implicit = false;
+  ImpArgs* imp = nullptr;           // step-kernel arguments (levels filled at create)
+  int imp_grid = 0;                 // blocks of the step kernel (1: one-CTA hierarchy)
+  size_t imp_smem = 0;              // its dynamic shared memory
+  double* imp_mem = nullptr;        // multigrid level arrays
+  MgState* d_mgstate = nullptr;     // [N_t] per-step convergence state
+  unsigned* d_bar = nullptr;        // grid barrier of the step kernel
+  MgCounters* d_mgc = nullptr;      // multigrid statistics
+  std::vector<double> imp_fc;       // [(N_t + 1) * nf] dt^2 cos(omega~_m t^n) cos(omega~_m dt)
 };
 
 namespace {
@@ -135,14 +145,18 @@ void reset_timing(mfwh_handle_t h) {
 }
 
 mfwh_status collect_timing(mfwh_handle_t h) {
-  if (h->d_err) {   // a blocked FP32 launch reports a tile copy that did not complete
+  if (h->d_err) {   // a bounded wait of a wave kernel ran out (1: FP32 tile copy; 2: barrier)
     CK(cudaMemcpyAsync(h->pinned, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     int flag = 0;
     std::memcpy(&flag, h->pinned, sizeof(int));
     if (flag) {
       CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
-      return fail(MFWH_ERR_CUDA, "FP32 wave kernel: a tile's tensor copy did not complete");
+      if (h->d_bar) CK(cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      return fail(MFWH_ERR_CUDA, flag == 2
+                                     ? "implicit step kernel: a grid barrier wait timed out"
+                                     : "FP32 wave kernel: a tile's tensor copy did not complete");
     }
   }
   double ms = 0.0;
@@ -272,8 +286,61 @@ mfwh_status apply_pi32(mfwh_handle_t h, const double* vin, double* vout, int for
 mfwh_status apply_pi_tb(mfwh_handle_t h, const double* vin, double* vout, int forced,
                         const double* vsub);
 
+// Implicit trapezoidal wave solve: one init launch, then one launch per step (multigrid solve
+// of A Z = rhs and the update of W, q and the next rhs; the last one writes v_out).
+mfwh_status apply_pi_implicit(mfwh_handle_t h, const double* vin, double* vout, int forced,
+                              const double* vsub) {
+  const Plan& P = h->plan;
+  const int nf = h->nf;
+  const int n_t = P.s.n_t;
+  cudaStream_t st = h->stream;
+  ImpArgs& A = *h->imp;
+  CK(cudaMemsetAsync(h->d_mgstate, 0, sizeof(MgState) * n_t, st));
+  ImpInit ini{};
+  for (int m = 0; m < nf; ++m) {
+    ini.w0[m] = P.w[m];
+    ini.fc0[m] = forced ? h->imp_fc[m] : 0.0;
+  }
+  launch_imp_init(nf, h->geom, vin, h->Wa, h->q, h->f, A.lev[0].u, A.lev[0].f, h->d_mgstate, ini,
+                  st);
+  h->total_launches += 1;
+  const bool timed = h->ev_used + 2 <= (int)h->ev.size();
+  if (timed) CK(cudaEventRecord(h->ev[h->ev_used], st));
+  A.q = h->q;
+  A.f = h->f;
+  A.vout = vout;
+  A.vsub = vsub;
+  A.subtract = vsub != nullptr;
+  A.has_e = h->sh.has_e && vin != nullptr;
+  A.vprev = vin;
+  std::memcpy(A.binv, h->sh.binv, sizeof(A.binv));
+  std::memcpy(A.emat, h->sh.emat, sizeof(A.emat));
+  for (int n = 0; n < n_t; ++n) {
+    A.st = h->d_mgstate + n;
+    A.st_next = n + 1 < n_t ? h->d_mgstate + n + 1 : nullptr;
+    A.Wp = (n % 2 == 0) ? h->Wb : h->Wa;   // W^{n-1}; step 0 writes W^1 into the spare level
+    A.first = n == 0;
+    A.last = n + 1 == n_t;
+    for (int m = 0; m < nf; ++m) {
+      A.wq[m] = P.w[(size_t)(n + 1) * nf + m];
+      A.fc[m] = (forced && n + 1 < n_t) ? h->imp_fc[(size_t)(n + 1) * nf + m] : 0.0;
+    }
+    cudaError_t e = launch_imp_step(P.dim, A, h->imp_grid, h->imp_smem, st);
+    if (e != cudaSuccess) return cuda_fail(e, "implicit step launch");
+  }
+  h->step_launches += n_t;
+  h->total_launches += n_t;
+  if (timed) {
+    CK(cudaEventRecord(h->ev[h->ev_used + 1], st));
+    h->ev_used += 2;
+  }
+  CK(cudaGetLastError());
+  return MFWH_OK;
+}
+
 mfwh_status apply_pi_direct(mfwh_handle_t h, const double* vin, double* vout, int forced,
                             const double* vsub) {
+  if (h->implicit) return apply_pi_implicit(h, vin, vout, forced, vsub);
   if (h->use32) return apply_pi32(h, vin, vout, forced, vsub);
   // The FP64 blocked kernel serves FP64 handles (depth 4 or 8); FP64 wave solves of an FP32
   // handle (the outer residuals of mfwh_solve_refined) take one step per launch.
@@ -388,7 +455,8 @@ mfwh_status apply_pi_tb(mfwh_handle_t h, const double* vin, double* vout, int fo
 // One wave solve: replayed from a captured graph in graph mode, launched directly otherwise.
 mfwh_status apply_pi(mfwh_handle_t h, const double* vin, double* vout, int forced,
                      const double* vsub) {
-  if (!h->graphs || (vsub && vsub != vin) || h->tune_steps > 0)
+  // implicit handles launch N_t + 1 kernels per wave solve: no graph
+  if (!h->graphs || (vsub && vsub != vin) || h->tune_steps > 0 || h->implicit)
     return apply_pi_direct(h, vin, vout, forced, vsub);
   const int key = (vin ? 1 : 0) | (forced ? 2 : 0) | (vsub ? 4 : 0) | (h->use32 ? 8 : 0);
   cudaStream_t st = h->gstream;
@@ -780,6 +848,64 @@ mfwh_status mfwh_create(const mfwh_problem* prob, void* stream, mfwh_handle_t* o
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "initialising FP32 workspace"));
   }
+  if (P.time_stepping == MFWH_TIME_IMPLICIT) {
+    if (h->P >= ((int64_t)1 << 31))
+      return cleanup(fail(MFWH_ERR_INVALID_ARG, "implicit time stepping: fewer than 2^31 points"));
+    h->implicit = true;
+    h->imp = new (std::nothrow) ImpArgs();
+    if (!h->imp) return cleanup(fail(MFWH_ERR_NOMEM, "host allocation failed"));
+    ImpArgs& A = *h->imp;
+    int64_t smem_d = 0;
+    if (!mg_plan_levels(g, P.s.h, P.c2_lo, P.c2_hi, P.s.dt, A.lev, &A.nlev, &A.lc, &smem_d))
+      return cleanup(fail(MFWH_ERR_INVALID_ARG,
+                          "implicit time stepping: the grid must halve (every n_i even, "
+                          "n_i / 2 >= 2) down to a level of at most 5000 points"));
+    // level arrays: u, f, r below the coarse level; u, f at the coarse level itself
+    int64_t total = 0;
+    for (int l = 0; l <= A.lc; ++l) total += (l < A.lc ? 3 : 2) * A.lev[l].points;
+    e = cudaMalloc(&h->imp_mem, sizeof(double) * total);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->imp_mem, 0, sizeof(double) * total, h->stream);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc (multigrid levels)"));
+    double* cur = h->imp_mem;
+    for (int l = 0; l <= A.lc; ++l) {
+      A.lev[l].u = cur;
+      A.lev[l].f = cur + A.lev[l].points;
+      A.lev[l].r = l < A.lc ? cur + 2 * A.lev[l].points : nullptr;
+      cur += (l < A.lc ? 3 : 2) * A.lev[l].points;
+    }
+    e = mg_launch_config(P.dim, A.lc, smem_d, &h->imp_grid, &h->imp_smem);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "multigrid launch configuration"));
+    A.layer_axis = P.layer_axis;
+    A.nf = h->nf;
+    A.nu1 = 2;
+    A.nu2 = 1;
+    // the coarsest grid is solved by Gauss-Seidel sweeps alone: enough for its longest line
+    const MgLevel& cl = A.lev[A.nlev - 1];
+    const int cn = std::max({cl.nx, cl.ny, P.dim == 3 ? cl.nz : 0});
+    A.coarse_sweeps = std::min(400, std::max(4, 2 * cn * cn));
+    A.max_cycles = P.mg_max_cycles;
+    A.tol = P.mg_tol;
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_mgstate, sizeof(MgState) * P.s.n_t);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_bar, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), h->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_mgc, sizeof(MgCounters));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_mgc, 0, sizeof(MgCounters), h->stream);
+    if (e == cudaSuccess && !h->d_err) {
+      e = cudaMalloc(&h->d_err, sizeof(int));
+      if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
+    }
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "implicit workspace"));
+    A.bar = h->d_bar;
+    A.err = h->d_err;
+    A.counters = h->d_mgc;
+    // F^n factor of eq. WaveSchemeForcing: beta + 2 alpha cos(omega~ dt) = cos(omega~ dt)
+    const double dt = P.s.dt;
+    h->imp_fc.resize((size_t)(P.s.n_t + 1) * h->nf);
+    for (int n = 0; n <= P.s.n_t; ++n)
+      for (int m = 0; m < h->nf; ++m)
+        h->imp_fc[(size_t)n * h->nf + m] =
+            dt * dt * P.cosf[(size_t)n * h->nf + m] * std::cos(P.s.omega_tilde[m] * dt);
+  }
   e = cudaMallocHost(&h->pinned, sizeof(double) * kPinned);
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMallocHost"));
   h->ev.resize(kEventPool);
@@ -1061,6 +1187,11 @@ void mfwh_destroy(mfwh_handle_t h) {
   for (double* b : bufs)
     if (b) cudaFree(b);
   if (h->d_err) cudaFree(h->d_err);
+  if (h->imp_mem) cudaFree(h->imp_mem);
+  if (h->d_mgstate) cudaFree(h->d_mgstate);
+  if (h->d_bar) cudaFree(h->d_bar);
+  if (h->d_mgc) cudaFree(h->d_mgc);
+  delete h->imp;
   float* fbufs[] = {h->f32, h->W32[0], h->W32[1], h->W32[2], h->W32[3], h->qs, h->qc,
                     h->wq32, h->fc32};
   for (float* b : fbufs)
@@ -1069,6 +1200,25 @@ void mfwh_destroy(mfwh_handle_t h) {
   for (auto& x : h->ev)
     if (x) cudaEventDestroy(x);
   delete h;
+}
+
+mfwh_status mfwh_mg_stats(mfwh_handle_t h, int64_t* solves, int64_t* cycles,
+                          int64_t* unconverged, int* levels, int reset) {
+  if (!h) return fail(MFWH_ERR_INVALID_ARG, "null handle");
+  if (!h->implicit) return fail(MFWH_ERR_INVALID_ARG, "not an implicit-time-stepping handle");
+  if (levels) *levels = h->imp->nlev;
+  CK(cudaMemcpyAsync(h->pinned, h->d_mgc, sizeof(MgCounters), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  MgCounters c;
+  std::memcpy(&c, h->pinned, sizeof(c));
+  if (solves) *solves = (int64_t)c.solves;
+  if (cycles) *cycles = (int64_t)c.cycles;
+  if (unconverged) *unconverged = (int64_t)c.unconverged;
+  if (reset) {
+    CK(cudaMemsetAsync(h->d_mgc, 0, sizeof(MgCounters), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  return MFWH_OK;
 }
 
 mfwh_status mfwh_set_graphs(mfwh_handle_t h, int enable) {
@@ -1104,20 +1254,34 @@ mfwh_status mfwh_solve_batch(const mfwh_handle_t* handles, int count, int restar
   std::atomic<int> ready{0};
   std::atomic<bool> go{false};
   std::chrono::steady_clock::time_point t0;   // written before `go`, read after it
-  auto work = [&](int i) {
-    mfwh_handle_t h = handles[i];
-    cudaSetDevice(h->device);
-    mfwh_solve_info& I = infos ? infos[i] : local[i];
+  // One worker per explicit handle.  Implicit handles share one worker and run in sequence:
+  // their step kernels are cooperative launches, which must not wait on each other's blocks.
+  std::vector<std::vector<int>> groups;
+  std::vector<int> imp;
+  for (int i = 0; i < count; ++i) {
+    if (handles[i]->implicit)
+      imp.push_back(i);
+    else
+      groups.push_back({i});
+  }
+  if (!imp.empty()) groups.push_back(imp);
+  auto work = [&](const std::vector<int>* idx) {
+    cudaSetDevice(handles[(*idx)[0]]->device);
     ready.fetch_add(1);
     while (!go.load()) std::this_thread::yield();
-    status[i] = mfwh_solve_gmres(h, restart, tol, max_iters, 0.0, v[i], &I);
-    secs[i] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    if (status[i] != MFWH_OK) msg[i] = g_error;
+    for (int i : *idx) {
+      mfwh_handle_t h = handles[i];
+      cudaSetDevice(h->device);
+      mfwh_solve_info& I = infos ? infos[i] : local[i];
+      status[i] = mfwh_solve_gmres(h, restart, tol, max_iters, 0.0, v[i], &I);
+      secs[i] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (status[i] != MFWH_OK) msg[i] = g_error;
+    }
   };
   std::vector<std::thread> pool;
-  pool.reserve(count);
-  for (int i = 0; i < count; ++i) pool.emplace_back(work, i);
-  while (ready.load() < count) std::this_thread::yield();
+  pool.reserve(groups.size());
+  for (auto& grp : groups) pool.emplace_back(work, &grp);
+  while (ready.load() < (int)groups.size()) std::this_thread::yield();
   t0 = std::chrono::steady_clock::now();
   go.store(true);
   for (auto& t : pool) t.join();
@@ -1142,6 +1306,12 @@ mfwh_status mfwh_autotune(const mfwh_problem* prob, void* stream, int* time_bloc
   Plan P;
   mfwh_status st = plan_problem(prob, &P);
   if (st != MFWH_OK) return st;
+  if (P.time_stepping == MFWH_TIME_IMPLICIT) {   // one step per launch; nothing to choose
+    *time_block = 1;
+    *tile_shape = 0;
+    if (ms_per_step) *ms_per_step = 0.0;
+    return MFWH_OK;
+  }
   int dev = 0;
   CK(cudaGetDevice(&dev));
   using Key = std::tuple<int, int, int64_t, int64_t, int64_t, int, int>;

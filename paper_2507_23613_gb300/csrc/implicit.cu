@@ -1,0 +1,541 @@
+// Implicit trapezoidal time stepping of the MFWH wave solve, FP64 (Section "Explicit and
+// implicit time-stepping", eq. WaveScheme with (alpha, beta) = (1/2, 0)).
+//
+// With A = I - (dt^2/2) L_h the scheme
+//   A W^{n+1} = 2 W^n - A W^{n-1} - dt^2 F^n,   F^n = sum_m f_m cos(omega~_m t^n) cos(omega~_m dt)
+// is solved as A Z = 2 W^n - dt^2 F^n, W^{n+1} = Z - W^{n-1}; the first step (eq.
+// implicitFirstStep with beta = 0) is the same solve with W^1 = Z / 2.  A is symmetric
+// positive definite and, for the steps of 5-10 per period the method uses, strongly
+// Laplacian-dominated on fine grids and identity-dominated on coarse ones, so geometric
+// multigrid solves it in a few V-cycles (the paper solves it with multigrid to 1e-10).
+//
+// Multigrid: vertex-centred coarsening by 2 in every axis, red-black Gauss-Seidel smoothing
+// (nu1 sweeps before, nu2 after the coarse correction), full-weighting restriction of the
+// residual, multilinear prolongation, and the operator rediscretised on every level
+// (pointwise c^2 of the level's grid points).  Levels of at most kMgCoarsePoints points are
+// solved by one CTA in shared memory (the coarsest with coarse_sweeps sweeps).
+//
+// One step is one launch.  When the hierarchy has grid-wide levels the launch is
+// cooperative (all blocks resident) and phases are separated by a grid barrier whose waits
+// are bounded in time (2 s): a wait that runs out sets *err = 2 and makes every later
+// barrier of the launch pass through, so the launch ends and the host reports the error.
+// The convergence test max|rhs - A Z| <= tol max|rhs| is evaluated after the pre-smoothing of
+// each cycle from a grid-wide atomicMax, read by all blocks after a barrier, so that every
+// block takes the same decision.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace mfwh {
+namespace {
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ double nanmax(double a, double b) { return (b > a || b != b) ? b : a; }
+
+// Grid barrier for a cooperative launch.  Bounded wait; see the file comment.
+__device__ void grid_sync(unsigned* bar, int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0 && *(volatile int*)err == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g0 = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const uint64_t t0 = global_ns();
+      while (*gen == g0) {
+        __nanosleep(64);
+        if (*(volatile int*)err != 0) break;
+        if (global_ns() - t0 > 2000000000ull) {
+          atomicExch(err, 2);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// Max over the block (all threads get the result).  red: shared scratch of 32 doubles.
+__device__ double block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    double x = l < (int)(blockDim.x >> 5) ? red[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) x = nanmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    if (l == 0) red[0] = x;
+  }
+  __syncthreads();
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* slot, double v) {
+  atomicMax(slot, (unsigned long long)__double_as_longlong(v));
+}
+__device__ __forceinline__ double load_nonneg(const unsigned long long* slot) {
+  return __longlong_as_double((long long)*(const volatile unsigned long long*)slot);
+}
+
+// Sum of a_i (u_{p+e_i} + u_{p-e_i}) and the coefficients of point (i, j, k).
+template <int DIM>
+__device__ __forceinline__ double neighbours(const MgLevel& L, const double* u, int64_t p,
+                                             const double* a) {
+  double s = a[0] * (u[p - 1] + u[p + 1]) + a[1] * (u[p - L.sy] + u[p + L.sy]);
+  if (DIM == 3) s += a[2] * (u[p - L.sz] + u[p + L.sz]);
+  return s;
+}
+__device__ __forceinline__ bool upper(const MgLevel& L, int axis, int i, int j, int k) {
+  return (axis == 0 ? i : (axis == 1 ? j : k)) >= L.split;
+}
+template <int DIM>
+__device__ __forceinline__ double residual_at(const MgLevel& L, const double* u, const double* f,
+                                              int axis, int i, int j, int k) {
+  const int64_t p = (int64_t)k * L.sz + (int64_t)j * L.sy + i;
+  const bool hi = upper(L, axis, i, j, k);
+  const double s = neighbours<DIM>(L, u, p, hi ? L.a_hi : L.a_lo);
+  return f[p] - ((hi ? L.d_hi : L.d_lo) * u[p] - s);
+}
+
+// One red (color 0) or black (color 1) half-sweep; (t0, stride) split the colour's points.
+template <int DIM>
+__device__ void rb_half(const MgLevel& L, double* u, const double* f, int color, int axis,
+                        uint32_t t0, uint32_t stride) {
+  const uint32_t hw = (uint32_t)L.nx / 2;
+  const uint32_t my = (uint32_t)L.ny - 1;
+  const uint32_t total = hw * my * (DIM == 3 ? (uint32_t)L.nz - 1 : 1u);
+  for (uint32_t t = t0; t < total; t += stride) {
+    const uint32_t row = t / hw, it = t - row * hw;
+    const int j = 1 + (int)(row % my);
+    const int k = DIM == 3 ? 1 + (int)(row / my) : 0;
+    const int i = (((j + k + color) & 1) ? 1 : 2) + 2 * (int)it;
+    if (i > L.nx - 1) continue;
+    const int64_t p = (int64_t)k * L.sz + (int64_t)j * L.sy + i;
+    const bool hi = upper(L, axis, i, j, k);
+    const double s = neighbours<DIM>(L, u, p, hi ? L.a_hi : L.a_lo);
+    u[p] = (f[p] + s) * (hi ? L.dinv_hi : L.dinv_lo);
+  }
+}
+
+// Residual of the interior points into r (if r) and its max over this thread's points.
+template <int DIM>
+__device__ double residual_pass(const MgLevel& L, const double* u, const double* f, double* r,
+                                int axis, uint32_t t0, uint32_t stride) {
+  const uint32_t mx = (uint32_t)L.nx - 1, my = (uint32_t)L.ny - 1;
+  const uint32_t total = mx * my * (DIM == 3 ? (uint32_t)L.nz - 1 : 1u);
+  double m = 0.0;
+  for (uint32_t t = t0; t < total; t += stride) {
+    const int i = 1 + (int)(t % mx);
+    const uint32_t rest = t / mx;
+    const int j = 1 + (int)(rest % my);
+    const int k = DIM == 3 ? 1 + (int)(rest / my) : 0;
+    const double res = residual_at<DIM>(L, u, f, axis, i, j, k);
+    if (r) r[(int64_t)k * L.sz + (int64_t)j * L.sy + i] = res;
+    m = nanmax(m, fabs(res));
+  }
+  return m;
+}
+
+// Full weighting of the fine residual onto the coarse interior: weights 1/2 at offset 0 and
+// 1/4 at offsets +-1 per axis.  The residual comes from rf, or (rf null) is evaluated from
+// (uf, ff).  The coarse correction uc starts at 0.
+template <int DIM>
+__device__ void restrict_pass(const MgLevel& F, const double* rf, const double* uf,
+                              const double* ff, const MgLevel& C, double* fc, double* uc,
+                              int axis, uint32_t t0, uint32_t stride) {
+  const uint32_t mx = (uint32_t)C.nx - 1, my = (uint32_t)C.ny - 1;
+  const uint32_t total = mx * my * (DIM == 3 ? (uint32_t)C.nz - 1 : 1u);
+  for (uint32_t t = t0; t < total; t += stride) {
+    const int I = 1 + (int)(t % mx);
+    const uint32_t rest = t / mx;
+    const int J = 1 + (int)(rest % my);
+    const int K = DIM == 3 ? 1 + (int)(rest / my) : 0;
+    double acc = 0.0;
+    for (int c = (DIM == 3 ? -1 : 0); c <= (DIM == 3 ? 1 : 0); ++c) {
+      const double wc = DIM == 3 ? (c == 0 ? 0.5 : 0.25) : 1.0;
+      for (int b = -1; b <= 1; ++b) {
+        const double wb = b == 0 ? 0.5 : 0.25;
+        for (int a = -1; a <= 1; ++a) {
+          const double wa = a == 0 ? 0.5 : 0.25;
+          const int i = 2 * I + a, j = 2 * J + b, k = DIM == 3 ? 2 * K + c : 0;
+          const double r = rf ? rf[(int64_t)k * F.sz + (int64_t)j * F.sy + i]
+                              : residual_at<DIM>(F, uf, ff, axis, i, j, k);
+          acc += wc * wb * wa * r;
+        }
+      }
+    }
+    const int64_t P = (int64_t)K * C.sz + (int64_t)J * C.sy + I;
+    fc[P] = acc;
+    uc[P] = 0.0;
+  }
+}
+
+// u_f += multilinear interpolation of the coarse correction (coarse boundary values are 0).
+template <int DIM>
+__device__ void prolong_pass(const MgLevel& C, const double* uc, const MgLevel& F, double* uf,
+                             uint32_t t0, uint32_t stride) {
+  const uint32_t mx = (uint32_t)F.nx - 1, my = (uint32_t)F.ny - 1;
+  const uint32_t total = mx * my * (DIM == 3 ? (uint32_t)F.nz - 1 : 1u);
+  for (uint32_t t = t0; t < total; t += stride) {
+    const int i = 1 + (int)(t % mx);
+    const uint32_t rest = t / mx;
+    const int j = 1 + (int)(rest % my);
+    const int k = DIM == 3 ? 1 + (int)(rest / my) : 0;
+    const int I = i >> 1, J = j >> 1, K = k >> 1;
+    const bool oi = i & 1, oj = j & 1, ok = k & 1;
+    auto line = [&](int JJ, int KK) {
+      const double* c = uc + (int64_t)KK * C.sz + (int64_t)JJ * C.sy;
+      return oi ? 0.5 * (c[I] + c[I + 1]) : c[I];
+    };
+    auto plane = [&](int KK) { return oj ? 0.5 * (line(J, KK) + line(J + 1, KK)) : line(J, KK); };
+    double v = plane(K);
+    if (DIM == 3 && ok) v = 0.5 * (v + plane(K + 1));
+    uf[(int64_t)k * F.sz + (int64_t)j * F.sy + i] += v;
+  }
+}
+
+// ---- the coarse CTA: levels lc..nlev-1 in shared memory -----------------------------
+
+template <int DIM>
+__device__ void cta_smooth(const MgLevel& L, double* u, const double* f, int sweeps, int axis) {
+  for (int s = 0; s < sweeps; ++s) {
+    rb_half<DIM>(L, u, f, 0, axis, threadIdx.x, blockDim.x);
+    __syncthreads();
+    rb_half<DIM>(L, u, f, 1, axis, threadIdx.x, blockDim.x);
+    __syncthreads();
+  }
+}
+
+// One V-cycle on levels l0..nlev-1 (l0's pre-smoothing skipped when presmoothed).
+template <int DIM>
+__device__ void cta_vcycle(const ImpArgs& a, double* sm, int l0, bool presmoothed) {
+  const int axis = a.layer_axis;
+  for (int l = l0; l < a.nlev - 1; ++l) {
+    const MgLevel& L = a.lev[l];
+    const MgLevel& C = a.lev[l + 1];
+    double* u = sm + L.smem;
+    if (!(presmoothed && l == l0)) cta_smooth<DIM>(L, u, u + L.points, a.nu1, axis);
+    double* uc = sm + C.smem;
+    restrict_pass<DIM>(L, nullptr, u, u + L.points, C, uc + C.points, uc, axis, threadIdx.x,
+                       blockDim.x);
+    __syncthreads();
+  }
+  {
+    const MgLevel& L = a.lev[a.nlev - 1];
+    double* u = sm + L.smem;
+    cta_smooth<DIM>(L, u, u + L.points, a.coarse_sweeps, axis);
+  }
+  for (int l = a.nlev - 2; l >= l0; --l) {
+    const MgLevel& L = a.lev[l];
+    const MgLevel& C = a.lev[l + 1];
+    double* u = sm + L.smem;
+    prolong_pass<DIM>(C, sm + C.smem, L, u, threadIdx.x, blockDim.x);
+    __syncthreads();
+    cta_smooth<DIM>(L, u, u + L.points, a.nu2, axis);
+  }
+}
+
+// Zero the shared levels, then copy level lc's rhs (and, if with_u, its start) from global.
+__device__ void cta_load(const ImpArgs& a, double* sm, bool with_u) {
+  const MgLevel& L = a.lev[a.lc];
+  const MgLevel& last = a.lev[a.nlev - 1];
+  const int64_t total = last.smem + 2 * last.points;
+  for (int64_t t = threadIdx.x; t < total; t += blockDim.x) sm[t] = 0.0;
+  __syncthreads();
+  double* u = sm + L.smem;
+  for (int64_t p = threadIdx.x; p < L.points; p += blockDim.x) {
+    u[L.points + p] = L.f[p];
+    if (with_u) u[p] = L.u[p];
+  }
+  __syncthreads();
+}
+__device__ void cta_store(const ImpArgs& a, const double* sm) {
+  const MgLevel& L = a.lev[a.lc];
+  const double* u = sm + L.smem;
+  for (int64_t p = threadIdx.x; p < L.points; p += blockDim.x) L.u[p] = u[p];
+}
+
+// ---- the step kernel ----------------------------------------------------------------
+
+template <int DIM>
+__device__ void update_phase(const ImpArgs& a, double* red) {
+  const MgLevel& L = a.lev[0];
+  const int64_t P = L.points;
+  const uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  const int nf = a.nf;
+  double bmax = 0.0;
+  const uint32_t nxp = (uint32_t)L.nx + 1, nyp = (uint32_t)L.ny + 1;
+  for (uint32_t t = t0; t < (uint32_t)P; t += stride) {
+    const int i = (int)(t % nxp);
+    const uint32_t rest = t / nxp;
+    const int j = (int)(rest % nyp);
+    const int k = DIM == 3 ? (int)(rest / nyp) : 0;
+    const bool interior = i > 0 && i < L.nx && j > 0 && j < L.ny &&
+                          (DIM == 2 || (k > 0 && k < L.nz));
+    const int64_t p = t;
+    if (!interior) {
+      if (a.last)
+        for (int m = 0; m < nf; ++m) a.vout[m * P + p] = 0.0;
+      continue;
+    }
+    const double Z = L.u[p];
+    const double wn = a.first ? 0.5 * Z : Z - a.Wp[p];
+    if (a.last) {
+      double qq[MFWH_MAX_NF], vk[MFWH_MAX_NF];
+      for (int m = 0; m < nf; ++m) qq[m] = fma(a.wq[m], wn, a.q[m * P + p]);
+      if (a.has_e)
+        for (int m = 0; m < nf; ++m) vk[m] = a.vprev[m * P + p];
+      for (int m = 0; m < nf; ++m) {
+        double s = 0.0;
+        for (int jj = 0; jj < nf; ++jj) s = fma(a.binv[m * MFWH_MAX_NF + jj], qq[jj], s);
+        if (a.has_e)
+          for (int jj = 0; jj < nf; ++jj) s = fma(a.emat[m * MFWH_MAX_NF + jj], vk[jj], s);
+        a.vout[m * P + p] = a.subtract ? a.vsub[m * P + p] - s : s;
+      }
+      continue;
+    }
+    a.Wp[p] = wn;
+    double rhs = 2.0 * wn;
+    for (int m = 0; m < nf; ++m) {
+      a.q[m * P + p] = fma(a.wq[m], wn, a.q[m * P + p]);
+      if (a.fc[m] != 0.0) rhs = fma(-a.fc[m], a.f[m * P + p], rhs);
+    }
+    L.f[p] = rhs;
+    L.u[p] = 2.0 * wn;
+    bmax = nanmax(bmax, fabs(rhs));
+  }
+  if (!a.last) {
+    bmax = block_max(bmax, red);
+    if (threadIdx.x == 0) atomic_max_nonneg(&a.st_next->bmax, bmax);
+  }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kMgThreads, 2) k_imp_step(const ImpArgs a) {
+  extern __shared__ double sm[];
+  __shared__ double red[32];
+  if (*(volatile int*)a.err != 0) return;
+  const int axis = a.layer_axis;
+  const MgLevel& L0 = a.lev[0];
+  const double bmax = load_nonneg(&a.st->bmax);
+  const double thresh = a.tol * bmax;
+  int c = 0;
+  bool converged = false;
+  if (a.lc == 0) {
+    // the whole hierarchy in this CTA (one block)
+    cta_load(a, sm, true);
+    double* u = sm + L0.smem;
+    for (;; ++c) {
+      cta_smooth<DIM>(L0, u, u + L0.points, a.nu1, axis);
+      const double rm =
+          block_max(residual_pass<DIM>(L0, u, u + L0.points, nullptr, axis, threadIdx.x,
+                                       blockDim.x), red);
+      if (rm <= thresh) { converged = true; break; }
+      if (c == a.max_cycles) break;
+      cta_vcycle<DIM>(a, sm, 0, true);
+    }
+    cta_store(a, sm);
+    __syncthreads();
+  } else {
+    const uint32_t g0 = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+    for (;; ++c) {
+      for (int l = 0; l < a.lc; ++l) {
+        const MgLevel& L = a.lev[l];
+        for (int s = 0; s < a.nu1; ++s) {
+          rb_half<DIM>(L, L.u, L.f, 0, axis, g0, gs);
+          grid_sync(a.bar, a.err);
+          rb_half<DIM>(L, L.u, L.f, 1, axis, g0, gs);
+          grid_sync(a.bar, a.err);
+        }
+        const double rm = residual_pass<DIM>(L, L.u, L.f, L.r, axis, g0, gs);
+        if (l == 0) {
+          const double bm = block_max(rm, red);
+          if (threadIdx.x == 0) atomic_max_nonneg(&a.st->rmax[c], bm);
+        }
+        grid_sync(a.bar, a.err);
+        if (l == 0) {
+          if (load_nonneg(&a.st->rmax[c]) <= thresh) { converged = true; break; }
+          if (c == a.max_cycles) break;
+        }
+        const MgLevel& C = a.lev[l + 1];
+        restrict_pass<DIM>(L, L.r, nullptr, nullptr, C, C.f, C.u, axis, g0, gs);
+        grid_sync(a.bar, a.err);
+      }
+      if (converged || c == a.max_cycles) break;
+      if (blockIdx.x == 0) {
+        cta_load(a, sm, false);
+        cta_vcycle<DIM>(a, sm, a.lc, false);
+        cta_store(a, sm);
+      }
+      grid_sync(a.bar, a.err);
+      for (int l = a.lc - 1; l >= 0; --l) {
+        const MgLevel& L = a.lev[l];
+        prolong_pass<DIM>(a.lev[l + 1], a.lev[l + 1].u, L, L.u, g0, gs);
+        grid_sync(a.bar, a.err);
+        for (int s = 0; s < a.nu2; ++s) {
+          rb_half<DIM>(L, L.u, L.f, 0, axis, g0, gs);
+          grid_sync(a.bar, a.err);
+          rb_half<DIM>(L, L.u, L.f, 1, axis, g0, gs);
+          grid_sync(a.bar, a.err);
+        }
+      }
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    atomicAdd(&a.counters->solves, 1ull);
+    atomicAdd(&a.counters->cycles, (unsigned long long)c);
+    if (!converged) atomicAdd(&a.counters->unconverged, 1ull);
+  }
+  update_phase<DIM>(a, red);
+}
+
+template <int DIM>
+__global__ void k_imp_init(int nf, const Geom g, const double* __restrict__ v,
+                           double* __restrict__ W0, double* __restrict__ q,
+                           const double* __restrict__ f, double* __restrict__ Z,
+                           double* __restrict__ rhs, MgState* st, const ImpInit a) {
+  __shared__ double red[32];
+  const int64_t P = g.points;
+  double bmax = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = p % (g.nx + 1);
+    const int64_t rest = p / (g.nx + 1);
+    const int64_t j = rest % (g.ny + 1);
+    const int64_t k = DIM == 3 ? rest / (g.ny + 1) : 0;
+    const bool interior = i > 0 && i < g.nx && j > 0 && j < g.ny &&
+                          (DIM == 2 || (k > 0 && k < g.nz));
+    double w = 0.0;
+    if (interior && v)
+      for (int m = 0; m < nf; ++m) w += v[m * P + p];
+    W0[p] = w;
+    for (int m = 0; m < nf; ++m) q[m * P + p] = a.w0[m] * w;
+    double r = 2.0 * w;
+    if (interior)
+      for (int m = 0; m < nf; ++m)
+        if (a.fc0[m] != 0.0) r = fma(-a.fc0[m], f[m * P + p], r);
+    rhs[p] = interior ? r : 0.0;
+    Z[p] = 2.0 * w;
+    bmax = nanmax(bmax, fabs(rhs[p]));
+  }
+  bmax = block_max(bmax, red);
+  if (threadIdx.x == 0) atomic_max_nonneg(&st->bmax, bmax);
+}
+
+}  // namespace
+
+bool mg_plan_levels(const Geom& g, const double* h, double c2_lo, double c2_hi, double dt,
+                    MgLevel* lev, int* nlev, int* lc, int64_t* smem_doubles) {
+  int n[3] = {(int)g.nx, (int)g.ny, g.dim == 3 ? (int)g.nz : 0};
+  double hh[3] = {h[0], h[1], g.dim == 3 ? h[2] : 1.0};
+  int64_t split = g.layer_split;
+  const double kap = 0.5 * dt * dt;   // alpha dt^2 with alpha = 1/2
+  int L = 0;
+  *lc = -1;
+  for (;;) {
+    MgLevel& v = lev[L];
+    v = MgLevel{};
+    v.nx = n[0];
+    v.ny = n[1];
+    v.nz = n[2];
+    v.split = (int)std::min<int64_t>(split, (int64_t)1 << 30);
+    if (L == 0) {
+      v.sy = g.sy;
+      v.sz = g.sz;
+      v.points = g.points;
+    } else {
+      v.sy = n[0] + 1;
+      v.sz = (int64_t)(n[0] + 1) * (n[1] + 1);
+      v.points = v.sz * (g.dim == 3 ? n[2] + 1 : 1);
+    }
+    double slo = 0.0, shi = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      const bool on = a < g.dim;
+      v.a_lo[a] = on ? kap * c2_lo / (hh[a] * hh[a]) : 0.0;
+      v.a_hi[a] = on ? kap * c2_hi / (hh[a] * hh[a]) : 0.0;
+      slo += v.a_lo[a];
+      shi += v.a_hi[a];
+    }
+    v.d_lo = 1.0 + 2.0 * slo;
+    v.d_hi = 1.0 + 2.0 * shi;
+    v.dinv_lo = 1.0 / v.d_lo;
+    v.dinv_hi = 1.0 / v.d_hi;
+    if (*lc < 0 && v.points <= kMgCoarsePoints) *lc = L;
+    ++L;
+    bool can = L < kMgMaxLevels;
+    for (int a = 0; a < g.dim; ++a) can = can && n[a] % 2 == 0 && n[a] / 2 >= 2;
+    if (!can) break;
+    for (int a = 0; a < g.dim; ++a) {
+      n[a] /= 2;
+      hh[a] *= 2.0;
+    }
+    split = (split + 1) / 2;   // first coarse index J with 2J >= split
+  }
+  *nlev = L;
+  if (*lc < 0) return false;
+  int64_t off = 0;
+  for (int l = *lc; l < L; ++l) {
+    lev[l].smem = off;
+    off += 2 * lev[l].points;
+  }
+  *smem_doubles = off;
+  return true;
+}
+
+cudaError_t mg_launch_config(int dim, int lc, int64_t smem_doubles, int* grid, size_t* smem) {
+  // The attribute is per kernel, shared by every handle: it is always set to the same bound
+  // (above what any hierarchy needs), and each handle launches with its own size below it.
+  constexpr int kSmemBound = 120 * 1024;
+  *smem = (size_t)smem_doubles * sizeof(double);
+  if (*smem > (size_t)kSmemBound) return cudaErrorInvalidValue;
+  const void* fn = dim == 3 ? (const void*)k_imp_step<3> : (const void*)k_imp_step<2>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBound);
+  if (e != cudaSuccess) return e;
+  if (lc == 0) {
+    *grid = 1;
+    return cudaSuccess;
+  }
+  int dev = 0, sms = 0, occ = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kMgThreads, *smem)) != cudaSuccess)
+    return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  *grid = sms * occ;
+  return cudaSuccess;
+}
+
+void launch_imp_init(int nf, const Geom& g, const double* v, double* W0, double* q,
+                     const double* f, double* Z, double* rhs, MgState* st, const ImpInit& a,
+                     cudaStream_t s) {
+  const int64_t blocks = std::min<int64_t>((g.points + 255) / 256, 8 * 152);
+  if (g.dim == 3)
+    k_imp_init<3><<<(unsigned)blocks, 256, 0, s>>>(nf, g, v, W0, q, f, Z, rhs, st, a);
+  else
+    k_imp_init<2><<<(unsigned)blocks, 256, 0, s>>>(nf, g, v, W0, q, f, Z, rhs, st, a);
+}
+
+cudaError_t launch_imp_step(int dim, const ImpArgs& a, int grid, size_t smem, cudaStream_t st) {
+  void* args[] = {(void*)&a};
+  const void* fn = dim == 3 ? (const void*)k_imp_step<3> : (const void*)k_imp_step<2>;
+  if (grid == 1) return cudaLaunchKernel(fn, dim3(1), dim3(kMgThreads), args, smem, st);
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kMgThreads), args, smem, st);
+}
+
+}  // namespace mfwh

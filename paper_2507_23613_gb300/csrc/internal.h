@@ -26,6 +26,9 @@ struct Plan {
   int precision = MFWH_PREC_FP64;
   int order = 2;               // order of L_{ph}: 2 or 4
   int filter_update = MFWH_UPDATE_IMPLICIT;
+  int time_stepping = MFWH_TIME_EXPLICIT;
+  double mg_tol = 1e-10;       // implicit: relative max-norm residual of each step solve
+  int mg_max_cycles = 30;      // implicit: V-cycles per step solve at most
   int64_t n[3] = {1, 1, 1};
   std::vector<double> w;       // [(n_t + 1) * nf]  filter weights w_{n,m}
   std::vector<double> cosf;    // [(n_t + 1) * nf]  cos(omega~_m t^n)

@@ -136,6 +136,83 @@ void launch_residual_field(int nf, const Geom& g, const double* v, const double*
                            const double* omega2, double c2_lo, double c2_hi, const double* inv_h2,
                            double* R, cudaStream_t st);
 
+// ---- implicit trapezoidal time stepping with geometric multigrid (implicit.cu), FP64 ----
+// Step n of eq. WaveScheme with (alpha, beta) = (1/2, 0) is A Z = rhs, A = I - (dt^2/2) L_h,
+// rhs = 2 W^n - dt^2 F^n, followed by W^{n+1} = Z - W^{n-1} (W^1 = Z / 2: eq.
+// implicitFirstStep).  A is solved by V-cycles of red-black Gauss-Seidel, full-weighting
+// restriction, multilinear prolongation and rediscretised coarse operators, inside one
+// persistent (cooperative) launch per step that decides convergence on the device.
+constexpr int kMgMaxLevels = 16;
+constexpr int kMgMaxCycles = 60;
+constexpr int64_t kMgCoarsePoints = 5000;   // levels this small run in one CTA's shared memory
+constexpr int kMgThreads = 512;
+
+struct MgLevel {
+  int nx, ny, nz;             // cells per axis (nz = 0 in 2D)
+  int split;                  // first index along the layer axis in the upper layer
+  int64_t sy, sz, points;     // strides and points of the level's arrays
+  double a_lo[3], a_hi[3];    // (dt^2/2) c^2 / h_i^2 below / above the layer split
+  double d_lo, d_hi;          // diagonal of A: 1 + 2 sum_i a_i
+  double dinv_lo, dinv_hi;    // 1 / diagonal
+  double* u;                  // device arrays of the grid-wide levels and of the first coarse
+  double* f;                  // level (its right-hand side in, correction out); null below it
+  double* r;                  // residual (grid-wide levels)
+  int64_t smem;               // coarse levels: offset in doubles of u in shared memory (f follows)
+};
+
+// Convergence test of one step solve: bits of non-negative doubles, so that atomicMax orders them.
+struct MgState {
+  unsigned long long bmax;                     // max |rhs|
+  unsigned long long rmax[kMgMaxCycles + 1];   // max |rhs - A Z| at each test
+};
+struct MgCounters {
+  unsigned long long solves, cycles, unconverged;
+};
+
+struct ImpArgs {
+  MgLevel lev[kMgMaxLevels];
+  int nlev, lc;               // levels; first level solved by the coarse CTA (0: all of them)
+  int layer_axis, nf;
+  int nu1, nu2, coarse_sweeps, max_cycles;
+  double tol;
+  MgState* st;                // this step's test state
+  MgState* st_next;           // next step's (receives max |rhs|), null on the last step
+  MgCounters* counters;
+  unsigned* bar;              // grid barrier: [0] arrivals, [1] generation
+  int* err;                   // set to 2 when a barrier wait times out
+  double* Wp;                 // in: W^{n-1}, out: W^{n+1}
+  double* q;                  // filter sums [nf][points]
+  const double* f;            // forcing [nf][points]
+  int first, last;            // n == 0; n + 1 == N_t (epilogue instead of the next rhs)
+  double wq[MFWH_MAX_NF];     // w_{n+1,m}
+  double fc[MFWH_MAX_NF];     // dt^2 cos(omega~_m t^{n+1}) cos(omega~_m dt); 0: homogeneous
+  double* vout;               // epilogue as in StepHost
+  const double* vsub;
+  int subtract, has_e;
+  const double* vprev;
+  double binv[MFWH_MAX_NF * MFWH_MAX_NF];
+  double emat[MFWH_MAX_NF * MFWH_MAX_NF];
+};
+struct ImpInit {
+  double w0[MFWH_MAX_NF];     // w_{0,m}
+  double fc0[MFWH_MAX_NF];    // dt^2 cos(omega~_m dt) (t^0 = 0); 0: homogeneous
+};
+// Level geometry and coefficients for A = I - (dt^2/2) c^2 Delta_h on the grid g (level 0 uses
+// g's strides).  Coarsens while every n_i is even and n_i / 2 >= 2.  lc = first level with at
+// most kMgCoarsePoints points; returns false if no level is that small.  smem_doubles: shared
+// memory of the coarse CTA (u and f of levels lc..nlev-1).
+bool mg_plan_levels(const Geom& g, const double* h, double c2_lo, double c2_hi, double dt,
+                    MgLevel* lev, int* nlev, int* lc, int64_t* smem_doubles);
+// Blocks of the step kernel's cooperative launch (1 when lc == 0) and its shared memory.
+cudaError_t mg_launch_config(int dim, int lc, int64_t smem_doubles, int* grid, size_t* smem);
+// W^0 = sum_m v_m, q_m = w_{0,m} W^0, Z = 2 W^0, rhs = 2 W^0 - dt^2 F^0 (boundary 0) and
+// st->bmax = max |rhs|.  v may be null (W^0 = 0).
+void launch_imp_init(int nf, const Geom& g, const double* v, double* W0, double* q,
+                     const double* f, double* Z, double* rhs, MgState* st, const ImpInit& a,
+                     cudaStream_t st_);
+// One implicit step (multigrid solve and the update of W, q and the next rhs, or the epilogue).
+cudaError_t launch_imp_step(int dim, const ImpArgs& a, int grid, size_t smem, cudaStream_t st);
+
 // ---- Krylov vector kernels (krylov.cu), FP64 -------------------------------------
 constexpr int kMaxDots = 32;       // vectors handled by one multi-dot / multi-axpy launch
 constexpr int kMaxKrylov = 1024;   // largest Krylov basis (restart length + 1)

@@ -319,6 +319,22 @@ mfwh_status plan_problem(const mfwh_problem* p, Plan* out) {
     return fail(MFWH_ERR_INVALID_ARG, "the fourth-order operator takes one step per launch");
   if (p->dim == 3 && p->time_block > 1)
     return fail(MFWH_ERR_INVALID_ARG, "temporal blocking is available for 2D grids only");
+  if (p->time_stepping != MFWH_TIME_EXPLICIT && p->time_stepping != MFWH_TIME_IMPLICIT)
+    return fail(MFWH_ERR_INVALID_ARG, "time_stepping must be explicit or implicit");
+  const bool implicit = p->time_stepping == MFWH_TIME_IMPLICIT;
+  if (implicit) {
+    if (fp32) return fail(MFWH_ERR_INVALID_ARG, "implicit time stepping runs in FP64 only");
+    if (p->time_block > 1)
+      return fail(MFWH_ERR_INVALID_ARG, "implicit time stepping takes one step per launch");
+    if (p->order == 4)
+      return fail(MFWH_ERR_INVALID_ARG, "implicit time stepping uses the second-order operator");
+    if (p->steps_per_period != 0 && p->steps_per_period < 5)
+      return fail(MFWH_ERR_INVALID_ARG, "steps_per_period must be >= 5");
+    if (p->mg_tol != 0.0 && !(p->mg_tol > 0.0 && p->mg_tol < 1.0))
+      return fail(MFWH_ERR_INVALID_ARG, "mg_tol must be in (0, 1)");
+    if (p->mg_max_cycles < 0 || p->mg_max_cycles > 60)
+      return fail(MFWH_ERR_INVALID_ARG, "mg_max_cycles must be in 0..60");
+  }
 
   Plan& P = *out;
   P = Plan();
@@ -335,6 +351,11 @@ mfwh_status plan_problem(const mfwh_problem* p, Plan* out) {
   P.order = p->order == 4 ? 4 : 2;
   P.filter_update = p->filter_update;
   P.precision = p->precision;
+  P.time_stepping = p->time_stepping;
+  if (implicit) {
+    P.mg_tol = p->mg_tol != 0.0 ? p->mg_tol : 1e-10;
+    P.mg_max_cycles = p->mg_max_cycles != 0 ? p->mg_max_cycles : 30;
+  }
   double inv_h2 = 0.0;
   s.points = 1;
   s.interior_points = 1;
@@ -367,22 +388,41 @@ mfwh_status plan_problem(const mfwh_problem* p, Plan* out) {
     P.layer_split = split;
   }
 
-  // Time step (explicit leapfrog; Section "Time-step determination").
-  // Leapfrog needs dt^2 rho(-L_h) <= 4; rho = c_max^2 sum_i 4/h_i^2 for the second-order
-  // operator and c_max^2 sum_i (16/3)/h_i^2 for the fourth-order one.
-  const double dt_stab = (P.order == 4 ? std::sqrt(3.0) / 2.0 : 1.0) / (P.c_max * std::sqrt(inv_h2));
-  const double t1 = p->n_p * 2.0 * kPi / p->omega[0];
-  double nt_real = std::ceil(t1 / (p->cfl * dt_stab));
-  if (nt_real > 5e7) return fail(MFWH_ERR_INVALID_ARG, "too many time steps");
-  int n_t = std::max(2 * p->n_p + 1, (int)nt_real);
-  s.n_t = n_t;
-  s.dt = 2.0 * std::sin(kPi * p->n_p / n_t) / p->omega[0];
+  int n_t = 0;
+  if (implicit) {
+    // Trapezoidal scheme (Section "Time-step determination"): steps_per_period steps over the
+    // shortest period give N_t over N_p longest periods; dt then solves omega~_1 N_t dt =
+    // 2 pi N_p, i.e. (omega_1 dt)^2 = (1 - cos theta) / (beta/2 + alpha cos theta) with
+    // theta = 2 pi N_p / N_t and (alpha, beta) = (1/2, 0).  N_t > 4 N_p keeps cos theta > 0.
+    const int spp = p->steps_per_period != 0 ? p->steps_per_period : 10;
+    const double nt_real = std::ceil(spp * (double)p->n_p * p->omega[nf - 1] / p->omega[0] - 1e-12);
+    if (nt_real > 5e7) return fail(MFWH_ERR_INVALID_ARG, "too many time steps");
+    n_t = (int)nt_real;
+    const double theta = 2.0 * kPi * p->n_p / n_t;
+    const double x2 = (1.0 - std::cos(theta)) / (0.5 * std::cos(theta));
+    s.n_t = n_t;
+    s.dt = std::sqrt(x2) / p->omega[0];
+  } else {
+    // Time step (explicit leapfrog; Section "Time-step determination").
+    // Leapfrog needs dt^2 rho(-L_h) <= 4; rho = c_max^2 sum_i 4/h_i^2 for the second-order
+    // operator and c_max^2 sum_i (16/3)/h_i^2 for the fourth-order one.
+    const double dt_stab =
+        (P.order == 4 ? std::sqrt(3.0) / 2.0 : 1.0) / (P.c_max * std::sqrt(inv_h2));
+    const double t1 = p->n_p * 2.0 * kPi / p->omega[0];
+    double nt_real = std::ceil(t1 / (p->cfl * dt_stab));
+    if (nt_real > 5e7) return fail(MFWH_ERR_INVALID_ARG, "too many time steps");
+    n_t = std::max(2 * p->n_p + 1, (int)nt_real);
+    s.n_t = n_t;
+    s.dt = 2.0 * std::sin(kPi * p->n_p / n_t) / p->omega[0];
+  }
   const double dt = s.dt;
 
-  // Adjusted frequencies (eq. omegaImplicit, alpha = 0, beta = 1) and periods (eq. TbarDef).
+  // Adjusted frequencies (eq. omegaImplicit with the scheme's (alpha, beta)) and periods
+  // (eq. TbarDef).
+  const double alpha = implicit ? 0.5 : 0.0, beta = implicit ? 0.0 : 1.0;
   for (int m = 0; m < nf; ++m) {
     double x = p->omega[m] * dt;
-    double c = 1.0 - 0.5 * x * x;
+    double c = (1.0 - 0.5 * beta * x * x) / (1.0 + alpha * x * x);
     if (c < -1.0) return fail(MFWH_ERR_INVALID_ARG, "frequency above the time-step Nyquist limit");
     s.omega_tilde[m] = std::acos(c) / dt;
   }

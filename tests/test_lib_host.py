@@ -39,16 +39,18 @@ def test_exports_every_declared_symbol(lib):
     assert sorted(_lib.declared_symbols()) == names
 
 
-def _compare_setup(wl, n_p=1, mode=F.FILTER_OPTIMIZED, user=None, c_hi=None, order=2):
+def _compare_setup(wl, n_p=1, mode=F.FILTER_OPTIMIZED, user=None, c_hi=None, order=2,
+                   time_stepping="explicit", steps_per_period=10):
     kw = dict(n_p=n_p, filter_mode={F.FILTER_OPTIMIZED: 0, F.FILTER_TRADITIONAL: 1,
-                                     F.FILTER_USER: 2}[mode], user_params=user, order=order)
+                                     F.FILTER_USER: 2}[mode], user_params=user, order=order,
+              time_stepping=time_stepping, steps_per_period=steps_per_period)
     if c_hi is not None:
         kw.update(c_lo=1.0, c_hi=c_hi, interface=0.5, layer_axis=len(wl.n) - 1)
     prob, keep = M.make_problem(wl.n, wl.length, wl.omega, **kw)
     s = M.setup_arrays(M.plan(prob))
     h = [L / n for L, n in zip(wl.length, wl.n)]
     o = F.make_setup(wl.omega, h, 1.0 if c_hi is None else max(1.0, c_hi), 0.5, n_p, mode, user,
-                     order=order)
+                     order=order, time_stepping=time_stepping, steps_per_period=steps_per_period)
     assert s["n_t"] == o.n_t
     assert abs(s["dt"] - o.dt) <= 1e-15 * o.dt
     np.testing.assert_allclose(s["omega_tilde"], o.omega_t, rtol=1e-14)
@@ -109,6 +111,20 @@ def test_plan_matches_oracle_3d_two_layer():
     _compare_setup(wl, c_hi=1.5)
 
 
+def test_plan_matches_oracle_implicit():
+    """Trapezoidal scheme: N_t from the steps per shortest period, dt from omega~_1 N_t dt =
+    2 pi N_p; optimised, traditional and 3D two-layer set-ups agree with the oracle."""
+    wl = inputs.square_small()
+    s, o = _compare_setup(wl, time_stepping="implicit")
+    assert s["n_t"] == math.ceil(10 * wl.omega[-1] / wl.omega[0])
+    assert abs(s["dt"] - _implicit_dt(wl.omega[0], 1, s["n_t"])) < 1e-15
+    _compare_setup(wl, mode=F.FILTER_TRADITIONAL, time_stepping="implicit", steps_per_period=7)
+    big = inputs.square_large()
+    _compare_setup(big, n_p=big.n_p, time_stepping="implicit")
+    wl3 = inputs.gaussian_workload("t3", (24, 20, 16), 4, [8.3, 12.1, 19.0, 27.5], 300.0, 5)
+    _compare_setup(wl3, c_hi=1.5, n_p=2, time_stepping="implicit")
+
+
 def _implicit_dt(omega1, n_p, n_t):
     # trapezoidal scheme (alpha, beta) = (1/2, 0): cos(omega~ dt) = 1 / (1 + (omega dt)^2 / 2)
     # and omega~_1 N_t dt = 2 pi N_p, so (omega_1 dt)^2 = 2 (1 - cos theta) / cos theta.
@@ -165,6 +181,12 @@ def test_adjusted_frequency_matches_definition():
     dict(order=3),                     # only second and fourth order
     dict(filter_update=2),             # implicit (0) or explicit (1) only
     dict(order=4, time_block=8),       # fourth order takes one step per launch
+    dict(time_stepping="implicit", precision=1),        # implicit runs in FP64 only
+    dict(time_stepping="implicit", time_block=4),       # one step per launch
+    dict(time_stepping="implicit", order=4),            # second-order operator only
+    dict(time_stepping="implicit", steps_per_period=4),  # at least five steps per period
+    dict(time_stepping="implicit", mg_tol=1.5),
+    dict(time_stepping="implicit", mg_max_cycles=61),
 ])
 def test_invalid_problems_are_rejected(bad):
     args = dict(n=(64, 64), length=(1.0, 1.0), omega=[5.5, 9.3])
