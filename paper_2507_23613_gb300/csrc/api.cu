@@ -319,6 +319,7 @@ mfwh_status apply_pi_implicit(mfwh_handle_t h, const double* vin, double* vout, 
     A.st = h->d_mgstate + n;
     A.st_next = n + 1 < n_t ? h->d_mgstate + n + 1 : nullptr;
     A.Wp = (n % 2 == 0) ? h->Wb : h->Wa;   // W^{n-1}; step 0 writes W^1 into the spare level
+    A.Wc = (n % 2 == 0) ? h->Wa : h->Wb;   // W^n
     A.first = n == 0;
     A.last = n + 1 == n_t;
     for (int m = 0; m < nf; ++m) {
@@ -860,20 +861,46 @@ mfwh_status mfwh_create(const mfwh_problem* prob, void* stream, mfwh_handle_t* o
       return cleanup(fail(MFWH_ERR_INVALID_ARG,
                           "implicit time stepping: the grid must halve (every n_i even, "
                           "n_i / 2 >= 2) down to a level of at most 5000 points"));
-    // level arrays: u, f, r below the coarse level; u, f at the coarse level itself
-    int64_t total = 0;
-    for (int l = 0; l <= A.lc; ++l) total += (l < A.lc ? 3 : 2) * A.lev[l].points;
-    e = cudaMalloc(&h->imp_mem, sizeof(double) * total);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->imp_mem, 0, sizeof(double) * total, h->stream);
-    if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc (multigrid levels)"));
-    double* cur = h->imp_mem;
+    // Level arrays (bytes counted in 4-byte words).  FP64 defect correction (2D with
+    // grid-wide levels): level 0 holds Z, rhs (FP64) and e, r (FP32); levels 1..lc-1 hold u,
+    // e, rhs (FP32); level lc holds u, rhs (FP32).  Otherwise (FP64 V-cycles): u, f, r (FP64)
+    // below level lc and u, f (FP64) at level lc.
+    const bool mixed = mg_mixed(P.dim, A.lc);
+    int64_t words = 0;
     for (int l = 0; l <= A.lc; ++l) {
-      A.lev[l].u = cur;
-      A.lev[l].f = cur + A.lev[l].points;
-      A.lev[l].r = l < A.lc ? cur + 2 * A.lev[l].points : nullptr;
-      cur += (l < A.lc ? 3 : 2) * A.lev[l].points;
+      const int64_t n = A.lev[l].points;
+      if (mixed)
+        words += l == 0 ? 4 * n + 2 * n : (l < A.lc ? 3 * n : 2 * n);
+      else
+        words += (l < A.lc ? 3 : 2) * 2 * n;
     }
-    e = mg_launch_config(P.dim, A.lc, smem_d, &h->imp_grid, &h->imp_smem);
+    e = cudaMalloc(&h->imp_mem, 4 * words);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->imp_mem, 0, 4 * words, h->stream);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "cudaMalloc (multigrid levels)"));
+    char* cur = reinterpret_cast<char*>(h->imp_mem);
+    auto take64 = [&](int64_t n) { double* p = reinterpret_cast<double*>(cur); cur += 8 * n; return p; };
+    auto take32 = [&](int64_t n) { float* p = reinterpret_cast<float*>(cur); cur += 4 * n; return p; };
+    for (int l = 0; l <= A.lc; ++l) {
+      MgLevel& L = A.lev[l];
+      const int64_t n = L.points;
+      if (mixed) {
+        if (l == 0) {
+          L.u = take64(n);
+          L.f = take64(n);
+          L.v32 = take32(n);
+          L.f32 = take32(n);
+        } else {
+          L.u32 = take32(n);
+          L.f32 = take32(n);
+          if (l < A.lc) L.v32 = take32(n);
+        }
+      } else {
+        L.u = take64(n);
+        L.f = take64(n);
+        if (l < A.lc) L.r = take64(n);
+      }
+    }
+    e = mg_launch_config(P.dim, A.lc, smem_d, A.lev, &h->imp_grid, &h->imp_smem);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "multigrid launch configuration"));
     A.layer_axis = P.layer_axis;
     A.nf = h->nf;

@@ -1,5 +1,5 @@
-// Implicit trapezoidal time stepping of the MFWH wave solve, FP64 (Section "Explicit and
-// implicit time-stepping", eq. WaveScheme with (alpha, beta) = (1/2, 0)).
+// Implicit trapezoidal time stepping of the MFWH wave solve, FP64 results (Section "Explicit
+// and implicit time-stepping", eq. WaveScheme with (alpha, beta) = (1/2, 0)).
 //
 // With A = I - (dt^2/2) L_h the scheme
 //   A W^{n+1} = 2 W^n - A W^{n-1} - dt^2 F^n,   F^n = sum_m f_m cos(omega~_m t^n) cos(omega~_m dt)
@@ -10,18 +10,25 @@
 // multigrid solves it in a few V-cycles (the paper solves it with multigrid to 1e-10).
 //
 // Multigrid: vertex-centred coarsening by 2 in every axis, red-black Gauss-Seidel smoothing
-// (nu1 sweeps before, nu2 after the coarse correction), full-weighting restriction of the
+// (2 sweeps before, 1 after the coarse correction), full-weighting restriction of the
 // residual, multilinear prolongation, and the operator rediscretised on every level
 // (pointwise c^2 of the level's grid points).  Levels of at most kMgCoarsePoints points are
 // solved by one CTA in shared memory (the coarsest with coarse_sweeps sweeps).
+//
+// Precision.  A 2D hierarchy with grid-wide levels runs defect correction: each cycle forms
+// the residual r = rhs - A Z in FP64, solves A e = r approximately by one FP32 V-cycle from
+// e = 0, and adds e to Z in FP64, so the iterate converges to the FP64 solution at the
+// V-cycle's rate while the smoothing runs on the FP32 pipes (GB300 issues FP64 arithmetic at
+// a small fraction of its FP32 rate).  3D hierarchies and hierarchies held by one CTA run
+// the V-cycles on Z itself in FP64.
 //
 // One step is one launch.  When the hierarchy has grid-wide levels the launch is
 // cooperative (all blocks resident) and phases are separated by a grid barrier whose waits
 // are bounded in time (2 s): a wait that runs out sets *err = 2 and makes every later
 // barrier of the launch pass through, so the launch ends and the host reports the error.
-// The convergence test max|rhs - A Z| <= tol max|rhs| is evaluated after the pre-smoothing of
-// each cycle from a grid-wide atomicMax, read by all blocks after a barrier, so that every
-// block takes the same decision.
+// The convergence test max|rhs - A Z| <= tol max|rhs| is evaluated once per cycle from a
+// grid-wide atomicMax, read by all blocks after a barrier, so that every block takes the same
+// decision.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -55,7 +62,7 @@ __device__ void grid_sync(unsigned* bar, int* err) {
     } else {
       const uint64_t t0 = global_ns();
       while (*gen == g0) {
-        __nanosleep(64);
+        __nanosleep(32);
         if (*(volatile int*)err != 0) break;
         if (global_ns() - t0 > 2000000000ull) {
           atomicExch(err, 2);
@@ -93,30 +100,45 @@ __device__ __forceinline__ double load_nonneg(const unsigned long long* slot) {
   return __longlong_as_double((long long)*(const volatile unsigned long long*)slot);
 }
 
-// Sum of a_i (u_{p+e_i} + u_{p-e_i}) and the coefficients of point (i, j, k).
-template <int DIM>
-__device__ __forceinline__ double neighbours(const MgLevel& L, const double* u, int64_t p,
-                                             const double* a) {
-  double s = a[0] * (u[p - 1] + u[p + 1]) + a[1] * (u[p - L.sy] + u[p + L.sy]);
-  if (DIM == 3) s += a[2] * (u[p - L.sz] + u[p + L.sz]);
-  return s;
-}
+// Coefficients of a level in the arithmetic type R.
+template <typename R>
+struct Co;
+template <>
+struct Co<double> {
+  __device__ static const double* a(const MgLevel& L, bool hi) { return hi ? L.a_hi : L.a_lo; }
+  __device__ static double d(const MgLevel& L, bool hi) { return hi ? L.d_hi : L.d_lo; }
+  __device__ static double dinv(const MgLevel& L, bool hi) { return hi ? L.dinv_hi : L.dinv_lo; }
+};
+template <>
+struct Co<float> {
+  __device__ static const float* a(const MgLevel& L, bool hi) { return hi ? L.a32_hi : L.a32_lo; }
+  __device__ static float d(const MgLevel& L, bool hi) { return hi ? L.d32_hi : L.d32_lo; }
+  __device__ static float dinv(const MgLevel& L, bool hi) { return hi ? L.dinv32_hi : L.dinv32_lo; }
+};
+
 __device__ __forceinline__ bool upper(const MgLevel& L, int axis, int i, int j, int k) {
   return (axis == 0 ? i : (axis == 1 ? j : k)) >= L.split;
 }
-template <int DIM>
-__device__ __forceinline__ double residual_at(const MgLevel& L, const double* u, const double* f,
-                                              int axis, int i, int j, int k) {
+// Sum of a_i (u_{p+e_i} + u_{p-e_i}); sy, sz are the strides of the array u.
+template <int DIM, typename R>
+__device__ __forceinline__ R neighbours(const R* u, int64_t p, int64_t sy, int64_t sz, const R* a) {
+  R s = a[0] * (u[p - 1] + u[p + 1]) + a[1] * (u[p - sy] + u[p + sy]);
+  if (DIM == 3) s += a[2] * (u[p - sz] + u[p + sz]);
+  return s;
+}
+template <int DIM, typename R>
+__device__ __forceinline__ R residual_at(const MgLevel& L, const R* u, const R* f, int axis, int i,
+                                         int j, int k) {
   const int64_t p = (int64_t)k * L.sz + (int64_t)j * L.sy + i;
   const bool hi = upper(L, axis, i, j, k);
-  const double s = neighbours<DIM>(L, u, p, hi ? L.a_hi : L.a_lo);
-  return f[p] - ((hi ? L.d_hi : L.d_lo) * u[p] - s);
+  const R s = neighbours<DIM, R>(u, p, L.sy, L.sz, Co<R>::a(L, hi));
+  return f[p] - (Co<R>::d(L, hi) * u[p] - s);
 }
 
 // One red (color 0) or black (color 1) half-sweep; (t0, stride) split the colour's points.
-template <int DIM>
-__device__ void rb_half(const MgLevel& L, double* u, const double* f, int color, int axis,
-                        uint32_t t0, uint32_t stride) {
+template <int DIM, typename R>
+__device__ void rb_half(const MgLevel& L, R* u, const R* f, int color, int axis, uint32_t t0,
+                        uint32_t stride) {
   const uint32_t hw = (uint32_t)L.nx / 2;
   const uint32_t my = (uint32_t)L.ny - 1;
   const uint32_t total = hw * my * (DIM == 3 ? (uint32_t)L.nz - 1 : 1u);
@@ -128,12 +150,12 @@ __device__ void rb_half(const MgLevel& L, double* u, const double* f, int color,
     if (i > L.nx - 1) continue;
     const int64_t p = (int64_t)k * L.sz + (int64_t)j * L.sy + i;
     const bool hi = upper(L, axis, i, j, k);
-    const double s = neighbours<DIM>(L, u, p, hi ? L.a_hi : L.a_lo);
-    u[p] = (f[p] + s) * (hi ? L.dinv_hi : L.dinv_lo);
+    const R s = neighbours<DIM, R>(u, p, L.sy, L.sz, Co<R>::a(L, hi));
+    u[p] = (f[p] + s) * Co<R>::dinv(L, hi);
   }
 }
 
-// Residual of the interior points into r (if r) and its max over this thread's points.
+// Residual of the interior points into r (if r) and its max over this thread's points (FP64).
 template <int DIM>
 __device__ double residual_pass(const MgLevel& L, const double* u, const double* f, double* r,
                                 int axis, uint32_t t0, uint32_t stride) {
@@ -145,7 +167,7 @@ __device__ double residual_pass(const MgLevel& L, const double* u, const double*
     const uint32_t rest = t / mx;
     const int j = 1 + (int)(rest % my);
     const int k = DIM == 3 ? 1 + (int)(rest / my) : 0;
-    const double res = residual_at<DIM>(L, u, f, axis, i, j, k);
+    const double res = residual_at<DIM, double>(L, u, f, axis, i, j, k);
     if (r) r[(int64_t)k * L.sz + (int64_t)j * L.sy + i] = res;
     m = nanmax(m, fabs(res));
   }
@@ -155,10 +177,10 @@ __device__ double residual_pass(const MgLevel& L, const double* u, const double*
 // Full weighting of the fine residual onto the coarse interior: weights 1/2 at offset 0 and
 // 1/4 at offsets +-1 per axis.  The residual comes from rf, or (rf null) is evaluated from
 // (uf, ff).  The coarse correction uc starts at 0.
-template <int DIM>
-__device__ void restrict_pass(const MgLevel& F, const double* rf, const double* uf,
-                              const double* ff, const MgLevel& C, double* fc, double* uc,
-                              int axis, uint32_t t0, uint32_t stride) {
+template <int DIM, typename R>
+__device__ void restrict_pass(const MgLevel& F, const R* rf, const R* uf, const R* ff,
+                              const MgLevel& C, R* fc, R* uc, int axis, uint32_t t0,
+                              uint32_t stride) {
   const uint32_t mx = (uint32_t)C.nx - 1, my = (uint32_t)C.ny - 1;
   const uint32_t total = mx * my * (DIM == 3 ? (uint32_t)C.nz - 1 : 1u);
   for (uint32_t t = t0; t < total; t += stride) {
@@ -166,30 +188,47 @@ __device__ void restrict_pass(const MgLevel& F, const double* rf, const double* 
     const uint32_t rest = t / mx;
     const int J = 1 + (int)(rest % my);
     const int K = DIM == 3 ? 1 + (int)(rest / my) : 0;
-    double acc = 0.0;
+    R acc = 0;
     for (int c = (DIM == 3 ? -1 : 0); c <= (DIM == 3 ? 1 : 0); ++c) {
-      const double wc = DIM == 3 ? (c == 0 ? 0.5 : 0.25) : 1.0;
+      const R wc = DIM == 3 ? (c == 0 ? R(0.5) : R(0.25)) : R(1);
       for (int b = -1; b <= 1; ++b) {
-        const double wb = b == 0 ? 0.5 : 0.25;
+        const R wb = b == 0 ? R(0.5) : R(0.25);
         for (int a = -1; a <= 1; ++a) {
-          const double wa = a == 0 ? 0.5 : 0.25;
+          const R wa = a == 0 ? R(0.5) : R(0.25);
           const int i = 2 * I + a, j = 2 * J + b, k = DIM == 3 ? 2 * K + c : 0;
-          const double r = rf ? rf[(int64_t)k * F.sz + (int64_t)j * F.sy + i]
-                              : residual_at<DIM>(F, uf, ff, axis, i, j, k);
+          const R r = rf ? rf[(int64_t)k * F.sz + (int64_t)j * F.sy + i]
+                         : residual_at<DIM, R>(F, uf, ff, axis, i, j, k);
           acc += wc * wb * wa * r;
         }
       }
     }
     const int64_t P = (int64_t)K * C.sz + (int64_t)J * C.sy + I;
     fc[P] = acc;
-    uc[P] = 0.0;
+    uc[P] = 0;
   }
 }
 
-// u_f += multilinear interpolation of the coarse correction (coarse boundary values are 0).
-template <int DIM>
-__device__ void prolong_pass(const MgLevel& C, const double* uc, const MgLevel& F, double* uf,
-                             uint32_t t0, uint32_t stride) {
+// Multilinear interpolation at fine point (i, j, k) of a coarse grid function (coarse boundary
+// values are 0).
+template <int DIM, typename R>
+__device__ __forceinline__ R prolong_at(const MgLevel& C, const R* uc, int i, int j, int k) {
+  const int I = i >> 1, J = j >> 1, K = k >> 1;
+  auto line = [&](int JJ, int KK) {
+    const R* c = uc + (int64_t)KK * C.sz + (int64_t)JJ * C.sy;
+    return (i & 1) ? R(0.5) * (c[I] + c[I + 1]) : c[I];
+  };
+  auto plane = [&](int KK) {
+    return (j & 1) ? R(0.5) * (line(J, KK) + line(J + 1, KK)) : line(J, KK);
+  };
+  R v = plane(K);
+  if (DIM == 3 && (k & 1)) v = R(0.5) * (v + plane(K + 1));
+  return v;
+}
+
+// u_f += interpolation of the coarse correction at every fine interior point.
+template <int DIM, typename R>
+__device__ void prolong_pass(const MgLevel& C, const R* uc, const MgLevel& F, R* uf, uint32_t t0,
+                             uint32_t stride) {
   const uint32_t mx = (uint32_t)F.nx - 1, my = (uint32_t)F.ny - 1;
   const uint32_t total = mx * my * (DIM == 3 ? (uint32_t)F.nz - 1 : 1u);
   for (uint32_t t = t0; t < total; t += stride) {
@@ -197,82 +236,253 @@ __device__ void prolong_pass(const MgLevel& C, const double* uc, const MgLevel& 
     const uint32_t rest = t / mx;
     const int j = 1 + (int)(rest % my);
     const int k = DIM == 3 ? 1 + (int)(rest / my) : 0;
-    const int I = i >> 1, J = j >> 1, K = k >> 1;
-    const bool oi = i & 1, oj = j & 1, ok = k & 1;
-    auto line = [&](int JJ, int KK) {
-      const double* c = uc + (int64_t)KK * C.sz + (int64_t)JJ * C.sy;
-      return oi ? 0.5 * (c[I] + c[I + 1]) : c[I];
-    };
-    auto plane = [&](int KK) { return oj ? 0.5 * (line(J, KK) + line(J + 1, KK)) : line(J, KK); };
-    double v = plane(K);
-    if (DIM == 3 && ok) v = 0.5 * (v + plane(K + 1));
-    uf[(int64_t)k * F.sz + (int64_t)j * F.sy + i] += v;
+    uf[(int64_t)k * F.sz + (int64_t)j * F.sy + i] += prolong_at<DIM, R>(C, uc, i, j, k);
+  }
+}
+
+// ---- tiled FP32 phases of a 2D hierarchy --------------------------------------------
+// Shared-memory copies over the tile's region [is, is + Wd) x [js, js + Wd).  Tiles own fine
+// points [1 + t T, 1 + (t + 1) T) per axis and the coarse points I whose centre 2I is one of
+// them.  A point update, residual or restriction computes what rb_half, residual_at and
+// restrict_pass compute on the whole grid (same operations in the same order).
+
+// Half-sweep of colour `color` over the square [ri, ri + S) x [rj, rj + S).
+__device__ void tile_half(const MgLevel& F, float* su, const float* sf, int Wd, int is, int js,
+                          int ri, int rj, int S, int color, int axis) {
+  const int hw = (S + 1) / 2;
+  for (int t = threadIdx.x; t < hw * S; t += blockDim.x) {
+    const int r = t / hw, it = t - r * hw;
+    const int j = rj + r;
+    const int i = ri + (((ri + j + color) & 1) ? 1 : 0) + 2 * it;
+    if (i >= ri + S || i < 1 || i > F.nx - 1 || j < 1 || j > F.ny - 1) continue;
+    const int x = (j - js) * Wd + (i - is);
+    const bool hi = upper(F, axis, i, j, 0);
+    const float s = neighbours<2, float>(su, x, Wd, 0, Co<float>::a(F, hi));
+    su[x] = (sf[x] + s) * Co<float>::dinv(F, hi);
+  }
+}
+
+__device__ __forceinline__ float tile_res(const MgLevel& F, const float* su, const float* sf,
+                                          int Wd, int is, int js, int i, int j, int axis) {
+  const int x = (j - js) * Wd + (i - is);
+  const bool hi = upper(F, axis, i, j, 0);
+  const float s = neighbours<2, float>(su, x, Wd, 0, Co<float>::a(F, hi));
+  return sf[x] - (Co<float>::d(F, hi) * su[x] - s);
+}
+
+// Smooth e from 0 with 2 sweeps in shared memory (sf holds the right-hand side), then write
+// the owned points to F.v32 and restrict the residual onto C.f32.
+__device__ void tile_down_rest(const MgLevel& F, const MgLevel& C, float* su, const float* sf,
+                               int Wd, int is, int js, int i0, int j0, int T, int axis) {
+  const int H = kMgHalo;
+  for (int h = 0; h < 4; ++h) {
+    const int d = H - 1 - h;
+    tile_half(F, su, sf, Wd, is, js, i0 - d, j0 - d, T + 2 * d, h & 1, axis);
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < T * T; t += blockDim.x) {
+    const int i = i0 + t % T, j = j0 + t / T;
+    if (i > F.nx - 1 || j > F.ny - 1) continue;
+    F.v32[(int64_t)j * F.sy + i] = su[(j - js) * Wd + (i - is)];
+  }
+  const int Tc = T / 2, I0 = (i0 + 1) / 2, J0 = (j0 + 1) / 2;
+  for (int t = threadIdx.x; t < Tc * Tc; t += blockDim.x) {
+    const int I = I0 + t % Tc, J = J0 + t / Tc;
+    if (I > C.nx - 1 || J > C.ny - 1) continue;
+    float acc = 0.0f;
+    for (int b = -1; b <= 1; ++b) {
+      const float wb = b == 0 ? 0.5f : 0.25f;
+      for (int a = -1; a <= 1; ++a) {
+        const float wa = a == 0 ? 0.5f : 0.25f;
+        acc += 1.0f * wb * wa * tile_res(F, su, sf, Wd, is, js, 2 * I + a, 2 * J + b, axis);
+      }
+    }
+    C.f32[(int64_t)J * C.sy + I] = acc;
+  }
+}
+
+// Level 0 down phase: r = rhs - A Z in FP64 on the region (Z staged with one more ring),
+// F.f32 = r on owned points, then the FP32 smoothing of e from 0 and the restriction.
+// Returns the max |r| over this block's owned points.
+__device__ double down0_tiles(const MgLevel& F, const MgLevel& C, int axis, unsigned char* smraw) {
+  const int T = F.tile, H = kMgHalo, Wd = T + 2 * H, Wz = Wd + 2;
+  const int ntx = (F.nx - 1 + T - 1) / T, nty = (F.ny - 1 + T - 1) / T;
+  double* zs = reinterpret_cast<double*>(smraw);
+  float* su = reinterpret_cast<float*>(zs + Wz * Wz);
+  float* sf = su + Wd * Wd;
+  double m = 0.0;
+  for (int tile = blockIdx.x; tile < ntx * nty; tile += gridDim.x) {
+    const int i0 = 1 + (tile % ntx) * T, j0 = 1 + (tile / ntx) * T;
+    const int is = i0 - H, js = j0 - H;
+    for (int t = threadIdx.x; t < Wz * Wz; t += blockDim.x) {
+      const int i = is - 1 + t % Wz, j = js - 1 + t / Wz;
+      const bool in = i >= 0 && i <= F.nx && j >= 0 && j <= F.ny;
+      zs[t] = in ? F.u[(int64_t)j * F.sy + i] : 0.0;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < Wd * Wd; t += blockDim.x) {
+      const int i = is + t % Wd, j = js + t / Wd;
+      double r = 0.0;
+      if (i >= 1 && i <= F.nx - 1 && j >= 1 && j <= F.ny - 1) {
+        const int64_t p = (int64_t)j * F.sy + i;
+        const int x = (j - js + 1) * Wz + (i - is + 1);
+        const bool hi = upper(F, axis, i, j, 0);
+        const double s = neighbours<2, double>(zs, x, Wz, 0, Co<double>::a(F, hi));
+        r = F.f[p] - (Co<double>::d(F, hi) * zs[x] - s);
+        if (i >= i0 && i < i0 + T && j >= j0 && j < j0 + T) {
+          m = nanmax(m, fabs(r));
+          F.f32[p] = (float)r;
+        }
+      }
+      sf[t] = (float)r;
+      su[t] = 0.0f;
+    }
+    __syncthreads();
+    tile_down_rest(F, C, su, sf, Wd, is, js, i0, j0, T, axis);
+    __syncthreads();
+  }
+  return m;
+}
+
+// Down phase of a coarser grid-wide level: e from 0 with right-hand side F.f32.
+__device__ void down_tiles(const MgLevel& F, const MgLevel& C, int axis, unsigned char* smraw) {
+  const int T = F.tile, H = kMgHalo, Wd = T + 2 * H;
+  const int ntx = (F.nx - 1 + T - 1) / T, nty = (F.ny - 1 + T - 1) / T;
+  float* su = reinterpret_cast<float*>(smraw);
+  float* sf = su + Wd * Wd;
+  for (int tile = blockIdx.x; tile < ntx * nty; tile += gridDim.x) {
+    const int i0 = 1 + (tile % ntx) * T, j0 = 1 + (tile / ntx) * T;
+    const int is = i0 - H, js = j0 - H;
+    for (int t = threadIdx.x; t < Wd * Wd; t += blockDim.x) {
+      const int i = is + t % Wd, j = js + t / Wd;
+      const bool in = i >= 1 && i <= F.nx - 1 && j >= 1 && j <= F.ny - 1;
+      sf[t] = in ? F.f32[(int64_t)j * F.sy + i] : 0.0f;
+      su[t] = 0.0f;
+    }
+    __syncthreads();
+    tile_down_rest(F, C, su, sf, Wd, is, js, i0, j0, T, axis);
+    __syncthreads();
+  }
+}
+
+// Up phase: e = F.v32 + P (coarse correction e_c), one red-black sweep, then F.u32 = e on
+// owned points (levels > 0) or Z += e in FP64 (level 0).
+__device__ void up_tiles(const MgLevel& F, const MgLevel& C, const float* ec, bool level0,
+                         int axis, unsigned char* smraw) {
+  const int T = F.tile, H = 2, Wd = T + 2 * H;
+  const int ntx = (F.nx - 1 + T - 1) / T, nty = (F.ny - 1 + T - 1) / T;
+  float* su = reinterpret_cast<float*>(smraw);
+  float* sf = su + Wd * Wd;
+  for (int tile = blockIdx.x; tile < ntx * nty; tile += gridDim.x) {
+    const int i0 = 1 + (tile % ntx) * T, j0 = 1 + (tile / ntx) * T;
+    const int is = i0 - H, js = j0 - H;
+    for (int t = threadIdx.x; t < Wd * Wd; t += blockDim.x) {
+      const int i = is + t % Wd, j = js + t / Wd;
+      float uu = 0.0f, ff = 0.0f;
+      if (i >= 1 && i <= F.nx - 1 && j >= 1 && j <= F.ny - 1) {
+        const int64_t p = (int64_t)j * F.sy + i;
+        uu = F.v32[p] + prolong_at<2, float>(C, ec, i, j, 0);
+        ff = F.f32[p];
+      }
+      su[t] = uu;
+      sf[t] = ff;
+    }
+    __syncthreads();
+    for (int h = 0; h < 2; ++h) {
+      const int d = 1 - h;
+      tile_half(F, su, sf, Wd, is, js, i0 - d, j0 - d, T + 2 * d, h & 1, axis);
+      __syncthreads();
+    }
+    for (int t = threadIdx.x; t < T * T; t += blockDim.x) {
+      const int i = i0 + t % T, j = j0 + t / T;
+      if (i > F.nx - 1 || j > F.ny - 1) continue;
+      const int64_t p = (int64_t)j * F.sy + i;
+      const float e = su[(j - js) * Wd + (i - is)];
+      if (level0)
+        F.u[p] += (double)e;
+      else
+        F.u32[p] = e;
+    }
+    __syncthreads();
   }
 }
 
 // ---- the coarse CTA: levels lc..nlev-1 in shared memory -----------------------------
 
-template <int DIM>
-__device__ void cta_smooth(const MgLevel& L, double* u, const double* f, int sweeps, int axis) {
+template <int DIM, typename R>
+__device__ void cta_smooth(const MgLevel& L, R* u, const R* f, int sweeps, int axis) {
   for (int s = 0; s < sweeps; ++s) {
-    rb_half<DIM>(L, u, f, 0, axis, threadIdx.x, blockDim.x);
+    rb_half<DIM, R>(L, u, f, 0, axis, threadIdx.x, blockDim.x);
     __syncthreads();
-    rb_half<DIM>(L, u, f, 1, axis, threadIdx.x, blockDim.x);
+    rb_half<DIM, R>(L, u, f, 1, axis, threadIdx.x, blockDim.x);
     __syncthreads();
   }
 }
 
 // One V-cycle on levels l0..nlev-1 (l0's pre-smoothing skipped when presmoothed).
-template <int DIM>
-__device__ void cta_vcycle(const ImpArgs& a, double* sm, int l0, bool presmoothed) {
+template <int DIM, typename R>
+__device__ void cta_vcycle(const ImpArgs& a, R* sm, int l0, bool presmoothed) {
   const int axis = a.layer_axis;
   for (int l = l0; l < a.nlev - 1; ++l) {
     const MgLevel& L = a.lev[l];
     const MgLevel& C = a.lev[l + 1];
-    double* u = sm + L.smem;
-    if (!(presmoothed && l == l0)) cta_smooth<DIM>(L, u, u + L.points, a.nu1, axis);
-    double* uc = sm + C.smem;
-    restrict_pass<DIM>(L, nullptr, u, u + L.points, C, uc + C.points, uc, axis, threadIdx.x,
-                       blockDim.x);
+    R* u = sm + L.smem;
+    if (!(presmoothed && l == l0)) cta_smooth<DIM, R>(L, u, u + L.points, a.nu1, axis);
+    R* uc = sm + C.smem;
+    restrict_pass<DIM, R>(L, nullptr, u, u + L.points, C, uc + C.points, uc, axis, threadIdx.x,
+                          blockDim.x);
     __syncthreads();
   }
   {
     const MgLevel& L = a.lev[a.nlev - 1];
-    double* u = sm + L.smem;
-    cta_smooth<DIM>(L, u, u + L.points, a.coarse_sweeps, axis);
+    R* u = sm + L.smem;
+    cta_smooth<DIM, R>(L, u, u + L.points, a.coarse_sweeps, axis);
   }
   for (int l = a.nlev - 2; l >= l0; --l) {
     const MgLevel& L = a.lev[l];
     const MgLevel& C = a.lev[l + 1];
-    double* u = sm + L.smem;
-    prolong_pass<DIM>(C, sm + C.smem, L, u, threadIdx.x, blockDim.x);
+    R* u = sm + L.smem;
+    prolong_pass<DIM, R>(C, sm + C.smem, L, u, threadIdx.x, blockDim.x);
     __syncthreads();
-    cta_smooth<DIM>(L, u, u + L.points, a.nu2, axis);
+    cta_smooth<DIM, R>(L, u, u + L.points, a.nu2, axis);
   }
 }
 
 // Zero the shared levels, then copy level lc's rhs (and, if with_u, its start) from global.
-__device__ void cta_load(const ImpArgs& a, double* sm, bool with_u) {
+template <typename R>
+__device__ void cta_load(const ImpArgs& a, R* sm, bool with_u) {
   const MgLevel& L = a.lev[a.lc];
   const MgLevel& last = a.lev[a.nlev - 1];
   const int64_t total = last.smem + 2 * last.points;
-  for (int64_t t = threadIdx.x; t < total; t += blockDim.x) sm[t] = 0.0;
+  for (int64_t t = threadIdx.x; t < total; t += blockDim.x) sm[t] = 0;
   __syncthreads();
-  double* u = sm + L.smem;
+  R* u = sm + L.smem;
   for (int64_t p = threadIdx.x; p < L.points; p += blockDim.x) {
-    u[L.points + p] = L.f[p];
-    if (with_u) u[p] = L.u[p];
+    if constexpr (sizeof(R) == 8) {
+      u[L.points + p] = L.f[p];
+      if (with_u) u[p] = L.u[p];
+    } else {
+      u[L.points + p] = L.f32[p];
+    }
   }
   __syncthreads();
 }
-__device__ void cta_store(const ImpArgs& a, const double* sm) {
+template <typename R>
+__device__ void cta_store(const ImpArgs& a, const R* sm) {
   const MgLevel& L = a.lev[a.lc];
-  const double* u = sm + L.smem;
-  for (int64_t p = threadIdx.x; p < L.points; p += blockDim.x) L.u[p] = u[p];
+  const R* u = sm + L.smem;
+  for (int64_t p = threadIdx.x; p < L.points; p += blockDim.x) {
+    if constexpr (sizeof(R) == 8)
+      L.u[p] = u[p];
+    else
+      L.u32[p] = u[p];
+  }
 }
 
 // ---- the step kernel ----------------------------------------------------------------
 
+// W^{n+1} = Z - W^{n-1} (or Z / 2), filter sums, and the next solve's rhs and start; on the
+// last step the epilogue V = C q + E V^k instead.
 template <int DIM>
 __device__ void update_phase(const ImpArgs& a, double* red) {
   const MgLevel& L = a.lev[0];
@@ -317,7 +527,8 @@ __device__ void update_phase(const ImpArgs& a, double* red) {
       if (a.fc[m] != 0.0) rhs = fma(-a.fc[m], a.f[m * P + p], rhs);
     }
     L.f[p] = rhs;
-    L.u[p] = 2.0 * wn;
+    // start of the next solve: Z^{n+1} = W^{n+2} + W^n ~ 2 W^{n+1} + (W^{n+1} - 2 W^n + W^{n-1})
+    L.u[p] = 2.0 * wn + (Z - 2.0 * a.Wc[p]);
     bmax = nanmax(bmax, fabs(rhs));
   }
   if (!a.last) {
@@ -328,7 +539,7 @@ __device__ void update_phase(const ImpArgs& a, double* red) {
 
 template <int DIM>
 __global__ void __launch_bounds__(kMgThreads, 2) k_imp_step(const ImpArgs a) {
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double red[32];
   if (*(volatile int*)a.err != 0) return;
   const int axis = a.layer_axis;
@@ -337,30 +548,57 @@ __global__ void __launch_bounds__(kMgThreads, 2) k_imp_step(const ImpArgs a) {
   const double thresh = a.tol * bmax;
   int c = 0;
   bool converged = false;
-  if (a.lc == 0) {
-    // the whole hierarchy in this CTA (one block)
-    cta_load(a, sm, true);
+  if (DIM == 2 && a.lc > 0) {
+    // FP64 defect correction with FP32 V-cycles (tiled grid-wide levels)
+    for (;; ++c) {
+      const double m = down0_tiles(L0, a.lev[1], axis, smraw);
+      const double bm = block_max(m, red);
+      if (threadIdx.x == 0) atomic_max_nonneg(&a.st->rmax[c], bm);
+      grid_sync(a.bar, a.err);
+      if (load_nonneg(&a.st->rmax[c]) <= thresh) { converged = true; break; }
+      if (c == a.max_cycles) break;
+      for (int l = 1; l < a.lc; ++l) {
+        down_tiles(a.lev[l], a.lev[l + 1], axis, smraw);
+        grid_sync(a.bar, a.err);
+      }
+      if (blockIdx.x == 0) {
+        float* sm = reinterpret_cast<float*>(smraw);
+        cta_load<float>(a, sm, false);
+        cta_vcycle<DIM, float>(a, sm, a.lc, false);
+        cta_store<float>(a, sm);
+      }
+      grid_sync(a.bar, a.err);
+      for (int l = a.lc - 1; l >= 0; --l) {
+        up_tiles(a.lev[l], a.lev[l + 1], a.lev[l + 1].u32, l == 0, axis, smraw);
+        grid_sync(a.bar, a.err);
+      }
+    }
+  } else if (a.lc == 0) {
+    // the whole hierarchy in this CTA (one block), FP64
+    double* sm = reinterpret_cast<double*>(smraw);
+    cta_load<double>(a, sm, true);
     double* u = sm + L0.smem;
     for (;; ++c) {
-      cta_smooth<DIM>(L0, u, u + L0.points, a.nu1, axis);
+      cta_smooth<DIM, double>(L0, u, u + L0.points, a.nu1, axis);
       const double rm =
           block_max(residual_pass<DIM>(L0, u, u + L0.points, nullptr, axis, threadIdx.x,
                                        blockDim.x), red);
       if (rm <= thresh) { converged = true; break; }
       if (c == a.max_cycles) break;
-      cta_vcycle<DIM>(a, sm, 0, true);
+      cta_vcycle<DIM, double>(a, sm, 0, true);
     }
-    cta_store(a, sm);
+    cta_store<double>(a, sm);
     __syncthreads();
   } else {
+    // grid-wide FP64 V-cycles on Z (3D)
     const uint32_t g0 = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
     for (;; ++c) {
       for (int l = 0; l < a.lc; ++l) {
         const MgLevel& L = a.lev[l];
         for (int s = 0; s < a.nu1; ++s) {
-          rb_half<DIM>(L, L.u, L.f, 0, axis, g0, gs);
+          rb_half<DIM, double>(L, L.u, L.f, 0, axis, g0, gs);
           grid_sync(a.bar, a.err);
-          rb_half<DIM>(L, L.u, L.f, 1, axis, g0, gs);
+          rb_half<DIM, double>(L, L.u, L.f, 1, axis, g0, gs);
           grid_sync(a.bar, a.err);
         }
         const double rm = residual_pass<DIM>(L, L.u, L.f, L.r, axis, g0, gs);
@@ -374,24 +612,25 @@ __global__ void __launch_bounds__(kMgThreads, 2) k_imp_step(const ImpArgs a) {
           if (c == a.max_cycles) break;
         }
         const MgLevel& C = a.lev[l + 1];
-        restrict_pass<DIM>(L, L.r, nullptr, nullptr, C, C.f, C.u, axis, g0, gs);
+        restrict_pass<DIM, double>(L, L.r, nullptr, nullptr, C, C.f, C.u, axis, g0, gs);
         grid_sync(a.bar, a.err);
       }
       if (converged || c == a.max_cycles) break;
       if (blockIdx.x == 0) {
-        cta_load(a, sm, false);
-        cta_vcycle<DIM>(a, sm, a.lc, false);
-        cta_store(a, sm);
+        double* sm = reinterpret_cast<double*>(smraw);
+        cta_load<double>(a, sm, false);
+        cta_vcycle<DIM, double>(a, sm, a.lc, false);
+        cta_store<double>(a, sm);
       }
       grid_sync(a.bar, a.err);
       for (int l = a.lc - 1; l >= 0; --l) {
         const MgLevel& L = a.lev[l];
-        prolong_pass<DIM>(a.lev[l + 1], a.lev[l + 1].u, L, L.u, g0, gs);
+        prolong_pass<DIM, double>(a.lev[l + 1], a.lev[l + 1].u, L, L.u, g0, gs);
         grid_sync(a.bar, a.err);
         for (int s = 0; s < a.nu2; ++s) {
-          rb_half<DIM>(L, L.u, L.f, 0, axis, g0, gs);
+          rb_half<DIM, double>(L, L.u, L.f, 0, axis, g0, gs);
           grid_sync(a.bar, a.err);
-          rb_half<DIM>(L, L.u, L.f, 1, axis, g0, gs);
+          rb_half<DIM, double>(L, L.u, L.f, 1, axis, g0, gs);
           grid_sync(a.bar, a.err);
         }
       }
@@ -441,7 +680,7 @@ __global__ void k_imp_init(int nf, const Geom g, const double* __restrict__ v,
 }  // namespace
 
 bool mg_plan_levels(const Geom& g, const double* h, double c2_lo, double c2_hi, double dt,
-                    MgLevel* lev, int* nlev, int* lc, int64_t* smem_doubles) {
+                    MgLevel* lev, int* nlev, int* lc, int64_t* smem_elems) {
   int n[3] = {(int)g.nx, (int)g.ny, g.dim == 3 ? (int)g.nz : 0};
   double hh[3] = {h[0], h[1], g.dim == 3 ? h[2] : 1.0};
   int64_t split = g.layer_split;
@@ -469,6 +708,8 @@ bool mg_plan_levels(const Geom& g, const double* h, double c2_lo, double c2_hi, 
       const bool on = a < g.dim;
       v.a_lo[a] = on ? kap * c2_lo / (hh[a] * hh[a]) : 0.0;
       v.a_hi[a] = on ? kap * c2_hi / (hh[a] * hh[a]) : 0.0;
+      v.a32_lo[a] = (float)v.a_lo[a];
+      v.a32_hi[a] = (float)v.a_hi[a];
       slo += v.a_lo[a];
       shi += v.a_hi[a];
     }
@@ -476,6 +717,10 @@ bool mg_plan_levels(const Geom& g, const double* h, double c2_lo, double c2_hi, 
     v.d_hi = 1.0 + 2.0 * shi;
     v.dinv_lo = 1.0 / v.d_lo;
     v.dinv_hi = 1.0 / v.d_hi;
+    v.d32_lo = (float)v.d_lo;
+    v.d32_hi = (float)v.d_hi;
+    v.dinv32_lo = (float)v.dinv_lo;
+    v.dinv32_hi = (float)v.dinv_hi;
     if (*lc < 0 && v.points <= kMgCoarsePoints) *lc = L;
     ++L;
     bool can = L < kMgMaxLevels;
@@ -494,15 +739,19 @@ bool mg_plan_levels(const Geom& g, const double* h, double c2_lo, double c2_hi, 
     lev[l].smem = off;
     off += 2 * lev[l].points;
   }
-  *smem_doubles = off;
+  *smem_elems = off;
   return true;
 }
 
-cudaError_t mg_launch_config(int dim, int lc, int64_t smem_doubles, int* grid, size_t* smem) {
+cudaError_t mg_launch_config(int dim, int lc, int64_t smem_elems, MgLevel* lev, int* grid,
+                             size_t* smem) {
   // The attribute is per kernel, shared by every handle: it is always set to the same bound
   // (above what any hierarchy needs), and each handle launches with its own size below it.
   constexpr int kSmemBound = 120 * 1024;
-  *smem = (size_t)smem_doubles * sizeof(double);
+  const bool mixed = mg_mixed(dim, lc);
+  int64_t need = smem_elems * (mixed ? 4 : 8);
+  if (mixed) need = std::max(need, mg_tile_smem_bytes(kMgTileMax));
+  *smem = (size_t)need;
   if (*smem > (size_t)kSmemBound) return cudaErrorInvalidValue;
   const void* fn = dim == 3 ? (const void*)k_imp_step<3> : (const void*)k_imp_step<2>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBound);
@@ -518,6 +767,22 @@ cudaError_t mg_launch_config(int dim, int lc, int64_t smem_doubles, int* grid, s
     return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
   *grid = sms * occ;
+  if (mixed) {
+    for (int l = 0; l < lc; ++l) {
+      int best = kMgTileMax;
+      int64_t best_cost = -1;
+      for (int T = kMgTileMax; T >= 8; T /= 2) {
+        const int64_t tiles = (int64_t)((lev[l].nx - 1 + T - 1) / T) * ((lev[l].ny - 1 + T - 1) / T);
+        const int64_t rounds = (tiles + *grid - 1) / *grid;
+        const int64_t cost = rounds * (T + 2 * kMgHalo) * (T + 2 * kMgHalo);
+        if (best_cost < 0 || cost < best_cost) {
+          best_cost = cost;
+          best = T;
+        }
+      }
+      lev[l].tile = best;
+    }
+  }
   return cudaSuccess;
 }
 

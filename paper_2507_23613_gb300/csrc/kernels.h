@@ -154,11 +154,31 @@ struct MgLevel {
   double a_lo[3], a_hi[3];    // (dt^2/2) c^2 / h_i^2 below / above the layer split
   double d_lo, d_hi;          // diagonal of A: 1 + 2 sum_i a_i
   double dinv_lo, dinv_hi;    // 1 / diagonal
-  double* u;                  // device arrays of the grid-wide levels and of the first coarse
-  double* f;                  // level (its right-hand side in, correction out); null below it
-  double* r;                  // residual (grid-wide levels)
-  int64_t smem;               // coarse levels: offset in doubles of u in shared memory (f follows)
+  float a32_lo[3], a32_hi[3];   // the same coefficients rounded to FP32
+  float d32_lo, d32_hi, dinv32_lo, dinv32_hi;
+  double* u;                  // FP64 arrays: level 0's iterate Z and right-hand side; the
+  double* f;                  // grid-wide levels and the first coarse level of a 3D hierarchy
+  double* r;                  // residual (grid-wide 3D levels)
+  float* u32;                 // FP32 arrays of a 2D hierarchy: correction after the up phase,
+  float* v32;                 // after the down phase, and the level's right-hand side (level 0:
+  float* f32;                 // the FP64 residual rhs - A Z rounded to FP32)
+  int tile;                   // grid-wide 2D levels: edge of the square tile of owned points
+  int64_t smem;               // coarse levels: offset in elements of u in shared memory (f follows)
 };
+// A 2D hierarchy with grid-wide levels is solved by defect correction: every cycle forms
+// r = rhs - A Z in FP64, applies one FP32 V-cycle to A e = r from e = 0, and adds e to Z in FP64.
+// Its grid-wide levels run tiled phases: a CTA loads a tile plus a halo of kMgHalo points into
+// shared memory, applies the two pre-smoothing sweeps there (each half-sweep shrinks the valid
+// region by one point) and restricts the residual of its tile; the up phase loads a tile plus
+// 2 points, adds the prolonged correction and applies the post-smoothing sweep.
+constexpr int kMgTileMax = 64;
+constexpr int kMgHalo = 6;     // 2 nu1 + 2 with nu1 = 2
+// Shared memory in bytes of the tiled phases with tile edge T: level 0's down phase holds Z
+// (FP64, one more ring) and e, r (FP32); the other phases hold u and f (FP32).
+inline int64_t mg_tile_smem_bytes(int T) {
+  const int64_t w = T + 2 * kMgHalo;
+  return (w + 2) * (w + 2) * 8 + 2 * w * w * 4;
+}
 
 // Convergence test of one step solve: bits of non-negative doubles, so that atomicMax orders them.
 struct MgState {
@@ -181,6 +201,7 @@ struct ImpArgs {
   unsigned* bar;              // grid barrier: [0] arrivals, [1] generation
   int* err;                   // set to 2 when a barrier wait times out
   double* Wp;                 // in: W^{n-1}, out: W^{n+1}
+  const double* Wc;           // W^n (start of the next solve: 2 W^{n+1} + Z - 2 W^n)
   double* q;                  // filter sums [nf][points]
   const double* f;            // forcing [nf][points]
   int first, last;            // n == 0; n + 1 == N_t (epilogue instead of the next rhs)
@@ -199,12 +220,17 @@ struct ImpInit {
 };
 // Level geometry and coefficients for A = I - (dt^2/2) c^2 Delta_h on the grid g (level 0 uses
 // g's strides).  Coarsens while every n_i is even and n_i / 2 >= 2.  lc = first level with at
-// most kMgCoarsePoints points; returns false if no level is that small.  smem_doubles: shared
-// memory of the coarse CTA (u and f of levels lc..nlev-1).
+// most kMgCoarsePoints points; returns false if no level is that small.  smem_elems: shared
+// memory of the coarse CTA in elements (u and f of levels lc..nlev-1).
 bool mg_plan_levels(const Geom& g, const double* h, double c2_lo, double c2_hi, double dt,
-                    MgLevel* lev, int* nlev, int* lc, int64_t* smem_doubles);
-// Blocks of the step kernel's cooperative launch (1 when lc == 0) and its shared memory.
-cudaError_t mg_launch_config(int dim, int lc, int64_t smem_doubles, int* grid, size_t* smem);
+                    MgLevel* lev, int* nlev, int* lc, int64_t* smem_elems);
+// Blocks of the step kernel's cooperative launch (1 when lc == 0) and its shared memory; in
+// 2D it also picks each grid-wide level's tile edge (64, 32, 16 or 8: fewest rounds of tiles
+// over the blocks times the tile's loaded points) and grows the shared memory to hold it.
+cudaError_t mg_launch_config(int dim, int lc, int64_t smem_elems, MgLevel* lev, int* grid,
+                             size_t* smem);
+// A 2D hierarchy with grid-wide levels (lc > 0) runs the FP32 defect-correction cycles.
+inline bool mg_mixed(int dim, int lc) { return dim == 2 && lc > 0; }
 // W^0 = sum_m v_m, q_m = w_{0,m} W^0, Z = 2 W^0, rhs = 2 W^0 - dt^2 F^0 (boundary 0) and
 // st->bmax = max |rhs|.  v may be null (W^0 = 0).
 void launch_imp_init(int nf, const Geom& g, const double* v, double* W0, double* q,

@@ -138,8 +138,8 @@ def test_implicit_gmres_converges_to_direct_solution():
 
 
 def test_implicit_graph_mode_and_batch():
-    s1, p1, wl1 = pair("grid_2d", mg_tol=0.0)
-    s2, p2, wl2 = pair("one_cta_2d", mg_tol=0.0)
+    s1, p1, wl1 = pair("grid_2d", mg_tol=1e-12)
+    s2, p2, wl2 = pair("one_cta_2d", mg_tol=1e-12)
     e = M.Solver(wl2.n, wl2.length, wl2.omega, dev(wl2.forcing))     # explicit handle
     v = random_v(wl1, 3)
     a = apply(s1, v, True)
@@ -147,12 +147,12 @@ def test_implicit_graph_mode_and_batch():
     b = apply(s1, v, True)
     assert np.array_equal(a, b)
     vs = [torch.zeros(w.forcing.shape, dtype=torch.float64, device="cuda") for w in (wl1, wl2, wl2)]
-    st, infos, secs = M.solve_batch([s1, s2, e], vs, restart=100, tol=1e-9, max_iters=400)
+    st, infos, secs = M.solve_batch([s1, s2, e], vs, restart=100, tol=1e-11, max_iters=400)
     assert st == _lib.OK
     for sol, prob in ((vs[0], p1), (vs[1], p2)):
         U = W.helmholtz_direct(prob)
-        assert np.all(rel_err(sol.cpu().numpy(), U) < 1e-6)
-    assert all(i["rel_residual"] < 1e-9 for i in infos)
+        assert np.all(rel_err(sol.cpu().numpy(), U) < 1e-7)
+    assert all(i["rel_residual"] < 1e-11 for i in infos)
     e.close()
 
 
