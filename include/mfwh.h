@@ -107,11 +107,13 @@ typedef struct {
                                 y above 8 frequencies) */
   int time_stepping;         /* MFWH_TIME_EXPLICIT (0, default): leapfrog, alpha = 0, beta = 1;
                                 MFWH_TIME_IMPLICIT: trapezoidal scheme alpha = 1/2, beta = 0 of
-                                eq. WaveScheme (FP64, second order, one step per launch).  Every
+                                eq. WaveScheme (FP64 results, one step per launch).  Every
                                 step solves (I - dt^2/2 L_h) Z = 2 W^n - dt^2 F^n by geometric
                                 multigrid on the device; W^{n+1} = Z - W^{n-1} (W^1 = Z/2).
                                 Grids must halve (all n_i even, n_i/2 >= 2) down to a level of
-                                at most 5000 points. */
+                                at most 5000 points.  Order 4 is available for 2D grids of more
+                                than 5000 points (the second-order multigrid preconditions the
+                                fourth-order residual). */
   int steps_per_period;      /* implicit: steps over the shortest period 2 pi / omega_nf
                                 (0 means 10; >= 5).  N_t = ceil(steps_per_period N_p omega_nf /
                                 omega_1); dt solves omega~_1 N_t dt = 2 pi N_p. */

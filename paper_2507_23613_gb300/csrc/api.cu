@@ -861,6 +861,14 @@ mfwh_status mfwh_create(const mfwh_problem* prob, void* stream, mfwh_handle_t* o
       return cleanup(fail(MFWH_ERR_INVALID_ARG,
                           "implicit time stepping: the grid must halve (every n_i even, "
                           "n_i / 2 >= 2) down to a level of at most 5000 points"));
+    if (P.order == 4) {
+      if (!mg_mixed(P.dim, A.lc))
+        return cleanup(fail(MFWH_ERR_INVALID_ARG,
+                            "implicit time stepping with the fourth-order operator needs a 2D "
+                            "grid of more than 5000 points"));
+      mg_set_order4(&A.lev[0], P.s.h, P.c2_lo, P.c2_hi, P.s.dt, P.dim);
+    }
+    A.omega_dc = P.order == 4 ? 6.0 / 7.0 : 1.0;
     // Level arrays (bytes counted in 4-byte words).  FP64 defect correction (2D with
     // grid-wide levels): level 0 holds Z, rhs (FP64) and e, r (FP32); levels 1..lc-1 hold u,
     // e, rhs (FP32); level lc holds u, rhs (FP32).  Otherwise (FP64 V-cycles): u, f, r (FP64)

@@ -301,11 +301,23 @@ __device__ void tile_down_rest(const MgLevel& F, const MgLevel& C, float* su, co
   }
 }
 
-// Level 0 down phase: r = rhs - A Z in FP64 on the region (Z staged with one more ring),
-// F.f32 = r on owned points, then the FP32 smoothing of e from 0 and the restriction.
-// Returns the max |r| over this block's owned points.
+// Z at (i, j) for the residual stencils: grid values, the odd reflection -Z one point beyond
+// a boundary (the fourth-order ghost value), 0 farther out (never used).
+__device__ __forceinline__ double z_ghost(const MgLevel& F, int i, int j) {
+  double sgn = 1.0;
+  if (i == -1) { i = 1; sgn = -sgn; }
+  if (i == F.nx + 1) { i = F.nx - 1; sgn = -sgn; }
+  if (j == -1) { j = 1; sgn = -sgn; }
+  if (j == F.ny + 1) { j = F.ny - 1; sgn = -sgn; }
+  if (i < 0 || i > F.nx || j < 0 || j > F.ny) return 0.0;
+  return sgn * F.u[(int64_t)j * F.sy + i];
+}
+
+// Level 0 down phase: r = rhs - A Z in FP64 on the region (Z staged with two more rings; A is
+// the second- or fourth-order operator), F.f32 = r on owned points, then the FP32 smoothing
+// of e from 0 and the restriction.  Returns the max |r| over this block's owned points.
 __device__ double down0_tiles(const MgLevel& F, const MgLevel& C, int axis, unsigned char* smraw) {
-  const int T = F.tile, H = kMgHalo, Wd = T + 2 * H, Wz = Wd + 2;
+  const int T = F.tile, H = kMgHalo, Wd = T + 2 * H, Wz = Wd + 4;
   const int ntx = (F.nx - 1 + T - 1) / T, nty = (F.ny - 1 + T - 1) / T;
   double* zs = reinterpret_cast<double*>(smraw);
   float* su = reinterpret_cast<float*>(zs + Wz * Wz);
@@ -314,21 +326,27 @@ __device__ double down0_tiles(const MgLevel& F, const MgLevel& C, int axis, unsi
   for (int tile = blockIdx.x; tile < ntx * nty; tile += gridDim.x) {
     const int i0 = 1 + (tile % ntx) * T, j0 = 1 + (tile / ntx) * T;
     const int is = i0 - H, js = j0 - H;
-    for (int t = threadIdx.x; t < Wz * Wz; t += blockDim.x) {
-      const int i = is - 1 + t % Wz, j = js - 1 + t / Wz;
-      const bool in = i >= 0 && i <= F.nx && j >= 0 && j <= F.ny;
-      zs[t] = in ? F.u[(int64_t)j * F.sy + i] : 0.0;
-    }
+    for (int t = threadIdx.x; t < Wz * Wz; t += blockDim.x)
+      zs[t] = z_ghost(F, is - 2 + t % Wz, js - 2 + t / Wz);
     __syncthreads();
     for (int t = threadIdx.x; t < Wd * Wd; t += blockDim.x) {
       const int i = is + t % Wd, j = js + t / Wd;
       double r = 0.0;
       if (i >= 1 && i <= F.nx - 1 && j >= 1 && j <= F.ny - 1) {
         const int64_t p = (int64_t)j * F.sy + i;
-        const int x = (j - js + 1) * Wz + (i - is + 1);
+        const int x = (j - js + 2) * Wz + (i - is + 2);
         const bool hi = upper(F, axis, i, j, 0);
-        const double s = neighbours<2, double>(zs, x, Wz, 0, Co<double>::a(F, hi));
-        r = F.f[p] - (Co<double>::d(F, hi) * zs[x] - s);
+        if (F.order4) {
+          const double* a4 = hi ? F.a4_hi : F.a4_lo;
+          const double* b4 = hi ? F.b4_hi : F.b4_lo;
+          const double s = a4[0] * (zs[x - 1] + zs[x + 1]) + a4[1] * (zs[x - Wz] + zs[x + Wz]) +
+                           b4[0] * (zs[x - 2] + zs[x + 2]) +
+                           b4[1] * (zs[x - 2 * Wz] + zs[x + 2 * Wz]);
+          r = F.f[p] - ((hi ? F.d4_hi : F.d4_lo) * zs[x] - s);
+        } else {
+          const double s = neighbours<2, double>(zs, x, Wz, 0, Co<double>::a(F, hi));
+          r = F.f[p] - (Co<double>::d(F, hi) * zs[x] - s);
+        }
         if (i >= i0 && i < i0 + T && j >= j0 && j < j0 + T) {
           m = nanmax(m, fabs(r));
           F.f32[p] = (float)r;
@@ -368,7 +386,7 @@ __device__ void down_tiles(const MgLevel& F, const MgLevel& C, int axis, unsigne
 // Up phase: e = F.v32 + P (coarse correction e_c), one red-black sweep, then F.u32 = e on
 // owned points (levels > 0) or Z += e in FP64 (level 0).
 __device__ void up_tiles(const MgLevel& F, const MgLevel& C, const float* ec, bool level0,
-                         int axis, unsigned char* smraw) {
+                         double omega_dc, int axis, unsigned char* smraw) {
   const int T = F.tile, H = 2, Wd = T + 2 * H;
   const int ntx = (F.nx - 1 + T - 1) / T, nty = (F.ny - 1 + T - 1) / T;
   float* su = reinterpret_cast<float*>(smraw);
@@ -399,7 +417,7 @@ __device__ void up_tiles(const MgLevel& F, const MgLevel& C, const float* ec, bo
       const int64_t p = (int64_t)j * F.sy + i;
       const float e = su[(j - js) * Wd + (i - is)];
       if (level0)
-        F.u[p] += (double)e;
+        F.u[p] = fma(omega_dc, (double)e, F.u[p]);
       else
         F.u32[p] = e;
     }
@@ -569,7 +587,7 @@ __global__ void __launch_bounds__(kMgThreads, 2) k_imp_step(const ImpArgs a) {
       }
       grid_sync(a.bar, a.err);
       for (int l = a.lc - 1; l >= 0; --l) {
-        up_tiles(a.lev[l], a.lev[l + 1], a.lev[l + 1].u32, l == 0, axis, smraw);
+        up_tiles(a.lev[l], a.lev[l + 1], a.lev[l + 1].u32, l == 0, a.omega_dc, axis, smraw);
         grid_sync(a.bar, a.err);
       }
     }
@@ -741,6 +759,24 @@ bool mg_plan_levels(const Geom& g, const double* h, double c2_lo, double c2_hi, 
   }
   *smem_elems = off;
   return true;
+}
+
+void mg_set_order4(MgLevel* lev0, const double* h, double c2_lo, double c2_hi, double dt, int dim) {
+  const double kap = 0.5 * dt * dt;
+  double slo = 0.0, shi = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const bool on = a < dim;
+    const double ih2 = on ? 1.0 / (h[a] * h[a]) : 0.0;
+    lev0->a4_lo[a] = kap * c2_lo * ih2 * 16.0 / 12.0;
+    lev0->a4_hi[a] = kap * c2_hi * ih2 * 16.0 / 12.0;
+    lev0->b4_lo[a] = -kap * c2_lo * ih2 / 12.0;
+    lev0->b4_hi[a] = -kap * c2_hi * ih2 / 12.0;
+    slo += kap * c2_lo * ih2 * 30.0 / 12.0;
+    shi += kap * c2_hi * ih2 * 30.0 / 12.0;
+  }
+  lev0->d4_lo = 1.0 + slo;
+  lev0->d4_hi = 1.0 + shi;
+  lev0->order4 = 1;
 }
 
 cudaError_t mg_launch_config(int dim, int lc, int64_t smem_elems, MgLevel* lev, int* grid,

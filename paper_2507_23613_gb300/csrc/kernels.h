@@ -155,6 +155,12 @@ struct MgLevel {
   double d_lo, d_hi;          // diagonal of A: 1 + 2 sum_i a_i
   double dinv_lo, dinv_hi;    // 1 / diagonal
   float a32_lo[3], a32_hi[3];   // the same coefficients rounded to FP32
+  // Level 0 with the fourth-order operator (order4 = 1): A_4 = I - (dt^2/2) c^2 Delta_4h with
+  // first-neighbour weights a4 = (4/3)(dt^2/2) c^2 / h_i^2, second-neighbour weights
+  // b4 = -(dt^2/2) c^2 / (12 h_i^2) and diagonal d4 = 1 + (5/2)(dt^2/2) c^2 sum_i 1/h_i^2;
+  // the ghost value beyond the boundary is minus the point next to it.
+  int order4;
+  double a4_lo[3], a4_hi[3], b4_lo[3], b4_hi[3], d4_lo, d4_hi;
   float d32_lo, d32_hi, dinv32_lo, dinv32_hi;
   double* u;                  // FP64 arrays: level 0's iterate Z and right-hand side; the
   double* f;                  // grid-wide levels and the first coarse level of a 3D hierarchy
@@ -174,10 +180,11 @@ struct MgLevel {
 constexpr int kMgTileMax = 64;
 constexpr int kMgHalo = 6;     // 2 nu1 + 2 with nu1 = 2
 // Shared memory in bytes of the tiled phases with tile edge T: level 0's down phase holds Z
-// (FP64, one more ring) and e, r (FP32); the other phases hold u and f (FP32).
+// (FP64, two more rings for the fourth-order residual) and e, r (FP32); the other phases hold
+// u and f (FP32).
 inline int64_t mg_tile_smem_bytes(int T) {
   const int64_t w = T + 2 * kMgHalo;
-  return (w + 2) * (w + 2) * 8 + 2 * w * w * 4;
+  return (w + 4) * (w + 4) * 8 + 2 * w * w * 4;
 }
 
 // Convergence test of one step solve: bits of non-negative doubles, so that atomicMax orders them.
@@ -195,6 +202,8 @@ struct ImpArgs {
   int layer_axis, nf;
   int nu1, nu2, coarse_sweeps, max_cycles;
   double tol;
+  double omega_dc;            // Z += omega_dc e: 1 (second order), 6/7 (fourth order, where the
+                              // second-order V-cycle preconditions A_4: eigenvalues in [1, 4/3])
   MgState* st;                // this step's test state
   MgState* st_next;           // next step's (receives max |rhs|), null on the last step
   MgCounters* counters;
@@ -224,6 +233,8 @@ struct ImpInit {
 // memory of the coarse CTA in elements (u and f of levels lc..nlev-1).
 bool mg_plan_levels(const Geom& g, const double* h, double c2_lo, double c2_hi, double dt,
                     MgLevel* lev, int* nlev, int* lc, int64_t* smem_elems);
+// Fourth-order coefficients of level 0 (sets lev0.order4).
+void mg_set_order4(MgLevel* lev0, const double* h, double c2_lo, double c2_hi, double dt, int dim);
 // Blocks of the step kernel's cooperative launch (1 when lc == 0) and its shared memory; in
 // 2D it also picks each grid-wide level's tile edge (64, 32, 16 or 8: fewest rounds of tiles
 // over the blocks times the tile's loaded points) and grows the shared memory to hold it.

@@ -58,18 +58,18 @@ CASES = {
 }
 
 
-def pair(name, filter_update=0, mg_tol=MG_TOL, n_p=1, mode=F.FILTER_OPTIMIZED):
+def pair(name, filter_update=0, mg_tol=MG_TOL, n_p=1, mode=F.FILTER_OPTIMIZED, order=2):
     n, length, omega, b, c_hi = CASES[name]
     wl = inputs.gaussian_workload(name, n, len(omega), omega, b, 17, length=length)
     kw = dict(n_p=n_p, filter_mode={F.FILTER_OPTIMIZED: 0, F.FILTER_TRADITIONAL: 1}[mode],
-              time_stepping="implicit", mg_tol=mg_tol, filter_update=filter_update)
+              time_stepping="implicit", mg_tol=mg_tol, filter_update=filter_update, order=order)
     c2 = 1.0
     if c_hi is not None:
         kw.update(c_lo=1.0, c_hi=c_hi, interface=0.5, layer_axis=len(n) - 1)
         c2 = inputs.two_layer_c2(n, length, 1.0, c_hi, 0.5)
     s = M.Solver(n, length, omega, dev(wl.forcing), **kw)
     p = W.make_problem(W.Grid(n, length), omega, wl.forcing, c2=c2, n_p=n_p, filter_mode=mode,
-                       time_stepping="implicit", explicit_filter=filter_update == 1)
+                       time_stepping="implicit", explicit_filter=filter_update == 1, order=order)
     assert s.setup["n_t"] == p.setup.n_t
     assert abs(s.setup["dt"] - p.setup.dt) < 1e-15 * p.setup.dt
     return s, p, wl
@@ -156,7 +156,38 @@ def test_implicit_graph_mode_and_batch():
     e.close()
 
 
+@pytest.mark.parametrize("name", ["grid_2d", "aniso_2d"])
+def test_implicit_fourth_order_pi_matches_oracle(name):
+    """Fourth-order L_4h (odd-reflection ghosts) in the FP64 residual, the second-order
+    multigrid as the correction solver (damped by 6/7).  The step tolerance is 1e-12: the
+    rounding floor of the fourth-order residual (diagonal ~500 on the anisotropic grid) lies
+    near 5e-14."""
+    s, p, wl = pair(name, order=4, mg_tol=1e-12)
+    v = random_v(wl, 6)
+    for forced in (True, False):
+        got = apply(s, v, forced)
+        want = W.apply_Pi(p, v, forced=forced)
+        assert np.all(rel_err(got, want) < TOL), (forced, rel_err(got, want))
+    st = s.mg_stats()
+    assert st["unconverged"] == 0
+
+
+def test_implicit_fourth_order_fixed_point_and_gmres():
+    s, p, wl = pair("grid_2d", order=4, n_p=2, mg_tol=1e-12)
+    U = W.helmholtz_direct(p)
+    assert np.all(rel_err(apply(s, U, True), U) < 1e-10)
+    s2, p2, wl2 = pair("grid_2d", order=4, mg_tol=0.0)
+    U2 = W.helmholtz_direct(p2)
+    v = torch.zeros(wl2.forcing.shape, dtype=torch.float64, device="cuda")
+    info = s2.solve_gmres(v, restart=100, tol=1e-10, max_iters=400)
+    assert np.all(rel_err(v.cpu().numpy(), U2) < 1e-7)
+    assert np.max(info["helmholtz_residual"]) < 1e-7
+
+
 def test_implicit_rejects_grids_without_a_small_level():
+    with pytest.raises(_lib.MfwhError) as err:
+        M.Solver((32, 32), (1.0, 1.0), [5.0, 9.0], time_stepping="implicit", order=4)
+    assert err.value.status == _lib.ERR_INVALID_ARG
     with pytest.raises(_lib.MfwhError) as err:
         M.Solver((101, 100), (1.0, 1.0), [5.0, 9.0], time_stepping="implicit")
     assert err.value.status == _lib.ERR_INVALID_ARG

@@ -123,6 +123,8 @@ def test_plan_matches_oracle_implicit():
     _compare_setup(big, n_p=big.n_p, time_stepping="implicit")
     wl3 = inputs.gaussian_workload("t3", (24, 20, 16), 4, [8.3, 12.1, 19.0, 27.5], 300.0, 5)
     _compare_setup(wl3, c_hi=1.5, n_p=2, time_stepping="implicit")
+    s4, _ = _compare_setup(wl, order=4, time_stepping="implicit")   # dt does not depend on order
+    assert s4["n_t"] == s["n_t"] and s4["dt"] == s["dt"]
 
 
 def _implicit_dt(omega1, n_p, n_t):
@@ -183,7 +185,7 @@ def test_adjusted_frequency_matches_definition():
     dict(order=4, time_block=8),       # fourth order takes one step per launch
     dict(time_stepping="implicit", precision=1),        # implicit runs in FP64 only
     dict(time_stepping="implicit", time_block=4),       # one step per launch
-    dict(time_stepping="implicit", order=4),            # second-order operator only
+    dict(time_stepping="implicit", order=4, n=(8, 8, 8), length=(1.0, 1.0, 1.0)),  # 2D only
     dict(time_stepping="implicit", steps_per_period=4),  # at least five steps per period
     dict(time_stepping="implicit", mg_tol=1.5),
     dict(time_stepping="implicit", mg_max_cycles=61),
