@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--ws-epochs", type=int, default=15)
     ap.add_argument("--ws-gen-seconds", type=float, default=300.0,
                     help="time limit of the training-data generation")
+    ap.add_argument("--implicit-scaling", action="store_true",
+                    help="implicit fourth-order MFWH from 129^2 to 2049^2 (the paper's MG table)")
     ap.add_argument("--implicit", action="store_true",
                     help="implicit trapezoidal time stepping (multigrid) beside explicit FP64")
     ap.add_argument("--cube", action="store_true",
@@ -602,6 +604,63 @@ def run_implicit(args):
     print(json.dumps(out), flush=True)
 
 
+# The paper's multigrid scaling table (Figure squareGridCpuScaling: square, order 4, implicit
+# time stepping, the three-frequency problem of eq. Nf3parameters, Ogmg to 1e-10 on a CPU):
+# grid spacing -> (wave solves, multigrid cycles per solve, CPU seconds).
+PAPER_MG_TABLE = {64: (22, 7.1, 5.6), 128: (22, 7.0, 14.3), 256: (22, 7.0, 49.9),
+                  512: (20, 6.7, 169.8), 1024: (20, 6.7, 690.9), 2048: (20, 6.7, 2862.0)}
+
+
+def run_implicit_scaling(args):
+    """O(N) check of implicit MFWH with multigrid on GB300: the three-frequency problem of
+    eq. Nf3parameters on the unit square, fourth-order operator, implicit trapezoidal steps
+    (10 per shortest period, multigrid to 1e-10), unrestarted GMRES to 1e-10, from 129^2 to
+    2049^2 (65^2 is below the library's minimum grid for fourth-order implicit stepping)."""
+    import torch
+    import paper_2507_23613_gb300 as M
+    from paper_2507_23613_gb300 import build, inputs
+    torch.cuda.set_device(0)
+    build.build()
+    M._lib.load()
+    rows = []
+    for n in (128, 256, 512, 1024, 2048):
+        wl = inputs.paper_three_frequency(n)
+        f = torch.from_numpy(wl.forcing).cuda()
+        s = M.Solver(wl.n, wl.length, wl.omega, f, n_p=wl.n_p, order=4, time_stepping="implicit")
+        v = torch.zeros_like(f)
+        s.solve_gmres(v, restart=5, tol=0.0, max_iters=5, raise_on_error=False)   # warm-up
+        v.zero_()
+        s.mg_stats(reset=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = s.solve_gmres(v, restart=300, tol=1e-10, max_iters=300, raise_on_error=False)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        st = s.mg_stats()
+        pts = (n + 1) ** 2
+        paper = PAPER_MG_TABLE[n]
+        rows.append({"grid": [n + 1, n + 1], "points": pts, "n_t": s.setup["n_t"],
+                     "wave_solves": info["pi_applications"], "gmres_status": int(info["status"]),
+                     "rel_residual": info["rel_residual"],
+                     "max_helmholtz_residual": float(np.max(info["helmholtz_residual"])),
+                     "mg_cycles_per_step": round(st["cycles"] / max(st["solves"], 1), 2),
+                     "mg_unconverged_steps": st["unconverged"], "seconds": round(sec, 3),
+                     "us_per_point": round(sec / pts * 1e6, 3),
+                     "paper_cpu": {"wave_solves": paper[0], "mg_cycles": paper[1],
+                                   "seconds": paper[2]}})
+        s.close()
+    out = {"metric": "implicit MFWH time to 1e-10 vs grid (O(N) scaling)", "unit": "s",
+           "value": rows[-1]["seconds"], "higher_is_better": False, "n_gpus": 1, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": "paper3freq_square_order4_implicit",
+                                          "omega": [5.1, 10.1, 15.1], "n_p": 2, "order": 4,
+                                          "steps_per_period": 10, "mg_tol": 1e-10,
+                                          "gmres_tol": 1e-10},
+           "rows": rows,
+           "paper_context": "Figure squareGridCpuScaling: CPU (Ogmg) seconds on the paper's "
+                            "machine; a different machine and solver, quoted as context"}
+    print(json.dumps(out), flush=True)
+
+
 def run_warm_start(args):
     """Learned warm start: MFWH-converged FP64 solutions of seeded problems train the network
     (inputs f_m / max|f_m| and omega_m / 45, target the shape V_m / max|V_m|, amplitude fitted to
@@ -738,6 +797,8 @@ def main():
         return run_warm_start(args) if rank == 0 else None
     if args.implicit:
         return run_implicit(args) if rank == 0 else None
+    if args.implicit_scaling:
+        return run_implicit_scaling(args) if rank == 0 else None
 
     import torch
     import paper_2507_23613_gb300 as M
