@@ -232,7 +232,7 @@ mfwh_status mfwh_solve_refined(mfwh_handle_t h, int restart, double inner_tol, i
                                double target, int max_refinements, double* v,
                                mfwh_solve_info* info);
 
-/* ---- many problems: graphs, batches, autotuning (SURVEY's batched workload; the paper
+/* ---- many problems: graphs, batches, autotuning (batched workloads; the paper
  * solves one problem at a time) ---------------------------------------------------- */
 
 /* CUDA-graph mode for one handle.  With enable != 0, each variant of the wave solve used by
@@ -242,7 +242,8 @@ mfwh_status mfwh_solve_refined(mfwh_handle_t h, int restart, double inner_tol, i
  * as one graph launch per application of Pi, between a device-to-device copy in and out.
  * Results are bit-identical to direct launches.  enable = 0 drops the graphs.  Synchronises
  * the handle's stream.  Capture happens on the first use of a variant: do not call the
- * handle inside another stream capture then. */
+ * handle inside another stream capture then.  Implicit handles (MFWH_TIME_IMPLICIT) accept
+ * the call and keep launching directly (N_t + 1 launches per Pi). */
 mfwh_status mfwh_set_graphs(mfwh_handle_t h, int enable);
 
 /* Solve count independent problems concurrently: one host thread per handle runs
@@ -250,7 +251,9 @@ mfwh_status mfwh_set_graphs(mfwh_handle_t h, int enable);
  * own stream (give the handles distinct streams to overlap them on the GPU; handles in graph
  * mode launch one graph per Pi).  seconds[i] (host array, may be NULL) receives the time from
  * the common start to the end of problem i's solve.  Handles must be distinct; infos may be
- * NULL.  Returns MFWH_OK when every solve converged, else the first failing status (hard
+ * NULL.  Implicit handles share one host thread and are solved one after another (their
+ * step kernels are cooperative launches that must not wait on each other's blocks).
+ * Returns MFWH_OK when every solve converged, else the first failing status (hard
  * errors before MFWH_ERR_NOT_CONVERGED) with its problem index in mfwh_last_error(). */
 mfwh_status mfwh_solve_batch(const mfwh_handle_t* handles, int count, int restart, double tol,
                              int max_iters, double* const* v, mfwh_solve_info* infos,
@@ -267,7 +270,7 @@ mfwh_status mfwh_solve_batch(const mfwh_handle_t* handles, int count, int restar
 mfwh_status mfwh_autotune(const mfwh_problem* prob, void* stream, int* time_block,
                           int* tile_shape, double* ms_per_step);
 
-/* ---- learned warm start (SURVEY's warm-start extension; the paper starts GMRES from zero)
+/* ---- learned warm start (an extension; the paper starts GMRES from zero)
  * A small convolutional network maps one frequency's forcing (and its frequency, as a second
  * constant channel) to an initial iterate V_m^0.  L layers of 3 x 3 "same" convolutions
  * (zero padding) with bias and ReLU after every layer but the last; in_channels inputs,
