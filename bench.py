@@ -511,18 +511,29 @@ def run_implicit(args):
     torch.cuda.set_device(0)
     build.build()
     M._lib.load()
-    wl = inputs.square_large(args.seed)
+    layer = {}
+    restart = RESTART
+    if args.cube:
+        # the 3D workload instead: 257^3, two layers, N_f = 4, GMRES(15)
+        wl = inputs.cube_layered(args.seed + 1000)
+        lay = wl.layer
+        layer = dict(c_lo=lay["c_lo"], c_hi=lay["c_hi"], interface=lay["interface"],
+                     layer_axis=lay["axis"])
+        restart = 15
+    else:
+        wl = inputs.square_large(args.seed)
+    dim = len(wl.n)
     f = torch.from_numpy(wl.forcing).cuda()
     stream = torch.cuda.Stream()
     hbm_peak, peak_kind = peaks()
     res = {}
     for name, kw in (("implicit", dict(time_stepping="implicit")), ("explicit", {})):
         s = M.Solver(wl.n, wl.length, wl.omega, f, stream=stream.cuda_stream, n_p=wl.n_p,
-                     cfl=wl.cfl, **kw)
+                     cfl=wl.cfl, **kw, **layer)
         n_t = s.setup["n_t"]
         v = torch.zeros_like(f)
         for _ in range(max(1, args.warmup)):
-            s.solve_gmres(v, restart=RESTART, tol=0.0, max_iters=RESTART, raise_on_error=False)
+            s.solve_gmres(v, restart=restart, tol=0.0, max_iters=restart, raise_on_error=False)
         if name == "implicit":
             s.mg_stats(reset=True)
         ms_tot, step_ms, step_l, launches, apps = 0.0, 0.0, 0, 0, 0
@@ -532,7 +543,7 @@ def run_implicit(args):
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             ev0.record(stream)
-            info = s.solve_gmres(v, restart=RESTART, tol=0.0, max_iters=RESTART,
+            info = s.solve_gmres(v, restart=restart, tol=0.0, max_iters=restart,
                                  raise_on_error=False)
             ev1.record(stream)
             torch.cuda.synchronize()
@@ -555,15 +566,15 @@ def run_implicit(args):
                       "mg_unconverged_steps": st["unconverged"]})
             interior = wl.interior_points
             # one forced map per cycle, the rest homogeneous
-            per_app = [implicit_bytes_per_point(wl.nf, i == 0, cps) for i in range(apps // k)]
+            per_app = [implicit_bytes_per_point(wl.nf, i == 0, cps, dim) for i in range(apps // k)]
             alg = interior * n_t * sum(per_app) * k
             gbs = alg / (step_ms * 1e-3) / 1e9
             r["roofline"] = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak,
                              "unit": "GB/s", "frac": round(gbs / hbm_peak, 4),
-                             "peak_source": peak_kind, "kernel": "k_imp_step<2>",
+                             "peak_source": peak_kind, "kernel": f"k_imp_step<{dim}>",
                              "alg_bytes_per_launch": round(alg / step_l),
                              "avg_launch_us": round(step_ms * 1e3 / step_l, 2),
-                             "note": "finest-level multigrid arrays (3 x 8.4 MB) are L2-resident"}
+                             "note": "2D: finest-level multigrid arrays are L2-resident"}
         if args.solve:
             # time to solution: unrestarted GMRES to 1e-8 (the paper's solver), and FP64
             # defect correction to max_m r_h <= 1e-6 (inner GMRES to 1e-6 relative)
@@ -594,9 +605,8 @@ def run_implicit(args):
     out = {"metric": "implicit vs explicit FP64 MFWH wave solve", "unit": "ms",
            "value": res["implicit"]["ms_per_wave_solve"], "higher_is_better": False,
            "n_gpus": 1, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"square{wl.n[0] + 1}x{wl.n[1] + 1}_nf{wl.nf}_np{wl.n_p}"
-                                  f"_implicit_gmres{RESTART}_cycle",
-                      "grid": [wl.n[0] + 1, wl.n[1] + 1], "nf": wl.nf, "n_p": wl.n_p,
+           "config": {"workload": f"{wl.name}_implicit_gmres{restart}_cycle",
+                      "grid": [k_ + 1 for k_ in wl.n], "nf": wl.nf, "n_p": wl.n_p,
                       "steps_per_period": 10, "mg_tol": 1e-10},
            "implicit": res["implicit"], "explicit": res["explicit"],
            "speedup_per_wave_solve": round(res["explicit"]["ms_per_wave_solve"]
@@ -791,6 +801,8 @@ def main():
         return run_reference(args, rank, world)
     if args.batched:
         return run_batched(args) if rank == 0 else None
+    if args.implicit:
+        return run_implicit(args) if rank == 0 else None
     if args.cube:
         return run_cube(args) if rank == 0 else None
     if args.warm_start:

@@ -104,6 +104,24 @@ def test_implicit_pi_matches_oracle(name):
     assert np.array_equal(edge, got)
 
 
+@pytest.mark.parametrize("nf", [1, 16])
+def test_implicit_pi_extreme_frequency_counts(nf):
+    """One and the maximum number of frequencies (traditional filters: both sides use the
+    closed-form parameters of eq. origParamAdjust)."""
+    om = np.linspace(5.0, 5.0 + 3.0 * (nf - 1), nf)
+    n, length = (128, 128), (1.0, 1.0)
+    wl = inputs.gaussian_workload("nfimp", n, nf, om, 150.0, 40 + nf)
+    n_p = 2 if nf > 1 else 1
+    s = M.Solver(n, length, om, dev(wl.forcing), n_p=n_p, filter_mode=1,
+                 time_stepping="implicit", mg_tol=MG_TOL)
+    p = W.make_problem(W.Grid(n, length), om, wl.forcing, n_p=n_p,
+                       filter_mode=F.FILTER_TRADITIONAL, time_stepping="implicit")
+    assert s.setup["n_t"] == p.setup.n_t
+    v = random_v(wl, 9)
+    got = apply(s, v, True)
+    assert np.all(rel_err(got, W.apply_Pi(p, v, forced=True)) < TOL)
+
+
 def test_implicit_pi_explicit_filter_and_traditional():
     s, p, wl = pair("grid_2d", filter_update=1, mode=F.FILTER_TRADITIONAL)
     v = random_v(wl, 8)
