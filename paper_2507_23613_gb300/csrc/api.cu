@@ -869,18 +869,18 @@ mfwh_status mfwh_create(const mfwh_problem* prob, void* stream, mfwh_handle_t* o
       mg_set_order4(&A.lev[0], P.s.h, P.c2_lo, P.c2_hi, P.s.dt, P.dim);
     }
     A.omega_dc = P.order == 4 ? 6.0 / 7.0 : 1.0;
-    // Level arrays (bytes counted in 4-byte words).  FP64 defect correction (2D with
-    // grid-wide levels): level 0 holds Z, rhs (FP64) and e, r (FP32); levels 1..lc-1 hold u,
-    // e, rhs (FP32); level lc holds u, rhs (FP32).  Otherwise (FP64 V-cycles): u, f, r (FP64)
-    // below level lc and u, f (FP64) at level lc.
+    // Level arrays (bytes counted in 4-byte words).  FP64 defect correction (grid-wide
+    // levels): level 0 holds Z, rhs (FP64) and the FP32 correction arrays; levels 1..lc-1 hold
+    // three FP32 arrays; level lc holds u, rhs (FP32).  One-CTA hierarchies (FP64 V-cycles):
+    // u, f (FP64) at level 0 = lc.
     const bool mixed = mg_mixed(P.dim, A.lc);
     int64_t words = 0;
     for (int l = 0; l <= A.lc; ++l) {
       const int64_t n = A.lev[l].points;
       if (mixed)
-        words += l == 0 ? 4 * n + 2 * n : (l < A.lc ? 3 * n : 2 * n);
+        words += l == 0 ? 4 * n + (P.dim == 3 ? 3 : 2) * n : (l < A.lc ? 3 * n : 2 * n);
       else
-        words += (l < A.lc ? 3 : 2) * 2 * n;
+        words += 2 * 2 * n;
     }
     e = cudaMalloc(&h->imp_mem, 4 * words);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->imp_mem, 0, 4 * words, h->stream);
@@ -897,6 +897,7 @@ mfwh_status mfwh_create(const mfwh_problem* prob, void* stream, mfwh_handle_t* o
           L.f = take64(n);
           L.v32 = take32(n);
           L.f32 = take32(n);
+          if (P.dim == 3) L.u32 = take32(n);
         } else {
           L.u32 = take32(n);
           L.f32 = take32(n);
@@ -905,7 +906,6 @@ mfwh_status mfwh_create(const mfwh_problem* prob, void* stream, mfwh_handle_t* o
       } else {
         L.u = take64(n);
         L.f = take64(n);
-        if (l < A.lc) L.r = take64(n);
       }
     }
     e = mg_launch_config(P.dim, A.lc, smem_d, A.lev, &h->imp_grid, &h->imp_smem);

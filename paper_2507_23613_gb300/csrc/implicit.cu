@@ -19,8 +19,9 @@
 // the residual r = rhs - A Z in FP64, solves A e = r approximately by one FP32 V-cycle from
 // e = 0, and adds e to Z in FP64, so the iterate converges to the FP64 solution at the
 // V-cycle's rate while the smoothing runs on the FP32 pipes (GB300 issues FP64 arithmetic at
-// a small fraction of its FP32 rate).  3D hierarchies and hierarchies held by one CTA run
-// the V-cycles on Z itself in FP64.
+// a small fraction of its FP32 rate).  2D grid-wide levels run in tiled shared-memory phases,
+// 3D ones in grid-wide phases.  Hierarchies held by one CTA (grids of at most 5000 points)
+// run the V-cycles on Z itself in FP64.
 //
 // One step is one launch.  When the hierarchy has grid-wide levels the launch is
 // cooperative (all blocks resident) and phases are separated by a grid barrier whose waits
@@ -172,6 +173,57 @@ __device__ double residual_pass(const MgLevel& L, const double* u, const double*
     m = nanmax(m, fabs(res));
   }
   return m;
+}
+
+// Residual of the interior points stored into r (type R).
+template <int DIM, typename R>
+__device__ void residual_store(const MgLevel& L, const R* u, const R* f, R* r, int axis,
+                               uint32_t t0, uint32_t stride) {
+  const uint32_t mx = (uint32_t)L.nx - 1, my = (uint32_t)L.ny - 1;
+  const uint32_t total = mx * my * (DIM == 3 ? (uint32_t)L.nz - 1 : 1u);
+  for (uint32_t t = t0; t < total; t += stride) {
+    const int i = 1 + (int)(t % mx);
+    const uint32_t rest = t / mx;
+    const int j = 1 + (int)(rest % my);
+    const int k = DIM == 3 ? 1 + (int)(rest / my) : 0;
+    r[(int64_t)k * L.sz + (int64_t)j * L.sy + i] = residual_at<DIM, R>(L, u, f, axis, i, j, k);
+  }
+}
+
+// Level 0 of a grid-wide 3D hierarchy: r = rhs - A Z in FP64 into f32 (the correction's
+// right-hand side), e = 0 in u32; returns the max |r| over this thread's points.
+template <int DIM>
+__device__ double residual_to32(const MgLevel& L, int axis, uint32_t t0, uint32_t stride) {
+  const uint32_t mx = (uint32_t)L.nx - 1, my = (uint32_t)L.ny - 1;
+  const uint32_t total = mx * my * (DIM == 3 ? (uint32_t)L.nz - 1 : 1u);
+  double m = 0.0;
+  for (uint32_t t = t0; t < total; t += stride) {
+    const int i = 1 + (int)(t % mx);
+    const uint32_t rest = t / mx;
+    const int j = 1 + (int)(rest % my);
+    const int k = DIM == 3 ? 1 + (int)(rest / my) : 0;
+    const double res = residual_at<DIM, double>(L, L.u, L.f, axis, i, j, k);
+    const int64_t p = (int64_t)k * L.sz + (int64_t)j * L.sy + i;
+    L.f32[p] = (float)res;
+    L.u32[p] = 0.0f;
+    m = nanmax(m, fabs(res));
+  }
+  return m;
+}
+
+// Z += omega e at the interior points (FP64).
+template <int DIM>
+__device__ void add_correction(const MgLevel& L, double omega, uint32_t t0, uint32_t stride) {
+  const uint32_t mx = (uint32_t)L.nx - 1, my = (uint32_t)L.ny - 1;
+  const uint32_t total = mx * my * (DIM == 3 ? (uint32_t)L.nz - 1 : 1u);
+  for (uint32_t t = t0; t < total; t += stride) {
+    const int i = 1 + (int)(t % mx);
+    const uint32_t rest = t / mx;
+    const int j = 1 + (int)(rest % my);
+    const int k = DIM == 3 ? 1 + (int)(rest / my) : 0;
+    const int64_t p = (int64_t)k * L.sz + (int64_t)j * L.sy + i;
+    L.u[p] = fma(omega, (double)L.u32[p], L.u[p]);
+  }
 }
 
 // Full weighting of the fine residual onto the coarse interior: weights 1/2 at offset 0 and
@@ -608,50 +660,49 @@ __global__ void __launch_bounds__(kMgThreads, 2) k_imp_step(const ImpArgs a) {
     cta_store<double>(a, sm);
     __syncthreads();
   } else {
-    // grid-wide FP64 V-cycles on Z (3D)
+    // 3D: FP64 defect correction with grid-wide FP32 V-cycles (one barrier per phase)
     const uint32_t g0 = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
     for (;; ++c) {
+      const double rm = residual_to32<DIM>(L0, axis, g0, gs);
+      const double bm = block_max(rm, red);
+      if (threadIdx.x == 0) atomic_max_nonneg(&a.st->rmax[c], bm);
+      grid_sync(a.bar, a.err);
+      if (load_nonneg(&a.st->rmax[c]) <= thresh) { converged = true; break; }
+      if (c == a.max_cycles) break;
       for (int l = 0; l < a.lc; ++l) {
         const MgLevel& L = a.lev[l];
         for (int s = 0; s < a.nu1; ++s) {
-          rb_half<DIM, double>(L, L.u, L.f, 0, axis, g0, gs);
+          rb_half<DIM, float>(L, L.u32, L.f32, 0, axis, g0, gs);
           grid_sync(a.bar, a.err);
-          rb_half<DIM, double>(L, L.u, L.f, 1, axis, g0, gs);
+          rb_half<DIM, float>(L, L.u32, L.f32, 1, axis, g0, gs);
           grid_sync(a.bar, a.err);
         }
-        const double rm = residual_pass<DIM>(L, L.u, L.f, L.r, axis, g0, gs);
-        if (l == 0) {
-          const double bm = block_max(rm, red);
-          if (threadIdx.x == 0) atomic_max_nonneg(&a.st->rmax[c], bm);
-        }
+        residual_store<DIM, float>(L, L.u32, L.f32, L.v32, axis, g0, gs);
         grid_sync(a.bar, a.err);
-        if (l == 0) {
-          if (load_nonneg(&a.st->rmax[c]) <= thresh) { converged = true; break; }
-          if (c == a.max_cycles) break;
-        }
         const MgLevel& C = a.lev[l + 1];
-        restrict_pass<DIM, double>(L, L.r, nullptr, nullptr, C, C.f, C.u, axis, g0, gs);
+        restrict_pass<DIM, float>(L, L.v32, nullptr, nullptr, C, C.f32, C.u32, axis, g0, gs);
         grid_sync(a.bar, a.err);
       }
-      if (converged || c == a.max_cycles) break;
       if (blockIdx.x == 0) {
-        double* sm = reinterpret_cast<double*>(smraw);
-        cta_load<double>(a, sm, false);
-        cta_vcycle<DIM, double>(a, sm, a.lc, false);
-        cta_store<double>(a, sm);
+        float* sm = reinterpret_cast<float*>(smraw);
+        cta_load<float>(a, sm, false);
+        cta_vcycle<DIM, float>(a, sm, a.lc, false);
+        cta_store<float>(a, sm);
       }
       grid_sync(a.bar, a.err);
       for (int l = a.lc - 1; l >= 0; --l) {
         const MgLevel& L = a.lev[l];
-        prolong_pass<DIM, double>(a.lev[l + 1], a.lev[l + 1].u, L, L.u, g0, gs);
+        prolong_pass<DIM, float>(a.lev[l + 1], a.lev[l + 1].u32, L, L.u32, g0, gs);
         grid_sync(a.bar, a.err);
         for (int s = 0; s < a.nu2; ++s) {
-          rb_half<DIM, double>(L, L.u, L.f, 0, axis, g0, gs);
+          rb_half<DIM, float>(L, L.u32, L.f32, 0, axis, g0, gs);
           grid_sync(a.bar, a.err);
-          rb_half<DIM, double>(L, L.u, L.f, 1, axis, g0, gs);
+          rb_half<DIM, float>(L, L.u32, L.f32, 1, axis, g0, gs);
           grid_sync(a.bar, a.err);
         }
       }
+      add_correction<DIM>(L0, a.omega_dc, g0, gs);
+      grid_sync(a.bar, a.err);
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -786,7 +837,7 @@ cudaError_t mg_launch_config(int dim, int lc, int64_t smem_elems, MgLevel* lev, 
   constexpr int kSmemBound = 120 * 1024;
   const bool mixed = mg_mixed(dim, lc);
   int64_t need = smem_elems * (mixed ? 4 : 8);
-  if (mixed) need = std::max(need, mg_tile_smem_bytes(kMgTileMax));
+  if (mixed && dim == 2) need = std::max(need, mg_tile_smem_bytes(kMgTileMax));
   *smem = (size_t)need;
   if (*smem > (size_t)kSmemBound) return cudaErrorInvalidValue;
   const void* fn = dim == 3 ? (const void*)k_imp_step<3> : (const void*)k_imp_step<2>;
@@ -803,7 +854,7 @@ cudaError_t mg_launch_config(int dim, int lc, int64_t smem_elems, MgLevel* lev, 
     return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
   *grid = sms * occ;
-  if (mixed) {
+  if (mixed && dim == 2) {
     for (int l = 0; l < lc; ++l) {
       int best = kMgTileMax;
       int64_t best_cost = -1;

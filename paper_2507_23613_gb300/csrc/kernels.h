@@ -162,12 +162,12 @@ struct MgLevel {
   int order4;
   double a4_lo[3], a4_hi[3], b4_lo[3], b4_hi[3], d4_lo, d4_hi;
   float d32_lo, d32_hi, dinv32_lo, dinv32_hi;
-  double* u;                  // FP64 arrays: level 0's iterate Z and right-hand side; the
-  double* f;                  // grid-wide levels and the first coarse level of a 3D hierarchy
-  double* r;                  // residual (grid-wide 3D levels)
-  float* u32;                 // FP32 arrays of a 2D hierarchy: correction after the up phase,
-  float* v32;                 // after the down phase, and the level's right-hand side (level 0:
-  float* f32;                 // the FP64 residual rhs - A Z rounded to FP32)
+  double* u;                  // FP64 arrays: level 0's iterate Z and right-hand side (and the
+  double* f;                  // levels of a one-CTA hierarchy, in shared memory)
+  float* u32;                 // FP32 arrays: the correction (2D: after the up phase), the 2D
+  float* v32;                 // correction after the down phase or the 3D residual of the
+  float* f32;                 // correction equation, and the level's right-hand side (level 0:
+                              // the FP64 residual rhs - A Z rounded to FP32)
   int tile;                   // grid-wide 2D levels: edge of the square tile of owned points
   int64_t smem;               // coarse levels: offset in elements of u in shared memory (f follows)
 };
@@ -240,8 +240,9 @@ void mg_set_order4(MgLevel* lev0, const double* h, double c2_lo, double c2_hi, d
 // over the blocks times the tile's loaded points) and grows the shared memory to hold it.
 cudaError_t mg_launch_config(int dim, int lc, int64_t smem_elems, MgLevel* lev, int* grid,
                              size_t* smem);
-// A 2D hierarchy with grid-wide levels (lc > 0) runs the FP32 defect-correction cycles.
-inline bool mg_mixed(int dim, int lc) { return dim == 2 && lc > 0; }
+// A hierarchy with grid-wide levels (lc > 0) runs the FP32 defect-correction cycles (tiled
+// phases in 2D, grid-wide phases in 3D).
+inline bool mg_mixed(int dim, int lc) { return (dim == 2 || dim == 3) && lc > 0; }
 // W^0 = sum_m v_m, q_m = w_{0,m} W^0, Z = 2 W^0, rhs = 2 W^0 - dt^2 F^0 (boundary 0) and
 // st->bmax = max |rhs|.  v may be null (W^0 = 0).
 void launch_imp_init(int nf, const Geom& g, const double* v, double* W0, double* q,
