@@ -89,9 +89,11 @@ typedef struct {
   double c_delta;            /* c_delta of eq. LambdaRange (paper: 2) */
   int precision;             /* MFWH_PREC_FP64, MFWH_PREC_FP32_KAHAN or MFWH_PREC_FP32_BLOCKSUM */
   int time_block;            /* leapfrog steps per pass over HBM: 0 = library default (1 for
-                                FP64; 16 for FP32 in 2D), 1 = one step per kernel launch,
-                                4 or 8 (or 16 for FP32) = temporal blocking with that depth
-                                (2D grids only).  Results are bit-identical for every depth. */
+                                FP64 and for 3D; 16 for FP32 in 2D), 1 = one step per kernel
+                                launch; 2D: 4 or 8 (or 16 for FP32) = temporal blocking with
+                                that depth; 3D: 2 or 4 for the FP32 precisions.  Results are
+                                bit-identical for every depth (FP32_BLOCKSUM: for every depth
+                                with the same partial-sum length). */
   int order;                 /* order p of the spatial operator L_{ph}: 2 (0 means 2) or 4.
                                 Order 4: (-W_{j-2} + 16 W_{j-1} - 30 W_j + 16 W_{j+1} - W_{j+2})
                                 / (12 h^2) per axis, ghost values W_{-1} = -W_1 and
@@ -262,7 +264,8 @@ mfwh_status mfwh_solve_batch(const mfwh_handle_t* handles, int count, int restar
 /* Autotuner for the blocked wave kernels.  Times the first steps (at most 96) of a
  * homogeneous wave solve of prob on the current device for each candidate temporal depth and
  * tile shape (FP32, 2D: depths 4, 8, 16 x tile shapes 0, 1, 2; FP64, 2D: depths 1, 4, 8;
- * 3D: depth 1), keeping the fastest: *time_block and *tile_shape receive it, *ms_per_step
+ * FP32, 3D: depths 1, 2, 4; FP64 3D and fourth order: depth 1), keeping the fastest:
+ * *time_block and *tile_shape receive it, *ms_per_step
  * (may be NULL) its time per leapfrog step.  Results are cached per device, grid, number of
  * frequencies and precision for the life of the process.  Allocates (and frees) one handle's
  * workspace per candidate on the given stream; synchronous.  Implicit time stepping has no

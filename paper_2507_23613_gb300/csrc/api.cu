@@ -242,8 +242,12 @@ mfwh_status apply_pi32(mfwh_handle_t h, const double* vin, double* vout, int for
       a.steps = std::min(P.time_block, n_run - n0);
       a.last = n0 + a.steps == n_t;
       const float* D_in = n0 == 0 ? nullptr : h->W32[2 * cur + 1];
-      launch_tb2d32(nf, h->geom, h->W32[2 * cur], D_in, h->W32[2 * (1 - cur)],
-                    h->W32[2 * (1 - cur) + 1], h->f32, h->qs, h->qc, vout, vsub, a, st);
+      if (P.dim == 3)
+        launch_tb3d32(nf, h->geom, h->W32[2 * cur], D_in, h->W32[2 * (1 - cur)],
+                      h->W32[2 * (1 - cur) + 1], h->f32, h->qs, h->qc, vout, vsub, a, st);
+      else
+        launch_tb2d32(nf, h->geom, h->W32[2 * cur], D_in, h->W32[2 * (1 - cur)],
+                      h->W32[2 * (1 - cur) + 1], h->f32, h->qs, h->qc, vout, vsub, a, st);
       ++launches;
       n0 += a.steps;
       cur = 1 - cur;
@@ -1364,8 +1368,10 @@ mfwh_status mfwh_autotune(const mfwh_problem* prob, void* stream, int* time_bloc
     }
   }
   std::vector<std::pair<int, int>> cand;
-  if (P.dim == 3 || P.order == 4) {
+  if (P.order == 4 || (P.dim == 3 && P.precision == MFWH_PREC_FP64)) {
     cand = {{1, 0}};
+  } else if (P.dim == 3) {
+    cand = {{1, 0}, {2, 0}, {4, 0}};
   } else if (P.precision == MFWH_PREC_FP64) {
     cand = {{1, 0}, {4, 0}, {8, 0}};
   } else {

@@ -112,6 +112,11 @@ void launch_last32(int nf, const Geom& g, const float* W, const float* D, const 
 void launch_tb2d32(int nf, const Geom& g, const float* W_in, const float* D_in, float* W_out,
                    float* D_out, const float* f, float* qs, float* qc, double* vout,
                    const double* vsub, const TB32Host& h, cudaStream_t st);
+// Up to h.depth (2 or 4) steps of a 3D grid per launch (second-order operator); outputs must
+// not alias inputs.  Same arguments as launch_tb2d32 (tile shape ignored).
+void launch_tb3d32(int nf, const Geom& g, const float* W_in, const float* D_in, float* W_out,
+                   float* D_out, const float* f, float* qs, float* qc, double* vout,
+                   const double* vsub, const TB32Host& h, cudaStream_t st);
 void launch_to_float(const double* x, float* y, int64_t n, cudaStream_t st);
 
 // W^0 = sum_m v_m (0 on the boundary; v == nullptr gives W^0 = 0) and q_m = w0_m W^0.

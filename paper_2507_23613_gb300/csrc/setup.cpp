@@ -306,9 +306,15 @@ mfwh_status plan_problem(const mfwh_problem* p, Plan* out) {
       p->precision != MFWH_PREC_FP32_BLOCKSUM)
     return fail(MFWH_ERR_INVALID_ARG, "unsupported precision");
   const bool fp32 = p->precision != MFWH_PREC_FP64;
-  if (p->time_block != 0 && p->time_block != 1 && p->time_block != 4 && p->time_block != 8 &&
-      !(fp32 && p->time_block == 16))
+  if (p->dim == 3) {
+    if (p->time_block != 0 && p->time_block != 1 &&
+        !(fp32 && (p->time_block == 2 || p->time_block == 4)))
+      return fail(MFWH_ERR_INVALID_ARG,
+                  "3D time_block must be 0 or 1 (or 2 or 4 for the FP32 precisions)");
+  } else if (p->time_block != 0 && p->time_block != 1 && p->time_block != 4 &&
+             p->time_block != 8 && !(fp32 && p->time_block == 16)) {
     return fail(MFWH_ERR_INVALID_ARG, "time_block must be 0, 1, 4 or 8 (or 16 for FP32)");
+  }
   if (p->tile_shape < 0 || p->tile_shape > 2)
     return fail(MFWH_ERR_INVALID_ARG, "tile_shape must be 0, 1 or 2");
   if (p->filter_update != MFWH_UPDATE_IMPLICIT && p->filter_update != MFWH_UPDATE_EXPLICIT)
@@ -317,8 +323,6 @@ mfwh_status plan_problem(const mfwh_problem* p, Plan* out) {
     return fail(MFWH_ERR_INVALID_ARG, "order must be 2 or 4");
   if (p->order == 4 && p->time_block > 1)
     return fail(MFWH_ERR_INVALID_ARG, "the fourth-order operator takes one step per launch");
-  if (p->dim == 3 && p->time_block > 1)
-    return fail(MFWH_ERR_INVALID_ARG, "temporal blocking is available for 2D grids only");
   if (p->time_stepping != MFWH_TIME_EXPLICIT && p->time_stepping != MFWH_TIME_IMPLICIT)
     return fail(MFWH_ERR_INVALID_ARG, "time_stepping must be explicit or implicit");
   const bool implicit = p->time_stepping == MFWH_TIME_IMPLICIT;

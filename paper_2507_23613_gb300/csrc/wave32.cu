@@ -27,7 +27,26 @@ W32Ops ops_for(int nf) {
   }
 }
 
+Tb3dFn tb3_for(int nf) {
+  switch ((nf + 1) / 2) {
+    case 1: return w32_tb3_p1(nf);
+    case 2: return w32_tb3_p2(nf);
+    case 3: return w32_tb3_p3(nf);
+    case 4: return w32_tb3_p4(nf);
+    case 5: return w32_tb3_p5(nf);
+    case 6: return w32_tb3_p6(nf);
+    case 7: return w32_tb3_p7(nf);
+    default: return w32_tb3_p8(nf);
+  }
+}
+
 }  // namespace
+
+void launch_tb3d32(int nf, const Geom& g, const float* W_in, const float* D_in, float* W_out,
+                   float* D_out, const float* f, float* qs, float* qc, double* vout,
+                   const double* vsub, const TB32Host& h, cudaStream_t st) {
+  tb3_for(nf)(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, h, st);
+}
 
 void launch_init32(int nf, const Geom& g, const double* v, float* W0, float* qs, float* qc,
                    const float* w0, cudaStream_t st) {

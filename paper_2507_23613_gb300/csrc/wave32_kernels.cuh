@@ -591,6 +591,159 @@ k_init32(const double* __restrict__ v, float* __restrict__ W0, float* __restrict
   }
 }
 
+// ---- temporally blocked 3D kernel ------------------------------------------------
+// Overlapped tiling in all three axes: a CTA owns a (32 - 2T) x 8 x 8 tile and keeps the tile
+// plus a halo of T points per side of W^n, W^{n+1} and D in shared memory, 32 points wide in
+// x so that a warp covers a row.  At step s of a launch of S steps it updates every interior
+// point of the tile grown by S - 1 - s points per side (reading the values of the previous
+// step one point further out), so the owned points are exact after S steps.  The rows (y, z)
+// of the region are spread over the warps and a row's points over the lanes.  Thread (x, y)
+// with x < 32 - 2T owns the 8 points of tile column (x, y) and keeps their filter sums in
+// registers (ACC as in k_tb2d32).  Each point update performs the operations of
+// step_point<NF, 3, 2> in the same order, so with ACC = 0 every depth is bit-identical to
+// one step per launch.
+constexpr int kT3W = 32, kT3Y = 8, kT3Z = 8, kT3Threads = kT3W * kT3Y;
+
+template <int NF, int T, int ACC>
+__global__ void __launch_bounds__(kT3Threads, ACC == 1 ? 2 : 1)
+k_tb3d32(const float* __restrict__ W_in, const float* __restrict__ D_in,
+         float* __restrict__ W_out, float* __restrict__ D_out, const float* __restrict__ f,
+         float* __restrict__ qs, float* __restrict__ qc, double* vout, const double* vsub,
+         const TB32Args<NF> a, const Last32Binv<NF> b, const Geom g) {
+  constexpr int BX = kT3W - 2 * T;
+  constexpr int EX = kT3W, EY = kT3Y + 2 * T, EZ = kT3Z + 2 * T;
+  constexpr int SXY = EX * EY, E = SXY * EZ;
+  extern __shared__ __align__(16) float sm3[];
+  float* Wc = sm3;
+  float* Wn = sm3 + E;
+  float* Dv = sm3 + 2 * E;
+  float* s_wq = sm3 + 3 * E;    // [T][NF]
+  float* s_fc = s_wq + T * NF;  // [T][NF]
+  const int tid = threadIdx.x;
+  const int tx = tid % kT3W, ty = tid / kT3W;   // lanes along x, warps along rows
+  const int64_t x0 = (int64_t)blockIdx.x * BX - T, y0 = (int64_t)blockIdx.y * kT3Y - T,
+                z0 = (int64_t)blockIdx.z * kT3Z - T;
+  {
+    const int64_t gx = x0 + tx;
+    for (int row = ty; row < EY * EZ; row += kT3Y) {
+      const int lz = row / EY, ly = row - lz * EY;
+      const int64_t gy = y0 + ly, gz = z0 + lz;
+      const bool in = gz >= 0 && gz <= g.nz && gy >= 0 && gy <= g.ny && gx >= 0 && gx <= g.nx;
+      const int64_t q = gz * g.szw + gy * g.syw + gx;
+      const int e = lz * SXY + ly * EX + tx;
+      const float w = in ? W_in[q] : 0.0f;
+      Wc[e] = w;
+      Wn[e] = w;
+      Dv[e] = (in && D_in != nullptr) ? D_in[q] : 0.0f;
+    }
+  }
+  for (int e = tid; e < a.steps * NF; e += kT3Threads) {
+    const int st = e / NF, m = e - st * NF;
+    const int n = a.n0 + st;
+    s_wq[e] = a.wq[(n + 1) * NF + m];
+    s_fc[e] = a.forced ? a.fc[n * NF + m] : 0.0f;
+  }
+  // the owned column (threads with tx < BX)
+  const bool owner = tx < BX;
+  const int64_t gx = x0 + T + tx, gy = y0 + T + ty;
+  const bool col_int = owner && gx > 0 && gx < g.nx && gy > 0 && gy < g.ny;
+  bool own_int[kT3Z];
+  float ks[kT3Z][NF], kc[kT3Z][NF], part[kT3Z][NF];
+#pragma unroll
+  for (int k = 0; k < kT3Z; ++k) {
+    const int64_t gz = z0 + T + k;
+    own_int[k] = col_int && gz > 0 && gz < g.nz;
+    const int64_t p = gz * g.sz + gy * g.sy + gx;
+#pragma unroll
+    for (int m = 0; m < NF; ++m) {
+      part[k][m] = 0.0f;
+      ks[k][m] = (ACC == 0 && own_int[k]) ? qs[m * g.points + p] : 0.0f;
+      kc[k][m] = (ACC == 0 && own_int[k]) ? qc[m * g.points + p] : 0.0f;
+    }
+  }
+  __syncthreads();
+  for (int s = 0; s < a.steps; ++s) {
+    const int r = a.steps - 1 - s;
+    const bool first = a.n0 + s == 0;
+    const Coef32 lo = first ? a.first_lo : a.reg_lo;
+    const Coef32 hi = first ? a.first_hi : a.reg_hi;
+    const float* fc = s_fc + s * NF;
+    // the region [T - r, T + tile + r) per axis
+    const int l0 = T - r, RY = kT3Y + 2 * r, RZ = kT3Z + 2 * r;
+    const int lx = l0 + tx;
+    const int64_t px = x0 + lx;
+    const bool x_ok = lx < T + BX + r && px > 0 && px < g.nx;
+    for (int row = ty; row < RY * RZ; row += kT3Y) {
+      const int rz = row / RY, ry = row - rz * RY;
+      const int ly = l0 + ry, lz = l0 + rz;
+      const int64_t py = y0 + ly, pz = z0 + lz;
+      if (!x_ok || py <= 0 || py >= g.ny || pz <= 0 || pz >= g.nz) continue;
+      const int l = lz * SXY + ly * EX + lx;
+      const int64_t li = g.layer_axis == 0 ? px : (g.layer_axis == 1 ? py : pz);
+      const Coef32& L = li >= g.layer_split ? hi : lo;
+      const float w = Wc[l];
+      const float dxx = (Wc[l - 1] - w) + (Wc[l + 1] - w);
+      const float dyy = (Wc[l - EX] - w) + (Wc[l + EX] - w);
+      const float dzz = (Wc[l - SXY] - w) + (Wc[l + SXY] - w);
+      const int64_t p = pz * g.sz + py * g.sy + px;
+      const float inc = increment<NF, 3>(L, dxx, dyy, dzz, fc, f, p, g.points, a.forced);
+      const float dn = Dv[l] + inc;
+      Dv[l] = dn;
+      Wn[l] = w + dn;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kT3Z; ++k) {
+      if (!own_int[k]) continue;
+      const float wn = Wn[(T + k) * SXY + (T + ty) * EX + T + tx];
+#pragma unroll
+      for (int m = 0; m < NF; ++m) {
+        if (ACC == 0)
+          kahan_add(ks[k][m], kc[k][m], s_wq[s * NF + m], wn);
+        else
+          part[k][m] = fmaf(s_wq[s * NF + m], wn, part[k][m]);
+      }
+    }
+    float* t = Wc;
+    Wc = Wn;
+    Wn = t;
+  }
+  // Wc holds W^{n0+steps} and Dv the matching D on the owned points
+  if (!owner) return;
+#pragma unroll
+  for (int k = 0; k < kT3Z; ++k) {
+    const int64_t gz = z0 + T + k;
+    if (gx > g.nx || gy > g.ny || gz > g.nz) continue;
+    const int64_t p = gz * g.sz + gy * g.sy + gx;
+    const int l = (T + k) * SXY + (T + ty) * EX + T + tx;
+    if (ACC == 1 && own_int[k]) {
+#pragma unroll
+      for (int m = 0; m < NF; ++m) {
+        ks[k][m] = qs[m * g.points + p];
+        kc[k][m] = qc[m * g.points + p];
+        kahan_fold(ks[k][m], kc[k][m], part[k][m]);
+      }
+    }
+    if (!a.last) {
+      if (!own_int[k]) continue;
+      const int64_t q = gz * g.szw + gy * g.syw + gx;
+      W_out[q] = Wc[l];
+      D_out[q] = Dv[l];
+#pragma unroll
+      for (int m = 0; m < NF; ++m) {
+        qs[m * g.points + p] = ks[k][m];
+        qc[m * g.points + p] = kc[k][m];
+      }
+    } else {
+      if (!own_int[k]) {
+#pragma unroll
+        for (int m = 0; m < NF; ++m) ks[k][m] = kc[k][m] = 0.0f;
+      }
+      filter_solve_out<NF>(ks[k], kc[k], b, a.subtract, vsub, vout, p, g.points, own_int[k]);
+    }
+  }
+}
+
 // ---- host launchers --------------------------------------------------------------
 
 template <int NF>
@@ -798,10 +951,66 @@ void tb32_nf(const Geom& g, const float* W_in, const float* D_in, float* W_out, 
     tb32_acc<NF, 16>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, h, st);
 }
 
+template <int NF, int T, int ACC>
+void tb3d32_launch(const Geom& g, const float* W_in, const float* D_in, float* W_out,
+                   float* D_out, const float* f, float* qs, float* qc, double* vout,
+                   const double* vsub, const TB32Host& h, cudaStream_t st) {
+  constexpr int E = kT3W * (kT3Y + 2 * T) * (kT3Z + 2 * T);
+  constexpr int BX = kT3W - 2 * T;
+  constexpr size_t smem = sizeof(float) * (3 * E + 2 * T * NF);
+  static bool configured[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !configured[dev]) {
+    cudaFuncSetAttribute(k_tb3d32<NF, T, ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    if (dev >= 0 && dev < 64) configured[dev] = true;
+  }
+  TB32Args<NF> a;
+  a.reg_lo = h.reg_lo;
+  a.reg_hi = h.reg_hi;
+  a.first_lo = h.first_lo;
+  a.first_hi = h.first_hi;
+  a.wq = h.wq;
+  a.fc = h.fc;
+  a.n0 = h.n0;
+  a.steps = h.steps;
+  a.forced = h.forced;
+  a.last = h.last;
+  a.subtract = vsub != nullptr;
+  a.err = h.err;
+  const Last32Binv<NF> b = binv_args<NF>(h.binv, h.emat, h.has_e, h.vprev);
+  const dim3 grid((unsigned)((g.nx + BX) / BX), (unsigned)((g.ny + kT3Y) / kT3Y),
+                  (unsigned)((g.nz + kT3Z) / kT3Z));
+  k_tb3d32<NF, T, ACC><<<grid, kT3Threads, smem, st>>>(W_in, D_in, W_out, D_out, f, qs, qc,
+                                                          vout, vsub, a, b, g);
+}
+
+// Depth 2 or 4 (a launch of at most T steps; the halo is T points).
+template <int NF>
+void tb3d32_nf(const Geom& g, const float* W_in, const float* D_in, float* W_out, float* D_out,
+               const float* f, float* qs, float* qc, double* vout, const double* vsub,
+               const TB32Host& h, cudaStream_t st) {
+  if (h.depth <= 2) {
+    if (h.acc == 1)
+      tb3d32_launch<NF, 2, 1>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, h, st);
+    else
+      tb3d32_launch<NF, 2, 0>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, h, st);
+  } else {
+    if (h.acc == 1)
+      tb3d32_launch<NF, 4, 1>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, h, st);
+    else
+      tb3d32_launch<NF, 4, 0>(g, W_in, D_in, W_out, D_out, f, qs, qc, vout, vsub, h, st);
+  }
+}
+
 template <int NF>
 W32Ops make_w32_ops() {
   return W32Ops{init32_nf<NF>, step32_nf<NF>, last32_nf<NF>, tb32_nf<NF>};
 }
+
+using Tb3dFn = void (*)(const Geom&, const float*, const float*, float*, float*, const float*,
+                        float*, float*, double*, const double*, const TB32Host&, cudaStream_t);
 
 }  // namespace
 
@@ -814,5 +1023,14 @@ W32Ops w32_ops_p5(int nf);
 W32Ops w32_ops_p6(int nf);
 W32Ops w32_ops_p7(int nf);
 W32Ops w32_ops_p8(int nf);
+// The 3D blocked launcher for nf, from the translation unit that instantiates nf.
+Tb3dFn w32_tb3_p1(int nf);
+Tb3dFn w32_tb3_p2(int nf);
+Tb3dFn w32_tb3_p3(int nf);
+Tb3dFn w32_tb3_p4(int nf);
+Tb3dFn w32_tb3_p5(int nf);
+Tb3dFn w32_tb3_p6(int nf);
+Tb3dFn w32_tb3_p7(int nf);
+Tb3dFn w32_tb3_p8(int nf);
 
 }  // namespace mfwh

@@ -11,4 +11,8 @@ W32Ops w32_ops_p1(int nf) {
   }
 }
 
+Tb3dFn w32_tb3_p1(int nf) {
+  return nf == 1 ? tb3d32_nf<1> : tb3d32_nf<2>;
+}
+
 }  // namespace mfwh

@@ -11,4 +11,8 @@ W32Ops w32_ops_p2(int nf) {
   }
 }
 
+Tb3dFn w32_tb3_p2(int nf) {
+  return nf == 3 ? tb3d32_nf<3> : tb3d32_nf<4>;
+}
+
 }  // namespace mfwh

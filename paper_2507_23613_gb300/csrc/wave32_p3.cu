@@ -11,4 +11,8 @@ W32Ops w32_ops_p3(int nf) {
   }
 }
 
+Tb3dFn w32_tb3_p3(int nf) {
+  return nf == 5 ? tb3d32_nf<5> : tb3d32_nf<6>;
+}
+
 }  // namespace mfwh

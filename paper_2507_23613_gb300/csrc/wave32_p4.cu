@@ -11,4 +11,8 @@ W32Ops w32_ops_p4(int nf) {
   }
 }
 
+Tb3dFn w32_tb3_p4(int nf) {
+  return nf == 7 ? tb3d32_nf<7> : tb3d32_nf<8>;
+}
+
 }  // namespace mfwh

@@ -11,4 +11,8 @@ W32Ops w32_ops_p5(int nf) {
   }
 }
 
+Tb3dFn w32_tb3_p5(int nf) {
+  return nf == 9 ? tb3d32_nf<9> : tb3d32_nf<10>;
+}
+
 }  // namespace mfwh

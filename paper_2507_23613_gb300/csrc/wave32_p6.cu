@@ -11,4 +11,8 @@ W32Ops w32_ops_p6(int nf) {
   }
 }
 
+Tb3dFn w32_tb3_p6(int nf) {
+  return nf == 11 ? tb3d32_nf<11> : tb3d32_nf<12>;
+}
+
 }  // namespace mfwh

@@ -11,4 +11,8 @@ W32Ops w32_ops_p7(int nf) {
   }
 }
 
+Tb3dFn w32_tb3_p7(int nf) {
+  return nf == 13 ? tb3d32_nf<13> : tb3d32_nf<14>;
+}
+
 }  // namespace mfwh

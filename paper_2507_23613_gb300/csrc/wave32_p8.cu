@@ -11,4 +11,8 @@ W32Ops w32_ops_p8(int nf) {
   }
 }
 
+Tb3dFn w32_tb3_p8(int nf) {
+  return nf == 15 ? tb3d32_nf<15> : tb3d32_nf<16>;
+}
+
 }  // namespace mfwh

@@ -133,6 +133,47 @@ def test_fp32_pi_3d_two_layer():
     assert np.all(err <= TOL_PI32), err
 
 
+@pytest.mark.parametrize("case", ["cube_two_layer", "thin", "nf16"])
+def test_fp32_3d_blocked_is_bit_identical_and_matches_oracle(case):
+    """3D temporal blocking (depths 2 and 4, 32 x 8 x 8 tiles with halo) performs the
+    one-step kernel's FP32 operations per point: Pi, S and GMRES iterates agree bit for bit
+    under Kahan sums; the blocked BLOCKSUM map stays within the FP32 bound of the oracle."""
+    kw = {}
+    if case == "cube_two_layer":
+        wl = inputs.gaussian_workload("cube", (20, 18, 16), 3, [7.0, 11.0, 16.0], 150.0, 5)
+        kw = dict(c_lo=1.0, c_hi=1.5, interface=0.5, layer_axis=2)
+        c2 = inputs.two_layer_c2(wl.n, wl.length, 1.0, 1.5, 0.5)
+    elif case == "thin":
+        wl = inputs.gaussian_workload("thin", (40, 6, 9), 2, [6.0, 11.0], 100.0, 6,
+                                      length=(2.0, 0.3, 0.45))
+        c2 = 1.0
+    else:
+        om = np.linspace(5.0, 50.0, 16)
+        wl = inputs.gaussian_workload("nf16c", (12, 10, 14), 16, om, 60.0, 47)
+        wl.n_p = 2
+        c2 = 1.0
+    v = random_v(wl, 12)
+    outs = {}
+    for tb in (1, 2, 4):
+        s = fp32_solver(wl, time_block=tb, **kw)
+        res = [apply(s, v, True), apply(s, v, False)]
+        x = torch.zeros(v.shape, dtype=torch.float64, device="cuda")
+        s.solve_gmres(x, restart=4, tol=0.0, max_iters=5, raise_on_error=False)
+        res.append(x.cpu().numpy())
+        outs[tb] = res
+        s.close()
+    for tb in (2, 4):
+        for a, b in zip(outs[tb], outs[1]):
+            assert np.array_equal(a, b), (tb, np.max(np.abs(a - b)))
+    prob = W.make_problem(W.Grid(wl.n, wl.length), wl.omega, wl.forcing, c2=c2, cfl=wl.cfl,
+                          n_p=wl.n_p, filter_mode=F.FILTER_TRADITIONAL)
+    sb = M.Solver(wl.n, wl.length, wl.omega, dev(wl.forcing), n_p=wl.n_p, cfl=wl.cfl,
+                  precision=_lib.PREC_FP32_BLOCKSUM, time_block=4,
+                  filter_mode=_lib.FILTER_TRADITIONAL, **kw)
+    err = rel_err(apply(sb, v, True), W.apply_Pi(prob, v, True))
+    assert np.all(err <= TOL_PI32), err
+
+
 def test_fp32_two_layer_2d_blocked_matches_unblocked():
     """Layer coefficients selected per point inside the blocked kernel (interface at y = 0.5)."""
     wl = inputs.gaussian_workload("layer2d", (64, 48), 4, [6.0, 9.0, 13.0, 18.0], 200.0, 8)
