@@ -75,6 +75,8 @@ def parse():
                     help="implicit fourth-order MFWH from 129^2 to 2049^2 (the paper's MG table)")
     ap.add_argument("--implicit", action="store_true",
                     help="implicit trapezoidal time stepping (multigrid) beside explicit FP64")
+    ap.add_argument("--cube-n", type=int, default=256,
+                    help="cells per axis of the 3D workload (256: the 257^3 configuration)")
     ap.add_argument("--cube", action="store_true",
                     help="run the 3D two-layer workload (257^3, N_f = 4, GMRES(15) cycle)")
     ap.add_argument("--no-clocks", action="store_true",
@@ -432,7 +434,7 @@ def run_cube(args):
     torch.cuda.set_device(0)
     build.build()
     M._lib.load()
-    wl = inputs.cube_layered(args.seed + 1000)
+    wl = inputs.cube_layered(args.seed + 1000, n=args.cube_n)
     lay = wl.layer
     f = torch.from_numpy(wl.forcing).cuda()
     stream = torch.cuda.Stream()
