@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--ws-epochs", type=int, default=15)
     ap.add_argument("--ws-gen-seconds", type=float, default=300.0,
                     help="time limit of the training-data generation")
+    ap.add_argument("--oracle-timings", action="store_true",
+                    help="the oracle timed on the host on the 65^2, 1025^2 and 257^3 workloads")
     ap.add_argument("--implicit-scaling", action="store_true",
                     help="implicit fourth-order MFWH from 129^2 to 2049^2 (the paper's MG table)")
     ap.add_argument("--implicit", action="store_true",
@@ -221,7 +223,7 @@ def cpu_baseline(wl, budget_s=15.0):
     from oracle import wave as W
     import copy
     g = W.Grid(wl.n, wl.length)
-    prob = W.make_problem(g, wl.omega, wl.forcing, cfl=wl.cfl, n_p=wl.n_p)
+    prob = W.make_problem(g, wl.omega, wl.forcing, c2=wl.c2, cfl=wl.cfl, n_p=wl.n_p)
     n_full = prob.setup.n_t
     # calibrate on a few steps, then run a sample of about budget_s seconds
     steps = 4
@@ -239,8 +241,68 @@ def cpu_baseline(wl, budget_s=15.0):
     pts = wl.interior_points * steps
     return {"value": pts / dt / 1e9, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
             "sample": (f"numpy oracle, homogeneous map, {steps} of {n_full} leapfrog+filter steps "
-                       f"on the full {wl.n[0] + 1}x{wl.n[1] + 1} grid, N_f={wl.nf}, "
+                       f"on the full {'x'.join(str(k + 1) for k in wl.n)} grid, N_f={wl.nf}, "
                        f"{dt:.1f} s, single-threaded numpy")}
+
+
+def run_oracle_timings(args):
+    """The FP64 oracle timed on the host beside the GPU on the small and large 2D workloads and
+    the 3D one: the 65^2 workload fully (40 fixed-point iterations, and GMRES to 1e-8), the
+    1025^2 and 257^3 maps on a bounded number of steps with the per-step rate extrapolated to
+    a whole map (labelled as such).  The GPU times the same calls when a device is present."""
+    import torch
+    from oracle import wave as W
+    import paper_2507_23613_gb300 as M
+    from paper_2507_23613_gb300 import build, inputs
+    gpu = torch.cuda.is_available()
+    if gpu:
+        torch.cuda.set_device(0)
+        build.build()
+        M._lib.load()
+    out = {"metric": "oracle (host) vs GPU times", "unit": "s", "higher_is_better": False,
+           "data": "synthetic", "cores": 1, "kind": "oracle"}
+    # 65^2, N_f = 2: 40 fixed-point iterations and GMRES to 1e-8, in full
+    wl = inputs.square_small()
+    g = W.Grid(wl.n, wl.length)
+    prob = W.make_problem(g, wl.omega, wl.forcing, cfl=wl.cfl, n_p=wl.n_p)
+    t0 = time.perf_counter()
+    W.fixed_point_iteration(prob, np.zeros_like(wl.forcing), 40)
+    t_fpi = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, ginfo = W.gmres(prob, restart=20, tol=1e-8, max_iters=400)
+    t_gm = time.perf_counter() - t0
+    row = {"oracle_fpi40_s": round(t_fpi, 3), "oracle_gmres_1e-8_s": round(t_gm, 3),
+           "oracle_gmres_iterations": ginfo.iterations, "n_t": prob.setup.n_t}
+    if gpu:
+        s = M.Solver(wl.n, wl.length, wl.omega, torch.from_numpy(wl.forcing).cuda(),
+                     n_p=wl.n_p, cfl=wl.cfl)
+        v = torch.zeros(wl.forcing.shape, dtype=torch.float64, device="cuda")
+        s.solve_fpi(v, 40)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        v.zero_()
+        s.solve_fpi(v, 40)
+        torch.cuda.synchronize()
+        row["gpu_fpi40_s"] = round(time.perf_counter() - t0, 4)
+        v.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = s.solve_gmres(v, restart=20, tol=1e-8, max_iters=400, raise_on_error=False)
+        torch.cuda.synchronize()
+        row["gpu_gmres_1e-8_s"] = round(time.perf_counter() - t0, 4)
+        row["gpu_gmres_iterations"] = info["iterations"]
+        s.close()
+    out["square65_nf2"] = row
+    # large workloads: a bounded sample of the homogeneous map, extrapolated per step
+    for name, wl in (("square1025_nf8", inputs.square_large(args.seed)),
+                     ("cube257_nf4", inputs.cube_layered(args.seed + 1000))):
+        info = cpu_baseline(wl, budget_s=10.0)
+        n_t = W.make_problem(W.Grid(wl.n, wl.length), wl.omega, wl.forcing, c2=wl.c2,
+                             cfl=wl.cfl, n_p=wl.n_p).setup.n_t
+        per_map = wl.interior_points * n_t / (info["value"] * 1e9)
+        out[name] = {"oracle_gpts_s": round(info["value"], 4), "sample": info["sample"],
+                     "n_t": n_t, "oracle_map_s_extrapolated": round(per_map, 1)}
+    print(json.dumps(out), flush=True)
 
 
 def run_reference(args, rank, world):
@@ -815,6 +877,8 @@ def main():
         return run_batched(args) if rank == 0 else None
     if args.implicit:
         return run_implicit(args) if rank == 0 else None
+    if args.oracle_timings:
+        return run_oracle_timings(args) if rank == 0 else None
     if args.cube:
         return run_cube(args) if rank == 0 else None
     if args.warm_start:
