@@ -347,6 +347,31 @@ def test_full_size_eigenmode_closed_form(mode):
         solver.close()
 
 
+@pytest.mark.parametrize("prec,tb,tol", [(_lib.PREC_FP64, 1, TOL),
+                                         (_lib.PREC_FP32_KAHAN, 4, 3e-4)])
+def test_full_size_3d_eigenmode_closed_form(prec, tb, tol):
+    """The 257^3, N_f = 4 configuration (c = 1 so that Dirichlet modes are eigenfunctions):
+    Pi maps a mode to the same mode with the closed-form coefficients, on the FP64 one-step
+    kernel (to 1e-10) and on the FP32 blocked kernel at depth 4 (to the FP32 bound)."""
+    wl = inputs.cube_layered()
+    g = W.Grid(wl.n, wl.length)
+    setup = F.make_setup(wl.omega, g.h, 1.0, wl.cfl, wl.n_p, F.FILTER_TRADITIONAL)
+    rng = np.random.default_rng(45)
+    phi, lam2 = W.dirichlet_mode(g, (5, 3, 7))
+    a = rng.normal(size=wl.nf)
+    v = rng.normal(size=wl.nf)
+    f = a[:, None, None, None] * phi
+    solver = M.Solver(wl.n, wl.length, wl.omega, dev(f), n_p=wl.n_p, cfl=wl.cfl,
+                      filter_mode=1, precision=prec, time_block=tb)
+    assert solver.setup["n_t"] == setup.n_t
+    out = torch.empty(f.shape, dtype=torch.float64, device="cuda")
+    solver.apply_Pi(dev(v[:, None, None, None] * phi), out, forced=True)
+    want = _closed_form_Pi(setup, lam2, a, v)[:, None, None, None] * phi
+    err = rel_err(out.cpu().numpy(), want)
+    assert np.all(err <= tol), (err, tol)
+    solver.close()
+
+
 def test_gmres_long_basis_parity():
     """No restart with a basis longer than one multi-dot launch handles (40 > 32 vectors)."""
     wl = inputs.gaussian_workload("t", (33, 33), 3, [6.1, 9.7, 15.2], 200.0, 15)
