@@ -202,6 +202,37 @@ def test_implicit_fourth_order_fixed_point_and_gmres():
     assert np.max(info["helmholtz_residual"]) < 1e-7
 
 
+def test_implicit_full_size_eigenmode_closed_form():
+    """The 1025^2, N_f = 8, N_p = 2 workload with implicit steps: Pi maps a Dirichlet mode to
+    the same mode with the closed-form coefficients (theta from the roots of the scheme's
+    characteristic polynomial), through the full multigrid hierarchy (10 levels)."""
+    wl = inputs.square_large()
+    g = W.Grid(wl.n, wl.length)
+    setup = F.make_setup(wl.omega, g.h, 1.0, wl.cfl, wl.n_p, F.FILTER_TRADITIONAL,
+                         time_stepping="implicit")
+    rng = np.random.default_rng(46)
+    for k in [(3, 5), (200, 17)]:
+        phi, lam2 = W.dirichlet_mode(g, k)
+        a = rng.normal(size=wl.nf)
+        v = rng.normal(size=wl.nf)
+        f = a[:, None, None] * phi
+        s = M.Solver(wl.n, wl.length, wl.omega, dev(f), n_p=wl.n_p, cfl=wl.cfl,
+                     filter_mode=1, time_stepping="implicit", mg_tol=1e-13)
+        assert s.setup["n_t"] == setup.n_t
+        got = apply(s, v[:, None, None] * phi, True)
+        x = lam2 * setup.dt ** 2
+        r = np.roots([1.0 + 0.5 * x, -2.0, 1.0 + 0.5 * x])
+        theta = float(np.max(np.abs(np.angle(r))))
+        u = a / (setup.omega ** 2 - lam2)
+        n = np.arange(setup.n_t + 1)
+        W_hat = (np.cos(n * theta) * np.sum(v - u)
+                 + np.cos(np.outer(n * setup.dt, setup.omega_t)) @ u)
+        want = np.linalg.solve(setup.B, setup.w.T @ W_hat)[:, None, None] * phi
+        assert np.all(rel_err(got, want) < 1e-9), (k, rel_err(got, want))
+        assert s.mg_stats()["levels"] == 10
+        s.close()
+
+
 def test_implicit_rejects_grids_without_a_small_level():
     with pytest.raises(_lib.MfwhError) as err:
         M.Solver((32, 32), (1.0, 1.0), [5.0, 9.0], time_stepping="implicit", order=4)
