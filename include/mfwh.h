@@ -170,6 +170,14 @@ mfwh_status mfwh_plan(const mfwh_problem* prob, mfwh_setup* out);
  * of a planned problem, written to w_out[(n_t+1) * nf] (host, row n, column m). */
 mfwh_status mfwh_plan_weights(const mfwh_problem* prob, double* w_out, int64_t capacity);
 
+/* Multigrid hierarchy of an implicit problem (MFWH_TIME_IMPLICIT), without a GPU: *levels
+ * levels, cells[l][0..2] the cells per axis of level l (x first; 0 for z in 2D), *coarse the
+ * first level solved by one CTA in shared memory (levels of at most 5000 points).  cells has
+ * room for 16 levels.  MFWH_ERR_INVALID_ARG if the problem is invalid or its grid does not
+ * halve down to such a level. */
+mfwh_status mfwh_plan_multigrid(const mfwh_problem* prob, int* levels, int* coarse,
+                                int64_t cells[16][3]);
+
 /* Adjusted frequencies of eq. omegaImplicit for scheme weights (alpha, beta):
  * out[m] = acos((1 - beta/2 (omega_m dt)^2) / (1 + alpha (omega_m dt)^2)) / dt.  Host arrays. */
 mfwh_status mfwh_adjusted_frequency(int nf, const double* omega, double dt,

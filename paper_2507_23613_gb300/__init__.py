@@ -88,6 +88,16 @@ def plan(problem):
     return s
 
 
+def plan_multigrid(problem):
+    """Multigrid hierarchy of an implicit problem (host only): (levels, coarse, cells), cells a
+    list of (nx, ny, nz) per level and coarse the first level solved by one CTA."""
+    levels, coarse = C.c_int(), C.c_int()
+    cells = (C.c_int64 * 3 * 16)()
+    _lib.check(_lib.load().mfwh_plan_multigrid(C.byref(problem), C.byref(levels),
+                                               C.byref(coarse), cells))
+    return levels.value, coarse.value, [tuple(cells[l]) for l in range(levels.value)]
+
+
 def plan_weights(problem, n_t, nf):
     w = np.zeros((n_t + 1) * nf)
     _lib.check(_lib.load().mfwh_plan_weights(C.byref(problem), _dptr(w), w.size))

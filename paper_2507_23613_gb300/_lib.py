@@ -137,6 +137,8 @@ _SIGNATURES = {
     "mfwh_residual_noalloc": (C.c_int, [C.POINTER(Problem), C.c_void_p, C.c_void_p, _dp, C.c_void_p]),
     "mfwh_get_setup": (C.c_int, [C.c_void_p, C.POINTER(Setup)]),
     "mfwh_last_timing": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "mfwh_plan_multigrid": (C.c_int, [C.POINTER(Problem), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                      C.POINTER(C.c_int64 * 3)]),
     "mfwh_mg_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                 C.POINTER(C.c_int64), C.POINTER(C.c_int), C.c_int]),
     "mfwh_destroy": (None, [C.c_void_p]),

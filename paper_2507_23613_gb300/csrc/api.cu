@@ -723,6 +723,41 @@ mfwh_status mfwh_plan(const mfwh_problem* prob, mfwh_setup* out) {
   return st;
 }
 
+mfwh_status mfwh_plan_multigrid(const mfwh_problem* prob, int* levels, int* coarse,
+                                int64_t cells[16][3]) {
+  if (!levels || !coarse || !cells) return fail(MFWH_ERR_INVALID_ARG, "null output");
+  Plan P;
+  mfwh_status st = plan_problem(prob, &P);
+  if (st != MFWH_OK) return st;
+  if (P.time_stepping != MFWH_TIME_IMPLICIT)
+    return fail(MFWH_ERR_INVALID_ARG, "not an implicit-time-stepping problem");
+  Geom g{};
+  g.nx = P.n[0];
+  g.ny = P.n[1];
+  g.nz = P.dim == 3 ? P.n[2] : 0;
+  g.sy = g.nx + 1;
+  g.sz = (g.nx + 1) * (g.ny + 1);
+  g.points = P.s.points;
+  g.dim = P.dim;
+  g.layer_axis = P.layer_axis;
+  g.layer_split = P.layer_split;
+  MgLevel lev[kMgMaxLevels];
+  int nlev = 0, lc = 0;
+  int64_t smem = 0;
+  if (!mg_plan_levels(g, P.s.h, P.c2_lo, P.c2_hi, P.s.dt, lev, &nlev, &lc, &smem))
+    return fail(MFWH_ERR_INVALID_ARG,
+                "implicit time stepping: the grid must halve (every n_i even, n_i / 2 >= 2) "
+                "down to a level of at most 5000 points");
+  *levels = nlev;
+  *coarse = lc;
+  for (int l = 0; l < 16; ++l) {
+    cells[l][0] = l < nlev ? lev[l].nx : 0;
+    cells[l][1] = l < nlev ? lev[l].ny : 0;
+    cells[l][2] = l < nlev ? lev[l].nz : 0;
+  }
+  return MFWH_OK;
+}
+
 mfwh_status mfwh_plan_weights(const mfwh_problem* prob, double* w_out, int64_t capacity) {
   if (!w_out) return fail(MFWH_ERR_INVALID_ARG, "null output");
   Plan P;

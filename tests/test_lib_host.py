@@ -206,3 +206,29 @@ def test_nearly_equal_frequencies_are_singular():
     with pytest.raises(_lib.MfwhError) as e:
         M.plan(prob)
     assert e.value.status == _lib.ERR_SINGULAR
+
+
+def test_multigrid_hierarchy_of_implicit_problems():
+    """Coarsening by 2 while every n_i is even and n_i / 2 >= 2; the one-CTA part starts at the
+    first level of at most 5000 points; a grid without such a level is rejected."""
+    def plan(n, length):
+        prob, keep = M.make_problem(n, length, [5.5, 9.3], time_stepping="implicit")
+        return M.plan_multigrid(prob)
+
+    lv, lc, cells = plan((1024, 1024), (1.0, 1.0))
+    assert lv == 10 and lc == 4 and cells[0] == (1024, 1024, 0) and cells[-1] == (2, 2, 0)
+    assert (cells[lc][0] + 1) * (cells[lc][1] + 1) <= 5000 < (cells[lc - 1][0] + 1) ** 2
+    lv, lc, cells = plan((96, 80), (1.2, 1.0))
+    assert cells == [(96, 80, 0), (48, 40, 0), (24, 20, 0), (12, 10, 0), (6, 5, 0)] and lc == 1
+    lv, lc, cells = plan((256, 256, 256), (1.0, 1.0, 1.0))
+    assert lv == 8 and lc == 4 and cells[lc] == (16, 16, 16)
+    lv, lc, cells = plan((256, 128), (1.0, 0.5))
+    assert lc == 2 and cells[-1] == (4, 2, 0)
+    assert plan((32, 32), (1.0, 1.0))[1] == 0          # the whole hierarchy in one CTA
+    for bad in [((101, 100), (1.0, 1.0))]:
+        with pytest.raises(_lib.MfwhError) as e:
+            plan(*bad)
+        assert e.value.status == _lib.ERR_INVALID_ARG
+    prob, keep = M.make_problem((64, 64), (1.0, 1.0), [5.5, 9.3])   # explicit problem
+    with pytest.raises(_lib.MfwhError):
+        M.plan_multigrid(prob)
