@@ -72,7 +72,10 @@ def parse():
     ap.add_argument("--ws-gen-seconds", type=float, default=300.0,
                     help="time limit of the training-data generation")
     ap.add_argument("--oracle-timings", action="store_true",
-                    help="the oracle timed on the host on the 65^2, 1025^2 and 257^3 workloads")
+                    help="with --impl reference: also the oracle's times on the 65^2, 1025^2 "
+                         "and 257^3 workloads")
+    ap.add_argument("--small", action="store_true",
+                    help="the 65^2, N_f = 2 workload on the GPU (fixed-point and GMRES times)")
     ap.add_argument("--implicit-scaling", action="store_true",
                     help="implicit fourth-order MFWH from 129^2 to 2049^2 (the paper's MG table)")
     ap.add_argument("--implicit", action="store_true",
@@ -245,23 +248,14 @@ def cpu_baseline(wl, budget_s=15.0):
                        f"{dt:.1f} s, single-threaded numpy")}
 
 
-def run_oracle_timings(args):
-    """The FP64 oracle timed on the host beside the GPU on the small and large 2D workloads and
-    the 3D one: the 65^2 workload fully (40 fixed-point iterations, and GMRES to 1e-8), the
-    1025^2 and 257^3 maps on a bounded number of steps with the per-step rate extrapolated to
-    a whole map (labelled as such).  The GPU times the same calls when a device is present."""
-    import torch
+def oracle_timings(args):
+    """The FP64 oracle timed on the host (part of the reference arm): the 65^2 workload in
+    full (40 fixed-point iterations, and GMRES to 1e-8), the 1025^2 and 257^3 maps on a
+    bounded number of steps with the per-step rate extrapolated to a whole map (labelled as
+    such)."""
     from oracle import wave as W
-    import paper_2507_23613_gb300 as M
-    from paper_2507_23613_gb300 import build, inputs
-    gpu = torch.cuda.is_available()
-    if gpu:
-        torch.cuda.set_device(0)
-        build.build()
-        M._lib.load()
-    out = {"metric": "oracle (host) vs GPU times", "unit": "s", "higher_is_better": False,
-           "data": "synthetic", "cores": 1, "kind": "oracle"}
-    # 65^2, N_f = 2: 40 fixed-point iterations and GMRES to 1e-8, in full
+    from paper_2507_23613_gb300 import inputs
+    out = {"cores": 1, "kind": "oracle"}
     wl = inputs.square_small()
     g = W.Grid(wl.n, wl.length)
     prob = W.make_problem(g, wl.omega, wl.forcing, cfl=wl.cfl, n_p=wl.n_p)
@@ -271,38 +265,52 @@ def run_oracle_timings(args):
     t0 = time.perf_counter()
     _, ginfo = W.gmres(prob, restart=20, tol=1e-8, max_iters=400)
     t_gm = time.perf_counter() - t0
-    row = {"oracle_fpi40_s": round(t_fpi, 3), "oracle_gmres_1e-8_s": round(t_gm, 3),
-           "oracle_gmres_iterations": ginfo.iterations, "n_t": prob.setup.n_t}
-    if gpu:
-        s = M.Solver(wl.n, wl.length, wl.omega, torch.from_numpy(wl.forcing).cuda(),
-                     n_p=wl.n_p, cfl=wl.cfl)
-        v = torch.zeros(wl.forcing.shape, dtype=torch.float64, device="cuda")
-        s.solve_fpi(v, 40)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        v.zero_()
-        s.solve_fpi(v, 40)
-        torch.cuda.synchronize()
-        row["gpu_fpi40_s"] = round(time.perf_counter() - t0, 4)
-        v.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        info = s.solve_gmres(v, restart=20, tol=1e-8, max_iters=400, raise_on_error=False)
-        torch.cuda.synchronize()
-        row["gpu_gmres_1e-8_s"] = round(time.perf_counter() - t0, 4)
-        row["gpu_gmres_iterations"] = info["iterations"]
-        s.close()
-    out["square65_nf2"] = row
-    # large workloads: a bounded sample of the homogeneous map, extrapolated per step
+    out["square65_nf2"] = {"fpi40_s": round(t_fpi, 3), "gmres_1e-8_s": round(t_gm, 3),
+                           "gmres_iterations": ginfo.iterations, "n_t": prob.setup.n_t}
     for name, wl in (("square1025_nf8", inputs.square_large(args.seed)),
                      ("cube257_nf4", inputs.cube_layered(args.seed + 1000))):
         info = cpu_baseline(wl, budget_s=10.0)
         n_t = W.make_problem(W.Grid(wl.n, wl.length), wl.omega, wl.forcing, c2=wl.c2,
                              cfl=wl.cfl, n_p=wl.n_p).setup.n_t
         per_map = wl.interior_points * n_t / (info["value"] * 1e9)
-        out[name] = {"oracle_gpts_s": round(info["value"], 4), "sample": info["sample"],
-                     "n_t": n_t, "oracle_map_s_extrapolated": round(per_map, 1)}
-    print(json.dumps(out), flush=True)
+        out[name] = {"gpts_s": round(info["value"], 4), "sample": info["sample"], "n_t": n_t,
+                     "map_s_extrapolated": round(per_map, 1)}
+    return out
+
+
+def run_small(args):
+    """The 65^2, N_f = 2 workload on the GPU through the C ABI: 40 fixed-point iterations and
+    GMRES(20) to 1e-8 from zero (wall time around each synchronous call)."""
+    import torch
+    import paper_2507_23613_gb300 as M
+    from paper_2507_23613_gb300 import build, inputs
+    torch.cuda.set_device(0)
+    build.build()
+    M._lib.load()
+    wl = inputs.square_small()
+    s = M.Solver(wl.n, wl.length, wl.omega, torch.from_numpy(wl.forcing).cuda(), n_p=wl.n_p,
+                 cfl=wl.cfl)
+    v = torch.zeros(wl.forcing.shape, dtype=torch.float64, device="cuda")
+    s.solve_fpi(v, 40)                                   # warm-up
+    torch.cuda.synchronize()
+    v.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.solve_fpi(v, 40)
+    torch.cuda.synchronize()
+    t_fpi = time.perf_counter() - t0
+    v.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info = s.solve_gmres(v, restart=20, tol=1e-8, max_iters=400, raise_on_error=False)
+    torch.cuda.synchronize()
+    t_gm = time.perf_counter() - t0
+    s.close()
+    print(json.dumps({"metric": "65^2 N_f = 2 solve times", "unit": "s", "value": round(t_gm, 4),
+                      "higher_is_better": False, "n_gpus": 1, "dtype": "f64",
+                      "data": "synthetic", "config": {"workload": "square65_nf2"},
+                      "fpi40_s": round(t_fpi, 4), "gmres_1e-8_s": round(t_gm, 4),
+                      "gmres_iterations": info["iterations"]}), flush=True)
 
 
 def run_reference(args, rank, world):
@@ -324,6 +332,8 @@ def run_reference(args, rank, world):
             "data": "synthetic", "config": workload_config(wl, None),
             "cpu_baseline": {**info, "value": value},
             "e2e": {"value": value, "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if args.oracle_timings:
+        line["oracle_timings"] = oracle_timings(args)
     print(json.dumps(line), flush=True)
 
 
@@ -877,8 +887,8 @@ def main():
         return run_batched(args) if rank == 0 else None
     if args.implicit:
         return run_implicit(args) if rank == 0 else None
-    if args.oracle_timings:
-        return run_oracle_timings(args) if rank == 0 else None
+    if args.small:
+        return run_small(args) if rank == 0 else None
     if args.cube:
         return run_cube(args) if rank == 0 else None
     if args.warm_start:
