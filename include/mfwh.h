@@ -113,9 +113,9 @@ typedef struct {
                                 step solves (I - dt^2/2 L_h) Z = 2 W^n - dt^2 F^n by geometric
                                 multigrid on the device; W^{n+1} = Z - W^{n-1} (W^1 = Z/2).
                                 Grids must halve (all n_i even, n_i/2 >= 2) down to a level of
-                                at most 5000 points.  Order 4 is available for 2D grids of more
-                                than 5000 points (the second-order multigrid preconditions the
-                                fourth-order residual). */
+                                at most 5000 points.  Order 4 is available for 2D and 3D grids
+                                of more than 5000 points (the second-order multigrid
+                                preconditions the fourth-order residual). */
   int steps_per_period;      /* implicit: steps over the shortest period 2 pi / omega_nf
                                 (0 means 10; >= 5).  N_t = ceil(steps_per_period N_p omega_nf /
                                 omega_1); dt solves omega~_1 N_t dt = 2 pi N_p. */
@@ -173,8 +173,9 @@ mfwh_status mfwh_plan_weights(const mfwh_problem* prob, double* w_out, int64_t c
 /* Multigrid hierarchy of an implicit problem (MFWH_TIME_IMPLICIT), without a GPU: *levels
  * levels, cells[l][0..2] the cells per axis of level l (x first; 0 for z in 2D), *coarse the
  * first level solved by one CTA in shared memory (levels of at most 5000 points).  cells has
- * room for 16 levels.  MFWH_ERR_INVALID_ARG if the problem is invalid or its grid does not
- * halve down to such a level. */
+ * room for 16 levels.  MFWH_ERR_INVALID_ARG if the problem is invalid, its grid does not
+ * halve down to such a level, or it takes the fourth-order operator on a grid of at most 5000
+ * points (the cases mfwh_create rejects for the hierarchy). */
 mfwh_status mfwh_plan_multigrid(const mfwh_problem* prob, int* levels, int* coarse,
                                 int64_t cells[16][3]);
 

@@ -748,6 +748,10 @@ mfwh_status mfwh_plan_multigrid(const mfwh_problem* prob, int* levels, int* coar
     return fail(MFWH_ERR_INVALID_ARG,
                 "implicit time stepping: the grid must halve (every n_i even, n_i / 2 >= 2) "
                 "down to a level of at most 5000 points");
+  if (P.order == 4 && !mg_mixed(P.dim, lc))
+    return fail(MFWH_ERR_INVALID_ARG,
+                "implicit time stepping with the fourth-order operator needs a grid of more "
+                "than 5000 points");
   *levels = nlev;
   *coarse = lc;
   for (int l = 0; l < 16; ++l) {
@@ -903,7 +907,7 @@ mfwh_status mfwh_create(const mfwh_problem* prob, void* stream, mfwh_handle_t* o
     if (P.order == 4) {
       if (!mg_mixed(P.dim, A.lc))
         return cleanup(fail(MFWH_ERR_INVALID_ARG,
-                            "implicit time stepping with the fourth-order operator needs a 2D "
+                            "implicit time stepping with the fourth-order operator needs a "
                             "grid of more than 5000 points"));
       mg_set_order4(&A.lev[0], P.s.h, P.c2_lo, P.c2_hi, P.s.dt, P.dim);
     }

@@ -190,8 +190,40 @@ __device__ void residual_store(const MgLevel& L, const R* u, const R* f, R* r, i
   }
 }
 
+// Z of a 3D level 0 at (i, j, k), each index in [-1, n + 1]: one point beyond the Dirichlet
+// boundary the fourth-order stencil reads the odd-reflection ghost (Z_{-1} = -Z_1,
+// Z_{n+1} = -Z_{n-1}), as L_4h is defined on the interior unknowns.
+__device__ __forceinline__ double z_ghost3(const MgLevel& F, int i, int j, int k) {
+  double sgn = 1.0;
+  if (i == -1) { i = 1; sgn = -sgn; }
+  if (i == F.nx + 1) { i = F.nx - 1; sgn = -sgn; }
+  if (j == -1) { j = 1; sgn = -sgn; }
+  if (j == F.ny + 1) { j = F.ny - 1; sgn = -sgn; }
+  if (k == -1) { k = 1; sgn = -sgn; }
+  if (k == F.nz + 1) { k = F.nz - 1; sgn = -sgn; }
+  return sgn * F.u[(int64_t)k * F.sz + (int64_t)j * F.sy + i];
+}
+
+// FP64 residual rhs - A_4 Z at an interior point of a 3D level 0 with the fourth-order
+// operator: A_4 = d4 - sum_a (a4_a (Z_{+-1}) + b4_a (Z_{+-2})) along each axis a.
+__device__ __forceinline__ double residual4_3d(const MgLevel& F, int axis, int i, int j, int k) {
+  const int64_t p = (int64_t)k * F.sz + (int64_t)j * F.sy + i;
+  const bool hi = upper(F, axis, i, j, k);
+  const double* a4 = hi ? F.a4_hi : F.a4_lo;
+  const double* b4 = hi ? F.b4_hi : F.b4_lo;
+  const double* u = F.u;
+  const double s =
+      a4[0] * (u[p - 1] + u[p + 1]) + a4[1] * (u[p - F.sy] + u[p + F.sy]) +
+      a4[2] * (u[p - F.sz] + u[p + F.sz]) +
+      b4[0] * (z_ghost3(F, i - 2, j, k) + z_ghost3(F, i + 2, j, k)) +
+      b4[1] * (z_ghost3(F, i, j - 2, k) + z_ghost3(F, i, j + 2, k)) +
+      b4[2] * (z_ghost3(F, i, j, k - 2) + z_ghost3(F, i, j, k + 2));
+  return F.f[p] - ((hi ? F.d4_hi : F.d4_lo) * u[p] - s);
+}
+
 // Level 0 of a grid-wide 3D hierarchy: r = rhs - A Z in FP64 into f32 (the correction's
-// right-hand side), e = 0 in u32; returns the max |r| over this thread's points.
+// right-hand side), e = 0 in u32; returns the max |r| over this thread's points.  A is the
+// second-order operator, or the fourth-order one when L.order4 is set.
 template <int DIM>
 __device__ double residual_to32(const MgLevel& L, int axis, uint32_t t0, uint32_t stride) {
   const uint32_t mx = (uint32_t)L.nx - 1, my = (uint32_t)L.ny - 1;
@@ -202,7 +234,8 @@ __device__ double residual_to32(const MgLevel& L, int axis, uint32_t t0, uint32_
     const uint32_t rest = t / mx;
     const int j = 1 + (int)(rest % my);
     const int k = DIM == 3 ? 1 + (int)(rest / my) : 0;
-    const double res = residual_at<DIM, double>(L, L.u, L.f, axis, i, j, k);
+    const double res = (DIM == 3 && L.order4) ? residual4_3d(L, axis, i, j, k)
+                                              : residual_at<DIM, double>(L, L.u, L.f, axis, i, j, k);
     const int64_t p = (int64_t)k * L.sz + (int64_t)j * L.sy + i;
     L.f32[p] = (float)res;
     L.u32[p] = 0.0f;

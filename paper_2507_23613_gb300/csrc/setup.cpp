@@ -330,9 +330,6 @@ mfwh_status plan_problem(const mfwh_problem* p, Plan* out) {
     if (fp32) return fail(MFWH_ERR_INVALID_ARG, "implicit time stepping runs in FP64 only");
     if (p->time_block > 1)
       return fail(MFWH_ERR_INVALID_ARG, "implicit time stepping takes one step per launch");
-    if (p->order == 4 && p->dim != 2)
-      return fail(MFWH_ERR_INVALID_ARG,
-                  "implicit time stepping with the fourth-order operator is available in 2D");
     if (p->steps_per_period != 0 && p->steps_per_period < 5)
       return fail(MFWH_ERR_INVALID_ARG, "steps_per_period must be >= 5");
     if (p->mg_tol != 0.0 && !(p->mg_tol > 0.0 && p->mg_tol < 1.0))

@@ -55,6 +55,7 @@ CASES = {
     "aniso_2d": ((256, 128), (1.0, 0.5), [6.0, 11.0], 300.0, None),
     "ragged_coarsest_2d": ((96, 80), (1.2, 1.0), [4.5, 8.0, 12.5], 200.0, None),
     "cube3d_two_layer": ((32, 32, 32), (1.0, 1.0, 1.0), [4.1, 7.9, 12.5], 60.0, 1.5),
+    "cube3d_o4": ((20, 20, 20), (1.0, 1.0, 1.0), [4.1, 7.9, 12.5], 60.0, 1.5),
 }
 
 
@@ -174,12 +175,12 @@ def test_implicit_graph_mode_and_batch():
     e.close()
 
 
-@pytest.mark.parametrize("name", ["grid_2d", "aniso_2d"])
+@pytest.mark.parametrize("name", ["grid_2d", "aniso_2d", "cube3d_o4"])
 def test_implicit_fourth_order_pi_matches_oracle(name):
     """Fourth-order L_4h (odd-reflection ghosts) in the FP64 residual, the second-order
-    multigrid as the correction solver (damped by 6/7).  The step tolerance is 1e-12: the
-    rounding floor of the fourth-order residual (diagonal ~500 on the anisotropic grid) lies
-    near 5e-14."""
+    multigrid as the correction solver (damped by 6/7); in 3D the residual runs in the
+    grid-wide phases.  The step tolerance is 1e-12: the rounding floor of the fourth-order
+    residual (diagonal ~500 on the anisotropic grid) lies near 5e-14."""
     s, p, wl = pair(name, order=4, mg_tol=1e-12)
     v = random_v(wl, 6)
     for forced in (True, False):
@@ -200,6 +201,14 @@ def test_implicit_fourth_order_fixed_point_and_gmres():
     info = s2.solve_gmres(v, restart=100, tol=1e-10, max_iters=400)
     assert np.all(rel_err(v.cpu().numpy(), U2) < 1e-7)
     assert np.max(info["helmholtz_residual"]) < 1e-7
+
+
+def test_implicit_fourth_order_3d_fixed_point():
+    s, p, wl = pair("cube3d_o4", order=4, mg_tol=1e-12)
+    assert s.mg_stats()["levels"] == 3
+    U = W.helmholtz_direct(p)
+    assert np.all(rel_err(apply(s, U, True), U) < 1e-10)
+    assert s.mg_stats()["unconverged"] == 0
 
 
 def test_implicit_full_size_eigenmode_closed_form():

@@ -125,6 +125,7 @@ def test_plan_matches_oracle_implicit():
     _compare_setup(wl3, c_hi=1.5, n_p=2, time_stepping="implicit")
     s4, _ = _compare_setup(wl, order=4, time_stepping="implicit")   # dt does not depend on order
     assert s4["n_t"] == s["n_t"] and s4["dt"] == s["dt"]
+    _compare_setup(wl3, c_hi=1.5, order=4, time_stepping="implicit")
 
 
 def _implicit_dt(omega1, n_p, n_t):
@@ -185,7 +186,6 @@ def test_adjusted_frequency_matches_definition():
     dict(order=4, time_block=8),       # fourth order takes one step per launch
     dict(time_stepping="implicit", precision=1),        # implicit runs in FP64 only
     dict(time_stepping="implicit", time_block=4),       # one step per launch
-    dict(time_stepping="implicit", order=4, n=(8, 8, 8), length=(1.0, 1.0, 1.0)),  # 2D only
     dict(time_stepping="implicit", steps_per_period=4),  # at least five steps per period
     dict(time_stepping="implicit", mg_tol=1.5),
     dict(time_stepping="implicit", mg_max_cycles=61),
@@ -229,6 +229,15 @@ def test_multigrid_hierarchy_of_implicit_problems():
         with pytest.raises(_lib.MfwhError) as e:
             plan(*bad)
         assert e.value.status == _lib.ERR_INVALID_ARG
+    # the fourth-order operator needs grid-wide levels (its FP64 residual runs there)
+    for n, ok in [((64, 64), False), ((8, 8, 8), False), ((96, 96), True), ((32, 32, 32), True)]:
+        prob, keep = M.make_problem(n, (1.0,) * len(n), [5.5, 9.3], time_stepping="implicit",
+                                    order=4)
+        if ok:
+            assert M.plan_multigrid(prob)[1] >= 1
+        else:
+            with pytest.raises(_lib.MfwhError):
+                M.plan_multigrid(prob)
     prob, keep = M.make_problem((64, 64), (1.0, 1.0), [5.5, 9.3])   # explicit problem
     with pytest.raises(_lib.MfwhError):
         M.plan_multigrid(prob)

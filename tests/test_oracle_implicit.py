@@ -93,6 +93,36 @@ def test_implicit_fixed_point_fourth_order():
     assert np.max(np.abs(W.apply_Pi(p, U) - U)) / np.max(np.abs(U)) < 1e-12
 
 
+def test_implicit_fourth_order_3d_fixed_point_and_eigenmodes():
+    """Fourth-order L_4h in 3D with implicit steps: the direct Helmholtz solution of the
+    two-layer cube is the fixed point, and superposed Dirichlet modes follow the closed form
+    with the fourth-order eigenvalues (theta from the roots of the characteristic
+    polynomial)."""
+    dims = (8, 8, 8)
+    c2 = inputs.two_layer_c2(dims, (1.0, 1.0, 1.0), 1.0, 1.5, 0.5)
+    wl = inputs.gaussian_workload("t", dims, 3, [4.1, 7.9, 12.5], 60.0, 4)
+    p = W.make_problem(W.Grid(dims, wl.length), wl.omega, wl.forcing, c2=c2, order=4,
+                       time_stepping="implicit")
+    U = W.helmholtz_direct(p)
+    assert np.max(np.abs(W.apply_Pi(p, U) - U)) / np.max(np.abs(U)) < 1e-12
+    g = W.Grid((6, 7, 8), (1.0, 1.2, 0.9))
+    rng = np.random.default_rng(21)
+    f = np.zeros((2,) + g.shape)
+    V = np.zeros_like(f)
+    coeffs = []
+    for k in [(1, 1, 1), (3, 2, 6), (5, 6, 7)]:
+        phi, lam2 = W.dirichlet_mode(g, k, order=4)
+        a, v = rng.normal(size=2), rng.normal(size=2)
+        f += a[:, None, None, None] * phi
+        V += v[:, None, None, None] * phi
+        coeffs.append((phi, lam2, a, v))
+    p = W.make_problem(g, [4.0, 9.5], f, order=4, time_stepping="implicit")
+    want = np.zeros_like(f)
+    for phi, lam2, a, v in coeffs:
+        want += _closed_form_Pi(p.setup, lam2, a, v)[:, None, None, None] * phi
+    np.testing.assert_allclose(W.apply_Pi(p, V), want, atol=1e-12)
+
+
 def test_implicit_eigenmode_closed_form_2d():
     """Dirichlet modes from the lowest to the highest (the highest with lam dt beyond the
     explicit stability limit 2) follow the closed form to rounding."""
