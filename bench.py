@@ -77,7 +77,8 @@ def parse():
     ap.add_argument("--small", action="store_true",
                     help="the 65^2, N_f = 2 workload on the GPU (fixed-point and GMRES times)")
     ap.add_argument("--implicit-scaling", action="store_true",
-                    help="implicit fourth-order MFWH from 129^2 to 2049^2 (the paper's MG table)")
+                    help="implicit fourth-order MFWH from 129^2 to 2049^2 (the paper's MG table);"
+                         " with --cube its 3D analogue from 33^3 to 129^3")
     ap.add_argument("--implicit", action="store_true",
                     help="implicit trapezoidal time stepping (multigrid) beside explicit FP64")
     ap.add_argument("--cube-n", type=int, default=256,
@@ -709,7 +710,8 @@ def run_implicit_scaling(args):
     """O(N) check of implicit MFWH with multigrid on GB300: the three-frequency problem of
     eq. Nf3parameters on the unit square, fourth-order operator, implicit trapezoidal steps
     (10 per shortest period, multigrid to 1e-10), unrestarted GMRES to 1e-10, from 129^2 to
-    2049^2 (65^2 is below the library's minimum grid for fourth-order implicit stepping)."""
+    2049^2 (65^2 is below the library's minimum grid for fourth-order implicit stepping).
+    With --cube, the same on its 3D analogue from 33^3 to 129^3."""
     import torch
     import paper_2507_23613_gb300 as M
     from paper_2507_23613_gb300 import build, inputs
@@ -717,8 +719,9 @@ def run_implicit_scaling(args):
     build.build()
     M._lib.load()
     rows = []
-    for n in (128, 256, 512, 1024, 2048):
-        wl = inputs.paper_three_frequency(n)
+    cube = args.cube
+    for n in ((32, 64, 128) if cube else (128, 256, 512, 1024, 2048)):
+        wl = inputs.paper_three_frequency_cube(n) if cube else inputs.paper_three_frequency(n)
         f = torch.from_numpy(wl.forcing).cuda()
         s = M.Solver(wl.n, wl.length, wl.omega, f, n_p=wl.n_p, order=4, time_stepping="implicit")
         v = torch.zeros_like(f)
@@ -731,27 +734,31 @@ def run_implicit_scaling(args):
         torch.cuda.synchronize()
         sec = time.perf_counter() - t0
         st = s.mg_stats()
-        pts = (n + 1) ** 2
-        paper = PAPER_MG_TABLE[n]
-        rows.append({"grid": [n + 1, n + 1], "points": pts, "n_t": s.setup["n_t"],
+        pts = (n + 1) ** len(wl.n)
+        paper = None if cube else PAPER_MG_TABLE[n]
+        rows.append({"grid": [n + 1] * len(wl.n), "points": pts, "n_t": s.setup["n_t"],
                      "wave_solves": info["pi_applications"], "gmres_status": int(info["status"]),
                      "rel_residual": info["rel_residual"],
                      "max_helmholtz_residual": float(np.max(info["helmholtz_residual"])),
                      "mg_cycles_per_step": round(st["cycles"] / max(st["solves"], 1), 2),
                      "mg_unconverged_steps": st["unconverged"], "seconds": round(sec, 3),
-                     "us_per_point": round(sec / pts * 1e6, 3),
-                     "paper_cpu": {"wave_solves": paper[0], "mg_cycles": paper[1],
-                                   "seconds": paper[2]}})
+                     "us_per_point": round(sec / pts * 1e6, 3)})
+        if paper:
+            rows[-1]["paper_cpu"] = {"wave_solves": paper[0], "mg_cycles": paper[1],
+                                     "seconds": paper[2]}
         s.close()
     out = {"metric": "implicit MFWH time to 1e-10 vs grid (O(N) scaling)", "unit": "s",
            "value": rows[-1]["seconds"], "higher_is_better": False, "n_gpus": 1, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": "paper3freq_square_order4_implicit",
+           "data": "synthetic",
+           "config": {"workload": ("paper3freq_cube_order4_implicit" if cube
+                                   else "paper3freq_square_order4_implicit"),
                                           "omega": [5.1, 10.1, 15.1], "n_p": 2, "order": 4,
                                           "steps_per_period": 10, "mg_tol": 1e-10,
                                           "gmres_tol": 1e-10},
            "rows": rows,
-           "paper_context": "Figure squareGridCpuScaling: CPU (Ogmg) seconds on the paper's "
-                            "machine; a different machine and solver, quoted as context"}
+           "paper_context": ("none: the paper's scaling study is 2D" if cube else
+                             "Figure squareGridCpuScaling: CPU (Ogmg) seconds on the paper's "
+                             "machine; a different machine and solver, quoted as context")}
     print(json.dumps(out), flush=True)
 
 
@@ -889,14 +896,12 @@ def main():
         return run_implicit(args) if rank == 0 else None
     if args.small:
         return run_small(args) if rank == 0 else None
+    if args.implicit_scaling:
+        return run_implicit_scaling(args) if rank == 0 else None
     if args.cube:
         return run_cube(args) if rank == 0 else None
     if args.warm_start:
         return run_warm_start(args) if rank == 0 else None
-    if args.implicit:
-        return run_implicit(args) if rank == 0 else None
-    if args.implicit_scaling:
-        return run_implicit_scaling(args) if rank == 0 else None
 
     import torch
     import paper_2507_23613_gb300 as M

@@ -150,6 +150,19 @@ def paper_three_frequency(n=128):
     return Workload(f"paper3freq_square{n}", dims, (1.0, 1.0), omega, forcing, 1.0, 0.5, 2)
 
 
+def paper_three_frequency_cube(n=64):
+    """A 3D analogue of the paper's three-frequency example: unit cube with n^3 cells, the same
+    omega, amplitudes, width b = 15 and N_p = 2, the centres of eq. Nf3parameters extended by
+    z = 0.5."""
+    dims = (n, n, n)
+    coords = coordinates(dims, (1.0, 1.0, 1.0))
+    omega = np.array([5.1, 10.1, 15.1])
+    amps = (25.0, 100.0, 225.0)
+    centres = ((0.6, 0.45, 0.5), (0.4, 0.5, 0.5), (0.55, 0.5, 0.5))
+    forcing = np.stack([gaussian(coords, c, a, 15.0 ** 2) for a, c in zip(amps, centres)])
+    return Workload(f"paper3freq_cube{n}", dims, (1.0, 1.0, 1.0), omega, forcing, 1.0, 0.5, 2)
+
+
 def warm_start_workload(seed, n=128, nf=6):
     """One problem of the learned-warm-start workload: unit square with n x n cells, N_f
     frequencies uniform in [15, 45] (adjacent gaps >= 1.5), 1-4 Gaussian sources per frequency
