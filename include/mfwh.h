@@ -51,7 +51,11 @@ typedef enum {
 } mfwh_status;
 
 enum { MFWH_FILTER_OPTIMIZED = 0, MFWH_FILTER_TRADITIONAL = 1, MFWH_FILTER_USER = 2 };
-/* Arithmetic of the wave solve.  FP64: every step in FP64.  FP32_KAHAN: wave levels and
+/* Arithmetic of the wave solve.  FP64: wave levels, steps and the filter solve in FP64; with
+   explicit time stepping the filter sums q_m are unevaluated float pairs (hi + lo, updated
+   with two-product/two-sum on the FP32 pipe, about 2^-47 relative per update), so their
+   magnitudes must stay below the float range (3.4e38) and keep full accuracy above about
+   1e-30.  FP32_KAHAN: wave levels and
    steps in FP32 (increment form of the leapfrog scheme), filter sums with a Kahan update at
    every step; the filter solve B^{-1} q, GMRES and the residual stay FP64.  FP32_BLOCKSUM:
    as FP32_KAHAN, but a blocked launch of T steps sums its T filter terms in plain FP32 and

@@ -119,6 +119,9 @@ void launch_tb3d32(int nf, const Geom& g, const float* W_in, const float* D_in, 
                    const double* vsub, const TB32Host& h, cudaStream_t st);
 void launch_to_float(const double* x, float* y, int64_t n, cudaStream_t st);
 
+// In launch_init, launch_step, launch_last and launch_tb2d, q holds the N_f filter sums
+// [N_f][points], each as a float pair (hi, lo) in the 8 bytes of a double (fpair.cuh); only
+// these kernels read or write it.
 // W^0 = sum_m v_m (0 on the boundary; v == nullptr gives W^0 = 0) and q_m = w0_m W^0.
 void launch_init(int nf, const Geom& g, const double* v, double* W0, double* q, const double* w0,
                  cudaStream_t st);

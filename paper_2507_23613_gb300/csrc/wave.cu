@@ -10,9 +10,12 @@
 // stored as two ping-pong grids; W^{n+1} overwrites W^{n-1} at the same point, so
 // each point is read and written by one thread only.  The forcing grids f_m and
 // the accumulators q_m are [N_f][points] arrays; the N_f accumulations of a point
-// run in registers on the value just computed, so W^{n+1} is never re-read.
+// run in registers on the value just computed, so W^{n+1} is never re-read.  The
+// accumulators are float pairs updated on the FP32 pipe (fpair.cuh); k_last adds the
+// final term in FP64 and solves for V in FP64.
 #include <cuda_runtime.h>
 
+#include "fpair.cuh"
 #include "kernels.h"
 
 namespace mfwh {
@@ -25,6 +28,7 @@ struct StepParams {
   LayerCoef lo, hi;
   double fneg[NF];   // kappa cos(omega~_m t^n)
   double wq[NF];
+  float wq_hi[NF], wq_lo[NF];   // w_{n+1,m} as a float pair
   int first, forced;
 };
 
@@ -50,6 +54,8 @@ StepParams<NF> to_params(const StepHost& a) {
   for (int m = 0; m < NF; ++m) {
     p.fneg[m] = a.fc[m];
     p.wq[m] = a.wq[m];
+    p.wq_hi[m] = (float)a.wq[m];
+    p.wq_lo[m] = (float)(a.wq[m] - (double)p.wq_hi[m]);
   }
   p.first = a.first;
   p.forced = a.forced;
@@ -122,7 +128,7 @@ __device__ __forceinline__ double leapfrog_point(const double* __restrict__ Wc,
 
 template <int NF, int DIM>
 __global__ void __launch_bounds__(kBX * kBY)
-k_init(const double* __restrict__ v, double* __restrict__ W0, double* __restrict__ q,
+k_init(const double* __restrict__ v, double* __restrict__ W0, float2* __restrict__ q,
        const InitParams<NF> a, const Geom g) {
   const PointIndex x = point_index<DIM>(g);
   if (!x.inside) return;
@@ -133,28 +139,29 @@ k_init(const double* __restrict__ v, double* __restrict__ W0, double* __restrict
   }
   W0[x.p] = w;
 #pragma unroll
-  for (int m = 0; m < NF; ++m) q[m * g.points + x.p] = a.w0[m] * w;
+  for (int m = 0; m < NF; ++m) q[m * g.points + x.p] = fpair_from(a.w0[m] * w);
 }
 
 template <int NF, int DIM, int ORDER>
 __global__ void __launch_bounds__(kBX * kBY)
 k_step(const double* __restrict__ Wc, double* __restrict__ Wp, const double* __restrict__ f,
-       double* __restrict__ q, const StepParams<NF> a, const Geom g) {
+       float2* __restrict__ q, const StepParams<NF> a, const Geom g) {
   const PointIndex x = point_index<DIM>(g);
   if (!x.interior) return;           // boundary values stay 0 (Dirichlet, g = 0)
   const double wn = leapfrog_point<NF, DIM, ORDER>(Wc, Wp, f, a, g, x);
   Wp[x.p] = wn;
+  const float2 xw = fpair_from(wn);
 #pragma unroll
   for (int m = 0; m < NF; ++m) {
-    double* qm = q + m * g.points + x.p;
-    *qm = fma(a.wq[m], wn, *qm);
+    float2* qm = q + m * g.points + x.p;
+    *qm = fpair_fma(a.wq_hi[m], a.wq_lo[m], xw.x, xw.y, *qm);
   }
 }
 
 template <int NF, int DIM, int ORDER>
 __global__ void __launch_bounds__(kBX * kBY)
 k_last(const double* __restrict__ Wc, const double* __restrict__ Wp, const double* __restrict__ f,
-       const double* __restrict__ q, double* vout, const double* vsub, const LastParams<NF> a,
+       const float2* __restrict__ q, double* vout, const double* vsub, const LastParams<NF> a,
        const Geom g) {
   const PointIndex x = point_index<DIM>(g);
   if (!x.inside) return;
@@ -166,7 +173,7 @@ k_last(const double* __restrict__ Wc, const double* __restrict__ Wp, const doubl
   const double wn = leapfrog_point<NF, DIM, ORDER>(Wc, Wp, f, a.st, g, x);
   double qq[NF];
 #pragma unroll
-  for (int m = 0; m < NF; ++m) qq[m] = fma(a.st.wq[m], wn, q[m * g.points + x.p]);
+  for (int m = 0; m < NF; ++m) qq[m] = fma(a.st.wq[m], wn, fpair_value(q[m * g.points + x.p]));
   double vk[NF];
   if (a.has_e) {
 #pragma unroll
@@ -292,27 +299,29 @@ void init_nf(const Geom& g, const double* v, double* W0, double* q, const double
              cudaStream_t st) {
   InitParams<NF> a;
   for (int m = 0; m < NF; ++m) a.w0[m] = w0[m];
+  float2* qp = reinterpret_cast<float2*>(q);
   dim3 blk(kBX, kBY);
   if (g.dim == 2)
-    k_init<NF, 2><<<step_grid(g), blk, 0, st>>>(v, W0, q, a, g);
+    k_init<NF, 2><<<step_grid(g), blk, 0, st>>>(v, W0, qp, a, g);
   else
-    k_init<NF, 3><<<step_grid(g), blk, 0, st>>>(v, W0, q, a, g);
+    k_init<NF, 3><<<step_grid(g), blk, 0, st>>>(v, W0, qp, a, g);
 }
 
 template <int NF>
 void step_nf(const Geom& g, const double* Wc, double* Wp, const double* f, double* q,
              const StepHost& h, cudaStream_t st) {
   const StepParams<NF> a = to_params<NF>(h);
+  float2* qp = reinterpret_cast<float2*>(q);
   dim3 blk(kBX, kBY);
   if (g.order == 4) {
     if (g.dim == 2)
-      k_step<NF, 2, 4><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, q, a, g);
+      k_step<NF, 2, 4><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, qp, a, g);
     else
-      k_step<NF, 3, 4><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, q, a, g);
+      k_step<NF, 3, 4><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, qp, a, g);
   } else if (g.dim == 2) {
-    k_step<NF, 2, 2><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, q, a, g);
+    k_step<NF, 2, 2><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, qp, a, g);
   } else {
-    k_step<NF, 3, 2><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, q, a, g);
+    k_step<NF, 3, 2><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, qp, a, g);
   }
 }
 
@@ -329,16 +338,17 @@ void last_nf(const Geom& g, const double* Wc, const double* Wp, const double* f,
   a.subtract = h.subtract;
   a.has_e = h.has_e && h.vprev != nullptr;
   a.vprev = h.vprev;
+  const float2* qp = reinterpret_cast<const float2*>(q);
   dim3 blk(kBX, kBY);
   if (g.order == 4) {
     if (g.dim == 2)
-      k_last<NF, 2, 4><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, q, vout, vsub, a, g);
+      k_last<NF, 2, 4><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, qp, vout, vsub, a, g);
     else
-      k_last<NF, 3, 4><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, q, vout, vsub, a, g);
+      k_last<NF, 3, 4><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, qp, vout, vsub, a, g);
   } else if (g.dim == 2) {
-    k_last<NF, 2, 2><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, q, vout, vsub, a, g);
+    k_last<NF, 2, 2><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, qp, vout, vsub, a, g);
   } else {
-    k_last<NF, 3, 2><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, q, vout, vsub, a, g);
+    k_last<NF, 3, 2><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, qp, vout, vsub, a, g);
   }
 }
 

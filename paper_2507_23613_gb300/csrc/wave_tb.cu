@@ -17,6 +17,7 @@
 // solve can fuse the filter solve V = B^{-1} q (eq. waveHoltzMatrixIteration).
 #include <cuda_runtime.h>
 
+#include "fpair.cuh"
 #include "kernels.h"
 
 namespace mfwh {
@@ -72,7 +73,7 @@ template <int NF, int T, int K>
 __global__ void __launch_bounds__(kTX * kTY, 1)
 k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
        double* __restrict__ Wc_out, double* __restrict__ Wp_out, const double* __restrict__ f,
-       double* __restrict__ q, double* vout, const double* vsub, const TBParams<NF> a,
+       float2* __restrict__ q, double* vout, const double* vsub, const TBParams<NF> a,
        const Geom g) {
   constexpr int BX = kTX, BY = kTY * K;
   constexpr int EX = BX + 2 * T, EY = BY + 2 * T;
@@ -81,6 +82,8 @@ k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
   double* B = smem + EX * EY;   // previous level, overwritten by the next one
   double* s_wq = smem + 2 * EX * EY;   // [T][NF] filter weights of the new level per step
   double* s_fc = s_wq + T * NF;        // [T][NF] kappa cos(omega~_m t^n) per step
+  float* s_wh = reinterpret_cast<float*>(s_fc + T * NF);   // [T][NF] s_wq as float pairs
+  float* s_wl = s_wh + T * NF;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * kTX + tx;
   constexpr int NT = kTX * kTY;
@@ -100,11 +103,17 @@ k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
   for (int e = tid; e < a.steps * NF; e += NT) {
     const int st = e / NF, m = e % NF;
     const int n = a.n0 + st;
-    s_wq[e] = a.wq_table[(n + 1) * NF + m];
+    const double w = a.wq_table[(n + 1) * NF + m];
+    s_wq[e] = w;
+    s_wh[e] = (float)w;
+    s_wl[e] = (float)(w - (double)s_wh[e]);
     s_fc[e] = a.forced ? (n == 0 ? a.half_dt2 : a.dt2) * a.cos_table[n * NF + m] : 0.0;
   }
-  // Owned tile points: (T + tx, T + ty + kTY k); their filter sums live in registers.
-  double qr[K][NF];
+  // Owned tile points: (T + tx, T + ty + kTY k); their filter sums live in registers as float
+  // pairs, updated as in k_step.  The final step of a wave solve (a.last) adds its term in
+  // FP64 in the epilogue, as k_last does.
+  float2 qr[K][NF];
+  double wlast[K];
   int64_t own_p[K];
   bool own_int[K], own_in[K];
 #pragma unroll
@@ -114,7 +123,9 @@ k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
     own_int[k] = interior_pt(gx, gy, g);
     own_p[k] = gy * g.sy + gx;
 #pragma unroll
-    for (int m = 0; m < NF; ++m) qr[k][m] = own_int[k] ? q[m * g.points + own_p[k]] : 0.0;
+    for (int m = 0; m < NF; ++m)
+      qr[k][m] = own_int[k] ? q[m * g.points + own_p[k]] : make_float2(0.0f, 0.0f);
+    wlast[k] = 0.0;
   }
   __syncthreads();
 
@@ -125,7 +136,9 @@ k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
     const LayerCoef lo = first ? a.first_lo : a.reg_lo;
     const LayerCoef hi = first ? a.first_hi : a.reg_hi;
     const double* fneg = s_fc + s * NF;
-    const double* wq = s_wq + s * NF;
+    const float* wh = s_wh + s * NF;
+    const float* wl = s_wl + s * NF;
+    const bool final_step = a.last && s == a.steps - 1;
     // owned tile points
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -136,8 +149,13 @@ k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
       const LayerCoef& L = li >= g.layer_split ? hi : lo;
       const double wn = update_point<NF>(A, B, l, EX, L, fneg, f, own_p[k], g.points, a.forced);
       B[l] = wn;
+      if (final_step) {
+        wlast[k] = wn;
+      } else {
+        const float2 xw = fpair_from(wn);
 #pragma unroll
-      for (int m = 0; m < NF; ++m) qr[k][m] = fma(wq[m], wn, qr[k][m]);
+        for (int m = 0; m < NF; ++m) qr[k][m] = fpair_fma(wh[m], wl[m], xw.x, xw.y, qr[k][m]);
+      }
     }
     // ring of radius r around the tile (halo points later steps need)
     if (r > 0) {
@@ -189,6 +207,10 @@ k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       if (!own_in[k]) continue;
+      const double* wq = s_wq + (a.steps - 1) * NF;
+      double qq[NF];
+#pragma unroll
+      for (int j = 0; j < NF; ++j) qq[j] = fma(wq[j], wlast[k], fpair_value(qr[k][j]));
       double vk[NF];
 #pragma unroll
       for (int j = 0; j < NF; ++j)
@@ -198,7 +220,7 @@ k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
       for (int m = 0; m < NF; ++m) {
         double s = 0.0;
 #pragma unroll
-        for (int j = 0; j < NF; ++j) s = fma(a.binv[m * NF + j], qr[k][j], s);
+        for (int j = 0; j < NF; ++j) s = fma(a.binv[m * NF + j], qq[j], s);
         if (a.has_e) {
 #pragma unroll
           for (int j = 0; j < NF; ++j) s = fma(a.emat[m * NF + j], vk[j], s);
@@ -222,7 +244,7 @@ void tb_launch_nf(const Geom& g, const double* Wc_in, const double* Wp_in, doubl
   constexpr int K = NF <= 8 ? 4 : 2;
   constexpr int BX = kTX, BY = kTY * K;
   constexpr int EX = BX + 2 * T, EY = BY + 2 * T;
-  constexpr size_t smem = sizeof(double) * (2 * EX * EY + 2 * T * NF);
+  constexpr size_t smem = sizeof(double) * (2 * EX * EY + 3 * T * NF);
   // The attribute is per device; set it once per device for this instance.
   static bool configured[64] = {};
   int dev = 0;
@@ -253,8 +275,9 @@ void tb_launch_nf(const Geom& g, const double* Wc_in, const double* Wp_in, doubl
       a.emat[m * NF + j] = h.emat[m * MFWH_MAX_NF + j];
     }
   dim3 grid((unsigned)((g.nx + 1 + BX - 1) / BX), (unsigned)((g.ny + 1 + BY - 1) / BY));
-  k_tb2d<NF, T, K><<<grid, dim3(kTX, kTY), smem, st>>>(Wc_in, Wp_in, Wc_out, Wp_out, f, q, vout,
-                                                       vsub, a, g);
+  k_tb2d<NF, T, K><<<grid, dim3(kTX, kTY), smem, st>>>(Wc_in, Wp_in, Wc_out, Wp_out, f,
+                                                       reinterpret_cast<float2*>(q), vout, vsub,
+                                                       a, g);
 }
 
 template <int NF>

@@ -381,13 +381,17 @@ def test_gmres_long_basis_parity():
     assert info["iterations"] == 40 and info["restarts"] == 1
     x, oinfo = W.gmres(prob, restart=100, tol=0.0, max_iters=40)
     assert np.all(rel_err(v, x) <= max(1e-9, opt_tol(prob))), rel_err(v, x)
-    np.testing.assert_allclose(info["history"], oinfo.history, rtol=1e-6)
+    # The library's maps keep the filter sums as float pairs: a few 2^-48 relative per update,
+    # at most about N_t 2^-46 of the sums per map.  The relative residuals of the history are
+    # compared to that absolute level (about 1.4e-12 here; measured differences near 1e-14).
+    np.testing.assert_allclose(info["history"], oinfo.history, rtol=1e-6,
+                               atol=prob.setup.n_t * 2.0 ** -46)
 
 
 def test_full_size_gmres_cycle_residual_is_true_residual():
     """Two GMRES(20) cycles on the benchmark workload: the Arnoldi residual estimate the
-    solver reports equals the true residual ||Pi(V) - V||_2 / ||Pi(0)||_2 of the returned V,
-    and the estimate does not increase within a cycle."""
+    solver reports equals the true residual ||Pi(V) - V||_2 / ||Pi(0)||_2 of the returned V
+    (to the accuracy of the maps), and the estimate does not increase within a cycle."""
     wl = inputs.square_large()
     solver = M.Solver(wl.n, wl.length, wl.omega, dev(wl.forcing), n_p=wl.n_p, cfl=wl.cfl)
     v = torch.zeros(wl.forcing.shape, dtype=torch.float64, device="cuda")
@@ -401,6 +405,13 @@ def test_full_size_gmres_cycle_residual_is_true_residual():
     b = torch.empty_like(v)
     solver.apply_Pi(None, b, forced=True)
     torch.cuda.synchronize()
-    true_res = float(torch.linalg.norm(pv - v) / torch.linalg.norm(b))
-    assert abs(true_res - info["rel_residual"]) <= 1e-6 * info["rel_residual"] + 1e-13, (true_res, info["rel_residual"])
+    nb = float(torch.linalg.norm(b))
+    true_res = float(torch.linalg.norm(pv - v)) / nb
+    # Each map carries the float-pair filter sums' error, at most about N_t 2^-46 of its
+    # output.  The estimate combines 20 products S v_j per cycle (coefficients y with
+    # sum |y_j| <= sqrt(40) ||V||); the true residual takes one more map of V.
+    eps_map = solver.setup["n_t"] * 2.0 ** -46
+    bound = eps_map * (float(torch.linalg.norm(pv)) + 40 ** 0.5 * float(torch.linalg.norm(v))) / nb
+    assert abs(true_res - info["rel_residual"]) <= 1e-6 * info["rel_residual"] + 1e-13 + bound, \
+        (true_res, info["rel_residual"], bound)
     assert np.all(np.isfinite(info["helmholtz_residual"]))
