@@ -1,0 +1,60 @@
+"""Host-side checks of bench.py's accounting (CPU only): the algorithmic bytes and FP64 flops
+per point-step behind the roofline, the rule that a committed ncu traffic figure is used only
+while the kernel source it was taken on is unchanged, and the oracle baseline's report."""
+
+import os
+import sys
+
+import pytest
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+from paper_2507_23613_gb300 import inputs  # noqa: E402
+
+
+def test_bytes_and_flops_per_point_step():
+    # homogeneous: read W^n, W^{n-1}, q_1..8; write W^{n+1}, q_1..8 (8-byte words)
+    assert bench.bytes_per_point_step(8, False) == (3 + 2 * 8) * 8 == 152
+    # forced adds the 8 forcing grids
+    assert bench.bytes_per_point_step(8, True) == (3 + 3 * 8) * 8 == 216
+    # FP64 flops: 3 leapfrog FMAs, 3 stencil adds, the float-pair split; forcing FMAs if forced
+    assert bench.flops_per_point_step(8, False) == 10
+    assert bench.flops_per_point_step(8, True) == 26
+    assert bench.flops_per_point_step(4, False, dim=3) == 12
+
+
+def test_traffic_only_for_the_kernel_it_was_taken_on(tmp_path, monkeypatch):
+    key = bench.kernel_source_key()
+    assert len(key) == 16 and key == bench.kernel_source_key()
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "k.txt").write_text("# comment: 1\nsource_sha256: %s\ndram_bytes_per_launch: 123.5\n"
+                                % key)
+    (prof / "old.txt").write_text("source_sha256: 0000000000000000\ndram_bytes_per_launch: 9\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.kernel_traffic("k.txt", key) == 123.5
+    assert bench.kernel_traffic("old.txt", key) is None
+    assert bench.kernel_traffic("missing.txt", key) is None
+
+
+def test_committed_fp32_profile_matches_its_kernel():
+    """The FP32 blocked kernel's ncu summary carries the hash of the source it was taken on."""
+    assert bench.kernel_traffic("k_tb2d32_square1025_nf8.txt", bench.fp32_kernel_source_key()) \
+        is not None
+
+
+def test_cpu_baseline_report():
+    info = bench.cpu_baseline(inputs.square_small(), budget_s=0.2)
+    assert info["kind"] == "oracle" and info["cores"] == 1 and info["unit"] == "Gpts/s"
+    assert info["value"] > 0 and "65x65" in info["sample"]
+
+
+@pytest.mark.parametrize("argv,flag", [(["--small"], "small"),
+                                       (["--implicit-scaling", "--cube"], "implicit_scaling"),
+                                       (["--impl", "reference", "--oracle-timings"],
+                                        "oracle_timings")])
+def test_modes_parse(argv, flag, monkeypatch):
+    monkeypatch.setattr(sys, "argv", ["bench.py"] + argv)
+    args = bench.parse()
+    assert getattr(args, flag)
+    assert args.steps == 3 and args.warmup == 3 and args.gpus == 1
