@@ -7,6 +7,7 @@ Where the paper is silent the reading used is stated in the docstring.
 
 import math
 from dataclasses import dataclass
+from fractions import Fraction
 
 import numpy as np
 
@@ -68,12 +69,15 @@ def implicit_time_step(omega1, omega_max, n_p, steps_per_period=10, scheme=TRAPE
 def period_counts(omega, n_p):
     """eq. TbarDef with periods T_m = 2 pi / omega_m.
 
-    T_f = N_p T_1, N_{p,m} = floor(T_f / T_m) and T_{f,m} = N_{p,m} T_m.  The
-    ratio T_f / T_m is formed as N_p omega_m / omega_1 so that it is exact for m = 1.
+    T_f = N_p T_1, N_{p,m} = floor(T_f / T_m) and T_{f,m} = N_{p,m} T_m.  The floor
+    of T_f / T_m = N_p omega_m / omega_1 is taken in exact rational arithmetic on the
+    given floating-point frequencies, so N_{p,1} = N_p and no count is lost when a
+    ratio lies within rounding of an integer.
     """
     omega = np.asarray(omega, dtype=np.float64)
-    ratio = n_p * omega / omega[0]
-    n_pm = np.floor(ratio).astype(np.int64)
+    w1 = Fraction(float(omega[0]))
+    n_pm = np.array([math.floor(int(n_p) * Fraction(float(w)) / w1) for w in omega],
+                    dtype=np.int64)
     t_fm = n_pm * (2.0 * math.pi / omega)
     t_f = n_p * 2.0 * math.pi / omega[0]
     return n_pm, t_fm, t_f

@@ -65,7 +65,9 @@ def _compare_setup(wl, n_p=1, mode=F.FILTER_OPTIMIZED, user=None, c_hi=None, ord
     np.testing.assert_allclose(s["B"], o.B, atol=max(1e-12, rel) * 10 * np.max(np.abs(o.B)))
     w = M.plan_weights(prob, s["n_t"], wl.nf)
     np.testing.assert_allclose(w, o.w, atol=max(1e-12, rel) * 10 * np.max(np.abs(o.w)))
-    np.testing.assert_allclose(s["B_inv"] @ s["B"], np.eye(wl.nf), atol=1e-9)
+    # B^{-1} B = I to the accuracy cond(B) allows (the library accepts cond_1(B) <= 1e12)
+    tol_inv = max(1e-9, 100 * eps * np.linalg.cond(s["B"], 1))
+    np.testing.assert_allclose(s["B_inv"] @ s["B"], np.eye(wl.nf), atol=tol_inv)
     return s, o
 
 
@@ -241,3 +243,36 @@ def test_multigrid_hierarchy_of_implicit_problems():
     prob, keep = M.make_problem((64, 64), (1.0, 1.0), [5.5, 9.3])   # explicit problem
     with pytest.raises(_lib.MfwhError):
         M.plan_multigrid(prob)
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_plan_matches_oracle_seeded_sweep(seed):
+    """Seeded sweep of the set-up (step size, N_t, adjusted frequencies, N_{p,m}, filter
+    parameters, B, weights) over dimension, N_f = 1..16, N_p = 1..3, filter modes, operator
+    order, time stepping and two-layer media, each against the oracle.  Where the library
+    refuses a problem as singular, the oracle must confirm it: cond_1(B) above 1e11, or
+    least-squares parameters that the data do not determine (10 eps cond(M)^2 > 1e-2)."""
+    rng = np.random.default_rng(9100 + seed)
+    dim = int(rng.integers(2, 4))
+    n = tuple(int(k) for k in rng.choice([16, 24, 32, 40], size=dim))
+    nf = int(rng.integers(1, 17))
+    lo = float(rng.uniform(3.0, 10.0))
+    band = (lo, lo + nf * float(rng.uniform(2.5, 4.5)))
+    length = tuple(float(x) for x in rng.uniform(0.8, 1.4, size=dim))
+    wl = inputs.gaussian_workload(f"sweep{seed}", n, nf,
+                                  lambda r: inputs.draw_frequencies(r, nf, *band, min_gap=1.0),
+                                  100.0, seed, length=length)
+    mode = [F.FILTER_OPTIMIZED, F.FILTER_TRADITIONAL][int(rng.integers(0, 2))]
+    kw = dict(n_p=int(rng.integers(1, 4)), mode=mode, order=int(rng.choice([2, 4])),
+              time_stepping=["explicit", "implicit"][int(rng.integers(0, 2))],
+              c_hi=[None, 1.5][int(rng.integers(0, 2))])
+    h = [L / k for L, k in zip(wl.length, wl.n)]
+    o = F.make_setup(wl.omega, h, 1.0 if kw["c_hi"] is None else 1.5, 0.5, kw["n_p"], mode,
+                     None, order=kw["order"], time_stepping=kw["time_stepping"])
+    try:
+        _compare_setup(wl, **kw)
+    except _lib.MfwhError as e:
+        assert e.status == _lib.ERR_SINGULAR, e
+        eps = np.finfo(float).eps
+        undetermined = np.isfinite(o.cond_M) and 10 * eps * o.cond_M ** 2 > 1e-2
+        assert np.linalg.cond(o.B, 1) > 1e11 or undetermined, (np.linalg.cond(o.B, 1), o.cond_M)

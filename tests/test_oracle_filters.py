@@ -2,6 +2,7 @@
 paper prints, closed forms and the paper's theorems.  CPU only."""
 
 import json
+from fractions import Fraction
 import math
 import os
 
@@ -238,3 +239,26 @@ def test_filter_matrix_definition():
     """B_{mj} equals the discrete filter function beta_{d,m} evaluated at omega~_j."""
     s = _setup([5.5, 9.3, 14.2], F.FILTER_OPTIMIZED)
     np.testing.assert_allclose(s.B, F.discrete_beta(s.w, s.omega_t, s.dt).T, atol=1e-14)
+
+
+def test_period_count_of_the_first_frequency_is_n_p():
+    """eq. TbarDef: T_f = N_p T_1, so N_{p,1} = floor(T_f / T_1) = N_p exactly.  Forming
+    N_p omega_1 / omega_1 in floating point can round below N_p (about 7 % of random omega_1
+    for N_p = 3); these values are such cases."""
+    for n_p, w1 in [(3, 6.324608295390162), (5, 6.692997385840716), (6, 25.67958426865055),
+                    (7, 18.463274230059614)]:
+        assert math.floor(n_p * w1 / w1) == n_p - 1          # the rounding trap
+        n_pm, t_fm, t_f = F.period_counts(np.array([w1, 2.3 * w1]), n_p)
+        assert n_pm[0] == n_p
+        assert abs(t_fm[0] - t_f) <= 1e-15 * t_f
+    rng = np.random.default_rng(12)
+    for _ in range(200):
+        w = np.sort(rng.uniform(1.0, 80.0, size=4))
+        n_p = int(rng.integers(1, 8))
+        n_pm, _, _ = F.period_counts(w, n_p)
+        assert n_pm[0] == n_p
+        # brute force of the definition: the largest k with k T_m <= T_f, in exact arithmetic
+        t_f = Fraction(n_p) / Fraction(float(w[0]))
+        for m in range(4):
+            k = int(n_pm[m])
+            assert Fraction(k) / Fraction(float(w[m])) <= t_f < Fraction(k + 1) / Fraction(float(w[m]))
