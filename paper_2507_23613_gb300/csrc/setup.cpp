@@ -209,13 +209,14 @@ mfwh_status optimise_parameters(int nf, const double* omega, int n_p, int n_t, i
     set_error(os.str());
     return MFWH_ERR_SINGULAR;
   }
-  // G^{-1} z and G^{-1} H.
-  std::vector<double> Gz(n2, 0.0), GH(n2 * nf, 0.0);
-  for (int i = 0; i < n2; ++i)
-    for (int k = 0; k < n2; ++k) {
-      Gz[i] += Ginv[i * n2 + k] * z[k];
-      for (int j = 0; j < nf; ++j) GH[i * nf + j] += Ginv[i * n2 + k] * H[k * nf + j];
-    }
+  // G^{-1} z and G^{-1} H by LU solves with partial pivoting.  The explicit inverse serves
+  // only the condition estimate: products with it are not backward stable, and with cond(G)
+  // near the limit they leave the constraints of eq. constraintsT visibly unmet.
+  std::vector<double> Gz = z, GH = H;
+  if (!lu_solve(n2, G, Gz, 1) || !lu_solve(n2, G, GH, nf)) {
+    set_error("filter optimisation: constraint matrix G is singular");
+    return MFWH_ERR_SINGULAR;
+  }
 
   // Spectral interval and midpoint nodes (eq. LambdaRange).  lam_max / delta equals
   // the integer 2 N_{p,Nf} + c_delta N_f, hence the guard against rounding up.
@@ -244,21 +245,20 @@ mfwh_status optimise_parameters(int nf, const double* omega, int n_p, int n_t, i
     set_error("filter optimisation: least-squares matrix is rank deficient");
     return MFWH_ERR_SINGULAR;
   }
-  // y = G^{-1} (z - H x_a) (eq. yOpt).
-  std::vector<double> rhs(n2);
+  // y = G^{-1} (z - H x_a) (eq. yOpt), again by an LU solve.
+  std::vector<double> y(n2);
   for (int i = 0; i < n2; ++i) {
-    rhs[i] = z[i];
-    for (int j = 0; j < nf; ++j) rhs[i] -= H[i * nf + j] * xa[j];
+    y[i] = z[i];
+    for (int j = 0; j < nf; ++j) y[i] -= H[i * nf + j] * xa[j];
+  }
+  if (!lu_solve(n2, G, y, 1)) {
+    set_error("filter optimisation: constraint matrix G is singular");
+    return MFWH_ERR_SINGULAR;
   }
   for (int m = 0; m < nf; ++m) {
-    double yc = 0.0, ys = 0.0;
-    for (int i = 0; i < n2; ++i) {
-      yc += Ginv[m * n2 + i] * rhs[i];
-      ys += Ginv[(nf + m) * n2 + i] * rhs[i];
-    }
     params[3 * m + 0] = xa[m];
-    params[3 * m + 1] = yc;
-    params[3 * m + 2] = ys;
+    params[3 * m + 1] = y[m];
+    params[3 * m + 2] = y[nf + m];
   }
   if (lam_max_out) *lam_max_out = lam_max;
   if (n_lambda_out) *n_lambda_out = n_lambda;
