@@ -295,3 +295,28 @@ def test_plan_matches_oracle_seeded_sweep(seed):
         eps = np.finfo(float).eps
         undetermined = np.isfinite(o.cond_M) and 10 * eps * o.cond_M ** 2 > 1e-2
         assert np.linalg.cond(o.B, 1) > 1e11 or undetermined, (np.linalg.cond(o.B, 1), o.cond_M)
+
+
+def test_status_strings_and_thread_local_error_message():
+    """Every status has a name; the message of a failed call is kept per thread."""
+    import threading
+    lib = _lib.load()
+    names = {lib.mfwh_status_string(k).decode() for k in range(8)}
+    assert len(names) == 8 and "ok" in names
+    assert lib.mfwh_status_string(99).decode() == "unknown status"
+    prob, keep = M.make_problem((64, 64), (1.0, 1.0), [9.3, 5.5])   # not increasing
+    with pytest.raises(_lib.MfwhError) as e:
+        M.plan(prob)
+    assert "increasing" in str(e.value)
+    seen = []
+
+    def other():
+        ok, keep2 = M.make_problem((64, 64), (1.0, 1.0), [5.5, 9.3])
+        M.plan(ok)                                # succeeds in this thread
+        seen.append(lib.mfwh_last_error().decode())
+
+    t = threading.Thread(target=other)
+    t.start()
+    t.join()
+    assert "increasing" not in seen[0]
+    assert "increasing" in lib.mfwh_last_error().decode()   # this thread's message survives
