@@ -267,8 +267,9 @@ def test_multigrid_hierarchy_of_implicit_problems():
 @pytest.mark.parametrize("seed", range(24))
 def test_plan_matches_oracle_seeded_sweep(seed):
     """Seeded sweep of the set-up (step size, N_t, adjusted frequencies, N_{p,m}, filter
-    parameters, B, weights) over dimension, N_f = 1..16, N_p = 1..3, filter modes, operator
-    order, time stepping and two-layer media, each against the oracle.  Where the library
+    parameters, B, weights) over dimension, N_f = 1..16, N_p = 1..3, the three filter modes
+    (optimised, traditional, seeded user parameters), operator order, time stepping and
+    two-layer media, each against the oracle.  Where the library
     refuses a problem as singular, the oracle must confirm it: cond_1(B) above 1e11, or
     least-squares parameters that the data do not determine (10 eps cond(M)^2 > 1e-2)."""
     rng = np.random.default_rng(9100 + seed)
@@ -281,13 +282,14 @@ def test_plan_matches_oracle_seeded_sweep(seed):
     wl = inputs.gaussian_workload(f"sweep{seed}", n, nf,
                                   lambda r: inputs.draw_frequencies(r, nf, *band, min_gap=1.0),
                                   100.0, seed, length=length)
-    mode = [F.FILTER_OPTIMIZED, F.FILTER_TRADITIONAL][int(rng.integers(0, 2))]
+    mode = [F.FILTER_OPTIMIZED, F.FILTER_TRADITIONAL, F.FILTER_USER][int(rng.integers(0, 3))]
+    user = inputs.random_filter_params(700 + seed, nf) if mode == F.FILTER_USER else None
     kw = dict(n_p=int(rng.integers(1, 4)), mode=mode, order=int(rng.choice([2, 4])),
               time_stepping=["explicit", "implicit"][int(rng.integers(0, 2))],
-              c_hi=[None, 1.5][int(rng.integers(0, 2))])
+              c_hi=[None, 1.5][int(rng.integers(0, 2))], user=user)
     h = [L / k for L, k in zip(wl.length, wl.n)]
     o = F.make_setup(wl.omega, h, 1.0 if kw["c_hi"] is None else 1.5, 0.5, kw["n_p"], mode,
-                     None, order=kw["order"], time_stepping=kw["time_stepping"])
+                     user, order=kw["order"], time_stepping=kw["time_stepping"])
     try:
         _compare_setup(wl, **kw)
     except _lib.MfwhError as e:
