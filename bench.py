@@ -884,7 +884,8 @@ def workload_config(wl, n_t):
             "step": "one GMRES(20) cycle from zero: b = Pi(0), 20 Arnoldi steps, update, residual check",
             "grid": [wl.n[0] + 1, wl.n[1] + 1], "nf": wl.nf, "n_p": wl.n_p, "n_t": n_t,
             "omega_band": [10.0, 60.0], "gaussian_b": 400.0, "cfl": wl.cfl,
-            "restart": RESTART, "tol": TOL, "precision": "fp64",
+            "restart": RESTART, "tol": TOL,
+            "precision": "fp64 wave levels, steps and filter solve; filter sums as float pairs",
             "l2": "working set (forcing, accumulators, Krylov basis: > 1 GB) is larger than L2"}
 
 

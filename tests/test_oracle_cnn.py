@@ -73,3 +73,39 @@ def test_adam_step_written_out():
     np.testing.assert_allclose(p1, p - 0.01 * g / (np.abs(g) + 1e-8))
     np.testing.assert_allclose(m1, 0.1 * g)
     np.testing.assert_allclose(v1, 0.001 * g * g)
+
+
+def test_adam_constant_gradient_moves_lr_per_step():
+    """With a constant gradient g the bias-corrected moments are exactly g and g^2 at every
+    step (m_t = (1 - beta1^t) g, v_t = (1 - beta2^t) g^2), so step t moves p by
+    lr g / (|g| + eps).  A bias correction without its power t (1 - beta instead of
+    1 - beta^t) moves 1.34 lr at t = 2 and fails here."""
+    g = np.array([0.5, -0.25, 3.0])
+    p = np.array([1.0, -2.0, 0.5])
+    m = np.zeros(3)
+    v = np.zeros(3)
+    lr = 0.01
+    for t in range(1, 6):
+        p_new, m, v = cnn.adam_step(p, g, m, v, t, lr)
+        np.testing.assert_allclose(p - p_new, lr * g / (np.abs(g) + 1e-8), rtol=1e-12)
+        p = p_new
+
+
+def test_adam_three_steps_worked_example():
+    """Three steps with gradients 1/2, -3/10, 1/5 from p = 1, lr = 0.01, computed by hand
+    in exact fractions: m = 1/20, 3/200, 67/2000; v = 1/4000, 1359/4000000,
+    1517641/4000000000; bias-corrected at t = 2: m^ = (3/200)/(19/100) = 3/38,
+    v^ = (1359/4000000)/(1999/1000000) = 1359/7996."""
+    p = np.array([1.0])
+    m = np.zeros(1)
+    v = np.zeros(1)
+    want_m = [0.05, 0.015, 0.0335]
+    want_v = [0.00025, 0.00033975, 0.00037941025]
+    want_p = [1.0 - 0.01 * 0.5 / (0.5 + 1e-8),
+              1.0 - 0.01 * 0.5 / (0.5 + 1e-8) - 0.01 * (3.0 / 38.0) / ((1359.0 / 7996.0) ** 0.5 + 1e-8),
+              0.9846107430790882]
+    for t, g in enumerate([0.5, -0.3, 0.2], start=1):
+        p, m, v = cnn.adam_step(p, np.array([g]), m, v, t, 0.01)
+        np.testing.assert_allclose(m, want_m[t - 1], rtol=1e-14)
+        np.testing.assert_allclose(v, want_v[t - 1], rtol=1e-14)
+        np.testing.assert_allclose(p, want_p[t - 1], rtol=1e-14)
