@@ -145,11 +145,20 @@ def kernel_traffic(profile, kernel_key):
         return None
 
 
+def _code_only(text):
+    """Source text without comments and without whitespace, so that the hash of a kernel's
+    source changes with its code and not with its comments."""
+    import re
+    text = re.sub(rb"/\*.*?\*/", b"", text, flags=re.S)
+    text = re.sub(rb"//[^\n]*", b"", text)
+    return re.sub(rb"\s+", b"", text)
+
+
 def _region(path, end_marker):
     with open(os.path.join(ROOT, "paper_2507_23613_gb300", "csrc", path), "rb") as fh:
         text = fh.read()
     cut = text.find(end_marker.encode())
-    return text if cut < 0 else text[:cut]
+    return _code_only(text if cut < 0 else text[:cut])
 
 
 def kernel_source_key():

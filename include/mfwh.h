@@ -47,7 +47,11 @@ typedef enum {
   MFWH_ERR_NOMEM = 4,         /* device or host allocation failed */
   MFWH_ERR_NOT_CONVERGED = 5, /* GMRES reached max_iters above the tolerance */
   MFWH_ERR_SPURIOUS = 6,      /* GMRES converged but the Helmholtz residual check failed */
-  MFWH_ERR_NONFINITE = 7      /* NaN or Inf in an iterate or residual */
+  MFWH_ERR_NONFINITE = 7,     /* NaN or Inf in an iterate or residual */
+  MFWH_ERR_TIMEOUT = 8        /* a bounded wait inside a kernel ran out: a grid-barrier wait of
+                                 the implicit step kernel (limit: mfwh_set_wait_limit) or a
+                                 tile's tensor copy of the FP32 blocked kernel; that wave solve's
+                                 results are invalid, the handle stays usable */
 } mfwh_status;
 
 enum { MFWH_FILTER_OPTIMIZED = 0, MFWH_FILTER_TRADITIONAL = 1, MFWH_FILTER_USER = 2 };
@@ -64,7 +68,7 @@ enum { MFWH_FILTER_OPTIMIZED = 0, MFWH_FILTER_TRADITIONAL = 1, MFWH_FILTER_USER 
 enum { MFWH_PREC_FP64 = 0, MFWH_PREC_FP32_KAHAN = 1, MFWH_PREC_FP32_BLOCKSUM = 2 };
 /* How the filter sums become the next iterate (Section "The MFWH algorithm"). */
 enum { MFWH_UPDATE_IMPLICIT = 0, MFWH_UPDATE_EXPLICIT = 1 };
-enum { MFWH_C_CONST = 0, MFWH_C_TWO_LAYER = 1 };
+enum { MFWH_C_CONST = 0, MFWH_C_TWO_LAYER = 1, MFWH_C_FIELD = 2 };
 /* Time stepping of the wave solve (Section "Explicit and implicit time-stepping"). */
 enum { MFWH_TIME_EXPLICIT = 0, MFWH_TIME_IMPLICIT = 1 };
 
@@ -81,8 +85,10 @@ typedef struct {
   const double* forcing;     /* host or device, [nf][points] values of f_m at the grid points;
                                 copied into the handle by mfwh_create (may be NULL: zero forcing) */
   int c_mode;                /* MFWH_C_CONST: c = c_lo everywhere;
-                                MFWH_C_TWO_LAYER: c = c_lo where x_axis < interface, c_hi elsewhere */
-  double c_lo, c_hi;         /* wave speeds (> 0) */
+                                MFWH_C_TWO_LAYER: c = c_lo where x_axis < interface, c_hi elsewhere;
+                                MFWH_C_FIELD: c^2 given per grid point by c2_field (L = c^2 Delta
+                                in non-divergence form, L_h W = c_j^2 Delta_h W at point j) */
+  double c_lo, c_hi;         /* wave speeds (> 0; c_lo is not used with MFWH_C_FIELD) */
   double interface;          /* coordinate of the layer interface (TWO_LAYER) */
   int layer_axis;            /* 0 = x, 1 = y, 2 = z (TWO_LAYER) */
   int n_p;                   /* N_p: periods of the longest period integrated (>= 1) */
@@ -126,6 +132,14 @@ typedef struct {
   double mg_tol;             /* implicit: a step's multigrid solve stops when
                                 max|rhs - A Z| <= mg_tol max|rhs| (0 means 1e-10) */
   int mg_max_cycles;         /* implicit: V-cycles per step at most (0 means 30; <= 60) */
+  const double* c2_field;    /* MFWH_C_FIELD: host or device [points], c^2 at every grid point
+                                (all values finite and > 0); copied into the handle by
+                                mfwh_create.  c_max^2 = the largest value (all points) sets the
+                                explicit time step.  Supported with explicit time stepping and
+                                MFWH_PREC_FP64, one step per launch (time_block 0 or 1), second
+                                or fourth order; other combinations return
+                                MFWH_ERR_INVALID_ARG.  mfwh_plan and the other host-only calls
+                                read a device field through the CUDA runtime. */
 } mfwh_problem;
 
 /* Everything the set-up derives from a problem (Algorithm 1, first two lines;
@@ -347,16 +361,22 @@ mfwh_status mfwh_residual(mfwh_handle_t h, const double* v, double* r_out);
  * reduction scratch is one fixed array of MFWH_NOALLOC_SCRATCH_DOUBLES doubles
  * (256 KiB) in the library's device memory, which every GPU that loads the
  * library holds until the process exits.
- *   prob:    grid (dim, n, length), nf, omega and the wave-speed fields, as for
- *            mfwh_create; the other fields are not used
+ *   prob:    grid (dim, n, length), nf, omega, order and the wave-speed fields, as for
+ *            mfwh_create (with MFWH_C_FIELD, c2_field must be device memory of the
+ *            current device, values not checked); the other fields are not used
  *   forcing: device [nf][points], the values f_m
  *   v:       device [nf][points]
+ *            (forcing and v: device memory of the current device, or managed
+ *            memory; other pointers are rejected with MFWH_ERR_INVALID_ARG)
  *   r_out:   host [nf], receives r_h^{(m)}
  *   stream:  cudaStream_t to run on (NULL = legacy default stream); the call
  *            synchronises that stream before it returns.
  * The first call on each device looks up the array's device address (set-up,
- * once per device, with that device current): make that first call before any
- * stream capture.  Every call uses the same array, so calls whose work
+ * once per device, with that device current) and keeps it for the life of the
+ * process: make that first call before any stream capture.  A cudaDeviceReset
+ * of that device unloads the library's device code and leaves the kept address
+ * stale, so after one do not call this entry point on that device again.
+ * Every call uses the same array, so calls whose work
  * overlaps on the GPU (from other threads or streams) race and must be
  * serialised by the caller.  A call needs 1216 * nf + 2 * nf doubles; a
  * problem needing more than the array holds is rejected (MFWH_ERR_INVALID_ARG). */
@@ -385,6 +405,18 @@ mfwh_status mfwh_last_timing(mfwh_handle_t h, double* step_ms, int64_t* step_lau
  * reading them.  Synchronises the stream.  MFWH_ERR_INVALID_ARG for an explicit handle. */
 mfwh_status mfwh_mg_stats(mfwh_handle_t h, int64_t* solves, int64_t* cycles,
                           int64_t* unconverged, int* levels, int reset);
+
+/* Time limit of one grid-barrier wait inside the implicit step kernel (MFWH_TIME_IMPLICIT
+ * handles whose hierarchy has grid-wide levels; Section "Explicit and implicit time-stepping"),
+ * in seconds; seconds <= 0 restores the default of 2 s.  The blocks of that cooperative launch
+ * meet at a barrier between multigrid phases.  When one wait runs out, the kernel records it
+ * in a device flag and every later barrier of the launch lets its blocks through, so the launch
+ * ends (its results are then invalid) and the remaining step launches of the wave solve return
+ * at once.  The call that completes the solve (mfwh_solve_fpi, mfwh_solve_gmres,
+ * mfwh_solve_refined, mfwh_residual after it, or mfwh_last_timing after mfwh_apply_Pi) then
+ * returns MFWH_ERR_TIMEOUT and clears the flag and the barrier state, so the handle can be
+ * used again.  Explicit handles accept the call and ignore the limit (no grid barriers). */
+mfwh_status mfwh_set_wait_limit(mfwh_handle_t h, double seconds);
 
 /* Release the handle and its device workspace (waits for its stream). */
 void mfwh_destroy(mfwh_handle_t h);

@@ -38,9 +38,11 @@ def make_problem(n, length, omega, forcing=None, c_lo=1.0, c_hi=None, interface=
                  layer_axis=2, n_p=1, cfl=0.5, filter_mode=_lib.FILTER_OPTIMIZED,
                  user_params=None, n_delta=20, c_delta=2.0, time_block=0, precision=None,
                  tile_shape=0, order=2, filter_update=0, time_stepping="explicit",
-                 steps_per_period=0, mg_tol=0.0, mg_max_cycles=0):
+                 steps_per_period=0, mg_tol=0.0, mg_max_cycles=0, c2_field=None):
     """Fill an mfwh_problem.  Returned keep-alive list holds the arrays it points to.
-    time_stepping: "explicit" (leapfrog) or "implicit" (trapezoidal, multigrid solves)."""
+    time_stepping: "explicit" (leapfrog) or "implicit" (trapezoidal, multigrid solves).
+    c2_field: c^2 at every grid point (numpy array or CUDA tensor, float64, grid shape);
+    selects MFWH_C_FIELD."""
     p = _lib.Problem()
     p.dim = len(n)
     for a in range(3):
@@ -55,6 +57,12 @@ def make_problem(n, length, omega, forcing=None, c_lo=1.0, c_hi=None, interface=
         p.forcing = C.cast(ptr, C.POINTER(C.c_double))
         keep.append(forcing)
     p.c_mode = _lib.C_CONST if c_hi is None else _lib.C_TWO_LAYER
+    if c2_field is not None:
+        if c_hi is not None:
+            raise ValueError("give either c_hi (two layers) or c2_field, not both")
+        p.c_mode = _lib.C_FIELD
+        p.c2_field = C.cast(_as_ptr(c2_field), C.POINTER(C.c_double))
+        keep.append(c2_field)
     p.c_lo = float(c_lo)
     p.c_hi = float(c_hi if c_hi is not None else c_lo)
     p.interface = float(interface)
@@ -279,6 +287,10 @@ class Solver:
         if st not in (_lib.OK, _lib.ERR_NOT_CONVERGED):
             _lib.check(st)
         return st == _lib.OK, ratio.value
+
+    def set_wait_limit(self, seconds):
+        """Limit (s) of one grid-barrier wait of the implicit step kernel; <= 0: default 2 s."""
+        _lib.check(_lib.load().mfwh_set_wait_limit(self._handle, float(seconds)))
 
     def set_graphs(self, enable=True):
         _lib.check(_lib.load().mfwh_set_graphs(self._handle, int(bool(enable))))

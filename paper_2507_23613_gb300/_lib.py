@@ -20,6 +20,7 @@ ERR_NOMEM = 4
 ERR_NOT_CONVERGED = 5
 ERR_SPURIOUS = 6
 ERR_NONFINITE = 7
+ERR_TIMEOUT = 8
 
 FILTER_OPTIMIZED = 0
 FILTER_TRADITIONAL = 1
@@ -31,6 +32,7 @@ UPDATE_IMPLICIT = 0
 UPDATE_EXPLICIT = 1
 C_CONST = 0
 C_TWO_LAYER = 1
+C_FIELD = 2
 TIME_EXPLICIT = 0
 TIME_IMPLICIT = 1
 
@@ -65,6 +67,7 @@ class Problem(C.Structure):
         ("steps_per_period", C.c_int),
         ("mg_tol", C.c_double),
         ("mg_max_cycles", C.c_int),
+        ("c2_field", _dp),
     ]
 
 
@@ -141,6 +144,7 @@ _SIGNATURES = {
                                       C.POINTER(C.c_int64 * 3)]),
     "mfwh_mg_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                 C.POINTER(C.c_int64), C.POINTER(C.c_int), C.c_int]),
+    "mfwh_set_wait_limit": (C.c_int, [C.c_void_p, C.c_double]),
     "mfwh_destroy": (None, [C.c_void_p]),
     "mfwh_last_error": (C.c_char_p, []),
     "mfwh_status_string": (C.c_char_p, [C.c_int]),

@@ -64,6 +64,47 @@ bool is_device_ptr(const void* p) {
   return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
 }
 
+// Largest value of a problem's c^2 field (MFWH_C_FIELD), read from host or device memory, for
+// the time step of plan_problem: NaN when a value is not finite or not > 0 (plan_problem then
+// rejects the problem); 0 for the other c modes and for grids plan_problem rejects anyway.
+mfwh_status field_max(const mfwh_problem* p, double* mx) {
+  *mx = 0.0;
+  if (!p || p->c_mode != MFWH_C_FIELD || !p->c2_field || (p->dim != 2 && p->dim != 3))
+    return MFWH_OK;
+  int64_t points = 1;
+  for (int a = 0; a < p->dim; ++a) {
+    if (p->n[a] < 2 || p->n[a] > (1 << 20)) return MFWH_OK;
+    points *= p->n[a] + 1;
+  }
+  if (points > ((int64_t)1 << 34)) return MFWH_OK;
+  std::vector<double> copy;
+  const double* c2 = p->c2_field;
+  if (is_device_ptr(c2)) {
+    copy.resize((size_t)points);
+    CK(cudaMemcpy(copy.data(), c2, sizeof(double) * points, cudaMemcpyDefault));
+    c2 = copy.data();
+  }
+  double m = 0.0;
+  for (int64_t i = 0; i < points; ++i) {
+    const double x = c2[i];
+    if (!(x > 0.0) || !std::isfinite(x)) {
+      *mx = std::nan("");
+      return MFWH_OK;
+    }
+    m = std::max(m, x);
+  }
+  *mx = m;
+  return MFWH_OK;
+}
+
+// plan_problem with the c^2 field's maximum read first.
+mfwh_status plan_with_field(const mfwh_problem* p, Plan* P) {
+  double c2m = 0.0;
+  mfwh_status st = field_max(p, &c2m);
+  if (st != MFWH_OK) return st;
+  return plan_problem(p, P, c2m);
+}
+
 }  // namespace
 
 struct mfwh_handle_s {
@@ -78,6 +119,7 @@ struct mfwh_handle_s {
   double inv_h2[3] = {0, 0, 0};
   double omega2[MFWH_MAX_NF] = {};
   double* f = nullptr;              // forcing [nf][P]
+  double* c2f = nullptr;            // c^2 per point [P] (MFWH_C_FIELD)
   bool use32 = false;               // wave solves in FP32 (the FP32 precisions)
   // CUDA-graph mode (mfwh_set_graphs): each variant of the wave solve is captured once on the
   // staging buffers g_in / g_out and replayed as one graph launch.
@@ -130,6 +172,7 @@ struct mfwh_handle_s {
   MgState* d_mgstate = nullptr;     // [N_t] per-step convergence state
   unsigned* d_bar = nullptr;        // grid barrier of the step kernel
   MgCounters* d_mgc = nullptr;      // multigrid statistics
+  double wait_s = 2.0;              // limit of one grid-barrier wait of the step kernel (s)
   std::vector<double> imp_fc;       // [(N_t + 1) * nf] dt^2 cos(omega~_m t^n) cos(omega~_m dt)
 };
 
@@ -154,9 +197,9 @@ mfwh_status collect_timing(mfwh_handle_t h) {
       CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
       if (h->d_bar) CK(cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), h->stream));
       CK(cudaStreamSynchronize(h->stream));
-      return fail(MFWH_ERR_CUDA, flag == 2
-                                     ? "implicit step kernel: a grid barrier wait timed out"
-                                     : "FP32 wave kernel: a tile's tensor copy did not complete");
+      return fail(MFWH_ERR_TIMEOUT,
+                  flag == 2 ? "implicit step kernel: a grid barrier wait timed out"
+                            : "FP32 wave kernel: a tile's tensor copy did not complete");
     }
   }
   double ms = 0.0;
@@ -299,6 +342,7 @@ mfwh_status apply_pi_implicit(mfwh_handle_t h, const double* vin, double* vout, 
   const int n_t = P.s.n_t;
   cudaStream_t st = h->stream;
   ImpArgs& A = *h->imp;
+  A.wait_ns = (unsigned long long)(h->wait_s * 1e9);
   CK(cudaMemsetAsync(h->d_mgstate, 0, sizeof(MgState) * n_t, st));
   ImpInit ini{};
   for (int m = 0; m < nf; ++m) {
@@ -373,6 +417,7 @@ mfwh_status apply_pi_direct(mfwh_handle_t h, const double* vin, double* vout, in
     const double a_cur = first ? 1.0 : 2.0;
     layer_coef(h, P.c2_lo, a_cur, kappa, &a.lo);
     layer_coef(h, P.c2_hi, a_cur, kappa, &a.hi);
+    a.a_cur = a_cur;
     a.first = first;
     for (int m = 0; m < nf; ++m) {
       a.fc[m] = kappa * P.cosf[(size_t)n * nf + m];
@@ -711,6 +756,7 @@ const char* mfwh_status_string(mfwh_status s) {
     case MFWH_ERR_NOT_CONVERGED: return "not converged";
     case MFWH_ERR_SPURIOUS: return "converged to a non-solution (Helmholtz residual check failed)";
     case MFWH_ERR_NONFINITE: return "non-finite values";
+    case MFWH_ERR_TIMEOUT: return "a bounded wait inside a kernel ran out";
   }
   return "unknown status";
 }
@@ -718,7 +764,7 @@ const char* mfwh_status_string(mfwh_status s) {
 mfwh_status mfwh_plan(const mfwh_problem* prob, mfwh_setup* out) {
   if (!out) return fail(MFWH_ERR_INVALID_ARG, "null output");
   Plan P;
-  mfwh_status st = plan_problem(prob, &P);
+  mfwh_status st = plan_with_field(prob, &P);
   if (st == MFWH_OK) *out = P.s;
   return st;
 }
@@ -727,7 +773,7 @@ mfwh_status mfwh_plan_multigrid(const mfwh_problem* prob, int* levels, int* coar
                                 int64_t cells[16][3]) {
   if (!levels || !coarse || !cells) return fail(MFWH_ERR_INVALID_ARG, "null output");
   Plan P;
-  mfwh_status st = plan_problem(prob, &P);
+  mfwh_status st = plan_with_field(prob, &P);
   if (st != MFWH_OK) return st;
   if (P.time_stepping != MFWH_TIME_IMPLICIT)
     return fail(MFWH_ERR_INVALID_ARG, "not an implicit-time-stepping problem");
@@ -765,7 +811,7 @@ mfwh_status mfwh_plan_multigrid(const mfwh_problem* prob, int* levels, int* coar
 mfwh_status mfwh_plan_weights(const mfwh_problem* prob, double* w_out, int64_t capacity) {
   if (!w_out) return fail(MFWH_ERR_INVALID_ARG, "null output");
   Plan P;
-  mfwh_status st = plan_problem(prob, &P);
+  mfwh_status st = plan_with_field(prob, &P);
   if (st != MFWH_OK) return st;
   if ((int64_t)P.w.size() > capacity) return fail(MFWH_ERR_INVALID_ARG, "w_out too small");
   std::memcpy(w_out, P.w.data(), sizeof(double) * P.w.size());
@@ -800,7 +846,7 @@ mfwh_status mfwh_create(const mfwh_problem* prob, void* stream, mfwh_handle_t* o
   *out = nullptr;
   auto* h = new (std::nothrow) mfwh_handle_s();
   if (!h) return fail(MFWH_ERR_NOMEM, "host allocation failed");
-  mfwh_status st = plan_problem(prob, &h->plan);
+  mfwh_status st = plan_with_field(prob, &h->plan);
   if (st != MFWH_OK) {
     delete h;
     return st;
@@ -1008,6 +1054,13 @@ mfwh_status mfwh_create(const mfwh_problem* prob, void* stream, mfwh_handle_t* o
   if (e == cudaSuccess) e = cudaMemsetAsync(h->f, 0, sizeof(double) * h->N, h->stream);
   if (e == cudaSuccess && prob->forcing)
     e = cudaMemcpyAsync(h->f, prob->forcing, sizeof(double) * h->N, cudaMemcpyDefault, h->stream);
+  if (e == cudaSuccess && P.c2_field) {
+    e = cudaMalloc(&h->c2f, sizeof(double) * h->P);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->c2f, prob->c2_field, sizeof(double) * h->P, cudaMemcpyDefault,
+                          h->stream);
+    h->geom.c2f = h->c2f;
+  }
   if (e == cudaSuccess && h->f32) {
     launch_to_float(h->f, h->f32, h->N, h->stream);
     e = cudaGetLastError();
@@ -1265,6 +1318,7 @@ void mfwh_destroy(mfwh_handle_t h) {
   for (double* b : bufs)
     if (b) cudaFree(b);
   if (h->d_err) cudaFree(h->d_err);
+  if (h->c2f) cudaFree(h->c2f);
   if (h->imp_mem) cudaFree(h->imp_mem);
   if (h->d_mgstate) cudaFree(h->d_mgstate);
   if (h->d_bar) cudaFree(h->d_bar);
@@ -1278,6 +1332,14 @@ void mfwh_destroy(mfwh_handle_t h) {
   for (auto& x : h->ev)
     if (x) cudaEventDestroy(x);
   delete h;
+}
+
+mfwh_status mfwh_set_wait_limit(mfwh_handle_t h, double seconds) {
+  if (!h) return fail(MFWH_ERR_INVALID_ARG, "null handle");
+  if (std::isnan(seconds) || seconds > 3600.0)
+    return fail(MFWH_ERR_INVALID_ARG, "wait limit must be at most 3600 s");
+  h->wait_s = seconds > 0.0 ? seconds : 2.0;
+  return MFWH_OK;
 }
 
 mfwh_status mfwh_mg_stats(mfwh_handle_t h, int64_t* solves, int64_t* cycles,
@@ -1382,7 +1444,7 @@ mfwh_status mfwh_autotune(const mfwh_problem* prob, void* stream, int* time_bloc
                           int* tile_shape, double* ms_per_step) {
   if (!prob || !time_block || !tile_shape) return fail(MFWH_ERR_INVALID_ARG, "null argument");
   Plan P;
-  mfwh_status st = plan_problem(prob, &P);
+  mfwh_status st = plan_with_field(prob, &P);
   if (st != MFWH_OK) return st;
   if (P.time_stepping == MFWH_TIME_IMPLICIT) {   // one step per launch; nothing to choose
     *time_block = 1;
@@ -1392,10 +1454,11 @@ mfwh_status mfwh_autotune(const mfwh_problem* prob, void* stream, int* time_bloc
   }
   int dev = 0;
   CK(cudaGetDevice(&dev));
-  using Key = std::tuple<int, int, int64_t, int64_t, int64_t, int, int>;
+  using Key = std::tuple<int, int, int64_t, int64_t, int64_t, int, int, int>;
   static std::mutex mu;
   static std::map<Key, std::tuple<int, int, double>> cache;
-  const Key key{dev, P.dim, P.n[0], P.n[1], P.dim == 3 ? P.n[2] : 0, P.s.nf, P.precision};
+  const Key key{dev, P.dim, P.n[0], P.n[1], P.dim == 3 ? P.n[2] : 0, P.s.nf, P.precision,
+                P.c2_field ? 1 : 0};
   {
     std::lock_guard<std::mutex> lk(mu);
     auto it = cache.find(key);
@@ -1407,7 +1470,7 @@ mfwh_status mfwh_autotune(const mfwh_problem* prob, void* stream, int* time_bloc
     }
   }
   std::vector<std::pair<int, int>> cand;
-  if (P.order == 4 || (P.dim == 3 && P.precision == MFWH_PREC_FP64)) {
+  if (P.order == 4 || P.c2_field || (P.dim == 3 && P.precision == MFWH_PREC_FP64)) {
     cand = {{1, 0}};
   } else if (P.dim == 3) {
     cand = {{1, 0}, {2, 0}, {4, 0}};

@@ -25,11 +25,14 @@
 //
 // One step is one launch.  When the hierarchy has grid-wide levels the launch is
 // cooperative (all blocks resident) and phases are separated by a grid barrier whose waits
-// are bounded in time (2 s): a wait that runs out sets *err = 2 and makes every later
-// barrier of the launch pass through, so the launch ends and the host reports the error.
-// The convergence test max|rhs - A Z| <= tol max|rhs| is evaluated once per cycle from a
-// grid-wide atomicMax, read by all blocks after a barrier, so that every block takes the same
-// decision.
+// are bounded in time (ImpArgs::wait_ns, 2 s by default): a wait that runs out sets *err = 2
+// and makes every later barrier of the launch pass through, so the launch ends and the host
+// reports the error.  The convergence test max|rhs - A Z| <= tol max|rhs| is evaluated once
+// per cycle from a grid-wide atomicMax, read after a barrier; one thread per block reads it
+// and shares it through shared memory, so the threads of a block always take the same branch
+// (also after a timed-out barrier, when blocks may read the maximum at different moments).
+// No index depends on data, and every loop has a bound, so a launch whose barriers pass
+// through still ends after its usual number of phases with all accesses in bounds.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -48,8 +51,8 @@ __device__ __forceinline__ uint64_t global_ns() {
 
 __device__ __forceinline__ double nanmax(double a, double b) { return (b > a || b != b) ? b : a; }
 
-// Grid barrier for a cooperative launch.  Bounded wait; see the file comment.
-__device__ void grid_sync(unsigned* bar, int* err) {
+// Grid barrier for a cooperative launch.  Bounded wait (wait_ns); see the file comment.
+__device__ void grid_sync(unsigned* bar, int* err, unsigned long long wait_ns) {
   __syncthreads();
   if (threadIdx.x == 0 && *(volatile int*)err == 0) {
     volatile unsigned* gen = bar + 1;
@@ -65,7 +68,7 @@ __device__ void grid_sync(unsigned* bar, int* err) {
       while (*gen == g0) {
         __nanosleep(32);
         if (*(volatile int*)err != 0) break;
-        if (global_ns() - t0 > 2000000000ull) {
+        if (global_ns() - t0 > wait_ns) {
           atomicExch(err, 2);
           break;
         }
@@ -99,6 +102,16 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* slot, doub
 }
 __device__ __forceinline__ double load_nonneg(const unsigned long long* slot) {
   return __longlong_as_double((long long)*(const volatile unsigned long long*)slot);
+}
+
+// Convergence test of cycle c taken once per block: thread 0 reads the grid-wide maximum and
+// shares the decision, so that all threads of the block branch alike.  flag: shared int.
+__device__ bool block_converged(const MgState* st, int c, double thresh, int* flag) {
+  if (threadIdx.x == 0) *flag = load_nonneg(&st->rmax[c]) <= thresh ? 1 : 0;
+  __syncthreads();
+  const bool r = *flag != 0;
+  __syncthreads();
+  return r;
 }
 
 // Coefficients of a level in the arithmetic type R.
@@ -644,7 +657,11 @@ template <int DIM>
 __global__ void __launch_bounds__(kMgThreads, 2) k_imp_step(const ImpArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double red[32];
-  if (*(volatile int*)a.err != 0) return;
+  __shared__ int s_flag;
+  // A barrier of an earlier step timed out: return (the same decision for the whole block).
+  if (threadIdx.x == 0) s_flag = *(volatile int*)a.err;
+  __syncthreads();
+  if (s_flag != 0) return;
   const int axis = a.layer_axis;
   const MgLevel& L0 = a.lev[0];
   const double bmax = load_nonneg(&a.st->bmax);
@@ -657,12 +674,12 @@ __global__ void __launch_bounds__(kMgThreads, 2) k_imp_step(const ImpArgs a) {
       const double m = down0_tiles(L0, a.lev[1], axis, smraw);
       const double bm = block_max(m, red);
       if (threadIdx.x == 0) atomic_max_nonneg(&a.st->rmax[c], bm);
-      grid_sync(a.bar, a.err);
-      if (load_nonneg(&a.st->rmax[c]) <= thresh) { converged = true; break; }
+      grid_sync(a.bar, a.err, a.wait_ns);
+      if (block_converged(a.st, c, thresh, &s_flag)) { converged = true; break; }
       if (c == a.max_cycles) break;
       for (int l = 1; l < a.lc; ++l) {
         down_tiles(a.lev[l], a.lev[l + 1], axis, smraw);
-        grid_sync(a.bar, a.err);
+        grid_sync(a.bar, a.err, a.wait_ns);
       }
       if (blockIdx.x == 0) {
         float* sm = reinterpret_cast<float*>(smraw);
@@ -670,10 +687,10 @@ __global__ void __launch_bounds__(kMgThreads, 2) k_imp_step(const ImpArgs a) {
         cta_vcycle<DIM, float>(a, sm, a.lc, false);
         cta_store<float>(a, sm);
       }
-      grid_sync(a.bar, a.err);
+      grid_sync(a.bar, a.err, a.wait_ns);
       for (int l = a.lc - 1; l >= 0; --l) {
         up_tiles(a.lev[l], a.lev[l + 1], a.lev[l + 1].u32, l == 0, a.omega_dc, axis, smraw);
-        grid_sync(a.bar, a.err);
+        grid_sync(a.bar, a.err, a.wait_ns);
       }
     }
   } else if (a.lc == 0) {
@@ -699,22 +716,22 @@ __global__ void __launch_bounds__(kMgThreads, 2) k_imp_step(const ImpArgs a) {
       const double rm = residual_to32<DIM>(L0, axis, g0, gs);
       const double bm = block_max(rm, red);
       if (threadIdx.x == 0) atomic_max_nonneg(&a.st->rmax[c], bm);
-      grid_sync(a.bar, a.err);
-      if (load_nonneg(&a.st->rmax[c]) <= thresh) { converged = true; break; }
+      grid_sync(a.bar, a.err, a.wait_ns);
+      if (block_converged(a.st, c, thresh, &s_flag)) { converged = true; break; }
       if (c == a.max_cycles) break;
       for (int l = 0; l < a.lc; ++l) {
         const MgLevel& L = a.lev[l];
         for (int s = 0; s < a.nu1; ++s) {
           rb_half<DIM, float>(L, L.u32, L.f32, 0, axis, g0, gs);
-          grid_sync(a.bar, a.err);
+          grid_sync(a.bar, a.err, a.wait_ns);
           rb_half<DIM, float>(L, L.u32, L.f32, 1, axis, g0, gs);
-          grid_sync(a.bar, a.err);
+          grid_sync(a.bar, a.err, a.wait_ns);
         }
         residual_store<DIM, float>(L, L.u32, L.f32, L.v32, axis, g0, gs);
-        grid_sync(a.bar, a.err);
+        grid_sync(a.bar, a.err, a.wait_ns);
         const MgLevel& C = a.lev[l + 1];
         restrict_pass<DIM, float>(L, L.v32, nullptr, nullptr, C, C.f32, C.u32, axis, g0, gs);
-        grid_sync(a.bar, a.err);
+        grid_sync(a.bar, a.err, a.wait_ns);
       }
       if (blockIdx.x == 0) {
         float* sm = reinterpret_cast<float*>(smraw);
@@ -722,20 +739,20 @@ __global__ void __launch_bounds__(kMgThreads, 2) k_imp_step(const ImpArgs a) {
         cta_vcycle<DIM, float>(a, sm, a.lc, false);
         cta_store<float>(a, sm);
       }
-      grid_sync(a.bar, a.err);
+      grid_sync(a.bar, a.err, a.wait_ns);
       for (int l = a.lc - 1; l >= 0; --l) {
         const MgLevel& L = a.lev[l];
         prolong_pass<DIM, float>(a.lev[l + 1], a.lev[l + 1].u32, L, L.u32, g0, gs);
-        grid_sync(a.bar, a.err);
+        grid_sync(a.bar, a.err, a.wait_ns);
         for (int s = 0; s < a.nu2; ++s) {
           rb_half<DIM, float>(L, L.u32, L.f32, 0, axis, g0, gs);
-          grid_sync(a.bar, a.err);
+          grid_sync(a.bar, a.err, a.wait_ns);
           rb_half<DIM, float>(L, L.u32, L.f32, 1, axis, g0, gs);
-          grid_sync(a.bar, a.err);
+          grid_sync(a.bar, a.err, a.wait_ns);
         }
       }
       add_correction<DIM>(L0, a.omega_dc, g0, gs);
-      grid_sync(a.bar, a.err);
+      grid_sync(a.bar, a.err, a.wait_ns);
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {

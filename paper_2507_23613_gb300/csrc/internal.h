@@ -19,6 +19,7 @@ struct Plan {
   double c_max = 0.0;
   double c2_lo = 0.0, c2_hi = 0.0;   // c^2 on each side of the layer interface
   int64_t layer_split = 0;           // first grid index along layer_axis in the upper layer
+  bool c2_field = false;             // MFWH_C_FIELD: c^2 per point (c2_lo = c2_hi = 1 then)
   int layer_axis = 0;
   int dim = 2;
   int time_block = 1;          // steps per wave-kernel launch (1, 4, 8 or 16)
@@ -34,7 +35,9 @@ struct Plan {
   std::vector<double> cosf;    // [(n_t + 1) * nf]  cos(omega~_m t^n)
 };
 
-mfwh_status plan_problem(const mfwh_problem* prob, Plan* out);
+// c2_field_max: the largest value of prob->c2_field (MFWH_C_FIELD only; the caller reads the
+// field, which may be device memory, and checks that all values are finite and > 0).
+mfwh_status plan_problem(const mfwh_problem* prob, Plan* out, double c2_field_max = 0.0);
 
 // Discrete Algorithm 2 (see mfwh_opt_parameters).
 mfwh_status optimise_parameters(int nf, const double* omega, int n_p, int n_t, int n_delta,

@@ -21,6 +21,8 @@ struct Geom {
   int order;                 // order of L_{ph}: 2 or 4 (0 reads as 2)
   int64_t syw, szw;          // strides of j and k in the FP32 wave-level arrays W and D (2D
                              // FP32 handles pad rows to 32 floats for tensor copies; else sy, sz)
+  const double* c2f;         // c^2 per point [points] (MFWH_C_FIELD), else null; with a field
+                             // the layer coefficients are those of c = 1 (lower layer only)
 };
 
 // Leapfrog update at one point, written as
@@ -39,6 +41,9 @@ struct LayerCoef {
 
 struct StepHost {
   LayerCoef lo, hi;                 // coefficients below / above the layer split
+  double a_cur;                     // 2 (regular step) or 1 (first step): with a c^2 field the
+                                    // update is a_cur W^n - a_prev W^{n-1} + c_j^2 (L - a_cur W^n),
+                                    // L the sum over lo's terms (coefficients of c = 1)
   int first;                        // 1 on the first step: no W^{n-1} term
   int forced;                       // 0: homogeneous map S (no forcing)
   double fc[MFWH_MAX_NF];           // kappa cos(omega~_m t^n)
@@ -139,6 +144,8 @@ void launch_residual(int nf, const Geom& g, const double* v, const double* f, co
                      double c2_lo, double c2_hi, const double* inv_h2, double* partial, double* out,
                      cudaStream_t st);
 int64_t residual_partial_size(int nf);
+// Blocks of the residual kernel: residual_partial_size(nf) = kResidualBlocks * 2 * nf.
+constexpr int kResidualBlocks = 4 * 152;
 // Defect field R_m = f_m - (c^2 Delta_h + omega_m^2) v_m (0 on the boundary), [nf][points].
 void launch_residual_field(int nf, const Geom& g, const double* v, const double* f,
                            const double* omega2, double c2_lo, double c2_hi, const double* inv_h2,
@@ -217,6 +224,7 @@ struct ImpArgs {
   MgCounters* counters;
   unsigned* bar;              // grid barrier: [0] arrivals, [1] generation
   int* err;                   // set to 2 when a barrier wait times out
+  unsigned long long wait_ns; // limit of one barrier wait in nanoseconds
   double* Wp;                 // in: W^{n-1}, out: W^{n+1}
   const double* Wc;           // W^n (start of the next solve: 2 W^{n+1} + Z - 2 W^n)
   double* q;                  // filter sums [nf][points]

@@ -21,6 +21,9 @@ namespace {
 // Per-block partial maxima of the residual kernel followed by its reduced output.
 // Every GPU that loads the library holds this array until the process exits.
 static __device__ __align__(256) double g_residual_scratch[MFWH_NOALLOC_SCRATCH_DOUBLES];
+static_assert((int64_t)mfwh::kResidualBlocks * 2 * MFWH_MAX_NF + 2 * MFWH_MAX_NF <=
+                  MFWH_NOALLOC_SCRATCH_DOUBLES,
+              "the residual's partial maxima and output must fit the scratch array");
 
 constexpr int kMaxDevices = 128;
 std::mutex g_scratch_mu;
@@ -50,13 +53,16 @@ mfwh_status scratch_address(int device, double** out) {
   return MFWH_OK;
 }
 
-bool on_device(const void* p) {
+// True if p is managed memory or device memory of `device` (the current device): a
+// buffer on another GPU would be read through a peer mapping that may not exist.
+bool on_device(const void* p, int device) {
   cudaPointerAttributes attr;
   if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+  if (attr.type == cudaMemoryTypeManaged) return true;
+  return attr.type == cudaMemoryTypeDevice && attr.device == device;
 }
 
 mfwh_status bad(const char* msg) {
@@ -72,6 +78,12 @@ extern "C" mfwh_status mfwh_residual_noalloc(const mfwh_problem* p, const double
   if (p->dim != 2 && p->dim != 3) return bad("mfwh_residual_noalloc: dim must be 2 or 3");
   if (p->nf < 1 || p->nf > MFWH_MAX_NF || !p->omega)
     return bad("mfwh_residual_noalloc: nf must be in 1..16 with omega given");
+  for (int m = 0; m < p->nf; ++m)
+    if (!(std::isfinite(p->omega[m]) && p->omega[m] > 0.0))
+      return bad("mfwh_residual_noalloc: every omega must be finite and > 0");
+  if (p->order != 0 && p->order != 2 && p->order != 4)
+    return bad("mfwh_residual_noalloc: order must be 2 or 4 (0 means 2)");
+  // Guard: for nf <= MFWH_MAX_NF the static_assert above keeps the need within the array.
   const int64_t need = mfwh::residual_partial_size(p->nf) + 2 * p->nf;
   if (need > MFWH_NOALLOC_SCRATCH_DOUBLES) {
     std::ostringstream os;
@@ -84,7 +96,8 @@ extern "C" mfwh_status mfwh_residual_noalloc(const mfwh_problem* p, const double
   double inv_h2[3] = {0.0, 0.0, 0.0};
   int64_t n[3] = {0, 0, 0};
   for (int a = 0; a < p->dim; ++a) {
-    if (p->n[a] < 2 || p->n[a] > (1 << 20) || !(p->length[a] > 0.0))
+    if (p->n[a] < 2 || p->n[a] > (1 << 20) || !(p->length[a] > 0.0) ||
+        !std::isfinite(p->length[a]))
       return bad("mfwh_residual_noalloc: bad grid size or length");
     n[a] = p->n[a];
     const double h = p->length[a] / (double)p->n[a];
@@ -98,12 +111,18 @@ extern "C" mfwh_status mfwh_residual_noalloc(const mfwh_problem* p, const double
   g.points = g.sz * (p->dim == 3 ? g.nz + 1 : 1);
   g.dim = p->dim;
   g.order = p->order == 4 ? 4 : 2;
-  if (!(p->c_lo > 0.0)) return bad("mfwh_residual_noalloc: c_lo must be > 0");
-  double c2_lo = p->c_lo * p->c_lo, c2_hi = c2_lo;
+  const bool field = p->c_mode == MFWH_C_FIELD;
+  if (!field && (!(p->c_lo > 0.0) || !std::isfinite(p->c_lo)))
+    return bad("mfwh_residual_noalloc: c_lo must be finite and > 0");
+  double c2_lo = field ? 1.0 : p->c_lo * p->c_lo, c2_hi = c2_lo;
   g.layer_axis = 0;
   g.layer_split = g.nx + 1;
-  if (p->c_mode == MFWH_C_TWO_LAYER) {
-    if (!(p->c_hi > 0.0) || p->layer_axis < 0 || p->layer_axis >= p->dim)
+  if (field) {
+    if (!p->c2_field) return bad("mfwh_residual_noalloc: c2_field is NULL");
+    g.c2f = p->c2_field;   // checked below: device memory of the current device
+  } else if (p->c_mode == MFWH_C_TWO_LAYER) {
+    if (!(p->c_hi > 0.0) || !std::isfinite(p->c_hi) || p->layer_axis < 0 ||
+        p->layer_axis >= p->dim)
       return bad("mfwh_residual_noalloc: bad two-layer description");
     c2_hi = p->c_hi * p->c_hi;
     g.layer_axis = p->layer_axis;
@@ -120,15 +139,16 @@ extern "C" mfwh_status mfwh_residual_noalloc(const mfwh_problem* p, const double
   }
   double omega2[MFWH_MAX_NF];
   for (int m = 0; m < p->nf; ++m) omega2[m] = p->omega[m] * p->omega[m];
-  if (!on_device(forcing) || !on_device(v))
-    return bad("mfwh_residual_noalloc: forcing and v must be device pointers");
-
   int device = 0;
   cudaError_t e = cudaGetDevice(&device);
   if (e != cudaSuccess) {
     mfwh::set_error(std::string("mfwh_residual_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
     return MFWH_ERR_CUDA;
   }
+  if (!on_device(forcing, device) || !on_device(v, device) ||
+      (field && !on_device(p->c2_field, device)))
+    return bad("mfwh_residual_noalloc: forcing, v (and c2_field) must be device (or managed) "
+               "memory of the current device");
   double* scratch = nullptr;
   mfwh_status st = scratch_address(device, &scratch);
   if (st != MFWH_OK) return st;

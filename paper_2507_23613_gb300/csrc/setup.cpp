@@ -270,7 +270,7 @@ static mfwh_status fail(mfwh_status st, const std::string& msg) {
   return st;
 }
 
-mfwh_status plan_problem(const mfwh_problem* p, Plan* out) {
+mfwh_status plan_problem(const mfwh_problem* p, Plan* out, double c2_field_max) {
   if (!p || !out) return fail(MFWH_ERR_INVALID_ARG, "null problem or output");
   if (p->dim != 2 && p->dim != 3) return fail(MFWH_ERR_INVALID_ARG, "dim must be 2 or 3");
   if (p->nf < 1 || p->nf > MFWH_MAX_NF) return fail(MFWH_ERR_INVALID_ARG, "nf out of range 1..16");
@@ -289,8 +289,22 @@ mfwh_status plan_problem(const mfwh_problem* p, Plan* out) {
   }
   if (p->n_p < 1) return fail(MFWH_ERR_INVALID_ARG, "n_p must be >= 1");
   if (!(p->cfl > 0.0 && p->cfl <= 1.0)) return fail(MFWH_ERR_INVALID_ARG, "cfl must be in (0, 1]");
-  if (!(p->c_lo > 0.0)) return fail(MFWH_ERR_INVALID_ARG, "c_lo must be > 0");
-  if (p->c_mode == MFWH_C_TWO_LAYER) {
+  const bool field = p->c_mode == MFWH_C_FIELD;
+  if (field) {
+    if (!p->c2_field) return fail(MFWH_ERR_INVALID_ARG, "c2_field is NULL");
+    if (!(c2_field_max > 0.0) || !std::isfinite(c2_field_max))
+      return fail(MFWH_ERR_INVALID_ARG, "c2_field values must be finite and > 0");
+  } else if (!(p->c_lo > 0.0)) {
+    return fail(MFWH_ERR_INVALID_ARG, "c_lo must be > 0");
+  }
+  if (field) {
+    if (p->precision != MFWH_PREC_FP64)
+      return fail(MFWH_ERR_INVALID_ARG, "a c^2 field runs with the FP64 precision only");
+    if (p->time_stepping != MFWH_TIME_EXPLICIT)
+      return fail(MFWH_ERR_INVALID_ARG, "a c^2 field runs with explicit time stepping only");
+    if (p->time_block > 1)
+      return fail(MFWH_ERR_INVALID_ARG, "a c^2 field takes one step per launch");
+  } else if (p->c_mode == MFWH_C_TWO_LAYER) {
     if (!(p->c_hi > 0.0)) return fail(MFWH_ERR_INVALID_ARG, "c_hi must be > 0");
     if (p->layer_axis < 0 || p->layer_axis >= p->dim)
       return fail(MFWH_ERR_INVALID_ARG, "layer_axis out of range");
@@ -388,6 +402,11 @@ mfwh_status plan_problem(const mfwh_problem* p, Plan* out) {
     for (int64_t j = 0; j <= na; ++j)
       if (!((double)j * ha < p->interface)) { split = j; break; }
     P.layer_split = split;
+  } else if (field) {
+    // the kernels take c^2 from the field; the layer coefficients are those of c = 1
+    P.c2_field = true;
+    P.c_max = std::sqrt(c2_field_max);
+    P.c2_lo = P.c2_hi = 1.0;
   }
 
   int n_t = 0;

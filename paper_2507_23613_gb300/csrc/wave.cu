@@ -26,6 +26,7 @@ constexpr int kBX = 32, kBY = 8;
 template <int NF>
 struct StepParams {
   LayerCoef lo, hi;
+  double acur;
   double fneg[NF];   // kappa cos(omega~_m t^n)
   double wq[NF];
   float wq_hi[NF], wq_lo[NF];   // w_{n+1,m} as a float pair
@@ -51,6 +52,7 @@ StepParams<NF> to_params(const StepHost& a) {
   StepParams<NF> p;
   p.lo = a.lo;
   p.hi = a.hi;
+  p.acur = a.a_cur;
   for (int m = 0; m < NF; ++m) {
     p.fneg[m] = a.fc[m];
     p.wq[m] = a.wq[m];
@@ -82,7 +84,9 @@ __device__ __forceinline__ PointIndex point_index(const Geom& g) {
 
 // New wave level at an interior point (the leapfrog update with the composite forcing).
 // ORDER 4 adds the second neighbours along each axis; beyond the boundary the ghost value is
-// minus the centre point (odd reflection of homogeneous Dirichlet data).
+// minus the centre point (odd reflection of homogeneous Dirichlet data).  With a c^2 field
+// (g.c2f) the coefficients are those of c = 1 and the operator's terms are scaled by c_j^2:
+// W^{n+1} = a_cur W^n - W^{n-1} + c_j^2 (A0 W^n + Ax sx + ... - a_cur W^n).
 template <int NF, int DIM, int ORDER>
 __device__ __forceinline__ double leapfrog_point(const double* __restrict__ Wc,
                                                  const double* __restrict__ Wp,
@@ -98,7 +102,8 @@ __device__ __forceinline__ double leapfrog_point(const double* __restrict__ Wc,
   const double wc = Wc[p];
   const double sx = Wc[p - 1] + Wc[p + 1];
   const double sy = Wc[p - g.sy] + Wc[p + g.sy];
-  double acc = a.first ? A0 * wc : fma(A0, wc, -Wp[p]);
+  const bool field = g.c2f != nullptr;
+  double acc = field ? (A0 - a.acur) * wc : (a.first ? A0 * wc : fma(A0, wc, -Wp[p]));
   acc = fma(Ax, sx, acc);
   acc = fma(Ay, sy, acc);
   if (DIM == 3) {
@@ -119,6 +124,7 @@ __device__ __forceinline__ double leapfrog_point(const double* __restrict__ Wc,
       acc = fma(Bz, tz, acc);
     }
   }
+  if (field) acc = fma(g.c2f[p], acc, a.first ? a.acur * wc : fma(a.acur, wc, -Wp[p]));
   if (a.forced) {
 #pragma unroll
     for (int m = 0; m < NF; ++m) acc = fma(-a.fneg[m], f[m * g.points + p], acc);
@@ -197,7 +203,7 @@ k_last(const double* __restrict__ Wc, const double* __restrict__ Wp, const doubl
 
 // ---- Helmholtz residual -------------------------------------------------------
 
-constexpr int kResBlocks = 4 * 152;
+constexpr int kResBlocks = kResidualBlocks;
 
 __device__ __forceinline__ double nanmax(double a, double b) {
   // max that propagates NaN so that non-finite iterates are reported
@@ -237,7 +243,7 @@ k_residual(const double* __restrict__ v, const double* __restrict__ f, const Res
     if (i == 0 || i == g.nx || j == 0 || j == g.ny) continue;
     if (DIM == 3 && (k == 0 || k == g.nz)) continue;
     const int64_t li = g.layer_axis == 0 ? i : (g.layer_axis == 1 ? j : k);
-    const double c2 = li >= g.layer_split ? a.c2_hi : a.c2_lo;
+    const double c2 = g.c2f ? g.c2f[p] : (li >= g.layer_split ? a.c2_hi : a.c2_lo);
 #pragma unroll
     for (int m = 0; m < NF; ++m) {
       const double* vm = v + m * g.points;
@@ -366,8 +372,8 @@ k_residual_field(const double* __restrict__ v, const double* __restrict__ f,
     return;
   }
   const int64_t li = g.layer_axis == 0 ? x.i : (g.layer_axis == 1 ? x.j : x.k);
-  const double c2 = li >= g.layer_split ? a.c2_hi : a.c2_lo;
   const int64_t p = x.p;
+  const double c2 = g.c2f ? g.c2f[p] : (li >= g.layer_split ? a.c2_hi : a.c2_lo);
 #pragma unroll
   for (int m = 0; m < NF; ++m) {
     const double* vm = v + m * g.points;

@@ -400,8 +400,10 @@ k_tb2d32(const float* __restrict__ W_in, const float* __restrict__ D_in,
       for (int e = tid; e < E; e += NT) Dv[e] = 0.0f;
     const bool ok = mbar_wait(bar, 0, 1 << 22);
     if (__syncthreads_or(!ok)) {
-      // The copies did not complete within the bound: report it, give them one more bounded
-      // wait so that none lands in shared memory after the CTA is gone, and stop.
+      // The copies did not complete within the bound: report it (the host fails the call with
+      // MFWH_ERR_TIMEOUT), give them one more bounded wait to land while the CTA still owns its
+      // shared memory, and stop.  If that wait runs out too the CTA stops all the same: every
+      // wait in this kernel must end.
       if (tid == 0) atomicExch(a.err, 1);
       mbar_wait(bar, 0, 1 << 22);
       return;

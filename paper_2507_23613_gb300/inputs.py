@@ -108,6 +108,15 @@ def two_layer_c2(n, length, c_lo, c_hi, z_interface):
     return np.where(z < z_interface, c_lo * c_lo, c_hi * c_hi)
 
 
+def random_c2(n, seed, c_lo=1.0, c_hi=1.5):
+    """Seeded c^2 field on the grid of n cells per axis: c drawn uniformly in [c_lo, c_hi]
+    independently at every grid point (a rough medium for the MFWH_C_FIELD mode)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    shape = tuple(k + 1 for k in reversed(n))
+    c = rng.uniform(c_lo, c_hi, size=shape)
+    return c * c
+
+
 def cube_layered(seed=3000, n=256, nf=4):
     """257^3 unit cube, c = 1.0 / 1.5 split at z = 0.5, N_f = 4 in [8, 30], Gaussians b = 300, CFL 0.5."""
     dims = (n, n, n)

@@ -249,3 +249,29 @@ def test_implicit_rejects_grids_without_a_small_level():
     with pytest.raises(_lib.MfwhError) as err:
         M.Solver((101, 100), (1.0, 1.0), [5.0, 9.0], time_stepping="implicit")
     assert err.value.status == _lib.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("name", ["grid_2d", "cube3d_two_layer"])
+def test_barrier_timeout_is_reported_and_handle_recovers(name):
+    """Failure detection without a fault.  With a barrier wait limit of 1 ns a wait of the
+    step kernel's grid barrier runs out: the kernel records it, lets its blocks through the
+    remaining barriers (every loop bounded, every index geometric), the later step launches
+    return at once, and the solve reports MFWH_ERR_TIMEOUT.  With the default limit restored
+    the same handle's map matches the oracle again."""
+    s, p, wl = pair(name)
+    v = random_v(wl, 9)
+    s.set_wait_limit(1e-9)
+    x = dev(v)
+    with pytest.raises(_lib.MfwhError) as e:
+        s.solve_fpi(x, 1)
+    assert e.value.status == _lib.ERR_TIMEOUT
+    assert "timed out" in str(e.value)
+    s.set_wait_limit(0.0)                 # back to the default (2 s)
+    got = apply(s, v, True)
+    s.last_timing()                       # no flag left set: the call succeeds
+    want = W.apply_Pi(p, v, forced=True)
+    assert np.all(rel_err(got, want) < TOL), rel_err(got, want)
+    with pytest.raises(_lib.MfwhError) as e:
+        s.set_wait_limit(float("nan"))
+    assert e.value.status == _lib.ERR_INVALID_ARG
+    s.close()

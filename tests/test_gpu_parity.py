@@ -415,3 +415,63 @@ def test_full_size_gmres_cycle_residual_is_true_residual():
     assert abs(true_res - info["rel_residual"]) <= 1e-6 * info["rel_residual"] + 1e-13 + bound, \
         (true_res, info["rel_residual"], bound)
     assert np.all(np.isfinite(info["helmholtz_residual"]))
+
+
+# ---------------------------------------------------------------------------
+# c^2 given per grid point (MFWH_C_FIELD): L = c^2 Delta, non-divergence form
+# ---------------------------------------------------------------------------
+
+def _field_pair(wl, c2, mode=1, order=2):
+    solver = M.Solver(wl.n, wl.length, wl.omega, dev(wl.forcing), n_p=wl.n_p, cfl=wl.cfl,
+                      filter_mode=mode, order=order, c2_field=dev(c2))
+    fm = {0: F.FILTER_OPTIMIZED, 1: F.FILTER_TRADITIONAL}[mode]
+    prob = W.make_problem(W.Grid(wl.n, wl.length), wl.omega, wl.forcing, c2=c2, cfl=wl.cfl,
+                          n_p=wl.n_p, filter_mode=fm, order=order)
+    assert solver.setup["n_t"] == prob.setup.n_t
+    return solver, prob
+
+
+@pytest.mark.parametrize("dims,order", [((20, 18, 16), 2), ((40, 33), 2), ((40, 33), 4),
+                                        ((22, 19, 17), 4)])
+def test_pi_random_c2_field(dims, order):
+    """c drawn uniformly in [1, 1.5] at every point (2D and 3D, second and fourth order),
+    forced and homogeneous maps element by element against the oracle."""
+    om = [8.3, 12.1, 19.0] if len(dims) == 3 else [6.1, 9.7, 15.2]
+    wl = inputs.gaussian_workload("field", dims, 3, om, 300.0, 23)
+    c2 = inputs.random_c2(dims, 24, 1.0, 1.5)
+    for mode in (1, 0):
+        solver, prob = _field_pair(wl, c2, mode=mode, order=order)
+        check_pi(solver, prob, random_v(wl, 25), forced=True)
+        check_pi(solver, prob, random_v(wl, 26), forced=False)
+        solver.close()
+
+
+def test_field_of_two_layers_matches_two_layer_mode():
+    """A field holding the two-layer medium gives the two-layer handle's map (different
+    rounding order of the same operator), and its residual matches the oracle's."""
+    wl = inputs.gaussian_workload("cube", (20, 18, 16), 4, [8.3, 12.1, 19.0, 27.5], 300.0, 21)
+    c2 = inputs.two_layer_c2(wl.n, wl.length, 1.0, 1.5, 0.5)
+    sf, prob = _field_pair(wl, c2, mode=0)
+    sl, _ = make_pair(wl, c_hi=1.5)
+    v = dev(random_v(wl, 27))
+    a = torch.empty_like(v)
+    b = torch.empty_like(v)
+    sf.apply_Pi(v, a, forced=True)
+    sl.apply_Pi(v, b, forced=True)
+    torch.cuda.synchronize()
+    assert np.all(rel_err(a.cpu().numpy(), b.cpu().numpy().reshape(a.shape)) <= 1e-12)
+    r = random_v(wl, 28)
+    np.testing.assert_allclose(sf.residual(dev(r)), W.helmholtz_residual(prob, r), rtol=1e-9)
+    np.testing.assert_allclose(sf.residual(dev(r)), sl.residual(dev(r)), rtol=1e-12)
+
+
+def test_gmres_with_c2_field_reaches_discrete_helmholtz():
+    """GMRES on a random medium converges to the sparse direct solution of
+    (c_j^2 Delta_h + omega^2) U = f."""
+    wl = inputs.gaussian_workload("fieldg", (30, 26), 3, [6.1, 9.7, 15.2], 200.0, 29)
+    c2 = inputs.random_c2(wl.n, 30, 1.0, 1.5)
+    solver, prob = _field_pair(wl, c2, mode=0)
+    v = np.zeros_like(wl.forcing)
+    info = solver.solve_gmres(v, restart=100, tol=1e-12, max_iters=600, spurious_tol=1e-8)
+    U = W.helmholtz_direct(prob)
+    assert np.all(rel_err(v, U) <= 1e-9), (rel_err(v, U), info["iterations"])

@@ -76,3 +76,11 @@ def test_printed_three_frequency_problem():
         assert abs(wl.forcing[m].max() - amp) < 1e-12
     cube = inputs.paper_three_frequency_cube(20)
     assert np.allclose(_peak_centre(cube, 0), (0.6, 0.45, 0.5), atol=1e-12)
+
+
+def test_random_c2_field_is_seeded_and_in_range():
+    a = inputs.random_c2((6, 5, 4), 3, 1.0, 1.5)
+    b = inputs.random_c2((6, 5, 4), 3, 1.0, 1.5)
+    assert a.shape == (5, 6, 7) and np.array_equal(a, b)
+    assert a.min() >= 1.0 and a.max() <= 2.25
+    assert not np.array_equal(a, inputs.random_c2((6, 5, 4), 4, 1.0, 1.5))

@@ -14,6 +14,7 @@ import pytest
 import paper_2507_23613_gb300 as M
 from paper_2507_23613_gb300 import _lib, build, inputs
 from oracle import filters as F
+from oracle import wave as W
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "mfwh.h")
@@ -303,8 +304,8 @@ def test_status_strings_and_thread_local_error_message():
     """Every status has a name; the message of a failed call is kept per thread."""
     import threading
     lib = _lib.load()
-    names = {lib.mfwh_status_string(k).decode() for k in range(8)}
-    assert len(names) == 8 and "ok" in names
+    names = {lib.mfwh_status_string(k).decode() for k in range(9)}
+    assert len(names) == 9 and "ok" in names and "unknown status" not in names
     assert lib.mfwh_status_string(99).decode() == "unknown status"
     prob, keep = M.make_problem((64, 64), (1.0, 1.0), [9.3, 5.5])   # not increasing
     with pytest.raises(_lib.MfwhError) as e:
@@ -322,3 +323,43 @@ def test_status_strings_and_thread_local_error_message():
     t.join()
     assert "increasing" not in seen[0]
     assert "increasing" in lib.mfwh_last_error().decode()   # this thread's message survives
+
+
+def test_plan_with_c2_field_matches_oracle():
+    """MFWH_C_FIELD: the time step follows c_max^2 = the field's largest value, as in the
+    oracle (which takes c_max from the same array); a field equal to the two-layer medium
+    plans like the two-layer problem."""
+    n, length = (24, 20, 16), (1.0, 1.1, 0.9)
+    om = [8.3, 12.1, 19.0, 27.5]
+    c2 = inputs.random_c2(n, 11, 1.0, 1.5)
+    prob, keep = M.make_problem(n, length, om, c2_field=c2)
+    s = M.setup_arrays(M.plan(prob))
+    o = W.make_problem(W.Grid(n, length), om, np.zeros((4,) + c2.shape), c2=c2).setup
+    assert s["n_t"] == o.n_t and abs(s["dt"] - o.dt) <= 1e-15 * o.dt
+    layer = inputs.two_layer_c2(n, length, 1.0, 1.5, 0.5)
+    pf, keep = M.make_problem(n, length, om, c2_field=layer)
+    pl, keep2 = M.make_problem(n, length, om, c_lo=1.0, c_hi=1.5, interface=0.5, layer_axis=2)
+    a, b = M.setup_arrays(M.plan(pf)), M.setup_arrays(M.plan(pl))
+    assert a["n_t"] == b["n_t"] and a["dt"] == b["dt"]
+    np.testing.assert_array_equal(a["B"], b["B"])
+
+
+@pytest.mark.parametrize("bad", ["negative", "nan", "fp32", "implicit", "blocked"])
+def test_invalid_c2_fields_are_rejected(bad):
+    n, length, om = (32, 32), (1.0, 1.0), [5.5, 9.3]
+    c2 = inputs.random_c2(n, 12)
+    kw = {}
+    if bad == "negative":
+        c2[3, 4] = -1.0
+    elif bad == "nan":
+        c2[5, 5] = np.nan
+    elif bad == "fp32":
+        kw["precision"] = _lib.PREC_FP32_KAHAN
+    elif bad == "implicit":
+        kw["time_stepping"] = "implicit"
+    else:
+        kw["time_block"] = 4
+    prob, keep = M.make_problem(n, length, om, c2_field=c2, **kw)
+    with pytest.raises(_lib.MfwhError) as e:
+        M.plan(prob)
+    assert e.value.status == _lib.ERR_INVALID_ARG

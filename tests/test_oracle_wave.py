@@ -63,6 +63,22 @@ def test_fixed_point_3d_two_layer():
     assert np.max(np.abs(PU - U)) / np.max(np.abs(U)) < 1e-12
 
 
+@pytest.mark.parametrize("dims", [(12, 10), (8, 7, 6)])
+def test_fixed_point_with_random_c2_field(dims):
+    """The same invariant with c^2 drawn independently at every grid point (c in [1, 1.5]):
+    the sparse direct solution of (c_j^2 Delta_h + omega^2) U = f is the fixed point of the
+    map, whose time step takes c_max from the field."""
+    c2 = inputs.random_c2(dims, 21, 1.0, 1.5)
+    p = _problem(dims, [4.1, 7.9, 12.5], c2=c2, b=60.0)
+    U = W.helmholtz_direct(p)
+    PU = W.apply_Pi(p, U)
+    assert np.max(np.abs(PU - U)) / np.max(np.abs(U)) < 1e-12
+    # a constant field (c^2 = 1.7) solves like the constant-speed problem: L_h scales by c^2
+    pc = _problem(dims, [4.1, 7.9, 12.5], c2=np.full(c2.shape, 1.7), b=60.0)
+    ps = _problem(dims, [4.1, 7.9, 12.5], c2=1.7, b=60.0)
+    np.testing.assert_allclose(W.helmholtz_direct(pc), W.helmholtz_direct(ps), rtol=0, atol=1e-13)
+
+
 def test_fixed_point_fails_with_unadjusted_B():
     """Planted mistake: building B with the unadjusted omega_j instead of omega~_j breaks
     the fixed point, so the invariant does test that reading."""
