@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--solve", action="store_true", help="also time one unrestarted solve to 1e-8")
     ap.add_argument("--time-block", type=int, default=0,
                     help="leapfrog steps per kernel launch (0 = library default)")
+    ap.add_argument("--tile-shape", type=int, default=0,
+                    help="tile shape of the blocked kernels (library's tile_shape)")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 wave-solve leg")
     ap.add_argument("--fp32-only", action="store_true",
                     help="run only the FP32 leg and print it (for profiling its kernel)")
@@ -233,32 +235,109 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(wl, budget_s=15.0):
-    """The oracle's map on the full grid for a bounded number of time steps (test
-    infrastructure, timed as it stands); returns Gpts/s and a description."""
+def _oracle_sample_problem(make, steps):
+    """The oracle's problem for the workload inputs.<make[0]>(**make[1]), cut to its first
+    `steps` time steps (test infrastructure)."""
     from oracle import wave as W
+    from paper_2507_23613_gb300 import inputs
     import copy
+    wl = getattr(inputs, make[0])(**make[1])
     g = W.Grid(wl.n, wl.length)
     prob = W.make_problem(g, wl.omega, wl.forcing, c2=wl.c2, cfl=wl.cfl, n_p=wl.n_p)
     n_full = prob.setup.n_t
-    # calibrate on a few steps, then run a sample of about budget_s seconds
-    steps = 4
-    while True:
-        sub = copy.copy(prob)
-        sub.setup = copy.copy(prob.setup)
-        sub.setup.n_t = steps
-        sub.setup.w = prob.setup.w[:steps + 1]
+    sub = copy.copy(prob)
+    sub.setup = copy.copy(prob.setup)
+    sub.setup.n_t = min(steps, n_full)
+    sub.setup.w = prob.setup.w[:sub.setup.n_t + 1]
+    return sub, wl, n_full
+
+
+def _oracle_worker(make, steps, commands, results):
+    """One host process of the CPU baseline: build the sample once, then time the oracle's
+    homogeneous map over it each time a command arrives (None ends the process)."""
+    from oracle import wave as W
+    sub, wl, _ = _oracle_sample_problem(make, steps)
+    v = np.zeros_like(wl.forcing)
+    results.put(None)                       # ready
+    while commands.get() is not None:
         t0 = time.perf_counter()
-        W.apply_Pi(sub, np.zeros_like(wl.forcing), forced=False)
-        dt = time.perf_counter() - t0
-        if dt > budget_s / 4 or steps >= n_full:
-            break
-        steps = min(n_full, int(steps * max(2.0, budget_s / max(dt, 1e-3))))
-    pts = wl.interior_points * steps
-    return {"value": pts / dt / 1e9, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
-            "sample": (f"numpy oracle, homogeneous map, {steps} of {n_full} leapfrog+filter steps "
-                       f"on the full {'x'.join(str(k + 1) for k in wl.n)} grid, N_f={wl.nf}, "
-                       f"{dt:.1f} s, single-threaded numpy")}
+        W.apply_Pi(sub, v, forced=False)
+        results.put(time.perf_counter() - t0)
+
+
+class OracleRig:
+    """The oracle's map (test infrastructure, timed as it stands) on the host cores: `workers`
+    processes (default: all cores), each running the homogeneous map of the workload
+    inputs.<make[0]>(**make[1]) on the full grid for the same bounded number of time steps,
+    numpy single-threaded in each.  The number of steps is calibrated on one process to take
+    about budget_s / 4 .. budget_s; one sample is all processes' point-steps over the slowest
+    process's time, started together."""
+
+    def __init__(self, make, budget_s=15.0, workers=None):
+        import multiprocessing as mp
+        from oracle import wave as W
+        self.workers = workers or os.cpu_count() or 1
+        steps = 4
+        while True:
+            sub, wl, n_full = _oracle_sample_problem(make, steps)
+            t0 = time.perf_counter()
+            W.apply_Pi(sub, np.zeros_like(wl.forcing), forced=False)
+            dt = time.perf_counter() - t0
+            if dt > budget_s / 4 or steps >= n_full:
+                break
+            steps = min(n_full, int(steps * max(2.0, budget_s / max(dt, 1e-3))))
+        self.steps, self.n_full, self.wl, self.last_dt = steps, n_full, wl, dt
+        self.procs = []
+        if self.workers > 1:
+            ctx = mp.get_context("spawn")
+            keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")
+            saved = {k: os.environ.get(k) for k in keys}
+            os.environ.update({k: "1" for k in keys})
+            self.results = ctx.Queue()
+            self.cmds = [ctx.Queue() for _ in range(self.workers)]
+            for c in self.cmds:
+                pr = ctx.Process(target=_oracle_worker, args=(make, steps, c, self.results),
+                                 daemon=True)
+                pr.start()
+                self.procs.append(pr)
+            for k, val in saved.items():
+                if val is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = val
+            for _ in self.procs:
+                self.results.get(timeout=900)       # every worker has built its sample
+
+    def run(self):
+        """One sample: Gpts/s and a description."""
+        if self.procs:
+            for c in self.cmds:
+                c.put(1)
+            self.last_dt = max(self.results.get(timeout=900) for _ in self.procs)
+        wl = self.wl
+        pts = wl.interior_points * self.steps * self.workers
+        return {"value": pts / self.last_dt / 1e9, "unit": "Gpts/s", "cores": self.workers,
+                "kind": "oracle",
+                "sample": (f"numpy oracle, homogeneous map, {self.workers} process(es) x "
+                           f"{self.steps} of {self.n_full} leapfrog+filter steps each on the full "
+                           f"{'x'.join(str(k + 1) for k in wl.n)} grid, N_f={wl.nf}, slowest "
+                           f"{self.last_dt:.1f} s, numpy single-threaded per process")}
+
+    def close(self):
+        for c in getattr(self, "cmds", []):
+            c.put(None)
+        for pr in self.procs:
+            pr.join(timeout=60)
+        self.procs = []
+
+
+def cpu_baseline(make, budget_s=15.0, workers=None):
+    """One sample of the oracle on the host cores (OracleRig)."""
+    rig = OracleRig(make, budget_s, workers)
+    try:
+        return rig.run()
+    finally:
+        rig.close()
 
 
 def oracle_timings(args):
@@ -268,7 +347,8 @@ def oracle_timings(args):
     such)."""
     from oracle import wave as W
     from paper_2507_23613_gb300 import inputs
-    out = {"cores": 1, "kind": "oracle"}
+    out = {"cores": 1, "kind": "oracle",
+           "note": "the 65^2 runs use one core; the 1025^2 and 257^3 samples use all cores"}
     wl = inputs.square_small()
     g = W.Grid(wl.n, wl.length)
     prob = W.make_problem(g, wl.omega, wl.forcing, cfl=wl.cfl, n_p=wl.n_p)
@@ -280,9 +360,10 @@ def oracle_timings(args):
     t_gm = time.perf_counter() - t0
     out["square65_nf2"] = {"fpi40_s": round(t_fpi, 3), "gmres_1e-8_s": round(t_gm, 3),
                            "gmres_iterations": ginfo.iterations, "n_t": prob.setup.n_t}
-    for name, wl in (("square1025_nf8", inputs.square_large(args.seed)),
-                     ("cube257_nf4", inputs.cube_layered(args.seed + 1000))):
-        info = cpu_baseline(wl, budget_s=10.0)
+    for name, make in (("square1025_nf8", ("square_large", {"seed": args.seed})),
+                       ("cube257_nf4", ("cube_layered", {"seed": args.seed + 1000}))):
+        wl = getattr(inputs, make[0])(**make[1])
+        info = cpu_baseline(make, budget_s=10.0)
         n_t = W.make_problem(W.Grid(wl.n, wl.length), wl.omega, wl.forcing, c2=wl.c2,
                              cfl=wl.cfl, n_p=wl.n_p).setup.n_t
         per_map = wl.interior_points * n_t / (info["value"] * 1e9)
@@ -327,22 +408,29 @@ def run_small(args):
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle (test infrastructure, timed as it stands) on all host
+    cores (OracleRig), one bounded sample of the bench workload per step."""
     if rank != 0:
         return
     from paper_2507_23613_gb300 import inputs
+    make = ("square_large", {"seed": args.seed})
     wl = inputs.square_large(args.seed)
-    per = []
-    for _ in range(args.warmup):
-        cpu_baseline(wl, budget_s=5.0)
-    info = None
-    for _ in range(args.steps):
-        info = cpu_baseline(wl, budget_s=10.0)
-        per.append(info["value"])
+    rig = OracleRig(make, budget_s=4.0)
+    try:
+        for _ in range(args.warmup):
+            rig.run()
+        per = []
+        info = None
+        for _ in range(args.steps):
+            info = rig.run()
+            per.append(info["value"])
+    finally:
+        rig.close()
     value = statistics.mean(per)
     line = {"impl": "reference", "metric": "stencil Gpts/s (+N_f filters)", "value": value,
             "unit": "Gpts/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(wl, None),
+            "data": "synthetic", "config": workload_config(wl, rig.n_full),
             "cpu_baseline": {**info, "value": value},
             "e2e": {"value": value, "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     if args.oracle_timings:
@@ -943,7 +1031,8 @@ def main():
         print(json.dumps({"fp32": fp32_leg(args, wl, f_dev, stream, n_t32)}), flush=True)
         return
     solver = M.Solver(wl.n, wl.length, wl.omega, f_dev, stream=stream.cuda_stream,
-                      n_p=wl.n_p, cfl=wl.cfl, time_block=args.time_block)
+                      n_p=wl.n_p, cfl=wl.cfl, time_block=args.time_block,
+                      tile_shape=args.tile_shape)
     n_t = solver.setup["n_t"]
     N = wl.forcing.size
     v = torch.zeros(wl.forcing.shape, dtype=torch.float64, device="cuda")
@@ -1069,7 +1158,8 @@ def main():
         "fp32": fp32,
     }
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(wl)
+        line["cpu_baseline"] = cpu_baseline(("square_large", {"seed": multi.problem_seed(
+            args.seed, rank)}), budget_s=8.0)
     print(json.dumps(line), flush=True)
 
 

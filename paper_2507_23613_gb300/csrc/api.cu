@@ -466,6 +466,7 @@ mfwh_status apply_pi_tb(mfwh_handle_t h, const double* vin, double* vout, int fo
   a.dt2 = dt * dt;
   a.half_dt2 = 0.5 * dt * dt;
   a.depth = depth;
+  a.shape = P.tile_shape;
   a.forced = forced;
   a.subtract = vsub != nullptr;
   std::memcpy(a.binv, h->sh.binv, sizeof(a.binv));

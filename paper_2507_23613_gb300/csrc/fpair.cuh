@@ -27,6 +27,39 @@ __device__ __forceinline__ float2 fpair_from(double v) {
 
 __device__ __forceinline__ double fpair_value(float2 q) { return (double)q.x + (double)q.y; }
 
+// The pair of a double formed with integer and FP32 operations only, so that the FP64 pipe
+// (the step kernels' bottleneck on sm_103a) is not used: three FP64-pipe conversions and a
+// subtraction become about twenty integer and FP32 instructions.
+//   hi: |v| rounded to 24 significant bits (ties away from zero) on the bit pattern, v's sign;
+//   lo: the remainder |v| - |hi|, an integer d (|d| <= 2^28) in units of 2^(e-1075), e the
+//       biased exponent of v (the bit patterns of |v| and |hi| differ by exactly d, also when
+//       rounding carries |hi| into the next binade), converted to float and scaled.
+// hi + lo equals v to within 2^-48 |v|, as for fpair_from (which it matches except on exact
+// ties), for |v| from about 2^-101 (below, lo is a subnormal float and the pair keeps 2^-150
+// absolute) to 2^116.  |v| below 2^-126 gives (0, 0); |v| of 2^116 and more, infinities and
+// NaN take fpair_from.
+__device__ __forceinline__ float2 fpair_split(double v) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const unsigned long long a = bits & 0x7FFFFFFFFFFFFFFFull;
+  const unsigned long long h = (a + (1ull << 28)) & ~((1ull << 29) - 1ull);
+  const int eh = (int)(h >> 52);
+  if (eh > 1138) return fpair_from(v);
+  const int ev = (int)(a >> 52);
+  const unsigned sgn = (unsigned)(bits >> 32) & 0x80000000u;
+  const float hi = __uint_as_float(((unsigned)(h >> 29) - (896u << 23)) | sgn);
+  const int d = (int)((unsigned)a - (unsigned)h);
+  // lo = d 2^k, k = ev - 1075, as d 2^kk (kk = k, or k + 64 when 2^k is not a normal float)
+  // times 2^(k - kk): both factors are normal floats for 885 <= ev <= 1138 and d 2^kk stays
+  // below 2^91; only a subnormal lo rounds
+  const int k = ev - 1075;
+  const bool low = k < -126;
+  const int kk = low ? k + 64 : k;
+  const float mag = ((float)d * __uint_as_float((unsigned)(kk + 127) << 23)) *
+                    (low ? 0x1p-64f : 1.0f);
+  const float lo = __uint_as_float(__float_as_uint(mag) ^ sgn);
+  return eh < 897 ? make_float2(0.0f, 0.0f) : make_float2(hi, lo);
+}
+
 // q + (wh + wl)(xh + xl) as a renormalised pair.
 __device__ __forceinline__ float2 fpair_fma(float wh, float wl, float xh, float xl, float2 q) {
   const float ph = wh * xh;

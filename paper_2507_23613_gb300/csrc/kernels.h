@@ -65,6 +65,8 @@ struct TBHost {
   const double* cos_table;   // device [(N_t + 1) * nf] cos(omega~_m t^n)
   double dt2, half_dt2;
   int n0, steps, depth;      // first level index, steps in this launch, template depth (4 or 8)
+  int shape;                 // tile: 0 = 32 x 64, 1 = 32 x 32, 2 = 32 x 48 points (32 x 32
+                             // above 8 frequencies)
   int forced, last, subtract;
   double binv[MFWH_MAX_NF * MFWH_MAX_NF];   // epilogue as in StepHost
   double emat[MFWH_MAX_NF * MFWH_MAX_NF];

@@ -156,7 +156,7 @@ k_step(const double* __restrict__ Wc, double* __restrict__ Wp, const double* __r
   if (!x.interior) return;           // boundary values stay 0 (Dirichlet, g = 0)
   const double wn = leapfrog_point<NF, DIM, ORDER>(Wc, Wp, f, a, g, x);
   Wp[x.p] = wn;
-  const float2 xw = fpair_from(wn);
+  const float2 xw = fpair_split(wn);
 #pragma unroll
   for (int m = 0; m < NF; ++m) {
     float2* qm = q + m * g.points + x.p;

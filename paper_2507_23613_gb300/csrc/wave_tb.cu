@@ -1,21 +1,30 @@
-// Temporally blocked MFWH wave step for 2D grids, FP64, sm_103a.
+// Temporally blocked MFWH wave step for 2D grids, FP64 wave levels, sm_103a.
 //
-// One launch advances the leapfrog scheme (eq. WaveSchemeA; the first step of a
-// wave solve as eq. implicitFirstStep with alpha = 0) by up to T steps and
-// accumulates the N_f filter sums (eq. pDefQ) on the way.  Each CTA owns a
-// 32 x (16 K) tile of output points.  It loads W^n and W^{n-1} on the tile plus
-// a halo of T points into shared memory, then steps: at step s it updates the
-// tile plus a ring of radius steps-1-s (the points whose values later steps
-// still need), so after the last step W^{n+T} and W^{n+T-1} are exact on the
-// tile.  Every thread keeps the filter sums q_m of its K owned tile points in
-// registers for all T steps, so per point and launch HBM sees one read of the
-// two wave levels (with halo), one read-modify-write of the N_f sums and one
-// write of the two new levels, instead of T of each.
+// One launch advances the leapfrog scheme (eq. WaveSchemeA; the first step of a wave solve as
+// eq. implicitFirstStep with alpha = 0) by up to T steps and accumulates the N_f filter sums
+// (eq. pDefQ) on the way.  The interior points 1..n-1 of each axis are cut into tiles of
+// 32 x (16 K) points, one tile per CTA of 32 x 16 threads.  A CTA loads W^n and W^{n-1} on its
+// tile plus a halo of T points into shared memory; at step s it updates the tile and the ring
+// of radius T-1-s around it (the points later steps still read), so after T steps W^{n+T} and
+// W^{n+T-1} are exact on the tile.  Per point and launch HBM sees one read and one write of the
+// two levels and of the N_f filter sums, instead of T of each.
 //
-// The per-point arithmetic is the unblocked kernel's (k_step in wave.cu) in the
-// same order, so results are bit-identical to it.  The last launch of a wave
-// solve can fuse the filter solve V = B^{-1} q (eq. waveHoltzMatrixIteration).
+// Thread (tx, ty) owns the K consecutive tile rows ty K .. ty K + K - 1 of column tx: the two
+// wave levels and the N_f filter sums (float pairs, fpair.cuh) of its points stay in registers
+// for all T steps, vertical neighbours come from registers, and only the left and right
+// neighbours and the rows just above and below the strip come from shared memory.  The ring is
+// spread evenly over all threads by a flat index.  On sm_103a the FP64 pipe bounds this kernel
+// (a warp instruction occupies it for about 64 cycles), so the float pair of each new value is
+// split off its bit pattern on the integer and FP32 pipes (fpair_split) and the filter updates
+// run on the FP32 pipe: a point-step of the homogeneous 5-point scheme costs two FP64 adds and
+// three FP64 FMAs.
+//
+// The per-point arithmetic is the unblocked kernel's (k_step in wave.cu) in the same order, so
+// results are bit-identical to it.  The last launch of a wave solve fuses the filter solve
+// V = C q + E V^k (eq. waveHoltzMatrixIteration; E = 0 for the implicit filter).
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "fpair.cuh"
 #include "kernels.h"
@@ -44,29 +53,49 @@ struct TBParams {
   double emat[NF * NF];           // E
 };
 
-__device__ __forceinline__ bool interior_pt(int64_t gx, int64_t gy, const Geom& g) {
-  return gx > 0 && gx < g.nx && gy > 0 && gy < g.ny;
+// Clamp a local coordinate bound (64-bit global difference) to [lo, hi].
+__device__ __forceinline__ int clamp_local(int64_t v, int lo, int hi) {
+  return (int)(v < lo ? lo : (v > hi ? hi : v));
 }
 
-// New level at local point l of the tile (row length EX) from the current level A and the
-// previous level B (W^{n-1}, read at the point only); same operation order as k_step.
-// fneg: this step's kappa cos(omega~_m t^n), in shared memory.
-template <int NF>
-__device__ __forceinline__ double update_point(const double* A, const double* B, int l, int ex,
-                                               const LayerCoef& L, const double* fneg,
-                                               const double* __restrict__ f, int64_t p,
-                                               int64_t points, bool forced) {
+// New level at local point l (row length EX) of a ring point: the operations of k_step in the
+// same order.  A: W^n, Wprev: W^{n-1} at l (0 before the first step).
+template <int NF, int EX, bool FORCED>
+__device__ __forceinline__ double ring_update(const double* A, double wprev, int l,
+                                              const LayerCoef& L, bool first, const double* fneg,
+                                              const double* __restrict__ f, int64_t p,
+                                              int64_t points) {
   const double wc = A[l];
   const double sx = A[l - 1] + A[l + 1];
-  const double sy = A[l - ex] + A[l + ex];
-  double acc = fma(L.A0, wc, -B[l]);
+  const double sy = A[l - EX] + A[l + EX];
+  double acc = first ? L.A0 * wc : fma(L.A0, wc, -wprev);
   acc = fma(L.Ax, sx, acc);
   acc = fma(L.Ay, sy, acc);
-  if (forced) {
+  if (FORCED) {
 #pragma unroll
     for (int m = 0; m < NF; ++m) acc = fma(-fneg[m], f[m * points + p], acc);
   }
   return acc;
+}
+
+// Local coordinates of flat ring index e at radius r: the 2r rows of BX + 2r points above and
+// below the tile, then the BY rows of 2r points left and right of it.  Quotients by the row
+// lengths come from a float reciprocal: (e + 1/2) / len is at least 1/(2 len) from an integer,
+// far above the rounding of the product for the ring sizes used here.
+template <int T, int BX, int BY>
+__device__ __forceinline__ void ring_coords(int e, int r, int rw, int top, float inv_rw,
+                                            float inv_2r, int& lx, int& ly) {
+  if (e < top) {
+    const int row = (int)(((float)e + 0.5f) * inv_rw);
+    lx = T - r + (e - row * rw);
+    ly = row < r ? T - r + row : T + BY + row - r;
+  } else {
+    const int e2 = e - top;
+    const int row = (int)(((float)e2 + 0.5f) * inv_2r);
+    const int col = e2 - row * 2 * r;
+    ly = T + row;
+    lx = col < r ? T - r + col : T + BX + col - r;
+  }
 }
 
 template <int NF, int T, int K>
@@ -76,175 +105,229 @@ k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
        float2* __restrict__ q, double* vout, const double* vsub, const TBParams<NF> a,
        const Geom g) {
   constexpr int BX = kTX, BY = kTY * K;
-  constexpr int EX = BX + 2 * T, EY = BY + 2 * T;
+  constexpr int EX = BX + 2 * T, EY = BY + 2 * T, E = EX * EY;
+  constexpr int NT = kTX * kTY;
   extern __shared__ double smem[];
-  double* A = smem;             // current level
-  double* B = smem + EX * EY;   // previous level, overwritten by the next one
-  double* s_wq = smem + 2 * EX * EY;   // [T][NF] filter weights of the new level per step
-  double* s_fc = s_wq + T * NF;        // [T][NF] kappa cos(omega~_m t^n) per step
+  double* A = smem;                  // W^n on the extended tile
+  double* B = smem + E;              // W^{n-1} on the ring, overwritten by W^{n+1}
+  double* s_wq = smem + 2 * E;       // [T][NF] filter weights of the new level per step
+  double* s_fc = s_wq + T * NF;      // [T][NF] kappa cos(omega~_m t^n) per step
   float* s_wh = reinterpret_cast<float*>(s_fc + T * NF);   // [T][NF] s_wq as float pairs
   float* s_wl = s_wh + T * NF;
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int tid = ty * kTX + tx;
-  constexpr int NT = kTX * kTY;
-  const int64_t bx0 = (int64_t)blockIdx.x * BX, by0 = (int64_t)blockIdx.y * BY;
-  const int64_t x0 = bx0 - T, y0 = by0 - T;     // global coordinates of smem (0, 0)
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTX + tx;
+  // global coordinates of local (0, 0); tiles start at the first interior point
+  const int64_t x0 = 1 + (int64_t)blockIdx.x * BX - T, y0 = 1 + (int64_t)blockIdx.y * BY - T;
+  // local bounds: grid points [gl, gh], interior points [il, ih] (32-bit)
+  const int glx = clamp_local(-x0, 0, EX), ghx = clamp_local(g.nx - x0, -1, EX - 1);
+  const int gly = clamp_local(-y0, 0, EY), ghy = clamp_local(g.ny - y0, -1, EY - 1);
+  const int ilx = clamp_local(1 - x0, 0, EX), ihx = clamp_local(g.nx - 1 - x0, -1, EX - 1);
+  const int ily = clamp_local(1 - y0, 0, EY), ihy = clamp_local(g.ny - 1 - y0, -1, EY - 1);
+  // c^2 layer: points whose local coordinate along the layer axis is >= lay_thr use hi
+  const bool lay_x = g.layer_axis == 0;
+  const int lay_thr = clamp_local(g.layer_split - (lay_x ? x0 : y0), -1, EX + EY);
+  // every point updated by any step interior, all with one c^2: no per-point tests needed
+  const bool simple = ilx <= 1 && ihx >= EX - 2 && ily <= 1 && ihy >= EY - 2 &&
+                      (lay_thr <= 0 || lay_thr >= (lay_x ? EX : EY));
+  const bool all_hi = lay_thr <= 0;
 
-  // Load both levels on the tile plus halo; points outside the grid read as 0.
-  for (int e = tid; e < EX * EY; e += NT) {
-    const int lx = e % EX, ly = e / EX;
-    const int64_t gx = x0 + lx, gy = y0 + ly;
-    const bool in = gx >= 0 && gx <= g.nx && gy >= 0 && gy <= g.ny;
-    const int64_t p = gy * g.sy + gx;
+  // Both levels on the tile plus halo; points outside the grid read as 0.
+  for (int e = tid; e < E; e += NT) {
+    const int ly = e / EX, lx = e - ly * EX;
+    const bool in = ly >= gly && ly <= ghy && lx >= glx && lx <= ghx;
+    const int64_t p = (y0 + ly) * g.sy + x0 + lx;
     A[e] = in ? Wc_in[p] : 0.0;
     B[e] = (in && Wp_in != nullptr) ? Wp_in[p] : 0.0;
   }
   // Per-step coefficients of this launch.
   for (int e = tid; e < a.steps * NF; e += NT) {
-    const int st = e / NF, m = e % NF;
+    const int st = e / NF, m = e - st * NF;
     const int n = a.n0 + st;
     const double w = a.wq_table[(n + 1) * NF + m];
     s_wq[e] = w;
-    s_wh[e] = (float)w;
-    s_wl[e] = (float)(w - (double)s_wh[e]);
+    const float wh = (float)w;
+    s_wh[e] = wh;
+    s_wl[e] = (float)(w - (double)wh);
     s_fc[e] = a.forced ? (n == 0 ? a.half_dt2 : a.dt2) * a.cos_table[n * NF + m] : 0.0;
   }
-  // Owned tile points: (T + tx, T + ty + kTY k); their filter sums live in registers as float
-  // pairs, updated as in k_step.  The final step of a wave solve (a.last) adds its term in
-  // FP64 in the epilogue, as k_last does.
+  // The strip: local column lxo, rows lyo .. lyo + K - 1.
+  const int lxo = T + tx, lyo = T + ty * K;
+  const int64_t p0 = (y0 + lyo) * g.sy + x0 + lxo;
+  const bool col_int = lxo >= ilx && lxo <= ihx;
+  bool own_int[K], own_up[K];
+  double wc[K], wp[K], wlast[K];
   float2 qr[K][NF];
-  double wlast[K];
-  int64_t own_p[K];
-  bool own_int[K], own_in[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const int64_t gx = bx0 + tx, gy = by0 + ty + kTY * k;
-    own_in[k] = gx <= g.nx && gy <= g.ny;
-    own_int[k] = interior_pt(gx, gy, g);
-    own_p[k] = gy * g.sy + gx;
+    own_int[k] = col_int && lyo + k >= ily && lyo + k <= ihy;
+    own_up[k] = (lay_x ? lxo : lyo + k) >= lay_thr;
+    wlast[k] = 0.0;
 #pragma unroll
     for (int m = 0; m < NF; ++m)
-      qr[k][m] = own_int[k] ? q[m * g.points + own_p[k]] : make_float2(0.0f, 0.0f);
-    wlast[k] = 0.0;
+      qr[k][m] = own_int[k] ? q[m * g.points + p0 + k * g.sy] : make_float2(0.0f, 0.0f);
   }
   __syncthreads();
-
-  for (int s = 0; s < a.steps; ++s) {
-    const int r = a.steps - 1 - s;          // ring radius still needed after this step
-    const int n = a.n0 + s;                 // computing W^{n+1}
-    const bool first = n == 0;
-    const LayerCoef lo = first ? a.first_lo : a.reg_lo;
-    const LayerCoef hi = first ? a.first_hi : a.reg_hi;
-    const double* fneg = s_fc + s * NF;
-    const float* wh = s_wh + s * NF;
-    const float* wl = s_wl + s * NF;
-    const bool final_step = a.last && s == a.steps - 1;
-    // owned tile points
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      if (!own_int[k]) continue;
-      const int l = (T + ty + kTY * k) * EX + (T + tx);
-      const int64_t gx = bx0 + tx, gy = by0 + ty + kTY * k;
-      const int64_t li = g.layer_axis == 0 ? gx : gy;
-      const LayerCoef& L = li >= g.layer_split ? hi : lo;
-      const double wn = update_point<NF>(A, B, l, EX, L, fneg, f, own_p[k], g.points, a.forced);
-      B[l] = wn;
-      if (final_step) {
-        wlast[k] = wn;
-      } else {
-        const float2 xw = fpair_from(wn);
-#pragma unroll
-        for (int m = 0; m < NF; ++m) qr[k][m] = fpair_fma(wh[m], wl[m], xw.x, xw.y, qr[k][m]);
-      }
-    }
-    // ring of radius r around the tile (halo points later steps need)
-    if (r > 0) {
-      const int W = BX + 2 * r;
-      const int ring = 2 * r * W + 2 * r * BY;
-      for (int e = tid; e < ring; e += NT) {
-        int lx, ly;
-        if (e < r * W) {
-          ly = T - r + e / W;
-          lx = T - r + e % W;
-        } else if (e < 2 * r * W) {
-          const int e2 = e - r * W;
-          ly = T + BY + e2 / W;
-          lx = T - r + e2 % W;
-        } else if (e < 2 * r * W + r * BY) {
-          const int e3 = e - 2 * r * W;
-          ly = T + e3 / r;
-          lx = T - r + e3 % r;
-        } else {
-          const int e4 = e - 2 * r * W - r * BY;
-          ly = T + e4 / r;
-          lx = T + BX + e4 % r;
-        }
-        const int64_t gx = x0 + lx, gy = y0 + ly;
-        if (!interior_pt(gx, gy, g)) continue;
-        const int64_t li = g.layer_axis == 0 ? gx : gy;
-        const LayerCoef& L = li >= g.layer_split ? hi : lo;
-        const int l = ly * EX + lx;
-        B[l] = update_point<NF>(A, B, l, EX, L, fneg, f, gy * g.sy + gx, g.points, a.forced);
-      }
-    }
-    __syncthreads();
-    double* t = A;
-    A = B;
-    B = t;
+  for (int k = 0; k < K; ++k) {
+    wc[k] = A[(lyo + k) * EX + lxo];
+    wp[k] = B[(lyo + k) * EX + lxo];
   }
-  // A = W^{n0+steps}, B = W^{n0+steps-1} on the tile
+
+  // The steps in two compiled copies with the same per-point arithmetic: ALLINT for
+  // homogeneous launches of CTAs whose updated points are all interior with one c^2 (no
+  // forcing terms, no per-point interior or layer tests), and the general one.
+  auto run_steps = [&](auto allint_c) {
+    constexpr bool ALLINT = decltype(allint_c)::value;
+    for (int s = 0; s < a.steps; ++s) {
+      const int r = a.steps - 1 - s;          // ring radius still needed after this step
+      const int n = a.n0 + s;                 // computing W^{n+1}
+      const bool first = n == 0;
+      const LayerCoef& lo = first ? a.first_lo : a.reg_lo;
+      const LayerCoef& hi = first ? a.first_hi : a.reg_hi;
+      const double* fneg = s_fc + s * NF;
+      const bool final_step = a.last && s == a.steps - 1;
+      // owned strip: centre and vertical neighbours from registers
+      {
+        const double above = A[(lyo - 1) * EX + lxo];
+        const double below = A[(lyo + K) * EX + lxo];
+        double wn[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          wn[k] = wc[k];
+          if (!ALLINT && !own_int[k]) continue;   // boundary and outside points keep W = 0
+          const int l = (lyo + k) * EX + lxo;
+          const LayerCoef& L = ALLINT ? (all_hi ? hi : lo) : (own_up[k] ? hi : lo);
+          const double up = k == 0 ? above : wc[k - 1];
+          const double dn = k == K - 1 ? below : wc[k + 1];
+          const double sx = A[l - 1] + A[l + 1];
+          const double sy = up + dn;
+          double acc = first ? L.A0 * wc[k] : fma(L.A0, wc[k], -wp[k]);
+          acc = fma(L.Ax, sx, acc);
+          acc = fma(L.Ay, sy, acc);
+          if (!ALLINT && a.forced) {
+#pragma unroll
+            for (int m = 0; m < NF; ++m)
+              acc = fma(-fneg[m], f[m * g.points + p0 + k * g.sy], acc);
+          }
+          wn[k] = acc;
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          if (!ALLINT && !own_int[k]) continue;
+          B[(lyo + k) * EX + lxo] = wn[k];
+          wp[k] = wc[k];
+          wc[k] = wn[k];
+          if (final_step) {
+            wlast[k] = wn[k];
+          } else {
+            const float2 xw = fpair_split(wn[k]);
+#pragma unroll
+            for (int m = 0; m < NF; ++m)
+              qr[k][m] = fpair_fma(s_wh[s * NF + m], s_wl[s * NF + m], xw.x, xw.y, qr[k][m]);
+          }
+        }
+      }
+      // ring of radius r around the tile
+      if (r > 0) {
+        const int rw = BX + 2 * r;
+        const int top = 2 * r * rw;
+        const int ring = top + 2 * r * BY;
+        const float inv_rw = 1.0f / (float)rw, inv_2r = 1.0f / (float)(2 * r);
+        for (int e = tid; e < ring; e += NT) {
+          int lx, ly;
+          ring_coords<T, BX, BY>(e, r, rw, top, inv_rw, inv_2r, lx, ly);
+          if (!ALLINT && !simple && (lx < ilx || lx > ihx || ly < ily || ly > ihy)) continue;
+          const LayerCoef& L =
+              (ALLINT || simple) ? (all_hi ? hi : lo) : (((lay_x ? lx : ly) >= lay_thr) ? hi : lo);
+          const int l = ly * EX + lx;
+          const int64_t p = (y0 + ly) * g.sy + x0 + lx;
+          if (!ALLINT && a.forced)
+            B[l] = ring_update<NF, EX, true>(A, B[l], l, L, first, fneg, f, p, g.points);
+          else
+            B[l] = ring_update<NF, EX, false>(A, B[l], l, L, first, fneg, f, p, g.points);
+        }
+      }
+      __syncthreads();
+      double* t = A;
+      A = B;
+      B = t;
+    }
+  };
+  if (simple && !a.forced)
+    run_steps(std::true_type{});
+  else
+    run_steps(std::false_type{});
+
+  // wc = W^{n0+steps}, wp = W^{n0+steps-1} on the strip
   if (!a.last) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       if (!own_int[k]) continue;
-      const int l = (T + ty + kTY * k) * EX + (T + tx);
-      Wc_out[own_p[k]] = A[l];
-      Wp_out[own_p[k]] = B[l];
+      const int64_t p = p0 + k * g.sy;
+      Wc_out[p] = wc[k];
+      Wp_out[p] = wp[k];
 #pragma unroll
-      for (int m = 0; m < NF; ++m) q[m * g.points + own_p[k]] = qr[k][m];
+      for (int m = 0; m < NF; ++m) q[m * g.points + p] = qr[k][m];
     }
-  } else {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      if (!own_in[k]) continue;
-      const double* wq = s_wq + (a.steps - 1) * NF;
-      double qq[NF];
-#pragma unroll
-      for (int j = 0; j < NF; ++j) qq[j] = fma(wq[j], wlast[k], fpair_value(qr[k][j]));
-      double vk[NF];
-#pragma unroll
-      for (int j = 0; j < NF; ++j)
-        vk[j] = (a.has_e && own_int[k]) ? a.vprev[j * g.points + own_p[k]] : 0.0;
-      double out[NF];
-#pragma unroll
-      for (int m = 0; m < NF; ++m) {
-        double s = 0.0;
-#pragma unroll
-        for (int j = 0; j < NF; ++j) s = fma(a.binv[m * NF + j], qq[j], s);
-        if (a.has_e) {
-#pragma unroll
-          for (int j = 0; j < NF; ++j) s = fma(a.emat[m * NF + j], vk[j], s);
-        }
-        out[m] = s;
-      }
-#pragma unroll
-      for (int m = 0; m < NF; ++m) {
-        double val = 0.0;
-        if (own_int[k]) val = a.subtract ? vsub[m * g.points + own_p[k]] - out[m] : out[m];
-        vout[m * g.points + own_p[k]] = val;
-      }
-    }
+    return;
   }
+  // Last launch: V^{k+1} = C (q + w_{N_t} W^{N_t}) + E V^k at the interior points, 0 on the
+  // boundary points of this CTA's part of the grid.
+  const double* wq = s_wq + (a.steps - 1) * NF;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (!own_int[k]) continue;
+    const int64_t p = p0 + k * g.sy;
+    double qq[NF];
+#pragma unroll
+    for (int j = 0; j < NF; ++j) qq[j] = fma(wq[j], wlast[k], fpair_value(qr[k][j]));
+    double vk[NF];
+    if (a.has_e) {
+#pragma unroll
+      for (int j = 0; j < NF; ++j) vk[j] = a.vprev[j * g.points + p];
+    }
+    double out[NF];
+#pragma unroll
+    for (int m = 0; m < NF; ++m) {
+      double sacc = 0.0;
+#pragma unroll
+      for (int j = 0; j < NF; ++j) sacc = fma(a.binv[m * NF + j], qq[j], sacc);
+      if (a.has_e) {
+#pragma unroll
+        for (int j = 0; j < NF; ++j) sacc = fma(a.emat[m * NF + j], vk[j], sacc);
+      }
+      out[m] = sacc;
+    }
+#pragma unroll
+    for (int m = 0; m < NF; ++m)
+      vout[m * g.points + p] = a.subtract ? vsub[m * g.points + p] - out[m] : out[m];
+  }
+  // Boundary points: the CTA at each edge of the tile grid writes the boundary lines along
+  // its part of that edge (the parts partition the edges, corners included).
+  const int64_t xs = blockIdx.x == 0 ? 0 : 1 + (int64_t)blockIdx.x * BX;
+  const int64_t xe = blockIdx.x == gridDim.x - 1 ? g.nx + 1 : 1 + (int64_t)(blockIdx.x + 1) * BX;
+  const int64_t ys = blockIdx.y == 0 ? 0 : 1 + (int64_t)blockIdx.y * BY;
+  const int64_t ye = blockIdx.y == gridDim.y - 1 ? g.ny + 1 : 1 + (int64_t)(blockIdx.y + 1) * BY;
+  auto zero_point = [&](int64_t gx, int64_t gy) {
+#pragma unroll
+    for (int m = 0; m < NF; ++m) vout[m * g.points + gy * g.sy + gx] = 0.0;
+  };
+  if (ys == 0)
+    for (int64_t gx = xs + tid; gx < xe; gx += NT) zero_point(gx, 0);
+  if (ye == g.ny + 1)
+    for (int64_t gx = xs + tid; gx < xe; gx += NT) zero_point(gx, g.ny);
+  if (xs == 0)
+    for (int64_t gy = ys + tid; gy < ye; gy += NT) zero_point(0, gy);
+  if (xe == g.nx + 1)
+    for (int64_t gy = ys + tid; gy < ye; gy += NT) zero_point(g.nx, gy);
 }
 
-template <int NF, int T>
-void tb_launch_nf(const Geom& g, const double* Wc_in, const double* Wp_in, double* Wc_out,
-                  double* Wp_out, const double* f, double* q, double* vout, const double* vsub,
-                  const TBHost& h, cudaStream_t st) {
-  constexpr int K = NF <= 8 ? 4 : 2;
+template <int NF, int T, int K>
+void tb_launch_k(const Geom& g, const double* Wc_in, const double* Wp_in, double* Wc_out,
+                 double* Wp_out, const double* f, double* q, double* vout, const double* vsub,
+                 const TBHost& h, cudaStream_t st) {
   constexpr int BX = kTX, BY = kTY * K;
   constexpr int EX = BX + 2 * T, EY = BY + 2 * T;
-  constexpr size_t smem = sizeof(double) * (2 * EX * EY + 3 * T * NF);
+  constexpr size_t smem = sizeof(double) * (2 * EX * EY + 2 * T * NF) + sizeof(float) * 2 * T * NF;
   // The attribute is per device; set it once per device for this instance.
   static bool configured[64] = {};
   int dev = 0;
@@ -274,10 +357,27 @@ void tb_launch_nf(const Geom& g, const double* Wc_in, const double* Wp_in, doubl
       a.binv[m * NF + j] = h.binv[m * MFWH_MAX_NF + j];
       a.emat[m * NF + j] = h.emat[m * MFWH_MAX_NF + j];
     }
-  dim3 grid((unsigned)((g.nx + 1 + BX - 1) / BX), (unsigned)((g.ny + 1 + BY - 1) / BY));
+  // tiles over the interior points 1 .. n-1 of each axis
+  dim3 grid((unsigned)((g.nx - 1 + BX - 1) / BX), (unsigned)((g.ny - 1 + BY - 1) / BY));
   k_tb2d<NF, T, K><<<grid, dim3(kTX, kTY), smem, st>>>(Wc_in, Wp_in, Wc_out, Wp_out, f,
-                                                       reinterpret_cast<float2*>(q), vout, vsub,
-                                                       a, g);
+                                                      reinterpret_cast<float2*>(q), vout, vsub,
+                                                      a, g);
+}
+
+// Rows per thread: 4 (32 x 64 tiles), 3 (32 x 48) or 2 (32 x 32) by tile shape 0, 2, 1; above
+// 8 frequencies the filter sums of more than two points per thread would not fit in registers.
+template <int NF, int T>
+void tb_launch_shape(const Geom& g, const double* Wc_in, const double* Wp_in, double* Wc_out,
+                     double* Wp_out, const double* f, double* q, double* vout, const double* vsub,
+                     const TBHost& h, cudaStream_t st) {
+  if (NF > 8 || h.shape == 1)
+    tb_launch_k<NF, T, 2>(g, Wc_in, Wp_in, Wc_out, Wp_out, f, q, vout, vsub, h, st);
+  else if (h.shape == 2)
+    tb_launch_k<NF, T, (NF > 8 ? 2 : 3)>(g, Wc_in, Wp_in, Wc_out, Wp_out, f, q, vout, vsub, h,
+                                          st);
+  else
+    tb_launch_k<NF, T, (NF > 8 ? 2 : 4)>(g, Wc_in, Wp_in, Wc_out, Wp_out, f, q, vout, vsub, h,
+                                          st);
 }
 
 template <int NF>
@@ -285,9 +385,9 @@ void tb_launch_depth(const Geom& g, const double* Wc_in, const double* Wp_in, do
                      double* Wp_out, const double* f, double* q, double* vout, const double* vsub,
                      const TBHost& h, cudaStream_t st) {
   if (h.depth <= 4)
-    tb_launch_nf<NF, 4>(g, Wc_in, Wp_in, Wc_out, Wp_out, f, q, vout, vsub, h, st);
+    tb_launch_shape<NF, 4>(g, Wc_in, Wp_in, Wc_out, Wp_out, f, q, vout, vsub, h, st);
   else
-    tb_launch_nf<NF, 8>(g, Wc_in, Wp_in, Wc_out, Wp_out, f, q, vout, vsub, h, st);
+    tb_launch_shape<NF, 8>(g, Wc_in, Wp_in, Wc_out, Wp_out, f, q, vout, vsub, h, st);
 }
 
 }  // namespace

@@ -44,9 +44,21 @@ def test_committed_fp32_profile_matches_its_kernel():
 
 
 def test_cpu_baseline_report():
-    info = bench.cpu_baseline(inputs.square_small(), budget_s=0.2)
+    info = bench.cpu_baseline(("square_small", {}), budget_s=0.2, workers=1)
     assert info["kind"] == "oracle" and info["cores"] == 1 and info["unit"] == "Gpts/s"
     assert info["value"] > 0 and "65x65" in info["sample"]
+
+
+def test_cpu_baseline_on_several_cores():
+    """Two spawned processes time the same sample together; the rate counts both."""
+    rig = bench.OracleRig(("square_small", {}), budget_s=0.2, workers=2)
+    try:
+        one = rig.run()
+        two = rig.run()
+    finally:
+        rig.close()
+    assert one["cores"] == 2 and two["cores"] == 2 and "2 process(es)" in one["sample"]
+    assert one["value"] > 0 and two["value"] > 0
 
 
 @pytest.mark.parametrize("argv,flag", [(["--small"], "small"),

@@ -166,21 +166,28 @@ def test_pi_in_place():
     assert np.all(rel_err(buf.cpu().numpy(), W.apply_Pi(prob, v)) <= opt_tol(prob))
 
 
-@pytest.mark.parametrize("shape,nf,seed", [((70, 45), 8, 77), ((40, 33), 16, 31),
-                                            ((64, 64), 2, 5), ((2, 2), 2, 1)])
-def test_time_blocking_is_bit_identical(shape, nf, seed):
+@pytest.mark.parametrize("shape,nf,seed,layer", [((70, 45), 8, 77, None), ((40, 33), 16, 31, None),
+                                                  ((64, 64), 2, 5, None), ((2, 2), 2, 1, None),
+                                                  ((200, 170), 4, 9, None),
+                                                  ((150, 140), 3, 10, 0), ((130, 160), 3, 11, 1)])
+def test_time_blocking_is_bit_identical(shape, nf, seed, layer):
     """Temporal blocking (4 or 8 leapfrog steps per pass over HBM, halo tiles in shared
-    memory) performs the same floating-point operations per point as one step per launch,
-    so Pi, S and the GMRES iterate are bit-identical for every depth; also checked against
-    the oracle.  N_t is not a multiple of the depth on these grids (ragged last launch)."""
+    memory, tiles of 32 x 64, 32 x 32 and 32 x 48 points) performs the same floating-point
+    operations per point as one step per launch, so Pi, S and the GMRES iterate are
+    bit-identical for every depth and tile; also checked against the oracle.  N_t is not a
+    multiple of the depth on these grids (ragged last launch); the larger grids have CTAs whose
+    whole halo is interior (the kernels' test-free path) and two-layer media split along x or
+    y (c = 1 and 1.4 on either side of 0.37 of the length)."""
     om = np.linspace(6.0, 6.0 + 2.5 * (nf - 1), nf)
     wl = inputs.gaussian_workload("tb", shape, nf, om, 150.0, seed)
     wl.n_p = 2 if nf > 2 else 1
     v = random_v(wl, seed + 1)
+    kw = {} if layer is None else dict(c_lo=1.0, c_hi=1.4, interface=0.37, layer_axis=layer)
     outs = {}
-    for tb in (1, 4, 8):
+    for tb, tshape in ((1, 0), (4, 0), (4, 1), (4, 2), (8, 0), (8, 1), (8, 2)):
         solver = M.Solver(wl.n, wl.length, wl.omega, dev(wl.forcing), n_p=wl.n_p, cfl=wl.cfl,
-                          filter_mode=_lib.FILTER_TRADITIONAL, time_block=tb)
+                          filter_mode=_lib.FILTER_TRADITIONAL, time_block=tb, tile_shape=tshape,
+                          **kw)
         res = []
         for forced in (True, False):
             out = torch.empty(v.shape, dtype=torch.float64, device="cuda")
@@ -189,15 +196,22 @@ def test_time_blocking_is_bit_identical(shape, nf, seed):
         x = torch.zeros(v.shape, dtype=torch.float64, device="cuda")
         solver.solve_gmres(x, restart=5, tol=0.0, max_iters=7, raise_on_error=False)
         res.append(x.cpu().numpy())
-        outs[tb] = res
+        outs[(tb, tshape)] = res
         solver.close()
-    for tb in (4, 8):
-        for a, b in zip(outs[tb], outs[1]):
-            assert np.array_equal(a, b), (tb, np.max(np.abs(a - b)))
-    prob = W.make_problem(W.Grid(wl.n, wl.length), wl.omega, wl.forcing, cfl=wl.cfl,
+    for key, got in outs.items():
+        for a, b in zip(got, outs[(1, 0)]):
+            assert np.array_equal(a, b), (key, np.max(np.abs(a - b)))
+    c2 = 1.0
+    if layer is not None:
+        x = np.meshgrid(*[np.arange(n + 1) / n * L for n, L in zip(reversed(wl.n),
+                                                                   reversed(wl.length))],
+                        indexing="ij")
+        coord = x[1] if layer == 0 else x[0]
+        c2 = np.where(coord < 0.37, 1.0, 1.4 ** 2)
+    prob = W.make_problem(W.Grid(wl.n, wl.length), wl.omega, wl.forcing, c2=c2, cfl=wl.cfl,
                           n_p=wl.n_p, filter_mode=F.FILTER_TRADITIONAL)
-    assert np.all(rel_err(outs[8][0], W.apply_Pi(prob, v, forced=True)) <= TOL)
-    assert np.all(rel_err(outs[8][1], W.apply_Pi(prob, v, forced=False)) <= TOL)
+    assert np.all(rel_err(outs[(8, 0)][0], W.apply_Pi(prob, v, forced=True)) <= TOL)
+    assert np.all(rel_err(outs[(8, 0)][1], W.apply_Pi(prob, v, forced=False)) <= TOL)
 
 
 # ---------------------------------------------------------------------------

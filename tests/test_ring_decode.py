@@ -1,4 +1,5 @@
-"""Host check of the halo-ring index decode of the blocked FP32 kernel.
+"""Host check of the halo-ring index decode of the blocked kernels (FP32 k_tb2d32 and FP64
+k_tb2d use the same decode).
 
 At step s of a launch of T steps the kernel updates the ring of radius
 r = T - 1 - s around its BX x BY tile, enumerated by a flat index e; row and
@@ -11,7 +12,8 @@ import numpy as np
 import pytest
 
 BX = 32
-SHAPES = [16 * 2, 16 * 1, 32 * 1, 16 * 4, 16 * 2]   # BY of tile shapes 0-2 (K = 2 or 1)
+SHAPES = [16 * 2, 16 * 1, 32 * 1, 16 * 4, 16 * 2]   # BY of the FP32 tile shapes 0-2 (K = 2 or 1)
+SHAPES += [16 * 4, 16 * 2, 16 * 3]                   # BY of the FP64 tile shapes 0-2 (K = 4, 2, 3)
 
 
 def decode(e, r, T, BY):
