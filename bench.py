@@ -50,6 +50,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--solve", action="store_true", help="also time one unrestarted solve to 1e-8")
+    ap.add_argument("--no-tts", action="store_true",
+                    help="skip the time to a 1e-6 Helmholtz residual (FP64 and mixed arms)")
+    ap.add_argument("--tts-inner", type=float, default=1e-10,
+                    help="inner GMRES tolerance of the time-to-solution arms")
+    ap.add_argument("--tts-relax", type=float, default=1e-2,
+                    help="mixed arm: FP32 products once the inner residual is below this")
     ap.add_argument("--time-block", type=int, default=0,
                     help="leapfrog steps per kernel launch (0 = library default)")
     ap.add_argument("--tile-shape", type=int, default=0,
@@ -523,7 +529,8 @@ def run_batched(args):
     """Independent 2D problems (sizes 257^2..2049^2, N_f 1..16) solved concurrently: one
     host thread and one stream per problem, each wave solve one CUDA-graph launch, blocking
     depth and tile from the autotuner, FP32 wave solves with compensated filter sums.
-    Reports the per-problem solve times (p50, p99) and the aggregate stencil rate."""
+    Reports the per-problem solve times (p50, p99) and the aggregate stencil rate; then the
+    same solves in lockstep, one graph launch per application of the map across the batch."""
     import torch
     import paper_2507_23613_gb300 as M
     from paper_2507_23613_gb300 import _lib, build, inputs
@@ -577,6 +584,29 @@ def run_batched(args):
     wall = time.perf_counter() - t0
     pts = sum((wl.n[0] - 1) * (wl.n[1] - 1) * n_t * info["pi_applications"]
               for (wl, n_t), info in zip(chosen, infos))
+    # the same solves in lockstep: one graph launch per application of the map across the batch
+    bstream = torch.cuda.Stream()
+    for x in xs:
+        x.zero_()
+    M.solve_batch_graph(solvers, xs, restart=1, tol=0.0, max_iters=1, stream=bstream.cuda_stream,
+                        raise_on_error=False)           # warm-up
+    for x in xs:
+        x.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lst, linfos, lsecs = M.solve_batch_graph(solvers, xs, restart=restart, tol=0.0,
+                                             max_iters=args.batch_iters,
+                                             stream=bstream.cuda_stream, raise_on_error=False)
+    torch.cuda.synchronize()
+    lwall = time.perf_counter() - t0
+    lpts = sum((wl.n[0] - 1) * (wl.n[1] - 1) * n_t * info["pi_applications"]
+               for (wl, n_t), info in zip(chosen, linfos))
+    lockstep = {"value": round(lpts / lwall / 1e9, 3), "unit": "Gpts/s (aggregate)",
+                "p50_s": round(float(np.percentile(lsecs, 50)), 3),
+                "p99_s": round(float(np.percentile(lsecs, 99)), 3), "wall_s": round(lwall, 3),
+                "graph_launches": 1 + args.batch_iters, "status": lst,
+                "note": "mfwh_solve_batch_graph: every application of the map is one CUDA-graph "
+                        "launch whose branches are the problems' wave solves"}
     sizes = [wl.n[0] + 1 for wl, _ in chosen]
     line = {"metric": "batched MFWH: per-problem GMRES solve time", "impl": "native",
             "value": round(pts / wall / 1e9, 3), "unit": "Gpts/s (aggregate)",
@@ -590,7 +620,8 @@ def run_batched(args):
                        "nf": [wl.nf for wl, _ in chosen], "n_t": [n for _, n in chosen],
                        "solver": f"GMRES({restart}), {args.batch_iters} Arnoldi steps per problem",
                        "tuned": [list(t[:2]) for t in tuned], "device_gb": round(mem, 1)},
-            "status": st, "generate_s": round(t_gen, 1), "autotune_s": round(t_tune, 1)}
+            "status": st, "generate_s": round(t_gen, 1), "autotune_s": round(t_tune, 1),
+            "lockstep": lockstep}
     print(json.dumps(line), flush=True)
     for s in solvers:
         s.close()
@@ -976,6 +1007,50 @@ def run_warm_start(args):
     net.close()
 
 
+TTS_TARGET = 1e-6          # max_m r_h of the time-to-solution arms
+TTS_RESTART = 800          # no restart within the step budget
+TTS_MAX_ITERS = 1600
+
+
+def time_to_solution(args, wl, f_dev, stream, solver):
+    """Wall time to max_m r_h <= 1e-6 (eq. errorAndResid) on the bench workload from zero, for
+    two arms on the same GPU: FP64 (refinement with FP64 products: an FP64 GMRES solve,
+    repeated on the FP64 residual until r_h meets the target) and mixed precision (the same
+    refinement whose inner solves switch to FP32 wave solves once their residual is below
+    --tts-relax: relaxed inexact Krylov products).  Each arm: seconds, Arnoldi steps,
+    refinements, final max r_h, and whether the target was reached."""
+    import torch
+    import paper_2507_23613_gb300 as M
+    from paper_2507_23613_gb300 import _lib
+    out = {"target_max_rh": TTS_TARGET, "start": "zero", "inner_tol": args.tts_inner,
+           "restart": TTS_RESTART, "max_iters": TTS_MAX_ITERS}
+    s32 = M.Solver(wl.n, wl.length, wl.omega, f_dev, stream=stream.cuda_stream, n_p=wl.n_p,
+                   cfl=wl.cfl, precision=_lib.PREC_FP32_BLOCKSUM)
+    for name, call in (
+            ("fp64", lambda v: solver.solve_refined(
+                v, target=TTS_TARGET, inner_tol=args.tts_inner, restart=TTS_RESTART,
+                max_iters=TTS_MAX_ITERS, max_refinements=8, raise_on_error=False)),
+            ("mixed_relaxed_fp32", lambda v: s32.solve_relaxed(
+                v, target=TTS_TARGET, inner_tol=args.tts_inner, relax_below=args.tts_relax,
+                restart=TTS_RESTART, max_iters=TTS_MAX_ITERS, max_refinements=8,
+                raise_on_error=False))):
+        v = torch.zeros(wl.forcing.shape, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = call(v)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        rh = float(np.max(info["helmholtz_residual"]))
+        out[name] = {"seconds": round(secs, 2), "arnoldi_steps": info["iterations"],
+                     "refinements": info["refinements"], "max_helmholtz_residual": rh,
+                     "reached": bool(info["status"] == _lib.OK and rh <= TTS_TARGET)}
+        del v
+        torch.cuda.empty_cache()
+    out["mixed_relaxed_fp32"]["relax_below"] = args.tts_relax
+    s32.close()
+    return out
+
+
 def workload_config(wl, n_t):
     return {"workload": f"square{wl.n[0] + 1}x{wl.n[1] + 1}_nf{wl.nf}_np{wl.n_p}_gmres{RESTART}_cycle",
             "step": "one GMRES(20) cycle from zero: b = Pi(0), 20 Arnoldi steps, update, residual check",
@@ -1107,7 +1182,8 @@ def main():
                "h2d_bytes_per_step": 2 * N * WORD, "d2h_bytes_per_step": N * WORD,
                "note": "forcing and initial guess copied from pinned host memory, solution read back, every step"}
 
-    tts = None
+    tts = None if args.no_tts else time_to_solution(args, wl, f_dev, stream, solver)
+    solve = None
     if args.solve:
         with torch.cuda.stream(stream):
             v.zero_()
@@ -1115,10 +1191,10 @@ def main():
         t0 = time.perf_counter()
         info = solver.solve_gmres(v, restart=SOLVE_MAX_ITERS, tol=TOL, max_iters=SOLVE_MAX_ITERS,
                                   raise_on_error=False)
-        tts = {"seconds": round(time.perf_counter() - t0, 3), "tol": TOL, "restart": "none",
-               "converged": info["status"] == M._lib.OK, "iterations": info["iterations"],
-               "rel_residual": info["rel_residual"],
-               "max_helmholtz_residual": float(np.max(info["helmholtz_residual"]))}
+        solve = {"seconds": round(time.perf_counter() - t0, 3), "tol": TOL, "restart": "none",
+                 "converged": info["status"] == M._lib.OK, "iterations": info["iterations"],
+                 "rel_residual": info["rel_residual"],
+                 "max_helmholtz_residual": float(np.max(info["helmholtz_residual"]))}
 
     fp32 = None if args.no_fp32 else fp32_leg(args, wl, f_dev, stream, n_t)
 
@@ -1155,6 +1231,7 @@ def main():
                   "rel_residual_after_cycle": infos[-1][0]["rel_residual"],
                   "max_helmholtz_residual": float(np.max(infos[-1][0]["helmholtz_residual"]))},
         "time_to_solution": tts,
+        "unrestarted_solve_1e-8": solve,
         "fp32": fp32,
     }
     if not args.no_cpu_baseline and world == 1:

@@ -261,6 +261,19 @@ mfwh_status mfwh_solve_refined(mfwh_handle_t h, int restart, double inner_tol, i
                                double target, int max_refinements, double* v,
                                mfwh_solve_info* info);
 
+/* Mixed-precision solve with relaxed products: mfwh_solve_refined whose every inner GMRES
+ * starts with FP64 wave solves and switches to the handle's FP32 wave solves once its Arnoldi
+ * residual estimate falls below relax_below (0 < relax_below < 1) times the norm of that inner
+ * right-hand side; each restart cycle starts again in FP64.  This is an inexact Krylov method
+ * whose products may lose accuracy as the residual falls (the relaxation strategies of
+ * Simoncini and Szyld, SIAM J. Sci. Comput. 2003, and of Bouras and Fraysse, SIAM J. Matrix
+ * Anal. Appl. 2005); the paper itself uses FP64 throughout.  h: an FP32 handle
+ * (MFWH_PREC_FP32_KAHAN or MFWH_PREC_FP32_BLOCKSUM), else MFWH_ERR_INVALID_ARG.  Other
+ * arguments and results as for mfwh_solve_refined.  Synchronous. */
+mfwh_status mfwh_solve_relaxed(mfwh_handle_t h, int restart, double inner_tol, double relax_below,
+                               int max_iters, double target, int max_refinements, double* v,
+                               mfwh_solve_info* info);
+
 /* ---- many problems: graphs, batches, autotuning (batched workloads; the paper
  * solves one problem at a time) ---------------------------------------------------- */
 
@@ -287,6 +300,26 @@ mfwh_status mfwh_set_graphs(mfwh_handle_t h, int enable);
 mfwh_status mfwh_solve_batch(const mfwh_handle_t* handles, int count, int restart, double tol,
                              int max_iters, double* const* v, mfwh_solve_info* infos,
                              double* seconds);
+
+/* Lockstep batch: GMRES(restart) as mfwh_solve_gmres (spurious_tol 0) on count independent
+ * problems whose every application of the map is one CUDA-graph launch across the batch.  The
+ * problems advance together: each round applies the map once to every problem that has not
+ * finished (b = Pi(0) in the first round, then one product (I - S) u per round: u a problem's
+ * newest Arnoldi vector, or its iterate at the start of a restart cycle), all as one launch of a
+ * graph whose independent branches are the problems' captured wave solves; between launches
+ * each problem's Gram-Schmidt passes and Givens update run on `stream`, with one
+ * synchronisation per pass for the whole batch.  The graph is rebuilt when the set of
+ * unfinished problems changes.  Handles must be explicit (MFWH_TIME_EXPLICIT), distinct and on
+ * the current device; each is put in CUDA-graph mode (mfwh_set_graphs) if it is not.
+ * v[i]: host or device [nf][points] of problem i; in: initial guess, out: solution.  infos may
+ * be NULL; seconds[i] (host, may be NULL) receives the time from the start to the end of the
+ * round in which problem i finished.  stream: cudaStream_t of the batch (NULL = legacy default
+ * stream); it waits for each handle's stream at the start, and each handle's stream waits for
+ * it at the end.  Returns MFWH_OK when every problem converged, else the first hard error, else
+ * MFWH_ERR_NOT_CONVERGED, with the problem index in mfwh_last_error().  Synchronous. */
+mfwh_status mfwh_solve_batch_graph(const mfwh_handle_t* handles, int count, int restart,
+                                   double tol, int max_iters, double* const* v,
+                                   mfwh_solve_info* infos, double* seconds, void* stream);
 
 /* Autotuner for the blocked wave kernels.  Times the first steps (at most 96) of a
  * homogeneous wave solve of prob on the current device for each candidate temporal depth and

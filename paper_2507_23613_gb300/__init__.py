@@ -172,6 +172,29 @@ def solve_batch(solvers, vs, restart=20, tol=1e-8, max_iters=1000, raise_on_erro
     return st, out, secs
 
 
+def solve_batch_graph(solvers, vs, restart=20, tol=1e-8, max_iters=1000, stream=None,
+                      raise_on_error=True):
+    """Lockstep GMRES of independent problems, one CUDA-graph launch per application of the map
+    across the batch (mfwh_solve_batch_graph).  Returns (status, info dicts, seconds)."""
+    n = len(solvers)
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    hs = (C.c_void_p * n)(*[s._handle.value for s in solvers])
+    ptrs = (C.c_void_p * n)(*[_as_ptr(v).value for v in vs])
+    infos = (_lib.SolveInfo * n)()
+    secs = np.zeros(n)
+    st = _lib.load().mfwh_solve_batch_graph(hs, n, int(restart), float(tol), int(max_iters), ptrs,
+                                            infos, _dptr(secs), C.c_void_p(stream))
+    if raise_on_error:
+        _lib.check(st)
+    out = [{"iterations": infos[i].iterations, "pi_applications": infos[i].pi_applications,
+            "restarts": infos[i].restarts, "rel_residual": infos[i].rel_residual,
+            "helmholtz_residual": np.array(infos[i].helmholtz_residual[:solvers[i].nf])}
+           for i in range(n)]
+    return st, out, secs
+
+
 def setup_arrays(s):
     """numpy views of an mfwh_setup's tables, trimmed to nf."""
     nf = s.nf
@@ -258,6 +281,30 @@ class Solver:
         st = _lib.load().mfwh_solve_refined(self._handle, int(restart), float(inner_tol),
                                             int(max_iters), float(target), int(max_refinements),
                                             _as_ptr(v), C.byref(info))
+        if raise_on_error:
+            _lib.check(st)
+        return {
+            "status": st,
+            "iterations": info.iterations,
+            "pi_applications": info.pi_applications,
+            "restarts": info.restarts,
+            "refinements": info.refinements,
+            "rel_residual": info.rel_residual,
+            "helmholtz_residual": np.array(info.helmholtz_residual[:self.nf]),
+            "history": hist[:info.history_len].copy(),
+        }
+
+    def solve_relaxed(self, v, target=1e-6, inner_tol=1e-6, relax_below=1e-2, restart=200,
+                      max_iters=1000, max_refinements=8, history=512, raise_on_error=True):
+        """Refinement whose inner solves switch from FP64 to FP32 products once their residual
+        is below relax_below (mfwh_solve_relaxed; FP32 handles)."""
+        info = _lib.SolveInfo()
+        hist = np.zeros(max(history, 1))
+        info.history_capacity = history
+        info.history = _dptr(hist)
+        st = _lib.load().mfwh_solve_relaxed(self._handle, int(restart), float(inner_tol),
+                                            float(relax_below), int(max_iters), float(target),
+                                            int(max_refinements), _as_ptr(v), C.byref(info))
         if raise_on_error:
             _lib.check(st)
         return {

@@ -118,9 +118,14 @@ _SIGNATURES = {
                                    C.c_void_p, C.POINTER(SolveInfo)]),
     "mfwh_solve_refined": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_double,
                                      C.c_int, C.c_void_p, C.POINTER(SolveInfo)]),
+    "mfwh_solve_relaxed": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_int,
+                                     C.c_double, C.c_int, C.c_void_p, C.POINTER(SolveInfo)]),
     "mfwh_set_graphs": (C.c_int, [C.c_void_p, C.c_int]),
     "mfwh_solve_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_double, C.c_int,
                                    C.POINTER(C.c_void_p), C.POINTER(SolveInfo), _dp]),
+    "mfwh_solve_batch_graph": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_double,
+                                         C.c_int, C.POINTER(C.c_void_p), C.POINTER(SolveInfo),
+                                         _dp, C.c_void_p]),
     "mfwh_autotune": (C.c_int, [C.POINTER(Problem), C.c_void_p, C.POINTER(C.c_int),
                                 C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "mfwh_cnn_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_void_p,

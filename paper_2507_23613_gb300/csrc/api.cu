@@ -623,8 +623,21 @@ mfwh_status stage_in(mfwh_handle_t h, const double* v, double** dev, bool* on_de
 
 // GMRES(restart) on (I - S) x = Pi(0) for a device iterate x, counting into I (which it
 // does not reset).  *converged reports whether the Arnoldi residual fell below tol.
+// relax_below > 0 (relaxed products, FP32 handles only): the products start with FP64 wave
+// solves and switch to the handle's FP32 wave solves once the Arnoldi residual estimate is
+// below relax_below times ||rhs|| (an inexact Krylov method whose later products may be less
+// accurate); the handle's wave precision is restored on return.
 mfwh_status gmres_core(mfwh_handle_t h, int restart, double tol, int max_iters, double* x,
-                       const double* rhs, mfwh_solve_info& I, bool* converged_out) {
+                       const double* rhs, mfwh_solve_info& I, bool* converged_out,
+                       double relax_below = 0.0) {
+  const bool relax = relax_below > 0.0 && h->plan.precision != MFWH_PREC_FP64;
+  const bool use32_saved = h->use32;
+  if (relax) h->use32 = false;
+  struct Restore {
+    mfwh_handle_t h;
+    bool v;
+    ~Restore() { h->use32 = v; }
+  } restore_use32{h, use32_saved};
   const int64_t N = h->N;
   cudaStream_t s = h->stream;
   const int it0 = I.iterations;
@@ -657,6 +670,7 @@ mfwh_status gmres_core(mfwh_handle_t h, int restart, double tol, int max_iters, 
   while (!converged && I.iterations - it0 < max_iters) {
     double* V0 = h->basis;
     I.restarts++;
+    if (relax) h->use32 = false;   // every cycle's residual and first products in FP64
     if (x_nonzero) {   // r = b - (x - S x)
       st = apply_pi(h, x, V0, 0, x);
       if (st != MFWH_OK) return st;
@@ -719,6 +733,7 @@ mfwh_status gmres_core(mfwh_handle_t h, int restart, double tol, int max_iters, 
       g[j] = cs[j] * g[j];
       res = std::fabs(g[j + 1]);
       if (I.history && I.history_len < I.history_capacity) I.history[I.history_len++] = res / bnorm;
+      if (relax && !h->use32 && res / bnorm < relax_below) h->use32 = true;
       j_done = j + 1;
       if (res / bnorm < tol || I.iterations - it0 >= max_iters || hnext == 0.0) break;
       launch_axpby(w, 1.0 / hnext, w, 0.0, N, s);
@@ -1173,9 +1188,15 @@ mfwh_status mfwh_solve_gmres(mfwh_handle_t h, int restart, double tol, int max_i
   return MFWH_OK;
 }
 
-mfwh_status mfwh_solve_refined(mfwh_handle_t h, int restart, double inner_tol, int max_iters,
-                               double target, int max_refinements, double* v,
-                               mfwh_solve_info* info) {
+}  // extern "C"
+
+namespace {
+
+// Iterative refinement with FP64 outer residuals (mfwh_solve_refined); relax_below > 0 makes
+// each inner solve a relaxed one (FP64 products first, then FP32: see gmres_core).
+mfwh_status refine_core(mfwh_handle_t h, int restart, double inner_tol, int max_iters,
+                        double target, int max_refinements, double* v, mfwh_solve_info* info,
+                        double relax_below) {
   if (!h || !v) return fail(MFWH_ERR_INVALID_ARG, "null argument");
   if (restart < 1 || restart > kMaxRestart)
     return fail(MFWH_ERR_INVALID_ARG, "restart must be in 1..1023");
@@ -1243,7 +1264,8 @@ mfwh_status mfwh_solve_refined(mfwh_handle_t h, int restart, double inner_tol, i
     launch_axpby(h->vec_e, 0.0, h->vec_e, 0.0, N, s);
     h->total_launches++;
     bool conv = false;
-    st = gmres_core(h, restart, inner_tol, max_iters - I.iterations, h->vec_e, h->vec_r, I, &conv);
+    st = gmres_core(h, restart, inner_tol, max_iters - I.iterations, h->vec_e, h->vec_r, I, &conv,
+                    relax_below);
     if (st != MFWH_OK) break;
     if (!conv) inner = MFWH_ERR_NOT_CONVERGED;
     launch_axpby(x, 1.0, h->vec_e, 1.0, N, s);   // x += e
@@ -1267,6 +1289,27 @@ mfwh_status mfwh_solve_refined(mfwh_handle_t h, int restart, double inner_tol, i
     return fail(MFWH_ERR_NOT_CONVERGED, os.str());
   }
   return MFWH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mfwh_status mfwh_solve_refined(mfwh_handle_t h, int restart, double inner_tol, int max_iters,
+                               double target, int max_refinements, double* v,
+                               mfwh_solve_info* info) {
+  return refine_core(h, restart, inner_tol, max_iters, target, max_refinements, v, info, 0.0);
+}
+
+mfwh_status mfwh_solve_relaxed(mfwh_handle_t h, int restart, double inner_tol, double relax_below,
+                               int max_iters, double target, int max_refinements, double* v,
+                               mfwh_solve_info* info) {
+  if (h && h->plan.precision == MFWH_PREC_FP64)
+    return fail(MFWH_ERR_INVALID_ARG, "relaxed products need an FP32 handle");
+  if (!(relax_below > 0.0 && relax_below < 1.0))
+    return fail(MFWH_ERR_INVALID_ARG, "relax_below must be in (0, 1)");
+  return refine_core(h, restart, inner_tol, max_iters, target, max_refinements, v, info,
+                     relax_below);
 }
 
 mfwh_status mfwh_residual(mfwh_handle_t h, const double* v, double* r_out) {
@@ -1437,6 +1480,455 @@ mfwh_status mfwh_solve_batch(const mfwh_handle_t* handles, int count, int restar
     if (status[i] != MFWH_OK) {
       set_error("problem " + std::to_string(i) + ": " + msg[i]);
       return status[i];
+    }
+  return MFWH_OK;
+}
+
+// ---- lockstep batch: one graph launch per application of the map across the batch ----
+
+}  // extern "C"
+
+namespace {
+
+// The wave solve of one handle captured (not instantiated) on its staging buffers: forced = 1,
+// no input: g_out = Pi(0); forced = 0 with input: g_out = g_in - S g_in.  *steps / *total: the
+// step-kernel and all-kernel launches one replay performs.
+mfwh_status capture_child(mfwh_handle_t h, cudaStream_t cs, int forced, cudaGraph_t* out,
+                          int64_t* steps, int64_t* total) {
+  const int saved_ev = h->ev_used;
+  const int64_t sl = h->step_launches, tl = h->total_launches;
+  h->ev_used = (int)h->ev.size();   // no timing events inside the graph
+  cudaStream_t user = h->stream;
+  CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+  h->stream = cs;
+  mfwh_status st = forced ? apply_pi_direct(h, nullptr, h->g_out, 1, nullptr)
+                          : apply_pi_direct(h, h->g_in, h->g_out, 0, h->g_in);
+  h->stream = user;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &g);
+  h->ev_used = saved_ev;
+  *steps = h->step_launches - sl;
+  *total = h->total_launches - tl;
+  h->step_launches = sl;
+  h->total_launches = tl;
+  if (st != MFWH_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture (batch)");
+  *out = g;
+  return MFWH_OK;
+}
+
+// GMRES(restart) state of one problem of a lockstep batch (the steps of gmres_core, split at
+// each application of the map).
+struct LockstepProblem {
+  mfwh_handle_t h = nullptr;
+  cudaStream_t user_stream = nullptr;
+  bool swapped = false;                 // h->stream temporarily set to the batch stream
+  double* x = nullptr;                  // device iterate
+  double* v_user = nullptr;
+  bool on_dev = false;
+  mfwh_solve_info* I = nullptr;
+  std::vector<double> H, cs, sn, g, y, hcol, h2;
+  double bnorm = 0.0, res = 0.0;
+  int j = 0;                            // Arnoldi index in the current cycle
+  bool x_nonzero = false, converged = false, done = false, cycle_start = false;
+  mfwh_status st = MFWH_OK;
+  std::string msg;
+  double secs = 0.0;
+  cudaGraph_t child[2] = {nullptr, nullptr};   // [0]: A v on g_in, [1]: Pi(0)
+  int64_t child_steps[2] = {0, 0}, child_total[2] = {0, 0};
+  double* product_dest = nullptr;       // where this round's product goes
+};
+
+void lockstep_fail(LockstepProblem& P, mfwh_status st) {
+  P.st = st;
+  P.msg = g_error;
+  P.done = true;
+}
+
+// Parent graph with one child node per listed problem (variant k), instantiated.
+mfwh_status batch_graph(std::vector<LockstepProblem>& Ps, const std::vector<int>& idx, int k,
+                        cudaGraphExec_t* exec) {
+  cudaGraph_t parent = nullptr;
+  CK(cudaGraphCreate(&parent, 0));
+  for (int i : idx) {
+    cudaGraphNode_t node;
+    cudaError_t e = cudaGraphAddChildGraphNode(&node, parent, nullptr, 0, Ps[i].child[k]);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(parent);
+      return cuda_fail(e, "cudaGraphAddChildGraphNode");
+    }
+  }
+  cudaError_t e = cudaGraphInstantiate(exec, parent, 0);
+  cudaGraphDestroy(parent);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate (batch)");
+  return MFWH_OK;
+}
+
+// Queue the dot products <V_i, w> (i < k) of problem P into its pinned buffer at offset off.
+mfwh_status queue_dots(LockstepProblem& P, const double* V, int k, const double* w, int off) {
+  mfwh_handle_t h = P.h;
+  launch_multidot(V, h->N, k, w, h->N, h->dot_partial, h->dot_out, h->stream);
+  h->total_launches += multidot_launches(k);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(h->pinned + off, h->dot_out, sizeof(double) * k, cudaMemcpyDeviceToHost,
+                     h->stream));
+  return MFWH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mfwh_status mfwh_solve_batch_graph(const mfwh_handle_t* handles, int count, int restart,
+                                   double tol, int max_iters, double* const* v,
+                                   mfwh_solve_info* infos, double* seconds, void* stream) {
+  if (!handles || !v || count < 1) return fail(MFWH_ERR_INVALID_ARG, "bad batch arguments");
+  if (restart < 1 || restart > kMaxRestart || max_iters < 1 || !(tol >= 0.0))
+    return fail(MFWH_ERR_INVALID_ARG, "bad restart, max_iters or tol");
+  if (restart > max_iters) restart = max_iters;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  for (int i = 0; i < count; ++i) {
+    if (!handles[i] || !v[i]) return fail(MFWH_ERR_INVALID_ARG, "null handle or buffer in batch");
+    if (handles[i]->implicit)
+      return fail(MFWH_ERR_INVALID_ARG, "lockstep batches take explicit handles only");
+    if (handles[i]->device != dev)
+      return fail(MFWH_ERR_INVALID_ARG, "every handle must be on the current device");
+    for (int j = 0; j < i; ++j)
+      if (handles[j] == handles[i]) return fail(MFWH_ERR_INVALID_ARG, "a handle appears twice");
+  }
+  cudaStream_t bs = static_cast<cudaStream_t>(stream);
+  std::vector<LockstepProblem> Ps(count);
+  std::vector<mfwh_solve_info> local(count);
+  mfwh_status st = MFWH_OK;
+  for (int i = 0; i < count; ++i) {
+    LockstepProblem& P = Ps[i];
+    P.h = handles[i];
+    P.v_user = v[i];
+    P.I = infos ? &infos[i] : &local[i];
+    const int cap = P.I->history_capacity;
+    double* hist = P.I->history;
+    *P.I = mfwh_solve_info{};
+    P.I->history_capacity = cap;
+    P.I->history = hist;
+    P.I->rel_residual = NAN;
+    if (!P.h->graphs) {
+      st = mfwh_set_graphs(P.h, 1);
+      if (st != MFWH_OK) return st;
+    }
+    st = ensure_basis(P.h, restart + 1);
+    if (st != MFWH_OK) return st;
+    reset_timing(P.h);
+    P.H.assign((restart + 1) * restart, 0.0);
+    P.cs.assign(restart, 0.0);
+    P.sn.assign(restart, 0.0);
+    P.g.assign(restart + 1, 0.0);
+    P.y.assign(restart, 0.0);
+    P.hcol.assign(restart + 1, 0.0);
+    P.h2.assign(restart + 1, 0.0);
+  }
+  // Every handle's earlier work completes before the batch stream uses its buffers.
+  cudaEvent_t ev = nullptr;
+  CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  for (auto& P : Ps) {
+    CK(cudaEventRecord(ev, P.h->stream));
+    CK(cudaStreamWaitEvent(bs, ev, 0));
+  }
+  cudaStream_t cap = nullptr;
+  CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  auto restore = [&]() {
+    for (auto& P : Ps) {
+      if (P.swapped) P.h->stream = P.user_stream;
+      P.swapped = false;
+      for (auto& c : P.child)
+        if (c) cudaGraphDestroy(c);
+    }
+    cudaEventRecord(ev, bs);
+    for (auto& P : Ps) cudaStreamWaitEvent(P.h->stream, ev, 0);
+    cudaEventDestroy(ev);
+    if (cap) cudaStreamDestroy(cap);
+  };
+  for (auto& P : Ps) {
+    for (int k = 0; k < 2 && st == MFWH_OK; ++k)
+      st = capture_child(P.h, cap, k, &P.child[k], &P.child_steps[k], &P.child_total[k]);
+    if (st != MFWH_OK) {
+      restore();
+      return st;
+    }
+    P.user_stream = P.h->stream;
+    P.h->stream = bs;
+    P.swapped = true;
+    st = stage_in(P.h, P.v_user, &P.x, &P.on_dev);
+    if (st != MFWH_OK) {
+      restore();
+      return st;
+    }
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  auto elapsed = [&]() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  };
+  auto sync = [&]() -> mfwh_status {
+    CK(cudaStreamSynchronize(bs));
+    return MFWH_OK;
+  };
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  std::vector<int> exec_set[2];
+  auto launch_round = [&](const std::vector<int>& idx, int k) -> mfwh_status {
+    if (!exec[k] || exec_set[k] != idx) {
+      if (exec[k]) cudaGraphExecDestroy(exec[k]);
+      exec[k] = nullptr;
+      mfwh_status s2 = batch_graph(Ps, idx, k, &exec[k]);
+      if (s2 != MFWH_OK) return s2;
+      exec_set[k] = idx;
+    }
+    CK(cudaGraphLaunch(exec[k], bs));
+    for (int i : idx) {
+      LockstepProblem& P = Ps[i];
+      P.h->step_launches += P.child_steps[k];
+      P.h->total_launches += P.child_total[k];
+      P.I->pi_applications++;
+    }
+    return MFWH_OK;
+  };
+
+  // Round 0: b = Pi(0) for every problem, ||b||, ||x||.
+  std::vector<int> all(count);
+  for (int i = 0; i < count; ++i) all[i] = i;
+  st = launch_round(all, 1);
+  for (auto& P : Ps) {
+    if (st != MFWH_OK) break;
+    CK(cudaMemcpyAsync(P.h->vec_b, P.h->g_out, sizeof(double) * P.h->N,
+                       cudaMemcpyDeviceToDevice, bs));
+    st = queue_dots(P, P.h->vec_b, 1, P.h->vec_b, 0);
+    if (st == MFWH_OK) st = queue_dots(P, P.x, 1, P.x, 1);
+  }
+  if (st == MFWH_OK) st = sync();
+  for (auto& P : Ps) {
+    if (st != MFWH_OK) break;
+    P.bnorm = std::sqrt(P.h->pinned[0]);
+    const double xx = P.h->pinned[1];
+    if (!std::isfinite(P.bnorm) || !std::isfinite(xx)) {
+      set_error("non-finite right-hand side or initial guess");
+      lockstep_fail(P, MFWH_ERR_NONFINITE);
+      continue;
+    }
+    P.x_nonzero = xx > 0.0;
+    P.cycle_start = true;
+    if (P.bnorm == 0.0) {
+      launch_axpby(P.x, 0.0, P.x, 0.0, P.h->N, bs);
+      P.converged = P.done = true;
+      P.I->rel_residual = 0.0;
+    }
+  }
+
+  // Arnoldi rounds: every active problem needs exactly one product A u (u = x at the start
+  // of a cycle from a non-zero iterate, else its newest basis vector).
+  while (st == MFWH_OK) {
+    // start of cycle from x = 0: V_0 = b without a product
+    for (auto& P : Ps) {
+      if (P.done || !P.cycle_start || P.x_nonzero) continue;
+      P.I->restarts++;
+      launch_axpby(P.h->basis, 1.0, P.h->vec_b, 0.0, P.h->N, bs);
+      P.h->total_launches++;
+      st = queue_dots(P, P.h->basis, 1, P.h->basis, 0);
+      if (st != MFWH_OK) break;
+    }
+    if (st != MFWH_OK || (st = sync()) != MFWH_OK) break;
+    for (auto& P : Ps) {
+      if (P.done || !P.cycle_start || P.x_nonzero) continue;
+      const double beta = std::sqrt(P.h->pinned[0]);
+      P.cycle_start = false;
+      P.I->rel_residual = beta / P.bnorm;
+      if (!std::isfinite(beta)) {
+        set_error("non-finite Krylov residual");
+        lockstep_fail(P, MFWH_ERR_NONFINITE);
+        continue;
+      }
+      if (P.I->rel_residual < tol) {
+        P.converged = P.done = true;
+        continue;
+      }
+      launch_axpby(P.h->basis, 1.0 / beta, P.h->basis, 0.0, P.h->N, bs);
+      P.h->total_launches++;
+      std::fill(P.g.begin(), P.g.end(), 0.0);
+      P.g[0] = beta;
+      P.res = beta;
+      P.j = 0;
+    }
+    std::vector<int> active;
+    for (int i = 0; i < count; ++i)
+      if (!Ps[i].done) active.push_back(i);
+    if (active.empty()) break;
+    // inputs into the staging buffers, one graph launch, products out
+    for (int i : active) {
+      LockstepProblem& P = Ps[i];
+      const double* u = P.cycle_start ? P.x : P.h->basis + (int64_t)P.j * P.h->N;
+      P.product_dest = P.cycle_start ? P.h->basis : P.h->basis + (int64_t)(P.j + 1) * P.h->N;
+      CK(cudaMemcpyAsync(P.h->g_in, u, sizeof(double) * P.h->N, cudaMemcpyDeviceToDevice, bs));
+    }
+    st = launch_round(active, 0);
+    if (st != MFWH_OK) break;
+    for (int i : active) {
+      LockstepProblem& P = Ps[i];
+      CK(cudaMemcpyAsync(P.product_dest, P.h->g_out, sizeof(double) * P.h->N,
+                         cudaMemcpyDeviceToDevice, bs));
+      if (P.cycle_start) {   // r = b - (x - S x)
+        P.I->restarts++;
+        launch_axpby(P.h->basis, 1.0, P.h->vec_b, -1.0, P.h->N, bs);
+        P.h->total_launches++;
+        st = queue_dots(P, P.h->basis, 1, P.h->basis, 0);
+      } else {               // classical Gram-Schmidt, first pass
+        P.I->iterations++;
+        st = queue_dots(P, P.h->basis, P.j + 1, P.product_dest, 0);
+      }
+      if (st != MFWH_OK) break;
+    }
+    if (st != MFWH_OK || (st = sync()) != MFWH_OK) break;
+    // second Gram-Schmidt pass (Arnoldi problems)
+    for (int i : active) {
+      LockstepProblem& P = Ps[i];
+      if (P.cycle_start) continue;
+      std::memcpy(P.hcol.data(), P.h->pinned, sizeof(double) * (P.j + 1));
+      launch_multi_axpy(P.product_dest, P.h->basis, P.h->N, P.j + 1, P.hcol.data(), P.h->N, bs);
+      P.h->total_launches += multi_axpy_launches(P.j + 1);
+      st = queue_dots(P, P.h->basis, P.j + 1, P.product_dest, 0);
+      if (st != MFWH_OK) break;
+    }
+    if (st != MFWH_OK || (st = sync()) != MFWH_OK) break;
+    for (int i : active) {
+      LockstepProblem& P = Ps[i];
+      if (P.cycle_start) continue;
+      std::memcpy(P.h2.data(), P.h->pinned, sizeof(double) * (P.j + 1));
+      launch_multi_axpy(P.product_dest, P.h->basis, P.h->N, P.j + 1, P.h2.data(), P.h->N, bs);
+      P.h->total_launches += multi_axpy_launches(P.j + 1);
+      for (int k = 0; k <= P.j; ++k) P.hcol[k] += P.h2[k];
+      st = queue_dots(P, P.product_dest, 1, P.product_dest, 0);
+      if (st != MFWH_OK) break;
+    }
+    if (st != MFWH_OK || (st = sync()) != MFWH_OK) break;
+    // Givens rotations, convergence, end of cycle
+    for (int i : active) {
+      LockstepProblem& P = Ps[i];
+      const int64_t N = P.h->N;
+      if (P.cycle_start) {
+        const double beta = std::sqrt(P.h->pinned[0]);
+        P.cycle_start = false;
+        if (!std::isfinite(beta)) {
+          set_error("non-finite Krylov residual");
+          lockstep_fail(P, MFWH_ERR_NONFINITE);
+          continue;
+        }
+        P.I->rel_residual = beta / P.bnorm;
+        if (P.I->rel_residual < tol) {
+          P.converged = P.done = true;
+          continue;
+        }
+        launch_axpby(P.h->basis, 1.0 / beta, P.h->basis, 0.0, N, bs);
+        P.h->total_launches++;
+        std::fill(P.g.begin(), P.g.end(), 0.0);
+        P.g[0] = beta;
+        P.res = beta;
+        P.j = 0;
+        continue;
+      }
+      const int j = P.j;
+      const double hnext = std::sqrt(P.h->pinned[0]);
+      if (!std::isfinite(hnext)) {
+        set_error("non-finite Arnoldi vector");
+        lockstep_fail(P, MFWH_ERR_NONFINITE);
+        continue;
+      }
+      std::vector<double>& hc = P.hcol;
+      for (int k = 0; k < j; ++k) {
+        const double t = P.cs[k] * hc[k] + P.sn[k] * hc[k + 1];
+        hc[k + 1] = -P.sn[k] * hc[k] + P.cs[k] * hc[k + 1];
+        hc[k] = t;
+      }
+      const double r = std::hypot(hc[j], hnext);
+      P.cs[j] = r > 0.0 ? hc[j] / r : 1.0;
+      P.sn[j] = r > 0.0 ? hnext / r : 0.0;
+      hc[j] = r;
+      for (int k = 0; k <= j; ++k) P.H[k * restart + j] = hc[k];
+      P.g[j + 1] = -P.sn[j] * P.g[j];
+      P.g[j] = P.cs[j] * P.g[j];
+      P.res = std::fabs(P.g[j + 1]);
+      mfwh_solve_info& I = *P.I;
+      if (I.history && I.history_len < I.history_capacity)
+        I.history[I.history_len++] = P.res / P.bnorm;
+      const bool end = P.res / P.bnorm < tol || I.iterations >= max_iters || hnext == 0.0 ||
+                       j + 1 == restart;
+      if (!end) {
+        launch_axpby(P.product_dest, 1.0 / hnext, P.product_dest, 0.0, N, bs);
+        P.h->total_launches++;
+        P.j = j + 1;
+        continue;
+      }
+      // y = R^{-1} g, x += V y
+      const int jd = j + 1;
+      for (int k = jd - 1; k >= 0; --k) {
+        double acc = P.g[k];
+        for (int l = k + 1; l < jd; ++l) acc -= P.H[k * restart + l] * P.y[l];
+        P.y[k] = acc / P.H[k * restart + k];
+      }
+      for (int k = 0; k < jd; ++k) P.y[k] = -P.y[k];   // multi_axpy subtracts
+      launch_multi_axpy(P.x, P.h->basis, N, jd, P.y.data(), N, bs);
+      P.h->total_launches += multi_axpy_launches(jd);
+      P.x_nonzero = true;
+      I.rel_residual = P.res / P.bnorm;
+      if (I.rel_residual < tol) {
+        P.converged = P.done = true;
+      } else if (I.iterations >= max_iters) {
+        P.done = true;
+      } else {
+        P.cycle_start = true;
+      }
+    }
+    for (int i : active)
+      if (Ps[i].done) Ps[i].secs = elapsed();
+  }
+  for (auto& e2 : exec)
+    if (e2) cudaGraphExecDestroy(e2);
+  // Helmholtz residuals and results back to the caller's buffers.
+  if (st == MFWH_OK) {
+    for (auto& P : Ps) {
+      if (P.st != MFWH_OK) continue;
+      double r[MFWH_MAX_NF];
+      mfwh_status rs = residual_dev(P.h, P.x, r);
+      for (int m = 0; m < P.h->nf; ++m) P.I->helmholtz_residual[m] = rs == MFWH_OK ? r[m] : NAN;
+      if (rs != MFWH_OK) lockstep_fail(P, rs);
+      if (!P.on_dev)
+        CK(cudaMemcpyAsync(P.v_user, P.x, sizeof(double) * P.h->N, cudaMemcpyDeviceToHost, bs));
+    }
+    if (st == MFWH_OK) st = sync();
+    // a bounded wait inside a wave kernel that ran out fails that problem
+    for (auto& P : Ps) {
+      if (st != MFWH_OK || P.st != MFWH_OK) continue;
+      mfwh_status ts = collect_timing(P.h);
+      if (ts != MFWH_OK) lockstep_fail(P, ts);
+    }
+  }
+  const double t_end = elapsed();
+  restore();
+  if (st != MFWH_OK) return st;
+  for (int i = 0; i < count; ++i) {
+    if (Ps[i].secs == 0.0) Ps[i].secs = t_end;
+    if (seconds) seconds[i] = Ps[i].secs;
+  }
+  for (int i = 0; i < count; ++i)
+    if (Ps[i].st != MFWH_OK) {
+      set_error("problem " + std::to_string(i) + ": " + Ps[i].msg);
+      return Ps[i].st;
+    }
+  for (int i = 0; i < count; ++i)
+    if (!Ps[i].converged) {
+      std::ostringstream os;
+      os << "problem " << i << ": GMRES stopped after " << Ps[i].I->iterations
+         << " iterations at relative residual " << Ps[i].I->rel_residual;
+      return fail(MFWH_ERR_NOT_CONVERGED, os.str());
     }
   return MFWH_OK;
 }

@@ -36,17 +36,17 @@ __device__ __forceinline__ double fpair_value(float2 q) { return (double)q.x + (
 //       rounding carries |hi| into the next binade), converted to float and scaled.
 // hi + lo equals v to within 2^-48 |v|, as for fpair_from (which it matches except on exact
 // ties), for |v| from about 2^-101 (below, lo is a subnormal float and the pair keeps 2^-150
-// absolute) to 2^116.  |v| below 2^-126 gives (0, 0); |v| of 2^116 and more, infinities and
-// NaN take fpair_from.
+// absolute) to 2^116.  |v| below 2^-126 gives (0, 0); |v| of 2^116 and more gives an infinite
+// hi, and NaN a NaN hi (so that non-finite sums still show).  No branch: every path is a
+// select, so no FP64 instruction is issued, not even predicated off.
 __device__ __forceinline__ float2 fpair_split(double v) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
   const unsigned long long a = bits & 0x7FFFFFFFFFFFFFFFull;
   const unsigned long long h = (a + (1ull << 28)) & ~((1ull << 29) - 1ull);
   const int eh = (int)(h >> 52);
-  if (eh > 1138) return fpair_from(v);
   const int ev = (int)(a >> 52);
   const unsigned sgn = (unsigned)(bits >> 32) & 0x80000000u;
-  const float hi = __uint_as_float(((unsigned)(h >> 29) - (896u << 23)) | sgn);
+  const unsigned hb = ((unsigned)(h >> 29) - (896u << 23)) | sgn;
   const int d = (int)((unsigned)a - (unsigned)h);
   // lo = d 2^k, k = ev - 1075, as d 2^kk (kk = k, or k + 64 when 2^k is not a normal float)
   // times 2^(k - kk): both factors are normal floats for 885 <= ev <= 1138 and d 2^kk stays
@@ -57,7 +57,12 @@ __device__ __forceinline__ float2 fpair_split(double v) {
   const float mag = ((float)d * __uint_as_float((unsigned)(kk + 127) << 23)) *
                     (low ? 0x1p-64f : 1.0f);
   const float lo = __uint_as_float(__float_as_uint(mag) ^ sgn);
-  return eh < 897 ? make_float2(0.0f, 0.0f) : make_float2(hi, lo);
+  // |v| >= 2^116, infinity or NaN: hi = +-inf, or a NaN for NaN
+  const bool nan = ev == 2047 && (a & 0x000FFFFFFFFFFFFFull) != 0;
+  const unsigned big = sgn | 0x7F800000u | (nan ? 0x00400000u : 0u);
+  const float hi = __uint_as_float(eh > 1138 ? big : hb);
+  const bool zero = eh < 897 || eh > 1138;
+  return make_float2(eh < 897 ? 0.0f : hi, zero ? 0.0f : lo);
 }
 
 // q + (wh + wl)(xh + xl) as a renormalised pair.

@@ -85,9 +85,9 @@ __device__ __forceinline__ PointIndex point_index(const Geom& g) {
 // New wave level at an interior point (the leapfrog update with the composite forcing).
 // ORDER 4 adds the second neighbours along each axis; beyond the boundary the ghost value is
 // minus the centre point (odd reflection of homogeneous Dirichlet data).  With a c^2 field
-// (g.c2f) the coefficients are those of c = 1 and the operator's terms are scaled by c_j^2:
+// (FIELD, g.c2f) the coefficients are those of c = 1 and the operator's terms are scaled by c_j^2:
 // W^{n+1} = a_cur W^n - W^{n-1} + c_j^2 (A0 W^n + Ax sx + ... - a_cur W^n).
-template <int NF, int DIM, int ORDER>
+template <int NF, int DIM, int ORDER, bool FIELD, bool FORCED>
 __device__ __forceinline__ double leapfrog_point(const double* __restrict__ Wc,
                                                  const double* __restrict__ Wp,
                                                  const double* __restrict__ f,
@@ -102,8 +102,10 @@ __device__ __forceinline__ double leapfrog_point(const double* __restrict__ Wc,
   const double wc = Wc[p];
   const double sx = Wc[p - 1] + Wc[p + 1];
   const double sy = Wc[p - g.sy] + Wc[p + g.sy];
-  const bool field = g.c2f != nullptr;
-  double acc = field ? (A0 - a.acur) * wc : (a.first ? A0 * wc : fma(A0, wc, -Wp[p]));
+  // W^{n-1} is absent on the first step: a zero operand (not a second FP64 instruction under
+  // a predicate) keeps one FP64 FMA per point; fma(A0, wc, -0) rounds exactly as A0 * wc
+  const double wprev = a.first ? 0.0 : Wp[p];
+  double acc = FIELD ? (A0 - a.acur) * wc : fma(A0, wc, -wprev);
   acc = fma(Ax, sx, acc);
   acc = fma(Ay, sy, acc);
   if (DIM == 3) {
@@ -124,8 +126,8 @@ __device__ __forceinline__ double leapfrog_point(const double* __restrict__ Wc,
       acc = fma(Bz, tz, acc);
     }
   }
-  if (field) acc = fma(g.c2f[p], acc, a.first ? a.acur * wc : fma(a.acur, wc, -Wp[p]));
-  if (a.forced) {
+  if (FIELD) acc = fma(g.c2f[p], acc, fma(a.acur, wc, -wprev));
+  if (FORCED) {
 #pragma unroll
     for (int m = 0; m < NF; ++m) acc = fma(-a.fneg[m], f[m * g.points + p], acc);
   }
@@ -148,13 +150,13 @@ k_init(const double* __restrict__ v, double* __restrict__ W0, float2* __restrict
   for (int m = 0; m < NF; ++m) q[m * g.points + x.p] = fpair_from(a.w0[m] * w);
 }
 
-template <int NF, int DIM, int ORDER>
+template <int NF, int DIM, int ORDER, bool FIELD, bool FORCED>
 __global__ void __launch_bounds__(kBX * kBY)
 k_step(const double* __restrict__ Wc, double* __restrict__ Wp, const double* __restrict__ f,
        float2* __restrict__ q, const StepParams<NF> a, const Geom g) {
   const PointIndex x = point_index<DIM>(g);
   if (!x.interior) return;           // boundary values stay 0 (Dirichlet, g = 0)
-  const double wn = leapfrog_point<NF, DIM, ORDER>(Wc, Wp, f, a, g, x);
+  const double wn = leapfrog_point<NF, DIM, ORDER, FIELD, FORCED>(Wc, Wp, f, a, g, x);
   Wp[x.p] = wn;
   const float2 xw = fpair_split(wn);
 #pragma unroll
@@ -164,7 +166,7 @@ k_step(const double* __restrict__ Wc, double* __restrict__ Wp, const double* __r
   }
 }
 
-template <int NF, int DIM, int ORDER>
+template <int NF, int DIM, int ORDER, bool FIELD>
 __global__ void __launch_bounds__(kBX * kBY)
 k_last(const double* __restrict__ Wc, const double* __restrict__ Wp, const double* __restrict__ f,
        const float2* __restrict__ q, double* vout, const double* vsub, const LastParams<NF> a,
@@ -176,7 +178,8 @@ k_last(const double* __restrict__ Wc, const double* __restrict__ Wp, const doubl
     for (int m = 0; m < NF; ++m) vout[m * g.points + x.p] = 0.0;
     return;
   }
-  const double wn = leapfrog_point<NF, DIM, ORDER>(Wc, Wp, f, a.st, g, x);
+  const double wn = a.st.forced ? leapfrog_point<NF, DIM, ORDER, FIELD, true>(Wc, Wp, f, a.st, g, x)
+                                : leapfrog_point<NF, DIM, ORDER, FIELD, false>(Wc, Wp, f, a.st, g, x);
   double qq[NF];
 #pragma unroll
   for (int m = 0; m < NF; ++m) qq[m] = fma(a.st.wq[m], wn, fpair_value(q[m * g.points + x.p]));
@@ -313,21 +316,55 @@ void init_nf(const Geom& g, const double* v, double* W0, double* q, const double
     k_init<NF, 3><<<step_grid(g), blk, 0, st>>>(v, W0, qp, a, g);
 }
 
+// Kernel instance for the grid: dimension, operator order and whether c^2 is a field (a
+// compile-time choice, so that the constant-c kernels carry no field code at all).
+template <int NF, bool FIELD, bool FORCED>
+void step_nf_f(const Geom& g, const double* Wc, double* Wp, const double* f, float2* qp,
+               const StepParams<NF>& a, cudaStream_t st) {
+  dim3 blk(kBX, kBY);
+  if (g.order == 4) {
+    if (g.dim == 2)
+      k_step<NF, 2, 4, FIELD, FORCED><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, qp, a, g);
+    else
+      k_step<NF, 3, 4, FIELD, FORCED><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, qp, a, g);
+  } else if (g.dim == 2) {
+    k_step<NF, 2, 2, FIELD, FORCED><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, qp, a, g);
+  } else {
+    k_step<NF, 3, 2, FIELD, FORCED><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, qp, a, g);
+  }
+}
+
 template <int NF>
 void step_nf(const Geom& g, const double* Wc, double* Wp, const double* f, double* q,
              const StepHost& h, cudaStream_t st) {
   const StepParams<NF> a = to_params<NF>(h);
   float2* qp = reinterpret_cast<float2*>(q);
+  if (g.c2f) {
+    if (h.forced)
+      step_nf_f<NF, true, true>(g, Wc, Wp, f, qp, a, st);
+    else
+      step_nf_f<NF, true, false>(g, Wc, Wp, f, qp, a, st);
+  } else if (h.forced) {
+    step_nf_f<NF, false, true>(g, Wc, Wp, f, qp, a, st);
+  } else {
+    step_nf_f<NF, false, false>(g, Wc, Wp, f, qp, a, st);
+  }
+}
+
+template <int NF, bool FIELD>
+void last_nf_f(const Geom& g, const double* Wc, const double* Wp, const double* f,
+               const float2* qp, double* vout, const double* vsub, const LastParams<NF>& a,
+               cudaStream_t st) {
   dim3 blk(kBX, kBY);
   if (g.order == 4) {
     if (g.dim == 2)
-      k_step<NF, 2, 4><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, qp, a, g);
+      k_last<NF, 2, 4, FIELD><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, qp, vout, vsub, a, g);
     else
-      k_step<NF, 3, 4><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, qp, a, g);
+      k_last<NF, 3, 4, FIELD><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, qp, vout, vsub, a, g);
   } else if (g.dim == 2) {
-    k_step<NF, 2, 2><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, qp, a, g);
+    k_last<NF, 2, 2, FIELD><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, qp, vout, vsub, a, g);
   } else {
-    k_step<NF, 3, 2><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, qp, a, g);
+    k_last<NF, 3, 2, FIELD><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, qp, vout, vsub, a, g);
   }
 }
 
@@ -345,17 +382,10 @@ void last_nf(const Geom& g, const double* Wc, const double* Wp, const double* f,
   a.has_e = h.has_e && h.vprev != nullptr;
   a.vprev = h.vprev;
   const float2* qp = reinterpret_cast<const float2*>(q);
-  dim3 blk(kBX, kBY);
-  if (g.order == 4) {
-    if (g.dim == 2)
-      k_last<NF, 2, 4><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, qp, vout, vsub, a, g);
-    else
-      k_last<NF, 3, 4><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, qp, vout, vsub, a, g);
-  } else if (g.dim == 2) {
-    k_last<NF, 2, 2><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, qp, vout, vsub, a, g);
-  } else {
-    k_last<NF, 3, 2><<<step_grid(g), blk, 0, st>>>(Wc, Wp, f, qp, vout, vsub, a, g);
-  }
+  if (g.c2f)
+    last_nf_f<NF, true>(g, Wc, Wp, f, qp, vout, vsub, a, st);
+  else
+    last_nf_f<NF, false>(g, Wc, Wp, f, qp, vout, vsub, a, st);
 }
 
 // R_m = f_m - (c^2 Delta_h + omega_m^2) v_m at interior points, 0 on the boundary: the

@@ -59,16 +59,17 @@ __device__ __forceinline__ int clamp_local(int64_t v, int lo, int hi) {
 }
 
 // New level at local point l (row length EX) of a ring point: the operations of k_step in the
-// same order.  A: W^n, Wprev: W^{n-1} at l (0 before the first step).
+// same order.  A: W^n, wprev: W^{n-1} at l (0 on the first step of a wave solve, where the
+// first-step coefficients make the update W^1 = W^0 + dt^2/2 (c^2 Delta_h W^0 - F^0)).
 template <int NF, int EX, bool FORCED>
 __device__ __forceinline__ double ring_update(const double* A, double wprev, int l,
-                                              const LayerCoef& L, bool first, const double* fneg,
+                                              const LayerCoef& L, const double* fneg,
                                               const double* __restrict__ f, int64_t p,
                                               int64_t points) {
   const double wc = A[l];
   const double sx = A[l - 1] + A[l + 1];
   const double sy = A[l - EX] + A[l + EX];
-  double acc = first ? L.A0 * wc : fma(L.A0, wc, -wprev);
+  double acc = fma(L.A0, wc, -wprev);     // wprev = 0 on the first step: exactly L.A0 * wc
   acc = fma(L.Ax, sx, acc);
   acc = fma(L.Ay, sy, acc);
   if (FORCED) {
@@ -172,11 +173,13 @@ k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
     wp[k] = B[(lyo + k) * EX + lxo];
   }
 
-  // The steps in two compiled copies with the same per-point arithmetic: ALLINT for
+  // The steps in three compiled copies with the same per-point arithmetic: ALLINT for
   // homogeneous launches of CTAs whose updated points are all interior with one c^2 (no
-  // forcing terms, no per-point interior or layer tests), and the general one.
-  auto run_steps = [&](auto allint_c) {
+  // forcing terms, no per-point interior or layer tests), and the general one with and
+  // without the forcing terms (FORCED), so that no copy carries FP64 work under a predicate.
+  auto run_steps = [&](auto allint_c, auto forced_c) {
     constexpr bool ALLINT = decltype(allint_c)::value;
+    constexpr bool FORCED = decltype(forced_c)::value;
     for (int s = 0; s < a.steps; ++s) {
       const int r = a.steps - 1 - s;          // ring radius still needed after this step
       const int n = a.n0 + s;                 // computing W^{n+1}
@@ -200,10 +203,10 @@ k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
           const double dn = k == K - 1 ? below : wc[k + 1];
           const double sx = A[l - 1] + A[l + 1];
           const double sy = up + dn;
-          double acc = first ? L.A0 * wc[k] : fma(L.A0, wc[k], -wp[k]);
+          double acc = fma(L.A0, wc[k], -wp[k]);   // wp = 0 on the first step
           acc = fma(L.Ax, sx, acc);
           acc = fma(L.Ay, sy, acc);
-          if (!ALLINT && a.forced) {
+          if (FORCED) {
 #pragma unroll
             for (int m = 0; m < NF; ++m)
               acc = fma(-fneg[m], f[m * g.points + p0 + k * g.sy], acc);
@@ -240,10 +243,7 @@ k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
               (ALLINT || simple) ? (all_hi ? hi : lo) : (((lay_x ? lx : ly) >= lay_thr) ? hi : lo);
           const int l = ly * EX + lx;
           const int64_t p = (y0 + ly) * g.sy + x0 + lx;
-          if (!ALLINT && a.forced)
-            B[l] = ring_update<NF, EX, true>(A, B[l], l, L, first, fneg, f, p, g.points);
-          else
-            B[l] = ring_update<NF, EX, false>(A, B[l], l, L, first, fneg, f, p, g.points);
+          B[l] = ring_update<NF, EX, FORCED>(A, B[l], l, L, fneg, f, p, g.points);
         }
       }
       __syncthreads();
@@ -252,10 +252,12 @@ k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
       B = t;
     }
   };
-  if (simple && !a.forced)
-    run_steps(std::true_type{});
+  if (a.forced)
+    run_steps(std::false_type{}, std::true_type{});
+  else if (simple)
+    run_steps(std::true_type{}, std::false_type{});
   else
-    run_steps(std::false_type{});
+    run_steps(std::false_type{}, std::false_type{});
 
   // wc = W^{n0+steps}, wp = W^{n0+steps-1} on the strip
   if (!a.last) {

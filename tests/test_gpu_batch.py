@@ -143,3 +143,58 @@ def test_autotune_picks_a_valid_configuration():
     tb, shape, ms = M.autotune((12, 10, 8), (1.0, 1.0, 1.0), [6.0, 9.0],
                                precision=_lib.PREC_FP32_BLOCKSUM)
     assert (tb, shape) == (1, 0)
+
+
+@pytest.mark.parametrize("restart,max_iters,host", [(10, 60, False), (4, 11, True)])
+def test_lockstep_batch_matches_single_solves(restart, max_iters, host):
+    """The lockstep batch (one graph launch per application of the map across all problems)
+    runs each problem's GMRES with the same kernels in the same order as a single solve, so the
+    iterates are bit-identical; with restart 4 and 11 iterations problems restart from non-zero
+    iterates (a product of the iterate in a round) and stop unconverged; host buffers are
+    staged in and out."""
+    wls = problems()
+    precs = [_lib.PREC_FP64, _lib.PREC_FP32_BLOCKSUM, _lib.PREC_FP64, _lib.PREC_FP32_KAHAN]
+    single, singles_info = [], []
+    for k, (wl, prec) in enumerate(zip(wls, precs)):
+        s = M.Solver(wl.n, wl.length, wl.omega, dev(wl.forcing), n_p=wl.n_p, cfl=wl.cfl,
+                     precision=prec)
+        x = dev(random_v(wl, 70 + k))
+        singles_info.append(s.solve_gmres(x, restart=restart, tol=1e-9, max_iters=max_iters,
+                                          raise_on_error=False))
+        single.append(x.cpu().numpy())
+        s.close()
+    solvers = [M.Solver(wl.n, wl.length, wl.omega, dev(wl.forcing), n_p=wl.n_p, cfl=wl.cfl,
+                        precision=prec) for wl, prec in zip(wls, precs)]
+    xs = [random_v(wl, 70 + k) for k, wl in enumerate(wls)]
+    if not host:
+        xs = [dev(x) for x in xs]
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    st, infos, secs = M.solve_batch_graph(solvers, xs, restart=restart, tol=1e-9,
+                                          max_iters=max_iters, stream=side.cuda_stream,
+                                          raise_on_error=False)
+    torch.cuda.synchronize()
+    for x, ref, info, ref_info in zip(xs, single, infos, singles_info):
+        got = x if host else x.cpu().numpy()
+        assert np.array_equal(got, ref)
+        assert info["iterations"] == ref_info["iterations"]
+        assert info["pi_applications"] == ref_info["pi_applications"]
+        assert info["restarts"] == ref_info["restarts"]
+        np.testing.assert_array_equal(info["helmholtz_residual"], ref_info["helmholtz_residual"])
+    assert np.all(secs > 0)
+    want = _lib.OK if all(r["status"] == _lib.OK for r in singles_info) else _lib.ERR_NOT_CONVERGED
+    assert st == want
+    for s in solvers:
+        s.close()
+
+
+def test_lockstep_batch_rejects_implicit_and_repeated_handles():
+    wl = problems()[2]
+    a = M.Solver(wl.n, wl.length, wl.omega, dev(wl.forcing))
+    imp = M.Solver((32, 32), (1.0, 1.0), [5.5, 9.3], time_stepping="implicit")
+    x = torch.zeros(wl.forcing.shape, dtype=torch.float64, device="cuda")
+    y = torch.zeros((2, 33, 33), dtype=torch.float64, device="cuda")
+    for hs, vs in (([a, a], [x, x]), ([a, imp], [x, y])):
+        with pytest.raises(_lib.MfwhError) as e:
+            M.solve_batch_graph(hs, vs)
+        assert e.value.status == _lib.ERR_INVALID_ARG

@@ -233,6 +233,37 @@ def test_refined_fp32_reaches_fp64_accuracy(prec):
     assert np.array_equal(apply(s, np.zeros_like(wl.forcing), True), before)
 
 
+def test_relaxed_products_reach_fp64_accuracy():
+    """Relaxed inner solves (FP64 products until the inner residual is below 1e-3, FP32 after)
+    inside FP64 refinement reach the discrete Helmholtz solution to FP64-level accuracy; with
+    the switch set below the inner tolerance every product is FP64 and the result is the FP64
+    refinement's (same Arnoldi steps); an FP64 handle and a switch outside (0, 1) are refused."""
+    wl = inputs.square_small()
+    prob = W.make_problem(W.Grid(wl.n, wl.length), wl.omega, wl.forcing, cfl=wl.cfl, n_p=wl.n_p)
+    U = W.helmholtz_direct(prob)
+    s = M.Solver(wl.n, wl.length, wl.omega, dev(wl.forcing), n_p=wl.n_p, cfl=wl.cfl,
+                 precision=_lib.PREC_FP32_BLOCKSUM)
+    x = torch.zeros(wl.forcing.shape, dtype=torch.float64, device="cuda")
+    info = s.solve_relaxed(x, target=1e-10, inner_tol=1e-7, relax_below=1e-3, restart=100,
+                           max_iters=200, max_refinements=8)
+    assert info["status"] == _lib.OK
+    assert np.all(rel_err(x.cpu().numpy(), U) <= 1e-9)
+    assert np.all(W.helmholtz_residual(prob, x.cpu().numpy()) <= 1e-10)
+    # the switch never reached: FP64 products only, as an FP64 handle's refinement
+    f64 = M.Solver(wl.n, wl.length, wl.omega, dev(wl.forcing), n_p=wl.n_p, cfl=wl.cfl)
+    y = torch.zeros_like(x)
+    z = torch.zeros_like(x)
+    a = s.solve_relaxed(y, target=1e-9, inner_tol=1e-10, relax_below=1e-12, restart=100,
+                        max_iters=100)
+    b = f64.solve_refined(z, target=1e-9, inner_tol=1e-10, restart=100, max_iters=100)
+    assert a["iterations"] == b["iterations"] and a["refinements"] == b["refinements"]
+    assert torch.equal(y, z)
+    for solver, relax in ((f64, 1e-3), (s, 0.0), (s, 1.0)):
+        with pytest.raises(_lib.MfwhError) as e:
+            solver.solve_relaxed(torch.zeros_like(x), relax_below=relax)
+        assert e.value.status == _lib.ERR_INVALID_ARG
+
+
 def test_refined_fp64_handle_and_warm_start():
     wl = inputs.square_small()
     prob = W.make_problem(W.Grid(wl.n, wl.length), wl.omega, wl.forcing, cfl=wl.cfl, n_p=wl.n_p)
