@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--solve", action="store_true", help="also time one unrestarted solve to 1e-8")
     ap.add_argument("--no-tts", action="store_true",
                     help="skip the time to a 1e-6 Helmholtz residual (FP64 and mixed arms)")
-    ap.add_argument("--tts-inner", type=float, default=1e-10,
+    ap.add_argument("--tts-inner", type=float, default=1e-6,
                     help="inner GMRES tolerance of the time-to-solution arms")
     ap.add_argument("--tts-relax", type=float, default=1e-2,
                     help="mixed arm: FP32 products once the inner residual is below this")
@@ -1009,7 +1009,7 @@ def run_warm_start(args):
 
 TTS_TARGET = 1e-6          # max_m r_h of the time-to-solution arms
 TTS_RESTART = 800          # no restart within the step budget
-TTS_MAX_ITERS = 1600
+TTS_MAX_ITERS = 1000       # Arnoldi steps per arm at most
 
 
 def time_to_solution(args, wl, f_dev, stream, solver):

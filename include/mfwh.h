@@ -116,7 +116,11 @@ typedef struct {
                                 footnote to eq. filterII (same fixed point) */
   int tile_shape;            /* FP32 blocked kernel tile: 0 = 32x32, 512 threads (default);
                                 1 = 32x64, 512 threads; 2 = 64x64, 1024 threads (halved in
-                                y above 8 frequencies) */
+                                y above 8 frequencies).  FP64 blocked kernel tile (points x by
+                                y): 0 = 32x64, 512 threads; 1 = 32x32, 512 threads; 2 = 32x48,
+                                512 threads; 3 = 32x32, 256 threads, two CTAs per SM (above 8
+                                frequencies always 32x32, 512 threads).  Every tile gives
+                                bit-identical results. */
   int time_stepping;         /* MFWH_TIME_EXPLICIT (0, default): leapfrog, alpha = 0, beta = 1;
                                 MFWH_TIME_IMPLICIT: trapezoidal scheme alpha = 1/2, beta = 0 of
                                 eq. WaveScheme (FP64 results, one step per launch).  Every

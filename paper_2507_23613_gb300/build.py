@@ -75,7 +75,7 @@ def build(force=False, verbose=False):
             if o.strip():
                 print(o, file=sys.stderr)
     tmp = LIB + ".tmp"
-    _run([nvcc, "-shared", "-o", tmp] + [o for _, o in jobs] + ARCH + ["-lcudart_static", "-lpthread"])
+    _run([nvcc, "-shared", "-o", tmp] + [o for _, o in jobs] + ARCH + ["-lcudart_static", "-lpthread", "-ldl"])
     os.replace(tmp, LIB)
     return LIB
 

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "internal.h"
 #include "kernels.h"
@@ -52,6 +53,15 @@ mfwh_status fail(mfwh_status st, const std::string& msg) {
   set_error(msg);
   return st;
 }
+
+// NVTX range over a scope (create, each application of the map, each Arnoldi step, residual
+// checks, batch rounds): visible to profilers that record NVTX, a no-op otherwise.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 bool is_device_ptr(const void* p) {
   if (!p) return false;
@@ -506,6 +516,7 @@ mfwh_status apply_pi_tb(mfwh_handle_t h, const double* vin, double* vout, int fo
 // One wave solve: replayed from a captured graph in graph mode, launched directly otherwise.
 mfwh_status apply_pi(mfwh_handle_t h, const double* vin, double* vout, int forced,
                      const double* vsub) {
+  Range range(forced ? "mfwh: Pi (forced)" : "mfwh: Pi");
   // implicit handles launch N_t + 1 kernels per wave solve: no graph
   if (!h->graphs || (vsub && vsub != vin) || h->tune_steps > 0 || h->implicit)
     return apply_pi_direct(h, vin, vout, forced, vsub);
@@ -582,6 +593,7 @@ mfwh_status dots(mfwh_handle_t h, const double* V, int k, const double* w, doubl
 }
 
 mfwh_status residual_dev(mfwh_handle_t h, const double* v_dev, double* r_out) {
+  Range range("mfwh: residual");
   launch_residual(h->nf, h->geom, v_dev, h->f, h->omega2, h->plan.c2_lo, h->plan.c2_hi, h->inv_h2,
                   h->res_partial, h->res_out, h->stream);
   h->total_launches += 2;
@@ -697,6 +709,7 @@ mfwh_status gmres_core(mfwh_handle_t h, int restart, double tol, int max_iters, 
     int j_done = 0;
     double res = beta;
     for (int j = 0; j < restart; ++j) {
+      Range range("mfwh: Arnoldi step");
       double* Vj = h->basis + (int64_t)j * N;
       double* w = h->basis + (int64_t)(j + 1) * N;
       st = apply_pi(h, Vj, w, 0, Vj);   // w = A v_j = v_j - S v_j
@@ -858,6 +871,7 @@ mfwh_status mfwh_opt_parameters(int nf, const double* omega, int n_p, int n_t, i
 }
 
 mfwh_status mfwh_create(const mfwh_problem* prob, void* stream, mfwh_handle_t* out) {
+  Range range("mfwh: create");
   if (!out) return fail(MFWH_ERR_INVALID_ARG, "null output");
   *out = nullptr;
   auto* h = new (std::nothrow) mfwh_handle_s();
@@ -1728,6 +1742,7 @@ mfwh_status mfwh_solve_batch_graph(const mfwh_handle_t* handles, int count, int 
   // Arnoldi rounds: every active problem needs exactly one product A u (u = x at the start
   // of a cycle from a non-zero iterate, else its newest basis vector).
   while (st == MFWH_OK) {
+    Range range("mfwh: batch round");
     // start of cycle from x = 0: V_0 = b without a product
     for (auto& P : Ps) {
       if (P.done || !P.cycle_start || P.x_nonzero) continue;

@@ -329,8 +329,8 @@ mfwh_status plan_problem(const mfwh_problem* p, Plan* out, double c2_field_max) 
              p->time_block != 8 && !(fp32 && p->time_block == 16)) {
     return fail(MFWH_ERR_INVALID_ARG, "time_block must be 0, 1, 4 or 8 (or 16 for FP32)");
   }
-  if (p->tile_shape < 0 || p->tile_shape > 2)
-    return fail(MFWH_ERR_INVALID_ARG, "tile_shape must be 0, 1 or 2");
+  if (p->tile_shape < 0 || p->tile_shape > (fp32 ? 2 : 3))
+    return fail(MFWH_ERR_INVALID_ARG, "tile_shape must be 0, 1 or 2 (or 3 for FP64)");
   if (p->filter_update != MFWH_UPDATE_IMPLICIT && p->filter_update != MFWH_UPDATE_EXPLICIT)
     return fail(MFWH_ERR_INVALID_ARG, "filter_update must be implicit or explicit");
   if (p->order != 0 && p->order != 2 && p->order != 4)

@@ -3,16 +3,17 @@
 // One launch advances the leapfrog scheme (eq. WaveSchemeA; the first step of a wave solve as
 // eq. implicitFirstStep with alpha = 0) by up to T steps and accumulates the N_f filter sums
 // (eq. pDefQ) on the way.  The interior points 1..n-1 of each axis are cut into tiles of
-// 32 x (16 K) points, one tile per CTA of 32 x 16 threads.  A CTA loads W^n and W^{n-1} on its
+// 32 x (TY K) points, one tile per CTA of 32 x TY threads.  A CTA loads W^n and W^{n-1} on its
 // tile plus a halo of T points into shared memory; at step s it updates the tile and the ring
 // of radius T-1-s around it (the points later steps still read), so after T steps W^{n+T} and
 // W^{n+T-1} are exact on the tile.  Per point and launch HBM sees one read and one write of the
 // two levels and of the N_f filter sums, instead of T of each.
 //
-// Thread (tx, ty) owns the K consecutive tile rows ty K .. ty K + K - 1 of column tx: the two
-// wave levels and the N_f filter sums (float pairs, fpair.cuh) of its points stay in registers
-// for all T steps, vertical neighbours come from registers, and only the left and right
-// neighbours and the rows just above and below the strip come from shared memory.  The ring is
+// Thread (tx, ty) owns the K consecutive tile rows ty K .. ty K + K - 1 of column tx: the
+// current wave level and the N_f filter sums (float pairs, fpair.cuh) of its points stay in
+// registers for all T steps, vertical neighbours come from registers, and only the previous
+// level, the left and right neighbours and the rows just above and below the strip come from
+// shared memory.  The ring is
 // spread evenly over all threads by a flat index.  On sm_103a the FP64 pipe bounds this kernel
 // (a warp instruction occupies it for about 64 cycles), so the float pair of each new value is
 // split off its bit pattern on the integer and FP32 pipes (fpair_split) and the filter updates
@@ -33,7 +34,6 @@ namespace mfwh {
 namespace {
 
 constexpr int kTX = 32;   // threads in x = tile width
-constexpr int kTY = 16;   // threads in y; tile height = kTY * K
 
 template <int NF>
 struct TBParams {
@@ -99,15 +99,17 @@ __device__ __forceinline__ void ring_coords(int e, int r, int rw, int top, float
   }
 }
 
-template <int NF, int T, int K>
-__global__ void __launch_bounds__(kTX * kTY, 1)
+// TY threads in y (16: one CTA of 512 threads per SM; 8: two CTAs of 256 threads per SM, so
+// that one CTA's loads, stores and barriers overlap the other's FP64 work).
+template <int NF, int T, int K, int TY>
+__global__ void __launch_bounds__(kTX * TY, TY == 8 ? 2 : 1)
 k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
        double* __restrict__ Wc_out, double* __restrict__ Wp_out, const double* __restrict__ f,
        float2* __restrict__ q, double* vout, const double* vsub, const TBParams<NF> a,
        const Geom g) {
-  constexpr int BX = kTX, BY = kTY * K;
+  constexpr int BX = kTX, BY = TY * K;
   constexpr int EX = BX + 2 * T, EY = BY + 2 * T, E = EX * EY;
-  constexpr int NT = kTX * kTY;
+  constexpr int NT = kTX * TY;
   extern __shared__ double smem[];
   double* A = smem;                  // W^n on the extended tile
   double* B = smem + E;              // W^{n-1} on the ring, overwritten by W^{n+1}
@@ -155,24 +157,37 @@ k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
   const int64_t p0 = (y0 + lyo) * g.sy + x0 + lxo;
   const bool col_int = lxo >= ilx && lxo <= ihx;
   bool own_int[K], own_up[K];
-  double wc[K], wp[K], wlast[K];
+  double wc[K];
   float2 qr[K][NF];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     own_int[k] = col_int && lyo + k >= ily && lyo + k <= ihy;
     own_up[k] = (lay_x ? lxo : lyo + k) >= lay_thr;
-    wlast[k] = 0.0;
 #pragma unroll
     for (int m = 0; m < NF; ++m)
       qr[k][m] = own_int[k] ? q[m * g.points + p0 + k * g.sy] : make_float2(0.0f, 0.0f);
   }
   __syncthreads();
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    wc[k] = A[(lyo + k) * EX + lxo];
-    wp[k] = B[(lyo + k) * EX + lxo];
-  }
+  for (int k = 0; k < K; ++k) wc[k] = A[(lyo + k) * EX + lxo];
 
+  // The steps in three compiled copies with the same per-point arithmetic: ALLINT for
+  // homogeneous launches of CTAs whose updated points are all interior with one c^2 (no
+  // forcing terms, no per-point interior or layer tests), and the general one with and
+  // without the forcing terms (FORCED), so that no copy carries FP64 work under a predicate.
+  // The filter update of a step's new values is deferred into the next step, after that
+  // step's FP64 stencil in the same block, so that each warp's FP32 pair arithmetic overlaps
+  // FP64 work instead of following it behind the step's barrier; the updates keep their order.
+  float2 pend[K];   // float pairs of the newest owned values, not yet added to the sums
+  auto filter_update = [&](int s) {   // add pend with the weights of step s
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (!own_int[k]) continue;
+#pragma unroll
+      for (int m = 0; m < NF; ++m)
+        qr[k][m] = fpair_fma(s_wh[s * NF + m], s_wl[s * NF + m], pend[k].x, pend[k].y, qr[k][m]);
+    }
+  };
   // The steps in three compiled copies with the same per-point arithmetic: ALLINT for
   // homogeneous launches of CTAs whose updated points are all interior with one c^2 (no
   // forcing terms, no per-point interior or layer tests), and the general one with and
@@ -180,7 +195,8 @@ k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
   auto run_steps = [&](auto allint_c, auto forced_c) {
     constexpr bool ALLINT = decltype(allint_c)::value;
     constexpr bool FORCED = decltype(forced_c)::value;
-    for (int s = 0; s < a.steps; ++s) {
+    auto step = [&](int s, auto defer_c) {
+      constexpr bool DEFER = decltype(defer_c)::value;   // the previous step's update pending
       const int r = a.steps - 1 - s;          // ring radius still needed after this step
       const int n = a.n0 + s;                 // computing W^{n+1}
       const bool first = n == 0;
@@ -203,7 +219,8 @@ k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
           const double dn = k == K - 1 ? below : wc[k + 1];
           const double sx = A[l - 1] + A[l + 1];
           const double sy = up + dn;
-          double acc = fma(L.A0, wc[k], -wp[k]);   // wp = 0 on the first step
+          // W^{n-1} of the strip is still in B (0 on the first step)
+          double acc = fma(L.A0, wc[k], -B[l]);
           acc = fma(L.Ax, sx, acc);
           acc = fma(L.Ay, sy, acc);
           if (FORCED) {
@@ -213,20 +230,14 @@ k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
           }
           wn[k] = acc;
         }
+        if (DEFER) filter_update(s - 1);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
           if (!ALLINT && !own_int[k]) continue;
           B[(lyo + k) * EX + lxo] = wn[k];
-          wp[k] = wc[k];
           wc[k] = wn[k];
-          if (final_step) {
-            wlast[k] = wn[k];
-          } else {
-            const float2 xw = fpair_split(wn[k]);
-#pragma unroll
-            for (int m = 0; m < NF; ++m)
-              qr[k][m] = fpair_fma(s_wh[s * NF + m], s_wl[s * NF + m], xw.x, xw.y, qr[k][m]);
-          }
+          // the last level of a wave solve enters the sums in FP64 in the epilogue
+          if (!final_step) pend[k] = fpair_split(wn[k]);
         }
       }
       // ring of radius r around the tile
@@ -250,7 +261,9 @@ k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
       double* t = A;
       A = B;
       B = t;
-    }
+    };
+    step(0, std::false_type{});
+    for (int s = 1; s < a.steps; ++s) step(s, std::true_type{});
   };
   if (a.forced)
     run_steps(std::false_type{}, std::true_type{});
@@ -258,15 +271,17 @@ k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
     run_steps(std::true_type{}, std::false_type{});
   else
     run_steps(std::false_type{}, std::false_type{});
+  // the last step's update (except for the final level of a wave solve)
+  if (!a.last) filter_update(a.steps - 1);
 
-  // wc = W^{n0+steps}, wp = W^{n0+steps-1} on the strip
+  // wc = W^{n0+steps} on the strip, B = W^{n0+steps-1}
   if (!a.last) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       if (!own_int[k]) continue;
       const int64_t p = p0 + k * g.sy;
       Wc_out[p] = wc[k];
-      Wp_out[p] = wp[k];
+      Wp_out[p] = B[(lyo + k) * EX + lxo];
 #pragma unroll
       for (int m = 0; m < NF; ++m) q[m * g.points + p] = qr[k][m];
     }
@@ -281,7 +296,7 @@ k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
     const int64_t p = p0 + k * g.sy;
     double qq[NF];
 #pragma unroll
-    for (int j = 0; j < NF; ++j) qq[j] = fma(wq[j], wlast[k], fpair_value(qr[k][j]));
+    for (int j = 0; j < NF; ++j) qq[j] = fma(wq[j], wc[k], fpair_value(qr[k][j]));
     double vk[NF];
     if (a.has_e) {
 #pragma unroll
@@ -323,11 +338,11 @@ k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
     for (int64_t gy = ys + tid; gy < ye; gy += NT) zero_point(g.nx, gy);
 }
 
-template <int NF, int T, int K>
+template <int NF, int T, int K, int TY>
 void tb_launch_k(const Geom& g, const double* Wc_in, const double* Wp_in, double* Wc_out,
                  double* Wp_out, const double* f, double* q, double* vout, const double* vsub,
                  const TBHost& h, cudaStream_t st) {
-  constexpr int BX = kTX, BY = kTY * K;
+  constexpr int BX = kTX, BY = TY * K;
   constexpr int EX = BX + 2 * T, EY = BY + 2 * T;
   constexpr size_t smem = sizeof(double) * (2 * EX * EY + 2 * T * NF) + sizeof(float) * 2 * T * NF;
   // The attribute is per device; set it once per device for this instance.
@@ -335,7 +350,8 @@ void tb_launch_k(const Geom& g, const double* Wc_in, const double* Wp_in, double
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64 || !configured[dev]) {
-    cudaFuncSetAttribute(k_tb2d<NF, T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_tb2d<NF, T, K, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
     if (dev >= 0 && dev < 64) configured[dev] = true;
   }
   TBParams<NF> a;
@@ -361,25 +377,31 @@ void tb_launch_k(const Geom& g, const double* Wc_in, const double* Wp_in, double
     }
   // tiles over the interior points 1 .. n-1 of each axis
   dim3 grid((unsigned)((g.nx - 1 + BX - 1) / BX), (unsigned)((g.ny - 1 + BY - 1) / BY));
-  k_tb2d<NF, T, K><<<grid, dim3(kTX, kTY), smem, st>>>(Wc_in, Wp_in, Wc_out, Wp_out, f,
-                                                      reinterpret_cast<float2*>(q), vout, vsub,
-                                                      a, g);
+  k_tb2d<NF, T, K, TY><<<grid, dim3(kTX, TY), smem, st>>>(Wc_in, Wp_in, Wc_out, Wp_out, f,
+                                                          reinterpret_cast<float2*>(q), vout,
+                                                          vsub, a, g);
 }
 
-// Rows per thread: 4 (32 x 64 tiles), 3 (32 x 48) or 2 (32 x 32) by tile shape 0, 2, 1; above
-// 8 frequencies the filter sums of more than two points per thread would not fit in registers.
+// Tile shapes: 0 = 32 x 64 points (512 threads, 4 rows each), 1 = 32 x 32 (512 threads, 2
+// rows each), 2 = 32 x 48 (512 threads, 3 rows each), 3 = 32 x 32 (256 threads, 4 rows each,
+// two CTAs per SM).  Above 8 frequencies the filter sums of more than two points per thread
+// would not fit in registers, and every shape takes 32 x 32 tiles of 512 threads.
 template <int NF, int T>
 void tb_launch_shape(const Geom& g, const double* Wc_in, const double* Wp_in, double* Wc_out,
                      double* Wp_out, const double* f, double* q, double* vout, const double* vsub,
                      const TBHost& h, cudaStream_t st) {
-  if (NF > 8 || h.shape == 1)
-    tb_launch_k<NF, T, 2>(g, Wc_in, Wp_in, Wc_out, Wp_out, f, q, vout, vsub, h, st);
+  constexpr bool wide = NF > 8;
+  if (wide || h.shape == 1)
+    tb_launch_k<NF, T, 2, 16>(g, Wc_in, Wp_in, Wc_out, Wp_out, f, q, vout, vsub, h, st);
   else if (h.shape == 2)
-    tb_launch_k<NF, T, (NF > 8 ? 2 : 3)>(g, Wc_in, Wp_in, Wc_out, Wp_out, f, q, vout, vsub, h,
-                                          st);
+    tb_launch_k<NF, T, (wide ? 2 : 3), 16>(g, Wc_in, Wp_in, Wc_out, Wp_out, f, q, vout, vsub, h,
+                                             st);
+  else if (h.shape == 3)
+    tb_launch_k<NF, T, (wide ? 2 : 4), (wide ? 16 : 8)>(g, Wc_in, Wp_in, Wc_out, Wp_out, f, q,
+                                                          vout, vsub, h, st);
   else
-    tb_launch_k<NF, T, (NF > 8 ? 2 : 4)>(g, Wc_in, Wp_in, Wc_out, Wp_out, f, q, vout, vsub, h,
-                                          st);
+    tb_launch_k<NF, T, (wide ? 2 : 4), 16>(g, Wc_in, Wp_in, Wc_out, Wp_out, f, q, vout, vsub, h,
+                                             st);
 }
 
 template <int NF>

@@ -172,9 +172,10 @@ def test_pi_in_place():
                                                   ((150, 140), 3, 10, 0), ((130, 160), 3, 11, 1)])
 def test_time_blocking_is_bit_identical(shape, nf, seed, layer):
     """Temporal blocking (4 or 8 leapfrog steps per pass over HBM, halo tiles in shared
-    memory, tiles of 32 x 64, 32 x 32 and 32 x 48 points) performs the same floating-point
-    operations per point as one step per launch, so Pi, S and the GMRES iterate are
-    bit-identical for every depth and tile; also checked against the oracle.  N_t is not a
+    memory, tiles of 32 x 64, 32 x 32 and 32 x 48 points, CTAs of 512 or 256 threads) performs
+    the same floating-point operations per point as one step per launch, so Pi, S and the
+    GMRES iterate are bit-identical for every depth and tile; also checked against the
+    oracle.  N_t is not a
     multiple of the depth on these grids (ragged last launch); the larger grids have CTAs whose
     whole halo is interior (the kernels' test-free path) and two-layer media split along x or
     y (c = 1 and 1.4 on either side of 0.37 of the length)."""
@@ -184,7 +185,7 @@ def test_time_blocking_is_bit_identical(shape, nf, seed, layer):
     v = random_v(wl, seed + 1)
     kw = {} if layer is None else dict(c_lo=1.0, c_hi=1.4, interface=0.37, layer_axis=layer)
     outs = {}
-    for tb, tshape in ((1, 0), (4, 0), (4, 1), (4, 2), (8, 0), (8, 1), (8, 2)):
+    for tb, tshape in ((1, 0), (4, 0), (4, 1), (4, 2), (4, 3), (8, 0), (8, 1), (8, 2), (8, 3)):
         solver = M.Solver(wl.n, wl.length, wl.omega, dev(wl.forcing), n_p=wl.n_p, cfl=wl.cfl,
                           filter_mode=_lib.FILTER_TRADITIONAL, time_block=tb, tile_shape=tshape,
                           **kw)

@@ -202,7 +202,8 @@ def test_adjusted_frequency_matches_definition():
     dict(n=(8, 8, 8), length=(1.0, 1.0, 1.0), time_block=8),   # 3D is not blocked
     dict(time_block=16),               # depth 16 is FP32-only
     dict(precision=3),                 # unknown precision
-    dict(tile_shape=3),
+    dict(tile_shape=4),                # FP64 tiles 0-3
+    dict(tile_shape=3, precision=1),   # FP32 tiles 0-2
     dict(order=3),                     # only second and fourth order
     dict(filter_update=2),             # implicit (0) or explicit (1) only
     dict(order=4, time_block=8),       # fourth order takes one step per launch
