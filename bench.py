@@ -125,13 +125,12 @@ def bytes_per_point_step(nf, forced):
 
 
 def flops_per_point_step(nf, forced, dim=2):
-    """FP64 flops: stencil adds (2 dim - 1), three FMAs for the leapfrog, N_f FMAs for the
-    forcing when forced (an FMA counts 2), and the subtraction that splits W^{n+1} into a
-    float pair.  The N_f filter updates run on the FP32 pipe (float-pair arithmetic) and are
-    not counted here."""
-    fma = 3 + (nf if forced else 0)
-    adds = 2 * dim - 1 + 1
-    return 2 * fma + adds
+    """FP64 flops of one point-step as the step kernel executes them: dim adds for the
+    neighbour pairs, dim + 1 FMAs for the leapfrog (the centre term with W^{n-1} and one per
+    axis), N_f FMAs for the forcing when forced; an FMA counts 2.  The float-pair split of
+    W^{n+1} and the N_f filter updates run on the integer and FP32 pipes and are not counted."""
+    fma = dim + 1 + (nf if forced else 0)
+    return 2 * fma + dim
 
 
 def kernel_traffic(profile, kernel_key):

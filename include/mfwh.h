@@ -327,8 +327,9 @@ mfwh_status mfwh_solve_batch_graph(const mfwh_handle_t* handles, int count, int 
 
 /* Autotuner for the blocked wave kernels.  Times the first steps (at most 96) of a
  * homogeneous wave solve of prob on the current device for each candidate temporal depth and
- * tile shape (FP32, 2D: depths 4, 8, 16 x tile shapes 0, 1, 2; FP64, 2D: depths 1, 4, 8;
- * FP32, 3D: depths 1, 2, 4; FP64 3D and fourth order: depth 1), keeping the fastest:
+ * tile shape (FP32, 2D: depths 4, 8, 16 x tile shapes 0, 1, 2; FP64, 2D: depth 1, and depths
+ * 4, 8 x tile shapes 1, 3; FP32, 3D: depths 1, 2, 4; FP64 3D, fourth order and c^2 fields:
+ * depth 1), keeping the fastest:
  * *time_block and *tile_shape receive it, *ms_per_step
  * (may be NULL) its time per leapfrog step.  Results are cached per device, grid, number of
  * frequencies and precision for the life of the process.  Allocates (and frees) one handle's

@@ -1983,7 +1983,7 @@ mfwh_status mfwh_autotune(const mfwh_problem* prob, void* stream, int* time_bloc
   } else if (P.dim == 3) {
     cand = {{1, 0}, {2, 0}, {4, 0}};
   } else if (P.precision == MFWH_PREC_FP64) {
-    cand = {{1, 0}, {4, 0}, {8, 0}};
+    cand = {{1, 0}, {4, 1}, {4, 3}, {8, 1}, {8, 3}};
   } else {
     for (int T : {4, 8, 16})
       for (int shape : {0, 1, 2}) cand.push_back({T, shape});

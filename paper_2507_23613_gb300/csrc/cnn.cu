@@ -3,11 +3,12 @@
 // paper itself starts from zero).  L layers of 3 x 3 "same" convolutions (zero padding) with
 // bias, ReLU after every layer but the last, images [B][C][H][W].
 //
-// Arithmetic: activations and weights in BF16, products accumulated in FP32 on the tensor
-// cores (mma.sync m16n8k16, an implicit GEMM whose rows are 16 consecutive pixels of one image
-// row and whose reduction runs over (input channel, tap)); gradients, master weights and the
-// Adam state in FP32.  The weight gradient, a reduction over every pixel of the batch, runs on
-// the FP32 CUDA cores.
+// Arithmetic: activations and weights in BF16, products accumulated in FP32 on the
+// 5th-generation tensor cores (tcgen05.mma with the accumulator in tensor memory, operands in
+// shared memory: an implicit GEMM whose rows are 128 consecutive pixels of the batch and whose
+// reduction runs over (input channel, tap)), for the forward convolutions and the input
+// gradients; gradients, master weights and the Adam state in FP32.  The weight gradient, a
+// reduction over every pixel of the batch, runs on the FP32 CUDA cores.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -27,73 +28,221 @@ namespace {
 
 __host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-  const uint32_t l = __bfloat16_as_ushort(lo), h = __bfloat16_as_ushort(hi);
-  return l | (h << 16);
+// ---- 3 x 3 convolution as an implicit GEMM on the 5th-generation tensor cores ----------
+// D[p][n] = sum_k A[p][k] B[n][k] with p a pixel, n an output channel and k = ci * 9 + tap
+// (tap = dy * 3 + dx): A[p][k] = in[ci][y + dy - 1][x + dx - 1] (zero outside the image),
+// B[n][k] = Wk[n][k].  A CTA of 128 threads takes 128 consecutive pixels of the batch (M = 128)
+// and all output channels (N = 16 or 32, rows past Cout zero).  Each thread gathers its pixel's
+// row of A, 8 values of k at a time, into shared memory in the canonical K-major layout without
+// swizzle: 8 x 16-byte core matrices, the 16 row groups of a k-chunk 128 bytes apart (the
+// descriptor's stride byte offset) and successive k-chunks 16 * 128 bytes apart (its leading
+// byte offset); B likewise with N / 8 row groups.  One thread issues Kp / 16 MMAs
+// (tcgen05.mma, kind::f16, BF16 operands, FP32 accumulator in tensor memory) and commits them
+// to an mbarrier; after a bounded wait every warp reads its 32 rows of the accumulator
+// (tcgen05.ld) and applies bias and ReLU.  Shared and tensor memory are allocated with margins
+// past what a correct descriptor reads.
+constexpr int kConvM = 128;              // pixels per CTA (accumulator lanes)
+constexpr int kConvTmemCols = 256;       // tensor-memory columns allocated per CTA
+constexpr int kConvMaxKp = 288;          // 32 input channels x 9 taps
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Implicit-GEMM 3 x 3 convolution.  One warp computes 16 consecutive pixels (x0 .. x0 + 15 of
-// row y of image b) for all output channels (NT tiles of 8).  Wk: [Np][Kp] BF16, Wk[n][k] with
-// k = ci * 9 + tap (tap = dy * 3 + dx), zero for k >= Cin * 9 and n >= Cout.
+// Shared-memory matrix descriptor (tcgen05): start address, leading byte offset (between core
+// matrices along K), stride byte offset (between 8-row groups), all >> 4; descriptor version 1
+// (bit 46); no swizzle (layout type 0 in bits 61-63).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A and B (bits 7-9
+// and 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t conv_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(kConvM >> 4) << 24);
+}
+
+// Bounded wait for phase `parity` of an mbarrier; false when the bound ran out.
+__device__ __forceinline__ bool conv_mbar_wait(uint32_t bar, uint32_t parity, int limit) {
+  for (int it = 0; it < limit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
 template <int NT>
-__global__ void __launch_bounds__(128)
-k_conv_mma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ Wk,
-           const float* __restrict__ bias, int Cin, int Cout, int Kp, int B, int H, int W,
-           int relu, __nv_bfloat16* __restrict__ out_bf, float* __restrict__ out_f) {
-  const int lane = threadIdx.x & 31;
-  const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int segs = (W + 15) / 16;
-  if (warp >= B * H * segs) return;
-  const int seg = warp % segs, y = (warp / segs) % H, b = warp / (segs * H);
-  const int x0 = seg * 16;
-  const int g = lane >> 2, t = lane & 3;
+__global__ void __launch_bounds__(kConvM)
+k_conv_tc(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ Wk,
+          const float* __restrict__ bias, int Cin, int Cout, int Kp, int Np, int B, int H, int W,
+          int relu, __nv_bfloat16* __restrict__ out_bf, float* __restrict__ out_f,
+          int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char conv_smem[];
+  __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int K = Cin * 9;
-  const size_t plane = (size_t)H * W;
-  const __nv_bfloat16* inb = in + (size_t)b * Cin * plane;
-  const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-  // value of A[row r][col k] (pixel x0 + r, reduction index k)
-  auto a_val = [&](int r, int k) -> __nv_bfloat16 {
-    if (k >= K) return zero;
-    const int ci = k / 9, tap = k - ci * 9;
-    const int yy = y + tap / 3 - 1, xx = x0 + r + tap % 3 - 1;
-    if (yy < 0 || yy >= H || xx < 0 || xx >= W) return zero;
-    return inb[(size_t)ci * plane + (size_t)yy * W + xx];
-  };
-  float acc[NT][4];
+  const int nk = Kp / 8;                                  // k-chunks of 8
+  constexpr uint32_t kSbo = 128;                          // 8-row groups 128 bytes apart
+  constexpr uint32_t kLboA = (kConvM / 8) * 128;          // 2048 bytes per k-chunk of A
+  constexpr uint32_t kLboB = (NT / 8) * 128;              // bytes per k-chunk of B
+  unsigned char* sA = conv_smem;                          // kConvM x Kp BF16
+  unsigned char* sB = conv_smem + (size_t)kConvMaxKp / 8 * kLboA;   // NT x Kp BF16
+  const int64_t plane = (int64_t)H * W, total = (int64_t)B * plane;
+  const int64_t pix = (int64_t)blockIdx.x * kConvM + tid;
+
+  if (warp == 0) {   // tensor memory for the accumulator (whole warp, aligned)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(kConvTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mma_bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // A: this thread's pixel row, one 16-byte core-matrix row per k-chunk
+  {
+    const bool valid = pix < total;
+    const int b = valid ? (int)(pix / plane) : 0;
+    const int64_t rem = valid ? pix - (int64_t)b * plane : 0;
+    const int y = (int)(rem / W), x = (int)(rem - (int64_t)y * W);
+    const __nv_bfloat16* inb = in + (size_t)b * Cin * plane;
+    const uint16_t zero = 0;
+    for (int kc = 0; kc < nk; ++kc) {
+      uint16_t v[8];
 #pragma unroll
-  for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
-  for (int kc = 0; kc < Kp; kc += 16) {
-    const int c0 = kc + 2 * t, c2 = kc + 2 * t + 8;
-    const uint32_t a0 = pack_bf16(a_val(g, c0), a_val(g, c0 + 1));
-    const uint32_t a1 = pack_bf16(a_val(g + 8, c0), a_val(g + 8, c0 + 1));
-    const uint32_t a2 = pack_bf16(a_val(g, c2), a_val(g, c2 + 1));
-    const uint32_t a3 = pack_bf16(a_val(g + 8, c2), a_val(g + 8, c2 + 1));
-#pragma unroll
-    for (int j = 0; j < NT; ++j) {
-      const __nv_bfloat16* wr = Wk + (size_t)(j * 8 + g) * Kp;
-      const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wr + c0);
-      const uint32_t b1 = *reinterpret_cast<const uint32_t*>(wr + c2);
+      for (int j = 0; j < 8; ++j) {
+        const int k = kc * 8 + j;
+        v[j] = zero;
+        if (valid && k < K) {
+          const int ci = k / 9, tap = k - ci * 9;
+          const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+          if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+            v[j] = __bfloat16_as_ushort(inb[(size_t)ci * plane + (size_t)yy * W + xx]);
+        }
+      }
+      uint4 row;
+      row.x = v[0] | ((uint32_t)v[1] << 16);
+      row.y = v[2] | ((uint32_t)v[3] << 16);
+      row.z = v[4] | ((uint32_t)v[5] << 16);
+      row.w = v[6] | ((uint32_t)v[7] << 16);
+      *reinterpret_cast<uint4*>(sA + (size_t)kc * kLboA + (tid >> 3) * kSbo + (tid & 7) * 16) = row;
+    }
+  }
+  // B: NT rows of the weights (rows Np .. NT - 1 zero), 16 bytes per (row, k-chunk)
+  for (int e = tid; e < NT * nk; e += kConvM) {
+    const int n = e / nk, kc = e - n * nk;
+    uint4 row = make_uint4(0u, 0u, 0u, 0u);
+    if (n < Np) row = *reinterpret_cast<const uint4*>(Wk + (size_t)n * Kp + kc * 8);
+    *reinterpret_cast<uint4*>(sB + (size_t)kc * kLboB + (n >> 3) * kSbo + (n & 7) * 16) = row;
+  }
+  // make the operands visible to the tensor core's asynchronous proxy, then issue
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t taddr = tmem_base;
+  if (tid == 0) {
+    constexpr uint32_t idesc = conv_idesc(NT);
+    for (int ks = 0; ks < Kp / 16; ++ks) {
+      const uint64_t ad = smem_desc(smem_u32(sA) + ks * 2 * kLboA, kLboA, kSbo);
+      const uint64_t bd = smem_desc(smem_u32(sB) + ks * 2 * kLboB, kLboB, kSbo);
+      const uint32_t acc = ks > 0 ? 1u : 0u;
       asm volatile(
-          "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-          "{%8,%9}, {%0,%1,%2,%3};"
-          : "+f"(acc[j][0]), "+f"(acc[j][1]), "+f"(acc[j][2]), "+f"(acc[j][3])
-          : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+          "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(taddr),
+          "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+          : "memory");
     }
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&mma_bar))
+        : "memory");
   }
-#pragma unroll
-  for (int j = 0; j < NT; ++j) {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int r = g + (e >= 2 ? 8 : 0), n = j * 8 + 2 * t + (e & 1);
-      const int x = x0 + r;
-      if (n >= Cout || x >= W) continue;
-      float v = acc[j][e] + (bias ? bias[n] : 0.0f);
-      if (relu) v = fmaxf(v, 0.0f);
-      const size_t o = ((size_t)b * Cout + n) * plane + (size_t)y * W + x;
-      if (out_f) out_f[o] = v;
-      if (out_bf) out_bf[o] = __float2bfloat16(v);
+  const bool ok = conv_mbar_wait(smem_u32(&mma_bar), 0, 1 << 22);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (__syncthreads_or(!ok)) {
+    // The MMAs did not complete within the bound: report it, give them one more bounded wait,
+    // release the tensor memory and stop.
+    if (tid == 0) atomicExch(err, 1);
+    conv_mbar_wait(smem_u32(&mma_bar), 0, 1 << 22);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
+                   "r"(kConvTmemCols)
+                   : "memory");
     }
+    return;
   }
+  // accumulator row tid (lanes 32 warp .. 32 warp + 31), NT columns
+  float accv[NT];
+  const uint32_t lane_addr = taddr + ((uint32_t)(warp * 32) << 16);
+  if constexpr (NT == 16) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(lane_addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) accv[j] = __uint_as_float(r[j]);
+  } else {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(lane_addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) accv[j] = __uint_as_float(r[j]);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
+                 "r"(kConvTmemCols)
+                 : "memory");
+  }
+  if (pix >= total) return;
+  const int b = (int)(pix / plane);
+  const int64_t rem = pix - (int64_t)b * plane;
+#pragma unroll
+  for (int n = 0; n < NT; ++n) {
+    if (n >= Cout) break;
+    float v = accv[n] + (bias ? bias[n] : 0.0f);
+    if (relu) v = fmaxf(v, 0.0f);
+    const size_t o = ((size_t)b * Cout + n) * plane + rem;
+    if (out_f) out_f[o] = v;
+    if (out_bf) out_bf[o] = __float2bfloat16(v);
+  }
+}
+
+// Dynamic shared memory of k_conv_tc: A for the largest Kp, then B, plus a margin of one more
+// A-sized region, so that any reading of the two byte offsets stays inside the allocation.
+__host__ __device__ constexpr size_t conv_smem_bytes(int nt) {
+  return (size_t)kConvMaxKp / 8 * (kConvM / 8) * 128 * 2 + (size_t)kConvMaxKp / 8 * (nt / 8) * 128;
 }
 
 // Weight and bias gradients of one layer: gw[co][ci][tap] = sum_{b,y,x} g[b][co][y][x] *
@@ -287,6 +436,7 @@ struct mfwh_cnn_s {
   __nv_bfloat16* gbf = nullptr;
   float* part = nullptr;               // loss partial sums
   float* part_h = nullptr;             // pinned
+  int* err = nullptr;                  // device flag: a convolution's MMA wait ran out
 };
 
 namespace {
@@ -326,14 +476,39 @@ mfwh_status ensure_ws(mfwh_cnn_t c, int64_t bhw) {
 void conv(mfwh_cnn_t c, const __nv_bfloat16* in, const __nv_bfloat16* Wk, const float* bias,
           int Cin, int Cout, int Kp, int Np, int B, int H, int W, int relu, __nv_bfloat16* out_bf,
           float* out_f) {
-  const int warps = B * H * ((W + 15) / 16);
-  const int blocks = (warps + 3) / 4;
-  switch (Np / 8) {
-    case 1: k_conv_mma<1><<<blocks, 128, 0, c->stream>>>(in, Wk, bias, Cin, Cout, Kp, B, H, W, relu, out_bf, out_f); break;
-    case 2: k_conv_mma<2><<<blocks, 128, 0, c->stream>>>(in, Wk, bias, Cin, Cout, Kp, B, H, W, relu, out_bf, out_f); break;
-    case 3: k_conv_mma<3><<<blocks, 128, 0, c->stream>>>(in, Wk, bias, Cin, Cout, Kp, B, H, W, relu, out_bf, out_f); break;
-    default: k_conv_mma<4><<<blocks, 128, 0, c->stream>>>(in, Wk, bias, Cin, Cout, Kp, B, H, W, relu, out_bf, out_f); break;
+  const int64_t total = (int64_t)B * H * W;
+  const unsigned blocks = (unsigned)((total + kConvM - 1) / kConvM);
+  if (Np <= 16) {
+    k_conv_tc<16><<<blocks, kConvM, conv_smem_bytes(16), c->stream>>>(
+        in, Wk, bias, Cin, Cout, Kp, Np, B, H, W, relu, out_bf, out_f, c->err);
+  } else {
+    k_conv_tc<32><<<blocks, kConvM, conv_smem_bytes(32), c->stream>>>(
+        in, Wk, bias, Cin, Cout, Kp, Np, B, H, W, relu, out_bf, out_f, c->err);
   }
+}
+
+// The convolution kernels' shared-memory limit, once per device.
+mfwh_status conv_configure() {
+  static bool done[64] = {};
+  int dev = 0;
+  CKC(cudaGetDevice(&dev));
+  if (dev >= 0 && dev < 64 && done[dev]) return MFWH_OK;
+  CKC(cudaFuncSetAttribute(k_conv_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)conv_smem_bytes(16)));
+  CKC(cudaFuncSetAttribute(k_conv_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)conv_smem_bytes(32)));
+  if (dev >= 0 && dev < 64) done[dev] = true;
+  return MFWH_OK;
+}
+
+// A convolution's bounded MMA wait ran out since the last check: report it and clear the flag.
+mfwh_status check_err(mfwh_cnn_t c) {
+  int flag = 0;
+  CKC(cudaMemcpyAsync(&flag, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CKC(cudaStreamSynchronize(c->stream));
+  if (!flag) return MFWH_OK;
+  CKC(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+  return cnn_fail(MFWH_ERR_TIMEOUT, "cnn: a convolution's tensor-core wait timed out");
 }
 
 mfwh_status pack_all(mfwh_cnn_t c) {
@@ -412,8 +587,12 @@ mfwh_status mfwh_cnn_create(int layers, int channels, int in_channels, uint64_t 
         cudaMalloc(&c->Wt[l], sizeof(__nv_bfloat16) * c->Npt[l] * c->Kpt[l]) != cudaSuccess)
       return fail_free(cnn_fail(MFWH_ERR_NOMEM, "cnn: weight allocation failed"));
   if (cudaMalloc(&c->part, sizeof(float) * kLossBlocks) != cudaSuccess ||
-      cudaMallocHost(&c->part_h, sizeof(float) * kLossBlocks) != cudaSuccess)
+      cudaMallocHost(&c->part_h, sizeof(float) * kLossBlocks) != cudaSuccess ||
+      cudaMalloc(&c->err, sizeof(int)) != cudaSuccess)
     return fail_free(cnn_fail(MFWH_ERR_NOMEM, "cnn: allocation failed"));
+  if (cudaMemsetAsync(c->err, 0, sizeof(int), c->stream) != cudaSuccess)
+    return fail_free(cnn_fail(MFWH_ERR_CUDA, "cnn: initialisation failed"));
+  if (conv_configure() != MFWH_OK) return fail_free(MFWH_ERR_CUDA);
   if (cudaMemcpyAsync(c->p, h.data(), sizeof(float) * c->nparams, cudaMemcpyHostToDevice,
                       c->stream) != cudaSuccess ||
       cudaMemsetAsync(c->m, 0, sizeof(float) * c->nparams, c->stream) != cudaSuccess ||
@@ -450,7 +629,7 @@ mfwh_status mfwh_cnn_get_params(mfwh_cnn_t c, float* host, float* grads_host, in
     CKC(cudaMemcpyAsync(grads_host, c->grad, sizeof(float) * count, cudaMemcpyDeviceToHost,
                         c->stream));
   CKC(cudaStreamSynchronize(c->stream));
-  return MFWH_OK;
+  return check_err(c);
 }
 
 mfwh_status mfwh_cnn_forward(mfwh_cnn_t c, const float* x, int B, int H, int W, float* y) {
@@ -503,7 +682,7 @@ mfwh_status mfwh_cnn_train_step(mfwh_cnn_t c, const float* x, const float* targe
   double s = 0.0;
   for (int i = 0; i < kLossBlocks; ++i) s += c->part_h[i];
   if (loss) *loss = (float)(s * inv);
-  return MFWH_OK;
+  return check_err(c);
 }
 
 void mfwh_cnn_destroy(mfwh_cnn_t c) {
@@ -519,6 +698,7 @@ void mfwh_cnn_destroy(mfwh_cnn_t c) {
   for (auto* a : c->act)
     if (a) cudaFree(a);
   if (c->part_h) cudaFreeHost(c->part_h);
+  if (c->err) cudaFree(c->err);
   delete c;
 }
 
@@ -564,6 +744,11 @@ mfwh_status cnn_ws_predict(mfwh_cnn_t c, const double* f, const double* omega, i
       k_ws_output<<<256, 256, 0, st>>>(y, nf, H, W, v);
       if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
         res = cnn_fail(MFWH_ERR_CUDA, "warm start: output kernel failed");
+    }
+    if (res == MFWH_OK) {
+      c->stream = st;
+      res = check_err(c);
+      c->stream = keep;
     }
   }
   cudaStreamSynchronize(st);
