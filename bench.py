@@ -114,14 +114,23 @@ def peaks():
     return 6800.0, "fallback"
 
 
-# Nominal FP64 FMA rate of GB300 (1.25 TFLOP/s dense, the profiling recipe's table).
-FP64_PEAK_TFLOPS = 1.25
+# FP64 rate of GB300 from its unit counts: 152 SMs x 2 FP64 FMA lanes per SM and cycle (the
+# peak ncu reports for DFMA on sm_103) x 2 flops x the 2070 MHz maximum SM clock = 1.259
+# TFLOP/s (the nominal figure is 1.25).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 
 def bytes_per_point_step(nf, forced):
     """Algorithmic HBM bytes of one unblocked leapfrog+filter point-step:
     read W^n, W^{n-1}, q_m (and f_m when forced), write W^{n+1}, q_m."""
     return (3 + (3 if forced else 2) * nf) * WORD
+
+
+def blocked_bytes_per_point_launch(nf, forced):
+    """Algorithmic HBM bytes per interior point of one temporally blocked FP64 launch (any
+    number of steps): read and write both wave levels and the N_f float-pair filter sums,
+    and read the N_f forcing grids once when forced."""
+    return (4 + 2 * nf + (nf if forced else 0)) * WORD
 
 
 def flops_per_point_step(nf, forced, dim=2):
@@ -174,6 +183,16 @@ def kernel_source_key():
     h = hashlib.sha256()
     h.update(_region("wave.cu", "// ---- Helmholtz residual"))
     h.update(_region("kernels.h", "// Arguments of one temporally blocked launch"))
+    h.update(_region("fpair.cuh", "\0"))
+    return h.hexdigest()[:16]
+
+
+def blocked_kernel_source_key():
+    """Hash of the FP64 temporally blocked kernels' source (wave_tb_kernels.cuh), their
+    argument structs (kernels.h) and the float-pair arithmetic (fpair.cuh)."""
+    h = hashlib.sha256()
+    h.update(_region("wave_tb_kernels.cuh", "\0"))
+    h.update(_region("kernels.h", "// ---- FP32 path"))
     h.update(_region("fpair.cuh", "\0"))
     return h.hexdigest()[:16]
 
@@ -1199,19 +1218,49 @@ def main():
 
     if rank != 0:
         return
-    traffic = kernel_traffic("k_step_square1025_nf8.txt", kernel_source_key())
-    homog_launch_bytes = wl.interior_points * bytes_per_point_step(wl.nf, False)
+    # Steps per launch, from the library's own launch count (ceil(N_t / depth) per map).
+    launches_per_map = step_launches / max(pi_apps, 1)
+    depth = max(1, int(round(n_t / launches_per_map)))
     t_hbm = alg_bytes / (hbm_peak * 1e9)
     t_alu = alg_flops / (FP64_PEAK_TFLOPS * 1e12)
-    if t_hbm >= t_alu:
-        roof = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(achieved_gbs / hbm_peak, 4)}
+    unblocked = {"unit": "GB/s", "achieved": round(achieved_gbs, 1),
+                 "frac": round(achieved_gbs / hbm_peak, 4),
+                 "bytes_per_point_step": [bytes_per_point_step(wl.nf, False),
+                                          bytes_per_point_step(wl.nf, True)]}
+    if depth == 1:
+        traffic = kernel_traffic("k_step_square1025_nf8.txt", kernel_source_key())
+        kernel = "k_step/k_last (leapfrog + N_f filters, one step per launch)"
+        if t_hbm >= t_alu:
+            roof = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak,
+                    "unit": "GB/s", "frac": round(achieved_gbs / hbm_peak, 4)}
+        else:
+            roof = {"bound": "alu", "achieved": round(achieved_tf, 4), "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": round(achieved_tf / FP64_PEAK_TFLOPS, 4)}
+        roof["alg_bytes_per_launch"] = round(alg_bytes / max(step_launches, 1))
     else:
-        roof = {"bound": "alu", "achieved": round(achieved_tf, 4), "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": round(achieved_tf / FP64_PEAK_TFLOPS, 4)}
-    roof.update({"traffic": traffic, "kernel": "k_step/k_last (leapfrog + N_f filters)",
-                 "peak_source": peak_kind,
-                 "alg_bytes_per_launch": round(alg_bytes / max(step_launches, 1)),
+        # Blocked launches move (4 + 2 N_f (+ N_f forced)) words per point whatever their depth;
+        # the bound is the FP64 pipe (5 FP64 instructions per homogeneous point-step).
+        blk_bytes = wl.interior_points * (
+            forced_apps * -(-n_t // depth) * blocked_bytes_per_point_launch(wl.nf, True)
+            + homog_apps * -(-n_t // depth) * blocked_bytes_per_point_launch(wl.nf, False))
+        blk_gbs = blk_bytes / (step_ms_total * 1e-3) / 1e9
+        shape = args.tile_shape if args.time_block else 5
+        pipe = depth <= 4 and shape == 5 and wl.nf <= 8
+        traffic = (kernel_traffic("k_tb2d_pipe_square1025_nf8.txt", blocked_kernel_source_key())
+                   if pipe else None)
+        kernel = ("k_tb2d_pipe (%d leapfrog steps + N_f filters per pass, persistent CTAs "
+                  "copying the next tile while stepping one)" % depth if pipe else
+                  "k_tb2d (%d leapfrog steps + N_f filters per launch)" % depth)
+        roof = {"bound": "alu", "achieved": round(achieved_tf, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                "unit": "TFLOP/s", "frac": round(achieved_tf / FP64_PEAK_TFLOPS, 4),
+                "alg_bytes_per_launch": round(blk_bytes / max(step_launches, 1)),
+                "blocked_hbm": {"unit": "GB/s", "achieved": round(blk_gbs, 1),
+                                "frac": round(blk_gbs / hbm_peak, 4)},
+                "unblocked_byte_model": unblocked,
+                "steps_per_launch": depth}
+    roof.update({"traffic": traffic, "kernel": kernel, "peak_source": peak_kind,
+                 "peak_note": ("alu peak derived from unit counts: 152 SMs x 2 FP64 FMA lanes x "
+                               "2 flops x 2.07 GHz; hbm peak " + peak_kind),
                  "avg_launch_us": round(step_ms_total * 1e3 / max(step_launches, 1), 2),
                  "hbm_frac": round(achieved_gbs / hbm_peak, 4),
                  "fp64_alu_frac": round(achieved_tf / FP64_PEAK_TFLOPS, 4)})

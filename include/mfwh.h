@@ -98,12 +98,15 @@ typedef struct {
   int n_delta;               /* N_delta of eq. LambdaRange (paper: 20) */
   double c_delta;            /* c_delta of eq. LambdaRange (paper: 2) */
   int precision;             /* MFWH_PREC_FP64, MFWH_PREC_FP32_KAHAN or MFWH_PREC_FP32_BLOCKSUM */
-  int time_block;            /* leapfrog steps per pass over HBM: 0 = library default (1 for
-                                FP64 and for 3D; 16 for FP32 in 2D), 1 = one step per kernel
-                                launch; 2D: 4 or 8 (or 16 for FP32) = temporal blocking with
-                                that depth; 3D: 2 or 4 for the FP32 precisions.  Results are
-                                bit-identical for every depth (FP32_BLOCKSUM: for every depth
-                                with the same partial-sum length). */
+  int time_block;            /* leapfrog steps per pass over HBM: 0 = library default (3 for
+                                FP64 2D problems of up to 8 frequencies with second order,
+                                explicit steps and constant or two-layer c, on tile shape 5;
+                                1 for the other FP64 problems and for 3D; 16 for FP32 in 2D),
+                                1 = one step per kernel launch; 2D: 2, 3, 4 or 8 for FP64, 4, 8
+                                or 16 for FP32 = temporal blocking with that depth; 3D: 2 or 4
+                                for the FP32 precisions.  Results are bit-identical for every
+                                depth (FP32_BLOCKSUM: for every depth with the same partial-sum
+                                length). */
   int order;                 /* order p of the spatial operator L_{ph}: 2 (0 means 2) or 4.
                                 Order 4: (-W_{j-2} + 16 W_{j-1} - 30 W_j + 16 W_{j+1} - W_{j+2})
                                 / (12 h^2) per axis, ghost values W_{-1} = -W_1 and
@@ -118,9 +121,14 @@ typedef struct {
                                 1 = 32x64, 512 threads; 2 = 64x64, 1024 threads (halved in
                                 y above 8 frequencies).  FP64 blocked kernel tile (points x by
                                 y): 0 = 32x64, 512 threads; 1 = 32x32, 512 threads; 2 = 32x48,
-                                512 threads; 3 = 32x32, 256 threads, two CTAs per SM (above 8
-                                frequencies always 32x32, 512 threads).  Every tile gives
-                                bit-identical results. */
+                                512 threads; 3 = 32x32, 256 threads, two CTAs per SM; 4 =
+                                32x16, 512 threads, two CTAs per SM; 5 = 32x16 tiles stepped by
+                                persistent CTAs (three per SM) that copy the next tile while
+                                stepping one (depths 2 to 4, up to 8 frequencies; the default
+                                with time_block 0).  Depths 2 and 3 run shapes 4 and 5 (the
+                                others as 1), depth 8 runs shapes 0 to 3 (4 and 5 as 3); above
+                                8 frequencies shapes 0 to 3 run as 1 and 5 as 4.  Every tile
+                                gives bit-identical results. */
   int time_stepping;         /* MFWH_TIME_EXPLICIT (0, default): leapfrog, alpha = 0, beta = 1;
                                 MFWH_TIME_IMPLICIT: trapezoidal scheme alpha = 1/2, beta = 0 of
                                 eq. WaveScheme (FP64 results, one step per launch).  Every

@@ -131,6 +131,9 @@ struct mfwh_handle_s {
   double* f = nullptr;              // forcing [nf][P]
   double* c2f = nullptr;            // c^2 per point [P] (MFWH_C_FIELD)
   bool use32 = false;               // wave solves in FP32 (the FP32 precisions)
+  // FP64 wave solves (all of an FP64 handle's; the FP64 residuals and products of an FP32
+  // handle): steps per launch (1 = one step per launch) and blocked-kernel tile
+  int depth64 = 1, shape64 = 0;
   // CUDA-graph mode (mfwh_set_graphs): each variant of the wave solve is captured once on the
   // staging buffers g_in / g_out and replayed as one graph launch.
   bool graphs = false;
@@ -401,10 +404,10 @@ mfwh_status apply_pi_direct(mfwh_handle_t h, const double* vin, double* vout, in
                             const double* vsub) {
   if (h->implicit) return apply_pi_implicit(h, vin, vout, forced, vsub);
   if (h->use32) return apply_pi32(h, vin, vout, forced, vsub);
-  // The FP64 blocked kernel serves FP64 handles (depth 4 or 8); FP64 wave solves of an FP32
-  // handle (the outer residuals of mfwh_solve_refined) take one step per launch.
-  if (h->plan.time_block > 1 && h->plan.precision == MFWH_PREC_FP64)
-    return apply_pi_tb(h, vin, vout, forced, vsub);
+  // The FP64 blocked kernel (depth 2, 3, 4 or 8) serves the FP64 wave solves of FP64 handles
+  // with time_block > 1 and those of 2D FP32 handles (the FP64 residuals and products of
+  // mfwh_solve_refined and mfwh_solve_relaxed).
+  if (h->depth64 > 1) return apply_pi_tb(h, vin, vout, forced, vsub);
   const Plan& P = h->plan;
   const int nf = h->nf;
   const int n_t = P.s.n_t;
@@ -459,8 +462,9 @@ mfwh_status apply_pi_tb(mfwh_handle_t h, const double* vin, double* vout, int fo
   const int n_t = P.s.n_t;
   const int n_run = h->tune_steps > 0 ? std::min(h->tune_steps, n_t) : n_t;
   const double dt = P.s.dt;
-  const int depth = P.time_block;
-  if (depth != 4 && depth != 8) return fail(MFWH_ERR_INVALID_ARG, "FP64 blocking depth must be 4 or 8");
+  const int depth = h->depth64;
+  if (depth != 2 && depth != 3 && depth != 4 && depth != 8)
+    return fail(MFWH_ERR_INVALID_ARG, "FP64 blocking depth must be 2, 3, 4 or 8");
   cudaStream_t st = h->stream;
   launch_init(nf, h->geom, vin, h->Wa, h->q, &P.w[0], st);
   h->total_launches += 1;
@@ -473,10 +477,12 @@ mfwh_status apply_pi_tb(mfwh_handle_t h, const double* vin, double* vout, int fo
   layer_coef(h, P.c2_hi, 1.0, 0.5 * dt * dt, &a.first_hi);
   a.wq_table = h->d_wq;
   a.cos_table = h->d_cos;
+  a.wq_host = P.w.data();
+  a.cos_host = P.cosf.data();
   a.dt2 = dt * dt;
   a.half_dt2 = 0.5 * dt * dt;
   a.depth = depth;
-  a.shape = P.tile_shape;
+  a.shape = h->shape64;
   a.forced = forced;
   a.subtract = vsub != nullptr;
   std::memcpy(a.binv, h->sh.binv, sizeof(a.binv));
@@ -1098,6 +1104,15 @@ mfwh_status mfwh_create(const mfwh_problem* prob, void* stream, mfwh_handle_t* o
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "initialising workspace"));
   h->use32 = P.precision != MFWH_PREC_FP64;
+  if (P.precision == MFWH_PREC_FP64) {
+    h->depth64 = P.time_block;
+    h->shape64 = P.tile_shape;
+  } else if (P.dim == 2 && P.order == 2 && !P.c2_field && h->nf <= 8) {
+    // the FP64 wave solves of an FP32 handle take the FP64 default: 3 steps per pass on the
+    // persistent pipelined kernel (bit-identical to one step per launch)
+    h->depth64 = 3;
+    h->shape64 = 5;
+  }
   std::memset(&h->sh, 0, sizeof(h->sh));
   // Epilogue V^{k+1} = C q + E V^k: implicit filter C = B^{-1}, E = 0; explicit filter
   // C = diag(B)^{-1}, E = -diag(B)^{-1} (B - diag(B)).
@@ -1983,7 +1998,7 @@ mfwh_status mfwh_autotune(const mfwh_problem* prob, void* stream, int* time_bloc
   } else if (P.dim == 3) {
     cand = {{1, 0}, {2, 0}, {4, 0}};
   } else if (P.precision == MFWH_PREC_FP64) {
-    cand = {{1, 0}, {4, 1}, {4, 3}, {8, 1}, {8, 3}};
+    cand = {{1, 0}, {2, 5}, {3, 5}, {4, 5}, {4, 4}, {4, 3}, {8, 3}};
   } else {
     for (int T : {4, 8, 16})
       for (int shape : {0, 1, 2}) cand.push_back({T, shape});

@@ -63,9 +63,11 @@ struct TBHost {
   LayerCoef reg_lo, reg_hi, first_lo, first_hi;
   const double* wq_table;    // device [(N_t + 1) * nf] w_{n,m}
   const double* cos_table;   // device [(N_t + 1) * nf] cos(omega~_m t^n)
+  const double* wq_host;     // host copies of the two tables (the per-launch coefficients of
+  const double* cos_host;    // depths up to 4 travel as kernel parameters)
   double dt2, half_dt2;
-  int n0, steps, depth;      // first level index, steps in this launch, template depth (4 or 8)
-  int shape;                 // tile: 0 = 32 x 64, 1 = 32 x 32, 2 = 32 x 48 points (32 x 32
+  int n0, steps, depth;      // first level index, steps in this launch, template depth (2, 3, 4, 8)
+  int shape;                 // tile 0-5 (wave_tb_kernels.cuh): 0 = 32 x 64, 1 = 32 x 32, 2 = 32 x 48 points (32 x 32
                              // above 8 frequencies)
   int forced, last, subtract;
   double binv[MFWH_MAX_NF * MFWH_MAX_NF];   // epilogue as in StepHost

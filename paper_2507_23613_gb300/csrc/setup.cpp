@@ -326,11 +326,13 @@ mfwh_status plan_problem(const mfwh_problem* p, Plan* out, double c2_field_max) 
       return fail(MFWH_ERR_INVALID_ARG,
                   "3D time_block must be 0 or 1 (or 2 or 4 for the FP32 precisions)");
   } else if (p->time_block != 0 && p->time_block != 1 && p->time_block != 4 &&
-             p->time_block != 8 && !(fp32 && p->time_block == 16)) {
-    return fail(MFWH_ERR_INVALID_ARG, "time_block must be 0, 1, 4 or 8 (or 16 for FP32)");
+             p->time_block != 8 && !(fp32 && p->time_block == 16) &&
+             !(!fp32 && (p->time_block == 2 || p->time_block == 3))) {
+    return fail(MFWH_ERR_INVALID_ARG,
+                "time_block must be 0, 1, 4 or 8 (or 16 for FP32, 2 or 3 for FP64)");
   }
-  if (p->tile_shape < 0 || p->tile_shape > (fp32 ? 2 : 3))
-    return fail(MFWH_ERR_INVALID_ARG, "tile_shape must be 0, 1 or 2 (or 3 for FP64)");
+  if (p->tile_shape < 0 || p->tile_shape > (fp32 ? 2 : 5))
+    return fail(MFWH_ERR_INVALID_ARG, "tile_shape must be 0, 1 or 2 (0 to 5 for FP64)");
   if (p->filter_update != MFWH_UPDATE_IMPLICIT && p->filter_update != MFWH_UPDATE_EXPLICIT)
     return fail(MFWH_ERR_INVALID_ARG, "filter_update must be implicit or explicit");
   if (p->order != 0 && p->order != 2 && p->order != 4)
@@ -358,12 +360,16 @@ mfwh_status plan_problem(const mfwh_problem* p, Plan* out, double c2_field_max) 
   const int nf = p->nf;
   s.nf = nf;
   P.dim = p->dim;
-  // FP64 default: one step per launch.  On GB300 the FP64 step is bound by the FP64 pipe
-  // (about 1.2 TFLOP/s), so blocking saves HBM bytes it is not waiting for and adds halo work.
-  // FP32 default: 16 steps per launch in 2D (fastest measured depth on GB300).
-  P.time_block = p->time_block != 0 ? p->time_block
-                                     : (fp32 && p->dim == 2 && p->order != 4 ? 16 : 1);
-  P.tile_shape = p->tile_shape;
+  // Defaults (fastest measured on GB300).  FP64, 2D, second order, constant or two-layer c,
+  // explicit steps, up to 8 frequencies: 3 steps per pass over HBM on the persistent pipelined
+  // kernel (tile shape 5).  Other FP64 problems: one step per launch.  FP32 in 2D: 16 steps
+  // per launch.
+  const bool fp64_blocked = !fp32 && p->dim == 2 && p->order != 4 && !field && !implicit &&
+                            p->nf <= 8;
+  P.time_block = p->time_block != 0
+                     ? p->time_block
+                     : (fp32 && p->dim == 2 && p->order != 4 ? 16 : (fp64_blocked ? 3 : 1));
+  P.tile_shape = (p->time_block == 0 && fp64_blocked && p->tile_shape == 0) ? 5 : p->tile_shape;
   P.order = p->order == 4 ? 4 : 2;
   P.filter_update = p->filter_update;
   P.precision = p->precision;

@@ -1,432 +1,19 @@
-// Temporally blocked MFWH wave step for 2D grids, FP64 wave levels, sm_103a.
-//
-// One launch advances the leapfrog scheme (eq. WaveSchemeA; the first step of a wave solve as
-// eq. implicitFirstStep with alpha = 0) by up to T steps and accumulates the N_f filter sums
-// (eq. pDefQ) on the way.  The interior points 1..n-1 of each axis are cut into tiles of
-// 32 x (TY K) points, one tile per CTA of 32 x TY threads.  A CTA loads W^n and W^{n-1} on its
-// tile plus a halo of T points into shared memory; at step s it updates the tile and the ring
-// of radius T-1-s around it (the points later steps still read), so after T steps W^{n+T} and
-// W^{n+T-1} are exact on the tile.  Per point and launch HBM sees one read and one write of the
-// two levels and of the N_f filter sums, instead of T of each.
-//
-// Thread (tx, ty) owns the K consecutive tile rows ty K .. ty K + K - 1 of column tx: the
-// current wave level and the N_f filter sums (float pairs, fpair.cuh) of its points stay in
-// registers for all T steps, vertical neighbours come from registers, and only the previous
-// level, the left and right neighbours and the rows just above and below the strip come from
-// shared memory.  The ring is
-// spread evenly over all threads by a flat index.  On sm_103a the FP64 pipe bounds this kernel
-// (a warp instruction occupies it for about 64 cycles), so the float pair of each new value is
-// split off its bit pattern on the integer and FP32 pipes (fpair_split) and the filter updates
-// run on the FP32 pipe: a point-step of the homogeneous 5-point scheme costs two FP64 adds and
-// three FP64 FMAs.
-//
-// The per-point arithmetic is the unblocked kernel's (k_step in wave.cu) in the same order, so
-// results are bit-identical to it.  The last launch of a wave solve fuses the filter solve
-// V = C q + E V^k (eq. waveHoltzMatrixIteration; E = 0 for the implicit filter).
-#include <cuda_runtime.h>
-
-#include <type_traits>
-
-#include "fpair.cuh"
-#include "kernels.h"
+// Host entry point of the FP64 temporally blocked 2D wave step: dispatch on the number of
+// frequencies to the instantiations in wave_tb_p1.cu .. wave_tb_p5.cu.  The kernel and the
+// arithmetic it follows are described in wave_tb_kernels.cuh.
+#include "wave_tb_kernels.cuh"
 
 namespace mfwh {
-namespace {
-
-constexpr int kTX = 32;   // threads in x = tile width
-
-template <int NF>
-struct TBParams {
-  LayerCoef reg_lo, reg_hi;       // regular step (a_cur = 2, kappa = dt^2)
-  LayerCoef first_lo, first_hi;   // first step of a wave solve (a_cur = 1, kappa = dt^2 / 2)
-  const double* wq_table;         // [(N_t + 1) * NF] filter weights w_{n,m}
-  const double* cos_table;        // [(N_t + 1) * NF] cos(omega~_m t^n)
-  double dt2, half_dt2;
-  int n0;                         // this launch computes W^{n0+1} .. W^{n0+steps}
-  int steps;                      // 1 .. T
-  int forced;
-  int last;                       // fuse the filter solve; v_out written instead of W and q
-  int subtract;                   // v_out = v_sub - V^{k+1}
-  int has_e;                      // V^{k+1} = C q + E V^k with E != 0 (explicit filter)
-  const double* vprev;            // V^k
-  double binv[NF * NF];           // C
-  double emat[NF * NF];           // E
-};
-
-// Clamp a local coordinate bound (64-bit global difference) to [lo, hi].
-__device__ __forceinline__ int clamp_local(int64_t v, int lo, int hi) {
-  return (int)(v < lo ? lo : (v > hi ? hi : v));
-}
-
-// New level at local point l (row length EX) of a ring point: the operations of k_step in the
-// same order.  A: W^n, wprev: W^{n-1} at l (0 on the first step of a wave solve, where the
-// first-step coefficients make the update W^1 = W^0 + dt^2/2 (c^2 Delta_h W^0 - F^0)).
-template <int NF, int EX, bool FORCED>
-__device__ __forceinline__ double ring_update(const double* A, double wprev, int l,
-                                              const LayerCoef& L, const double* fneg,
-                                              const double* __restrict__ f, int64_t p,
-                                              int64_t points) {
-  const double wc = A[l];
-  const double sx = A[l - 1] + A[l + 1];
-  const double sy = A[l - EX] + A[l + EX];
-  double acc = fma(L.A0, wc, -wprev);     // wprev = 0 on the first step: exactly L.A0 * wc
-  acc = fma(L.Ax, sx, acc);
-  acc = fma(L.Ay, sy, acc);
-  if (FORCED) {
-#pragma unroll
-    for (int m = 0; m < NF; ++m) acc = fma(-fneg[m], f[m * points + p], acc);
-  }
-  return acc;
-}
-
-// Local coordinates of flat ring index e at radius r: the 2r rows of BX + 2r points above and
-// below the tile, then the BY rows of 2r points left and right of it.  Quotients by the row
-// lengths come from a float reciprocal: (e + 1/2) / len is at least 1/(2 len) from an integer,
-// far above the rounding of the product for the ring sizes used here.
-template <int T, int BX, int BY>
-__device__ __forceinline__ void ring_coords(int e, int r, int rw, int top, float inv_rw,
-                                            float inv_2r, int& lx, int& ly) {
-  if (e < top) {
-    const int row = (int)(((float)e + 0.5f) * inv_rw);
-    lx = T - r + (e - row * rw);
-    ly = row < r ? T - r + row : T + BY + row - r;
-  } else {
-    const int e2 = e - top;
-    const int row = (int)(((float)e2 + 0.5f) * inv_2r);
-    const int col = e2 - row * 2 * r;
-    ly = T + row;
-    lx = col < r ? T - r + col : T + BX + col - r;
-  }
-}
-
-// TY threads in y (16: one CTA of 512 threads per SM; 8: two CTAs of 256 threads per SM, so
-// that one CTA's loads, stores and barriers overlap the other's FP64 work).
-template <int NF, int T, int K, int TY>
-__global__ void __launch_bounds__(kTX * TY, TY == 8 ? 2 : 1)
-k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
-       double* __restrict__ Wc_out, double* __restrict__ Wp_out, const double* __restrict__ f,
-       float2* __restrict__ q, double* vout, const double* vsub, const TBParams<NF> a,
-       const Geom g) {
-  constexpr int BX = kTX, BY = TY * K;
-  constexpr int EX = BX + 2 * T, EY = BY + 2 * T, E = EX * EY;
-  constexpr int NT = kTX * TY;
-  extern __shared__ double smem[];
-  double* A = smem;                  // W^n on the extended tile
-  double* B = smem + E;              // W^{n-1} on the ring, overwritten by W^{n+1}
-  double* s_wq = smem + 2 * E;       // [T][NF] filter weights of the new level per step
-  double* s_fc = s_wq + T * NF;      // [T][NF] kappa cos(omega~_m t^n) per step
-  float* s_wh = reinterpret_cast<float*>(s_fc + T * NF);   // [T][NF] s_wq as float pairs
-  float* s_wl = s_wh + T * NF;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTX + tx;
-  // global coordinates of local (0, 0); tiles start at the first interior point
-  const int64_t x0 = 1 + (int64_t)blockIdx.x * BX - T, y0 = 1 + (int64_t)blockIdx.y * BY - T;
-  // local bounds: grid points [gl, gh], interior points [il, ih] (32-bit)
-  const int glx = clamp_local(-x0, 0, EX), ghx = clamp_local(g.nx - x0, -1, EX - 1);
-  const int gly = clamp_local(-y0, 0, EY), ghy = clamp_local(g.ny - y0, -1, EY - 1);
-  const int ilx = clamp_local(1 - x0, 0, EX), ihx = clamp_local(g.nx - 1 - x0, -1, EX - 1);
-  const int ily = clamp_local(1 - y0, 0, EY), ihy = clamp_local(g.ny - 1 - y0, -1, EY - 1);
-  // c^2 layer: points whose local coordinate along the layer axis is >= lay_thr use hi
-  const bool lay_x = g.layer_axis == 0;
-  const int lay_thr = clamp_local(g.layer_split - (lay_x ? x0 : y0), -1, EX + EY);
-  // every point updated by any step interior, all with one c^2: no per-point tests needed
-  const bool simple = ilx <= 1 && ihx >= EX - 2 && ily <= 1 && ihy >= EY - 2 &&
-                      (lay_thr <= 0 || lay_thr >= (lay_x ? EX : EY));
-  const bool all_hi = lay_thr <= 0;
-
-  // Both levels on the tile plus halo; points outside the grid read as 0.
-  for (int e = tid; e < E; e += NT) {
-    const int ly = e / EX, lx = e - ly * EX;
-    const bool in = ly >= gly && ly <= ghy && lx >= glx && lx <= ghx;
-    const int64_t p = (y0 + ly) * g.sy + x0 + lx;
-    A[e] = in ? Wc_in[p] : 0.0;
-    B[e] = (in && Wp_in != nullptr) ? Wp_in[p] : 0.0;
-  }
-  // Per-step coefficients of this launch.
-  for (int e = tid; e < a.steps * NF; e += NT) {
-    const int st = e / NF, m = e - st * NF;
-    const int n = a.n0 + st;
-    const double w = a.wq_table[(n + 1) * NF + m];
-    s_wq[e] = w;
-    const float wh = (float)w;
-    s_wh[e] = wh;
-    s_wl[e] = (float)(w - (double)wh);
-    s_fc[e] = a.forced ? (n == 0 ? a.half_dt2 : a.dt2) * a.cos_table[n * NF + m] : 0.0;
-  }
-  // The strip: local column lxo, rows lyo .. lyo + K - 1.
-  const int lxo = T + tx, lyo = T + ty * K;
-  const int64_t p0 = (y0 + lyo) * g.sy + x0 + lxo;
-  const bool col_int = lxo >= ilx && lxo <= ihx;
-  bool own_int[K], own_up[K];
-  double wc[K];
-  float2 qr[K][NF];
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    own_int[k] = col_int && lyo + k >= ily && lyo + k <= ihy;
-    own_up[k] = (lay_x ? lxo : lyo + k) >= lay_thr;
-#pragma unroll
-    for (int m = 0; m < NF; ++m)
-      qr[k][m] = own_int[k] ? q[m * g.points + p0 + k * g.sy] : make_float2(0.0f, 0.0f);
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < K; ++k) wc[k] = A[(lyo + k) * EX + lxo];
-
-  // The steps in three compiled copies with the same per-point arithmetic: ALLINT for
-  // homogeneous launches of CTAs whose updated points are all interior with one c^2 (no
-  // forcing terms, no per-point interior or layer tests), and the general one with and
-  // without the forcing terms (FORCED), so that no copy carries FP64 work under a predicate.
-  // The filter update of a step's new values is deferred into the next step, after that
-  // step's FP64 stencil in the same block, so that each warp's FP32 pair arithmetic overlaps
-  // FP64 work instead of following it behind the step's barrier; the updates keep their order.
-  float2 pend[K];   // float pairs of the newest owned values, not yet added to the sums
-  auto filter_update = [&](int s) {   // add pend with the weights of step s
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      if (!own_int[k]) continue;
-#pragma unroll
-      for (int m = 0; m < NF; ++m)
-        qr[k][m] = fpair_fma(s_wh[s * NF + m], s_wl[s * NF + m], pend[k].x, pend[k].y, qr[k][m]);
-    }
-  };
-  // The steps in three compiled copies with the same per-point arithmetic: ALLINT for
-  // homogeneous launches of CTAs whose updated points are all interior with one c^2 (no
-  // forcing terms, no per-point interior or layer tests), and the general one with and
-  // without the forcing terms (FORCED), so that no copy carries FP64 work under a predicate.
-  auto run_steps = [&](auto allint_c, auto forced_c) {
-    constexpr bool ALLINT = decltype(allint_c)::value;
-    constexpr bool FORCED = decltype(forced_c)::value;
-    auto step = [&](int s, auto defer_c) {
-      constexpr bool DEFER = decltype(defer_c)::value;   // the previous step's update pending
-      const int r = a.steps - 1 - s;          // ring radius still needed after this step
-      const int n = a.n0 + s;                 // computing W^{n+1}
-      const bool first = n == 0;
-      const LayerCoef& lo = first ? a.first_lo : a.reg_lo;
-      const LayerCoef& hi = first ? a.first_hi : a.reg_hi;
-      const double* fneg = s_fc + s * NF;
-      const bool final_step = a.last && s == a.steps - 1;
-      // owned strip: centre and vertical neighbours from registers
-      {
-        const double above = A[(lyo - 1) * EX + lxo];
-        const double below = A[(lyo + K) * EX + lxo];
-        double wn[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          wn[k] = wc[k];
-          if (!ALLINT && !own_int[k]) continue;   // boundary and outside points keep W = 0
-          const int l = (lyo + k) * EX + lxo;
-          const LayerCoef& L = ALLINT ? (all_hi ? hi : lo) : (own_up[k] ? hi : lo);
-          const double up = k == 0 ? above : wc[k - 1];
-          const double dn = k == K - 1 ? below : wc[k + 1];
-          const double sx = A[l - 1] + A[l + 1];
-          const double sy = up + dn;
-          // W^{n-1} of the strip is still in B (0 on the first step)
-          double acc = fma(L.A0, wc[k], -B[l]);
-          acc = fma(L.Ax, sx, acc);
-          acc = fma(L.Ay, sy, acc);
-          if (FORCED) {
-#pragma unroll
-            for (int m = 0; m < NF; ++m)
-              acc = fma(-fneg[m], f[m * g.points + p0 + k * g.sy], acc);
-          }
-          wn[k] = acc;
-        }
-        if (DEFER) filter_update(s - 1);
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          if (!ALLINT && !own_int[k]) continue;
-          B[(lyo + k) * EX + lxo] = wn[k];
-          wc[k] = wn[k];
-          // the last level of a wave solve enters the sums in FP64 in the epilogue
-          if (!final_step) pend[k] = fpair_split(wn[k]);
-        }
-      }
-      // ring of radius r around the tile
-      if (r > 0) {
-        const int rw = BX + 2 * r;
-        const int top = 2 * r * rw;
-        const int ring = top + 2 * r * BY;
-        const float inv_rw = 1.0f / (float)rw, inv_2r = 1.0f / (float)(2 * r);
-        for (int e = tid; e < ring; e += NT) {
-          int lx, ly;
-          ring_coords<T, BX, BY>(e, r, rw, top, inv_rw, inv_2r, lx, ly);
-          if (!ALLINT && !simple && (lx < ilx || lx > ihx || ly < ily || ly > ihy)) continue;
-          const LayerCoef& L =
-              (ALLINT || simple) ? (all_hi ? hi : lo) : (((lay_x ? lx : ly) >= lay_thr) ? hi : lo);
-          const int l = ly * EX + lx;
-          const int64_t p = (y0 + ly) * g.sy + x0 + lx;
-          B[l] = ring_update<NF, EX, FORCED>(A, B[l], l, L, fneg, f, p, g.points);
-        }
-      }
-      __syncthreads();
-      double* t = A;
-      A = B;
-      B = t;
-    };
-    step(0, std::false_type{});
-    for (int s = 1; s < a.steps; ++s) step(s, std::true_type{});
-  };
-  if (a.forced)
-    run_steps(std::false_type{}, std::true_type{});
-  else if (simple)
-    run_steps(std::true_type{}, std::false_type{});
-  else
-    run_steps(std::false_type{}, std::false_type{});
-  // the last step's update (except for the final level of a wave solve)
-  if (!a.last) filter_update(a.steps - 1);
-
-  // wc = W^{n0+steps} on the strip, B = W^{n0+steps-1}
-  if (!a.last) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      if (!own_int[k]) continue;
-      const int64_t p = p0 + k * g.sy;
-      Wc_out[p] = wc[k];
-      Wp_out[p] = B[(lyo + k) * EX + lxo];
-#pragma unroll
-      for (int m = 0; m < NF; ++m) q[m * g.points + p] = qr[k][m];
-    }
-    return;
-  }
-  // Last launch: V^{k+1} = C (q + w_{N_t} W^{N_t}) + E V^k at the interior points, 0 on the
-  // boundary points of this CTA's part of the grid.
-  const double* wq = s_wq + (a.steps - 1) * NF;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    if (!own_int[k]) continue;
-    const int64_t p = p0 + k * g.sy;
-    double qq[NF];
-#pragma unroll
-    for (int j = 0; j < NF; ++j) qq[j] = fma(wq[j], wc[k], fpair_value(qr[k][j]));
-    double vk[NF];
-    if (a.has_e) {
-#pragma unroll
-      for (int j = 0; j < NF; ++j) vk[j] = a.vprev[j * g.points + p];
-    }
-    double out[NF];
-#pragma unroll
-    for (int m = 0; m < NF; ++m) {
-      double sacc = 0.0;
-#pragma unroll
-      for (int j = 0; j < NF; ++j) sacc = fma(a.binv[m * NF + j], qq[j], sacc);
-      if (a.has_e) {
-#pragma unroll
-        for (int j = 0; j < NF; ++j) sacc = fma(a.emat[m * NF + j], vk[j], sacc);
-      }
-      out[m] = sacc;
-    }
-#pragma unroll
-    for (int m = 0; m < NF; ++m)
-      vout[m * g.points + p] = a.subtract ? vsub[m * g.points + p] - out[m] : out[m];
-  }
-  // Boundary points: the CTA at each edge of the tile grid writes the boundary lines along
-  // its part of that edge (the parts partition the edges, corners included).
-  const int64_t xs = blockIdx.x == 0 ? 0 : 1 + (int64_t)blockIdx.x * BX;
-  const int64_t xe = blockIdx.x == gridDim.x - 1 ? g.nx + 1 : 1 + (int64_t)(blockIdx.x + 1) * BX;
-  const int64_t ys = blockIdx.y == 0 ? 0 : 1 + (int64_t)blockIdx.y * BY;
-  const int64_t ye = blockIdx.y == gridDim.y - 1 ? g.ny + 1 : 1 + (int64_t)(blockIdx.y + 1) * BY;
-  auto zero_point = [&](int64_t gx, int64_t gy) {
-#pragma unroll
-    for (int m = 0; m < NF; ++m) vout[m * g.points + gy * g.sy + gx] = 0.0;
-  };
-  if (ys == 0)
-    for (int64_t gx = xs + tid; gx < xe; gx += NT) zero_point(gx, 0);
-  if (ye == g.ny + 1)
-    for (int64_t gx = xs + tid; gx < xe; gx += NT) zero_point(gx, g.ny);
-  if (xs == 0)
-    for (int64_t gy = ys + tid; gy < ye; gy += NT) zero_point(0, gy);
-  if (xe == g.nx + 1)
-    for (int64_t gy = ys + tid; gy < ye; gy += NT) zero_point(g.nx, gy);
-}
-
-template <int NF, int T, int K, int TY>
-void tb_launch_k(const Geom& g, const double* Wc_in, const double* Wp_in, double* Wc_out,
-                 double* Wp_out, const double* f, double* q, double* vout, const double* vsub,
-                 const TBHost& h, cudaStream_t st) {
-  constexpr int BX = kTX, BY = TY * K;
-  constexpr int EX = BX + 2 * T, EY = BY + 2 * T;
-  constexpr size_t smem = sizeof(double) * (2 * EX * EY + 2 * T * NF) + sizeof(float) * 2 * T * NF;
-  // The attribute is per device; set it once per device for this instance.
-  static bool configured[64] = {};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64 || !configured[dev]) {
-    cudaFuncSetAttribute(k_tb2d<NF, T, K, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    if (dev >= 0 && dev < 64) configured[dev] = true;
-  }
-  TBParams<NF> a;
-  a.reg_lo = h.reg_lo;
-  a.reg_hi = h.reg_hi;
-  a.first_lo = h.first_lo;
-  a.first_hi = h.first_hi;
-  a.wq_table = h.wq_table;
-  a.cos_table = h.cos_table;
-  a.dt2 = h.dt2;
-  a.half_dt2 = h.half_dt2;
-  a.n0 = h.n0;
-  a.steps = h.steps;
-  a.forced = h.forced;
-  a.last = h.last;
-  a.subtract = h.subtract;
-  a.has_e = h.has_e && h.vprev != nullptr;
-  a.vprev = h.vprev;
-  for (int m = 0; m < NF; ++m)
-    for (int j = 0; j < NF; ++j) {
-      a.binv[m * NF + j] = h.binv[m * MFWH_MAX_NF + j];
-      a.emat[m * NF + j] = h.emat[m * MFWH_MAX_NF + j];
-    }
-  // tiles over the interior points 1 .. n-1 of each axis
-  dim3 grid((unsigned)((g.nx - 1 + BX - 1) / BX), (unsigned)((g.ny - 1 + BY - 1) / BY));
-  k_tb2d<NF, T, K, TY><<<grid, dim3(kTX, TY), smem, st>>>(Wc_in, Wp_in, Wc_out, Wp_out, f,
-                                                          reinterpret_cast<float2*>(q), vout,
-                                                          vsub, a, g);
-}
-
-// Tile shapes: 0 = 32 x 64 points (512 threads, 4 rows each), 1 = 32 x 32 (512 threads, 2
-// rows each), 2 = 32 x 48 (512 threads, 3 rows each), 3 = 32 x 32 (256 threads, 4 rows each,
-// two CTAs per SM).  Above 8 frequencies the filter sums of more than two points per thread
-// would not fit in registers, and every shape takes 32 x 32 tiles of 512 threads.
-template <int NF, int T>
-void tb_launch_shape(const Geom& g, const double* Wc_in, const double* Wp_in, double* Wc_out,
-                     double* Wp_out, const double* f, double* q, double* vout, const double* vsub,
-                     const TBHost& h, cudaStream_t st) {
-  constexpr bool wide = NF > 8;
-  if (wide || h.shape == 1)
-    tb_launch_k<NF, T, 2, 16>(g, Wc_in, Wp_in, Wc_out, Wp_out, f, q, vout, vsub, h, st);
-  else if (h.shape == 2)
-    tb_launch_k<NF, T, (wide ? 2 : 3), 16>(g, Wc_in, Wp_in, Wc_out, Wp_out, f, q, vout, vsub, h,
-                                             st);
-  else if (h.shape == 3)
-    tb_launch_k<NF, T, (wide ? 2 : 4), (wide ? 16 : 8)>(g, Wc_in, Wp_in, Wc_out, Wp_out, f, q,
-                                                          vout, vsub, h, st);
-  else
-    tb_launch_k<NF, T, (wide ? 2 : 4), 16>(g, Wc_in, Wp_in, Wc_out, Wp_out, f, q, vout, vsub, h,
-                                             st);
-}
-
-template <int NF>
-void tb_launch_depth(const Geom& g, const double* Wc_in, const double* Wp_in, double* Wc_out,
-                     double* Wp_out, const double* f, double* q, double* vout, const double* vsub,
-                     const TBHost& h, cudaStream_t st) {
-  if (h.depth <= 4)
-    tb_launch_shape<NF, 4>(g, Wc_in, Wp_in, Wc_out, Wp_out, f, q, vout, vsub, h, st);
-  else
-    tb_launch_shape<NF, 8>(g, Wc_in, Wp_in, Wc_out, Wp_out, f, q, vout, vsub, h, st);
-}
-
-}  // namespace
 
 void launch_tb2d(int nf, const Geom& g, const double* Wc_in, const double* Wp_in, double* Wc_out,
                  double* Wp_out, const double* f, double* q, double* vout, const double* vsub,
                  const TBHost& h, cudaStream_t st) {
-  switch (nf) {
-#define CASE(N) \
-  case N: tb_launch_depth<N>(g, Wc_in, Wp_in, Wc_out, Wp_out, f, q, vout, vsub, h, st); break;
-    CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
-    CASE(9) CASE(10) CASE(11) CASE(12) CASE(13) CASE(14) CASE(15) CASE(16)
-#undef CASE
-    default: break;
-  }
+  TbFn fn = nf <= 3    ? tb_fn_p1(nf)
+            : nf <= 6  ? tb_fn_p2(nf)
+            : nf <= 8  ? tb_fn_p3(nf)
+            : nf <= 12 ? tb_fn_p4(nf)
+                       : tb_fn_p5(nf);
+  if (fn != nullptr) fn(g, Wc_in, Wp_in, Wc_out, Wp_out, f, q, vout, vsub, h, st);
 }
 
 }  // namespace mfwh

@@ -22,11 +22,16 @@ def test_bytes_and_flops_per_point_step():
     assert bench.flops_per_point_step(8, False) == 8
     assert bench.flops_per_point_step(8, True) == 24
     assert bench.flops_per_point_step(4, False, dim=3) == 11
+    # a blocked launch reads and writes both levels and the 8 float-pair sums once, whatever
+    # its depth; forced launches read the 8 forcing grids once
+    assert bench.blocked_bytes_per_point_launch(8, False) == (4 + 2 * 8) * 8 == 160
+    assert bench.blocked_bytes_per_point_launch(8, True) == (4 + 3 * 8) * 8 == 224
 
 
 def test_traffic_only_for_the_kernel_it_was_taken_on(tmp_path, monkeypatch):
     key = bench.kernel_source_key()
     assert len(key) == 16 and key == bench.kernel_source_key()
+    assert len(bench.blocked_kernel_source_key()) == 16 and bench.blocked_kernel_source_key() != key
     prof = tmp_path / "profiles"
     prof.mkdir()
     (prof / "k.txt").write_text("# comment: 1\nsource_sha256: %s\ndram_bytes_per_launch: 123.5\n"
@@ -36,6 +41,13 @@ def test_traffic_only_for_the_kernel_it_was_taken_on(tmp_path, monkeypatch):
     assert bench.kernel_traffic("k.txt", key) == 123.5
     assert bench.kernel_traffic("old.txt", key) is None
     assert bench.kernel_traffic("missing.txt", key) is None
+
+
+def test_committed_fp64_blocked_profile_matches_its_kernel():
+    """The FP64 pipelined blocked kernel's ncu summary carries the hash of the source it was
+    taken on (bench.py uses its DRAM bytes only while that holds)."""
+    assert bench.kernel_traffic("k_tb2d_pipe_square1025_nf8.txt",
+                                bench.blocked_kernel_source_key()) is not None
 
 
 def test_committed_fp32_profile_matches_its_kernel():

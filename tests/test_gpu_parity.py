@@ -171,8 +171,10 @@ def test_pi_in_place():
                                                   ((200, 170), 4, 9, None),
                                                   ((150, 140), 3, 10, 0), ((130, 160), 3, 11, 1)])
 def test_time_blocking_is_bit_identical(shape, nf, seed, layer):
-    """Temporal blocking (4 or 8 leapfrog steps per pass over HBM, halo tiles in shared
-    memory, tiles of 32 x 64, 32 x 32 and 32 x 48 points, CTAs of 512 or 256 threads) performs
+    """Temporal blocking (2, 3, 4 or 8 leapfrog steps per pass over HBM, halo tiles in shared
+    memory, tiles of 32 x 64, 32 x 48, 32 x 32 and 32 x 16 points, one to four rows per thread,
+    CTAs of 512 or 256 threads, and persistent CTAs that copy the next tile while stepping one)
+    performs
     the same floating-point operations per point as one step per launch, so Pi, S and the
     GMRES iterate are bit-identical for every depth and tile; also checked against the
     oracle.  N_t is not a
@@ -185,7 +187,8 @@ def test_time_blocking_is_bit_identical(shape, nf, seed, layer):
     v = random_v(wl, seed + 1)
     kw = {} if layer is None else dict(c_lo=1.0, c_hi=1.4, interface=0.37, layer_axis=layer)
     outs = {}
-    for tb, tshape in ((1, 0), (4, 0), (4, 1), (4, 2), (4, 3), (8, 0), (8, 1), (8, 2), (8, 3)):
+    for tb, tshape in ((1, 0), (2, 4), (2, 1), (2, 5), (3, 4), (3, 1), (3, 5), (4, 0), (4, 1),
+                       (4, 2), (4, 3), (4, 4), (4, 5), (8, 0), (8, 1), (8, 2), (8, 3)):
         solver = M.Solver(wl.n, wl.length, wl.omega, dev(wl.forcing), n_p=wl.n_p, cfl=wl.cfl,
                           filter_mode=_lib.FILTER_TRADITIONAL, time_block=tb, tile_shape=tshape,
                           **kw)

@@ -198,11 +198,12 @@ def test_adjusted_frequency_matches_definition():
     dict(cfl=1.5),
     dict(n_p=0),
     dict(omega=[1.0] * 17),            # too many frequencies
-    dict(time_block=3),                # temporal-blocking depth not 0, 1, 4 or 8
+    dict(time_block=5),                # temporal-blocking depth not 0, 1, 2, 3, 4 or 8
+    dict(time_block=3, precision=1),   # depths 2 and 3 are FP64-only
     dict(n=(8, 8, 8), length=(1.0, 1.0, 1.0), time_block=8),   # 3D is not blocked
     dict(time_block=16),               # depth 16 is FP32-only
     dict(precision=3),                 # unknown precision
-    dict(tile_shape=4),                # FP64 tiles 0-3
+    dict(tile_shape=6),                # FP64 tiles 0-5
     dict(tile_shape=3, precision=1),   # FP32 tiles 0-2
     dict(order=3),                     # only second and fourth order
     dict(filter_update=2),             # implicit (0) or explicit (1) only

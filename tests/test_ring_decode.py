@@ -13,7 +13,7 @@ import pytest
 
 BX = 32
 SHAPES = [16 * 2, 16 * 1, 32 * 1, 16 * 4, 16 * 2]   # BY of the FP32 tile shapes 0-2 (K = 2 or 1)
-SHAPES += [16 * 4, 16 * 2, 16 * 3]                   # BY of the FP64 tile shapes 0-2 (K = 4, 2, 3)
+SHAPES += [16 * 4, 16 * 2, 16 * 3, 8 * 4, 16 * 1]   # BY of the FP64 tile shapes 0-4
 
 
 def decode(e, r, T, BY):
@@ -34,7 +34,7 @@ def decode(e, r, T, BY):
     return lx, ly
 
 
-@pytest.mark.parametrize("T", [4, 8, 16])
+@pytest.mark.parametrize("T", [2, 3, 4, 8, 16])
 @pytest.mark.parametrize("BY", sorted(set(SHAPES)))
 def test_ring_decode_covers_each_point_once(T, BY):
     EX, EY = BX + 2 * T, BY + 2 * T
