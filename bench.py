@@ -73,6 +73,10 @@ def parse():
     ap.add_argument("--warm-start", action="store_true",
                     help="train the warm-start network on MFWH solutions and compare GMRES from "
                          "its prediction with GMRES from zero")
+    ap.add_argument("--cnn", action="store_true",
+                    help="time the warm-start network's forward pass and training step (tensor-"
+                         "core convolutions) on a synthetic batch")
+    ap.add_argument("--cnn-batch", type=int, default=48, help="images per batch with --cnn")
     ap.add_argument("--ws-n", type=int, default=128, help="cells per axis of the warm-start workload")
     ap.add_argument("--ws-train", type=int, default=683, help="training problems (6 samples each)")
     ap.add_argument("--ws-test", type=int, default=24, help="held-out problems")
@@ -911,6 +915,68 @@ def run_implicit_scaling(args):
     print(json.dumps(out), flush=True)
 
 
+def conv_flops(layers, channels, in_channels, pixels):
+    """Tensor-core FLOPs of one forward pass of the warm-start network: 2 x pixels x 9 taps x
+    Cin x Cout per 3 x 3 layer (in_channels -> channels, channels -> channels, ..., -> 1)."""
+    chans = [in_channels] + [channels] * (layers - 1) + [1]
+    return 2 * 9 * pixels * sum(a * b for a, b in zip(chans[:-1], chans[1:]))
+
+
+def run_cnn(args):
+    """The warm-start network's kernels on a synthetic batch (129^2 images, the warm-start
+    workload's grid, 2 input channels, 5 layers of 32 channels): forward passes (implicit-GEMM
+    convolutions on tcgen05) and training steps (forward, input and weight gradients, Adam)."""
+    import torch
+    import paper_2507_23613_gb300 as M
+    from paper_2507_23613_gb300 import build
+    torch.cuda.set_device(0)
+    build.build()
+    M._lib.load()
+    B, H = args.cnn_batch, args.ws_n + 1
+    g = torch.Generator(device="cuda").manual_seed(args.seed)
+    x = torch.randn((B, 2, H, H), generator=g, device="cuda", dtype=torch.float32)
+    t = torch.randn((B, 1, H, H), generator=g, device="cuda", dtype=torch.float32)
+    mask = torch.ones((B, 1, H, H), device="cuda", dtype=torch.float32)
+    y = torch.empty((B, 1, H, H), device="cuda", dtype=torch.float32)
+    net = M.CNN(layers=5, channels=32, in_channels=2, seed=args.seed)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        net.forward(x, y)
+        net.train_step(x, t, mask, 1e-4)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        net.forward(x, y)
+    ev[1].record(stream)
+    ev[2].record(stream)
+    for _ in range(args.steps):
+        net.train_step(x, t, mask, 1e-4)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = ev[0].elapsed_time(ev[1]) / args.steps
+    train_ms = ev[2].elapsed_time(ev[3]) / args.steps
+    flops = conv_flops(5, 32, 2, B * H * H)
+    peak = 1973.9
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        with open(pk) as fh:
+            peak = float(json.load(fh).get("bf16_tflops", peak))
+    tf = flops / (fwd_ms * 1e-3) / 1e12
+    net.close()
+    print(json.dumps({
+        "metric": "warm-start network forward TFLOP/s (BF16 tensor cores)", "value": round(tf, 2),
+        "unit": "TFLOP/s", "higher_is_better": True, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "cnn5x32_batch%d_%dx%d" % (B, H, H), "layers": 5, "channels": 32},
+        "forward_ms": round(fwd_ms, 3), "train_step_ms": round(train_ms, 3),
+        "roofline": {"bound": "tensor", "achieved": round(tf, 2), "peak": peak,
+                     "unit": "TFLOP/s", "frac": round(tf / peak, 4),
+                     "flops_per_forward": flops,
+                     "note": "K = 9 Cin <= 288 and N = Cout <= 32 per implicit GEMM: far too "
+                             "little reuse per operand byte for the tensor peak"}}), flush=True)
+
+
 def run_warm_start(args):
     """Learned warm start: MFWH-converged FP64 solutions of seeded problems train the network
     (inputs f_m / max|f_m| and omega_m / 45, target the shape V_m / max|V_m|, amplitude fitted to
@@ -1096,6 +1162,8 @@ def main():
         return run_cube(args) if rank == 0 else None
     if args.warm_start:
         return run_warm_start(args) if rank == 0 else None
+    if args.cnn:
+        return run_cnn(args) if rank == 0 else None
 
     import torch
     import paper_2507_23613_gb300 as M

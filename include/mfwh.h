@@ -464,6 +464,17 @@ mfwh_status mfwh_mg_stats(mfwh_handle_t h, int64_t* solves, int64_t* cycles,
  * used again.  Explicit handles accept the call and ignore the limit (no grid barriers). */
 mfwh_status mfwh_set_wait_limit(mfwh_handle_t h, double seconds);
 
+/* Index checks of the debugging build (a debugging aid; the paper has none).  The library
+ * built with -DMFWH_BOUNDS_CHECK (libmfwh_bc.so) tests the indices of the FP64 step kernels'
+ * global and shared-memory accesses against the extents of their arrays; an out-of-range
+ * index is skipped, counted in the handle's fault record, and the first one is kept.
+ * *count: out-of-range indices met by this handle's kernels so far, or -1 for the normal
+ * build (no checks compiled); *index, *extent: the first one and the extent it exceeded;
+ * *line: its source line (index, extent, line may be NULL).  Synchronises the stream in the
+ * checked build. */
+mfwh_status mfwh_debug_bounds(mfwh_handle_t h, int64_t* count, int64_t* index, int64_t* extent,
+                              int* line);
+
 /* Release the handle and its device workspace (waits for its stream). */
 void mfwh_destroy(mfwh_handle_t h);
 

@@ -342,6 +342,14 @@ class Solver:
     def set_graphs(self, enable=True):
         _lib.check(_lib.load().mfwh_set_graphs(self._handle, int(bool(enable))))
 
+    def debug_bounds(self):
+        """(count, index, extent, line) of the index-checked build's fault record; count is
+        -1 for the normal build (no checks compiled)."""
+        count, index, extent, line = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int()
+        _lib.check(_lib.load().mfwh_debug_bounds(self._handle, C.byref(count), C.byref(index),
+                                                 C.byref(extent), C.byref(line)))
+        return count.value, index.value, extent.value, line.value
+
     def residual(self, v):
         r = np.zeros(self.nf)
         _lib.check(_lib.load().mfwh_residual(self._handle, _as_ptr(v), _dptr(r)))

@@ -8,7 +8,8 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libmfwh.so")
+# MFWH_LIBRARY selects another build of the library (the index-checked libmfwh_bc.so).
+LIB_PATH = os.environ.get("MFWH_LIBRARY") or os.path.join(HERE, "libmfwh.so")
 
 MAX_NF = 16
 
@@ -150,6 +151,8 @@ _SIGNATURES = {
     "mfwh_mg_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                 C.POINTER(C.c_int64), C.POINTER(C.c_int), C.c_int]),
     "mfwh_set_wait_limit": (C.c_int, [C.c_void_p, C.c_double]),
+    "mfwh_debug_bounds": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
     "mfwh_destroy": (None, [C.c_void_p]),
     "mfwh_last_error": (C.c_char_p, []),
     "mfwh_status_string": (C.c_char_p, [C.c_int]),

@@ -17,6 +17,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmfwh.so")
+# the index-checked debugging build (-DMFWH_BOUNDS_CHECK, csrc/check.cuh)
+BUILD_BC = os.path.join(HERE, "_build_bc")
+LIB_BC = os.path.join(HERE, "libmfwh_bc.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -38,10 +41,10 @@ def _sources():
     return [os.path.join(CSRC, s) for s in srcs], hdrs
 
 
-def needs_build():
-    if not os.path.exists(LIB):
+def needs_build(lib=LIB):
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     srcs, hdrs = _sources()
     return any(os.path.getmtime(p) > t for p in srcs + hdrs + [os.path.abspath(__file__)])
 
@@ -53,20 +56,23 @@ def _run(cmd):
     return r.stdout + r.stderr
 
 
-def build(force=False, verbose=False):
-    """Compile every CUDA/C++ source of libmfwh for sm_103a; returns the library path."""
-    if not force and not needs_build():
-        return LIB
+def build(force=False, verbose=False, bounds_check=False):
+    """Compile every CUDA/C++ source of libmfwh for sm_103a; returns the library path.
+    bounds_check: the index-checked debugging build libmfwh_bc.so (-DMFWH_BOUNDS_CHECK)."""
+    lib, bdir = (LIB_BC, BUILD_BC) if bounds_check else (LIB, BUILD)
+    if not force and not needs_build(lib):
+        return lib
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(bdir, exist_ok=True)
     srcs, _ = _sources()
+    extra = ["-DMFWH_BOUNDS_CHECK"] if bounds_check else []
     jobs = []
     for s in srcs:
-        obj = os.path.join(BUILD, os.path.basename(s) + ".o")
+        obj = os.path.join(bdir, os.path.basename(s) + ".o")
         if s.endswith(".cu"):
-            cmd = [nvcc, "-c", s, "-o", obj] + NVCC_FLAGS
+            cmd = [nvcc, "-c", s, "-o", obj] + NVCC_FLAGS + extra
         else:
-            cmd = [os.environ.get("CXX", "g++"), "-c", s, "-o", obj] + CXX_FLAGS
+            cmd = [os.environ.get("CXX", "g++"), "-c", s, "-o", obj] + CXX_FLAGS + extra
         jobs.append((cmd, obj))
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
         outs = list(ex.map(lambda j: _run(j[0]), jobs))
@@ -74,10 +80,10 @@ def build(force=False, verbose=False):
         for o in outs:
             if o.strip():
                 print(o, file=sys.stderr)
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     _run([nvcc, "-shared", "-o", tmp] + [o for _, o in jobs] + ARCH + ["-lcudart_static", "-lpthread", "-ldl"])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

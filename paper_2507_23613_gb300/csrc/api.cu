@@ -130,6 +130,7 @@ struct mfwh_handle_s {
   double omega2[MFWH_MAX_NF] = {};
   double* f = nullptr;              // forcing [nf][P]
   double* c2f = nullptr;            // c^2 per point [P] (MFWH_C_FIELD)
+  BoundsFault* fault = nullptr;     // index-checked build: the kernels' fault record
   bool use32 = false;               // wave solves in FP32 (the FP32 precisions)
   // FP64 wave solves (all of an FP64 handle's; the FP64 residuals and products of an FP32
   // handle): steps per launch (1 = one step per launch) and blocked-kernel tile
@@ -1097,6 +1098,11 @@ mfwh_status mfwh_create(const mfwh_problem* prob, void* stream, mfwh_handle_t* o
                           h->stream);
     h->geom.c2f = h->c2f;
   }
+#ifdef MFWH_BOUNDS_CHECK
+  if (e == cudaSuccess) e = cudaMalloc(&h->fault, sizeof(BoundsFault));
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->fault, 0, sizeof(BoundsFault), h->stream);
+  h->geom.fault = h->fault;
+#endif
   if (e == cudaSuccess && h->f32) {
     launch_to_float(h->f, h->f32, h->N, h->stream);
     e = cudaGetLastError();
@@ -1371,6 +1377,23 @@ mfwh_status mfwh_last_timing(mfwh_handle_t h, double* step_ms, int64_t* step_lau
   return MFWH_OK;
 }
 
+mfwh_status mfwh_debug_bounds(mfwh_handle_t h, int64_t* count, int64_t* index, int64_t* extent,
+                              int* line) {
+  if (!h || !count) return fail(MFWH_ERR_INVALID_ARG, "null argument");
+  BoundsFault r{};
+#ifdef MFWH_BOUNDS_CHECK
+  CK(cudaMemcpyAsync(&r, h->fault, sizeof(r), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *count = (int64_t)r.count;
+#else
+  *count = -1;
+#endif
+  if (index) *index = r.index;
+  if (extent) *extent = r.extent;
+  if (line) *line = r.line;
+  return MFWH_OK;
+}
+
 void mfwh_destroy(mfwh_handle_t h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
@@ -1392,6 +1415,7 @@ void mfwh_destroy(mfwh_handle_t h) {
     if (b) cudaFree(b);
   if (h->d_err) cudaFree(h->d_err);
   if (h->c2f) cudaFree(h->c2f);
+  if (h->fault) cudaFree(h->fault);
   if (h->imp_mem) cudaFree(h->imp_mem);
   if (h->d_mgstate) cudaFree(h->d_mgstate);
   if (h->d_bar) cudaFree(h->d_bar);

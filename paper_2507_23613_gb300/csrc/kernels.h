@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include "check.cuh"
 #include "mfwh.h"
 
 namespace mfwh {
@@ -23,6 +24,8 @@ struct Geom {
                              // FP32 handles pad rows to 32 floats for tensor copies; else sy, sz)
   const double* c2f;         // c^2 per point [points] (MFWH_C_FIELD), else null; with a field
                              // the layer coefficients are those of c = 1 (lower layer only)
+  BoundsFault* fault;        // device fault record of the index-checked build (check.cuh), or
+                             // null; unused in the normal build
 };
 
 // Leapfrog update at one point, written as

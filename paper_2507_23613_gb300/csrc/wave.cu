@@ -140,6 +140,7 @@ k_init(const double* __restrict__ v, double* __restrict__ W0, float2* __restrict
        const InitParams<NF> a, const Geom g) {
   const PointIndex x = point_index<DIM>(g);
   if (!x.inside) return;
+  if (!MFWH_IDX(g.fault, x.p, g.points)) return;
   double w = 0.0;
   if (x.interior && v != nullptr) {
 #pragma unroll
@@ -156,6 +157,11 @@ k_step(const double* __restrict__ Wc, double* __restrict__ Wp, const double* __r
        float2* __restrict__ q, const StepParams<NF> a, const Geom g) {
   const PointIndex x = point_index<DIM>(g);
   if (!x.interior) return;           // boundary values stay 0 (Dirichlet, g = 0)
+  // index-checked build: the nearest neighbours along the outermost axis lie in the arrays
+  // (they bound every other read and write of the point; f, q: [NF][points])
+  const int64_t reach = DIM == 3 ? g.sz : g.sy;
+  if (!MFWH_IDX(g.fault, x.p - reach, g.points) || !MFWH_IDX(g.fault, x.p + reach, g.points))
+    return;
   const double wn = leapfrog_point<NF, DIM, ORDER, FIELD, FORCED>(Wc, Wp, f, a, g, x);
   Wp[x.p] = wn;
   const float2 xw = fpair_split(wn);
@@ -173,10 +179,16 @@ k_last(const double* __restrict__ Wc, const double* __restrict__ Wp, const doubl
        const Geom g) {
   const PointIndex x = point_index<DIM>(g);
   if (!x.inside) return;
+  if (!MFWH_IDX(g.fault, x.p, g.points)) return;
   if (!x.interior) {
 #pragma unroll
     for (int m = 0; m < NF; ++m) vout[m * g.points + x.p] = 0.0;
     return;
+  }
+  {
+    const int64_t reach = DIM == 3 ? g.sz : g.sy;
+    if (!MFWH_IDX(g.fault, x.p - reach, g.points) || !MFWH_IDX(g.fault, x.p + reach, g.points))
+      return;
   }
   const double wn = a.st.forced ? leapfrog_point<NF, DIM, ORDER, FIELD, true>(Wc, Wp, f, a.st, g, x)
                                 : leapfrog_point<NF, DIM, ORDER, FIELD, false>(Wc, Wp, f, a.st, g, x);

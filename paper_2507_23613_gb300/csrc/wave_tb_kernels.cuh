@@ -147,7 +147,8 @@ k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
   // Both levels on the tile plus halo; points outside the grid read as 0.
   for (int e = tid; e < E; e += NT) {
     const int ly = e / EX, lx = e - ly * EX;
-    const bool in = ly >= gly && ly <= ghy && lx >= glx && lx <= ghx;
+    const bool in = ly >= gly && ly <= ghy && lx >= glx && lx <= ghx &&
+                    MFWH_IDX(g.fault, (y0 + ly) * g.sy + x0 + lx, g.points);
     const int64_t p = (y0 + ly) * g.sy + x0 + lx;
     A[e] = in ? Wc_in[p] : 0.0;
     B[e] = (in && Wp_in != nullptr) ? Wp_in[p] : 0.0;
@@ -261,6 +262,8 @@ k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
           int lx, ly;
           ring_coords<T, BX, BY>(e, r, rw, top, inv_rw, inv_2r, lx, ly);
           if (!ALLINT && !simple && (lx < ilx || lx > ihx || ly < ily || ly > ihy)) continue;
+          if (!MFWH_IDX(g.fault, ly * EX + lx - EX, E) || !MFWH_IDX(g.fault, ly * EX + lx + EX, E))
+            continue;
           const LayerCoef& L =
               (ALLINT || simple) ? (all_hi ? hi : lo) : (((lay_x ? lx : ly) >= lay_thr) ? hi : lo);
           const int l = ly * EX + lx;
@@ -291,6 +294,7 @@ k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
     for (int k = 0; k < K; ++k) {
       if (!own_int[k]) continue;
       const int64_t p = p0 + k * g.sy;
+      if (!MFWH_IDX(g.fault, p, g.points)) continue;
       Wc_out[p] = wc[k];
       Wp_out[p] = B[(lyo + k) * EX + lxo];
 #pragma unroll
@@ -423,7 +427,9 @@ k_tb2d_pipe(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
   auto own_index = [&](int tile) -> int64_t {
     const int bx = tile % tiles_x, by = tile / tiles_x;
     const int64_t gx = 1 + (int64_t)bx * BX + tx, gy = 1 + (int64_t)by * BY + ty;
-    return (gx <= g.nx - 1 && gy <= g.ny - 1) ? gy * g.sy + gx : -1;
+    return (gx <= g.nx - 1 && gy <= g.ny - 1 && MFWH_IDX(g.fault, gy * g.sy + gx, g.points))
+               ? gy * g.sy + gx
+               : -1;
   };
   // Both levels of a tile on its extended tile into half h (zeros outside the grid, and for
   // W^{n-1} before the first step).
@@ -434,7 +440,8 @@ k_tb2d_pipe(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
     for (int e = tid; e < E; e += NT) {
       const int ly = e / EX, lx = e - ly * EX;
       const int64_t gx = x0 + lx, gy = y0 + ly;
-      const bool in = gx >= 0 && gx <= g.nx && gy >= 0 && gy <= g.ny;
+      const bool in = gx >= 0 && gx <= g.nx && gy >= 0 && gy <= g.ny &&
+                      MFWH_IDX(g.fault, gy * g.sy + gx, g.points);
       const int64_t p = in ? gy * g.sy + gx : 0;
       cp_async8(A + e, Wc_in + p, in ? 8 : 0);
       cp_async8(A + E + e, (Wp_in != nullptr ? Wp_in : Wc_in) + p,
@@ -529,7 +536,8 @@ k_tb2d_pipe(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
               ly = T + row;
               lx = col < r ? T - r + col : T + BX + col - r;
             }
-            if (ALLINT || simple || (lx >= ilx && lx <= ihx && ly >= ily && ly <= ihy)) {
+            if ((ALLINT || simple || (lx >= ilx && lx <= ihx && ly >= ily && ly <= ihy)) &&
+                MFWH_IDX(g.fault, ly * EX + lx - EX, E) && MFWH_IDX(g.fault, ly * EX + lx + EX, E)) {
               const LayerCoef& lo = first ? a.first_lo : a.reg_lo;
               const LayerCoef& hi = first ? a.first_hi : a.reg_hi;
               const LayerCoef& L = (ALLINT || simple)
@@ -556,7 +564,7 @@ k_tb2d_pipe(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
 
     // The filter updates of the tile's steps, then the sums' slots take the next tile's sums.
     cp_async_wait_prior();   // this thread's sums of this tile (the next tile's levels may pend)
-    if (own_int) {
+    if (own_int && MFWH_IDX(g.fault, p0, g.points)) {
       Wc_out[p0] = wc;
       Wp_out[p0] = B[lown];
       // one frequency at a time: few registers live
