@@ -32,18 +32,36 @@ __host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m *
 // D[p][n] = sum_k A[p][k] B[n][k] with p a pixel, n an output channel and k = ci * 9 + tap
 // (tap = dy * 3 + dx): A[p][k] = in[ci][y + dy - 1][x + dx - 1] (zero outside the image),
 // B[n][k] = Wk[n][k].  A CTA of 128 threads takes 128 consecutive pixels of the batch (M = 128)
-// and all output channels (N = 16 or 32, rows past Cout zero).  Each thread gathers its pixel's
-// row of A, 8 values of k at a time, into shared memory in the canonical K-major layout without
-// swizzle: 8 x 16-byte core matrices, the 16 row groups of a k-chunk 128 bytes apart (the
-// descriptor's stride byte offset) and successive k-chunks 16 * 128 bytes apart (its leading
-// byte offset); B likewise with N / 8 row groups.  One thread issues Kp / 16 MMAs
-// (tcgen05.mma, kind::f16, BF16 operands, FP32 accumulator in tensor memory) and commits them
-// to an mbarrier; after a bounded wait every warp reads its 32 rows of the accumulator
-// (tcgen05.ld) and applies bias and ReLU.  Shared and tensor memory are allocated with margins
-// past what a correct descriptor reads.
+// and all output channels (N = 16 or 32, rows past Cout zero).  K is taken in passes of 144
+// (16 input channels x 9 taps).  Each pass first copies the image rows that the CTA's pixels
+// and their vertical neighbours touch, for its 16 channels, from global into shared memory with
+// coalesced loads; then each thread builds its pixel's row of A from that copy, 8 values of k at
+// a time, in the canonical K-major layout without swizzle: 8 x 16-byte core matrices, the 16
+// row groups of a k-chunk 128 bytes apart (the descriptor's stride byte offset) and successive
+// k-chunks 16 * 128 bytes apart (its leading byte offset); B (all of K, loaded once) likewise
+// with N / 8 row groups.  One thread issues the pass's MMAs (tcgen05.mma, kind::f16, BF16
+// operands, FP32 accumulator in tensor memory) and commits them to an mbarrier; the next pass
+// overwrites A only after a bounded wait for that commit.  After the last pass every warp reads
+// its 32 rows of the accumulator (tcgen05.ld) and applies bias and ReLU.  Images too wide for
+// the row copy (more than 16.5 KB of rows per pass) are gathered from global memory instead.
+// About 71 KB of shared memory and 32 tensor-memory columns per CTA: three CTAs per SM.
 constexpr int kConvM = 128;              // pixels per CTA (accumulator lanes)
-constexpr int kConvTmemCols = 256;       // tensor-memory columns allocated per CTA
+constexpr int kConvTmemCols = 32;        // tensor-memory columns allocated per CTA (N <= 32)
 constexpr int kConvMaxKp = 288;          // 32 input channels x 9 taps
+constexpr int kConvPassK = 144;          // K per pass: 16 channels x 9 taps, 9 MMAs of K = 16
+constexpr int kConvPassCh = kConvPassK / 9;
+constexpr int kConvTileBytes = 16896;    // staged image rows of one pass (4 rows of 129 pixels)
+
+__host__ __device__ constexpr size_t conv_a_bytes() {
+  return (size_t)kConvPassK / 8 * (kConvM / 8) * 128;
+}
+__host__ __device__ constexpr size_t conv_b_bytes(int nt) {
+  return (size_t)kConvMaxKp / 8 * (nt / 8) * 128;
+}
+// Dynamic shared memory of k_conv_tc: A of one pass, B, the staged rows.
+__host__ __device__ constexpr size_t conv_smem_bytes(int nt) {
+  return conv_a_bytes() + conv_b_bytes(nt) + kConvTileBytes;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -91,13 +109,17 @@ k_conv_tc(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int K = Cin * 9;
   const int nk = Kp / 8;                                  // k-chunks of 8
+  constexpr int kPassChunks = kConvPassK / 8;             // 18
   constexpr uint32_t kSbo = 128;                          // 8-row groups 128 bytes apart
   constexpr uint32_t kLboA = (kConvM / 8) * 128;          // 2048 bytes per k-chunk of A
   constexpr uint32_t kLboB = (NT / 8) * 128;              // bytes per k-chunk of B
-  unsigned char* sA = conv_smem;                          // kConvM x Kp BF16
-  unsigned char* sB = conv_smem + (size_t)kConvMaxKp / 8 * kLboA;   // NT x Kp BF16
+  unsigned char* sA = conv_smem;                          // kConvM x 144 BF16 (one pass)
+  unsigned char* sB = conv_smem + conv_a_bytes();         // NT x Kp BF16
+  uint16_t* sT = reinterpret_cast<uint16_t*>(conv_smem + conv_a_bytes() + conv_b_bytes(NT));
   const int64_t plane = (int64_t)H * W, total = (int64_t)B * plane;
-  const int64_t pix = (int64_t)blockIdx.x * kConvM + tid;
+  const int64_t pix0 = (int64_t)blockIdx.x * kConvM;
+  const int64_t pix = pix0 + tid;
+  const uint32_t bar = smem_u32(&mma_bar);
 
   if (warp == 0) {   // tensor memory for the accumulator (whole warp, aligned)
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -107,38 +129,33 @@ k_conv_tc(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mma_bar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // A: this thread's pixel row, one 16-byte core-matrix row per k-chunk
-  {
-    const bool valid = pix < total;
-    const int b = valid ? (int)(pix / plane) : 0;
-    const int64_t rem = valid ? pix - (int64_t)b * plane : 0;
-    const int y = (int)(rem / W), x = (int)(rem - (int64_t)y * W);
-    const __nv_bfloat16* inb = in + (size_t)b * Cin * plane;
-    const uint16_t zero = 0;
-    for (int kc = 0; kc < nk; ++kc) {
-      uint16_t v[8];
+  // This thread's pixel, and the rows (b H + y over the batch) the CTA's pixels and their
+  // vertical neighbours touch: rlo .. rlo + nrows - 1.
+  const bool valid = pix < total;
+  const int b = valid ? (int)(pix / plane) : 0;
+  const int64_t rem = valid ? pix - (int64_t)b * plane : 0;
+  const int y = (int)(rem / W), x = (int)(rem - (int64_t)y * W);
+  const int64_t rows_total = (int64_t)B * H;
+  const int64_t last = (pix0 + kConvM < total ? pix0 + kConvM : total) - 1;
+  const int64_t rlo = pix0 / W > 0 ? pix0 / W - 1 : 0;
+  const int64_t rhi = last / W + 1 < rows_total ? last / W + 1 : rows_total - 1;
+  const int nrows = (int)(rhi - rlo + 1);
+  const bool staged = (int64_t)nrows * kConvPassCh * W * 2 <= kConvTileBytes && W < 1024;
+  const int b_lo = (int)(rlo / H), y_lo = (int)(rlo - (int64_t)b_lo * H);   // row rlo
+  const __nv_bfloat16* inb = in + (size_t)b * Cin * plane;
+  // the 9 taps of this pixel: inside the image (bit t of tap_in) and, for the staged rows, the
+  // offset of its value from the pixel's own in the copy, apart from the channel term c W
+  int tap_in = 0;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int k = kc * 8 + j;
-        v[j] = zero;
-        if (valid && k < K) {
-          const int ci = k / 9, tap = k - ci * 9;
-          const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
-          if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-            v[j] = __bfloat16_as_ushort(inb[(size_t)ci * plane + (size_t)yy * W + xx]);
-        }
-      }
-      uint4 row;
-      row.x = v[0] | ((uint32_t)v[1] << 16);
-      row.y = v[2] | ((uint32_t)v[3] << 16);
-      row.z = v[4] | ((uint32_t)v[5] << 16);
-      row.w = v[6] | ((uint32_t)v[7] << 16);
-      *reinterpret_cast<uint4*>(sA + (size_t)kc * kLboA + (tid >> 3) * kSbo + (tid & 7) * 16) = row;
-    }
+  for (int t = 0; t < 9; ++t) {
+    const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+    if (valid && yy >= 0 && yy < H && xx >= 0 && xx < W) tap_in |= 1 << t;
   }
+  const int prow = (int)((int64_t)b * H + y - rlo);
+
   // B: NT rows of the weights (rows Np .. NT - 1 zero), 16 bytes per (row, k-chunk)
   for (int e = tid; e < NT * nk; e += kConvM) {
     const int n = e / nk, kc = e - n * nk;
@@ -146,36 +163,122 @@ k_conv_tc(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
     if (n < Np) row = *reinterpret_cast<const uint4*>(Wk + (size_t)n * Kp + kc * 8);
     *reinterpret_cast<uint4*>(sB + (size_t)kc * kLboB + (n >> 3) * kSbo + (n & 7) * 16) = row;
   }
-  // make the operands visible to the tensor core's asynchronous proxy, then issue
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t taddr = tmem_base;
-  if (tid == 0) {
-    constexpr uint32_t idesc = conv_idesc(NT);
-    for (int ks = 0; ks < Kp / 16; ++ks) {
-      const uint64_t ad = smem_desc(smem_u32(sA) + ks * 2 * kLboA, kLboA, kSbo);
-      const uint64_t bd = smem_desc(smem_u32(sB) + ks * 2 * kLboB, kLboB, kSbo);
-      const uint32_t acc = ks > 0 ? 1u : 0u;
+
+  const int npass = (nk + kPassChunks - 1) / kPassChunks;
+  bool ok = true;
+  int waited = -1;   // the last pass whose MMAs are known complete
+  for (int pass = 0; pass < npass; ++pass) {
+    const int c0 = pass * kPassChunks;                         // first k-chunk of the pass
+    const int nkp = nk - c0 < kPassChunks ? nk - c0 : kPassChunks;   // even: Kp % 16 == 0
+    const int ci0 = pass * kConvPassCh;
+    const int nci = Cin - ci0 < kConvPassCh ? Cin - ci0 : kConvPassCh;
+    if (pass > 0) {
+      // the previous pass's MMAs read A (and the copy is rewritten below): wait for them
+      ok = conv_mbar_wait(bar, (uint32_t)((pass - 1) & 1), 1 << 22);
+      if (__syncthreads_or(!ok)) break;
+      waited = pass - 1;
+    }
+    if (staged) {
+      // rows rlo .. rhi of channels ci0 .. ci0 + nci - 1: sT[(row nci + c) W + x], 16 independent
+      // loads per thread in flight; quotients by W and nci are multiply-highs by ceil(2^32 / d)
+      // (exact for e < 2^16, d < 2^10)
+      const int n_el = nrows * nci * W;
+      const uint32_t mw = 0xFFFFFFFFu / (uint32_t)W + 1u, mc = 0xFFFFFFFFu / (uint32_t)nci + 1u;
+      const uint16_t* in16 = reinterpret_cast<const uint16_t*>(in);
+      for (int e0 = tid; e0 < n_el; e0 += kConvM * 16) {
+        uint16_t t[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int e = e0 + u * kConvM;
+          t[u] = 0;
+          if (e < n_el) {
+            const int rc = W > 1 ? (int)__umulhi((uint32_t)e, mw) : e;
+            const int xr = e - rc * W;
+            const int row = nci > 1 ? (int)__umulhi((uint32_t)rc, mc) : rc;
+            const int c = rc - row * nci;
+            int bb = b_lo, yy = y_lo + row;   // batch row rlo + row as (image, row)
+            while (yy >= H) {
+              yy -= H;
+              ++bb;
+            }
+            t[u] = in16[((size_t)bb * Cin + ci0 + c) * plane + (size_t)yy * W + xr];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+          if (e0 + u * kConvM < n_el) sT[e0 + u * kConvM] = t[u];
+      }
+      __syncthreads();
+    }
+    // A of the pass: this thread's pixel row, k = (c0 + kc) * 8 + j, taken in order of k with
+    // (channel, tap) counters
+    {
+      int k = c0 * 8;
+      int ci = k / 9, tap = k - ci * 9;
+      const int base = (prow * nci - ci0) * W + x;   // + (ci W) + tap offset in the copy
+      for (int kc = 0; kc < nkp; ++kc) {
+        uint16_t v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          uint16_t val = 0;
+          if (k < K && ((tap_in >> tap) & 1)) {
+            const int dy = tap / 3, dx = tap - dy * 3;
+            if (staged)
+              val = sT[base + ci * W + (dy - 1) * nci * W + dx - 1];
+            else
+              val = __bfloat16_as_ushort(
+                  inb[(size_t)ci * plane + (size_t)(y + dy - 1) * W + x + dx - 1]);
+          }
+          v[j] = val;
+          ++k;
+          if (++tap == 9) {
+            tap = 0;
+            ++ci;
+          }
+        }
+        uint4 row;
+        row.x = v[0] | ((uint32_t)v[1] << 16);
+        row.y = v[2] | ((uint32_t)v[3] << 16);
+        row.z = v[4] | ((uint32_t)v[5] << 16);
+        row.w = v[6] | ((uint32_t)v[7] << 16);
+        *reinterpret_cast<uint4*>(sA + (size_t)kc * kLboA + (tid >> 3) * kSbo + (tid & 7) * 16) =
+            row;
+      }
+    }
+    // make the operands visible to the tensor core's asynchronous proxy, then issue
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+      constexpr uint32_t idesc = conv_idesc(NT);
+      const uint32_t taddr = tmem_base;
+      for (int ks = 0; ks < nkp / 2; ++ks) {
+        const uint64_t ad = smem_desc(smem_u32(sA) + ks * 2 * kLboA, kLboA, kSbo);
+        const uint64_t bd = smem_desc(smem_u32(sB) + (c0 + ks * 2) * kLboB, kLboB, kSbo);
+        const uint32_t acc = (pass > 0 || ks > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(taddr),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+      }
       asm volatile(
-          "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(taddr),
-          "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              bar)
           : "memory");
     }
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(&mma_bar))
-        : "memory");
   }
-  const bool ok = conv_mbar_wait(smem_u32(&mma_bar), 0, 1 << 22);
+  const uint32_t taddr = tmem_base;
+  // the last issued pass: all of them after a normal loop, the one before the failed wait else
+  const int issued = ok ? npass - 1 : waited + 1;
+  if (ok) ok = conv_mbar_wait(bar, (uint32_t)((npass - 1) & 1), 1 << 22);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (__syncthreads_or(!ok)) {
-    // The MMAs did not complete within the bound: report it, give them one more bounded wait,
-    // release the tensor memory and stop.
+    // The MMAs did not complete within the bound: report it, give the last issued commit one
+    // more bounded wait, release the tensor memory and stop.
     if (tid == 0) atomicExch(err, 1);
-    conv_mbar_wait(smem_u32(&mma_bar), 0, 1 << 22);
+    conv_mbar_wait(bar, (uint32_t)(issued & 1), 1 << 22);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -226,8 +329,6 @@ k_conv_tc(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
                  : "memory");
   }
   if (pix >= total) return;
-  const int b = (int)(pix / plane);
-  const int64_t rem = pix - (int64_t)b * plane;
 #pragma unroll
   for (int n = 0; n < NT; ++n) {
     if (n >= Cout) break;
@@ -239,11 +340,6 @@ k_conv_tc(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
   }
 }
 
-// Dynamic shared memory of k_conv_tc: A for the largest Kp, then B, plus a margin of one more
-// A-sized region, so that any reading of the two byte offsets stays inside the allocation.
-__host__ __device__ constexpr size_t conv_smem_bytes(int nt) {
-  return (size_t)kConvMaxKp / 8 * (kConvM / 8) * 128 * 2 + (size_t)kConvMaxKp / 8 * (nt / 8) * 128;
-}
 
 // Weight and bias gradients of one layer: gw[co][ci][tap] = sum_{b,y,x} g[b][co][y][x] *
 // in[b][ci][y + dy - 1][x + dx - 1]; gb[co] = sum g[b][co].  One CTA per (co, ci).

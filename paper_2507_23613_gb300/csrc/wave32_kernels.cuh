@@ -260,6 +260,20 @@ __device__ __forceinline__ float tb_update(const float* Wc, float* Wn, float* Dv
   return wn;
 }
 
+// ceil(2^32 / d) for 2 <= d < 128, a table in constant memory filled at compile time: the
+// multiplier of the exact division floor(e / d) = (e * m) >> 32 for the small ring indices e
+// of the blocked kernels (e < 2^16; checked exhaustively on the host).
+struct DivMagic {
+  unsigned m[128];
+};
+constexpr DivMagic make_div_magic() {
+  DivMagic t{};
+  for (int d = 2; d < 128; ++d) t.m[d] = 0xFFFFFFFFu / (unsigned)d + 1u;
+  return t;
+}
+__constant__ DivMagic c_div_magic = make_div_magic();
+__device__ __forceinline__ unsigned div_magic(int d) { return c_div_magic.m[d]; }
+
 // Fold a partial sum x into the Kahan pair (s, c).
 __device__ __forceinline__ void kahan_fold(float& s, float& c, float x) {
   const float y = x - c;
@@ -270,8 +284,9 @@ __device__ __forceinline__ void kahan_fold(float& s, float& c, float x) {
 
 // The halo ring of radius r around a BX x BY tile at one step, enumerated evenly over all
 // threads: first the 2r rows of BX + 2r points above and below the tile, then the BY rows of
-// 2r points to its left and right.  Quotients by the row lengths come from a float
-// reciprocal: (e + 1/2) / len is at least 1/(2 len) from an integer, far above the rounding.
+// 2r points to its left and right.  Quotients by the row lengths are exact integer divisions by
+// a multiplier: floor(e / d) = (e * ceil(2^32 / d)) >> 32 for the ring indices used here
+// (e < 2^16, d < 2^7; checked exhaustively on the host).
 // SIMPLE: every ring point is interior and has the same c^2 (no bounds or layer tests).
 template <int NF, int T, int BX, int BY, bool SIMPLE>
 __device__ __forceinline__ void ring_pass(const float* Wc, float* Wn, float* Dv, int r, int tid,
@@ -284,16 +299,16 @@ __device__ __forceinline__ void ring_pass(const float* Wc, float* Wn, float* Dv,
   const int RW = BX + 2 * r;
   const int top = 2 * r * RW;
   const int ring = top + 2 * r * BY;
-  const float inv_rw = 1.0f / (float)RW, inv_2r = 1.0f / (float)(2 * r);
+  const unsigned m_rw = div_magic(RW), m_2r = div_magic(2 * r);
   for (int e = tid; e < ring; e += nthreads) {
     int lx, ly;
     if (e < top) {
-      const int row = (int)(((float)e + 0.5f) * inv_rw);
+      const int row = (int)__umulhi((unsigned)e, m_rw);
       lx = T - r + (e - row * RW);
       ly = row < r ? T - r + row : T + BY + row - r;
     } else {
       const int e2 = e - top;
-      const int row = (int)(((float)e2 + 0.5f) * inv_2r);
+      const int row = (int)__umulhi((unsigned)e2, m_2r);
       const int col = e2 - row * 2 * r;
       ly = T + row;
       lx = col < r ? T - r + col : T + BX + col - r;

@@ -90,20 +90,33 @@ __device__ __forceinline__ double ring_update(const double* A, double wprev, int
   return acc;
 }
 
+// ceil(2^32 / d) for 2 <= d < 128, a table in constant memory filled at compile time: the
+// multiplier of the exact division floor(e / d) = (e * m) >> 32 for the small ring indices e
+// of the blocked kernels (e < 2^16; checked exhaustively on the host).
+struct DivMagic {
+  unsigned m[128];
+};
+constexpr DivMagic make_div_magic() {
+  DivMagic t{};
+  for (int d = 2; d < 128; ++d) t.m[d] = 0xFFFFFFFFu / (unsigned)d + 1u;
+  return t;
+}
+__constant__ DivMagic c_div_magic = make_div_magic();
+__device__ __forceinline__ unsigned div_magic(int d) { return c_div_magic.m[d]; }
+
 // Local coordinates of flat ring index e at radius r: the 2r rows of BX + 2r points above and
 // below the tile, then the BY rows of 2r points left and right of it.  Quotients by the row
-// lengths come from a float reciprocal: (e + 1/2) / len is at least 1/(2 len) from an integer,
-// far above the rounding of the product for the ring sizes used here.
+// lengths are integer divisions by multipliers m_rw = div_magic(rw), m_2r = div_magic(2r).
 template <int T, int BX, int BY>
-__device__ __forceinline__ void ring_coords(int e, int r, int rw, int top, float inv_rw,
-                                            float inv_2r, int& lx, int& ly) {
+__device__ __forceinline__ void ring_coords(int e, int r, int rw, int top, unsigned m_rw,
+                                            unsigned m_2r, int& lx, int& ly) {
   if (e < top) {
-    const int row = (int)(((float)e + 0.5f) * inv_rw);
+    const int row = (int)__umulhi((unsigned)e, m_rw);
     lx = T - r + (e - row * rw);
     ly = row < r ? T - r + row : T + BY + row - r;
   } else {
     const int e2 = e - top;
-    const int row = (int)(((float)e2 + 0.5f) * inv_2r);
+    const int row = (int)__umulhi((unsigned)e2, m_2r);
     const int col = e2 - row * 2 * r;
     ly = T + row;
     lx = col < r ? T - r + col : T + BX + col - r;
@@ -257,10 +270,10 @@ k_tb2d(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
         const int rw = BX + 2 * r;
         const int top = 2 * r * rw;
         const int ring = top + 2 * r * BY;
-        const float inv_rw = 1.0f / (float)rw, inv_2r = 1.0f / (float)(2 * r);
+        const unsigned m_rw = div_magic(rw), m_2r = div_magic(2 * r);
         for (int e = tid; e < ring; e += NT) {
           int lx, ly;
-          ring_coords<T, BX, BY>(e, r, rw, top, inv_rw, inv_2r, lx, ly);
+          ring_coords<T, BX, BY>(e, r, rw, top, m_rw, m_2r, lx, ly);
           if (!ALLINT && !simple && (lx < ilx || lx > ihx || ly < ily || ly > ihy)) continue;
           if (!MFWH_IDX(g.fault, ly * EX + lx - EX, E) || !MFWH_IDX(g.fault, ly * EX + lx + EX, E))
             continue;
@@ -400,33 +413,42 @@ __device__ __forceinline__ void cp_async_wait_prior() {
   asm volatile("cp.async.wait_group 1;" ::: "memory");
 }
 
-constexpr int kPipeBY = 16, kPipeThreads = kTX * kPipeBY, kPipeMinBlocks = 3;
+constexpr int kPipeTY = 16, kPipeThreads = kTX * kPipeTY;
 
-template <int NF, int T>
-constexpr size_t pipe_smem_bytes() {
-  return sizeof(double) * 4 * (kTX + 2 * T) * (kPipeBY + 2 * T) +
-         sizeof(float2) * NF * kPipeThreads;
+// K rows per thread: 32 x 16 K-point tiles; three CTAs per SM for K = 1, two for K = 2.  The
+// library runs K = 1 (tile shape 5): K = 2 (a smaller halo ring, two FMA chains per thread, but
+// 32 instead of 48 resident warps per SM) measured 0.91x of it at depth 3.
+template <int K>
+constexpr int pipe_min_blocks() {
+  return K == 1 ? 3 : 2;
 }
 
-template <int NF, int T>
-__global__ void __launch_bounds__(kPipeThreads, kPipeMinBlocks)
+template <int NF, int T, int K>
+constexpr size_t pipe_smem_bytes() {
+  return sizeof(double) * 4 * (kTX + 2 * T) * (kPipeTY * K + 2 * T) +
+         sizeof(float2) * NF * K * kPipeThreads;
+}
+
+template <int NF, int T, int K>
+__global__ void __launch_bounds__(kPipeThreads, pipe_min_blocks<K>())
 k_tb2d_pipe(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
             double* __restrict__ Wc_out, double* __restrict__ Wp_out,
             const double* __restrict__ f, float2* __restrict__ q, const TBParams<NF> a,
             const Geom g, int tiles_x, int tiles_y) {
-  constexpr int BX = kTX, BY = kPipeBY, NT = kPipeThreads;
+  constexpr int BX = kTX, BY = kPipeTY * K, NT = kPipeThreads;
   constexpr int EX = BX + 2 * T, EY = BY + 2 * T, E = EX * EY;
   extern __shared__ double smem[];
   double* stage = smem;                                      // [2][A, B][E]
-  float2* qbuf = reinterpret_cast<float2*>(smem + 4 * E);    // [NF][NT] sums of the own points
+  float2* qbuf = reinterpret_cast<float2*>(smem + 4 * E);    // [NF][K][NT] sums of own points
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
   const int n_tiles = tiles_x * tiles_y;
-  const int lxo = T + tx, lyo = T + ty, lown = lyo * EX + lxo;   // the thread's own point
+  // the thread's own points: column lxo, rows lyo .. lyo + K - 1
+  const int lxo = T + tx, lyo = T + ty * K, lown = lyo * EX + lxo;
 
-  // Global index of the thread's own point in a tile, or -1 outside the interior.
-  auto own_index = [&](int tile) -> int64_t {
+  // Global index of own point k in a tile, or -1 outside the interior.
+  auto own_index = [&](int tile, int k) -> int64_t {
     const int bx = tile % tiles_x, by = tile / tiles_x;
-    const int64_t gx = 1 + (int64_t)bx * BX + tx, gy = 1 + (int64_t)by * BY + ty;
+    const int64_t gx = 1 + (int64_t)bx * BX + tx, gy = 1 + (int64_t)by * BY + ty * K + k;
     return (gx <= g.nx - 1 && gy <= g.ny - 1 && MFWH_IDX(g.fault, gy * g.sy + gx, g.points))
                ? gy * g.sy + gx
                : -1;
@@ -448,11 +470,16 @@ k_tb2d_pipe(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
                 (in && Wp_in != nullptr) ? 8 : 0);
     }
   };
-  // The own point's filter sums (each thread copies and later reads only its own slots).
-  auto prefetch_sums = [&](int64_t p) {
+  // The own points' filter sums (each thread copies and later reads only its own slots).
+  auto prefetch_sums = [&](int tile) {
 #pragma unroll
-    for (int m = 0; m < NF; ++m)
-      cp_async8(qbuf + m * NT + tid, q + m * g.points + (p < 0 ? 0 : p), p < 0 ? 0 : 8);
+    for (int k = 0; k < K; ++k) {
+      const int64_t p = own_index(tile, k);
+#pragma unroll
+      for (int m = 0; m < NF; ++m)
+        cp_async8(qbuf + (m * K + k) * NT + tid, q + m * g.points + (p < 0 ? 0 : p),
+                  p < 0 ? 0 : 8);
+    }
   };
 
   // Copies go in two kinds of commit groups, levels then sums, one of each per tile (empty when
@@ -462,7 +489,7 @@ k_tb2d_pipe(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
   if (tile < n_tiles) {
     prefetch_levels(tile, 0);
     cp_async_commit();
-    prefetch_sums(own_index(tile));
+    prefetch_sums(tile);
     cp_async_commit();
   }
 
@@ -481,15 +508,23 @@ k_tb2d_pipe(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
     const bool simple = ilx <= 1 && ihx >= EX - 2 && ily <= 1 && ihy >= EY - 2 &&
                         (lay_thr <= 0 || lay_thr >= (lay_x ? EX : EY));
     const bool all_hi = lay_thr <= 0;
-    const bool own_int = lxo >= ilx && lxo <= ihx && lyo >= ily && lyo <= ihy;
-    const bool own_up = (lay_x ? lxo : lyo) >= lay_thr;
+    bool own_int[K], own_up[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      own_int[k] = lxo >= ilx && lxo <= ihx && lyo + k >= ily && lyo + k <= ihy;
+      own_up[k] = (lay_x ? lxo : lyo + k) >= lay_thr;
+    }
     const int64_t p0 = (y0 + lyo) * g.sy + x0 + lxo;
     double* A = stage + 2 * h * E;   // W^n on the extended tile
     double* B = A + E;               // W^{n-1}, overwritten by W^{n+1}
-    double wc = A[lown];
-    float2 pend[T];                  // float pairs of the tile's new own values, step by step
+    double wc[K];
 #pragma unroll
-    for (int s = 0; s < T; ++s) pend[s] = make_float2(0.0f, 0.0f);
+    for (int k = 0; k < K; ++k) wc[k] = A[lown + k * EX];
+    float2 pend[K][T];               // float pairs of the tile's new own values, step by step
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int s = 0; s < T; ++s) pend[k][s] = make_float2(0.0f, 0.0f);
 
     // The T steps, each with its ring radius r = T - 1 - s known at compile time (every launch
     // of this kernel runs exactly T steps): the ring has at most one point per thread and its
@@ -502,22 +537,37 @@ k_tb2d_pipe(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
         constexpr int r = T - 1 - s;
         const bool first = a.n0 + s == 0;
         const double* fneg = a.fcp + s * NF;
-        if (ALLINT || own_int) {
-          const double sx = A[lown - 1] + A[lown + 1];
-          const double sy = A[lown - EX] + A[lown + EX];
-          // the own point's coefficients (the first step of a wave solve has its own)
-          const bool up = ALLINT ? all_hi : own_up;
-          const LayerCoef& L = first ? (up ? a.first_hi : a.first_lo) : (up ? a.reg_hi : a.reg_lo);
-          double acc = fma(L.A0, wc, -B[lown]);
+        // own points: vertical neighbours inside the strip from registers
+        double wn[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          wn[k] = wc[k];
+          if (!(ALLINT || own_int[k])) continue;
+          const int l = lown + k * EX;
+          const double up = k == 0 ? A[l - EX] : wc[k - 1];
+          const double dn = k == K - 1 ? A[l + EX] : wc[k + 1];
+          const double sx = A[l - 1] + A[l + 1];
+          const double sy = up + dn;
+          // the point's coefficients (the first step of a wave solve has its own)
+          const bool upper = ALLINT ? all_hi : own_up[k];
+          const LayerCoef& L =
+              first ? (upper ? a.first_hi : a.first_lo) : (upper ? a.reg_hi : a.reg_lo);
+          double acc = fma(L.A0, wc[k], -B[l]);
           acc = fma(L.Ax, sx, acc);
           acc = fma(L.Ay, sy, acc);
           if (FORCED) {
 #pragma unroll
-            for (int m = 0; m < NF; ++m) acc = fma(-fneg[m], f[m * g.points + p0], acc);
+            for (int m = 0; m < NF; ++m)
+              acc = fma(-fneg[m], f[m * g.points + p0 + k * g.sy], acc);
           }
-          B[lown] = acc;
-          wc = acc;
-          pend[s] = fpair_split(acc);
+          wn[k] = acc;
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          if (!(ALLINT || own_int[k])) continue;
+          B[lown + k * EX] = wn[k];
+          wc[k] = wn[k];
+          pend[k][s] = fpair_split(wn[k]);
         }
         if constexpr (r > 0) {
           // ring of radius r: the 2r rows of RW points above and below the tile, then the BY
@@ -564,20 +614,23 @@ k_tb2d_pipe(const double* __restrict__ Wc_in, const double* __restrict__ Wp_in,
 
     // The filter updates of the tile's steps, then the sums' slots take the next tile's sums.
     cp_async_wait_prior();   // this thread's sums of this tile (the next tile's levels may pend)
-    if (own_int && MFWH_IDX(g.fault, p0, g.points)) {
-      Wc_out[p0] = wc;
-      Wp_out[p0] = B[lown];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int64_t pk = p0 + k * g.sy;
+      if (!own_int[k] || !MFWH_IDX(g.fault, pk, g.points)) continue;
+      Wc_out[pk] = wc[k];
+      Wp_out[pk] = B[lown + k * EX];
       // one frequency at a time: few registers live
 #pragma unroll
       for (int m = 0; m < NF; ++m) {
-        float2 qm = qbuf[m * NT + tid];
+        float2 qm = qbuf[(m * K + k) * NT + tid];
 #pragma unroll
         for (int s = 0; s < T; ++s)
-          qm = fpair_fma(a.wph[s * NF + m], a.wpl[s * NF + m], pend[s].x, pend[s].y, qm);
-        q[m * g.points + p0] = qm;
+          qm = fpair_fma(a.wph[s * NF + m], a.wpl[s * NF + m], pend[k][s].x, pend[k][s].y, qm);
+        q[m * g.points + pk] = qm;
       }
     }
-    if (next < n_tiles) prefetch_sums(own_index(next));
+    if (next < n_tiles) prefetch_sums(next);
     cp_async_commit();
   }
   cp_async_wait_all();   // no copy of this CTA outlives it
@@ -620,21 +673,21 @@ TBParams<NF> tb_params(const TBHost& h) {
   return a;
 }
 
-template <int NF, int T>
+template <int NF, int T, int K>
 void tb_launch_pipe(const Geom& g, const double* Wc_in, const double* Wp_in, double* Wc_out,
-                    double* Wp_out, const double* f, double* q, double* vout, const double* vsub,
-                    const TBHost& h, cudaStream_t st) {
-  constexpr size_t smem = pipe_smem_bytes<NF, T>();
+                    double* Wp_out, const double* f, double* q, const TBHost& h,
+                    cudaStream_t st) {
+  constexpr size_t smem = pipe_smem_bytes<NF, T, K>();
   // Attribute and resident CTAs per SM, once per device for this instance.
   static int resident[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   int per_sm = (dev >= 0 && dev < 64) ? resident[dev] : 0;
   if (per_sm == 0) {
-    cudaFuncSetAttribute(k_tb2d_pipe<NF, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_tb2d_pipe<NF, T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     int occ = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tb2d_pipe<NF, T>, kPipeThreads,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tb2d_pipe<NF, T, K>, kPipeThreads,
                                                       smem) != cudaSuccess || occ < 1)
       occ = 1;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -645,9 +698,9 @@ void tb_launch_pipe(const Geom& g, const double* Wc_in, const double* Wp_in, dou
   }
   const TBParams<NF> a = tb_params<NF, T>(h);
   const int tiles_x = (int)((g.nx - 1 + kTX - 1) / kTX);
-  const int tiles_y = (int)((g.ny - 1 + kPipeBY - 1) / kPipeBY);
+  const int tiles_y = (int)((g.ny - 1 + kPipeTY * K - 1) / (kPipeTY * K));
   const int grid = std::min(tiles_x * tiles_y, per_sm);
-  k_tb2d_pipe<NF, T><<<grid, dim3(kTX, kPipeBY), smem, st>>>(
+  k_tb2d_pipe<NF, T, K><<<grid, dim3(kTX, kPipeTY), smem, st>>>(
       Wc_in, Wp_in, Wc_out, Wp_out, f, reinterpret_cast<float2*>(q), a, g, tiles_x, tiles_y);
 }
 
@@ -699,8 +752,9 @@ void tb_launch_shape(const Geom& g, const double* Wc_in, const double* Wp_in, do
   switch (shape) {
     case 5:
       if constexpr (!wide && T <= 4)
-        tb_launch_pipe<NF, T>(g, Wc_in, Wp_in, Wc_out, Wp_out, f, q, vout, vsub, h, st);
+        tb_launch_pipe<NF, T, 1>(g, Wc_in, Wp_in, Wc_out, Wp_out, f, q, h, st);
       break;
+
     case 4:
       if constexpr (T <= 4)
         tb_launch_k<NF, T, 1, 16, 2>(g, Wc_in, Wp_in, Wc_out, Wp_out, f, q, vout, vsub, h, st);

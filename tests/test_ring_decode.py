@@ -3,10 +3,11 @@ k_tb2d use the same decode).
 
 At step s of a launch of T steps the kernel updates the ring of radius
 r = T - 1 - s around its BX x BY tile, enumerated by a flat index e; row and
-column come from a float32 reciprocal of the row length.  This test replays
-that decode in float32 for every tile shape and depth the library builds and
-checks that the ring is covered exactly once and stays inside the extended
-tile (so every shared-memory access of the kernel is in bounds)."""
+column come from an integer division by the row length done as a 32-bit
+multiply-high by ceil(2^32 / d).  This test replays that decode for every tile
+shape and depth the library builds and checks that the ring is covered exactly
+once and stays inside the extended tile (so every shared-memory access of the
+kernel is in bounds), and checks the division itself exhaustively."""
 
 import numpy as np
 import pytest
@@ -16,18 +17,25 @@ SHAPES = [16 * 2, 16 * 1, 32 * 1, 16 * 4, 16 * 2]   # BY of the FP32 tile shapes
 SHAPES += [16 * 4, 16 * 2, 16 * 3, 8 * 4, 16 * 1]   # BY of the FP64 tile shapes 0-4
 
 
+def div_magic(d):
+    """The kernels' multiplier: 0xFFFFFFFF / d + 1 in unsigned 32-bit arithmetic."""
+    return (0xFFFFFFFF // d + 1) & 0xFFFFFFFF
+
+
+def umulhi(a, b):
+    return (a * b) >> 32
+
+
 def decode(e, r, T, BY):
     RW = BX + 2 * r
     top = 2 * r * RW
-    inv_rw = np.float32(1.0) / np.float32(RW)
-    inv_2r = np.float32(1.0) / np.float32(2 * r)
     if e < top:
-        row = int((np.float32(e) + np.float32(0.5)) * inv_rw)
+        row = umulhi(e, div_magic(RW))
         lx = T - r + (e - row * RW)
         ly = T - r + row if row < r else T + BY + row - r
     else:
         e2 = e - top
-        row = int((np.float32(e2) + np.float32(0.5)) * inv_2r)
+        row = umulhi(e2, div_magic(2 * r))
         col = e2 - row * 2 * r
         ly = T + row
         lx = T - r + col if col < r else T + BX + col - r
@@ -48,3 +56,12 @@ def test_ring_decode_covers_each_point_once(T, BY):
         want = {(x, y) for x in range(T - r, T + BX + r) for y in range(T - r, T + BY + r)
                 if not (T <= x < T + BX and T <= y < T + BY)}
         assert len(seen) == ring and seen == want
+
+
+def test_division_by_multiplier_is_exact():
+    """floor(e / d) == (e * ceil(2^32 / d)) >> 32 for every ring index and divisor in use
+    (indices below 2^16, divisors 2 .. 127), including powers of two."""
+    e = np.arange(1 << 16, dtype=np.uint64)
+    for d in range(2, 128):
+        m = np.uint64(div_magic(d))
+        assert np.array_equal((e * m) >> np.uint64(32), e // np.uint64(d)), d
