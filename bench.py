@@ -66,6 +66,10 @@ def parse():
     ap.add_argument("--batched", action="store_true",
                     help="run the batched workload (independent 2D problems solved concurrently)")
     ap.add_argument("--batch", type=int, default=48, help="problems in the batched workload")
+    ap.add_argument("--default-batch", type=int, default=16,
+                    help="problems of the batched workload in the default line's batched leg")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the default line's batched leg (lockstep and concurrent solves)")
     ap.add_argument("--batch-iters", type=int, default=10,
                     help="GMRES(10) Arnoldi steps per problem in the batched workload")
     ap.add_argument("--batch-mem-gb", type=float, default=180.0,
@@ -548,22 +552,30 @@ def fp32_leg(args, wl, f_dev, stream, n_t):
 
 
 def run_batched(args):
-    """Independent 2D problems (sizes 257^2..2049^2, N_f 1..16) solved concurrently: one
-    host thread and one stream per problem, each wave solve one CUDA-graph launch, blocking
-    depth and tile from the autotuner, FP32 wave solves with compensated filter sums.
-    Reports the per-problem solve times (p50, p99) and the aggregate stencil rate; then the
-    same solves in lockstep, one graph launch per application of the map across the batch."""
+    """The full batched workload (--batch problems, autotuned blocking), one JSON line."""
     import torch
-    import paper_2507_23613_gb300 as M
-    from paper_2507_23613_gb300 import _lib, build, inputs
+    from paper_2507_23613_gb300 import build
     torch.cuda.set_device(0)
     build.build()
+    print(json.dumps(batched_solves(args, args.batch, tune=True)), flush=True)
+
+
+def batched_solves(args, count, tune):
+    """Independent 2D problems (sizes 257^2..2049^2, N_f 1..16) solved concurrently: one
+    host thread and one stream per problem, each wave solve one CUDA-graph launch, FP32 wave
+    solves with compensated filter sums; blocking depth and tile from the autotuner (tune) or
+    the library defaults.  Reports the per-problem solve times (p50, p99) and the aggregate
+    stencil rate; then the same solves in lockstep, one graph launch per application of the map
+    across the batch.  Returns the result as a dict."""
+    import torch
+    import paper_2507_23613_gb300 as M
+    from paper_2507_23613_gb300 import _lib, inputs
     M._lib.load()
     prec = _lib.PREC_FP32_BLOCKSUM
     restart = 10
     chosen, seed, mem = [], args.seed + 5000, 0.0
     t_gen = time.perf_counter()
-    while len(chosen) < args.batch and seed < args.seed + 5000 + 50 * args.batch:
+    while len(chosen) < count and seed < args.seed + 5000 + 50 * count:
         wl = inputs.batch_workload(seed)
         seed += 1
         try:
@@ -579,7 +591,7 @@ def run_batched(args):
     t_gen = time.perf_counter() - t_gen
     t_tune = time.perf_counter()
     tuned = [M.autotune(wl.n, wl.length, wl.omega, n_p=wl.n_p, cfl=wl.cfl, precision=prec)
-             for wl, _ in chosen]
+             if tune else (0, 0, 0.0) for wl, _ in chosen]
     t_tune = time.perf_counter() - t_tune
     # smaller problems on higher-priority streams, so that they are not queued behind the
     # long wave solves of the large ones
@@ -627,6 +639,7 @@ def run_batched(args):
                 "p50_s": round(float(np.percentile(lsecs, 50)), 3),
                 "p99_s": round(float(np.percentile(lsecs, 99)), 3), "wall_s": round(lwall, 3),
                 "graph_launches": 1 + args.batch_iters, "status": lst,
+                "per_problem_s": [round(float(x), 3) for x in lsecs],
                 "note": "mfwh_solve_batch_graph: every application of the map is one CUDA-graph "
                         "launch whose branches are the problems' wave solves"}
     sizes = [wl.n[0] + 1 for wl, _ in chosen]
@@ -641,12 +654,14 @@ def run_batched(args):
                        "size_counts": {str(k + 1): sizes.count(k + 1) for k in inputs.BATCH_SIZES},
                        "nf": [wl.nf for wl, _ in chosen], "n_t": [n for _, n in chosen],
                        "solver": f"GMRES({restart}), {args.batch_iters} Arnoldi steps per problem",
-                       "tuned": [list(t[:2]) for t in tuned], "device_gb": round(mem, 1)},
+                       "blocking": ("autotuned " + str([list(t[:2]) for t in tuned])) if tune
+                                   else "library defaults (16 FP32 steps per launch)",
+                       "device_gb": round(mem, 1)},
             "status": st, "generate_s": round(t_gen, 1), "autotune_s": round(t_tune, 1),
             "lockstep": lockstep}
-    print(json.dumps(line), flush=True)
     for s in solvers:
         s.close()
+    return line
 
 
 def run_cube(args):
@@ -1283,6 +1298,9 @@ def main():
                  "max_helmholtz_residual": float(np.max(info["helmholtz_residual"]))}
 
     fp32 = None if args.no_fp32 else fp32_leg(args, wl, f_dev, stream, n_t)
+    batched = None
+    if not args.no_batched and rank == 0:
+        batched = batched_solves(args, args.default_batch, tune=False)
 
     if rank != 0:
         return
@@ -1349,6 +1367,7 @@ def main():
         "time_to_solution": tts,
         "unrestarted_solve_1e-8": solve,
         "fp32": fp32,
+        "batched": batched,
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(("square_large", {"seed": multi.problem_seed(
