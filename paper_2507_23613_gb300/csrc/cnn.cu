@@ -29,31 +29,45 @@ namespace {
 __host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 // ---- 3 x 3 convolution as an implicit GEMM on the 5th-generation tensor cores ----------
-// D[p][n] = sum_k A[p][k] B[n][k] with p a pixel, n an output channel and k = ci * 9 + tap
-// (tap = dy * 3 + dx): A[p][k] = in[ci][y + dy - 1][x + dx - 1] (zero outside the image),
-// B[n][k] = Wk[n][k].  A CTA of 128 threads takes 128 consecutive pixels of the batch (M = 128)
-// and all output channels (N = 16 or 32, rows past Cout zero).  K is taken in passes of 144
-// (16 input channels x 9 taps).  Each pass first copies the image rows that the CTA's pixels
-// and their vertical neighbours touch, for its 16 channels, from global into shared memory with
-// coalesced loads; then each thread builds its pixel's row of A from that copy, 8 values of k at
-// a time, in the canonical K-major layout without swizzle: 8 x 16-byte core matrices, the 16
+// D[p][n] = sum_k A[p][k] B[n][k] with p a pixel, n an output channel and k the position of
+// (input channel ci, tap = dy * 3 + dx) in the order of conv_kidx below: A[p][k] =
+// in[ci][y + dy - 1][x + dx - 1] (zero outside the image), B[n][k] = Wk[n][k].  A CTA of 128
+// threads takes 128 consecutive pixels of the batch (M = 128) and all output channels (N = 16
+// or 32, rows past Cout zero).  K is taken in passes, one group of GC = 8 or 16 input channels
+// per pass.  Each pass first copies the image rows that the CTA's pixels and their vertical
+// neighbours touch, for its channel group, from global into shared memory, channel innermost;
+// then each thread builds its pixel's row of A from that copy, one tap of 8 channels (one
+// 16-byte load) per k-chunk, in the canonical K-major layout without swizzle: 8 x 16-byte core matrices, the 16
 // row groups of a k-chunk 128 bytes apart (the descriptor's stride byte offset) and successive
 // k-chunks 16 * 128 bytes apart (its leading byte offset); B (all of K, loaded once) likewise
 // with N / 8 row groups.  One thread issues the pass's MMAs (tcgen05.mma, kind::f16, BF16
 // operands, FP32 accumulator in tensor memory) and commits them to an mbarrier; the next pass
 // overwrites A only after a bounded wait for that commit.  After the last pass every warp reads
 // its 32 rows of the accumulator (tcgen05.ld) and applies bias and ReLU.  Images too wide for
-// the row copy (more than 16.5 KB of rows per pass) are gathered from global memory instead.
+// the row copy (more than 16.5 KB of rows per pass) are read from global memory instead.
 // About 71 KB of shared memory and 32 tensor-memory columns per CTA: three CTAs per SM.
 constexpr int kConvM = 128;              // pixels per CTA (accumulator lanes)
 constexpr int kConvTmemCols = 32;        // tensor-memory columns allocated per CTA (N <= 32)
 constexpr int kConvMaxKp = 288;          // 32 input channels x 9 taps
-constexpr int kConvPassK = 144;          // K per pass: 16 channels x 9 taps, 9 MMAs of K = 16
-constexpr int kConvPassCh = kConvPassK / 9;
 constexpr int kConvTileBytes = 16896;    // staged image rows of one pass (4 rows of 129 pixels)
 
+// K order.  The input channels are taken in groups of GC = 8 (at most 8 channels) or 16, one
+// group per pass; within a pass k = tap * GC + c (c the channel within the group, tap = dy * 3 +
+// dx), padded to a multiple of 16 (9 x 8 = 72 -> 80; 9 x 16 = 144).  So each 8-value k-chunk is
+// one tap of 8 consecutive channels.
+__host__ __device__ constexpr int conv_group(int cin) { return cin <= 8 ? 8 : 16; }
+__host__ __device__ constexpr int conv_pass_k(int gc) { return (9 * gc + 15) / 16 * 16; }
+// Padded K of a convolution with cin input channels, and the position of (ci, tap) in it.
+__host__ __device__ constexpr int conv_kp(int cin) {
+  return (cin + conv_group(cin) - 1) / conv_group(cin) * conv_pass_k(conv_group(cin));
+}
+__host__ __device__ constexpr int conv_kidx(int cin, int ci, int tap) {
+  return ci / conv_group(cin) * conv_pass_k(conv_group(cin)) + tap * conv_group(cin) +
+         ci % conv_group(cin);
+}
+
 __host__ __device__ constexpr size_t conv_a_bytes() {
-  return (size_t)kConvPassK / 8 * (kConvM / 8) * 128;
+  return (size_t)conv_pass_k(16) / 8 * (kConvM / 8) * 128;
 }
 __host__ __device__ constexpr size_t conv_b_bytes(int nt) {
   return (size_t)kConvMaxKp / 8 * (nt / 8) * 128;
@@ -97,7 +111,7 @@ __device__ __forceinline__ bool conv_mbar_wait(uint32_t bar, uint32_t parity, in
   return false;
 }
 
-template <int NT>
+template <int NT, int GC>
 __global__ void __launch_bounds__(kConvM)
 k_conv_tc(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ Wk,
           const float* __restrict__ bias, int Cin, int Cout, int Kp, int Np, int B, int H, int W,
@@ -107,9 +121,9 @@ k_conv_tc(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
   __shared__ __align__(8) uint64_t mma_bar;
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int K = Cin * 9;
-  const int nk = Kp / 8;                                  // k-chunks of 8
-  constexpr int kPassChunks = kConvPassK / 8;             // 18
+  const int nk = Kp / 8;                                  // k-chunks of 8 (Kp = conv_kp(Cin))
+  constexpr int kPassChunks = conv_pass_k(GC) / 8;        // 18 (GC = 16) or 10 (GC = 8)
+  constexpr int kGroups = GC / 8;                         // k-chunks per tap
   constexpr uint32_t kSbo = 128;                          // 8-row groups 128 bytes apart
   constexpr uint32_t kLboA = (kConvM / 8) * 128;          // 2048 bytes per k-chunk of A
   constexpr uint32_t kLboB = (NT / 8) * 128;              // bytes per k-chunk of B
@@ -143,17 +157,17 @@ k_conv_tc(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
   const int64_t rlo = pix0 / W > 0 ? pix0 / W - 1 : 0;
   const int64_t rhi = last / W + 1 < rows_total ? last / W + 1 : rows_total - 1;
   const int nrows = (int)(rhi - rlo + 1);
-  const bool staged = (int64_t)nrows * kConvPassCh * W * 2 <= kConvTileBytes && W < 1024;
+  const bool staged = (int64_t)nrows * W * GC * 2 <= kConvTileBytes;
   const int b_lo = (int)(rlo / H), y_lo = (int)(rlo - (int64_t)b_lo * H);   // row rlo
   const __nv_bfloat16* inb = in + (size_t)b * Cin * plane;
-  // the 9 taps of this pixel: inside the image (bit t of tap_in) and, for the staged rows, the
-  // offset of its value from the pixel's own in the copy, apart from the channel term c W
+  // the 9 taps of this pixel: inside the image (bit t of tap_in)
   int tap_in = 0;
 #pragma unroll
   for (int t = 0; t < 9; ++t) {
     const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
     if (valid && yy >= 0 && yy < H && xx >= 0 && xx < W) tap_in |= 1 << t;
   }
+  // the staged copy's element of (row prow, column x) is sT[(prow W + x) GC + c]
   const int prow = (int)((int64_t)b * H + y - rlo);
 
   // B: NT rows of the weights (rows Np .. NT - 1 zero), 16 bytes per (row, k-chunk)
@@ -170,8 +184,8 @@ k_conv_tc(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
   for (int pass = 0; pass < npass; ++pass) {
     const int c0 = pass * kPassChunks;                         // first k-chunk of the pass
     const int nkp = nk - c0 < kPassChunks ? nk - c0 : kPassChunks;   // even: Kp % 16 == 0
-    const int ci0 = pass * kConvPassCh;
-    const int nci = Cin - ci0 < kConvPassCh ? Cin - ci0 : kConvPassCh;
+    const int ci0 = pass * GC;                                  // the pass's channel group
+    const int nci = Cin - ci0 < GC ? Cin - ci0 : GC;
     if (pass > 0) {
       // the previous pass's MMAs read A (and the copy is rewritten below): wait for them
       ok = conv_mbar_wait(bar, (uint32_t)((pass - 1) & 1), 1 << 22);
@@ -179,71 +193,64 @@ k_conv_tc(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
       waited = pass - 1;
     }
     if (staged) {
-      // rows rlo .. rhi of channels ci0 .. ci0 + nci - 1: sT[(row nci + c) W + x], 16 independent
-      // loads per thread in flight; quotients by W and nci are multiply-highs by ceil(2^32 / d)
-      // (exact for e < 2^16, d < 2^10)
-      const int n_el = nrows * nci * W;
-      const uint32_t mw = 0xFFFFFFFFu / (uint32_t)W + 1u, mc = 0xFFFFFFFFu / (uint32_t)nci + 1u;
+      // rows rlo .. rhi of the group's channels, channel innermost: sT[(row W + x) GC + c]
+      // (zero for c >= nci).  Item (row, 8-channel part g, 32-column segment) per warp: each
+      // lane loads its column's 8 channels (8 independent loads) and stores them as 16 bytes.
+      const int nxs = (W + 31) / 32;
+      const int items = nrows * kGroups * nxs;
       const uint16_t* in16 = reinterpret_cast<const uint16_t*>(in);
-      for (int e0 = tid; e0 < n_el; e0 += kConvM * 16) {
-        uint16_t t[16];
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const int e = e0 + u * kConvM;
-          t[u] = 0;
-          if (e < n_el) {
-            const int rc = W > 1 ? (int)__umulhi((uint32_t)e, mw) : e;
-            const int xr = e - rc * W;
-            const int row = nci > 1 ? (int)__umulhi((uint32_t)rc, mc) : rc;
-            const int c = rc - row * nci;
-            int bb = b_lo, yy = y_lo + row;   // batch row rlo + row as (image, row)
-            while (yy >= H) {
-              yy -= H;
-              ++bb;
-            }
-            t[u] = in16[((size_t)bb * Cin + ci0 + c) * plane + (size_t)yy * W + xr];
-          }
+      for (int it = warp; it < items; it += kConvM / 32) {
+        const int row = it / (kGroups * nxs), rest = it - row * (kGroups * nxs);
+        const int g = rest / nxs, xr = (rest - g * nxs) * 32 + lane;
+        if (xr >= W) continue;
+        if (8 * g >= nci) {   // a part of the group past the last channel: zeros
+          *reinterpret_cast<uint4*>(sT + ((size_t)row * W + xr) * GC + 8 * g) =
+              make_uint4(0u, 0u, 0u, 0u);
+          continue;
         }
+        int bb = b_lo, yy = y_lo + row;   // batch row rlo + row as (image, row)
+        while (yy >= H) {
+          yy -= H;
+          ++bb;
+        }
+        const uint16_t* src = in16 + ((size_t)bb * Cin + ci0 + 8 * g) * plane + (size_t)yy * W + xr;
+        uint16_t v[8];
 #pragma unroll
-        for (int u = 0; u < 16; ++u)
-          if (e0 + u * kConvM < n_el) sT[e0 + u * kConvM] = t[u];
+        for (int j = 0; j < 8; ++j) v[j] = 8 * g + j < nci ? src[(size_t)j * plane] : (uint16_t)0;
+        uint4 pk;
+        pk.x = v[0] | ((uint32_t)v[1] << 16);
+        pk.y = v[2] | ((uint32_t)v[3] << 16);
+        pk.z = v[4] | ((uint32_t)v[5] << 16);
+        pk.w = v[6] | ((uint32_t)v[7] << 16);
+        *reinterpret_cast<uint4*>(sT + ((size_t)row * W + xr) * GC + 8 * g) = pk;
       }
       __syncthreads();
     }
-    // A of the pass: this thread's pixel row, k = (c0 + kc) * 8 + j, taken in order of k with
-    // (channel, tap) counters
-    {
-      int k = c0 * 8;
-      int ci = k / 9, tap = k - ci * 9;
-      const int base = (prow * nci - ci0) * W + x;   // + (ci W) + tap offset in the copy
-      for (int kc = 0; kc < nkp; ++kc) {
-        uint16_t v[8];
+    // A of the pass: this thread's pixel row; k-chunk kc is tap kc / kGroups of the channels
+    // 8 (kc % kGroups) .. + 7 of the group: one 16-byte load from the copy
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          uint16_t val = 0;
-          if (k < K && ((tap_in >> tap) & 1)) {
-            const int dy = tap / 3, dx = tap - dy * 3;
-            if (staged)
-              val = sT[base + ci * W + (dy - 1) * nci * W + dx - 1];
-            else
-              val = __bfloat16_as_ushort(
-                  inb[(size_t)ci * plane + (size_t)(y + dy - 1) * W + x + dx - 1]);
-          }
-          v[j] = val;
-          ++k;
-          if (++tap == 9) {
-            tap = 0;
-            ++ci;
-          }
+    for (int kc = 0; kc < kPassChunks; ++kc) {
+      const int tap = kc / kGroups, g = kc - tap * kGroups;
+      uint4 row = make_uint4(0u, 0u, 0u, 0u);
+      if (tap < 9 && ((tap_in >> tap) & 1) && (staged || 8 * g < nci)) {
+        const int dy = tap / 3, dx = tap - dy * 3;
+        if (staged) {
+          row = *reinterpret_cast<const uint4*>(
+              sT + ((size_t)(prow + dy - 1) * W + x + dx - 1) * GC + 8 * g);
+        } else {
+          const __nv_bfloat16* src =
+              inb + (size_t)(ci0 + 8 * g) * plane + (size_t)(y + dy - 1) * W + x + dx - 1;
+          uint16_t v[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            v[j] = 8 * g + j < nci ? __bfloat16_as_ushort(src[(size_t)j * plane]) : (uint16_t)0;
+          row.x = v[0] | ((uint32_t)v[1] << 16);
+          row.y = v[2] | ((uint32_t)v[3] << 16);
+          row.z = v[4] | ((uint32_t)v[5] << 16);
+          row.w = v[6] | ((uint32_t)v[7] << 16);
         }
-        uint4 row;
-        row.x = v[0] | ((uint32_t)v[1] << 16);
-        row.y = v[2] | ((uint32_t)v[3] << 16);
-        row.z = v[4] | ((uint32_t)v[5] << 16);
-        row.w = v[6] | ((uint32_t)v[7] << 16);
-        *reinterpret_cast<uint4*>(sA + (size_t)kc * kLboA + (tid >> 3) * kSbo + (tid & 7) * 16) =
-            row;
       }
+      *reinterpret_cast<uint4*>(sA + (size_t)kc * kLboA + (tid >> 3) * kSbo + (tid & 7) * 16) = row;
     }
     // make the operands visible to the tensor core's asynchronous proxy, then issue
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -436,16 +443,17 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
   }
 }
 
-// BF16 GEMM layouts of one layer's weights w[co][ci][3][3]: forward Wk[co][ci * 9 + tap] and,
-// for the input gradient, the flipped transpose Wt[ci][co * 9 + 8 - tap].
+// BF16 GEMM layouts of one layer's weights w[co][ci][3][3] in the K order of conv_kidx: forward
+// Wk[co][kidx(ci, tap)] and, for the input gradient, the flipped transpose
+// Wt[ci][kidx(co, 8 - tap)].
 __global__ void k_pack(const float* __restrict__ w, int Cin, int Cout, int Kp, int Kpt,
                        __nv_bfloat16* __restrict__ Wk, __nv_bfloat16* __restrict__ Wt) {
   const int n = Cout * Cin * 9;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int tap = i % 9, ci = (i / 9) % Cin, co = i / (9 * Cin);
     const __nv_bfloat16 v = __float2bfloat16(w[i]);
-    Wk[(size_t)co * Kp + ci * 9 + tap] = v;
-    Wt[(size_t)ci * Kpt + co * 9 + (8 - tap)] = v;
+    Wk[(size_t)co * Kp + conv_kidx(Cin, ci, tap)] = v;
+    Wt[(size_t)ci * Kpt + conv_kidx(Cout, co, 8 - tap)] = v;
   }
 }
 
@@ -574,13 +582,15 @@ void conv(mfwh_cnn_t c, const __nv_bfloat16* in, const __nv_bfloat16* Wk, const 
           float* out_f) {
   const int64_t total = (int64_t)B * H * W;
   const unsigned blocks = (unsigned)((total + kConvM - 1) / kConvM);
-  if (Np <= 16) {
-    k_conv_tc<16><<<blocks, kConvM, conv_smem_bytes(16), c->stream>>>(
+  auto launch = [&](auto kernel, int nt) {
+    kernel<<<blocks, kConvM, conv_smem_bytes(nt), c->stream>>>(
         in, Wk, bias, Cin, Cout, Kp, Np, B, H, W, relu, out_bf, out_f, c->err);
-  } else {
-    k_conv_tc<32><<<blocks, kConvM, conv_smem_bytes(32), c->stream>>>(
-        in, Wk, bias, Cin, Cout, Kp, Np, B, H, W, relu, out_bf, out_f, c->err);
-  }
+  };
+  const bool g8 = conv_group(Cin) == 8;
+  if (Np <= 16)
+    g8 ? launch(k_conv_tc<16, 8>, 16) : launch(k_conv_tc<16, 16>, 16);
+  else
+    g8 ? launch(k_conv_tc<32, 8>, 32) : launch(k_conv_tc<32, 16>, 32);
 }
 
 // The convolution kernels' shared-memory limit, once per device.
@@ -589,9 +599,13 @@ mfwh_status conv_configure() {
   int dev = 0;
   CKC(cudaGetDevice(&dev));
   if (dev >= 0 && dev < 64 && done[dev]) return MFWH_OK;
-  CKC(cudaFuncSetAttribute(k_conv_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  CKC(cudaFuncSetAttribute(k_conv_tc<16, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)conv_smem_bytes(16)));
-  CKC(cudaFuncSetAttribute(k_conv_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  CKC(cudaFuncSetAttribute(k_conv_tc<16, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)conv_smem_bytes(16)));
+  CKC(cudaFuncSetAttribute(k_conv_tc<32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)conv_smem_bytes(32)));
+  CKC(cudaFuncSetAttribute(k_conv_tc<32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)conv_smem_bytes(32)));
   if (dev >= 0 && dev < 64) done[dev] = true;
   return MFWH_OK;
@@ -656,9 +670,9 @@ mfwh_status mfwh_cnn_create(int layers, int channels, int in_channels, uint64_t 
     c->nparams += (int64_t)co * ci * 9;
     c->boff.push_back(c->nparams);
     c->nparams += co;
-    c->Kp.push_back(round_up(ci * 9, 16));
+    c->Kp.push_back(conv_kp(ci));
     c->Np.push_back(round_up(co, 8));
-    c->Kpt.push_back(round_up(co * 9, 16));
+    c->Kpt.push_back(conv_kp(co));
     c->Npt.push_back(round_up(ci, 8));
   }
   // He-normal weights (std sqrt(2 / (9 Cin))), zero biases, from a seeded host generator
