@@ -365,3 +365,64 @@ def test_invalid_c2_fields_are_rejected(bad):
     with pytest.raises(_lib.MfwhError) as e:
         M.plan(prob)
     assert e.value.status == _lib.ERR_INVALID_ARG
+
+
+def test_entry_points_reject_null_handles_and_bad_arguments_before_any_cuda_call(lib):
+    """The header's error behaviour for missing handles and arguments: MFWH_ERR_INVALID_ARG and
+    a message, decided on the host before any CUDA call (this runs without a GPU); the destroy
+    calls accept NULL."""
+    import ctypes as C
+    null = None
+    info = _lib.SolveInfo()
+    d = C.c_double(0.0)
+    i64 = C.c_int64(0)
+    i32 = C.c_int(0)
+    r = (C.c_double * 16)()
+    calls = {
+        "mfwh_set_forcing": lambda: lib.mfwh_set_forcing(null, null),
+        "mfwh_apply_Pi": lambda: lib.mfwh_apply_Pi(null, null, null, 1),
+        "mfwh_solve_fpi": lambda: lib.mfwh_solve_fpi(null, 1, null),
+        "mfwh_solve_gmres": lambda: lib.mfwh_solve_gmres(null, 20, 1e-8, 20, 0.0, null,
+                                                         C.byref(info)),
+        "mfwh_solve_refined": lambda: lib.mfwh_solve_refined(null, 20, 1e-6, 20, 1e-6, 3, null,
+                                                             C.byref(info)),
+        "mfwh_solve_relaxed": lambda: lib.mfwh_solve_relaxed(null, 20, 1e-6, 1e-2, 20, 1e-6, 3,
+                                                             null, C.byref(info)),
+        "mfwh_set_graphs": lambda: lib.mfwh_set_graphs(null, 1),
+        "mfwh_solve_batch": lambda: lib.mfwh_solve_batch(null, 0, 20, 1e-8, 20, null, null, null),
+        "mfwh_solve_batch_graph": lambda: lib.mfwh_solve_batch_graph(null, 0, 20, 1e-8, 20, null,
+                                                                     null, null, null),
+        "mfwh_autotune": lambda: lib.mfwh_autotune(null, null, C.byref(i32), C.byref(i32),
+                                                   C.byref(d)),
+        "mfwh_residual": lambda: lib.mfwh_residual(null, null, r),
+        "mfwh_residual_noalloc": lambda: lib.mfwh_residual_noalloc(null, null, null, r, null),
+        "mfwh_get_setup": lambda: lib.mfwh_get_setup(null, C.byref(_lib.Setup())),
+        "mfwh_last_timing": lambda: lib.mfwh_last_timing(null, C.byref(d), C.byref(i64),
+                                                         C.byref(i64)),
+        "mfwh_mg_stats": lambda: lib.mfwh_mg_stats(null, C.byref(i64), C.byref(i64),
+                                                   C.byref(i64), C.byref(i32), 0),
+        "mfwh_set_wait_limit": lambda: lib.mfwh_set_wait_limit(null, 1.0),
+        "mfwh_debug_bounds": lambda: lib.mfwh_debug_bounds(null, C.byref(i64), C.byref(i64),
+                                                           C.byref(i64), C.byref(i32)),
+        "mfwh_warm_start_data": lambda: lib.mfwh_warm_start_data(null, 1.0, null, null, null),
+        "mfwh_warm_start": lambda: lib.mfwh_warm_start(null, null, 1.0, null, C.byref(d)),
+        "mfwh_cnn_set_params": lambda: lib.mfwh_cnn_set_params(null, null, 0),
+        "mfwh_cnn_get_params": lambda: lib.mfwh_cnn_get_params(null, null, null, 0),
+        "mfwh_cnn_forward": lambda: lib.mfwh_cnn_forward(null, null, 1, 8, 8, null),
+        "mfwh_cnn_train_step": lambda: lib.mfwh_cnn_train_step(null, null, null, null, 1, 8, 8,
+                                                               1e-3, null),
+        # a network of one layer, before any device memory is touched
+        "mfwh_cnn_create": lambda: lib.mfwh_cnn_create(1, 32, 4, 7, null, C.byref(C.c_void_p())),
+    }
+    for name, call in calls.items():
+        st = call()
+        assert st == _lib.ERR_INVALID_ARG, (name, st, lib.mfwh_last_error())
+        assert lib.mfwh_last_error(), name
+    # mfwh_create: no output pointer, then no problem (the output is set to NULL first)
+    out = C.c_void_p(1234)
+    assert lib.mfwh_create(null, null, null) == _lib.ERR_INVALID_ARG
+    assert lib.mfwh_create(null, null, C.byref(out)) == _lib.ERR_INVALID_ARG
+    assert out.value is None
+    assert lib.mfwh_cnn_param_count(null) == 0
+    lib.mfwh_destroy(null)
+    lib.mfwh_cnn_destroy(null)
