@@ -11,6 +11,13 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a GB300 and the built CUDA library")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+    # A planted oracle mistake (tests/oracle_mutants.py), set only by the child processes of
+    # tests/test_oracle_mutants.py: the oracle's pins must then fail.
+    mutant = os.environ.get("MFWH_ORACLE_MUTANT")
+    if mutant:
+        sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+        import oracle_mutants
+        oracle_mutants.apply(mutant)
 
 
 def printed_tolerance(text):

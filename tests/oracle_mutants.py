@@ -1,0 +1,165 @@
+"""Plausible mistakes planted in the oracle, one at a time (test infrastructure).
+
+Each mutant rewrites one line of one oracle function, as a slip in transcribing the paper
+would: a dropped factor, a wrong sign, a shifted index, a transposed operand, an unadjusted
+frequency.  tests/test_oracle_mutants.py runs the oracle's pins once per mutant, in a fresh
+process where conftest.py applies it (environment variable MFWH_ORACLE_MUTANT), and requires
+a pin to fail: the pins, not the oracle's agreement with the library, catch each mistake.
+Nothing here is imported by the library or by the oracle.
+"""
+
+import inspect
+import textwrap
+
+# name: (module, function or Class.method, text to replace, replacement, what it corrupts)
+MUTANTS = {
+    # --- the wave solve and filter sums (oracle/wave.py) --------------------------------------
+    "forcing_sign": (
+        "oracle.wave", "composite_forcing",
+        "F[inner] += prob.forcing[m][inner]", "F[inner] -= prob.forcing[m][inner]",
+        "sign of F^n, eq. WaveSchemeForcing"),
+    "forcing_time_shift": (
+        "oracle.wave", "composite_forcing", "t = n * s.dt", "t = (n + 1) * s.dt",
+        "forcing at t^{n+1} instead of t^n, eq. WaveSchemeA"),
+    "forcing_unadjusted_omega": (
+        "oracle.wave", "composite_forcing", "math.cos(s.omega_t[m] * t)", "math.cos(s.omega[m] * t)",
+        "omega instead of omega~ in the forcing, eq. WaveSchemeForcing"),
+    "first_step_without_half": (
+        "oracle.wave", "apply_Pi", "W1[inner] = (W0 + 0.5 * dt2 *", "W1[inner] = (W0 + dt2 *",
+        "factor 1/2 of the first step, eq. implicitFirstStep"),
+    "step_forcing_sign": (
+        "oracle.wave", "apply_Pi", "- F(n)))[inner]", "+ F(n)))[inner]",
+        "sign of F^n in the later steps, eq. WaveSchemeA"),
+    "filter_weight_index": (
+        "oracle.wave", "apply_Pi", "q[m] += s.w[n + 1, m] * W_next", "q[m] += s.w[n, m] * W_next",
+        "weight w_{n+1} of W^{n+1} in q_m, eq. pDefQ"),
+    "filter_weight_of_w0": (
+        "oracle.wave", "apply_Pi", "q[m] += s.w[0, m] * W0", "q[m] += s.w[1, m] * W0",
+        "weight w_0 of W^0 in q_m, eq. pDefQ"),
+    "filter_solve_transposed": (
+        "oracle.wave", "_filter_update", "np.linalg.solve(s.B, flat)", "np.linalg.solve(s.B.T, flat)",
+        "B V = q solved with B^T, eq. waveHoltzMatrixIteration"),
+    "explicit_filter_transposed": (
+        "oracle.wave", "_filter_update", "off = s.B - np.diag(np.diag(s.B))",
+        "off = s.B.T - np.diag(np.diag(s.B))", "off-diagonal B_mj of the explicit filter, "
+        "footnote to eq. filterII"),
+    "laplacian_one_spacing": (
+        "oracle.wave", "laplacian", "acc += (W[tuple(plus)] - 2.0 * W[inner] + W[tuple(minus)]) / (h * h)",
+        "acc += (W[tuple(plus)] - 2.0 * W[inner] + W[tuple(minus)]) / (grid.h[0] * grid.h[0])",
+        "h_x used for every axis in Delta_h"),
+    "laplacian_c_not_squared": (
+        "oracle.wave", "laplacian", "out[inner] = c2 * acc", "out[inner] = np.sqrt(c2) * acc",
+        "c instead of c^2 in L = c^2 Delta"),
+    "laplacian4_centre": (
+        "oracle.wave", "laplacian", "- 30.0 * sh(0)", "- 32.0 * sh(0)",
+        "centre weight of the fourth-order stencil"),
+    "laplacian4_even_ghost": (
+        "oracle.wave", "laplacian", 'reflect_type="odd"', 'reflect_type="even"',
+        "odd reflection of the Dirichlet ghost values, fourth order"),
+    "implicit_lagged_level": (
+        "oracle.wave", "_apply_Pi_implicit", "Lh(beta * W_cur + alpha * W_prev)",
+        "Lh(beta * W_cur + alpha * W_cur)", "alpha L_h W^{n-1} term of eq. WaveSchemeA"),
+    "residual_sign": (
+        "oracle.wave", "helmholtz_residual", "+ prob.setup.omega[m] ** 2 * V[m]",
+        "- prob.setup.omega[m] ** 2 * V[m]", "sign of omega^2, eq. errorAndResid"),
+    "residual_unnormalised": (
+        "oracle.wave", "helmholtz_residual", "den = np.max(np.abs(prob.forcing[m][inner]))",
+        "den = 1.0", "normalisation by max|f_m|, eq. errorAndResid"),
+    "gmres_projection_index": (
+        "oracle.wave", "gmres", "w = w - Hbar[i, j] * basis[i]", "w = w - Hbar[i, j] * basis[j]",
+        "Gram-Schmidt against basis vector i"),
+    "gmres_update_index": (
+        "oracle.wave", "gmres", "x = x + y[i] * basis[i]", "x = x + y[i] * basis[0]",
+        "solution update x + V y"),
+    # --- set-up (oracle/filters.py) -----------------------------------------------------------
+    "adjusted_frequency_factor": (
+        "oracle.filters", "adjusted_frequency", "(1.0 - 0.5 * beta * x * x)", "(1.0 - beta * x * x)",
+        "factor beta/2 of eq. omegaImplicit"),
+    "time_step_without_sqrt_d": (
+        "oracle.filters", "explicit_time_step", "math.sqrt(float(np.sum(1.0 / (h * h))))",
+        "math.sqrt(float(np.max(1.0 / (h * h))))", "von Neumann limit summed over the axes"),
+    "time_step_unadjusted": (
+        "oracle.filters", "explicit_time_step", "dt = 2.0 * math.sin(math.pi * n_p / n_t) / omega1",
+        "dt = 2.0 * math.pi * n_p / n_t / omega1", "dt that makes omega~_1 N_t dt = 2 pi N_p"),
+    "implicit_time_step_factor": (
+        "oracle.filters", "implicit_time_step", "(0.5 * beta + alpha * math.cos(theta))",
+        "(0.5 * beta + alpha)", "implicit dt from omega~_1 dt = theta"),
+    "period_count_ceil": (
+        "oracle.filters", "period_counts", "math.floor(int(n_p)", "math.ceil(int(n_p)",
+        "floor in N_{p,m}, eq. TbarDef"),
+    "trapezoid_interior_end": (
+        "oracle.filters", "trapezoid_weights", "sigma[n, m] = dt if 0 < n < k else 0.5 * dt",
+        "sigma[n, m] = dt if 0 < n <= k else 0.5 * dt", "half weight at t_k, eq. DefNI"),
+    "trapezoid_partial_panel": (
+        "oracle.filters", "trapezoid_weights", "sigma[k + 1, m] += 0.5 * dt * r * r",
+        "sigma[k + 1, m] += dt * r * r", "partial panel [t_k, T_{f,m}], eq. DefNI"),
+    "kernel_sine_sign": (
+        "oracle.filters", "filter_kernel", "a + c * np.cos(tau) + s * np.sin(tau)",
+        "a + c * np.cos(tau) - s * np.sin(tau)", "sign of the sine term, eq. newFilterKernel"),
+    "traditional_factor": (
+        "oracle.filters", "traditional_parameters", "(2.0 * np.tan(omega_t * dt))",
+        "(np.tan(omega_t * dt))", "factor 2 of eq. origParamAdjust"),
+    "weights_scale": (
+        "oracle.filters", "filter_weights", "(2.0 / t_fm[m])", "(1.0 / t_fm[m])",
+        "factor 2 / T~_{f,m} of eq. pDefQ"),
+    "filter_matrix_transposed": (
+        "oracle.filters", "filter_matrix", "return w.T @ cos_tab", "return cos_tab.T @ w",
+        "B_{mj} with m and j exchanged, eq. filterA"),
+    "lambda_range": (
+        "oracle.filters", "_optimise", "lam_max = omega[-1] + c_delta * nf * delta_nf",
+        "lam_max = omega[-1] + c_delta * delta_nf", "right end of Lambda, eq. LambdaRange"),
+    "lambda_spacing": (
+        "oracle.filters", "_optimise", "delta_nf = omega[-1] / (2.0 * n_pm[-1])",
+        "delta_nf = omega[-1] / n_pm[-1]", "Delta_{N_f} of eq. LambdaRange"),
+    "lambda_nodes_not_midpoints": (
+        "oracle.filters", "_optimise", "(np.arange(1, n_lambda + 1) - 0.5)",
+        "np.arange(1, n_lambda + 1)", "midpoint nodes lambda_k of Algorithm 2"),
+    "parameters_c_s_exchanged": (
+        "oracle.filters", "_optimise", "params = np.stack([x_a, y[:nf], y[nf:]], axis=1)",
+        "params = np.stack([x_a, y[nf:], y[:nf]], axis=1)", "order (a, c, s) of y, eq. yOpt"),
+    "derivative_sign": (
+        "oracle.filters", "_QuadratureBasis._eval", "return (-np.sin(arg) * t) @ (wt * base)",
+        "return (np.sin(arg) * t) @ (wt * base)", "d/dlambda cos(lambda t), eq. constraintsVec"),
+    "mu_row_sums": (
+        "oracle.filters", "mu_discrete", "np.linalg.inv(B).sum(axis=0)",
+        "np.linalg.inv(B).sum(axis=1)", "gamma_m as column sums of B^{-1}, eq. MFWHmud"),
+    # --- warm-start network (oracle/cnn.py) ---------------------------------------------------
+    "conv_flipped_kernel": (
+        "oracle.cnn", "conv_same", 'np.einsum("oc,bchw->bohw", w[:, :, dy, dx], patch)',
+        'np.einsum("oc,bchw->bohw", w[:, :, 2 - dy, 2 - dx], patch)',
+        "convolution instead of cross-correlation"),
+    "conv_backward_shift": (
+        "oracle.cnn", "conv_same_backward", "gxp[:, :, dy:dy + H, dx:dx + W] +=",
+        "gxp[:, :, 2 - dy:2 - dy + H, 2 - dx:2 - dx + W] +=", "input gradient scattered back"),
+    "relu_derivative_dropped": (
+        "oracle.cnn", "loss_and_grads", "g = gx * (acts[i] > 0.0)", "g = gx",
+        "ReLU derivative in backpropagation"),
+    "loss_gradient_factor": (
+        "oracle.cnn", "loss_and_grads", "g = 2.0 * diff / count", "g = diff / count",
+        "factor 2 of the squared-error gradient"),
+    "adam_bias_power": (
+        "oracle.cnn", "adam_step", "mhat = m / (1.0 - beta1 ** t)", "mhat = m / (1.0 - beta1)",
+        "power t of Adam's bias correction"),
+    "adam_eps_inside_sqrt": (
+        "oracle.cnn", "adam_step", "(np.sqrt(vhat) + eps)", "np.sqrt(vhat + eps)",
+        "epsilon added after the square root in Adam"),
+}
+
+
+def apply(name):
+    """Replace the target function (or method) of mutant `name` by its mutated copy."""
+    import importlib
+
+    mod_name, target, old, new, _ = MUTANTS[name]
+    mod = importlib.import_module(mod_name)
+    owner, attr = mod, target
+    if "." in target:
+        cls, attr = target.split(".")
+        owner = getattr(mod, cls)
+    src = textwrap.dedent(inspect.getsource(getattr(owner, attr)))
+    if src.count(old) != 1:
+        raise ValueError(f"mutant {name}: expected the text once in {target}, found "
+                         f"{src.count(old)} times")
+    namespace = dict(mod.__dict__)
+    exec(compile(src.replace(old, new), f"<mutant {name}>", "exec"), namespace)
+    setattr(owner, attr, namespace[attr])
