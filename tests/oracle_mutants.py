@@ -71,6 +71,23 @@ MUTANTS = {
     "gmres_update_index": (
         "oracle.wave", "gmres", "x = x + y[i] * basis[i]", "x = x + y[i] * basis[0]",
         "solution update x + V y"),
+    "implicit_first_step_forcing_half": (
+        "oracle.wave", "_apply_Pi_implicit", "- 0.5 * dt2 * F(0))", "- dt2 * F(0))",
+        "factor 1/2 of F^0 in the implicit first step, eq. implicitFirstStep"),
+    "implicit_forcing_factor_half": (
+        "oracle.wave", "composite_forcing", "factor = beta + 2.0 * alpha * math.cos",
+        "factor = beta + alpha * math.cos", "factor beta + 2 alpha cos(omega~ dt), "
+        "eq. WaveSchemeForcing"),
+    "direct_solve_sign": (
+        "oracle.wave", "helmholtz_direct", "spla.spsolve(L + prob.setup.omega[m] ** 2 * I, rhs)",
+        "spla.spsolve(L - prob.setup.omega[m] ** 2 * I, rhs)",
+        "the direct reference solves L_h U + omega^2 U = f, eq. discreteHelmholtz"),
+    "gmres_restart_residual_sign": (
+        "oracle.wave", "gmres", "r = b - A(x) if np.any(x) else b.copy()",
+        "r = b + A(x) if np.any(x) else b.copy()", "restart residual b - A x"),
+    "gmres_initial_guess_ignored": (
+        "oracle.wave", "gmres", "x = np.zeros_like(b) if V0 is None else np.array(V0, dtype=np.float64)",
+        "x = np.zeros_like(b)", "GMRES from the given initial guess"),
     # --- set-up (oracle/filters.py) -----------------------------------------------------------
     "adjusted_frequency_factor": (
         "oracle.filters", "adjusted_frequency", "(1.0 - 0.5 * beta * x * x)", "(1.0 - beta * x * x)",
@@ -123,6 +140,19 @@ MUTANTS = {
     "mu_row_sums": (
         "oracle.filters", "mu_discrete", "np.linalg.inv(B).sum(axis=0)",
         "np.linalg.inv(B).sum(axis=1)", "gamma_m as column sums of B^{-1}, eq. MFWHmud"),
+    "period_lengths_of_first_frequency": (
+        "oracle.filters", "period_counts", "t_fm = n_pm * (2.0 * math.pi / omega)",
+        "t_fm = n_pm * (2.0 * math.pi / omega[0])", "T~_{f,m} = N_{p,m} 2 pi / omega~_m, "
+        "eq. TbarDef"),
+    "weights_time_shift": (
+        "oracle.filters", "filter_weights", "t = np.arange(n_t + 1) * dt",
+        "t = np.arange(1, n_t + 2) * dt", "kernel evaluated at t^n, eq. pDefQ"),
+    "beta_sine": (
+        "oracle.filters", "discrete_beta", "np.cos(np.outer(lam_tilde, t)) @ w",
+        "np.sin(np.outer(lam_tilde, t)) @ w", "cos(lambda t^n) in beta_d, eq. betadDefA"),
+    "trapezoid_first_weight": (
+        "oracle.filters", "trapezoid_weights", "if k == 0:\n            sigma[0, m] = 0.0",
+        "if k == 0:\n            sigma[0, m] = 0.5 * dt", "no full panel when T_{f,m} < dt"),
     # --- warm-start network (oracle/cnn.py) ---------------------------------------------------
     "conv_flipped_kernel": (
         "oracle.cnn", "conv_same", 'np.einsum("oc,bchw->bohw", w[:, :, dy, dx], patch)',
@@ -143,6 +173,15 @@ MUTANTS = {
     "adam_eps_inside_sqrt": (
         "oracle.cnn", "adam_step", "(np.sqrt(vhat) + eps)", "np.sqrt(vhat + eps)",
         "epsilon added after the square root in Adam"),
+    "relu_on_output": (
+        "oracle.cnn", "forward", "if i + 1 < len(params):", "if i < len(params):",
+        "no ReLU after the last layer"),
+    "adam_first_moment_weight": (
+        "oracle.cnn", "adam_step", "m = beta1 * m + (1.0 - beta1) * g", "m = beta1 * m + beta1 * g",
+        "weight 1 - beta1 of the new gradient in Adam's first moment"),
+    "adam_second_moment_linear": (
+        "oracle.cnn", "adam_step", "v = beta2 * v + (1.0 - beta2) * g * g",
+        "v = beta2 * v + (1.0 - beta2) * np.abs(g)", "squared gradient in Adam's second moment"),
 }
 
 

@@ -119,7 +119,8 @@ def test_trapezoid_weights_exact_for_linears():
     """eq. DefNI: the rule integrates linear functions exactly on [0, T_{f,m}], and on
     a grid-aligned interval it is the plain trapezoid rule."""
     dt, n_t = 0.0137, 97
-    t_fm = np.array([n_t * dt, 0.731, 1.0003, 0.5 * dt * 3])
+    # the last case has T_{f,m} < dt: no full panel, only the partial one from t_0
+    t_fm = np.array([n_t * dt, 0.731, 1.0003, 0.5 * dt * 3, 0.4 * dt])
     sigma = F.trapezoid_weights(n_t, dt, t_fm)
     t = np.arange(n_t + 1) * dt
     for m, T in enumerate(t_fm):

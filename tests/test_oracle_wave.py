@@ -225,6 +225,23 @@ def test_gmres_matches_dense_and_direct():
     assert np.max(W.helmholtz_residual(p, x)) < 1e-9
 
 
+def test_gmres_starts_from_the_initial_guess():
+    """GMRES from V0 iterates on the residual b - A V0: started at the fixed point U (the
+    direct Helmholtz solution, for which A U = b) it stops before any Arnoldi step and returns
+    U; started at U / 2 (residual b / 2) its first step stays below the initial relative
+    residual 1/2, and it reaches U."""
+    p = _problem((9, 9), [5.5, 9.3])
+    U = W.helmholtz_direct(p)
+    x, info = W.gmres(p, V0=U, restart=10, tol=1e-8, max_iters=50)
+    assert info.converged and info.iterations == 0
+    assert np.max(np.abs(x - U)) == 0.0
+    x, info = W.gmres(p, V0=0.5 * U, restart=10, tol=1e-8, max_iters=1)
+    assert info.iterations == 1 and info.history[0] < 0.5 + 1e-12   # GMRES never increases it
+    x, info = W.gmres(p, V0=0.5 * U, restart=10, tol=1e-13, max_iters=400)
+    assert info.converged
+    assert np.max(np.abs(x - U)) < 1e-9 * np.max(np.abs(U))
+
+
 def test_gmres_full_krylov_is_exact():
     """Without restarts GMRES terminates with the exact solution after at most dim steps."""
     p = _problem((5, 5), [5.5, 9.3])
