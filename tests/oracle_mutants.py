@@ -88,6 +88,18 @@ MUTANTS = {
     "gmres_initial_guess_ignored": (
         "oracle.wave", "gmres", "x = np.zeros_like(b) if V0 is None else np.array(V0, dtype=np.float64)",
         "x = np.zeros_like(b)", "GMRES from the given initial guess"),
+    "fpi_residual_max_norm": (
+        "oracle.wave", "fpi_residual", "return math.sqrt(float(np.mean(d * d)))",
+        "return float(np.max(np.abs(d)))", "root mean square of V^k - V^{k-1}, eq. residual"),
+    "fpi_restarts_from_initial": (
+        "oracle.wave", "fixed_point_iteration", "V = apply_Pi(prob, V, forced=True)",
+        "V = apply_Pi(prob, V0, forced=True)", "V^{k+1} = Pi(V^k), Algorithm 1"),
+    "boundary_second_last_line": (
+        "oracle.wave", "zero_boundary", "idx[ax] = -1", "idx[ax] = -2",
+        "Dirichlet data on the last grid line"),
+    "laplacian_matrix4_ghost_sign": (
+        "oracle.wave", "laplacian_matrix", "main[0] += 1.0", "main[0] -= 1.0",
+        "odd-reflection ghost value folded into the first row, fourth order"),
     # --- set-up (oracle/filters.py) -----------------------------------------------------------
     "adjusted_frequency_factor": (
         "oracle.filters", "adjusted_frequency", "(1.0 - 0.5 * beta * x * x)", "(1.0 - beta * x * x)",
@@ -153,6 +165,16 @@ MUTANTS = {
     "trapezoid_first_weight": (
         "oracle.filters", "trapezoid_weights", "if k == 0:\n            sigma[0, m] = 0.0",
         "if k == 0:\n            sigma[0, m] = 0.5 * dt", "no full panel when T_{f,m} < dt"),
+    "setup_optimises_unadjusted_omega": (
+        "oracle.filters", "make_setup", "opt = opt_parameters_discrete(omega_t, n_p, n_t",
+        "opt = opt_parameters_discrete(omega, n_p, n_t", "Algorithm 2 with inputs omega~"),
+    "step_count_floor": (
+        "oracle.filters", "explicit_time_step",
+        "int(math.ceil(t_final / (cfl * dt_stab)))", "int(math.floor(t_final / (cfl * dt_stab)))",
+        "smallest N_t whose step fits under the CFL limit"),
+    "gauss_nodes_unscaled": (
+        "oracle.filters", "opt_parameters_continuous", "nodes = [0.5 * tm * (x + 1.0) for tm in t_fm]",
+        "nodes = [tm * (x + 1.0) for tm in t_fm]", "Gauss-Legendre nodes mapped to [0, T_{f,m}]"),
     # --- warm-start network (oracle/cnn.py) ---------------------------------------------------
     "conv_flipped_kernel": (
         "oracle.cnn", "conv_same", 'np.einsum("oc,bchw->bohw", w[:, :, dy, dx], patch)',
@@ -182,6 +204,9 @@ MUTANTS = {
     "adam_second_moment_linear": (
         "oracle.cnn", "adam_step", "v = beta2 * v + (1.0 - beta2) * g * g",
         "v = beta2 * v + (1.0 - beta2) * np.abs(g)", "squared gradient in Adam's second moment"),
+    "conv_bias_dropped_in_gradient": (
+        "oracle.cnn", "conv_same_backward", "gb = gout.sum(axis=(0, 2, 3))",
+        "gb = gout.sum(axis=(0, 2, 3)) * 0.0", "bias gradient"),
 }
 
 

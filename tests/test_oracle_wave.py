@@ -225,6 +225,25 @@ def test_gmres_matches_dense_and_direct():
     assert np.max(W.helmholtz_residual(p, x)) < 1e-9
 
 
+def test_fpi_residual_definition():
+    """eq. residual: (r^{(k)})^2 is the sum of squared changes over the N_f frequencies and the
+    N_a points of Omega_h (the interior points), divided by N_f N_a.  Worked cases on a 6 x 5
+    grid (20 interior points) with N_f = 2: one interior change of 3 gives 3 / sqrt(40); the
+    same change c everywhere in the interior gives |c|; changes on boundary points do not
+    count."""
+    g = W.Grid((6, 5), (1.0, 1.0))
+    old = np.zeros((2,) + g.shape)
+    new = old.copy()
+    new[1, 2, 3] = 3.0
+    assert abs(W.fpi_residual(new, old, g) - 3.0 / math.sqrt(40.0)) < 1e-15
+    new = old.copy()
+    new[(slice(None),) + g.interior()] = -0.25
+    assert abs(W.fpi_residual(new, old, g) - 0.25) < 1e-15
+    new[:, 0, :] = 7.0
+    new[:, :, -1] = -5.0
+    assert abs(W.fpi_residual(new, old, g) - 0.25) < 1e-15
+
+
 def test_gmres_starts_from_the_initial_guess():
     """GMRES from V0 iterates on the residual b - A V0: started at the fixed point U (the
     direct Helmholtz solution, for which A U = b) it stops before any Arnoldi step and returns
