@@ -30,6 +30,29 @@ def _as_ptr(x):
     raise TypeError(f"unsupported buffer type {type(x)!r}")
 
 
+def _numel(x):
+    return int(x.numel()) if hasattr(x, "numel") else int(x.size)
+
+
+def _sized(x, count, what):
+    """_as_ptr of a buffer that must hold at least count float64 values.  The library reads or
+    writes count values through the pointer and cannot check the buffer's size itself, so a
+    short buffer is refused here, before any call."""
+    ptr = _as_ptr(x)
+    if x is not None and _numel(x) < count:
+        raise ValueError(f"{what}: {_numel(x)} values, the problem needs {count} "
+                         "(nf x grid points)")
+    return ptr
+
+
+def _problem_values(problem):
+    """nf x grid points of an mfwh_problem: the length of its [nf][points] buffers."""
+    points = 1
+    for a in range(problem.dim):
+        points *= int(problem.n[a]) + 1
+    return int(problem.nf) * points
+
+
 def _dptr(arr):
     return arr.ctypes.data_as(C.POINTER(C.c_double))
 
@@ -52,8 +75,11 @@ def make_problem(n, length, omega, forcing=None, c_lo=1.0, c_hi=None, interface=
     p.nf = om.size
     p.omega = _dptr(om)
     keep = [om]
+    points = 1
+    for a in range(len(n)):
+        points *= int(n[a]) + 1
     if forcing is not None:
-        ptr = _as_ptr(forcing)
+        ptr = _sized(forcing, om.size * points, "forcing")
         p.forcing = C.cast(ptr, C.POINTER(C.c_double))
         keep.append(forcing)
     p.c_mode = _lib.C_CONST if c_hi is None else _lib.C_TWO_LAYER
@@ -61,7 +87,7 @@ def make_problem(n, length, omega, forcing=None, c_lo=1.0, c_hi=None, interface=
         if c_hi is not None:
             raise ValueError("give either c_hi (two layers) or c2_field, not both")
         p.c_mode = _lib.C_FIELD
-        p.c2_field = C.cast(_as_ptr(c2_field), C.POINTER(C.c_double))
+        p.c2_field = C.cast(_sized(c2_field, points, "c2_field"), C.POINTER(C.c_double))
         keep.append(c2_field)
     p.c_lo = float(c_lo)
     p.c_hi = float(c_hi if c_hi is not None else c_lo)
@@ -72,6 +98,9 @@ def make_problem(n, length, omega, forcing=None, c_lo=1.0, c_hi=None, interface=
     p.filter_mode = int(filter_mode)
     if user_params is not None:
         up = np.ascontiguousarray(user_params, dtype=np.float64).reshape(-1)
+        if int(filter_mode) == _lib.FILTER_USER and up.size < 3 * om.size:
+            raise ValueError(f"user_params: {up.size} values, the problem needs {3 * om.size} "
+                             "((a, c, s) per frequency)")
         p.user_params = _dptr(up)
         keep.append(up)
     p.n_delta = int(n_delta)
@@ -136,8 +165,10 @@ def mfwh_residual_noalloc(problem, forcing, v, stream=None):
         import torch
         stream = torch.cuda.current_stream().cuda_stream
     r = np.zeros(problem.nf)
-    _lib.check(_lib.load().mfwh_residual_noalloc(C.byref(problem), _as_ptr(forcing), _as_ptr(v),
-                                                 _dptr(r), C.c_void_p(stream)))
+    count = _problem_values(problem)
+    _lib.check(_lib.load().mfwh_residual_noalloc(C.byref(problem), _sized(forcing, count, "forcing"),
+                                                 _sized(v, count, "v"), _dptr(r),
+                                                 C.c_void_p(stream)))
     return r
 
 
@@ -158,7 +189,9 @@ def solve_batch(solvers, vs, restart=20, tol=1e-8, max_iters=1000, raise_on_erro
     Returns (status, per-problem info dicts, per-problem seconds)."""
     n = len(solvers)
     hs = (C.c_void_p * n)(*[s._handle.value for s in solvers])
-    ptrs = (C.c_void_p * n)(*[_as_ptr(v).value for v in vs])
+    if len(vs) != n:
+        raise ValueError("one solution buffer per solver")
+    ptrs = (C.c_void_p * n)(*[_sized(v, sv.values, "v").value for sv, v in zip(solvers, vs)])
     infos = (_lib.SolveInfo * n)()
     secs = np.zeros(n)
     st = _lib.load().mfwh_solve_batch(hs, n, int(restart), float(tol), int(max_iters), ptrs,
@@ -181,7 +214,9 @@ def solve_batch_graph(solvers, vs, restart=20, tol=1e-8, max_iters=1000, stream=
         import torch
         stream = torch.cuda.current_stream().cuda_stream
     hs = (C.c_void_p * n)(*[s._handle.value for s in solvers])
-    ptrs = (C.c_void_p * n)(*[_as_ptr(v).value for v in vs])
+    if len(vs) != n:
+        raise ValueError("one solution buffer per solver")
+    ptrs = (C.c_void_p * n)(*[_sized(v, sv.values, "v").value for sv, v in zip(solvers, vs)])
     infos = (_lib.SolveInfo * n)()
     secs = np.zeros(n)
     st = _lib.load().mfwh_solve_batch_graph(hs, n, int(restart), float(tol), int(max_iters), ptrs,
@@ -227,6 +262,7 @@ class Solver:
         s = _lib.Setup()
         _lib.check(lib.mfwh_get_setup(self._handle, C.byref(s)))
         self.setup = setup_arrays(s)
+        self.values = self.nf * int(self.setup["points"])   # length of every [nf][points] buffer
 
     def close(self):
         if getattr(self, "_handle", None) and self._handle.value:
@@ -240,15 +276,18 @@ class Solver:
             pass
 
     def set_forcing(self, forcing):
-        _lib.check(_lib.load().mfwh_set_forcing(self._handle, _as_ptr(forcing)))
+        _lib.check(_lib.load().mfwh_set_forcing(self._handle,
+                                                _sized(forcing, self.values, "forcing")))
 
     def mfwh_apply_Pi(self, v_in, v_out, forced=True):
-        _lib.check(_lib.load().mfwh_apply_Pi(self._handle, _as_ptr(v_in), _as_ptr(v_out), int(forced)))
+        _lib.check(_lib.load().mfwh_apply_Pi(self._handle, _sized(v_in, self.values, "v_in"),
+                                             _sized(v_out, self.values, "v_out"), int(forced)))
 
     apply_Pi = mfwh_apply_Pi
 
     def solve_fpi(self, v, iters):
-        _lib.check(_lib.load().mfwh_solve_fpi(self._handle, int(iters), _as_ptr(v)))
+        _lib.check(_lib.load().mfwh_solve_fpi(self._handle, int(iters),
+                                              _sized(v, self.values, "v")))
 
     def solve_gmres(self, v, restart=20, tol=1e-8, max_iters=1000, spurious_tol=0.0,
                     history=512, raise_on_error=True):
@@ -257,7 +296,8 @@ class Solver:
         info.history_capacity = history
         info.history = _dptr(hist)
         st = _lib.load().mfwh_solve_gmres(self._handle, int(restart), float(tol), int(max_iters),
-                                          float(spurious_tol), _as_ptr(v), C.byref(info))
+                                          float(spurious_tol), _sized(v, self.values, "v"),
+                                          C.byref(info))
         if raise_on_error:
             _lib.check(st)
         out = {
@@ -280,7 +320,7 @@ class Solver:
         info.history = _dptr(hist)
         st = _lib.load().mfwh_solve_refined(self._handle, int(restart), float(inner_tol),
                                             int(max_iters), float(target), int(max_refinements),
-                                            _as_ptr(v), C.byref(info))
+                                            _sized(v, self.values, "v"), C.byref(info))
         if raise_on_error:
             _lib.check(st)
         return {
@@ -304,7 +344,8 @@ class Solver:
         info.history = _dptr(hist)
         st = _lib.load().mfwh_solve_relaxed(self._handle, int(restart), float(inner_tol),
                                             float(relax_below), int(max_iters), float(target),
-                                            int(max_refinements), _as_ptr(v), C.byref(info))
+                                            int(max_refinements), _sized(v, self.values, "v"),
+                                            C.byref(info))
         if raise_on_error:
             _lib.check(st)
         return {
@@ -321,7 +362,8 @@ class Solver:
     def warm_start_data(self, v, x_out, t_out, omega_scale=45.0):
         """Network inputs [nf][2][H][W] and targets [nf][1][H][W] (float32 device tensors)
         from a solution v of this problem (mfwh_warm_start_data)."""
-        _lib.check(_lib.load().mfwh_warm_start_data(self._handle, float(omega_scale), _as_ptr(v),
+        _lib.check(_lib.load().mfwh_warm_start_data(self._handle, float(omega_scale),
+                                                    _sized(v, self.values, "v"),
                                                     C.c_void_p(x_out.data_ptr()),
                                                     C.c_void_p(t_out.data_ptr())))
 
@@ -329,8 +371,8 @@ class Solver:
         """Write the network's initial iterate into v (mfwh_warm_start); returns (kept, ratio)
         with ratio = ||b - (v - S v)|| / ||b|| of the returned start."""
         ratio = C.c_double()
-        st = _lib.load().mfwh_warm_start(self._handle, net._h, float(omega_scale), _as_ptr(v),
-                                         C.byref(ratio))
+        st = _lib.load().mfwh_warm_start(self._handle, net._h, float(omega_scale),
+                                         _sized(v, self.values, "v"), C.byref(ratio))
         if st not in (_lib.OK, _lib.ERR_NOT_CONVERGED):
             _lib.check(st)
         return st == _lib.OK, ratio.value
@@ -352,7 +394,7 @@ class Solver:
 
     def residual(self, v):
         r = np.zeros(self.nf)
-        _lib.check(_lib.load().mfwh_residual(self._handle, _as_ptr(v), _dptr(r)))
+        _lib.check(_lib.load().mfwh_residual(self._handle, _sized(v, self.values, "v"), _dptr(r)))
         return r
 
     def last_timing(self):

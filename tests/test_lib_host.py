@@ -426,3 +426,45 @@ def test_entry_points_reject_null_handles_and_bad_arguments_before_any_cuda_call
     assert lib.mfwh_cnn_param_count(null) == 0
     lib.mfwh_destroy(null)
     lib.mfwh_cnn_destroy(null)
+
+
+def test_binding_refuses_short_buffers_before_any_call(lib):
+    """The library reads and writes nf x points values through each solution or forcing
+    pointer and cannot check a buffer's size; the binding refuses a short buffer with
+    ValueError before it calls the library (a full-size buffer with no handle reaches the
+    library, which answers MFWH_ERR_INVALID_ARG)."""
+    import ctypes as C
+    n, nf = (16, 12), 2
+    points = 17 * 13
+    full = np.zeros(nf * points)
+    short = np.zeros(nf * points - 1)
+    with pytest.raises(ValueError):
+        M.make_problem(n, (1.0, 1.0), [5.5, 9.3], forcing=short)
+    with pytest.raises(ValueError):
+        M.make_problem(n, (1.0, 1.0), [5.5, 9.3], c2_field=np.ones(points - 1))
+    with pytest.raises(ValueError):
+        M.make_problem(n, (1.0, 1.0), [5.5, 9.3], filter_mode=_lib.FILTER_USER,
+                       user_params=np.ones(5))
+    prob, keep = M.make_problem(n, (1.0, 1.0), [5.5, 9.3], forcing=full,
+                                c2_field=np.ones(points))
+    with pytest.raises(ValueError):
+        M.mfwh_residual_noalloc(prob, short, full, stream=0)
+    with pytest.raises(ValueError):
+        M.mfwh_residual_noalloc(prob, full, short, stream=0)
+
+    s = object.__new__(M.Solver)            # a solver without a handle: no GPU needed
+    s._handle, s.nf, s.values = C.c_void_p(), nf, nf * points
+    calls = [lambda b: s.set_forcing(b), lambda b: s.apply_Pi(full, b),
+             lambda b: s.apply_Pi(b, full), lambda b: s.solve_fpi(b, 1),
+             lambda b: s.solve_gmres(b), lambda b: s.solve_refined(b),
+             lambda b: s.solve_relaxed(b), lambda b: s.residual(b)]
+    for call in calls:
+        with pytest.raises(ValueError):
+            call(short)
+        with pytest.raises(_lib.MfwhError) as e:
+            call(full)
+        assert e.value.status == _lib.ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        M.solve_batch([s, s], [full])
+    with pytest.raises(ValueError):
+        M.solve_batch([s], [short])
