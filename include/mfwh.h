@@ -350,8 +350,10 @@ mfwh_status mfwh_autotune(const mfwh_problem* prob, void* stream, int* time_bloc
  * A small convolutional network maps one frequency's forcing (and its frequency, as a second
  * constant channel) to an initial iterate V_m^0.  L layers of 3 x 3 "same" convolutions
  * (zero padding) with bias and ReLU after every layer but the last; in_channels inputs,
- * `channels` hidden channels, one output.  Activations and weights in BF16, products summed in
- * FP32 on the tensor cores (mma.sync); gradients, master weights and Adam state in FP32.
+ * `channels` hidden channels, one output.  Activations and weights in BF16; the convolutions
+ * and their input gradients sum products in FP32 on the 5th-generation tensor cores
+ * (tcgen05.mma, accumulators in tensor memory), the weight gradients on the FP32 CUDA cores;
+ * gradients, master weights and Adam state in FP32.
  * Images are device float32 arrays [B][C][H][W] (x fastest).  Parameters, flat FP32: for each
  * layer l, w_l[Cout][Cin][3][3] (cross-correlation: out[y][x] += w[dy][dx] in[y+dy-1][x+dx-1])
  * then b_l[Cout].  The network owns its workspace, which grows with B * H * W. */

@@ -362,10 +362,11 @@ class Solver:
     def warm_start_data(self, v, x_out, t_out, omega_scale=45.0):
         """Network inputs [nf][2][H][W] and targets [nf][1][H][W] (float32 device tensors)
         from a solution v of this problem (mfwh_warm_start_data)."""
-        _lib.check(_lib.load().mfwh_warm_start_data(self._handle, float(omega_scale),
-                                                    _sized(v, self.values, "v"),
-                                                    C.c_void_p(x_out.data_ptr()),
-                                                    C.c_void_p(t_out.data_ptr())))
+        vp = _sized(v, self.values, "v")
+        CNN._need(x_out, 2 * self.values, "x_out")
+        CNN._need(t_out, self.values, "t_out")
+        xp, tp = CNN._f32(x_out), CNN._f32(t_out)
+        _lib.check(_lib.load().mfwh_warm_start_data(self._handle, float(omega_scale), vp, xp, tp))
 
     def warm_start(self, net, v, omega_scale=45.0):
         """Write the network's initial iterate into v (mfwh_warm_start); returns (kept, ratio)
@@ -452,18 +453,34 @@ class CNN:
         return (p, g) if grads else p
 
     @staticmethod
+    def _need(t, count, what):
+        """The library reads or writes count values through a tensor's pointer and cannot check
+        its size: refuse a shorter tensor."""
+        if _numel(t) < count:
+            raise ValueError(f"{what}: {_numel(t)} values, {count} needed")
+
+    @staticmethod
     def _f32(t):
         import torch
         if t.dtype != torch.float32 or not t.is_contiguous() or not t.is_cuda:
             raise TypeError("expected a contiguous float32 CUDA tensor")
         return C.c_void_p(t.data_ptr())
 
-    def forward(self, x, y):
+    def _images(self, x):
+        if len(x.shape) != 4 or x.shape[1] != self.in_channels:
+            raise ValueError(f"x: expected [B][{self.in_channels}][H][W], got {tuple(x.shape)}")
         B, _, H, W = x.shape
+        return int(B), int(H), int(W)
+
+    def forward(self, x, y):
+        B, H, W = self._images(x)
+        self._need(y, B * H * W, "y")
         _lib.check(_lib.load().mfwh_cnn_forward(self._h, self._f32(x), B, H, W, self._f32(y)))
 
     def train_step(self, x, target, mask, lr):
-        B, _, H, W = x.shape
+        B, H, W = self._images(x)
+        self._need(target, B * H * W, "target")
+        self._need(mask, H * W, "mask")
         loss = C.c_float()
         _lib.check(_lib.load().mfwh_cnn_train_step(self._h, self._f32(x), self._f32(target),
                                                    self._f32(mask), B, H, W, float(lr),

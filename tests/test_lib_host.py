@@ -468,3 +468,31 @@ def test_binding_refuses_short_buffers_before_any_call(lib):
         M.solve_batch([s, s], [full])
     with pytest.raises(ValueError):
         M.solve_batch([s], [short])
+
+    # the warm-start network's images and the training pairs (float32 device tensors: a
+    # full-size host tensor passes the size check and is then refused as not on the device)
+    torch = pytest.importorskip("torch")
+    net = object.__new__(M.CNN)
+    net._h, net.in_channels = C.c_void_p(), 2
+    B, H, W = 3, 13, 17
+    x = torch.zeros((B, 2, H, W), dtype=torch.float32)
+    y = torch.zeros((B, 1, H, W), dtype=torch.float32)
+    mask = torch.zeros((H, W), dtype=torch.float32)
+    with pytest.raises(ValueError):
+        net.forward(torch.zeros((B, 3, H, W), dtype=torch.float32), y)
+    with pytest.raises(ValueError):
+        net.forward(x, y[:, :, :-1])
+    with pytest.raises(TypeError):
+        net.forward(x, y)
+    with pytest.raises(ValueError):
+        net.train_step(x, y, mask[:-1], 1e-3)
+    with pytest.raises(TypeError):
+        net.train_step(x, y, mask, 1e-3)
+    xo = torch.zeros((nf, 2, 13, 17), dtype=torch.float32)
+    to = torch.zeros((nf, 1, 13, 17), dtype=torch.float32)
+    with pytest.raises(ValueError):
+        s.warm_start_data(full, xo[:, :1], to)
+    with pytest.raises(ValueError):
+        s.warm_start_data(full, xo, to[:1])
+    with pytest.raises(TypeError):
+        s.warm_start_data(full, xo, to)
