@@ -189,7 +189,9 @@ typedef struct {
 /* ---- host-only set-up arithmetic (no GPU needed) ------------------------------ */
 
 /* Full set-up of a problem without touching a GPU (time step, omega~, N_{p,m},
- * quadrature, filter parameters, B and B^{-1}).  Time step reading: dt_stab =
+ * quadrature, filter parameters, B and B^{-1}): the first two lines of Algorithm 1, with
+ * Section "Time-step determination", eq. omegaImplicit, eq. TbarDef, eq. DefNI, Algorithm 2
+ * or eq. origParamAdjust, eq. pDefQ and eq. filterA.  Time step reading: dt_stab =
  * 1/(c_max sqrt(sum 1/h_i^2)); N_t = ceil(N_p (2 pi/omega_1) / (cfl dt_stab));
  * dt = 2 sin(pi N_p / N_t) / omega_1 so that omega~_1 N_t dt = 2 pi N_p.
  * Returns MFWH_ERR_SINGULAR if B has 1-norm condition number > 1e12 or the
@@ -200,8 +202,10 @@ mfwh_status mfwh_plan(const mfwh_problem* prob, mfwh_setup* out);
  * of a planned problem, written to w_out[(n_t+1) * nf] (host, row n, column m). */
 mfwh_status mfwh_plan_weights(const mfwh_problem* prob, double* w_out, int64_t capacity);
 
-/* Multigrid hierarchy of an implicit problem (MFWH_TIME_IMPLICIT), without a GPU: *levels
- * levels, cells[l][0..2] the cells per axis of level l (x first; 0 for z in 2D), *coarse the
+/* Multigrid hierarchy of an implicit problem (MFWH_TIME_IMPLICIT; the paper solves each implicit
+ * step by multigrid, Section "Numerical results and O(N) scaling"; this hierarchy is the
+ * library's own), without a GPU: *levels levels, cells[l][0..2] the cells per axis of
+ * level l (x first; 0 for z in 2D), *coarse the
  * first level solved by one CTA in shared memory (levels of at most 5000 points).  cells has
  * room for 16 levels.  MFWH_ERR_INVALID_ARG if the problem is invalid, its grid does not
  * halve down to such a level, or it takes the fourth-order operator on a grid of at most 5000
@@ -224,11 +228,14 @@ mfwh_status mfwh_opt_parameters(int nf, const double* omega, int n_p, int n_t,
 
 /* ---- device calls ------------------------------------------------------------ */
 
-/* Plan the problem and allocate its device workspace on the current CUDA device.
- * stream: cudaStream_t all work is issued on (NULL = legacy default stream). */
+/* Plan the problem (the set-up of Algorithm 1, as mfwh_plan) and allocate its device workspace
+ * on the current CUDA device.  prob->forcing (host or device) and prob->c2_field are copied.
+ * stream: cudaStream_t all work is issued on (NULL = legacy default stream).  *out is NULL on
+ * failure (MFWH_ERR_INVALID_ARG, MFWH_ERR_SINGULAR, MFWH_ERR_NOMEM or MFWH_ERR_CUDA). */
 mfwh_status mfwh_create(const mfwh_problem* prob, void* stream, mfwh_handle_t* out);
 
-/* Replace the forcing f_m: host or device [nf][points].  Ordered on the handle's stream. */
+/* Replace the forcings f_m of eq. MultipleHelmholtz: host or device [nf][points], copied.
+ * Ordered on the handle's stream. */
 mfwh_status mfwh_set_forcing(mfwh_handle_t h, const double* forcing);
 
 /* One application of the MFWH map (the loop body of Algorithm 1):
@@ -432,10 +439,11 @@ mfwh_status mfwh_residual(mfwh_handle_t h, const double* v, double* r_out);
 mfwh_status mfwh_residual_noalloc(const mfwh_problem* prob, const double* forcing,
                                   const double* v, double* r_out, void* stream);
 
-/* Copy of the handle's set-up. */
+/* Copy of the handle's set-up (the quantities of Algorithm 1's set-up, as mfwh_plan). */
 mfwh_status mfwh_get_setup(mfwh_handle_t h, mfwh_setup* out);
 
-/* Timing of the most recent mfwh_apply_Pi / mfwh_solve_fpi / mfwh_solve_gmres /
+/* Measurement (no counterpart in the paper).  Timing of the most recent mfwh_apply_Pi /
+ * mfwh_solve_fpi / mfwh_solve_gmres /
  * mfwh_residual call, measured with CUDA events on the handle's stream:
  * step_ms = device time of the leapfrog+filter step kernels (the N_t launches of
  * every Pi application, the initial W^0 kernel excluded), step_launches = how
@@ -445,7 +453,8 @@ mfwh_status mfwh_get_setup(mfwh_handle_t h, mfwh_setup* out);
 mfwh_status mfwh_last_timing(mfwh_handle_t h, double* step_ms, int64_t* step_launches,
                              int64_t* total_launches);
 
-/* Multigrid statistics of an implicit handle (MFWH_TIME_IMPLICIT), accumulated over every
+/* Multigrid statistics of an implicit handle (MFWH_TIME_IMPLICIT; the paper reports multigrid
+ * cycles per wave solve in Section "Numerical results and O(N) scaling"), accumulated over every
  * step solve since the handle was created or the counters were last reset:
  * solves = step solves, cycles = V-cycles applied (a solve whose start already meets
  * mg_tol applies none), unconverged = solves that reached mg_max_cycles above mg_tol.
@@ -480,6 +489,8 @@ mfwh_status mfwh_debug_bounds(mfwh_handle_t h, int64_t* count, int64_t* index, i
 /* Release the handle and its device workspace (waits for its stream). */
 void mfwh_destroy(mfwh_handle_t h);
 
+/* Error reporting (no counterpart in the paper): the message of the last failed call on this
+ * thread (valid until the next call on it), and a fixed description of a status code. */
 const char* mfwh_last_error(void);
 const char* mfwh_status_string(mfwh_status s);
 
