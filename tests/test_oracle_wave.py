@@ -207,6 +207,26 @@ def test_spectrum_of_S_is_mu_d():
     assert np.max(np.abs(ev.imag)) < 1e-10
 
 
+def test_resonant_frequency_leaves_a_unit_eigenvalue():
+    """A frequency at a discrete eigenvalue, omega_1 = lambda_h of the (1, 1) Dirichlet mode,
+    makes the discrete Helmholtz operator singular.  At the MFWH level the mode's adjusted
+    eigenvalue equals omega~_1 (the same map sends lambda_h to lambda~ and omega_1 to
+    omega~_1), and mu_d(omega~_1) = 1 (Theorem 3, constraints eq. constraintsT), so S has the
+    eigenvalue 1 and A = I - S is singular: the fixed-point system has no unique solution.
+    Moving omega_1 off the eigenvalue by 1 % keeps every eigenvalue of S away from 1."""
+    g = W.Grid((6, 6), (1.0, 1.0))
+    _, lam2 = W.dirichlet_mode(g, (1, 1))
+    for shift, resonant in ((1.0, True), (1.01, False)):
+        omega = [math.sqrt(lam2) * shift, 9.3]
+        wl = inputs.gaussian_workload("t", (6, 6), 2, omega, 200.0, 11)
+        p = W.make_problem(g, omega, wl.forcing, filter_mode=F.FILTER_TRADITIONAL)
+        gap = np.min(np.abs(np.linalg.eigvals(_dense_S(p)) - 1.0))
+        if resonant:
+            assert gap < 1e-9, gap
+        else:
+            assert gap > 1e-3, gap
+
+
 # ---------------------------------------------------------------------------
 # GMRES, FPI rate and the residual
 # ---------------------------------------------------------------------------
