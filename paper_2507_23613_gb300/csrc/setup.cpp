@@ -131,6 +131,19 @@ struct CosineSum {
   }
 };
 
+// N_{p,m} = floor(T_f / T_m) = floor(N_p omega_m / omega_1) (eq. TbarDef) for the given
+// frequencies, exactly: their floating-point quotient can round up to an integer that the
+// exact ratio stays just below.  The quotient's floor is corrected by comparing N_p omega_m
+// with k omega_1 in long double, where both products are exact while N_p and k stay below
+// 2^11 (at most 53 + 11 significant bits).
+int period_count(int n_p, double omega_m, double omega_1) {
+  long k = (long)std::floor(n_p * (omega_m / omega_1));
+  const long double num = (long double)n_p * (long double)omega_m;
+  while (k > 0 && (long double)k * (long double)omega_1 > num) --k;
+  while ((long double)(k + 1) * (long double)omega_1 <= num) ++k;
+  return (int)k;
+}
+
 }  // namespace
 
 void trapezoid_weights(int n_t, double dt, int nf, const double* t_fm, double* sigma) {
@@ -163,7 +176,7 @@ mfwh_status optimise_parameters(int nf, const double* omega, int n_p, int n_t, i
   std::vector<int> n_pm(nf);
   double t_f = 0.0;
   for (int m = 0; m < nf; ++m) {
-    n_pm[m] = (int)std::floor(n_p * (omega[m] / omega[0]));
+    n_pm[m] = period_count(n_p, omega[m], omega[0]);
     t_fm[m] = n_pm[m] * (2.0 * kPi / omega[m]);
     t_f = std::max(t_f, t_fm[m]);
   }
@@ -454,7 +467,7 @@ mfwh_status plan_problem(const mfwh_problem* p, Plan* out, double c2_field_max) 
     s.omega_tilde[m] = std::acos(c) / dt;
   }
   for (int m = 0; m < nf; ++m) {
-    s.n_pm[m] = (int)std::floor(p->n_p * (s.omega_tilde[m] / s.omega_tilde[0]));
+    s.n_pm[m] = period_count(p->n_p, s.omega_tilde[m], s.omega_tilde[0]);
     s.t_fm[m] = s.n_pm[m] * (2.0 * kPi / s.omega_tilde[m]);
   }
   std::vector<double> sigma((size_t)(n_t + 1) * nf);

@@ -496,3 +496,19 @@ def test_binding_refuses_short_buffers_before_any_call(lib):
         s.warm_start_data(full, xo, to[:1])
     with pytest.raises(TypeError):
         s.warm_start_data(full, xo, to)
+
+
+def test_period_counts_exact_at_a_rounding_corner():
+    """eq. TbarDef: N_{p,m} = floor(N_p omega_m / omega_1) of the given frequencies.  With
+    omega_3 the largest double below 3 omega_1, the floating-point quotient rounds to 3 while
+    the exact ratio stays below it, so N_{p,3} = 2 for N_p = 1.  The library's Algorithm 2
+    then matches the oracle's (exact rational floor): Lambda, N_lambda and the parameters."""
+    from fractions import Fraction
+    b, a = 9.677471780157282, 29.032415340471843
+    assert a / b == 3.0 and Fraction(a) < 3 * Fraction(b)
+    om = [b, 1.7 * b, a]
+    params, lam, nl = M.opt_parameters(om, 1, 200)
+    o = F.opt_parameters_discrete(om, 1, 200)
+    assert list(o.n_pm) == [1, 1, 2]
+    assert nl == o.n_lambda and abs(lam - o.lam_max) <= 1e-13 * o.lam_max
+    np.testing.assert_allclose(params, o.params, atol=1e-10 * np.max(np.abs(o.params)))

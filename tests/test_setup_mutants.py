@@ -38,9 +38,17 @@ MUTANTS = {
     "trapezoid_after_end_weight": (
         "0.5 * dt * (1.0 - beta) * (1.0 - beta);", "0.5 * dt * (1.0 - beta);",
         "weight at t_{k+1}, eq. DefNI"),
-    "optimiser_period_ceil": (
-        "n_pm[m] = (int)std::floor(n_p * (omega[m] / omega[0]));",
-        "n_pm[m] = (int)std::ceil(n_p * (omega[m] / omega[0]));", "floor in N_{p,m}, eq. TbarDef"),
+    "optimiser_period_without_n_p": (
+        "n_pm[m] = period_count(n_p, omega[m], omega[0]);",
+        "n_pm[m] = period_count(1, omega[m], omega[0]);", "N_{p,m} = floor(N_p T_1 / T_m), eq. TbarDef"),
+    # (a slip in one of period_count's two correction loops is corrected by the other)
+    "period_count_rounded_quotient": (
+        "  return (int)k;\n}", "  return (int)std::floor(n_p * (omega_m / omega_1));\n}",
+        "N_{p,m} from the rounded quotient (the library's earlier form), eq. TbarDef"),
+    "period_count_rounded_products": (
+        "while (k > 0 && (long double)k * (long double)omega_1 > num) --k;",
+        "while (k > 0 && (long double)(k * omega_1) > num) --k;",
+        "exact comparison for the floor of N_p omega_m / omega_1, eq. TbarDef"),
     "optimiser_sine_sign": (
         "fs[m].g[n] = wgt * std::sin(omega[m] * t);", "fs[m].g[n] = -wgt * std::sin(omega[m] * t);",
         "sine component function, eq. compFuncs"),
@@ -90,8 +98,8 @@ MUTANTS = {
         "double c = (1.0 - 0.5 * beta * x * x) / (1.0 + alpha * x * x);",
         "double c = (1.0 - beta * x * x) / (1.0 + alpha * x * x);", "eq. omegaImplicit"),
     "period_counts_unadjusted": (
-        "s.n_pm[m] = (int)std::floor(p->n_p * (s.omega_tilde[m] / s.omega_tilde[0]));",
-        "s.n_pm[m] = (int)std::floor(p->n_p * (p->omega[m] / p->omega[0]));",
+        "s.n_pm[m] = period_count(p->n_p, s.omega_tilde[m], s.omega_tilde[0]);",
+        "s.n_pm[m] = period_count(p->n_p, p->omega[m], p->omega[0]);",
         "N_{p,m} from omega~, eq. TbarDef"),
     "period_length_unadjusted": (
         "s.t_fm[m] = s.n_pm[m] * (2.0 * kPi / s.omega_tilde[m]);",
@@ -127,6 +135,10 @@ extern "C" int shim_plan(const mfwh_problem* p, mfwh_setup* out, double* w, long
   std::memcpy(w, P.w.data(), sizeof(double) * P.w.size());
   return 0;
 }
+extern "C" int shim_opt(int nf, const double* omega, int n_p, int n_t, double* params,
+                        double* lam_max, int* n_lambda) {
+  return (int)mfwh::optimise_parameters(nf, omega, n_p, n_t, 20, 2.0, params, lam_max, n_lambda);
+}
 """
 
 # (grid cells, lengths, omega, N_p, c_hi, order, time stepping, filter mode)
@@ -155,17 +167,48 @@ def _oracle(case):
                         order=order, time_stepping=ts)
 
 
-def _plan(fn, case):
+# Algorithm 2 alone (optimise_parameters) on frequencies given as they are: the second case
+# sits at a rounding corner of eq. TbarDef, where omega_3 is the largest double below
+# 3 omega_1, so the floating-point quotient omega_3 / omega_1 rounds to 3 while the exact
+# ratio, and so N_{p,3} = floor(N_p omega_3 / omega_1) for N_p = 1, stays below (N_{p,3} = 2).
+_B, _A = 9.677471780157282, 29.032415340471843
+OPT_CASES = [([5.5, 9.3, 14.2], 2, 300), ([_B, 1.7 * _B, _A], 1, 200)]
+
+
+def _plan(lib, case):
     prob, keep = _problem(case)
     s = _lib.Setup()
     w = np.zeros(1 << 20)
-    st = fn(C.byref(prob), C.byref(s), w.ctypes.data_as(C.POINTER(C.c_double)), w.size)
+    st = lib.shim_plan(C.byref(prob), C.byref(s), w.ctypes.data_as(C.POINTER(C.c_double)),
+                       w.size)
     return st, s, w
 
 
-def _disagreement(fn, case, o):
+def _opt(lib, case):
+    omega, n_p, n_t = case
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    params = np.zeros((om.size, 3))
+    lam, nl = C.c_double(), C.c_int()
+    dp = C.POINTER(C.c_double)
+    st = lib.shim_opt(om.size, om.ctypes.data_as(dp), n_p, n_t, params.ctypes.data_as(dp),
+                      C.byref(lam), C.byref(nl))
+    return st, params, lam.value, nl.value
+
+
+def _opt_disagreement(lib, case, o):
+    st, params, lam, nl = _opt(lib, case)
+    if st != 0:
+        return f"status {st}"
+    if nl != o.n_lambda or abs(lam - o.lam_max) > 1e-13 * o.lam_max:
+        return "Lambda"
+    if np.max(np.abs(params - o.params)) > 1e-10 * np.max(np.abs(o.params)):
+        return "parameters"
+    return None
+
+
+def _disagreement(lib, case, o):
     """None if the set-up agrees with the oracle's, else what differs."""
-    st, s, w = _plan(fn, case)
+    st, s, w = _plan(lib, case)
     if st != 0:
         return f"status {st}"
     a = M.setup_arrays(s)
@@ -201,7 +244,10 @@ def _compile(name, src_text, out_dir):
     lib.shim_plan.restype = C.c_int
     lib.shim_plan.argtypes = [C.POINTER(_lib.Problem), C.POINTER(_lib.Setup),
                               C.POINTER(C.c_double), C.c_longlong]
-    return lib.shim_plan
+    lib.shim_opt.restype = C.c_int
+    lib.shim_opt.argtypes = [C.c_int, C.POINTER(C.c_double), C.c_int, C.c_int,
+                             C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int)]
+    return lib
 
 
 @pytest.fixture(scope="module")
@@ -223,14 +269,25 @@ def builds(tmp_path_factory):
 
 @pytest.fixture(scope="module")
 def oracle_setups():
-    return [_oracle(c) for c in CASES]
+    return ([_oracle(c) for c in CASES],
+            [F.opt_parameters_discrete(om, n_p, n_t) for om, n_p, n_t in OPT_CASES])
+
+
+def _all_disagreements(lib, oracle_setups):
+    plans, opts = oracle_setups
+    return ([_disagreement(lib, c, o) for c, o in zip(CASES, plans)]
+            + [_opt_disagreement(lib, c, o) for c, o in zip(OPT_CASES, opts)])
 
 
 def test_unmutated_setup_agrees_with_oracle_and_library(builds, oracle_setups):
     build.build()
-    lib = _lib.load()
-    for case, o in zip(CASES, oracle_setups):
-        assert _disagreement(builds[None], case, o) is None, case
+    _lib.load()
+    assert _all_disagreements(builds[None], oracle_setups) == [None] * (len(CASES) + len(OPT_CASES))
+    for case in OPT_CASES:
+        st, params, lam, nl = _opt(builds[None], case)
+        ref = M.opt_parameters(*case)
+        assert np.array_equal(params, ref[0]) and lam == ref[1] and nl == ref[2], case
+    for case in CASES:
         # the shim returns exactly what the library's own planner returns
         st, s, w = _plan(builds[None], case)
         prob, keep = _problem(case)
@@ -245,5 +302,4 @@ def test_unmutated_setup_agrees_with_oracle_and_library(builds, oracle_setups):
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_oracle_comparison_catches_setup_mutant(builds, oracle_setups, name):
-    found = [_disagreement(builds[name], c, o) for c, o in zip(CASES, oracle_setups)]
-    assert any(f is not None for f in found), name
+    assert any(f is not None for f in _all_disagreements(builds[name], oracle_setups)), name
