@@ -3,7 +3,8 @@
 The FP32 wave path (precision MFWH_PREC_FP32_KAHAN) advances the leapfrog scheme (eq.
 WaveSchemeA, first step eq. implicitFirstStep) in increment form with FP32 wave levels,
 D^{n+1} = D^n + kappa (c^2 Delta_h W^n - F^n), W^{n+1} = W^n + D^{n+1}, accumulates the
-filter sums (eq. pDefQ) as Kahan pairs, and solves B V = q in FP64.  This test writes that
+filter sums (eq. pDefQ) as Kahan pairs (or, in its blocked form, as plain float32 partial
+sums over each launch folded into the Kahan pairs), and solves B V = q in FP64.  This test writes that
 arithmetic out in numpy float32, operation by operation in the kernels' order (coefficients
 and weights rounded to float32 on the host; a fused multiply-add as the float32 rounding of
 its exact float64 value), and measures how far one map Pi lands from the FP64 oracle per
@@ -31,8 +32,11 @@ def _fma32(a, b, c):
             + np.asarray(c, np.float64)).astype(f32)
 
 
-def _pi_fp32(p, V, forced):
-    """One map Pi (or S for forced=False) in the FP32 path's arithmetic."""
+def _pi_fp32(p, V, forced, block=0):
+    """One map Pi (or S for forced=False) in the FP32 path's arithmetic.  block = 0: Kahan
+    update at every step (MFWH_PREC_FP32_KAHAN); block = T: plain float32 partial sums over
+    each launch of T steps, folded into the Kahan pair at the launch's end
+    (MFWH_PREC_FP32_BLOCKSUM)."""
     s = p.setup
     g = p.grid
     inner = g.interior()
@@ -45,6 +49,7 @@ def _pi_fp32(p, V, forced):
     wq = s.w.astype(f32)
     qs = np.stack([(wq[0, m] * w).astype(f32) for m in range(p.nf)])
     qc = np.zeros_like(qs)
+    part = np.zeros_like(qs)
     ff = p.forcing.astype(f32)
     inv_h2 = [1.0 / (h * h) for h in g.h]                # h listed x first; array axes reversed
     for n in range(s.n_t):
@@ -76,8 +81,18 @@ def _pi_fp32(p, V, forced):
         D[inner] = dn
         w = w.copy()
         w[inner] = wn
-        for m in range(p.nf):                            # Kahan update with w_{n+1,m}
-            sm, cm = qs[m][inner], qc[m][inner]
+        for m in range(p.nf):
+            if block:                                    # partial sum of the launch
+                part[m][inner] = _fma32(wq[n + 1, m], wn, part[m][inner])
+                if (n + 1) % block == 0 or n + 1 == s.n_t:     # fold at the launch's end
+                    sm, cm, x = qs[m][inner], qc[m][inner], part[m][inner]
+                    y = (x - cm).astype(f32)
+                    t = (sm + y).astype(f32)
+                    qc[m][inner] = ((t - sm) - y).astype(f32)
+                    qs[m][inner] = t
+                    part[m][inner] = 0.0
+                continue
+            sm, cm = qs[m][inner], qc[m][inner]          # Kahan update with w_{n+1,m}
             y = _fma32(wq[n + 1, m], wn, -cm)
             t = (sm + y).astype(f32)
             qc[m][inner] = ((t - sm) - y).astype(f32)
@@ -123,7 +138,10 @@ def test_fp32_arithmetic_stays_well_inside_the_gpu_tolerance(name, wl, n_p, c2):
     p = W.make_problem(g, wl.omega, wl.forcing, c2=c2, n_p=n_p,
                        filter_mode=F.FILTER_TRADITIONAL)
     v = _random_v(wl, 3)
+    blocks = (0, 16) if g.dim == 2 else (0, 4)           # the blocked FP32 kernels' depths
     for forced in (True, False):
-        err = _rel_err(_pi_fp32(p, v, forced), W.apply_Pi(p, v, forced=forced))
-        assert np.all(err <= TOL_PI32 / 4), (name, forced, err)
-        assert np.all(err > 1e-9), (name, forced, err)   # the model does round: not FP64
+        want = W.apply_Pi(p, v, forced=forced)
+        for block in blocks:
+            err = _rel_err(_pi_fp32(p, v, forced, block), want)
+            assert np.all(err <= TOL_PI32 / 4), (name, forced, block, err)
+            assert np.all(err > 1e-9), (name, forced, block, err)   # the model does round
