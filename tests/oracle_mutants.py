@@ -100,6 +100,9 @@ MUTANTS = {
     "laplacian_matrix4_ghost_sign": (
         "oracle.wave", "laplacian_matrix", "main[0] += 1.0", "main[0] -= 1.0",
         "odd-reflection ghost value folded into the first row, fourth order"),
+    "explicit_filter_no_diagonal_solve": (
+        "oracle.wave", "_filter_update", "((flat - off @ Vk) / np.diag(s.B)[:, None])",
+        "(flat - off @ Vk)", "division by B_mm in the explicit filter, footnote to eq. filterII"),
     # --- set-up (oracle/filters.py) -----------------------------------------------------------
     "adjusted_frequency_factor": (
         "oracle.filters", "adjusted_frequency", "(1.0 - 0.5 * beta * x * x)", "(1.0 - beta * x * x)",
@@ -175,6 +178,15 @@ MUTANTS = {
     "gauss_nodes_unscaled": (
         "oracle.filters", "opt_parameters_continuous", "nodes = [0.5 * tm * (x + 1.0) for tm in t_fm]",
         "nodes = [tm * (x + 1.0) for tm in t_fm]", "Gauss-Legendre nodes mapped to [0, T_{f,m}]"),
+    "component_scale": (
+        "oracle.filters", "_QuadratureBasis._eval", "wt = self.weights[m] * (2.0 / self.t_fm[m])",
+        "wt = self.weights[m] * (1.0 / self.t_fm[m])", "factor 2 / T_{f,m} of eq. compFuncs"),
+    "discrete_basis_first_weights": (
+        "oracle.filters", "opt_parameters_discrete", "[sigma[:, m] for m in range(omega.size)]",
+        "[sigma[:, 0] for m in range(omega.size)]", "each filter's own quadrature weights, eq. betadDefA"),
+    "gauss_weights_unscaled": (
+        "oracle.filters", "opt_parameters_continuous", "weights = [0.5 * tm * wx for tm in t_fm]",
+        "weights = [tm * wx for tm in t_fm]", "Gauss-Legendre weights mapped to [0, T_{f,m}]"),
     # --- warm-start network (oracle/cnn.py) ---------------------------------------------------
     "conv_flipped_kernel": (
         "oracle.cnn", "conv_same", 'np.einsum("oc,bchw->bohw", w[:, :, dy, dx], patch)',
